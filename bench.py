@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Throughput of the FP64 Taylor-Couette step on GB300: grid-point-steps/s.
+
+Workload: the 64 x 128 x 128 run with Boussinesq temperature and the dynamic
+CFL step (eta = 0.71, Re_i = 3000, Re_o = -1000, Ra = 1e4, Pr = 0.7), seeded
+divergence-free perturbation.  One step = one predictor-corrector step (two
+nonlinear evaluations, two radial stages, the dt policy and any refactoring).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 runs N independent replicas (the path has no exchange step), one rank
+per GPU under torchrun; value = all ranks' grid-point-steps / max rank time.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from inputs import WORKLOADS, psi_coefficients, temperature_coefficients  # noqa: E402
+
+WORKLOAD = "tc_fp64T_nr64_n128"
+METRIC = "grid-point-steps/s"
+# FP64 peak of the ALU roofline: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM
+# (2 DFMA/clk/SM); an FMA loop measured 1.19 TFLOP/s at ~1.99 GHz on this part.
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def config_of(wl, extra=None):
+    cfg = {"workload": f"{wl.name}: Nr={wl.Nr} Ntheta={wl.Ntheta} Nz={wl.Nz} eta={wl.eta} "
+                       f"Re_i={wl.Re_i} Re_o={wl.Re_o} Ra={wl.Ra} Pr={wl.Pr} "
+                       f"dt={'CFL dynamic' if wl.dt <= 0 else wl.dt}",
+           "grid_points": wl.points, "fields": 4 if wl.Ra else 3}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ oracle timing
+def oracle_throughput(wl, budget_s=20.0, max_steps=None):
+    """Time the FP64 oracle (scipy.fft transform mode) on this host's cores.
+
+    Returns (pt-steps/s, steps timed, seconds, cores, sample description).
+    """
+    from oracle import Model
+    t0 = time.perf_counter()
+    mdl = Model(wl, "fft")
+    X = mdl.initial_state(psi_coefficients(wl.seed, wl.mp, wl.kp),
+                          temperature_coefficients(wl.seed, wl.mp, wl.kp) if wl.Ra else None)
+    setup = time.perf_counter() - t0
+    dt_prev = 0.0
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        X, _, dt_prev, _ = mdl.step(X, wl.dt, dt_prev)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_steps and n >= max_steps):
+            break
+    cores = os.cpu_count()
+    sample = (f"{n} full steps of {wl.name} from its seeded initial state "
+              f"(oracle, scipy.fft transforms, LAPACK radial solves; set-up {setup:.1f} s excluded)")
+    return wl.points * n / el, n, el, cores, sample
+
+
+# ------------------------------------------------------- algorithmic flops
+def fft_flops(n):
+    """Nominal flops of a complex FFT of length n (5 n log2 n)."""
+    return 5.0 * n * math.log2(n)
+
+
+def kernel_flops(name, wl):
+    """Algorithmic FP64 flops of one launch of a hot kernel (None if not modelled)."""
+    nf = 4 if wl.Ra else 3
+    M, K = (wl.Ntheta - 1) // 3, (wl.Nz - 1) // 3
+    NM, NK = M + 1, 2 * K + 1
+    if name == "k_theta":
+        # per z-row: 2 nf inverse + 2 forward complex FFTs along theta (two real
+        # fields each), ~30 flops of products and curvature terms per point
+        return wl.Nr * wl.Nz * ((2 * nf + 2) * fft_flops(wl.Ntheta) + 30 * wl.Ntheta)
+    if name == "k_zinv":
+        # 3 fields per component and m column, plus the 9-point d/dr (72 flops/coeff)
+        return wl.Nr * nf * NM * (3 * fft_flops(wl.Nz) + 72 * NK)
+    if name == "k_zfwd":
+        return wl.Nr * nf * NM * fft_flops(wl.Nz)
+    return None
+
+
+def source_hash(names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1908_00587_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    ent = rec.get(kernel)
+    if not ent or ent.get("source_hash") != source_hash(ent.get("sources", [])):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    # bounded sample: about a minute of oracle steps whatever K is
+    value, n, el, cores, sample = oracle_throughput(wl, budget_s=60.0, max_steps=args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": n, "warmup": 0, "ms_per_step": 1e3 * el / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(wl, {"sample_of_requested_steps": args.steps}),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__ as g
+    if rank == 0:
+        g.build()
+    if dist:
+        dist.barrier()
+    from paper_1908_00587_gb300 import tc
+
+    wl = WORKLOADS[args.workload]
+    run = tc.Run.from_workload(wl)
+    stream = torch.cuda.current_stream()
+    run.set_stream(stream.cuda_stream)
+    psi = psi_coefficients(wl.seed, wl.mp, wl.kp)
+    tco = temperature_coefficients(wl.seed, wl.mp, wl.kp) if wl.Ra else None
+    run.init_perturbation(psi, wl.amp, tco, wl.amp_T)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        run.step(1, wl.dt)
+    torch.cuda.synchronize()
+
+    tc.tc_set_option(run.ctx, "timing", 1)
+    tc.tc_reset_timing(run.ctx)
+    launches0 = tc.tc_get_info(run.ctx).launches
+    clocks = Clocks(local)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)               # evict L2 between timed steps
+        starts[i].record(stream)
+        run.step(1, wl.dt)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    clk = clocks.stop()
+    launches = tc.tc_get_info(run.ctx).launches - launches0
+    timing = tc.tc_get_timing(run.ctx)
+    tc.tc_set_option(run.ctx, "timing", 0)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = wl.points * args.steps * world / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers: state in from pinned
+    # host memory, one step, state out to pinned host memory
+    host = torch.empty(run.shape, dtype=torch.complex128, pin_memory=True).numpy()
+    run.get_state(host)
+    ne = min(args.e2e_steps, args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        run.set_state(host)
+        run.step(1, wl.dt)
+        run.get_state(host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    state_bytes = int(np.prod(run.shape)) * 16
+    e2e = {"value": wl.points * ne * world / e2e_s, "unit": METRIC,
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+           "steps": ne}
+
+    # roofline of the dominant kernel (FP64-ALU bound: see the design doc)
+    dom = max(timing, key=lambda k: timing[k][1])
+    nl, ms = timing[dom]
+    fl = kernel_flops(dom, wl)
+    roof = {"kernel": dom, "bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+            "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM",
+            "share_of_step": ms / total_ms if not dist else None,
+            "ms_per_launch": ms / nl}
+    if fl is not None:
+        ach = fl / (ms / nl * 1e-3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / FP64_PEAK_TFLOPS,
+                     "flops_per_launch": fl})
+    else:
+        roof.update({"achieved": None, "frac": None})
+    tr = traffic_for(dom)
+    roof["traffic"] = tr
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in sorted(timing.items())}
+
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": config_of(wl, {"l2": "flushed between timed steps (512 MiB write)",
+                                     "parallelism": f"replicas x{world}",
+                                     "stated_error": "rel L2 <= 1e-10 vs FP64 oracle"}),
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "kernels": kernels}
+    run.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, el, cores, sample = oracle_throughput(wl, budget_s=15.0)
+        line["cpu_baseline"] = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * tc.h -- C ABI of libtc, a GB300 (sm_103a) implementation of the
+ * pseudospectral time step for Taylor-Couette flow (nsCouette, arXiv:1908.00587).
+ *
+ * Method (paper Sec. 2.1): Fourier-Galerkin in theta and z (z periodic), 9-point
+ * finite differences in r on Chebyshev-Gauss-Lobatto points, a semi-implicit
+ * predictor-corrector with dynamic time step, optional Boussinesq temperature
+ * with a radial temperature drop and gravity along z.  The linear terms are
+ * solved independently per Fourier mode (Sec. 2.2); the nonlinear terms are
+ * formed on the 3/2-padded physical grid.
+ *
+ * Units: gap d = r_o - r_i = 1, time d^2/nu, velocity nu/d; r_i = eta/(1-eta).
+ * Walls: u_theta(r_i) = Re_i, u_theta(r_o) = Re_o, T(r_i) = +1/2, T(r_o) = -1/2.
+ *
+ * Spectral state layout (all entry points, host or device): complex128 as
+ * interleaved (re, im) doubles, C order [field][r][m][kk], with
+ *   field = u_r, u_theta, u_z (, T when Ra != 0),
+ *   r  = 0..Nr-1 ascending from the inner wall,
+ *   m  = 0..M,  M = floor((Ntheta-1)/3)   (Hermitian half in theta),
+ *   kk = 0..2K, K = floor((Nz-1)/3), axial index k = kk for kk <= K and
+ *        kk - (2K+1) otherwise (FFT order); axial wavenumber 2 pi k / Lz.
+ * The m = 0 column must satisfy u(0,-k) = conj(u(0,k)).
+ *
+ * Conventions: every call returns a tc_status; nothing is thrown across the
+ * ABI.  Errors are not sticky except TC_ERR_CUDA, after which only tc_destroy
+ * is valid on that context.  Caller buffers are never retained after a call
+ * returns.  All device work runs on the context's stream (default: the legacy
+ * default stream; see tc_set_stream); calls that return data to the host
+ * synchronise that stream.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_ctx tc_ctx;
+
+typedef enum {
+  TC_OK = 0,
+  TC_ERR_ARG = 1,          /* invalid argument (size, range, null pointer)      */
+  TC_ERR_CUDA = 2,         /* CUDA runtime error; context is poisoned            */
+  TC_ERR_OOM = 3,          /* device allocation failed or over memory budget     */
+  TC_ERR_NONFINITE = 4,    /* NaN/Inf found in the state                         */
+  TC_ERR_CFL = 5,          /* CFL number above the configured limit              */
+  TC_ERR_STATE = 6,        /* state violates the m = 0 Hermitian symmetry        */
+  TC_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up                 */
+  TC_ERR_UNSUPPORTED = 8   /* size or option not supported                       */
+} tc_status;
+
+/* Global quantities of the current state (tc_diagnostics).
+ *   t          simulated time
+ *   dt         last time step used
+ *   E          (1/2) int |u|^2 dV
+ *   E_pert     same for u minus the basic state of tc_create
+ *   torque_i/o 2 pi Lz r^2 (d u_theta/dr - u_theta/r) of the mean flow at r_i / r_o
+ *   P_wall     power the walls put into the fluid
+ *   eps        viscous dissipation int 2 S:S dV
+ *   buoy_work  Gr int u_z T dV  (Gr = Ra/Pr)
+ *   Nu_i/o     mean dT/dr at the wall over that of the conductive state (Sec. 4)
+ *   div_max    max |div u| over all stored coefficients
+ *   div_rms    (int |div u|^2 dV / V)^(1/2)
+ *   cfl        CFL number of the last step's start-of-step state times dt
+ */
+typedef struct {
+  double t, dt, E, E_pert, torque_i, torque_o, P_wall, eps, buoy_work;
+  double Nu_i, Nu_o, div_max, div_rms, cfl;
+} tc_diag;
+
+/* Sizes derived by tc_create. */
+typedef struct {
+  int Nr, Ntheta, Nz, M, K, nfields;
+  long long coeffs_per_field;   /* Nr * (M+1) * (2K+1) */
+  long long state_bytes;        /* nfields * coeffs_per_field * 16 */
+  size_t device_bytes;          /* device memory held by the context */
+  long long launches;           /* kernels launched since tc_create */
+} tc_info;
+
+/* Device time of one kernel accumulated while option "timing" is 1. */
+typedef struct {
+  char name[32];
+  long long launches;   /* launches timed since the last tc_reset_timing */
+  double ms;            /* summed CUDA-event time of those launches */
+} tc_kernel_time;
+
+/* Create a run (Sec. 2.1: one input defines points, modes, rotation rates).
+ * Nr >= 9 radial points (walls included); Ntheta, Nz physical (3/2-padded)
+ * sizes of the form 2^a 3^b 5^c, Ntheta even and >= 4, Nz >= 4, both <= 1024;
+ * 0 < eta < 1; Lz > 0; Pr > 0 when Ra != 0.  Temperature is carried only when
+ * Ra != 0.  The state starts as the discrete basic state: circular Couette
+ * flow, and with Ra != 0 the conductive temperature and its steady axial flow.
+ * Errors: TC_ERR_ARG, TC_ERR_UNSUPPORTED, TC_ERR_OOM, TC_ERR_CUDA. */
+tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz,
+                    double Re_i, double Re_o, double Ra, double Pr, tc_ctx **out);
+
+/* Free everything the context holds.  Accepts NULL. */
+tc_status tc_destroy(tc_ctx *ctx);
+
+/* Set a numeric option.  Keys:
+ *   "cfl"       CFL coefficient of the dynamic step (default 0.25)
+ *   "dt_max"    largest dynamic step (default 1e-3)
+ *   "cfl_limit" abort a step with TC_ERR_CFL above this CFL number (default 0 = off)
+ *   "check"     1: report NaN/Inf produced by tc_step (default 1)
+ *   "timing"    1: bracket every kernel launch with CUDA events on the
+ *               context's stream (tc_get_timing); 0: off (default)
+ * Errors: TC_ERR_ARG for an unknown key or out-of-range value. */
+tc_status tc_set_option(tc_ctx *ctx, const char *key, double value);
+
+/* Use a caller-owned cudaStream_t for all device work (NULL: default stream). */
+tc_status tc_set_stream(tc_ctx *ctx, void *cuda_stream);
+
+/* Sizes of the run. */
+tc_status tc_get_info(const tc_ctx *ctx, tc_info *out);
+
+/* Copy a spectral state in (where = 0: host pointer, 1: device pointer), layout
+ * above.  The input is checked on the device before it replaces the state:
+ * TC_ERR_NONFINITE on NaN/Inf, TC_ERR_STATE if the m = 0 column's asymmetry
+ * exceeds 1e-12 of the largest coefficient; otherwise the m = 0 column is
+ * symmetrised (k > 0 kept) and the state replaced.
+ * The simulated time is reset to 0 and the dynamic step forgets its history. */
+tc_status tc_set_state(tc_ctx *ctx, const void *spec, int where);
+
+/* Copy the current spectral state out (where = 0 host, 1 device). */
+tc_status tc_get_state(const tc_ctx *ctx, void *spec, int where);
+
+/* Copy the pressure of the last corrector stage out: complex128 [r][m][kk].
+ * The (0,0) mode is left zero (the mean pressure is not solved for). */
+tc_status tc_get_pressure(const tc_ctx *ctx, void *spec, int where);
+
+/* Set the state to the basic state plus a divergence-free perturbation
+ * u' = curl(psi) (Sec. 2.1: divergence-free initial conditions exciting
+ * selected Fourier modes).
+ *   psi    host, complex128 [3][mp+1][2kp+1] raw coefficients of (psi_r,
+ *          psi_theta, psi_z), axial index natural (-kp..kp); each component
+ *          gets the radial profile (1-x^2)^2, x = 2(r-r_i)-1; the m = 0 column
+ *          is made Hermitian (k > 0 kept); u' is zeroed at the wall nodes and
+ *          scaled so that max over the physical grid of |u'| equals amp.
+ *   tcoef  host, complex128 [mp+1][2kp+1] or NULL: T' = (1-x^2) x tcoef, scaled
+ *          so that max |T'| = amp_T (ignored when Ra == 0 or amp_T <= 0).
+ * Requires mp <= M and kp <= K. */
+tc_status tc_init_perturbation(tc_ctx *ctx, const double *psi, int mp, int kp,
+                               double amp, const double *tcoef, double amp_T);
+
+/* Advance nsteps predictor-corrector steps (Sec. 2.1).  dt > 0: fixed step;
+ * dt <= 0: dynamic step from the CFL bound of each start-of-step state,
+ * dt* = min(dt_max, cfl / max(|u_r|/dr, |u_theta|/(r dtheta), |u_z|/dz)),
+ * taken at once when smaller than the current step and only above 1.1x the
+ * current step when larger.  dt_used (host, nullable) receives nsteps steps.
+ * Errors: TC_ERR_ARG, TC_ERR_NONFINITE, TC_ERR_CFL, TC_ERR_CUDA. */
+tc_status tc_step(tc_ctx *ctx, int nsteps, double dt, double *dt_used);
+
+/* Diagnostics of the current state (one small device->host copy). */
+tc_status tc_diagnostics(tc_ctx *ctx, tc_diag *out);
+
+/* Stage entry points, used to check each stage on its own.
+ * tc_nonlinear: dealiased nonlinear terms [N_r, N_theta, N_z(, N_T)] of a
+ *   spectral state given on the device (layout of the state), written to a
+ *   device buffer of the same size; *cfl_rate (host, nullable) receives
+ *   max(|u_r|/dr, |u_theta|/(r dtheta), |u_z|/dz) over the physical grid.
+ * tc_stage_solve: one implicit stage.  rhs (device) holds the explicit
+ *   right-hand side in +- form [R+, R-, R_z(, R_T)] at every radial node
+ *   (R+- = R_r +- i R_theta); the solution of (I/dt - L/2) X = R - grad p,
+ *   div X = 0 at both walls, with the wall values, is written to x_out
+ *   (device, primitive fields) and the pressure to p_out (device, nullable). */
+tc_status tc_nonlinear(tc_ctx *ctx, const void *state_dev, void *n_dev, double *cfl_rate);
+tc_status tc_stage_solve(tc_ctx *ctx, const void *rhs_dev, double dt, void *x_out_dev,
+                         void *p_out_dev);
+
+/* Per-kernel device times recorded while "timing" is on: fills up to cap
+ * entries of out (host) and sets *count.  Synchronises the stream. */
+tc_status tc_get_timing(tc_ctx *ctx, tc_kernel_time *out, int cap, int *count);
+/* Forget the recorded times. */
+tc_status tc_reset_timing(tc_ctx *ctx);
+
+/* Human-readable name of a status. */
+const char *tc_status_string(tc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_H */

@@ -10,4 +10,5 @@ from .seeded import (  # noqa: F401
     psi_coefficients,
     temperature_coefficients,
     ensemble_members,
+    random_state,
 )

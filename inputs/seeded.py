@@ -120,3 +120,21 @@ def ensemble_members(n: int = 64, seed: int = 5000) -> list:
             eta=float(etas[i]), Lz=2 * math.pi / 3.16, Re_i=float(res[i]),
             amp=1e-3, mp=4, kp=4, seed=seed + i, steps=100, dt=1e-3))
     return out
+
+
+def random_state(seed: int, nf: int, Nr: int, M: int, K: int, scale=1.0) -> np.ndarray:
+    """Random spectral coefficients of real fields, complex128 (nf, Nr, M+1, 2K+1).
+
+    Axis 3 is in FFT order (0..K, -K..-1).  Entries are N(0,1) draws in C
+    order (re, im) times ``scale`` (scalar or per-field sequence); the m = 0
+    column is then given the structure every real field has, u(0,-k) =
+    conj(u(0,k)) with a real (0,0) entry, so the array is a valid input.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = rng.standard_normal((nf, Nr, M + 1, 2 * K + 1, 2))
+    a = d[..., 0] + 1j * d[..., 1]
+    a *= np.asarray(scale, dtype=np.float64).reshape(-1, 1, 1, 1) if np.ndim(scale) else scale
+    for k in range(1, K + 1):
+        a[:, :, 0, 2 * K + 1 - k] = np.conj(a[:, :, 0, k])
+    a[:, :, 0, 0] = a[:, :, 0, 0].real
+    return a

@@ -1,0 +1,196 @@
+// Batched complex FFTs of length N = 2^a 3^b 5^c held in shared memory.
+//
+// Self-sorting (Stockham) mixed-radix passes with radices 8, 4, 2, 3, 5: pass
+// p of radix R with stride Ns (product of the earlier radices) takes, for each
+// butterfly j < N/R, the R inputs x[j + q N/R], multiplies input q by
+// w^(q (j mod Ns)) with w = exp(s 2 pi i / (Ns R)), applies a length-R DFT and
+// stores output p at (j div Ns) Ns R + (j mod Ns) + p Ns.  Ping-pong between
+// two shared buffers; every thread of the CTA cooperates on the whole batch.
+// s = -1 is the forward transform, s = +1 the (unnormalised) inverse.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tc_internal.h"
+
+namespace tc {
+
+template <typename T>
+struct V2t;
+template <>
+struct V2t<double> {
+  using type = double2;
+};
+template <>
+struct V2t<float> {
+  using type = float2;
+};
+
+template <typename V>
+__device__ __forceinline__ V cadd(V a, V b) {
+  return {a.x + b.x, a.y + b.y};
+}
+template <typename V>
+__device__ __forceinline__ V csub(V a, V b) {
+  return {a.x - b.x, a.y - b.y};
+}
+template <typename V>
+__device__ __forceinline__ V cmul(V a, V b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename V>
+__device__ __forceinline__ V cmulc(V a, V b) {
+  return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+// a * (S i), S = +-1
+template <int S, typename V>
+__device__ __forceinline__ V mul_si(V a) {
+  return S > 0 ? V{-a.y, a.x} : V{a.y, -a.x};
+}
+
+// Length-R DFTs, out_p = sum_q v_q exp(S 2 pi i p q / R), in place.
+template <int S, typename V>
+__device__ __forceinline__ void dft2(V *v) {
+  V a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <int S, typename V>
+__device__ __forceinline__ void dft4(V *v) {
+  V t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  V t2 = cadd(v[1], v[3]), t3 = mul_si<S>(csub(v[1], v[3]));
+  v[0] = cadd(t0, t2);
+  v[2] = csub(t0, t2);
+  v[1] = cadd(t1, t3);
+  v[3] = csub(t1, t3);
+}
+
+template <int S, typename V>
+__device__ __forceinline__ void dft8(V *v) {
+  using T = decltype(v[0].x);
+  const T h = (T)0.70710678118654752440;  // sqrt(2)/2
+  V a[4], b[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    a[q] = cadd(v[q], v[q + 4]);
+    b[q] = csub(v[q], v[q + 4]);
+  }
+  // b_q *= exp(S 2 pi i q / 8)
+  {
+    V x = b[1];
+    b[1] = V{h * (x.x - (T)S * x.y), h * ((T)S * x.x + x.y)};
+    b[2] = mul_si<S>(b[2]);
+    x = b[3];
+    b[3] = V{h * (-x.x - (T)S * x.y), h * ((T)S * x.x - x.y)};
+  }
+  dft4<S>(a);
+  dft4<S>(b);
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    v[2 * p] = a[p];
+    v[2 * p + 1] = b[p];
+  }
+}
+
+template <int S, typename V>
+__device__ __forceinline__ void dft3(V *v) {
+  using T = decltype(v[0].x);
+  const T s3 = (T)0.86602540378443864676;  // sqrt(3)/2
+  V t = cadd(v[1], v[2]);
+  V u = csub(v[1], v[2]);
+  V a = V{v[0].x - (T)0.5 * t.x, v[0].y - (T)0.5 * t.y};
+  V b = mul_si<S>(V{s3 * u.x, s3 * u.y});
+  v[0] = cadd(v[0], t);
+  v[1] = cadd(a, b);
+  v[2] = csub(a, b);
+}
+
+template <int S, typename V>
+__device__ __forceinline__ void dft5(V *v) {
+  using T = decltype(v[0].x);
+  const T c1 = (T)0.30901699437494742410;   // cos(2 pi/5) = (sqrt5 - 1)/4
+  const T c2 = (T)-0.80901699437494742410;  // cos(4 pi/5) = -(sqrt5 + 1)/4
+  const T s1 = (T)0.95105651629515357212;   // sin(2 pi/5)
+  const T s2 = (T)0.58778525229247312917;   // sin(4 pi/5)
+  V t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  V t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  V a1 = V{v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y};
+  V a2 = V{v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y};
+  V b1 = mul_si<S>(V{s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y});
+  V b2 = mul_si<S>(V{s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y});
+  v[0] = cadd(v[0], cadd(t1, t2));
+  v[1] = cadd(a1, b1);
+  v[4] = csub(a1, b1);
+  v[2] = cadd(a2, b2);
+  v[3] = csub(a2, b2);
+}
+
+template <int R, int S, typename V>
+__device__ __forceinline__ void dftR(V *v) {
+  if constexpr (R == 2) dft2<S>(v);
+  if constexpr (R == 3) dft3<S>(v);
+  if constexpr (R == 4) dft4<S>(v);
+  if constexpr (R == 5) dft5<S>(v);
+  if constexpr (R == 8) dft8<S>(v);
+}
+
+// One Stockham pass over `batch` transforms stored `bstride` apart.
+// tw[t] = exp(-2 pi i t / N).
+template <int R, int S, typename V>
+__device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__restrict__ dst,
+                                              int N, int Ns, int batch, int bstride,
+                                              const V *__restrict__ tw) {
+  const int nb = N / R;
+  const int total = nb * batch;
+  const int twstep = N / (Ns * R);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int b = t / nb;
+    const int j = t - b * nb;
+    const V *s = src + b * bstride;
+    V *d = dst + b * bstride;
+    const int k = j % Ns;
+    V v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = s[j + q * nb];
+    if (Ns > 1) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        const V w = tw[q * k * twstep];
+        v[q] = (S < 0) ? cmul(v[q], w) : cmulc(v[q], w);
+      }
+    }
+    dftR<R, S>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int p = 0; p < R; ++p) d[base + p * Ns] = v[p];
+  }
+}
+
+// Full transform of `batch` sequences held in buffer a (b is scratch of the
+// same size).  Returns the buffer holding the result.  All threads of the CTA
+// must call it; it ends with a __syncthreads().
+template <int S, typename V>
+__device__ V *fft_batch(V *a, V *b, const FFTPlan &pl, int batch, int bstride,
+                        const V *__restrict__ tw) {
+  int Ns = 1;
+  for (int p = 0; p < pl.npass; ++p) {
+    const int R = pl.radix[p];
+    switch (R) {
+      case 8: stockham_pass<8, S>(a, b, pl.n, Ns, batch, bstride, tw); break;
+      case 4: stockham_pass<4, S>(a, b, pl.n, Ns, batch, bstride, tw); break;
+      case 2: stockham_pass<2, S>(a, b, pl.n, Ns, batch, bstride, tw); break;
+      case 3: stockham_pass<3, S>(a, b, pl.n, Ns, batch, bstride, tw); break;
+      default: stockham_pass<5, S>(a, b, pl.n, Ns, batch, bstride, tw); break;
+    }
+    __syncthreads();
+    V *t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+}  // namespace tc

@@ -1,0 +1,623 @@
+// Linear stage: per-Fourier-mode radial Helmholtz / Poisson solves.
+//
+// Paper Sec. 2.2: the Fourier modes are independent in the linear terms (the
+// MPI code distributes them in slabs and OpenMP threads loop over them; the
+// GPU code uses its own linear-algebra kernels).  Here one thread owns one
+// radial system; consecutive threads take consecutive modes, so every load of
+// a radial node is coalesced across systems in the [r][m][k] layout.
+//
+// Scheme (predictor-corrector of Sec. 2.1, Crank-Nicolson weight c = 1/2):
+//   R   = X^n/dt + (1-c) L X^n + (1-c) N^n + c N        (N = N^n or N(X*))
+//   p0  : L p0 = div R inside, D1 p0 = 0 at both walls
+//   u0  : (I/dt - c L+-) u+- = R+- - (D1 p0 -+ (m/r) p0),
+//         (I/dt - c L) u_z = R_z - i beta p0, no-slip rows
+//   u   = u0 + a_i u_a + a_o u_b with the 2x2 influence matrix chosen so that
+//         div u = 0 at both wall nodes (u_a, u_b from unit wall fluxes of p).
+// u+- = u_r +- i u_theta decouples the viscous terms:
+//   L+- = D2 + D1/r - (m+-1)^2/r^2 - beta^2, L = D2 + D1/r - m^2/r^2 - beta^2.
+// The band LU (no pivoting; the operators are diagonally dominant or, for the
+// pressure, checked against the pivoted dense solve in the tests) stores 8
+// sub-diagonals, the inverse diagonal and 8 super-diagonals per row.
+#include <cuda_runtime.h>
+
+#include "tc_internal.h"
+
+namespace tc {
+
+namespace {
+
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ double2 operator*(double a, double2 b) { return {a * b.x, a * b.y}; }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__device__ __forceinline__ double2 mul_i(double2 a) { return {-a.y, a.x}; }      // i a
+__device__ __forceinline__ double2 div_2i(double2 a) { return {0.5 * a.y, -0.5 * a.x}; }  // a/(2i)
+
+__device__ __forceinline__ void axpy(double &acc, double l, double x) { acc -= l * x; }
+__device__ __forceinline__ void axpy(double2 &acc, double l, double2 x) {
+  acc.x -= l * x.x;
+  acc.y -= l * x.y;
+}
+__device__ __forceinline__ double scale(double a, double s) { return a * s; }
+__device__ __forceinline__ double2 scale(double2 a, double s) { return {a.x * s, a.y * s}; }
+
+__device__ __forceinline__ int kval(int kk, int K, int NK) { return kk <= K ? kk : kk - NK; }
+
+// Row j of an operator, entries at columns j-8 .. j+8 (a[0..16]).
+// kind 0: Poisson (Neumann D1 rows at the walls), 1: Helmholtz (identity rows).
+__device__ __forceinline__ void build_row(const Radial &rad, int Nr, int j, int kind, double q2,
+                                          double beta2, double idt, double ck, double *a) {
+#pragma unroll
+  for (int e = 0; e < kBandW; ++e) a[e] = 0.0;
+  const int st = rad.s0[j];
+  if (j == 0 || j == Nr - 1) {
+    if (kind == 1) {
+      a[kBand] = 1.0;
+    } else {
+#pragma unroll
+      for (int t = 0; t < kStencil; ++t) a[st + t - j + kBand] = rad.D1[j * kStencil + t];
+    }
+    return;
+  }
+  const double ir = rad.inv_r[j];
+#pragma unroll
+  for (int t = 0; t < kStencil; ++t) {
+    const double l = rad.D2[j * kStencil + t] + rad.D1[j * kStencil + t] * ir;
+    a[st + t - j + kBand] = (kind == 1) ? -ck * l : l;
+  }
+  const double d = q2 * ir * ir + beta2;
+  if (kind == 1)
+    a[kBand] += idt + ck * d;
+  else
+    a[kBand] -= d;
+}
+
+// In-place band LU (Doolittle, no pivoting) of one operator, rows built on the fly.
+__device__ void band_factor(const Radial &rad, int Nr, int kind, double q2, double beta2,
+                            double idt, double ck, double *LU, int nop, int o) {
+  for (int j = 0; j < Nr; ++j) {
+    double a[kBandW];
+    build_row(rad, Nr, j, kind, q2, beta2, idt, ck, a);
+#pragma unroll
+    for (int e = 0; e < kBand; ++e) {
+      const int i = j - kBand + e;
+      if (i < 0) continue;
+      const double l = a[e] * LU[((long long)i * kBandW + kBand) * nop + o];
+      a[e] = l;
+#pragma unroll
+      for (int f = 1; f <= kBand; ++f) {
+        if (e + f < kBandW) a[e + f] -= l * LU[((long long)i * kBandW + kBand + f) * nop + o];
+      }
+    }
+    a[kBand] = 1.0 / a[kBand];
+#pragma unroll
+    for (int e = 0; e < kBandW; ++e) LU[((long long)j * kBandW + e) * nop + o] = a[e];
+  }
+}
+
+// Solve with stored factors, in place on x[j * xs], j = 0..Nr-1.
+template <typename V>
+__device__ void band_solve(const double *__restrict__ LU, int nop, int o, int Nr, V *x,
+                           long long xs) {
+  V w[kBand];
+#pragma unroll
+  for (int e = 0; e < kBand; ++e) w[e] = V{};
+  for (int j = 0; j < Nr; ++j) {
+    V acc = x[j * xs];
+    const double *row = LU + (long long)j * kBandW * nop + o;
+#pragma unroll
+    for (int e = 0; e < kBand; ++e) axpy(acc, row[e * nop], w[e]);
+#pragma unroll
+    for (int e = 0; e < kBand - 1; ++e) w[e] = w[e + 1];
+    w[kBand - 1] = acc;
+    x[j * xs] = acc;
+  }
+#pragma unroll
+  for (int e = 0; e < kBand; ++e) w[e] = V{};
+  for (int j = Nr - 1; j >= 0; --j) {
+    V acc = x[j * xs];
+    const double *row = LU + (long long)j * kBandW * nop + o;
+#pragma unroll
+    for (int f = 1; f <= kBand; ++f) axpy(acc, row[(kBand + f) * nop], w[f - 1]);
+    acc = scale(acc, row[kBand * nop]);
+#pragma unroll
+    for (int f = kBand - 1; f > 0; --f) w[f] = w[f - 1];
+    w[0] = acc;
+    x[j * xs] = acc;
+  }
+}
+
+__global__ void k_factor_poisson(LinParams p) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= p.nopP || o == 0) return;   // (0,0) has no pressure solve
+  const int m = o / (p.sz.K + 1), ak = o % (p.sz.K + 1);
+  const double beta = p.alpha * ak;
+  band_factor(p.rad, p.sz.Nr, 0, (double)m * m, beta * beta, 0.0, 0.0, p.LUP, p.nopP, o);
+}
+
+__global__ void k_factor_helm(LinParams p, const DevScalars *sc) {
+  if (!sc->refactor) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.nopH + p.nopT) return;
+  const double idt = 1.0 / sc->dt;
+  const int K1 = p.sz.K + 1;
+  if (t < p.nopH) {
+    const int q = t / K1, ak = t % K1;
+    const double beta = p.alpha * ak;
+    band_factor(p.rad, p.sz.Nr, 1, (double)q * q, beta * beta, idt, kCN, p.LUH, p.nopH, t);
+  } else {
+    const int o = t - p.nopH;
+    const int m = o / K1, ak = o % K1;
+    const double beta = p.alpha * ak;
+    band_factor(p.rad, p.sz.Nr, 1, (double)m * m, beta * beta, idt, kCN * p.kappaT, p.LUT,
+                p.nopT, o);
+  }
+}
+
+// Homogeneous solutions and the inverse influence matrix, per (m, |k|).
+__global__ void k_influence(LinParams p, const DevScalars *sc) {
+  if (!sc->refactor) return;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= p.nopP || o == 0) return;
+  const int Nr = p.sz.Nr, K1 = p.sz.K + 1, nop = p.nopP;
+  const int m = o / K1, ak = o % K1;
+  const Radial &rad = p.rad;
+  const long long fs = (long long)Nr * nop;
+  double *F = p.infl;   // [8][Nr][nop]
+  auto at = [&](int f, int j) -> double & { return F[f * fs + (long long)j * nop + o]; };
+  const int oHp = (m + 1) * K1 + ak, oHm = (m >= 1 ? m - 1 : 1) * K1 + ak, oHz = m * K1 + ak;
+  for (int s = 0; s < 2; ++s) {
+    for (int j = 0; j < Nr; ++j) at(s, j) = (j == (s == 0 ? 0 : Nr - 1)) ? 1.0 : 0.0;
+    band_solve<double>(p.LUP, nop, o, Nr, &at(s, 0), nop);
+    for (int j = 0; j < Nr; ++j) {
+      double up = 0.0, um = 0.0, z = 0.0;
+      if (j > 0 && j < Nr - 1) {
+        const int st = rad.s0[j];
+        double d1p = 0.0;
+#pragma unroll
+        for (int t = 0; t < kStencil; ++t) d1p += rad.D1[j * kStencil + t] * at(s, st + t);
+        const double mp = m * at(s, j) * rad.inv_r[j];
+        up = -(d1p - mp);
+        um = -(d1p + mp);
+        z = at(s, j);
+      }
+      at(2 + 2 * s, j) = up;
+      at(3 + 2 * s, j) = um;
+      at(6 + s, j) = z;
+    }
+    band_solve<double>(p.LUH, p.nopH, oHp, Nr, &at(2 + 2 * s, 0), nop);
+    band_solve<double>(p.LUH, p.nopH, oHm, Nr, &at(3 + 2 * s, 0), nop);
+    band_solve<double>(p.LUH, p.nopH, oHz, Nr, &at(6 + s, 0), nop);
+  }
+  // A[w][s] = div of homogeneous solution s at wall w (only u_r is non-zero
+  // next to the wall; the wall values themselves are zero)
+  double A[2][2];
+  for (int w = 0; w < 2; ++w) {
+    const int j = (w == 0) ? 0 : Nr - 1;
+    const int st = rad.s0[j];
+    for (int s = 0; s < 2; ++s) {
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 0; t < kStencil; ++t) {
+        const double ur = 0.5 * (at(2 + 2 * s, st + t) + at(3 + 2 * s, st + t));
+        acc += rad.D1[j * kStencil + t] * (rad.r[st + t] * ur);
+      }
+      A[w][s] = acc * rad.inv_r[j];
+    }
+  }
+  const double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+  const double id = 1.0 / det;
+  p.Ainv[0 * nop + o] = A[1][1] * id;
+  p.Ainv[1 * nop + o] = -A[0][1] * id;
+  p.Ainv[2 * nop + o] = -A[1][0] * id;
+  p.Ainv[3 * nop + o] = A[0][0] * id;
+}
+
+__global__ void k_dt_policy(DevScalars *sc, double dt_fixed, double cfl, double dt_max,
+                            double *dt_hist, int step) {
+  const double rate = __longlong_as_double((long long)sc->rate_bits);
+  sc->rate_last = rate;
+  sc->rate_bits = 0ull;
+  double dt;
+  if (dt_fixed > 0.0) {
+    dt = dt_fixed;
+  } else {
+    const double dt_star = (rate <= 0.0) ? dt_max : fmin(dt_max, cfl / rate);
+    const double prev = sc->dt_prev;
+    dt = (prev <= 0.0 || dt_star < prev || dt_star > 1.1 * prev) ? dt_star : prev;
+  }
+  sc->dt = dt;
+  sc->dt_prev = dt;
+  sc->refactor = (dt != sc->dt_factored) ? 1 : 0;
+  if (sc->refactor) sc->dt_factored = dt;
+  if (dt_hist) dt_hist[step] = dt;
+}
+
+// Y' = X/dt + (1-c) L X + (1-c) N, in +- form, at every node.
+__global__ void k_rhs(const double2 *__restrict__ X, const double2 *__restrict__ N,
+                      double2 *__restrict__ Yb, LinParams p, const DevScalars *sc) {
+  const Sizes &s = p.sz;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.S) return;
+  const int j = (int)(i / s.nmode);
+  const int mode = (int)(i - (long long)j * s.nmode);
+  const int m = mode / s.NK, kk = mode % s.NK;
+  const double beta = p.alpha * kval(kk, s.K, s.NK);
+  const double idt = 1.0 / sc->dt;
+  const double ir = p.rad.inv_r[j];
+  const int st = p.rad.s0[j];
+  const double *d1 = p.rad.D1 + j * kStencil, *d2 = p.rad.D2 + j * kStencil;
+  const double b2 = beta * beta, ir2 = ir * ir;
+  const double om = 1.0 - kCN;
+  // u+, u-
+  {
+    double2 D1p = {0, 0}, D2p = {0, 0}, D1m = {0, 0}, D2m = {0, 0};
+#pragma unroll
+    for (int t = 0; t < kStencil; ++t) {
+      const long long o = (long long)(st + t) * s.nmode + mode;
+      const double2 xr = X[o], xt = X[s.S + o];
+      const double2 xp = {xr.x - xt.y, xr.y + xt.x}, xm = {xr.x + xt.y, xr.y - xt.x};
+      D1p = D1p + d1[t] * xp;
+      D2p = D2p + d2[t] * xp;
+      D1m = D1m + d1[t] * xm;
+      D2m = D2m + d2[t] * xm;
+    }
+    const double2 xr = X[i], xt = X[s.S + i];
+    const double2 xp = {xr.x - xt.y, xr.y + xt.x}, xm = {xr.x + xt.y, xr.y - xt.x};
+    const double2 nr = N[i], nt = N[s.S + i];
+    const double2 np = {nr.x - nt.y, nr.y + nt.x}, nm = {nr.x + nt.y, nr.y - nt.x};
+    const double qp = (double)(m + 1) * (m + 1), qm = (double)(m - 1) * (m - 1);
+    const double2 Lp = D2p + ir * D1p - (qp * ir2 + b2) * xp;
+    const double2 Lm = D2m + ir * D1m - (qm * ir2 + b2) * xm;
+    Yb[i] = idt * xp + om * Lp + om * np;
+    Yb[s.S + i] = idt * xm + om * Lm + om * nm;
+  }
+  for (int c = 2; c < s.nf; ++c) {
+    double2 D1x = {0, 0}, D2x = {0, 0};
+#pragma unroll
+    for (int t = 0; t < kStencil; ++t) {
+      const double2 x = X[c * s.S + (long long)(st + t) * s.nmode + mode];
+      D1x = D1x + d1[t] * x;
+      D2x = D2x + d2[t] * x;
+    }
+    const double2 x = X[c * s.S + i];
+    const double kap = (c == 3) ? p.kappaT : 1.0;
+    const double2 L = kap * (D2x + ir * D1x - ((double)m * m * ir2 + b2) * x);
+    Yb[c * s.S + i] = idt * x + om * L + om * N[c * s.S + i];
+  }
+}
+
+// Explicit right-hand side R = Y' + c N of component comp at flat index i.
+__device__ __forceinline__ double2 rhs_pm(const double2 *Yb, const double2 *N, long long S,
+                                          long long i, int comp) {
+  const double2 y = Yb[comp * S + i];
+  if (comp == 0) {
+    const double2 nr = N[i], nt = N[S + i];
+    return y + kCN * double2{nr.x - nt.y, nr.y + nt.x};
+  }
+  if (comp == 1) {
+    const double2 nr = N[i], nt = N[S + i];
+    return y + kCN * double2{nr.x + nt.y, nr.y - nt.x};
+  }
+  return y + kCN * N[comp * S + i];
+}
+
+__global__ void k_poisson(const double2 *__restrict__ Yb, const double2 *__restrict__ N,
+                          double2 *__restrict__ P, LinParams p) {
+  const Sizes &s = p.sz;
+  const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mode >= s.nmode || mode == 0) return;
+  const int m = mode / s.NK, kk = mode % s.NK;
+  const int kv = kval(kk, s.K, s.NK);
+  const double beta = p.alpha * kv;
+  const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
+  const int Nr = s.Nr;
+  for (int j = 0; j < Nr; ++j) {
+    double2 b = {0.0, 0.0};
+    if (j > 0 && j < Nr - 1) {
+      const int st = p.rad.s0[j];
+      double2 acc = {0.0, 0.0};
+#pragma unroll
+      for (int t = 0; t < kStencil; ++t) {
+        const long long ii = (long long)(st + t) * s.nmode + mode;
+        const double2 rr = 0.5 * (rhs_pm(Yb, N, s.S, ii, 0) + rhs_pm(Yb, N, s.S, ii, 1));
+        acc = acc + (p.rad.D1[j * kStencil + t] * p.rad.r[st + t]) * rr;
+      }
+      const long long ij = (long long)j * s.nmode + mode;
+      const double2 rt = div_2i(rhs_pm(Yb, N, s.S, ij, 0) - rhs_pm(Yb, N, s.S, ij, 1));
+      const double2 rz = rhs_pm(Yb, N, s.S, ij, 2);
+      const double ir = p.rad.inv_r[j];
+      b = ir * acc + (m * ir) * mul_i(rt) + beta * mul_i(rz);
+    }
+    P[(long long)j * s.nmode + mode] = b;
+  }
+  band_solve<double2>(p.LUP, p.nopP, o, Nr, P + mode, s.nmode);
+}
+
+__global__ void k_helm(const double2 *__restrict__ Yb, const double2 *__restrict__ N,
+                       const double2 *__restrict__ P, double2 *__restrict__ U0, LinParams p) {
+  const Sizes &s = p.sz;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s.nf * s.nmode) return;
+  const int comp = t / s.nmode;
+  const int mode = t - comp * s.nmode;
+  const int m = mode / s.NK, kk = mode % s.NK;
+  const int kv = kval(kk, s.K, s.NK);
+  const int ak = kv < 0 ? -kv : kv;
+  const double beta = p.alpha * kv;
+  const int K1 = s.K + 1, Nr = s.Nr;
+  const long long S = s.S;
+  double2 *x = U0 + comp * S + mode;
+  const long long xs = s.nmode;
+  if (mode == 0) {
+    if (comp == 1) return;
+    double lo = 0.0, hi = 0.0;
+    if (comp == 0) {
+      lo = p.Re_i;
+      hi = p.Re_o;
+    } else if (comp == 3) {
+      lo = 0.5;
+      hi = -0.5;
+    }
+    for (int j = 0; j < Nr; ++j) {
+      double2 b;
+      if (j == 0) {
+        b = {lo, 0.0};
+      } else if (j == Nr - 1) {
+        b = {hi, 0.0};
+      } else if (comp == 0) {
+        const long long ij = (long long)j * s.nmode;
+        b = div_2i(rhs_pm(Yb, N, S, ij, 0) - rhs_pm(Yb, N, S, ij, 1));
+      } else {
+        b = rhs_pm(Yb, N, S, (long long)j * s.nmode, comp);
+      }
+      x[j * xs] = b;
+    }
+    if (comp == 0) {
+      band_solve<double2>(p.LUH, p.nopH, 1 * K1 + 0, Nr, x, xs);
+      // u+ = i u_theta, u- = -i u_theta (u_r = 0)
+      for (int j = 0; j < Nr; ++j) {
+        const double2 ut = x[j * xs];
+        x[j * xs] = mul_i(ut);
+        U0[S + (long long)j * s.nmode] = double2{ut.y, -ut.x};
+      }
+    } else if (comp == 2) {
+      band_solve<double2>(p.LUH, p.nopH, 0, Nr, x, xs);
+    } else {
+      band_solve<double2>(p.LUT, p.nopT, 0, Nr, x, xs);
+    }
+    return;
+  }
+  for (int j = 0; j < Nr; ++j) {
+    double2 b = {0.0, 0.0};
+    if (j > 0 && j < Nr - 1) {
+      const long long ij = (long long)j * s.nmode + mode;
+      b = rhs_pm(Yb, N, S, ij, comp);
+      if (comp < 3) {
+        const double2 pj = P[ij];
+        if (comp == 2) {
+          b = b - beta * mul_i(pj);
+        } else {
+          const int st = p.rad.s0[j];
+          double2 d1p = {0.0, 0.0};
+#pragma unroll
+          for (int q = 0; q < kStencil; ++q)
+            d1p = d1p + p.rad.D1[j * kStencil + q] * P[(long long)(st + q) * s.nmode + mode];
+          const double2 mp = (m * p.rad.inv_r[j]) * pj;
+          b = (comp == 0) ? b - (d1p - mp) : b - (d1p + mp);
+        }
+      }
+    }
+    x[j * xs] = b;
+  }
+  if (comp == 0) {
+    band_solve<double2>(p.LUH, p.nopH, (m + 1) * K1 + ak, Nr, x, xs);
+  } else if (comp == 1) {
+    band_solve<double2>(p.LUH, p.nopH, (m >= 1 ? m - 1 : 1) * K1 + ak, Nr, x, xs);
+  } else if (comp == 2) {
+    band_solve<double2>(p.LUH, p.nopH, m * K1 + ak, Nr, x, xs);
+  } else {
+    band_solve<double2>(p.LUT, p.nopT, m * K1 + ak, Nr, x, xs);
+  }
+}
+
+// Influence coefficients per mode: alpha = -Ainv [div u0 (r_i), div u0 (r_o)].
+__global__ void k_alpha(const double2 *__restrict__ U0, double2 *__restrict__ alpha, LinParams p) {
+  const Sizes &s = p.sz;
+  const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mode >= s.nmode || mode == 0) return;
+  const int m = mode / s.NK, kk = mode % s.NK;
+  const int kv = kval(kk, s.K, s.NK);
+  const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
+  double2 d[2];
+  for (int w = 0; w < 2; ++w) {
+    const int j = (w == 0) ? 0 : s.Nr - 1;
+    const int st = p.rad.s0[j];
+    double2 acc = {0.0, 0.0};
+#pragma unroll
+    for (int t = 0; t < kStencil; ++t) {
+      const long long ii = (long long)(st + t) * s.nmode + mode;
+      const double2 ur = 0.5 * (U0[ii] + U0[s.S + ii]);
+      acc = acc + p.rad.D1[j * kStencil + t] * (p.rad.r[st + t] * ur);
+    }
+    d[w] = p.rad.inv_r[j] * acc;
+  }
+  const int nop = p.nopP;
+  const double a00 = p.Ainv[o], a01 = p.Ainv[nop + o], a10 = p.Ainv[2 * nop + o],
+               a11 = p.Ainv[3 * nop + o];
+  alpha[mode] = double2{-(a00 * d[0].x + a01 * d[1].x), -(a00 * d[0].y + a01 * d[1].y)};
+  alpha[s.nmode + mode] =
+      double2{-(a10 * d[0].x + a11 * d[1].x), -(a10 * d[0].y + a11 * d[1].y)};
+}
+
+__global__ void k_correct(const double2 *__restrict__ U0, const double2 *__restrict__ P0,
+                          const double2 *__restrict__ alpha, double2 *__restrict__ Xout,
+                          double2 *__restrict__ Pout, LinParams p, DevScalars *sc) {
+  const Sizes &s = p.sz;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.S) return;
+  const int j = (int)(i / s.nmode);
+  const int mode = (int)(i - (long long)j * s.nmode);
+  const long long S = s.S;
+  double2 up = U0[i], um = U0[S + i], uz = U0[2 * S + i];
+  double2 pr = {0.0, 0.0};
+  if (mode != 0) {
+    const int m = mode / s.NK, kk = mode % s.NK;
+    const int kv = kval(kk, s.K, s.NK);
+    const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
+    const double beta = p.alpha * kv;
+    const double2 a = alpha[mode], b = alpha[s.nmode + mode];
+    const long long fs = (long long)s.Nr * p.nopP;
+    const long long jo = (long long)j * p.nopP + o;
+    const double *F = p.infl;
+    pr = P0[i];
+    pr = pr + F[0 * fs + jo] * a;
+    pr = pr + F[1 * fs + jo] * b;
+    up = up + F[2 * fs + jo] * a;
+    um = um + F[3 * fs + jo] * a;
+    up = up + F[4 * fs + jo] * b;
+    um = um + F[5 * fs + jo] * b;
+    // u_z of a homogeneous solution = -i beta zeta
+    uz = uz + (-beta * F[6 * fs + jo]) * mul_i(a);
+    uz = uz + (-beta * F[7 * fs + jo]) * mul_i(b);
+  }
+  const double2 xr = 0.5 * (up + um);
+  const double2 xt = div_2i(up - um);
+  Xout[i] = xr;
+  Xout[S + i] = xt;
+  Xout[2 * S + i] = uz;
+  bool bad = !(isfinite(xr.x) && isfinite(xr.y) && isfinite(xt.x) && isfinite(xt.y) &&
+               isfinite(uz.x) && isfinite(uz.y));
+  if (s.nf == 4) {
+    const double2 T = U0[3 * S + i];
+    Xout[3 * S + i] = T;
+    bad = bad || !(isfinite(T.x) && isfinite(T.y));
+  }
+  if (Pout) Pout[i] = pr;
+  if (bad) atomicOr(&sc->nonfinite, 1);
+}
+
+__global__ void k_check_finite(const double2 *__restrict__ X, long long n, DevScalars *sc) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = X[i];
+  if (!(isfinite(v.x) && isfinite(v.y))) atomicOr(&sc->nonfinite, 1);
+}
+
+// Largest magnitude, Hermitian defect of the m = 0 column and NaN/Inf of a
+// candidate state (tc_set_state), one thread per coefficient.
+__global__ void k_state_check(const double2 *__restrict__ X, Sizes s, DevScalars *sc) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double amax = 0.0, defect = 0.0;
+  bool bad = false;
+  if (i < (long long)s.nf * s.S) {
+    const double2 v = X[i];
+    bad = !(isfinite(v.x) && isfinite(v.y));
+    amax = fmax(fabs(v.x), fabs(v.y));
+    const long long col = i % s.nmode;     // m * NK + kk
+    if (col == 0) {
+      defect = fabs(v.y);
+    } else if (col <= s.K) {
+      const double2 w = X[i - col + (s.NK - col)];
+      defect = fmax(fabs(v.x - w.x), fabs(v.y + w.y));
+    }
+  }
+  if (bad) atomicOr(&sc->nonfinite, 1);
+  for (int o = 16; o > 0; o >>= 1) {
+    amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    defect = fmax(defect, __shfl_xor_sync(0xffffffffu, defect, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (amax == amax) atomicMax(&sc->chk_bits[0], (unsigned long long)__double_as_longlong(amax));
+    if (defect == defect)
+      atomicMax(&sc->chk_bits[1], (unsigned long long)__double_as_longlong(defect));
+  }
+}
+
+// u(0,-k) = conj(u(0,k)) (k > 0 kept), real (0,0), for every field and node.
+__global__ void k_symmetrise(double2 *__restrict__ X, Sizes s) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)s.nf * s.Nr * (s.K + 1);
+  if (t >= n) return;
+  const int k = (int)(t % (s.K + 1));
+  const long long fj = t / (s.K + 1);         // field * Nr + node
+  double2 *col = X + fj * s.nmode;            // m = 0 column of that node
+  if (k == 0) {
+    col[0].y = 0.0;
+  } else {
+    const double2 v = col[k];
+    col[s.NK - k] = double2{v.x, -v.y};
+  }
+}
+
+inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_factor_poisson(tc_ctx *c) {
+  LaunchScope ls(c, KFACTH);
+  k_factor_poisson<<<blocks(c->lin.nopP, 128), 128, 0, c->stream>>>(c->lin);
+}
+
+void launch_refactor(tc_ctx *c) {
+  const LinParams &p = c->lin;
+  {
+    LaunchScope ls(c, KFACTH);
+    k_factor_helm<<<blocks(p.nopH + p.nopT, 128), 128, 0, c->stream>>>(p, c->scal);
+  }
+  LaunchScope ls(c, KINFL);
+  k_influence<<<blocks(p.nopP, 128), 128, 0, c->stream>>>(p, c->scal);
+}
+
+void launch_dt_policy(tc_ctx *c, double dt_fixed, int step_index) {
+  LaunchScope ls(c, KDT);
+  k_dt_policy<<<1, 1, 0, c->stream>>>(c->scal, dt_fixed, c->cfl, c->dt_max,
+                                       step_index >= 0 ? c->dt_hist : nullptr,
+                                       step_index >= 0 ? step_index : 0);
+}
+
+void launch_rhs(tc_ctx *c, const double2 *X, const double2 *N0) {
+  LaunchScope ls(c, KRHS);
+  k_rhs<<<blocks(c->sz.S, 128), 128, 0, c->stream>>>(X, N0, c->Yb, c->lin, c->scal);
+}
+
+void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout) {
+  const Sizes &s = c->sz;
+  const LinParams &p = c->lin;
+  {
+    LaunchScope ls(c, KPOIS);
+    k_poisson<<<blocks(s.nmode, 64), 64, 0, c->stream>>>(c->Yb, N, c->P, p);
+  }
+  {
+    LaunchScope ls(c, KHELM);
+    k_helm<<<blocks((long long)s.nf * s.nmode, 64), 64, 0, c->stream>>>(c->Yb, N, c->P, c->U0,
+                                                                        p);
+  }
+  {
+    LaunchScope ls(c, KALPHA);
+    k_alpha<<<blocks(s.nmode, 128), 128, 0, c->stream>>>(c->U0, c->alpha_buf, p);
+  }
+  LaunchScope ls(c, KCORR);
+  k_correct<<<blocks(s.S, 128), 128, 0, c->stream>>>(c->U0, c->P, c->alpha_buf, Xout, Pout, p,
+                                                      c->scal);
+}
+
+void launch_state_check(tc_ctx *c, const double2 *X) {
+  LaunchScope ls(c, KCORR);
+  k_state_check<<<blocks((long long)c->sz.nf * c->sz.S, 256), 256, 0, c->stream>>>(X, c->sz,
+                                                                                 c->scal);
+}
+
+void launch_symmetrise(tc_ctx *c, double2 *X) {
+  LaunchScope ls(c, KCORR);
+  k_symmetrise<<<blocks((long long)c->sz.nf * c->sz.Nr * (c->sz.K + 1), 256), 256, 0,
+                 c->stream>>>(X, c->sz);
+}
+
+void launch_check_finite(tc_ctx *c, const double2 *X, long long n) {
+  k_check_finite<<<blocks(n, 256), 256, 0, c->stream>>>(X, n, c->scal);
+}
+
+}  // namespace tc

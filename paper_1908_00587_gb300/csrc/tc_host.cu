@@ -1,0 +1,807 @@
+// Host side of libtc: validation, radial tables, device memory, the step loop
+// and the C ABI entry points declared in include/tc.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tc_internal.h"
+
+using cplx = std::complex<double>;
+
+namespace tc {
+
+const char *const kKernelNames[KNUM] = {
+    "k_zinv", "k_theta", "k_zfwd", "k_dt_policy", "k_factor", "k_influence",
+    "k_rhs", "k_poisson", "k_helm", "k_alpha", "k_correct", "k_diag"};
+
+LaunchScope::LaunchScope(tc_ctx *c_, int id_) : c(c_), id(id_) {
+  c->launches++;
+  KernelTimer &t = c->timers[id];
+  t.launches++;
+  if (!c->timing) return;
+  if ((int)t.ev.size() < 2 * (t.used + 1)) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    t.ev.push_back(a);
+    t.ev.push_back(b);
+  }
+  cudaEventRecord(t.ev[2 * t.used], c->stream);
+}
+
+LaunchScope::~LaunchScope() {
+  if (!c->timing) return;
+  KernelTimer &t = c->timers[id];
+  cudaEventRecord(t.ev[2 * t.used + 1], c->stream);
+  t.used++;
+}
+
+FFTPlan make_plan(int n) {
+  FFTPlan p{};
+  p.n = n;
+  int e2 = 0, m = n;
+  while (m % 2 == 0) {
+    m /= 2;
+    ++e2;
+  }
+  std::vector<int> rs;
+  // as many radix-8 passes as possible; a remainder of 2^1 is folded into two
+  // radix-4 passes when that is possible (cheaper than a radix-2 pass)
+  int n8 = e2 / 3, rem = e2 % 3;
+  if (rem == 1 && n8 >= 1) {
+    --n8;
+    rs.push_back(4);
+    rs.push_back(4);
+  } else if (rem == 1) {
+    rs.push_back(2);
+  } else if (rem == 2) {
+    rs.push_back(4);
+  }
+  for (int i = 0; i < n8; ++i) rs.insert(rs.begin(), 8);
+  while (m % 3 == 0) {
+    rs.push_back(3);
+    m /= 3;
+  }
+  while (m % 5 == 0) {
+    rs.push_back(5);
+    m /= 5;
+  }
+  p.npass = (int)rs.size();
+  for (int i = 0; i < p.npass; ++i) p.radix[i] = rs[i];
+  return p;
+}
+
+namespace {
+
+bool smooth235(int n) {
+  if (n < 1) return false;
+  for (int f : {2, 3, 5})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+// Finite-difference weights at x0 on nodes x[0..n-1] for derivatives 0..2
+// (Fornberg, Math. Comp. 51 (1988): weights of the Lagrange interpolant's
+// derivatives, built by adding one node at a time).
+void fd_weights(double x0, const double *x, int n, double w[3][kStencil]) {
+  for (int d = 0; d < 3; ++d)
+    for (int j = 0; j < n; ++j) w[d][j] = 0.0;
+  w[0][0] = 1.0;
+  double c1 = 1.0, c4 = x[0] - x0;
+  for (int i = 1; i < n; ++i) {
+    const int mn = std::min(i, 2);
+    double c2 = 1.0;
+    const double c5 = c4;
+    c4 = x[i] - x0;
+    for (int j = 0; j < i; ++j) {
+      const double c3 = x[i] - x[j];
+      c2 *= c3;
+      if (j == i - 1) {
+        for (int d = mn; d >= 1; --d) w[d][i] = c1 * (d * w[d - 1][i - 1] - c5 * w[d][i - 1]) / c2;
+        w[0][i] = -c1 * c5 * w[0][i - 1] / c2;
+      }
+      for (int d = mn; d >= 1; --d) w[d][j] = (c4 * w[d][j] - d * w[d - 1][j]) / c3;
+      w[0][j] = c4 * w[0][j] / c3;
+    }
+    c1 = c2;
+  }
+}
+
+// Clenshaw-Curtis weights on N+1 Chebyshev-Gauss-Lobatto points of [-1, 1]:
+// w_j = (c_j/N) (1 - sum_{k=1}^{N/2} b_k cos(2 k j pi / N) / (4k^2 - 1)),
+// c_j = 1 at the ends and 2 inside, b_k = 1 for k = N/2 and 2 otherwise.
+std::vector<double> cc_weights(int Nr) {
+  const int N = Nr - 1;
+  std::vector<double> w(Nr);
+  for (int j = 0; j <= N; ++j) {
+    long double s = 1.0L;
+    for (int k = 1; k <= N / 2; ++k) {
+      const long double b = (2 * k == N) ? 1.0L : 2.0L;
+      const long long arg = (2LL * k * j) % (2LL * N);
+      s -= b * cosl(3.141592653589793238462643383279502884L * (long double)arg / (long double)N) /
+           (4.0L * k * k - 1.0L);
+    }
+    const long double cj = (j == 0 || j == N) ? 1.0L : 2.0L;
+    w[j] = (double)(cj / N * s);
+  }
+  return w;
+}
+
+// Dense solve with partial pivoting (set-up only: basic state).
+std::vector<double> dense_solve(std::vector<double> A, std::vector<double> b, int n) {
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[i * n + k]) > std::fabs(A[piv * n + k])) piv = i;
+    if (piv != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[piv * n + j]);
+      std::swap(b[k], b[piv]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const double l = A[i * n + k] / A[k * n + k];
+      if (l == 0.0) continue;
+      for (int j = k; j < n; ++j) A[i * n + j] -= l * A[k * n + j];
+      b[i] -= l * b[k];
+    }
+  }
+  std::vector<double> x(n);
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int j = i + 1; j < n; ++j) s -= A[i * n + j] * x[j];
+    x[i] = s / A[i * n + i];
+  }
+  return x;
+}
+
+std::vector<double2> twiddles(int n) {
+  std::vector<double2> t(n);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < n; ++i) {
+    const long double a = 2.0L * pi * (long double)i / (long double)n;
+    t[i] = double2{(double)cosl(a), (double)(-sinl(a))};
+  }
+  return t;
+}
+
+struct CudaError {
+  cudaError_t e;
+};
+
+inline void ck(cudaError_t e) {
+  if (e != cudaSuccess) throw CudaError{e};
+}
+
+template <typename T>
+T *dalloc(tc_ctx *c, size_t count) {
+  void *p = nullptr;
+  const size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw std::bad_alloc();
+  }
+  c->allocs.push_back(p);
+  c->device_bytes += bytes;
+  return static_cast<T *>(p);
+}
+
+// L(q) restricted to (m,k) = (0,0) with Dirichlet rows: dense Nr x Nr.
+std::vector<double> dense_lap00(const tc_ctx *c, double q) {
+  const int Nr = c->sz.Nr;
+  std::vector<double> A((size_t)Nr * Nr, 0.0);
+  for (int j = 0; j < Nr; ++j) {
+    if (j == 0 || j == Nr - 1) {
+      A[(size_t)j * Nr + j] = 1.0;
+      continue;
+    }
+    const int st = c->s0[j];
+    for (int t = 0; t < kStencil; ++t)
+      A[(size_t)j * Nr + st + t] = c->D2[j * kStencil + t] + c->D1[j * kStencil + t] / c->r[j];
+    A[(size_t)j * Nr + j] -= q * q / (c->r[j] * c->r[j]);
+  }
+  return A;
+}
+
+tc_status fail_cuda(tc_ctx *c, cudaError_t e) {
+  if (c) c->poisoned = true;
+  std::fprintf(stderr, "libtc: CUDA error %s\n", cudaGetErrorString(e));
+  return TC_ERR_CUDA;
+}
+
+void build_tables(tc_ctx *c) {
+  const int Nr = c->sz.Nr;
+  c->r.resize(Nr);
+  for (int j = 0; j < Nr; ++j)
+    c->r[j] = c->r_i + 0.5 * (1.0 - std::cos(M_PI * (double)j / (double)(Nr - 1)));
+  c->D1.assign((size_t)Nr * kStencil, 0.0);
+  c->D2.assign((size_t)Nr * kStencil, 0.0);
+  c->s0.resize(Nr);
+  for (int j = 0; j < Nr; ++j) {
+    const int st = std::min(std::max(j - kStencil / 2, 0), Nr - kStencil);
+    c->s0[j] = st;
+    double w[3][kStencil];
+    fd_weights(c->r[j], &c->r[st], kStencil, w);
+    for (int t = 0; t < kStencil; ++t) {
+      c->D1[j * kStencil + t] = w[1][t];
+      c->D2[j * kStencil + t] = w[2][t];
+    }
+  }
+  std::vector<double> cc = cc_weights(Nr);
+  c->w.resize(Nr);
+  c->dr_min.resize(Nr);
+  for (int j = 0; j < Nr; ++j) {
+    c->w[j] = 0.5 * cc[j];
+    const double lo = j > 0 ? c->r[j] - c->r[j - 1] : 1e300;
+    const double hi = j < Nr - 1 ? c->r[j + 1] - c->r[j] : 1e300;
+    c->dr_min[j] = std::min(lo, hi);
+  }
+}
+
+void build_base(tc_ctx *c) {
+  const int Nr = c->sz.Nr;
+  const long long S = c->sz.S;
+  c->base.assign((size_t)2 * c->sz.nf * S, 0.0);
+  auto put = [&](int f, const std::vector<double> &prof) {
+    for (int j = 0; j < Nr; ++j) c->base[2 * ((size_t)f * S + (size_t)j * c->sz.nmode)] = prof[j];
+  };
+  std::vector<double> b(Nr, 0.0);
+  b[0] = c->Re_i;
+  b[Nr - 1] = c->Re_o;
+  put(1, dense_solve(dense_lap00(c, 1.0), b, Nr));
+  c->Tb_disc.assign(Nr, 0.0);
+  if (c->has_T) {
+    std::fill(b.begin(), b.end(), 0.0);
+    b[0] = 0.5;
+    b[Nr - 1] = -0.5;
+    c->Tb_disc = dense_solve(dense_lap00(c, 0.0), b, Nr);
+    put(3, c->Tb_disc);
+    for (int j = 0; j < Nr; ++j) b[j] = -c->Gr * c->Tb_disc[j];
+    b[0] = 0.0;
+    b[Nr - 1] = 0.0;
+    put(2, dense_solve(dense_lap00(c, 0.0), b, Nr));
+  }
+}
+
+void allocate(tc_ctx *c) {
+  const Sizes &s = c->sz;
+  const long long S = s.S;
+  const int nf = s.nf;
+  c->X = dalloc<double2>(c, (size_t)nf * S);
+  c->Xp = dalloc<double2>(c, (size_t)nf * S);
+  c->N0 = dalloc<double2>(c, (size_t)nf * S);
+  c->N1 = dalloc<double2>(c, (size_t)nf * S);
+  c->Yb = dalloc<double2>(c, (size_t)nf * S);
+  c->U0 = dalloc<double2>(c, (size_t)nf * S);
+  c->P = dalloc<double2>(c, (size_t)S);
+  c->base_dev = dalloc<double2>(c, (size_t)nf * S);
+  c->alpha_buf = dalloc<double2>(c, (size_t)2 * s.nmode);
+  c->V = dalloc<double2>(c, (size_t)3 * nf * s.Nr * s.Nz * s.NM);
+  c->W = dalloc<double2>(c, (size_t)nf * s.Nr * s.Nz * s.NM);
+  c->d_r = dalloc<double>(c, s.Nr);
+  c->d_inv_r = dalloc<double>(c, s.Nr);
+  c->d_D1 = dalloc<double>(c, (size_t)s.Nr * kStencil);
+  c->d_D2 = dalloc<double>(c, (size_t)s.Nr * kStencil);
+  c->d_dr = dalloc<double>(c, s.Nr);
+  c->d_wr = dalloc<double>(c, s.Nr);
+  c->d_s0 = dalloc<int>(c, s.Nr);
+  c->d_twz = dalloc<double2>(c, s.Nz);
+  c->d_twt = dalloc<double2>(c, s.Nt);
+  const int K1 = s.K + 1;
+  c->lin.nopP = s.NM * K1;
+  c->lin.nopH = (s.NM + 1) * K1;
+  c->lin.nopT = c->has_T ? s.NM * K1 : 0;
+  c->LUP = dalloc<double>(c, (size_t)s.Nr * kBandW * c->lin.nopP);
+  c->LUH = dalloc<double>(c, (size_t)s.Nr * kBandW * c->lin.nopH);
+  c->LUT = dalloc<double>(c, (size_t)s.Nr * kBandW * std::max(c->lin.nopT, 1));
+  c->infl = dalloc<double>(c, (size_t)8 * s.Nr * c->lin.nopP);
+  c->Ainv = dalloc<double>(c, (size_t)4 * c->lin.nopP);
+  c->diag_part = dalloc<double>(c, (size_t)s.Nr * 7);
+  c->diag_out = dalloc<double>(c, 16);
+  c->scal = dalloc<DevScalars>(c, 1);
+  c->dt_hist_cap = 1024;
+  c->dt_hist = dalloc<double>(c, c->dt_hist_cap);
+}
+
+void upload_tables(tc_ctx *c) {
+  const Sizes &s = c->sz;
+  std::vector<double> inv_r(s.Nr), wr(s.Nr);
+  for (int j = 0; j < s.Nr; ++j) {
+    inv_r[j] = 1.0 / c->r[j];
+    wr[j] = c->w[j] * c->r[j];
+  }
+  ck(cudaMemcpy(c->d_r, c->r.data(), s.Nr * sizeof(double), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(c->d_inv_r, inv_r.data(), s.Nr * sizeof(double), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(c->d_D1, c->D1.data(), c->D1.size() * sizeof(double), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(c->d_D2, c->D2.data(), c->D2.size() * sizeof(double), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(c->d_dr, c->dr_min.data(), s.Nr * sizeof(double), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(c->d_wr, wr.data(), s.Nr * sizeof(double), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(c->d_s0, c->s0.data(), s.Nr * sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<double2> tz = twiddles(s.Nz), tt = twiddles(s.Nt);
+  ck(cudaMemcpy(c->d_twz, tz.data(), s.Nz * sizeof(double2), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(c->d_twt, tt.data(), s.Nt * sizeof(double2), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(c->diag_part + (size_t)s.Nr * 6, c->Tb_disc.data(), s.Nr * sizeof(double),
+                cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(c->base_dev, c->base.data(), c->base.size() * sizeof(double),
+                cudaMemcpyHostToDevice));
+  DevScalars sc{};
+  ck(cudaMemcpy(c->scal, &sc, sizeof(sc), cudaMemcpyHostToDevice));
+  Radial rad{c->d_r, c->d_inv_r, c->d_D1, c->d_D2, c->d_dr, c->d_wr, c->d_s0};
+  NLParams &p = c->nl;
+  p.sz = s;
+  p.rad = rad;
+  p.alpha = 2.0 * M_PI / c->Lz;
+  p.Gr = c->Gr;
+  p.dth = 2.0 * M_PI / s.Nt;
+  p.dz = c->Lz / s.Nz;
+  p.pz = make_plan(s.Nz);
+  p.pt = make_plan(s.Nt);
+  p.twz = c->d_twz;
+  p.twt = c->d_twt;
+  LinParams &l = c->lin;
+  l.sz = s;
+  l.rad = rad;
+  l.alpha = p.alpha;
+  l.kappaT = c->has_T ? 1.0 / c->Pr : 1.0;
+  l.Re_i = c->Re_i;
+  l.Re_o = c->Re_o;
+  l.LUP = c->LUP;
+  l.LUH = c->LUH;
+  l.LUT = c->LUT;
+  l.infl = c->infl;
+  l.Ainv = c->Ainv;
+}
+
+}  // namespace
+}  // namespace tc
+
+using namespace tc;
+
+extern "C" {
+
+const char *tc_status_string(tc_status s) {
+  switch (s) {
+    case TC_OK: return "ok";
+    case TC_ERR_ARG: return "invalid argument";
+    case TC_ERR_CUDA: return "CUDA error (context poisoned)";
+    case TC_ERR_OOM: return "out of device memory";
+    case TC_ERR_NONFINITE: return "non-finite value in the state";
+    case TC_ERR_CFL: return "CFL limit exceeded";
+    case TC_ERR_STATE: return "state violates the m = 0 Hermitian symmetry";
+    case TC_ERR_TIMEOUT: return "device wait timed out";
+    case TC_ERR_UNSUPPORTED: return "unsupported size or option";
+  }
+  return "unknown status";
+}
+
+tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz, double Re_i, double Re_o,
+                    double Ra, double Pr, tc_ctx **out) {
+  if (!out) return TC_ERR_ARG;
+  *out = nullptr;
+  if (Nr < kStencil || Nr > 1024) return TC_ERR_ARG;
+  if (Ntheta < 4 || Ntheta % 2 != 0 || Nz < 4 || Ntheta > 1024 || Nz > 1024) return TC_ERR_ARG;
+  if (!smooth235(Ntheta) || !smooth235(Nz)) return TC_ERR_ARG;
+  if (!(eta > 0.0 && eta < 1.0) || !(Lz > 0.0) || !std::isfinite(Lz)) return TC_ERR_ARG;
+  if (!std::isfinite(Re_i) || !std::isfinite(Re_o) || !std::isfinite(Ra)) return TC_ERR_ARG;
+  if (Ra != 0.0 && !(Pr > 0.0 && std::isfinite(Pr))) return TC_ERR_ARG;
+  tc_ctx *c = new tc_ctx();
+  Sizes &s = c->sz;
+  s.Nr = Nr;
+  s.Nt = Ntheta;
+  s.Nz = Nz;
+  s.M = (Ntheta - 1) / 3;
+  s.K = (Nz - 1) / 3;
+  s.NM = s.M + 1;
+  s.NK = 2 * s.K + 1;
+  s.nmode = s.NM * s.NK;
+  c->has_T = (Ra != 0.0);
+  s.nf = c->has_T ? 4 : 3;
+  s.S = (long long)Nr * s.nmode;
+  c->eta = eta;
+  c->Lz = Lz;
+  c->Re_i = Re_i;
+  c->Re_o = Re_o;
+  c->Ra = Ra;
+  c->Pr = Pr;
+  c->Gr = c->has_T ? Ra / Pr : 0.0;
+  c->r_i = eta / (1.0 - eta);
+  c->r_o = 1.0 / (1.0 - eta);
+  try {
+    build_tables(c);
+    build_base(c);
+    allocate(c);
+    upload_tables(c);
+    setup_nonlinear(c);
+    if (c->smem_zinv > 227 * 1024 || c->smem_theta > 227 * 1024 || c->smem_zfwd > 227 * 1024) {
+      tc_destroy(c);
+      return TC_ERR_UNSUPPORTED;
+    }
+    ck(cudaMemcpy(c->X, c->base_dev, c->base.size() * sizeof(double), cudaMemcpyDeviceToDevice));
+    launch_factor_poisson(c);
+    ck(cudaGetLastError());
+    ck(cudaDeviceSynchronize());
+  } catch (const std::bad_alloc &) {
+    tc_destroy(c);
+    return TC_ERR_OOM;
+  } catch (const CudaError &e) {
+    std::fprintf(stderr, "libtc: CUDA error %s\n", cudaGetErrorString(e.e));
+    tc_destroy(c);
+    return TC_ERR_CUDA;
+  }
+  *out = c;
+  return TC_OK;
+}
+
+tc_status tc_destroy(tc_ctx *c) {
+  if (!c) return TC_OK;
+  for (void *p : c->allocs) cudaFree(p);
+  for (auto &t : c->timers)
+    for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
+  delete c;
+  return TC_OK;
+}
+
+tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
+  if (!c || !key) return TC_ERR_ARG;
+  const std::string k(key);
+  if (!std::isfinite(v)) return TC_ERR_ARG;
+  if (k == "cfl") {
+    if (!(v > 0.0)) return TC_ERR_ARG;
+    c->cfl = v;
+  } else if (k == "dt_max") {
+    if (!(v > 0.0)) return TC_ERR_ARG;
+    c->dt_max = v;
+  } else if (k == "cfl_limit") {
+    if (v < 0.0) return TC_ERR_ARG;
+    c->cfl_limit = v;
+  } else if (k == "check") {
+    c->check = v != 0.0;
+  } else if (k == "timing") {
+    c->timing = v != 0.0;
+  } else {
+    return TC_ERR_ARG;
+  }
+  return TC_OK;
+}
+
+tc_status tc_set_stream(tc_ctx *c, void *stream) {
+  if (!c) return TC_ERR_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return TC_OK;
+}
+
+tc_status tc_get_info(const tc_ctx *c, tc_info *o) {
+  if (!c || !o) return TC_ERR_ARG;
+  o->Nr = c->sz.Nr;
+  o->Ntheta = c->sz.Nt;
+  o->Nz = c->sz.Nz;
+  o->M = c->sz.M;
+  o->K = c->sz.K;
+  o->nfields = c->sz.nf;
+  o->coeffs_per_field = c->sz.S;
+  o->state_bytes = (long long)c->sz.nf * c->sz.S * 16;
+  o->device_bytes = c->device_bytes;
+  o->launches = c->launches;
+  return TC_OK;
+}
+
+tc_status tc_set_state(tc_ctx *c, const void *spec, int where) {
+  if (!c || !spec || (where != 0 && where != 1)) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  const size_t bytes = (size_t)16 * c->sz.nf * c->sz.S;
+  try {
+    // stage in Xp, check on the device, commit only a valid state
+    ck(cudaMemcpyAsync(c->Xp, spec, bytes,
+                       where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    // forget the dynamic-step history and the flags; the factors stay valid
+    // for the step they were built for
+    DevScalars sc{};
+    char *base = reinterpret_cast<char *>(c->scal);
+    ck(cudaMemsetAsync(base + offsetof(DevScalars, dt_prev), 0, sizeof(double), c->stream));
+    ck(cudaMemsetAsync(base + offsetof(DevScalars, rate_bits), 0,
+                       offsetof(DevScalars, rate_last) - offsetof(DevScalars, rate_bits),
+                       c->stream));
+    ck(cudaMemsetAsync(base + offsetof(DevScalars, nonfinite), 0, sizeof(int), c->stream));
+    launch_state_check(c, c->Xp);
+    ck(cudaGetLastError());
+    ck(cudaMemcpyAsync(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    if (sc.nonfinite) return TC_ERR_NONFINITE;
+    double amax, defect;
+    std::memcpy(&amax, &sc.chk_bits[0], sizeof(double));
+    std::memcpy(&defect, &sc.chk_bits[1], sizeof(double));
+    if (defect > 1e-12 * amax) return TC_ERR_STATE;
+    launch_symmetrise(c, c->Xp);
+    ck(cudaMemcpyAsync(c->X, c->Xp, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    ck(cudaGetLastError());
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  c->t = 0.0;
+  c->dt_last = 0.0;
+  return TC_OK;
+}
+
+tc_status tc_get_state(const tc_ctx *c, void *spec, int where) {
+  if (!c || !spec || (where != 0 && where != 1)) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  const size_t bytes = (size_t)16 * c->sz.nf * c->sz.S;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(spec, c->X, bytes, where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) return fail_cuda(const_cast<tc_ctx *>(c), e);
+  return TC_OK;
+}
+
+tc_status tc_get_pressure(const tc_ctx *c, void *spec, int where) {
+  if (!c || !spec || (where != 0 && where != 1)) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(spec, c->P, (size_t)16 * c->sz.S,
+                   where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) return fail_cuda(const_cast<tc_ctx *>(c), e);
+  return TC_OK;
+}
+
+tc_status tc_init_perturbation(tc_ctx *c, const double *psi, int mp, int kp, double amp,
+                               const double *tcoef, double amp_T) {
+  if (!c || !psi || mp < 0 || kp < 0 || !(amp >= 0.0)) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  const Sizes &s = c->sz;
+  if (mp > s.M || kp > s.K) return TC_ERR_ARG;
+  const int Nr = s.Nr, NK = s.NK, nk = 2 * kp + 1;
+  // psi_c(r, m, k) = (1 - x^2)^2 raw_c(m, k), Hermitian m = 0 column
+  std::vector<cplx> ps((size_t)3 * s.S, cplx(0.0, 0.0));
+  auto P = [&](int comp, int j, int m, int kk) -> cplx & {
+    return ps[(size_t)comp * s.S + (size_t)j * s.nmode + (size_t)m * NK + kk];
+  };
+  for (int j = 0; j < Nr; ++j) {
+    const double x = 2.0 * (c->r[j] - c->r_i) - 1.0;
+    const double prof = (1.0 - x * x) * (1.0 - x * x);
+    for (int comp = 0; comp < 3; ++comp)
+      for (int m = 0; m <= mp; ++m)
+        for (int k = -kp; k <= kp; ++k) {
+          const double *raw = psi + 2 * (((size_t)comp * (mp + 1) + m) * nk + (k + kp));
+          P(comp, j, m, (k + NK) % NK) = prof * cplx(raw[0], raw[1]);
+        }
+    for (int comp = 0; comp < 3; ++comp) {
+      for (int k = 1; k <= s.K; ++k) P(comp, j, 0, NK - k) = std::conj(P(comp, j, 0, k));
+      P(comp, j, 0, 0) = cplx(P(comp, j, 0, 0).real(), 0.0);
+    }
+  }
+  // u' = curl psi with the same D1 as the step
+  std::vector<double> u((size_t)2 * s.nf * s.S, 0.0);
+  const double alpha = 2.0 * M_PI / c->Lz;
+  const cplx I(0.0, 1.0);
+  for (int j = 1; j < Nr - 1; ++j) {
+    const int st = c->s0[j];
+    const double r = c->r[j];
+    for (int m = 0; m < s.NM; ++m)
+      for (int kk = 0; kk < NK; ++kk) {
+        const double beta = alpha * (kk <= s.K ? kk : kk - NK);
+        cplx d1pz(0, 0), d1rpt(0, 0);
+        for (int t = 0; t < kStencil; ++t) {
+          d1pz += c->D1[j * kStencil + t] * P(2, st + t, m, kk);
+          d1rpt += c->D1[j * kStencil + t] * (c->r[st + t] * P(1, st + t, m, kk));
+        }
+        const cplx pr = P(0, j, m, kk), pt = P(1, j, m, kk), pz = P(2, j, m, kk);
+        const cplx ur = I * (double)m * pz / r - I * beta * pt;
+        const cplx ut = I * beta * pr - d1pz;
+        const cplx uz = d1rpt / r - I * (double)m * pr / r;
+        const size_t o = (size_t)j * s.nmode + (size_t)m * NK + kk;
+        u[2 * o] = ur.real();
+        u[2 * o + 1] = ur.imag();
+        u[2 * (s.S + o)] = ut.real();
+        u[2 * (s.S + o) + 1] = ut.imag();
+        u[2 * (2 * s.S + o)] = uz.real();
+        u[2 * (2 * s.S + o) + 1] = uz.imag();
+      }
+  }
+  const bool withT = c->has_T && tcoef && amp_T > 0.0;
+  if (withT) {
+    std::vector<cplx> tp((size_t)s.S, cplx(0, 0));
+    for (int j = 0; j < Nr; ++j) {
+      const double x = 2.0 * (c->r[j] - c->r_i) - 1.0;
+      for (int m = 0; m <= mp; ++m)
+        for (int k = -kp; k <= kp; ++k) {
+          const double *raw = tcoef + 2 * ((size_t)m * nk + (k + kp));
+          tp[(size_t)j * s.nmode + (size_t)m * NK + (k + NK) % NK] =
+              (1.0 - x * x) * cplx(raw[0], raw[1]);
+        }
+      for (int k = 1; k <= s.K; ++k)
+        tp[(size_t)j * s.nmode + NK - k] = std::conj(tp[(size_t)j * s.nmode + k]);
+      tp[(size_t)j * s.nmode] = cplx(tp[(size_t)j * s.nmode].real(), 0.0);
+    }
+    for (long long i = 0; i < s.S; ++i) {
+      u[2 * (3 * s.S + i)] = tp[i].real();
+      u[2 * (3 * s.S + i) + 1] = tp[i].imag();
+    }
+  }
+  try {
+    ck(cudaMemcpy(c->Xp, u.data(), u.size() * sizeof(double), cudaMemcpyHostToDevice));
+    unsigned long long zero[2] = {0ull, 0ull};
+    ck(cudaMemcpy(c->scal->norm_bits, zero, sizeof(zero), cudaMemcpyHostToDevice));
+    launch_nonlinear(c, c->Xp, nullptr, nullptr, 1);
+    ck(cudaGetLastError());
+    unsigned long long nb[2];
+    ck(cudaMemcpy(nb, c->scal->norm_bits, sizeof(nb), cudaMemcpyDeviceToHost));
+    double umax, tmax;
+    std::memcpy(&umax, &nb[0], sizeof(double));
+    std::memcpy(&tmax, &nb[1], sizeof(double));
+    const double su = (umax > 0.0) ? amp / umax : 0.0;
+    const double sT = (withT && tmax > 0.0) ? amp_T / tmax : 0.0;
+    std::vector<double> X(c->base);
+    for (long long i = 0; i < 2 * 3 * s.S; ++i) X[i] += su * u[i];
+    if (s.nf == 4)
+      for (long long i = 2 * 3 * s.S; i < 2 * 4 * s.S; ++i) X[i] += sT * u[i];
+    ck(cudaMemcpy(c->X, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice));
+    DevScalars sc{};
+    ck(cudaMemcpy(c->scal, &sc, sizeof(sc), cudaMemcpyHostToDevice));
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  c->t = 0.0;
+  c->dt_last = 0.0;
+  return TC_OK;
+}
+
+tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
+  if (!c || nsteps < 0 || !std::isfinite(dt)) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  if (nsteps == 0) return TC_OK;
+  try {
+    if (nsteps > c->dt_hist_cap) {
+      double *h = nullptr;
+      ck(cudaMalloc(&h, sizeof(double) * nsteps));
+      cudaFree(c->dt_hist);
+      for (auto &p : c->allocs)
+        if (p == c->dt_hist) p = h;
+      c->dt_hist = h;
+      c->dt_hist_cap = nsteps;
+    }
+    int zero = 0;
+    ck(cudaMemcpyAsync(&c->scal->nonfinite, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    const double dt_fixed = dt > 0.0 ? dt : 0.0;
+    for (int n = 0; n < nsteps; ++n) {
+      launch_nonlinear(c, c->X, c->N0, &c->scal->rate_bits, 0);
+      launch_dt_policy(c, dt_fixed, n);
+      launch_refactor(c);
+      launch_rhs(c, c->X, c->N0);
+      launch_stage(c, c->N0, c->Xp, c->P);
+      launch_nonlinear(c, c->Xp, c->N1, nullptr, 0);
+      launch_stage(c, c->N1, c->X, c->P);
+    }
+    ck(cudaGetLastError());
+    std::vector<double> hist(nsteps);
+    ck(cudaMemcpyAsync(hist.data(), c->dt_hist, sizeof(double) * nsteps, cudaMemcpyDeviceToHost,
+                       c->stream));
+    DevScalars sc;
+    ck(cudaMemcpyAsync(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    for (int n = 0; n < nsteps; ++n) c->t += hist[n];
+    if (dt_used) std::memcpy(dt_used, hist.data(), sizeof(double) * nsteps);
+    c->dt_last = hist[nsteps - 1];
+    if (c->check && sc.nonfinite) return TC_ERR_NONFINITE;
+    if (c->cfl_limit > 0.0 && sc.rate_last * sc.dt > c->cfl_limit) return TC_ERR_CFL;
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  return TC_OK;
+}
+
+tc_status tc_nonlinear(tc_ctx *c, const void *state_dev, void *n_dev, double *cfl_rate) {
+  if (!c || !state_dev || !n_dev) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  try {
+    unsigned long long *rb = &c->scal->rate_bits;
+    unsigned long long z = 0ull;
+    ck(cudaMemcpyAsync(rb, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream));
+    launch_nonlinear(c, static_cast<const double2 *>(state_dev), static_cast<double2 *>(n_dev), rb,
+                     0);
+    ck(cudaGetLastError());
+    unsigned long long bits;
+    ck(cudaMemcpyAsync(&bits, rb, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaMemcpyAsync(rb, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    if (cfl_rate) std::memcpy(cfl_rate, &bits, sizeof(double));
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  return TC_OK;
+}
+
+tc_status tc_stage_solve(tc_ctx *c, const void *rhs_dev, double dt, void *x_out_dev,
+                         void *p_out_dev) {
+  if (!c || !rhs_dev || !x_out_dev || !(dt > 0.0) || !std::isfinite(dt)) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  const Sizes &s = c->sz;
+  try {
+    ck(cudaMemcpyAsync(c->Yb, rhs_dev, (size_t)16 * s.nf * s.S, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    ck(cudaMemsetAsync(c->N1, 0, (size_t)16 * s.nf * s.S, c->stream));
+    launch_dt_policy(c, dt, -1);
+    launch_refactor(c);
+    launch_stage(c, c->N1, static_cast<double2 *>(x_out_dev), c->P);
+    if (p_out_dev)
+      ck(cudaMemcpyAsync(p_out_dev, c->P, (size_t)16 * s.S, cudaMemcpyDeviceToDevice, c->stream));
+    ck(cudaGetLastError());
+    ck(cudaStreamSynchronize(c->stream));
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  return TC_OK;
+}
+
+tc_status tc_diagnostics(tc_ctx *c, tc_diag *o) {
+  if (!c || !o) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  try {
+    launch_diagnostics(c);
+    ck(cudaGetLastError());
+    double h[13];
+    ck(cudaMemcpyAsync(h, c->diag_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    o->t = c->t;
+    o->dt = h[0];
+    o->E = h[1];
+    o->E_pert = h[2];
+    o->torque_i = h[3];
+    o->torque_o = h[4];
+    o->P_wall = h[5];
+    o->eps = h[6];
+    o->buoy_work = h[7];
+    o->Nu_i = h[8];
+    o->Nu_o = h[9];
+    o->div_max = h[10];
+    o->div_rms = h[11];
+    o->cfl = h[12];
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  return TC_OK;
+}
+
+tc_status tc_get_timing(tc_ctx *c, tc_kernel_time *out, int cap, int *count) {
+  if (!c || (!out && cap > 0) || !count) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail_cuda(c, e);
+  int n = 0;
+  for (int k = 0; k < KNUM; ++k) {
+    KernelTimer &t = c->timers[k];
+    if (t.used == 0) continue;
+    double ms = 0.0;
+    for (int i = 0; i < t.used; ++i) {
+      float f = 0.0f;
+      e = cudaEventElapsedTime(&f, t.ev[2 * i], t.ev[2 * i + 1]);
+      if (e != cudaSuccess) return fail_cuda(c, e);
+      ms += f;
+    }
+    if (n < cap) {
+      std::memset(out[n].name, 0, sizeof(out[n].name));
+      std::strncpy(out[n].name, kKernelNames[k], sizeof(out[n].name) - 1);
+      out[n].launches = t.used;
+      out[n].ms = ms;
+    }
+    ++n;
+  }
+  *count = n;
+  return TC_OK;
+}
+
+tc_status tc_reset_timing(tc_ctx *c) {
+  if (!c) return TC_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail_cuda(c, e);
+  for (auto &t : c->timers) t.used = 0;
+  return TC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// Internal declarations of libtc: context, device tables and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "tc.h"
+
+namespace tc {
+
+constexpr int kStencil = 9;   // radial FD stencil (Sec. 2.1: 9 points by default)
+constexpr int kBand = 8;      // half bandwidth of the radial operators
+constexpr int kBandW = 17;    // stored band entries per row (8 lower, diag, 8 upper)
+constexpr double kCN = 0.5;   // implicit weight of the predictor-corrector
+
+struct FFTPlan {
+  int n;
+  int npass;
+  int radix[16];
+};
+
+FFTPlan make_plan(int n);
+
+// Problem sizes.
+struct Sizes {
+  int Nr, Nt, Nz, M, K, NM, NK, nmode, nf;
+  long long S;  // Nr * nmode coefficients per field
+};
+
+// Device-side radial tables (device pointers).
+struct Radial {
+  const double *r, *inv_r, *D1, *D2, *dr_min, *wr;  // wr = quadrature w_j r_j
+  const int *s0;                                     // stencil start per node
+};
+
+// Scalars shared between kernels on the device.
+struct DevScalars {
+  double dt;            // step in use
+  double dt_factored;   // step the Helmholtz factors belong to
+  double dt_prev;       // previous step (dynamic policy)
+  unsigned long long rate_bits;   // CFL rate of the last start-of-step state
+  unsigned long long norm_bits[2];  // max |u'|, max |T'| (initial condition)
+  unsigned long long chk_bits[2];   // tc_set_state: max |x|, max Hermitian defect
+  double rate_last;     // rate read by the policy
+  int refactor;         // 1 when the factors must be rebuilt this step
+  int nonfinite;        // set when a solve produced NaN/Inf
+};
+
+// Parameters of the nonlinear stage.
+struct NLParams {
+  Sizes sz;
+  Radial rad;
+  double alpha;         // 2 pi / Lz
+  double Gr;            // Ra / Pr
+  double dth, dz;       // grid spacings in theta and z
+  int MB;               // m columns per CTA in the z kernels
+  int LB;               // z rows per CTA in the theta kernel
+  FFTPlan pz, pt;
+  const double2 *twz, *twt;   // exp(-2 pi i t / N) tables (FP64 master copy)
+};
+
+// Parameters of the linear stage.
+struct LinParams {
+  Sizes sz;
+  Radial rad;
+  double alpha;
+  double kappaT;        // 1/Pr
+  double Re_i, Re_o;
+  int nopP, nopH, nopT; // operator counts: Poisson, velocity Helmholtz, T Helmholtz
+  double *LUP, *LUH, *LUT;   // band factors [row][17][op]
+  double *infl;         // influence data [8][Nr][nopP]: pa pb upa uma upb umb za zb
+  double *Ainv;         // [4][nopP]
+};
+
+}  // namespace tc
+
+namespace tc {
+// Kernels with per-launch timing (option "timing").
+enum KernelId {
+  KZINV, KTHETA, KZFWD, KDT, KFACTH, KINFL, KRHS, KPOIS, KHELM, KALPHA, KCORR, KDIAG, KNUM
+};
+extern const char *const kKernelNames[KNUM];
+
+struct KernelTimer {
+  std::vector<cudaEvent_t> ev;   // pairs (start, stop)
+  int used = 0;                  // pairs recorded since the last reset
+  long long launches = 0;
+};
+}  // namespace tc
+
+struct tc_ctx {
+  tc::Sizes sz;
+  double eta, Lz, Re_i, Re_o, Ra, Pr, Gr, r_i, r_o;
+  bool has_T;
+  double cfl = 0.25, dt_max = 1e-3, cfl_limit = 0.0;
+  int check = 1;
+  cudaStream_t stream = nullptr;
+  bool poisoned = false;
+  double t = 0.0, dt_last = 0.0, dt_prev_host = 0.0;
+  // host tables
+  std::vector<double> r, D1, D2, w, dr_min;
+  std::vector<int> s0;
+  std::vector<double> base;     // basic state, interleaved complex [nf][S]
+  std::vector<double> Tb_disc;  // discrete conductive profile (Nr)
+  // device memory
+  std::vector<void *> allocs;
+  size_t device_bytes = 0;
+  double2 *X, *Xp, *N0, *N1, *Yb, *U0, *P, *V, *W, *alpha_buf, *base_dev;
+  double *d_r, *d_inv_r, *d_D1, *d_D2, *d_dr, *d_wr;
+  int *d_s0;
+  double2 *d_twz, *d_twt;
+  double *LUP, *LUH, *LUT, *infl, *Ainv;
+  double *dt_hist;
+  int dt_hist_cap = 0;
+  double *diag_part, *diag_out;
+  tc::DevScalars *scal;
+  tc::NLParams nl;
+  tc::LinParams lin;
+  size_t smem_zinv, smem_theta, smem_zfwd;
+  long long launches = 0;        // kernels launched since tc_create
+  int timing = 0;
+  tc::KernelTimer timers[tc::KNUM];
+};
+
+namespace tc {
+// Brackets one kernel launch: counts it and, with timing on, records a pair
+// of events on the context's stream around it.
+struct LaunchScope {
+  tc_ctx *c;
+  int id;
+  LaunchScope(tc_ctx *c_, int id_);
+  ~LaunchScope();
+};
+}  // namespace tc
+
+namespace tc {
+
+// nonlinear.cu
+void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long long *rate_bits,
+                      int mode);
+void setup_nonlinear(tc_ctx *c);
+
+// linear.cu
+void launch_factor_poisson(tc_ctx *c);
+void launch_refactor(tc_ctx *c);
+void launch_dt_policy(tc_ctx *c, double dt_fixed, int step_index);
+void launch_rhs(tc_ctx *c, const double2 *X, const double2 *N0);
+void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout);
+void launch_check_finite(tc_ctx *c, const double2 *X, long long n);
+void launch_state_check(tc_ctx *c, const double2 *X);
+void launch_symmetrise(tc_ctx *c, double2 *X);
+
+// diag.cu
+void launch_diagnostics(tc_ctx *c);
+
+}  // namespace tc

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libtc (include/tc.h), argument marshalling only.
+
+Every computation runs in libtc's CUDA kernels.  The functions below keep the
+C names; ``Run`` wraps one context.  Spectral states are complex128 arrays of
+shape (nfields, Nr, M+1, 2K+1): NumPy arrays are passed as host pointers,
+CUDA torch tensors as device pointers.  There is no CPU fallback: importing
+this module without a built ``libtc.so`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libtc.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+STATUS = {0: "TC_OK", 1: "TC_ERR_ARG", 2: "TC_ERR_CUDA", 3: "TC_ERR_OOM",
+          4: "TC_ERR_NONFINITE", 5: "TC_ERR_CFL", 6: "TC_ERR_STATE",
+          7: "TC_ERR_TIMEOUT", 8: "TC_ERR_UNSUPPORTED"}
+
+
+class TCError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        msg = _lib.tc_status_string(status).decode()
+        super().__init__(f"{where}: {self.name} ({msg})")
+
+
+class tc_diag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("t", "dt", "E", "E_pert", "torque_i", "torque_o", "P_wall", "eps",
+                 "buoy_work", "Nu_i", "Nu_o", "div_max", "div_rms", "cfl")]
+
+
+class tc_info(ctypes.Structure):
+    _fields_ = [("Nr", ctypes.c_int), ("Ntheta", ctypes.c_int), ("Nz", ctypes.c_int),
+                ("M", ctypes.c_int), ("K", ctypes.c_int), ("nfields", ctypes.c_int),
+                ("coeffs_per_field", ctypes.c_longlong), ("state_bytes", ctypes.c_longlong),
+                ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_longlong)]
+
+
+class tc_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong),
+                ("ms", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_SIGS = {
+    "tc_create": [_I, _I, _I, _D, _D, _D, _D, _D, _D, ctypes.POINTER(_P)],
+    "tc_destroy": [_P],
+    "tc_set_option": [_P, ctypes.c_char_p, _D],
+    "tc_set_stream": [_P, _P],
+    "tc_get_info": [_P, ctypes.POINTER(tc_info)],
+    "tc_set_state": [_P, _P, _I],
+    "tc_get_state": [_P, _P, _I],
+    "tc_get_pressure": [_P, _P, _I],
+    "tc_init_perturbation": [_P, _P, _I, _I, _D, _P, _D],
+    "tc_step": [_P, _I, _D, _P],
+    "tc_diagnostics": [_P, ctypes.POINTER(tc_diag)],
+    "tc_nonlinear": [_P, _P, _P, _P],
+    "tc_stage_solve": [_P, _P, _D, _P, _P],
+    "tc_get_timing": [_P, _P, _I, ctypes.POINTER(_I)],
+    "tc_reset_timing": [_P],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.tc_status_string.argtypes = [ctypes.c_int]
+_lib.tc_status_string.restype = ctypes.c_char_p
+
+EXPORTED = sorted(list(_SIGS) + ["tc_status_string"])
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise TCError(st, where)
+
+
+def _ptr(a):
+    """(pointer, where) of a NumPy array (host, 0) or CUDA tensor (device, 1)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1
+    raise TypeError("expected a NumPy array or a CUDA tensor")
+
+
+# -- C names ------------------------------------------------------------------
+def tc_create(Nr, Ntheta, Nz, eta, Lz, Re_i, Re_o=0.0, Ra=0.0, Pr=1.0):
+    h = _P()
+    _check(_lib.tc_create(Nr, Ntheta, Nz, eta, Lz, Re_i, Re_o, Ra, Pr, ctypes.byref(h)),
+           "tc_create")
+    return h
+
+
+def tc_destroy(ctx):
+    _check(_lib.tc_destroy(ctx), "tc_destroy")
+
+
+def tc_set_option(ctx, key: str, value: float):
+    _check(_lib.tc_set_option(ctx, key.encode(), float(value)), f"tc_set_option({key})")
+
+
+def tc_set_stream(ctx, stream_ptr: int):
+    _check(_lib.tc_set_stream(ctx, stream_ptr), "tc_set_stream")
+
+
+def tc_get_info(ctx) -> tc_info:
+    i = tc_info()
+    _check(_lib.tc_get_info(ctx, ctypes.byref(i)), "tc_get_info")
+    return i
+
+
+def tc_set_state(ctx, spec):
+    p, where = _ptr(spec)
+    _check(_lib.tc_set_state(ctx, p, where), "tc_set_state")
+
+
+def tc_get_state(ctx, out):
+    p, where = _ptr(out)
+    _check(_lib.tc_get_state(ctx, p, where), "tc_get_state")
+    return out
+
+
+def tc_get_pressure(ctx, out):
+    p, where = _ptr(out)
+    _check(_lib.tc_get_pressure(ctx, p, where), "tc_get_pressure")
+    return out
+
+
+def tc_init_perturbation(ctx, psi, amp, tcoef=None, amp_T=0.0):
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    mp, kp = psi.shape[1] - 1, (psi.shape[2] - 1) // 2
+    tptr = None
+    if tcoef is not None:
+        tcoef = np.ascontiguousarray(tcoef, dtype=np.complex128)
+        tptr = tcoef.ctypes.data
+    _check(_lib.tc_init_perturbation(ctx, psi.ctypes.data, mp, kp, float(amp), tptr,
+                                     float(amp_T)), "tc_init_perturbation")
+
+
+def tc_step(ctx, nsteps: int, dt: float):
+    used = np.zeros(max(nsteps, 1), dtype=np.float64)
+    _check(_lib.tc_step(ctx, int(nsteps), float(dt), used.ctypes.data), "tc_step")
+    return used[:nsteps]
+
+
+def tc_diagnostics(ctx) -> dict:
+    d = tc_diag()
+    _check(_lib.tc_diagnostics(ctx, ctypes.byref(d)), "tc_diagnostics")
+    return {n: getattr(d, n) for n, _ in tc_diag._fields_}
+
+
+def tc_nonlinear(ctx, state_dev, n_dev) -> float:
+    rate = ctypes.c_double(0.0)
+    _check(_lib.tc_nonlinear(ctx, _ptr(state_dev)[0], _ptr(n_dev)[0], ctypes.byref(rate)),
+           "tc_nonlinear")
+    return rate.value
+
+
+def tc_stage_solve(ctx, rhs_dev, dt, x_out_dev, p_out_dev=None):
+    pp = _ptr(p_out_dev)[0] if p_out_dev is not None else None
+    _check(_lib.tc_stage_solve(ctx, _ptr(rhs_dev)[0], float(dt), _ptr(x_out_dev)[0], pp),
+           "tc_stage_solve")
+
+
+def tc_get_timing(ctx) -> dict:
+    """{kernel name: (launches, total ms)} recorded while option "timing" is 1."""
+    n = _I(0)
+    _check(_lib.tc_get_timing(ctx, None, 0, ctypes.byref(n)), "tc_get_timing")
+    arr = (tc_kernel_time * max(n.value, 1))()
+    _check(_lib.tc_get_timing(ctx, arr, n.value, ctypes.byref(n)), "tc_get_timing")
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].ms) for i in range(n.value)}
+
+
+def tc_reset_timing(ctx):
+    _check(_lib.tc_reset_timing(ctx), "tc_reset_timing")
+
+
+def tc_status_string(s: int) -> str:
+    return _lib.tc_status_string(s).decode()
+
+
+# -- convenience wrapper -------------------------------------------------------
+class Run:
+    """One Taylor-Couette run on the GPU (owns a tc_ctx)."""
+
+    def __init__(self, Nr, Ntheta, Nz, eta, Lz, Re_i, Re_o=0.0, Ra=0.0, Pr=1.0):
+        self.ctx = tc_create(Nr, Ntheta, Nz, eta, Lz, Re_i, Re_o, Ra, Pr)
+        i = tc_get_info(self.ctx)
+        self.Nr, self.Ntheta, self.Nz = i.Nr, i.Ntheta, i.Nz
+        self.M, self.K, self.nf = i.M, i.K, i.nfields
+        self.shape = (self.nf, self.Nr, self.M + 1, 2 * self.K + 1)
+        self.device_bytes = i.device_bytes
+
+    @classmethod
+    def from_workload(cls, wl):
+        run = cls(wl.Nr, wl.Ntheta, wl.Nz, wl.eta, wl.Lz, wl.Re_i, wl.Re_o, wl.Ra, wl.Pr)
+        if wl.dt <= 0:
+            tc_set_option(run.ctx, "cfl", wl.cfl)
+            tc_set_option(run.ctx, "dt_max", wl.dt_max)
+        return run
+
+    def close(self):
+        if self.ctx:
+            tc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, spec):
+        tc_set_state(self.ctx, spec)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.complex128)
+        return tc_get_state(self.ctx, out)
+
+    def get_pressure(self, out=None):
+        if out is None:
+            out = np.empty(self.shape[1:], dtype=np.complex128)
+        return tc_get_pressure(self.ctx, out)
+
+    def init_perturbation(self, psi, amp, tcoef=None, amp_T=0.0):
+        tc_init_perturbation(self.ctx, psi, amp, tcoef, amp_T)
+
+    def step(self, nsteps, dt):
+        return tc_step(self.ctx, nsteps, dt)
+
+    def diagnostics(self):
+        return tc_diagnostics(self.ctx)
+
+    def set_option(self, key, value):
+        tc_set_option(self.ctx, key, value)
+
+    def set_stream(self, stream_ptr):
+        tc_set_stream(self.ctx, stream_ptr)

@@ -1,0 +1,230 @@
+"""GPU parity: every stage of the CUDA path against the FP64 oracle.
+
+All inputs come from the seeded generators in ``inputs``; expected values come
+only from ``oracle``.  Tolerances: single stages 1e-12 relative to the largest
+output coefficient (they differ only by rounding order); whole runs relative
+L2 <= 1e-10 per field after 100 steps, weighted by c_m w_j r_j.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from inputs import (WORKLOADS, Workload, psi_coefficients, random_state,
+                    temperature_coefficients)
+from oracle import Model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1908_00587_gb300 import tc as mod
+    return mod
+
+
+def rel_l2(mdl, a, b):
+    w = (mdl.g.w * mdl.g.r)[:, None, None] * mdl.sp.cm[None, :, None]
+    out = []
+    for f in range(a.shape[0]):
+        num = np.sum(w * np.abs(a[f] - b[f]) ** 2)
+        den = np.sum(w * np.abs(b[f]) ** 2)
+        out.append(float(np.sqrt(num / den)))
+    return max(out)
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+SIZES = [
+    # Nr, Ntheta, Nz, Ra : several tiles, ragged tails, radices 2/3/5
+    (12, 24, 30, 500.0),
+    (20, 32, 32, 0.0),
+    (9, 48, 40, 0.0),
+    (16, 20, 12, 800.0),
+    (33, 36, 18, 0.0),
+]
+
+
+def _wl(Nr, Nt, Nz, Ra):
+    return Workload("p", Nr=Nr, Ntheta=Nt, Nz=Nz, eta=0.62, Lz=1.7, Re_i=60.0, Re_o=-15.0,
+                    Ra=Ra, Pr=0.8)
+
+
+@pytest.mark.parametrize("Nr,Nt,Nz,Ra", SIZES)
+def test_nonlinear_matches_oracle(tc, Nr, Nt, Nz, Ra):
+    wl = _wl(Nr, Nt, Nz, Ra)
+    mdl = Model(wl)
+    X = random_state(100 + Nr, mdl.nf, Nr, mdl.M, mdl.K)
+    ref, rate = mdl.nonlinear(X)
+    run = tc.Run.from_workload(wl)
+    out = dev(np.zeros_like(X))
+    got_rate = tc.tc_nonlinear(run.ctx, dev(X), out)
+    got = out.cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-12 * scale
+    assert abs(got_rate - rate) <= 1e-13 * rate
+    run.close()
+
+
+@pytest.mark.parametrize("Nr,Nt,Nz,Ra", SIZES)
+def test_stage_solve_matches_oracle(tc, Nr, Nt, Nz, Ra):
+    wl = _wl(Nr, Nt, Nz, Ra)
+    mdl = Model(wl)
+    Rr, Rt = random_state(200 + Nr, 2, Nr, mdl.M, mdl.K)
+    R = [Rr + 1j * Rt, Rr - 1j * Rt]
+    if mdl.nf == 4:
+        R += list(random_state(300 + Nr, 2, Nr, mdl.M, mdl.K))
+    else:
+        R += [random_state(300 + Nr, 1, Nr, mdl.M, mdl.K)[0]]
+    R = np.stack(R)
+    dt = 2.5e-3
+    Xref, Pref = mdl.stage_solve(list(R), dt)
+    run = tc.Run.from_workload(wl)
+    xo = dev(np.zeros_like(R))
+    po = dev(np.zeros(R.shape[1:], dtype=np.complex128))
+    tc.tc_stage_solve(run.ctx, dev(R), dt, xo, po)
+    X, P = xo.cpu().numpy(), po.cpu().numpy()
+    for f in range(mdl.nf):
+        assert np.abs(X[f] - Xref[f]).max() <= 1e-11 * np.abs(Xref[f]).max(), f
+    assert np.abs(P - Pref).max() <= 1e-11 * np.abs(Pref).max()
+    run.close()
+
+
+def test_initial_perturbation_matches_oracle(tc):
+    wl = WORKLOADS["tc_fp64T_nr64_n128"].scaled(Nr=24, Ntheta=32, Nz=48, mp=5, kp=6)
+    mdl = Model(wl)
+    psi = psi_coefficients(wl.seed, wl.mp, wl.kp)
+    tco = temperature_coefficients(wl.seed, wl.mp, wl.kp)
+    ref = mdl.initial_state(psi, tco)
+    run = tc.Run.from_workload(wl)
+    base = run.get_state()            # the library's own discrete basic state
+    run.init_perturbation(psi, wl.amp, tco, wl.amp_T)
+    got = run.get_state()
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    pert = got - base
+    pref = ref - mdl.base
+    assert np.abs(pert - pref).max() <= 1e-12 * np.abs(pref).max()
+    run.close()
+
+
+def test_basic_state_preserved(tc):
+    wl = WORKLOADS["tc_fp64_nr32_n32"]
+    mdl = Model(wl)
+    run = tc.Run.from_workload(wl)
+    X0 = run.get_state()
+    assert np.abs(X0 - mdl.base).max() <= 1e-13 * np.abs(mdl.base).max()
+    run.step(100, wl.dt)
+    X = run.get_state()
+    assert np.abs(X - X0).max() <= 1e-12 * np.abs(X0).max()
+    run.close()
+
+
+def _run_both(tc, wl, nsteps, transform="naive"):
+    mdl = Model(wl, transform)
+    psi = psi_coefficients(wl.seed, wl.mp, wl.kp)
+    tco = temperature_coefficients(wl.seed, wl.mp, wl.kp) if wl.Ra else None
+    run = tc.Run.from_workload(wl)
+    run.init_perturbation(psi, wl.amp, tco, wl.amp_T)
+    dts = run.step(nsteps, wl.dt)
+    got = run.get_state()
+    dg = run.diagnostics()
+    pg = run.get_pressure()
+    run.close()
+    X = mdl.initial_state(psi, tco)
+    ref_dts = []
+    dt_prev = 0.0
+    p = None
+    rate = 0.0
+    for _ in range(nsteps):
+        X, p, used, rate = mdl.step(X, wl.dt, dt_prev)
+        ref_dts.append(used)
+        dt_prev = used
+    return mdl, got, X, dts, np.array(ref_dts), dg, mdl.diagnostics(X, ref_dts[-1], rate), pg, p
+
+
+def test_step_parity_100_steps(tc):
+    wl = WORKLOADS["tc_fp64_nr32_n32"]
+    mdl, got, ref, dts, rdts, dg, dr, pg, pr = _run_both(tc, wl, 100, "fft")
+    err = rel_l2(mdl, got, ref)
+    assert err <= 1e-10, err
+    # perturbation part (informational bound): the O(Re) basic state carries
+    # round-off of ~1e-13 Re, magnified by Re/amp relative to the perturbation
+    pert = rel_l2(mdl, got - mdl.base, ref - mdl.base)
+    assert pert <= 1e-6, pert
+    np.testing.assert_array_equal(dts, rdts)
+    sel = np.ones(pr.shape, bool)
+    sel[:, 0, 0] = False
+    assert np.abs(pg - pr)[sel].max() <= 1e-9 * np.abs(pr[sel]).max()
+    for k in ("E", "E_pert", "torque_i", "torque_o", "P_wall", "eps"):
+        assert abs(dg[k] - dr[k]) <= 1e-9 * abs(dr[k]) + 1e-300, (k, dg[k], dr[k])
+    # the divergence is a cancellation of O(Re_i) gradients: bound it on that scale
+    for k in ("div_rms", "div_max"):
+        assert abs(dg[k] - dr[k]) <= 1e-13 * wl.Re_i, (k, dg[k], dr[k])
+
+
+def test_step_parity_temperature_dynamic_dt(tc):
+    wl = WORKLOADS["tc_fp64T_nr64_n128"].scaled(Nr=24, Ntheta=24, Nz=36, mp=4, kp=4)
+    mdl, got, ref, dts, rdts, dg, dr, _, _ = _run_both(tc, wl, 30, "fft")
+    assert np.all(np.abs(dts - rdts) <= 1e-8 * rdts)
+    err = rel_l2(mdl, got, ref)
+    assert err <= 1e-10, err
+    for k in ("E", "E_pert", "eps", "buoy_work", "Nu_i", "Nu_o", "P_wall", "cfl"):
+        assert abs(dg[k] - dr[k]) <= 1e-9 * abs(dr[k]) + 1e-300, (k, dg[k], dr[k])
+
+
+@pytest.mark.parametrize("Nr,Nt,Nz", [(17, 30, 20), (40, 48, 24), (9, 16, 60)])
+def test_step_parity_ragged_sizes(tc, Nr, Nt, Nz):
+    wl = Workload("rag", Nr=Nr, Ntheta=Nt, Nz=Nz, eta=0.71, Lz=2.3, Re_i=150.0, Re_o=-40.0,
+                  amp=5e-2, mp=min(3, (Nt - 1) // 3), kp=min(3, (Nz - 1) // 3), seed=5,
+                  dt=1e-3)
+    mdl, got, ref, *_ = _run_both(tc, wl, 20, "fft")
+    assert rel_l2(mdl, got, ref) <= 1e-10
+
+
+def test_bench_workload_parity(tc):
+    """The benchmarked configuration itself (64 x 128 x 128, temperature, CFL
+    step), a few steps against the oracle."""
+    wl = WORKLOADS["tc_fp64T_nr64_n128"]
+    mdl, got, ref, dts, rdts, dg, dr, _, _ = _run_both(tc, wl, 2, "fft")
+    assert np.all(np.abs(dts - rdts) <= 1e-8 * rdts)
+    assert rel_l2(mdl, got, ref) <= 1e-10
+    assert rel_l2(mdl, got - mdl.base, ref - mdl.base) <= 1e-6
+
+
+def test_set_state_validation(tc):
+    wl = WORKLOADS["tc_fp64_nr32_n32"]
+    run = tc.Run.from_workload(wl)
+    X = run.get_state()
+    Y = X.copy()
+    Y[0, 3, 0, 1] += 1.0          # breaks u(0,-1) = conj u(0,1)
+    with pytest.raises(tc.TCError) as e:
+        run.set_state(Y)
+    assert e.value.name == "TC_ERR_STATE"
+    Y = X.copy()
+    Y[1, 2, 2, 2] = np.nan
+    with pytest.raises(tc.TCError) as e:
+        run.set_state(Y)
+    assert e.value.name == "TC_ERR_NONFINITE"
+    run.set_state(X)                 # the valid state is accepted again
+    assert np.array_equal(run.get_state(), X)
+    with pytest.raises(tc.TCError):
+        run.set_option("bogus", 1.0)
+    run.close()
+
+
+def test_cfl_limit_reports(tc):
+    wl = WORKLOADS["tc_fp64_nr32_n32"]
+    run = tc.Run.from_workload(wl)
+    run.set_option("cfl_limit", 1e-6)
+    with pytest.raises(tc.TCError) as e:
+        run.step(1, 1e-3)
+    assert e.value.name == "TC_ERR_CFL"
+    run.close()
