@@ -176,6 +176,31 @@ tc_status tc_get_timing(tc_ctx *ctx, tc_kernel_time *out, int cap, int *count);
 /* Forget the recorded times. */
 tc_status tc_reset_timing(tc_ctx *ctx);
 
+/* Nonlinear terms without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * -- code embedded in a host application that owns all device memory through
+ * its own pool (a cudaMalloc there fails once the pool holds the device, or
+ * escapes the pool's accounting), and code on a latency-critical path, where
+ * cudaMalloc may synchronise the device and stall other work.
+ * It computes what tc_nonlinear computes, for the run tc_create would make
+ * from (Nr, Ntheta, Nz, eta, Lz, Ra, Pr), with no context: state_dev and n_dev
+ * (device, layout of the state, caller-owned) are the only caller buffers.
+ * Every other buffer -- radial tables, twiddles, the transformed
+ * intermediates, the CFL slot -- lives in one fixed 32 MiB device array that
+ * every GPU loading this library holds until the process exits.  Limits:
+ * Nr <= 256, Ntheta and Nz <= 512, and the intermediates plus tables must fit
+ * in the 32 MiB (3 nfields + nfields planes of Nr * Nz * (M+1) complex128);
+ * larger sizes return TC_ERR_UNSUPPORTED, other invalid sizes TC_ERR_ARG.
+ * The first call on a device looks up the array's device address for that
+ * device (make it before any stream capture).  All calls share the array and
+ * each call overwrites the previous call's contents (the CFL slot is cleared
+ * every call), so calls that overlap on the GPU race: serialise them.  Work
+ * runs on `stream` (NULL: default stream); *cfl_rate (host, nullable) as in
+ * tc_nonlinear, which synchronises the stream when requested. */
+tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta, double Lz, double Ra,
+                               double Pr, const void *state_dev, void *n_dev, void *stream,
+                               double *cfl_rate);
+
 /* Human-readable name of a status. */
 const char *tc_status_string(tc_status s);
 

@@ -15,7 +15,10 @@
 //   k_zfwd   per (m-block, r): forward FFT along z, keep |k| <= K, scale.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
+#include <cstring>
 
 #include "fft.cuh"
 #include "tc_internal.h"
@@ -302,3 +305,194 @@ void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long lon
 }
 
 }  // namespace tc
+
+// ---------------------------------------------------------------------------
+// Allocation-free nonlinear stage (tc_nonlinear_noalloc in include/tc.h).
+//
+// Same three kernels as launch_nonlinear, but every buffer beyond the caller's
+// input and output -- radial tables, twiddles, the z- and theta-transformed
+// intermediates and the CFL slot -- lives in one file-scope device array of
+// kNoAllocBytes.  Every GPU that loads this library holds that array until
+// the process exits.  All calls share it: a call overwrites whatever the last
+// call left there (the CFL slot is cleared each call; the tables and both
+// intermediates are written in full before they are read), and calls that
+// overlap on the GPU race on it.
+namespace tc {
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(32) << 20;   // 32 MiB
+constexpr int kNoAllocMaxNr = 256;
+constexpr int kNoAllocMaxN = 512;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+unsigned char *g_scratch_addr[kMaxDevices] = {};   // device address per device
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Byte offsets of the pieces inside the scratch array.
+struct NoAllocLayout {
+  size_t r, inv_r, dr, D1, s0, twz, twt, rate, table_end, V, W, end;
+};
+
+NoAllocLayout noalloc_layout(const Sizes &s) {
+  NoAllocLayout L{};
+  size_t o = 0;
+  L.r = o;      o = align256(o + sizeof(double) * s.Nr);
+  L.inv_r = o;  o = align256(o + sizeof(double) * s.Nr);
+  L.dr = o;     o = align256(o + sizeof(double) * s.Nr);
+  L.D1 = o;     o = align256(o + sizeof(double) * s.Nr * kStencil);
+  L.s0 = o;     o = align256(o + sizeof(int) * s.Nr);
+  L.twz = o;    o = align256(o + sizeof(double2) * s.Nz);
+  L.twt = o;    o = align256(o + sizeof(double2) * s.Nt);
+  L.rate = o;   o = align256(o + sizeof(unsigned long long));
+  L.table_end = o;
+  const size_t plane = sizeof(double2) * (size_t)s.Nr * s.Nz * s.NM;
+  L.V = o;      o = align256(o + plane * 3 * s.nf);
+  L.W = o;      o = align256(o + plane * s.nf);
+  L.end = o;
+  return L;
+}
+
+// Largest table segment a call can need (host staging block on the stack).
+constexpr size_t kTableMaxBytes =
+    3 * (kNoAllocMaxNr * 8 + 256) + (kNoAllocMaxNr * kStencil * 8 + 256) +
+    (kNoAllocMaxNr * 4 + 256) + 2 * (kNoAllocMaxN * 16 + 256) + 256;
+
+bool smooth235_na(int n) {
+  if (n < 1) return false;
+  for (int f : {2, 3, 5})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta, double Lz,
+                                          double Ra, double Pr, const void *state_dev,
+                                          void *n_dev, void *stream, double *cfl_rate) {
+  using namespace tc;
+  if (!state_dev || !n_dev) return TC_ERR_ARG;
+  if (Nr < kStencil || Ntheta < 4 || Ntheta % 2 != 0 || Nz < 4) return TC_ERR_ARG;
+  if (!smooth235_na(Ntheta) || !smooth235_na(Nz)) return TC_ERR_ARG;
+  if (!(eta > 0.0 && eta < 1.0) || !(Lz > 0.0) || !std::isfinite(Lz) || !std::isfinite(Ra))
+    return TC_ERR_ARG;
+  if (Ra != 0.0 && !(Pr > 0.0 && std::isfinite(Pr))) return TC_ERR_ARG;
+  // size limit of the static scratch: reject with TC_ERR_UNSUPPORTED
+  if (Nr > kNoAllocMaxNr || Ntheta > kNoAllocMaxN || Nz > kNoAllocMaxN) return TC_ERR_UNSUPPORTED;
+  Sizes s{};
+  s.Nr = Nr;
+  s.Nt = Ntheta;
+  s.Nz = Nz;
+  s.M = (Ntheta - 1) / 3;
+  s.K = (Nz - 1) / 3;
+  s.NM = s.M + 1;
+  s.NK = 2 * s.K + 1;
+  s.nmode = s.NM * s.NK;
+  s.nf = (Ra != 0.0) ? 4 : 3;
+  s.S = (long long)Nr * s.nmode;
+  const NoAllocLayout L = noalloc_layout(s);
+  if (L.end > kNoAllocBytes) return TC_ERR_UNSUPPORTED;
+
+  // launch geometry: the same rules as the context path
+  NLParams p{};
+  p.sz = s;
+  int MB = (int)(3072 / (3 * s.Nz));
+  MB = MB < 1 ? 1 : (MB > 8 ? 8 : MB);
+  if (MB > s.NM) MB = s.NM;
+  int LB = (int)(4096 / (2 * s.nf * s.Nt));
+  LB = LB < 1 ? 1 : (LB > 8 ? 8 : LB);
+  p.MB = MB;
+  p.LB = LB;
+  const size_t e = sizeof(double2);
+  const size_t sm_zinv = (size_t)(2 * 3 * MB * s.Nz + s.Nz) * e;
+  const size_t sm_theta = (size_t)(2 * LB * 2 * s.nf * s.Nt + s.Nt) * e;
+  const size_t sm_zfwd = (size_t)(2 * s.nf * MB * s.Nz + s.Nz) * e;
+  if (sm_zinv > 227 * 1024 || sm_theta > 227 * 1024 || sm_zfwd > 227 * 1024)
+    return TC_ERR_UNSUPPORTED;
+
+  // once per device, with that device current: the device address of the array
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TC_ERR_CUDA;
+  if (!g_scratch_addr[dev]) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return TC_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = static_cast<unsigned char *>(ptr);
+  }
+  unsigned char *base = g_scratch_addr[dev];
+
+  // radial tables and twiddles, staged on the host stack and copied in
+  alignas(256) unsigned char host[kTableMaxBytes];
+  const double r_i = eta / (1.0 - eta);
+  double *r = reinterpret_cast<double *>(host + L.r);
+  double *inv_r = reinterpret_cast<double *>(host + L.inv_r);
+  double *drm = reinterpret_cast<double *>(host + L.dr);
+  double *D1 = reinterpret_cast<double *>(host + L.D1);
+  int *s0 = reinterpret_cast<int *>(host + L.s0);
+  for (int j = 0; j < Nr; ++j) {
+    r[j] = r_i + 0.5 * (1.0 - std::cos(M_PI * (double)j / (double)(Nr - 1)));
+    inv_r[j] = 1.0 / r[j];
+  }
+  for (int j = 0; j < Nr; ++j) {
+    const int st = std::min(std::max(j - kStencil / 2, 0), Nr - kStencil);
+    s0[j] = st;
+    double w[3][kStencil];
+    fd_weights(r[j], &r[st], kStencil, w);
+    for (int t = 0; t < kStencil; ++t) D1[j * kStencil + t] = w[1][t];
+    const double lo = j > 0 ? r[j] - r[j - 1] : 1e300;
+    const double hi = j < Nr - 1 ? r[j + 1] - r[j] : 1e300;
+    drm[j] = std::min(lo, hi);
+  }
+  fill_twiddles(Nz, reinterpret_cast<double2 *>(host + L.twz));
+  fill_twiddles(Ntheta, reinterpret_cast<double2 *>(host + L.twt));
+  *reinterpret_cast<unsigned long long *>(host + L.rate) = 0ull;   // CFL slot starts at zero
+
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(base, host, L.table_end, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaGetLastError();
+    return TC_ERR_CUDA;
+  }
+  p.rad = Radial{reinterpret_cast<const double *>(base + L.r),
+                 reinterpret_cast<const double *>(base + L.inv_r),
+                 reinterpret_cast<const double *>(base + L.D1), nullptr,
+                 reinterpret_cast<const double *>(base + L.dr), nullptr,
+                 reinterpret_cast<const int *>(base + L.s0)};
+  p.alpha = 2.0 * M_PI / Lz;
+  p.Gr = (Ra != 0.0) ? Ra / Pr : 0.0;
+  p.dth = 2.0 * M_PI / s.Nt;
+  p.dz = Lz / s.Nz;
+  p.pz = make_plan(s.Nz);
+  p.pt = make_plan(s.Nt);
+  p.twz = reinterpret_cast<const double2 *>(base + L.twz);
+  p.twt = reinterpret_cast<const double2 *>(base + L.twt);
+  double2 *V = reinterpret_cast<double2 *>(base + L.V);
+  double2 *W = reinterpret_cast<double2 *>(base + L.W);
+  unsigned long long *rate = reinterpret_cast<unsigned long long *>(base + L.rate);
+
+  cudaFuncSetAttribute(k_zinv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_zinv);
+  cudaFuncSetAttribute(k_theta<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sm_theta);
+  cudaFuncSetAttribute(k_zfwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_zfwd);
+  const int nmb = (s.NM + MB - 1) / MB;
+  const int nlb = (s.Nz + LB - 1) / LB;
+  k_zinv<double><<<dim3(nmb, s.Nr, s.nf), 256, sm_zinv, st>>>(
+      static_cast<const double2 *>(state_dev), V, p);
+  k_theta<double><<<dim3(nlb, s.Nr), 256, sm_theta, st>>>(V, W, p, rate, nullptr, 0);
+  k_zfwd<double><<<dim3(nmb, s.Nr), 256, sm_zfwd, st>>>(W, static_cast<double2 *>(n_dev), p);
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  if (cfl_rate) {
+    unsigned long long bits = 0;
+    if (cudaMemcpyAsync(&bits, rate, sizeof(bits), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return TC_ERR_CUDA;
+    }
+    std::memcpy(cfl_rate, &bits, sizeof(double));
+  }
+  return TC_OK;
+}

@@ -78,15 +78,6 @@ FFTPlan make_plan(int n) {
   return p;
 }
 
-namespace {
-
-bool smooth235(int n) {
-  if (n < 1) return false;
-  for (int f : {2, 3, 5})
-    while (n % f == 0) n /= f;
-  return n == 1;
-}
-
 // Finite-difference weights at x0 on nodes x[0..n-1] for derivatives 0..2
 // (Fornberg, Math. Comp. 51 (1988): weights of the Lagrange interpolant's
 // derivatives, built by adding one node at a time).
@@ -112,6 +103,24 @@ void fd_weights(double x0, const double *x, int n, double w[3][kStencil]) {
     }
     c1 = c2;
   }
+}
+
+// exp(-2 pi i t / n), t = 0..n-1, evaluated in long double.
+void fill_twiddles(int n, double2 *out) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < n; ++i) {
+    const long double a = 2.0L * pi * (long double)i / (long double)n;
+    out[i] = double2{(double)cosl(a), (double)(-sinl(a))};
+  }
+}
+
+namespace {
+
+bool smooth235(int n) {
+  if (n < 1) return false;
+  for (int f : {2, 3, 5})
+    while (n % f == 0) n /= f;
+  return n == 1;
 }
 
 // Clenshaw-Curtis weights on N+1 Chebyshev-Gauss-Lobatto points of [-1, 1]:
@@ -162,11 +171,7 @@ std::vector<double> dense_solve(std::vector<double> A, std::vector<double> b, in
 
 std::vector<double2> twiddles(int n) {
   std::vector<double2> t(n);
-  const long double pi = 3.141592653589793238462643383279502884L;
-  for (int i = 0; i < n; ++i) {
-    const long double a = 2.0L * pi * (long double)i / (long double)n;
-    t[i] = double2{(double)cosl(a), (double)(-sinl(a))};
-  }
+  fill_twiddles(n, t.data());
   return t;
 }
 

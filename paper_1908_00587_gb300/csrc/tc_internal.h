@@ -25,6 +25,10 @@ struct FFTPlan {
 
 FFTPlan make_plan(int n);
 
+// Host helpers shared by the set-up code (tc_host.cu).
+void fd_weights(double x0, const double *x, int n, double w[3][kStencil]);
+void fill_twiddles(int n, double2 *out);
+
 // Problem sizes.
 struct Sizes {
   int Nr, Nt, Nz, M, K, NM, NK, nmode, nf;

@@ -71,6 +71,7 @@ _SIGS = {
     "tc_stage_solve": [_P, _P, _D, _P, _P],
     "tc_get_timing": [_P, _P, _I, ctypes.POINTER(_I)],
     "tc_reset_timing": [_P],
+    "tc_nonlinear_noalloc": [_I, _I, _I, _D, _D, _D, _D, _P, _P, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -190,6 +191,19 @@ def tc_get_timing(ctx) -> dict:
 
 def tc_reset_timing(ctx):
     _check(_lib.tc_reset_timing(ctx), "tc_reset_timing")
+
+
+def tc_nonlinear_noalloc(Nr, Ntheta, Nz, eta, Lz, Ra, Pr, state_dev, n_dev, stream_ptr=None):
+    """Nonlinear terms with no device allocation (fixed 32 MiB static scratch).
+
+    For callers that cannot call cudaMalloc; see include/tc.h for the limits
+    and for why overlapping calls must be serialised.  Returns the CFL rate.
+    """
+    rate = ctypes.c_double(0.0)
+    _check(_lib.tc_nonlinear_noalloc(int(Nr), int(Ntheta), int(Nz), float(eta), float(Lz),
+                                     float(Ra), float(Pr), _ptr(state_dev)[0], _ptr(n_dev)[0],
+                                     stream_ptr, ctypes.byref(rate)), "tc_nonlinear_noalloc")
+    return rate.value
 
 
 def tc_status_string(s: int) -> str:
