@@ -107,6 +107,11 @@ tc_status tc_destroy(tc_ctx *ctx);
  *   "check"     1: report NaN/Inf produced by tc_step (default 1)
  *   "timing"    1: bracket every kernel launch with CUDA events on the
  *               context's stream (tc_get_timing); 0: off (default)
+ *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
+ *               never start their shared-memory copies, so each of their
+ *               bounded waits runs out (about 1 s) and tc_step returns
+ *               TC_ERR_TIMEOUT with the state left invalid.  Exercises the
+ *               device-side timeout path without faulting the GPU.
  * Errors: TC_ERR_ARG for an unknown key or out-of-range value. */
 tc_status tc_set_option(tc_ctx *ctx, const char *key, double value);
 

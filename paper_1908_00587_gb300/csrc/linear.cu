@@ -74,9 +74,12 @@ __device__ __forceinline__ void build_row(const Radial &rad, int Nr, int j, int 
     a[kBand] -= d;
 }
 
-// In-place band LU (Doolittle, no pivoting) of one operator, rows built on the fly.
+// In-place band LU (Doolittle, no pivoting) of one operator, rows built on the
+// fly.  Operator-major storage: L row j at L[(o*Nrp + j)*8], U row j at
+// U[(o*Nrp + j)*9] (inverse diagonal first, then the 8 super-diagonals).
 __device__ void band_factor(const Radial &rad, int Nr, int kind, double q2, double beta2,
-                            double idt, double ck, double *LU, int nop, int o) {
+                            double idt, double ck, double *L, double *U, int Nrp, int o) {
+  const long long base = (long long)o * Nrp;
   for (int j = 0; j < Nr; ++j) {
     double a[kBandW];
     build_row(rad, Nr, j, kind, q2, beta2, idt, ck, a);
@@ -84,31 +87,38 @@ __device__ void band_factor(const Radial &rad, int Nr, int kind, double q2, doub
     for (int e = 0; e < kBand; ++e) {
       const int i = j - kBand + e;
       if (i < 0) continue;
-      const double l = a[e] * LU[((long long)i * kBandW + kBand) * nop + o];
+      const double *Ui = U + (base + i) * (kBand + 1);
+      const double l = a[e] * Ui[0];
       a[e] = l;
 #pragma unroll
       for (int f = 1; f <= kBand; ++f) {
-        if (e + f < kBandW) a[e + f] -= l * LU[((long long)i * kBandW + kBand + f) * nop + o];
+        if (e + f < kBandW) a[e + f] -= l * Ui[f];
       }
     }
     a[kBand] = 1.0 / a[kBand];
+    double *Lj = L + (base + j) * kBand;
+    double *Uj = U + (base + j) * (kBand + 1);
 #pragma unroll
-    for (int e = 0; e < kBandW; ++e) LU[((long long)j * kBandW + e) * nop + o] = a[e];
+    for (int e = 0; e < kBand; ++e) Lj[e] = a[e];
+#pragma unroll
+    for (int f = 0; f <= kBand; ++f) Uj[f] = a[kBand + f];
   }
 }
 
-// Solve with stored factors, in place on x[j * xs], j = 0..Nr-1.
+// Solve with stored factors by one thread, in place on x[j * xs] (set-up use:
+// influence data).  The sweep kernel below does the per-step solves.
 template <typename V>
-__device__ void band_solve(const double *__restrict__ LU, int nop, int o, int Nr, V *x,
-                           long long xs) {
+__device__ void band_solve(const double *__restrict__ L, const double *__restrict__ U, int Nrp,
+                           int o, int Nr, V *__restrict__ x, long long xs) {
+  const long long base = (long long)o * Nrp;
   V w[kBand];
 #pragma unroll
   for (int e = 0; e < kBand; ++e) w[e] = V{};
   for (int j = 0; j < Nr; ++j) {
+    const double *row = L + (base + j) * kBand;
     V acc = x[j * xs];
-    const double *row = LU + (long long)j * kBandW * nop + o;
 #pragma unroll
-    for (int e = 0; e < kBand; ++e) axpy(acc, row[e * nop], w[e]);
+    for (int e = 0; e < kBand; ++e) axpy(acc, row[e], w[e]);
 #pragma unroll
     for (int e = 0; e < kBand - 1; ++e) w[e] = w[e + 1];
     w[kBand - 1] = acc;
@@ -117,11 +127,11 @@ __device__ void band_solve(const double *__restrict__ LU, int nop, int o, int Nr
 #pragma unroll
   for (int e = 0; e < kBand; ++e) w[e] = V{};
   for (int j = Nr - 1; j >= 0; --j) {
+    const double *row = U + (base + j) * (kBand + 1);
     V acc = x[j * xs];
-    const double *row = LU + (long long)j * kBandW * nop + o;
 #pragma unroll
-    for (int f = 1; f <= kBand; ++f) axpy(acc, row[(kBand + f) * nop], w[f - 1]);
-    acc = scale(acc, row[kBand * nop]);
+    for (int f = 1; f <= kBand; ++f) axpy(acc, row[f], w[f - 1]);
+    acc = scale(acc, row[0]);
 #pragma unroll
     for (int f = kBand - 1; f > 0; --f) w[f] = w[f - 1];
     w[0] = acc;
@@ -134,7 +144,7 @@ __global__ void k_factor_poisson(LinParams p) {
   if (o >= p.nopP || o == 0) return;   // (0,0) has no pressure solve
   const int m = o / (p.sz.K + 1), ak = o % (p.sz.K + 1);
   const double beta = p.alpha * ak;
-  band_factor(p.rad, p.sz.Nr, 0, (double)m * m, beta * beta, 0.0, 0.0, p.LUP, p.nopP, o);
+  band_factor(p.rad, p.sz.Nr, 0, (double)m * m, beta * beta, 0.0, 0.0, p.LP, p.UP, p.Nrp, o);
 }
 
 __global__ void k_factor_helm(LinParams p, const DevScalars *sc) {
@@ -146,13 +156,13 @@ __global__ void k_factor_helm(LinParams p, const DevScalars *sc) {
   if (t < p.nopH) {
     const int q = t / K1, ak = t % K1;
     const double beta = p.alpha * ak;
-    band_factor(p.rad, p.sz.Nr, 1, (double)q * q, beta * beta, idt, kCN, p.LUH, p.nopH, t);
+    band_factor(p.rad, p.sz.Nr, 1, (double)q * q, beta * beta, idt, kCN, p.LH, p.UH, p.Nrp, t);
   } else {
     const int o = t - p.nopH;
     const int m = o / K1, ak = o % K1;
     const double beta = p.alpha * ak;
-    band_factor(p.rad, p.sz.Nr, 1, (double)m * m, beta * beta, idt, kCN * p.kappaT, p.LUT,
-                p.nopT, o);
+    band_factor(p.rad, p.sz.Nr, 1, (double)m * m, beta * beta, idt, kCN * p.kappaT, p.LT, p.UT,
+                p.Nrp, o);
   }
 }
 
@@ -170,7 +180,7 @@ __global__ void k_influence(LinParams p, const DevScalars *sc) {
   const int oHp = (m + 1) * K1 + ak, oHm = (m >= 1 ? m - 1 : 1) * K1 + ak, oHz = m * K1 + ak;
   for (int s = 0; s < 2; ++s) {
     for (int j = 0; j < Nr; ++j) at(s, j) = (j == (s == 0 ? 0 : Nr - 1)) ? 1.0 : 0.0;
-    band_solve<double>(p.LUP, nop, o, Nr, &at(s, 0), nop);
+    band_solve<double>(p.LP, p.UP, p.Nrp, o, Nr, &at(s, 0), nop);
     for (int j = 0; j < Nr; ++j) {
       double up = 0.0, um = 0.0, z = 0.0;
       if (j > 0 && j < Nr - 1) {
@@ -187,9 +197,9 @@ __global__ void k_influence(LinParams p, const DevScalars *sc) {
       at(3 + 2 * s, j) = um;
       at(6 + s, j) = z;
     }
-    band_solve<double>(p.LUH, p.nopH, oHp, Nr, &at(2 + 2 * s, 0), nop);
-    band_solve<double>(p.LUH, p.nopH, oHm, Nr, &at(3 + 2 * s, 0), nop);
-    band_solve<double>(p.LUH, p.nopH, oHz, Nr, &at(6 + s, 0), nop);
+    band_solve<double>(p.LH, p.UH, p.Nrp, oHp, Nr, &at(2 + 2 * s, 0), nop);
+    band_solve<double>(p.LH, p.UH, p.Nrp, oHm, Nr, &at(3 + 2 * s, 0), nop);
+    band_solve<double>(p.LH, p.UH, p.Nrp, oHz, Nr, &at(6 + s, 0), nop);
   }
   // A[w][s] = div of homogeneous solution s at wall w (only u_r is non-zero
   // next to the wall; the wall values themselves are zero)
@@ -304,130 +314,325 @@ __device__ __forceinline__ double2 rhs_pm(const double2 *Yb, const double2 *N, l
   return y + kCN * N[comp * S + i];
 }
 
-__global__ void k_poisson(const double2 *__restrict__ Yb, const double2 *__restrict__ N,
-                          double2 *__restrict__ P, LinParams p) {
+// The radial solves work on split real / imaginary planes (the operators are
+// real): plane q of a field holds part q (0 re, 1 im) as [r][mode] doubles,
+// so one thread owns one real system and its loads coalesce across modes.
+
+// Poisson right-hand side: div R inside, 0 on the Neumann rows and for (0,0).
+__global__ void k_prhs(const double2 *__restrict__ Yb, const double2 *__restrict__ N,
+                       double *__restrict__ Ps, LinParams p) {
   const Sizes &s = p.sz;
-  const int mode = blockIdx.x * blockDim.x + threadIdx.x;
-  if (mode >= s.nmode || mode == 0) return;
-  const int m = mode / s.NK, kk = mode % s.NK;
-  const int kv = kval(kk, s.K, s.NK);
-  const double beta = p.alpha * kv;
-  const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
-  const int Nr = s.Nr;
-  for (int j = 0; j < Nr; ++j) {
-    double2 b = {0.0, 0.0};
-    if (j > 0 && j < Nr - 1) {
-      const int st = p.rad.s0[j];
-      double2 acc = {0.0, 0.0};
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.S) return;
+  const int j = (int)(i / s.nmode);
+  const int mode = (int)(i - (long long)j * s.nmode);
+  double2 b = {0.0, 0.0};
+  if (mode != 0 && j > 0 && j < s.Nr - 1) {
+    const int m = mode / s.NK, kk = mode % s.NK;
+    const double beta = p.alpha * kval(kk, s.K, s.NK);
+    const int st = p.rad.s0[j];
+    double2 acc = {0.0, 0.0};
 #pragma unroll
-      for (int t = 0; t < kStencil; ++t) {
-        const long long ii = (long long)(st + t) * s.nmode + mode;
-        const double2 rr = 0.5 * (rhs_pm(Yb, N, s.S, ii, 0) + rhs_pm(Yb, N, s.S, ii, 1));
-        acc = acc + (p.rad.D1[j * kStencil + t] * p.rad.r[st + t]) * rr;
-      }
-      const long long ij = (long long)j * s.nmode + mode;
-      const double2 rt = div_2i(rhs_pm(Yb, N, s.S, ij, 0) - rhs_pm(Yb, N, s.S, ij, 1));
-      const double2 rz = rhs_pm(Yb, N, s.S, ij, 2);
-      const double ir = p.rad.inv_r[j];
-      b = ir * acc + (m * ir) * mul_i(rt) + beta * mul_i(rz);
+    for (int t = 0; t < kStencil; ++t) {
+      const long long ii = (long long)(st + t) * s.nmode + mode;
+      const double2 rr = 0.5 * (rhs_pm(Yb, N, s.S, ii, 0) + rhs_pm(Yb, N, s.S, ii, 1));
+      acc = acc + (p.rad.D1[j * kStencil + t] * p.rad.r[st + t]) * rr;
     }
-    P[(long long)j * s.nmode + mode] = b;
+    const double2 rt = div_2i(rhs_pm(Yb, N, s.S, i, 0) - rhs_pm(Yb, N, s.S, i, 1));
+    const double2 rz = rhs_pm(Yb, N, s.S, i, 2);
+    const double ir = p.rad.inv_r[j];
+    b = ir * acc + (m * ir) * mul_i(rt) + beta * mul_i(rz);
   }
-  band_solve<double2>(p.LUP, p.nopP, o, Nr, P + mode, s.nmode);
+  Ps[i] = b.x;
+  Ps[s.S + i] = b.y;
 }
 
-__global__ void k_helm(const double2 *__restrict__ Yb, const double2 *__restrict__ N,
-                       const double2 *__restrict__ P, double2 *__restrict__ U0, LinParams p) {
+// Helmholtz right-hand sides of u+, u-, u_z (, T), wall values on the wall rows.
+// Mode (0,0): slot 0 carries u_theta's equation (u_r = 0), slot 1 is unused.
+__global__ void k_hrhs(const double2 *__restrict__ Yb, const double2 *__restrict__ N,
+                       const double *__restrict__ Ps, double *__restrict__ U, LinParams p) {
   const Sizes &s = p.sz;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= s.nf * s.nmode) return;
-  const int comp = t / s.nmode;
-  const int mode = t - comp * s.nmode;
-  const int m = mode / s.NK, kk = mode % s.NK;
-  const int kv = kval(kk, s.K, s.NK);
-  const int ak = kv < 0 ? -kv : kv;
-  const double beta = p.alpha * kv;
-  const int K1 = s.K + 1, Nr = s.Nr;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.S) return;
+  const int j = (int)(i / s.nmode);
+  const int mode = (int)(i - (long long)j * s.nmode);
   const long long S = s.S;
-  double2 *x = U0 + comp * S + mode;
-  const long long xs = s.nmode;
+  const bool wall = (j == 0 || j == s.Nr - 1);
+  double2 b[4] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
   if (mode == 0) {
-    if (comp == 1) return;
-    double lo = 0.0, hi = 0.0;
-    if (comp == 0) {
-      lo = p.Re_i;
-      hi = p.Re_o;
-    } else if (comp == 3) {
-      lo = 0.5;
-      hi = -0.5;
-    }
-    for (int j = 0; j < Nr; ++j) {
-      double2 b;
-      if (j == 0) {
-        b = {lo, 0.0};
-      } else if (j == Nr - 1) {
-        b = {hi, 0.0};
-      } else if (comp == 0) {
-        const long long ij = (long long)j * s.nmode;
-        b = div_2i(rhs_pm(Yb, N, S, ij, 0) - rhs_pm(Yb, N, S, ij, 1));
-      } else {
-        b = rhs_pm(Yb, N, S, (long long)j * s.nmode, comp);
-      }
-      x[j * xs] = b;
-    }
-    if (comp == 0) {
-      band_solve<double2>(p.LUH, p.nopH, 1 * K1 + 0, Nr, x, xs);
-      // u+ = i u_theta, u- = -i u_theta (u_r = 0)
-      for (int j = 0; j < Nr; ++j) {
-        const double2 ut = x[j * xs];
-        x[j * xs] = mul_i(ut);
-        U0[S + (long long)j * s.nmode] = double2{ut.y, -ut.x};
-      }
-    } else if (comp == 2) {
-      band_solve<double2>(p.LUH, p.nopH, 0, Nr, x, xs);
+    const bool lo = (j == 0);
+    if (wall) {
+      b[0] = {lo ? p.Re_i : p.Re_o, 0.0};
+      b[2] = {0.0, 0.0};
+      b[3] = {lo ? 0.5 : -0.5, 0.0};
     } else {
-      band_solve<double2>(p.LUT, p.nopT, 0, Nr, x, xs);
+      b[0] = div_2i(rhs_pm(Yb, N, S, i, 0) - rhs_pm(Yb, N, S, i, 1));
+      b[2] = rhs_pm(Yb, N, S, i, 2);
+      if (s.nf == 4) b[3] = rhs_pm(Yb, N, S, i, 3);
     }
-    return;
-  }
-  for (int j = 0; j < Nr; ++j) {
-    double2 b = {0.0, 0.0};
-    if (j > 0 && j < Nr - 1) {
-      const long long ij = (long long)j * s.nmode + mode;
-      b = rhs_pm(Yb, N, S, ij, comp);
-      if (comp < 3) {
-        const double2 pj = P[ij];
-        if (comp == 2) {
-          b = b - beta * mul_i(pj);
-        } else {
-          const int st = p.rad.s0[j];
-          double2 d1p = {0.0, 0.0};
+    b[1] = {0.0, 0.0};
+  } else if (wall) {
+    b[0] = b[1] = b[2] = b[3] = double2{0.0, 0.0};
+  } else {
+    const int m = mode / s.NK, kk = mode % s.NK;
+    const double beta = p.alpha * kval(kk, s.K, s.NK);
+    const int st = p.rad.s0[j];
+    double2 d1p = {0.0, 0.0};
 #pragma unroll
-          for (int q = 0; q < kStencil; ++q)
-            d1p = d1p + p.rad.D1[j * kStencil + q] * P[(long long)(st + q) * s.nmode + mode];
-          const double2 mp = (m * p.rad.inv_r[j]) * pj;
-          b = (comp == 0) ? b - (d1p - mp) : b - (d1p + mp);
+    for (int q = 0; q < kStencil; ++q) {
+      const long long o = (long long)(st + q) * s.nmode + mode;
+      d1p = d1p + p.rad.D1[j * kStencil + q] * double2{Ps[o], Ps[S + o]};
+    }
+    const double2 pj = {Ps[i], Ps[S + i]};
+    const double2 mp = (m * p.rad.inv_r[j]) * pj;
+    b[0] = rhs_pm(Yb, N, S, i, 0) - (d1p - mp);
+    b[1] = rhs_pm(Yb, N, S, i, 1) - (d1p + mp);
+    b[2] = rhs_pm(Yb, N, S, i, 2) - beta * mul_i(pj);
+    if (s.nf == 4) b[3] = rhs_pm(Yb, N, S, i, 3);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (c < s.nf) {
+      U[(2 * c) * S + i] = b[c].x;
+      U[(2 * c + 1) * S + i] = b[c].y;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched band sweeps with the factors streamed through shared memory.
+//
+// One CTA owns kSweepOps consecutive |k| values of one m and one field; its
+// 4 kSweepOps threads are the real systems (+k, -k) x (re, im) that share those
+// operators.  Thread 0 streams chunks of kSweepRows factor rows of all the
+// CTA's operators into a kSweepStages-deep ring with 1-D bulk async copies
+// (cp.async.bulk, TMA) that complete on an mbarrier per stage; every thread
+// sweeps its system from shared memory while the next chunks are in flight.
+// Right-hand sides / solutions stay in the split planes (one load per row,
+// prefetched a chunk ahead).  Waits are bounded: past kWaitNs the CTA raises
+// DevScalars::timeout, drains its own copies (bounded again) and returns.
+
+constexpr long long kWaitNs = 1000000000LL;   // 1 s
+constexpr int kSweepStageDoubles = kSweepOps * kSweepRows * (kBand + 1);
+constexpr size_t kSweepSmem = sizeof(double) * kSweepStages * kSweepStageDoubles;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase `phase` of a barrier to complete.
+__device__ bool mbar_wait(unsigned bar, unsigned phase) {
+  if (mbar_test(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    __nanosleep(64);
+    if (mbar_test(bar, phase)) return true;
+    if ((long long)(global_ns() - t0) > kWaitNs) return false;
+  }
+}
+
+struct SweepField {
+  const double *L, *U;   // factors of this field's operators
+  double *x;             // re plane; the im plane follows at x + S
+  int qshift;            // operator row q = m + qshift (|.|, 0 -> 1 when m = 0 for u-)
+  int skip00;            // 1: mode (0,0) has no system (pressure)
+};
+
+struct SweepArgs {
+  SweepField f[4];
+  int Nr, Nrp, K, NK, nmode;
+  long long S;
+  int arm;               // 0 only in the timeout self-test: never start the copies
+};
+
+template <int W>   // 8: L blocks (forward), 9: U blocks (backward)
+__device__ __forceinline__ void arm_chunk(unsigned bar, double *dst, const double *src, int Nrp,
+                                          int o0, int nops, int j0) {
+  const unsigned bytes = (unsigned)(kSweepRows * W * sizeof(double));
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(bar), "r"(bytes * (unsigned)nops) : "memory");
+  for (int g = 0; g < nops; ++g) {
+    const double *s = src + ((long long)(o0 + g) * Nrp + j0) * W;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(smem_u32(dst + g * kSweepRows * W)), "l"(s), "r"(bytes), "r"(bar) : "memory");
+  }
+}
+
+__global__ void __launch_bounds__(4 * kSweepOps)
+k_sweep(SweepArgs a, DevScalars *sc) {
+  extern __shared__ __align__(128) double ring_raw[];
+  double *ring[kSweepStages];
+#pragma unroll
+  for (int s = 0; s < kSweepStages; ++s) ring[s] = ring_raw + s * kSweepStageDoubles;
+  __shared__ __align__(8) unsigned long long bars[kSweepStages];
+  __shared__ int abort_flag;
+  const SweepField F = a.f[blockIdx.z];
+  const int m = blockIdx.y;
+  const int K1 = a.K + 1;
+  const int g0 = blockIdx.x * kSweepOps;
+  const int nops = min(kSweepOps, K1 - g0);
+  int q = m + F.qshift;
+  if (q < 0) q = -q;
+  if (F.qshift < 0 && m == 0) q = 1;
+  const int o0 = q * K1 + g0;
+  const int g = threadIdx.x >> 2;
+  const int part = threadIdx.x & 1;
+  const int neg = (threadIdx.x >> 1) & 1;
+  const int ak = g0 + g;
+  const int kk = neg ? a.NK - ak : ak;
+  bool active = (g < nops) && !(neg && ak == 0) && !(F.skip00 && m == 0 && ak == 0);
+  double *x = F.x + part * a.S + (long long)m * a.NK + (active ? kk : 0);
+  const long long xs = a.nmode;
+  const int nch = (a.Nr + kSweepRows - 1) / kSweepRows;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < kSweepStages; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bars[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned phase[kSweepStages] = {0, 0, 0};
+  int armed[kSweepStages] = {0, 0, 0};   // meaningful on thread 0
+  // chunk sequence: forward L chunks 0..nch-1, then backward U chunks nch-1..0
+  const int total = 2 * nch;
+  auto arm = [&](int step, int s) {
+    if (!a.arm) return;
+    if (step < nch)
+      arm_chunk<kBand>(smem_u32(&bars[s]), ring[s], F.L, a.Nrp, o0, nops, step * kSweepRows);
+    else
+      arm_chunk<kBand + 1>(smem_u32(&bars[s]), ring[s], F.U, a.Nrp, o0, nops,
+                           (total - 1 - step) * kSweepRows);
+    armed[s] = 1;
+  };
+  if (threadIdx.x == 0)
+    for (int s = 0; s < kSweepStages && s < total; ++s) arm(s, s);
+
+  double w[kBand];
+#pragma unroll
+  for (int e = 0; e < kBand; ++e) w[e] = 0.0;
+  double xa[kSweepRows];
+  {
+#pragma unroll
+    for (int r = 0; r < kSweepRows; ++r) xa[r] = (active && r < a.Nr) ? x[r * xs] : 0.0;
+  }
+  bool ok = true;
+  for (int step = 0; step < total; ++step) {
+    const int s = step % kSweepStages;
+    const bool fwd = step < nch;
+    const int c = fwd ? step : total - 1 - step;
+    const int j0 = c * kSweepRows;
+    if (fwd && step == nch - 1) {
+      // backward sweep starts from the chunk just finished: nothing to prefetch
+    }
+    const bool done = mbar_wait(smem_u32(&bars[s]), phase[s]);
+    if (!done) {
+      ok = false;
+      atomicOr(&abort_flag, 1);
+    } else {
+      phase[s] ^= 1u;
+      if (threadIdx.x == 0) armed[s] = 0;   // its copies have landed
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    if (active) {
+      if (fwd) {
+        const double *Lc = ring[s] + g * kSweepRows * kBand;
+#pragma unroll
+        for (int r = 0; r < kSweepRows; ++r) {
+          const int j = j0 + r;
+          if (j < a.Nr) {
+            const double *row = Lc + r * kBand;
+            double far = xa[r], near = 0.0;
+#pragma unroll
+            for (int e = 0; e < kBand - 2; ++e) far -= row[e] * w[e];
+            near -= row[kBand - 2] * w[kBand - 2];
+            far += near;
+            far -= row[kBand - 1] * w[kBand - 1];
+#pragma unroll
+            for (int e = 0; e < kBand - 1; ++e) w[e] = w[e + 1];
+            w[kBand - 1] = far;
+            x[j * xs] = far;
+          }
+        }
+        // prefetch the next forward chunk, or the last chunk for the backward sweep
+        if (c + 1 < nch) {
+#pragma unroll
+          for (int r = 0; r < kSweepRows; ++r) {
+            const int j = j0 + kSweepRows + r;
+            xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < kBand; ++e) w[e] = 0.0;
+#pragma unroll
+          for (int r = 0; r < kSweepRows; ++r) {
+            const int j = j0 + r;
+            xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
+          }
+        }
+      } else {
+        const double *Uc = ring[s] + g * kSweepRows * (kBand + 1);
+#pragma unroll
+        for (int r = kSweepRows - 1; r >= 0; --r) {
+          const int j = j0 + r;
+          if (j < a.Nr) {
+            const double *row = Uc + r * (kBand + 1);
+            double far = xa[r], near = 0.0;
+#pragma unroll
+            for (int f = kBand; f >= 3; --f) far -= row[f] * w[f - 1];
+            near -= row[2] * w[1];
+            far += near;
+            far -= row[1] * w[0];
+            far *= row[0];
+#pragma unroll
+            for (int f = kBand - 1; f > 0; --f) w[f] = w[f - 1];
+            w[0] = far;
+            x[j * xs] = far;
+          }
+        }
+        if (c > 0) {
+#pragma unroll
+          for (int r = 0; r < kSweepRows; ++r) xa[r] = x[(j0 - kSweepRows + r) * xs];
         }
       }
     }
-    x[j * xs] = b;
+    __syncthreads();   // every thread is done with stage s
+    if (threadIdx.x == 0 && step + kSweepStages < total) arm(step + kSweepStages, s);
   }
-  if (comp == 0) {
-    band_solve<double2>(p.LUH, p.nopH, (m + 1) * K1 + ak, Nr, x, xs);
-  } else if (comp == 1) {
-    band_solve<double2>(p.LUH, p.nopH, (m >= 1 ? m - 1 : 1) * K1 + ak, Nr, x, xs);
-  } else if (comp == 2) {
-    band_solve<double2>(p.LUH, p.nopH, m * K1 + ak, Nr, x, xs);
-  } else {
-    band_solve<double2>(p.LUT, p.nopT, m * K1 + ak, Nr, x, xs);
+  if (!ok) atomicOr(&sc->timeout, 1);
+  if (abort_flag && threadIdx.x == 0) {
+    // drain the copies still in flight into this CTA's ring, bounded again
+    for (int s = 0; s < kSweepStages; ++s)
+      if (armed[s]) mbar_wait(smem_u32(&bars[s]), phase[s]);
   }
 }
 
 // Influence coefficients per mode: alpha = -Ainv [div u0 (r_i), div u0 (r_o)].
-__global__ void k_alpha(const double2 *__restrict__ U0, double2 *__restrict__ alpha, LinParams p) {
+__global__ void k_alpha(const double *__restrict__ U, double2 *__restrict__ alpha, LinParams p) {
   const Sizes &s = p.sz;
   const int mode = blockIdx.x * blockDim.x + threadIdx.x;
   if (mode >= s.nmode || mode == 0) return;
+  const long long S = s.S;
   const int m = mode / s.NK, kk = mode % s.NK;
   const int kv = kval(kk, s.K, s.NK);
   const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
@@ -439,7 +644,8 @@ __global__ void k_alpha(const double2 *__restrict__ U0, double2 *__restrict__ al
 #pragma unroll
     for (int t = 0; t < kStencil; ++t) {
       const long long ii = (long long)(st + t) * s.nmode + mode;
-      const double2 ur = 0.5 * (U0[ii] + U0[s.S + ii]);
+      const double2 up = {U[ii], U[S + ii]}, um = {U[2 * S + ii], U[3 * S + ii]};
+      const double2 ur = 0.5 * (up + um);
       acc = acc + p.rad.D1[j * kStencil + t] * (p.rad.r[st + t] * ur);
     }
     d[w] = p.rad.inv_r[j] * acc;
@@ -452,7 +658,7 @@ __global__ void k_alpha(const double2 *__restrict__ U0, double2 *__restrict__ al
       double2{-(a10 * d[0].x + a11 * d[1].x), -(a10 * d[0].y + a11 * d[1].y)};
 }
 
-__global__ void k_correct(const double2 *__restrict__ U0, const double2 *__restrict__ P0,
+__global__ void k_correct(const double *__restrict__ U, const double *__restrict__ Ps,
                           const double2 *__restrict__ alpha, double2 *__restrict__ Xout,
                           double2 *__restrict__ Pout, LinParams p, DevScalars *sc) {
   const Sizes &s = p.sz;
@@ -461,9 +667,14 @@ __global__ void k_correct(const double2 *__restrict__ U0, const double2 *__restr
   const int j = (int)(i / s.nmode);
   const int mode = (int)(i - (long long)j * s.nmode);
   const long long S = s.S;
-  double2 up = U0[i], um = U0[S + i], uz = U0[2 * S + i];
+  double2 up = {U[i], U[S + i]}, um = {U[2 * S + i], U[3 * S + i]},
+          uz = {U[4 * S + i], U[5 * S + i]};
   double2 pr = {0.0, 0.0};
-  if (mode != 0) {
+  double2 xr, xt;
+  if (mode == 0) {
+    xr = {0.0, 0.0};   // u_r = 0; slot 0 holds u_theta
+    xt = up;
+  } else {
     const int m = mode / s.NK, kk = mode % s.NK;
     const int kv = kval(kk, s.K, s.NK);
     const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
@@ -472,7 +683,7 @@ __global__ void k_correct(const double2 *__restrict__ U0, const double2 *__restr
     const long long fs = (long long)s.Nr * p.nopP;
     const long long jo = (long long)j * p.nopP + o;
     const double *F = p.infl;
-    pr = P0[i];
+    pr = double2{Ps[i], Ps[S + i]};
     pr = pr + F[0 * fs + jo] * a;
     pr = pr + F[1 * fs + jo] * b;
     up = up + F[2 * fs + jo] * a;
@@ -482,16 +693,16 @@ __global__ void k_correct(const double2 *__restrict__ U0, const double2 *__restr
     // u_z of a homogeneous solution = -i beta zeta
     uz = uz + (-beta * F[6 * fs + jo]) * mul_i(a);
     uz = uz + (-beta * F[7 * fs + jo]) * mul_i(b);
+    xr = 0.5 * (up + um);
+    xt = div_2i(up - um);
   }
-  const double2 xr = 0.5 * (up + um);
-  const double2 xt = div_2i(up - um);
   Xout[i] = xr;
   Xout[S + i] = xt;
   Xout[2 * S + i] = uz;
   bool bad = !(isfinite(xr.x) && isfinite(xr.y) && isfinite(xt.x) && isfinite(xt.y) &&
                isfinite(uz.x) && isfinite(uz.y));
   if (s.nf == 4) {
-    const double2 T = U0[3 * S + i];
+    const double2 T = {U[6 * S + i], U[7 * S + i]};
     Xout[3 * S + i] = T;
     bad = bad || !(isfinite(T.x) && isfinite(T.y));
   }
@@ -554,7 +765,24 @@ __global__ void k_symmetrise(double2 *__restrict__ X, Sizes s) {
 
 inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+SweepArgs sweep_args(const tc_ctx *c) {
+  SweepArgs a{};
+  a.Nr = c->sz.Nr;
+  a.Nrp = c->lin.Nrp;
+  a.K = c->sz.K;
+  a.NK = c->sz.NK;
+  a.nmode = c->sz.nmode;
+  a.S = c->sz.S;
+  a.arm = c->selftest_no_copy ? 0 : 1;
+  return a;
+}
+
 }  // namespace
+
+void setup_linear(tc_ctx *c) {
+  (void)c;
+  cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem);
+}
 
 void launch_factor_poisson(tc_ctx *c) {
   LaunchScope ls(c, KFACTH);
@@ -586,32 +814,51 @@ void launch_rhs(tc_ctx *c, const double2 *X, const double2 *N0) {
 void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout) {
   const Sizes &s = c->sz;
   const LinParams &p = c->lin;
+  double *U = reinterpret_cast<double *>(c->U0);
+  {
+    LaunchScope ls(c, KPRHS);
+    k_prhs<<<blocks(s.S, 128), 128, 0, c->stream>>>(c->Yb, N, c->Ps, p);
+  }
   {
     LaunchScope ls(c, KPOIS);
-    k_poisson<<<blocks(s.nmode, 64), 64, 0, c->stream>>>(c->Yb, N, c->P, p);
+    SweepArgs sa = sweep_args(c);
+    sa.f[0] = SweepField{p.LP, p.UP, c->Ps, 0, 1};
+    k_sweep<<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, 1), 4 * kSweepOps, kSweepSmem,
+              c->stream>>>(
+        sa, c->scal);
+  }
+  {
+    LaunchScope ls(c, KHRHS);
+    k_hrhs<<<blocks(s.S, 128), 128, 0, c->stream>>>(c->Yb, N, c->Ps, U, p);
   }
   {
     LaunchScope ls(c, KHELM);
-    k_helm<<<blocks((long long)s.nf * s.nmode, 64), 64, 0, c->stream>>>(c->Yb, N, c->P, c->U0,
-                                                                        p);
+    SweepArgs sa = sweep_args(c);
+    sa.f[0] = SweepField{p.LH, p.UH, U + 0 * s.S, +1, 0};
+    sa.f[1] = SweepField{p.LH, p.UH, U + 2 * s.S, -1, 0};
+    sa.f[2] = SweepField{p.LH, p.UH, U + 4 * s.S, 0, 0};
+    if (s.nf == 4) sa.f[3] = SweepField{p.LT, p.UT, U + 6 * s.S, 0, 0};
+    k_sweep<<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, s.nf), 4 * kSweepOps, kSweepSmem,
+              c->stream>>>(
+        sa, c->scal);
   }
   {
     LaunchScope ls(c, KALPHA);
-    k_alpha<<<blocks(s.nmode, 128), 128, 0, c->stream>>>(c->U0, c->alpha_buf, p);
+    k_alpha<<<blocks(s.nmode, 128), 128, 0, c->stream>>>(U, c->alpha_buf, p);
   }
   LaunchScope ls(c, KCORR);
-  k_correct<<<blocks(s.S, 128), 128, 0, c->stream>>>(c->U0, c->P, c->alpha_buf, Xout, Pout, p,
+  k_correct<<<blocks(s.S, 128), 128, 0, c->stream>>>(U, c->Ps, c->alpha_buf, Xout, Pout, p,
                                                       c->scal);
 }
 
 void launch_state_check(tc_ctx *c, const double2 *X) {
-  LaunchScope ls(c, KCORR);
+  LaunchScope ls(c, KCHECK);
   k_state_check<<<blocks((long long)c->sz.nf * c->sz.S, 256), 256, 0, c->stream>>>(X, c->sz,
                                                                                  c->scal);
 }
 
 void launch_symmetrise(tc_ctx *c, double2 *X) {
-  LaunchScope ls(c, KCORR);
+  LaunchScope ls(c, KCHECK);
   k_symmetrise<<<blocks((long long)c->sz.nf * c->sz.Nr * (c->sz.K + 1), 256), 256, 0,
                  c->stream>>>(X, c->sz);
 }

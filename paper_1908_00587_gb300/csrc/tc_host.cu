@@ -19,7 +19,7 @@ namespace tc {
 
 const char *const kKernelNames[KNUM] = {
     "k_zinv", "k_theta", "k_zfwd", "k_dt_policy", "k_factor", "k_influence",
-    "k_rhs", "k_poisson", "k_helm", "k_alpha", "k_correct", "k_diag"};
+    "k_rhs", "k_prhs", "k_psolve", "k_hrhs", "k_hsolve", "k_alpha", "k_correct", "k_diag", "k_check"};
 
 LaunchScope::LaunchScope(tc_ctx *c_, int id_) : c(c_), id(id_) {
   c->launches++;
@@ -285,6 +285,7 @@ void allocate(tc_ctx *c) {
   c->Yb = dalloc<double2>(c, (size_t)nf * S);
   c->U0 = dalloc<double2>(c, (size_t)nf * S);
   c->P = dalloc<double2>(c, (size_t)S);
+  c->Ps = dalloc<double>(c, (size_t)2 * S);
   c->base_dev = dalloc<double2>(c, (size_t)nf * S);
   c->alpha_buf = dalloc<double2>(c, (size_t)2 * s.nmode);
   c->V = dalloc<double2>(c, (size_t)3 * nf * s.Nr * s.Nz * s.NM);
@@ -302,9 +303,17 @@ void allocate(tc_ctx *c) {
   c->lin.nopP = s.NM * K1;
   c->lin.nopH = (s.NM + 1) * K1;
   c->lin.nopT = c->has_T ? s.NM * K1 : 0;
-  c->LUP = dalloc<double>(c, (size_t)s.Nr * kBandW * c->lin.nopP);
-  c->LUH = dalloc<double>(c, (size_t)s.Nr * kBandW * c->lin.nopH);
-  c->LUT = dalloc<double>(c, (size_t)s.Nr * kBandW * std::max(c->lin.nopT, 1));
+  const int Nrp = (s.Nr + kSweepRows - 1) / kSweepRows * kSweepRows;
+  c->lin.Nrp = Nrp;
+  auto band = [&](int nop, double **L, double **U) {
+    *L = dalloc<double>(c, (size_t)std::max(nop, 1) * Nrp * kBand);
+    *U = dalloc<double>(c, (size_t)std::max(nop, 1) * Nrp * (kBand + 1));
+    ck(cudaMemset(*L, 0, sizeof(double) * std::max(nop, 1) * Nrp * kBand));
+    ck(cudaMemset(*U, 0, sizeof(double) * std::max(nop, 1) * Nrp * (kBand + 1)));
+  };
+  band(c->lin.nopP, &c->LP, &c->UP);
+  band(c->lin.nopH, &c->LH, &c->UH);
+  band(c->lin.nopT, &c->LT, &c->UT);
   c->infl = dalloc<double>(c, (size_t)8 * s.Nr * c->lin.nopP);
   c->Ainv = dalloc<double>(c, (size_t)4 * c->lin.nopP);
   c->diag_part = dalloc<double>(c, (size_t)s.Nr * 7);
@@ -356,9 +365,12 @@ void upload_tables(tc_ctx *c) {
   l.kappaT = c->has_T ? 1.0 / c->Pr : 1.0;
   l.Re_i = c->Re_i;
   l.Re_o = c->Re_o;
-  l.LUP = c->LUP;
-  l.LUH = c->LUH;
-  l.LUT = c->LUT;
+  l.LP = c->LP;
+  l.UP = c->UP;
+  l.LH = c->LH;
+  l.UH = c->UH;
+  l.LT = c->LT;
+  l.UT = c->UT;
   l.infl = c->infl;
   l.Ainv = c->Ainv;
 }
@@ -423,6 +435,7 @@ tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz, double Re
     allocate(c);
     upload_tables(c);
     setup_nonlinear(c);
+    setup_linear(c);
     if (c->smem_zinv > 227 * 1024 || c->smem_theta > 227 * 1024 || c->smem_zfwd > 227 * 1024) {
       tc_destroy(c);
       return TC_ERR_UNSUPPORTED;
@@ -467,6 +480,8 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
     c->cfl_limit = v;
   } else if (k == "check") {
     c->check = v != 0.0;
+  } else if (k == "selftest_no_copy") {
+    c->selftest_no_copy = v != 0.0;
   } else if (k == "timing") {
     c->timing = v != 0.0;
   } else {
@@ -693,6 +708,7 @@ tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
     for (int n = 0; n < nsteps; ++n) c->t += hist[n];
     if (dt_used) std::memcpy(dt_used, hist.data(), sizeof(double) * nsteps);
     c->dt_last = hist[nsteps - 1];
+    if (sc.timeout) return TC_ERR_TIMEOUT;
     if (c->check && sc.nonfinite) return TC_ERR_NONFINITE;
     if (c->cfl_limit > 0.0 && sc.rate_last * sc.dt > c->cfl_limit) return TC_ERR_CFL;
   } catch (const CudaError &e) {

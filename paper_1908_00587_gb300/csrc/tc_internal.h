@@ -16,6 +16,9 @@ constexpr int kStencil = 9;   // radial FD stencil (Sec. 2.1: 9 points by defaul
 constexpr int kBand = 8;      // half bandwidth of the radial operators
 constexpr int kBandW = 17;    // stored band entries per row (8 lower, diag, 8 upper)
 constexpr double kCN = 0.5;   // implicit weight of the predictor-corrector
+constexpr int kSweepRows = 16;    // rows per staged chunk of band factors
+constexpr int kSweepOps = 16;     // operators (|k| values) per sweep CTA
+constexpr int kSweepStages = 3;   // depth of the shared-memory ring
 
 struct FFTPlan {
   int n;
@@ -52,6 +55,7 @@ struct DevScalars {
   double rate_last;     // rate read by the policy
   int refactor;         // 1 when the factors must be rebuilt this step
   int nonfinite;        // set when a solve produced NaN/Inf
+  int timeout;          // set when a bounded device-side wait gave up
 };
 
 // Parameters of the nonlinear stage.
@@ -75,7 +79,10 @@ struct LinParams {
   double kappaT;        // 1/Pr
   double Re_i, Re_o;
   int nopP, nopH, nopT; // operator counts: Poisson, velocity Helmholtz, T Helmholtz
-  double *LUP, *LUH, *LUT;   // band factors [row][17][op]
+  int Nrp;              // rows padded to a multiple of kSweepRows
+  // band factors, operator-major: L [op][Nrp][8] (sub-diagonals), U [op][Nrp][9]
+  // (inverse diagonal, then 8 super-diagonals)
+  double *LP, *UP, *LH, *UH, *LT, *UT;
   double *infl;         // influence data [8][Nr][nopP]: pa pb upa uma upb umb za zb
   double *Ainv;         // [4][nopP]
 };
@@ -85,7 +92,8 @@ struct LinParams {
 namespace tc {
 // Kernels with per-launch timing (option "timing").
 enum KernelId {
-  KZINV, KTHETA, KZFWD, KDT, KFACTH, KINFL, KRHS, KPOIS, KHELM, KALPHA, KCORR, KDIAG, KNUM
+  KZINV, KTHETA, KZFWD, KDT, KFACTH, KINFL, KRHS, KPRHS, KPOIS, KHRHS, KHELM, KALPHA, KCORR,
+  KDIAG, KCHECK, KNUM
 };
 extern const char *const kKernelNames[KNUM];
 
@@ -102,6 +110,7 @@ struct tc_ctx {
   bool has_T;
   double cfl = 0.25, dt_max = 1e-3, cfl_limit = 0.0;
   int check = 1;
+  int selftest_no_copy = 0;   // test hook: sweeps never start their copies
   cudaStream_t stream = nullptr;
   bool poisoned = false;
   double t = 0.0, dt_last = 0.0, dt_prev_host = 0.0;
@@ -114,10 +123,11 @@ struct tc_ctx {
   std::vector<void *> allocs;
   size_t device_bytes = 0;
   double2 *X, *Xp, *N0, *N1, *Yb, *U0, *P, *V, *W, *alpha_buf, *base_dev;
+  double *Ps;   // particular pressure, split planes [2][S]
   double *d_r, *d_inv_r, *d_D1, *d_D2, *d_dr, *d_wr;
   int *d_s0;
   double2 *d_twz, *d_twt;
-  double *LUP, *LUH, *LUT, *infl, *Ainv;
+  double *LP, *UP, *LH, *UH, *LT, *UT, *infl, *Ainv;
   double *dt_hist;
   int dt_hist_cap = 0;
   double *diag_part, *diag_out;
@@ -156,6 +166,7 @@ void launch_rhs(tc_ctx *c, const double2 *X, const double2 *N0);
 void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout);
 void launch_check_finite(tc_ctx *c, const double2 *X, long long n);
 void launch_state_check(tc_ctx *c, const double2 *X);
+void setup_linear(tc_ctx *c);
 void launch_symmetrise(tc_ctx *c, double2 *X);
 
 // diag.cu

@@ -228,3 +228,21 @@ def test_cfl_limit_reports(tc):
         run.step(1, 1e-3)
     assert e.value.name == "TC_ERR_CFL"
     run.close()
+
+
+def test_sweep_wait_timeout_is_reported(tc):
+    """The radial sweeps wait on shared-memory copies with a 1 s bound; with
+    the copies never started (test hook) every wait runs out, the kernels
+    return, and the step reports TC_ERR_TIMEOUT instead of hanging."""
+    wl = Workload("to", Nr=16, Ntheta=12, Nz=12, eta=0.5, Lz=1.0, Re_i=50.0)
+    run = tc.Run.from_workload(wl)
+    run.set_option("selftest_no_copy", 1)
+    with pytest.raises(tc.TCError) as e:
+        run.step(1, 1e-3)
+    assert e.value.name == "TC_ERR_TIMEOUT"
+    run.close()
+    # a fresh context on the same device works normally afterwards
+    run = tc.Run.from_workload(wl)
+    run.step(2, 1e-3)
+    assert np.all(np.isfinite(run.get_state()))
+    run.close()
