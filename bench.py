@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", type=int, default=None, choices=[0, 1],
+                    help="override the workload's precision (0 FP64, 1 mixed)")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -54,7 +56,9 @@ def config_of(wl, extra=None):
     cfg = {"workload": f"{wl.name}: Nr={wl.Nr} Ntheta={wl.Ntheta} Nz={wl.Nz} eta={wl.eta} "
                        f"Re_i={wl.Re_i} Re_o={wl.Re_o} Ra={wl.Ra} Pr={wl.Pr} "
                        f"dt={'CFL dynamic' if wl.dt <= 0 else wl.dt}",
-           "grid_points": wl.points, "fields": 4 if wl.Ra else 3}
+           "grid_points": wl.points, "fields": 4 if wl.Ra else 3,
+           "precision": "mixed: FP32 transforms of u', FP64 mean-flow products and solves"
+           if getattr(wl, "precision", 0) else "fp64"}
     if extra:
         cfg.update(extra)
     return cfg
@@ -219,6 +223,8 @@ def run_gb300(args):
     from paper_1908_00587_gb300 import tc
 
     wl = WORKLOADS[args.workload]
+    if args.precision is not None:
+        wl = wl.scaled(precision=args.precision)
     run = tc.Run.from_workload(wl)
     stream = torch.cuda.current_stream()
     run.set_stream(stream.cuda_stream)
@@ -305,7 +311,8 @@ def run_gb300(args):
 
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if getattr(wl, "precision", 0) else "f64",
             "data": "synthetic",
             "config": config_of(wl, {"l2": "flushed between timed steps (512 MiB write)",
                                      "parallelism": f"replicas x{world}",

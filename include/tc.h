@@ -101,6 +101,12 @@ tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz,
 tc_status tc_destroy(tc_ctx *ctx);
 
 /* Set a numeric option.  Keys:
+ *   "precision" 0: FP64 throughout (default).  1: mixed -- the transforms and
+ *               the products u'.grad u' of the perturbation u' = u - U(r)
+ *               run in FP32; the products with the (0,0) mean-flow mode U,
+ *               the buoyancy, the radial band LU solves, the influence
+ *               matrix and the state stay FP64.  Its error against the FP64
+ *               path is measured, not bounded (see the tests).
  *   "cfl"       CFL coefficient of the dynamic step (default 0.25)
  *   "dt_max"    largest dynamic step (default 1e-3)
  *   "cfl_limit" abort a step with TC_ERR_CFL above this CFL number (default 0 = off)

@@ -47,6 +47,7 @@ class Workload:
     dt: float = 1e-3       # > 0 fixed step, <= 0 dynamic CFL step
     dt_max: float = 1e-3
     cfl: float = 0.25
+    precision: int = 0     # 0: FP64 throughout; 1: FP32 transforms of u' (mixed)
 
     @property
     def points(self) -> int:
@@ -72,7 +73,7 @@ WORKLOADS = {
     "tc_mixed_nr256_n512": Workload(
         "tc_mixed_nr256_n512", Nr=256, Ntheta=512, Nz=512, eta=0.875,
         Lz=2 * math.pi / 3.16, Re_i=1e4, amp=0.1, mp=16, kp=16, seed=3,
-        steps=50, dt=2e-6),
+        steps=50, dt=2e-6, precision=1),
     # Discrete adjoint.
     "tc_adjoint_nr64_n64": Workload(
         "tc_adjoint_nr64_n64", Nr=64, Ntheta=64, Nz=64, eta=0.5,

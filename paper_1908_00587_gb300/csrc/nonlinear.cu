@@ -47,6 +47,82 @@ __device__ __forceinline__ void load_tw(V2<T> *dst, const double2 *src, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = V2<T>{(T)src[i].x, (T)src[i].y};
 }
 
+// Mixed precision: u = U + u_b with U = (0, U_theta(r), U_z(r)) and Tbar(r)
+// the (0,0) mode of u_theta, u_z, T; u_b (everything else, including the
+// (0,0) mode of u_r) goes through the FP32 transforms, which supply
+// u_b.grad u_b with its curvature terms.  The products in which U or Tbar
+// takes part are diagonal in (m, k) and are formed here in FP64:
+//   N_r = -(a u_r - 2 (U_theta/r) u_theta) + [U_theta^2 / r]_(0,0)
+//   N_theta = -(a u_theta + (U_theta/r + U_theta') u_r)
+//   N_z = -(a u_z + U_z' u_r) + Gr T          N_T = -(a T + Tbar' u_r)
+// with a = i (m U_theta / r + beta U_z) and (u, T) the u_b coefficients, the
+// buoyancy Gr T on the full temperature.  In exact arithmetic the sum equals
+// the dealiased product: multiplying by a function of r creates no new modes.
+__device__ double2 mean_flow_terms(const NLParams &p, int g, int r, int m, int kk) {
+  const Sizes &s = p.sz;
+  const double *pr = p.prof + r * 8;
+  const double Ut = pr[0], Uz = pr[1], dUt = pr[2], dUz = pr[3], dTb = pr[4];
+  const double ir = p.rad.inv_r[r];
+  const long long i = (long long)r * s.nmode + (long long)m * s.NK + kk;
+  const bool mean = (m == 0 && kk == 0);
+  const double beta = p.alpha * kval(kk, s.K, s.NK);
+  const double al = m * Ut * ir + beta * Uz;              // a = i al (0 for the mean)
+  const double2 zero = {0.0, 0.0};
+  const double2 ur = p.Xfull[i];
+  auto ia = [&](double2 v) { return double2{-al * v.y, al * v.x}; };
+  if (g == 0) {
+    const double2 ut = mean ? zero : p.Xfull[s.S + i];
+    const double2 t = ia(ur);
+    double2 o = double2{-(t.x - 2.0 * Ut * ir * ut.x), -(t.y - 2.0 * Ut * ir * ut.y)};
+    if (mean) o.x += Ut * Ut * ir;
+    return o;
+  }
+  if (g == 1) {
+    const double2 ut = mean ? zero : p.Xfull[s.S + i];
+    const double2 t = ia(ut);
+    const double c = Ut * ir + dUt;
+    return double2{-(t.x + c * ur.x), -(t.y + c * ur.y)};
+  }
+  if (g == 2) {
+    const double2 uz = mean ? zero : p.Xfull[2 * s.S + i];
+    const double2 t = ia(uz);
+    double2 o = double2{-(t.x + dUz * ur.x), -(t.y + dUz * ur.y)};
+    if (s.nf == 4) {
+      const double2 T = p.Xfull[3 * s.S + i];
+      o.x += p.Gr * T.x;
+      o.y += p.Gr * T.y;
+    }
+    return o;
+  }
+  const double2 T = mean ? zero : p.Xfull[3 * s.S + i];
+  const double2 t = ia(T);
+  return double2{-(t.x + dTb * ur.x), -(t.y + dTb * ur.y)};
+}
+
+// Mean profiles of the (0,0) mode and their radial derivatives, one thread per r.
+__global__ void k_meanprof(const double2 *__restrict__ X, double *__restrict__ prof, Sizes s,
+                           Radial rad) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= s.Nr) return;
+  const int st = rad.s0[r];
+  double dUt = 0.0, dUz = 0.0, dTb = 0.0;
+#pragma unroll
+  for (int q = 0; q < kStencil; ++q) {
+    const long long o = (long long)(st + q) * s.nmode;
+    const double w = rad.D1[r * kStencil + q];
+    dUt += w * X[s.S + o].x;
+    dUz += w * X[2 * s.S + o].x;
+    if (s.nf == 4) dTb += w * X[3 * s.S + o].x;
+  }
+  const long long o = (long long)r * s.nmode;
+  prof[r * 8 + 0] = X[s.S + o].x;
+  prof[r * 8 + 1] = X[2 * s.S + o].x;
+  prof[r * 8 + 2] = dUt;
+  prof[r * 8 + 3] = dUz;
+  prof[r * 8 + 4] = dTb;
+  prof[r * 8 + 5] = (s.nf == 4) ? X[3 * s.S + o].x : 0.0;
+}
+
 // V layout: [3*c + d][r][l][m], d = 0 value, 1 d/dr, 2 d/dz.
 template <typename T>
 __global__ void k_zinv(const double2 *__restrict__ X, V2<T> *__restrict__ Vout, NLParams p) {
@@ -70,13 +146,17 @@ __global__ void k_zinv(const double2 *__restrict__ X, V2<T> *__restrict__ Vout, 
     const int kk = t - mi * s.NK;
     const long long col = (long long)(m0 + mi) * s.NK + kk;
     const double2 *Xc = X + (long long)c * s.S;
-    const double2 val = Xc[(long long)r * s.nmode + col];
+    double2 val = Xc[(long long)r * s.nmode + col];
     double2 dr = {0.0, 0.0};
 #pragma unroll
     for (int q = 0; q < kStencil; ++q) {
       const double2 x = Xc[(long long)(st + q) * s.nmode + col];
       dr.x += d1[q] * x.x;
       dr.y += d1[q] * x.y;
+    }
+    if (p.mixed && col == 0 && c != 0) {   // U_theta, U_z, Tbar stay out of FP32
+      val = double2{0.0, 0.0};
+      dr = double2{0.0, 0.0};
     }
     const double beta = p.alpha * kval(kk, s.K, s.NK);
     const int pos = kpos(kk, s.K, s.NK, Nz);
@@ -156,6 +236,8 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     const V2<T> t0 = b[2 * Nt], t1 = b[3 * Nt];   // (ut, ut_t), (ut_r, ut_z)
     const V2<T> z0 = b[4 * Nt], z1 = b[5 * Nt];   // (uz, uz_t), (uz_r, uz_z)
     const T ur = r0.x, ut = t0.x, uz = z0.x;
+    // full velocity for the CFL bound (mixed: the transforms carry u' only)
+    const double Ut = p.mixed ? p.prof[r * 8 + 0] : 0.0, Uz = p.mixed ? p.prof[r * 8 + 1] : 0.0;
     if (mode == 1) {
       nu = fmax(nu, sqrt((double)ur * ur + (double)ut * ut + (double)uz * uz));
       if (s.nf == 4) nT = fmax(nT, fabs((double)b[6 * Nt].x));
@@ -171,7 +253,7 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     T NT_ = 0;
     if (s.nf == 4) {
       const V2<T> T0 = b[6 * Nt], T1 = b[7 * Nt];
-      Nz_ += (T)p.Gr * T0.x;
+      if (!p.mixed) Nz_ += (T)p.Gr * T0.x;   // mixed: buoyancy added in FP64
       NT_ = -(ur * T1.x + ut_r * T0.y + uz * T1.y);
     }
     V2<T> *o = out + li * 2 * Nt + j;
@@ -179,7 +261,7 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     o[Nt] = V2<T>{Nz_, NT_};
     if (rate_bits) {
       const double a = fmax(fabs((double)ur) / p.rad.dr_min[r],
-                            fmax(fabs((double)ut) / (rr * p.dth), fabs((double)uz) / p.dz));
+                            fmax(fabs((double)ut + Ut) / (rr * p.dth), fabs((double)uz + Uz) / p.dz));
       rate = fmax(rate, a);
     }
   }
@@ -252,8 +334,13 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
     const int mi = rest % nm;
     const int g = rest / nm;
     const V2<T> v = res[(g * nm + mi) * Nz + kpos(kk, s.K, s.NK, Nz)];
-    N[(long long)g * s.S + (long long)r * s.nmode + (long long)(m0 + mi) * s.NK + kk] =
-        double2{(double)v.x * scale, (double)v.y * scale};
+    double2 out = double2{(double)v.x * scale, (double)v.y * scale};
+    if (p.mixed) {
+      const double2 lin = mean_flow_terms(p, g, r, m0 + mi, kk);
+      out.x += lin.x;
+      out.y += lin.y;
+    }
+    N[(long long)g * s.S + (long long)r * s.nmode + (long long)(m0 + mi) * s.NK + kk] = out;
   }
 }
 
@@ -282,11 +369,54 @@ void setup_nonlinear(tc_ctx *c) {
                        (int)c->smem_theta);
   cudaFuncSetAttribute(k_zfwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)c->smem_zfwd);
+  // FP32 copies of the transforms (mixed precision): same blocking by bytes
+  NLParams &q = c->nl32;
+  q = p;
+  const size_t e32 = sizeof(float2);
+  int MB32 = (int)(6144 / (3 * s.Nz));
+  MB32 = MB32 < 1 ? 1 : (MB32 > 8 ? 8 : MB32);
+  if (MB32 > s.NM) MB32 = s.NM;
+  int LB32 = (int)(8192 / (2 * s.nf * s.Nt));
+  LB32 = LB32 < 1 ? 1 : (LB32 > 8 ? 8 : LB32);
+  q.MB = MB32;
+  q.LB = LB32;
+  c->smem32_zinv = (size_t)(2 * 3 * MB32 * s.Nz + s.Nz) * e32;
+  c->smem32_theta = (size_t)(2 * LB32 * 2 * s.nf * s.Nt + s.Nt) * e32;
+  c->smem32_zfwd = (size_t)(2 * s.nf * MB32 * s.Nz + s.Nz) * e32;
+  cudaFuncSetAttribute(k_zinv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)c->smem32_zinv);
+  cudaFuncSetAttribute(k_theta<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)c->smem32_theta);
+  cudaFuncSetAttribute(k_zfwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)c->smem32_zfwd);
 }
 
 void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long long *rate_bits,
                       int mode) {
   const Sizes &s = c->sz;
+  if (c->precision == 1 && mode == 0) {
+    NLParams q = c->nl32;
+    q.mixed = 1;
+    q.Xfull = X;
+    q.prof = c->prof;
+    float2 *V = reinterpret_cast<float2 *>(c->V);
+    float2 *W = reinterpret_cast<float2 *>(c->W);
+    {
+      LaunchScope ls(c, KZINV);
+      k_meanprof<<<(s.Nr + 63) / 64, 64, 0, c->stream>>>(X, c->prof, s, q.rad);
+      k_zinv<float><<<dim3((s.NM + q.MB - 1) / q.MB, s.Nr, s.nf), 256, c->smem32_zinv,
+                      c->stream>>>(X, V, q);
+    }
+    {
+      LaunchScope ls(c, KTHETA);
+      k_theta<float><<<dim3((s.Nz + q.LB - 1) / q.LB, s.Nr), 256, c->smem32_theta,
+                       c->stream>>>(V, W, q, rate_bits, c->scal->norm_bits, 0);
+    }
+    LaunchScope ls(c, KZFWD);
+    k_zfwd<float><<<dim3((s.NM + q.MB - 1) / q.MB, s.Nr), 256, c->smem32_zfwd, c->stream>>>(
+        W, N, q);
+    return;
+  }
   const NLParams &p = c->nl;
   const int nmb = (s.NM + p.MB - 1) / p.MB;
   {

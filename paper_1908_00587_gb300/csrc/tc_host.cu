@@ -290,6 +290,7 @@ void allocate(tc_ctx *c) {
   c->alpha_buf = dalloc<double2>(c, (size_t)2 * s.nmode);
   c->V = dalloc<double2>(c, (size_t)3 * nf * s.Nr * s.Nz * s.NM);
   c->W = dalloc<double2>(c, (size_t)nf * s.Nr * s.Nz * s.NM);
+  c->prof = dalloc<double>(c, (size_t)8 * s.Nr);
   c->d_r = dalloc<double>(c, s.Nr);
   c->d_inv_r = dalloc<double>(c, s.Nr);
   c->d_D1 = dalloc<double>(c, (size_t)s.Nr * kStencil);
@@ -436,7 +437,9 @@ tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz, double Re
     upload_tables(c);
     setup_nonlinear(c);
     setup_linear(c);
-    if (c->smem_zinv > 227 * 1024 || c->smem_theta > 227 * 1024 || c->smem_zfwd > 227 * 1024) {
+    if (c->smem_zinv > 227 * 1024 || c->smem_theta > 227 * 1024 || c->smem_zfwd > 227 * 1024 ||
+        c->smem32_zinv > 227 * 1024 || c->smem32_theta > 227 * 1024 ||
+        c->smem32_zfwd > 227 * 1024) {
       tc_destroy(c);
       return TC_ERR_UNSUPPORTED;
     }
@@ -480,6 +483,9 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
     c->cfl_limit = v;
   } else if (k == "check") {
     c->check = v != 0.0;
+  } else if (k == "precision") {
+    if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
+    c->precision = (int)v;
   } else if (k == "selftest_no_copy") {
     c->selftest_no_copy = v != 0.0;
   } else if (k == "timing") {

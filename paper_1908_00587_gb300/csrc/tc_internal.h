@@ -69,6 +69,11 @@ struct NLParams {
   int LB;               // z rows per CTA in the theta kernel
   FFTPlan pz, pt;
   const double2 *twz, *twt;   // exp(-2 pi i t / N) tables (FP64 master copy)
+  // mixed precision: the transforms carry only the perturbation u' = u - U(r)
+  // (FP32); the products with the mean mode U are added in FP64 in k_zfwd
+  int mixed;
+  const double2 *Xfull;       // state (mixed only)
+  const double *prof;         // [r][8]: U_theta, U_z, dU_theta/dr, dU_z/dr, dTbar/dr, T mean
 };
 
 // Parameters of the linear stage.
@@ -132,7 +137,10 @@ struct tc_ctx {
   int dt_hist_cap = 0;
   double *diag_part, *diag_out;
   tc::DevScalars *scal;
-  tc::NLParams nl;
+  tc::NLParams nl, nl32;
+  int precision = 0;            // 0: FP64 everywhere; 1: FP32 transforms/products
+  double *prof = nullptr;       // mean-flow profile for the mixed path
+  size_t smem32_zinv = 0, smem32_theta = 0, smem32_zfwd = 0;
   tc::LinParams lin;
   size_t smem_zinv, smem_theta, smem_zfwd;
   long long launches = 0;        // kernels launched since tc_create

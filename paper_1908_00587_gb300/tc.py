@@ -228,6 +228,8 @@ class Run:
         if wl.dt <= 0:
             tc_set_option(run.ctx, "cfl", wl.cfl)
             tc_set_option(run.ctx, "dt_max", wl.dt_max)
+        if getattr(wl, "precision", 0):
+            tc_set_option(run.ctx, "precision", wl.precision)
         return run
 
     def close(self):
