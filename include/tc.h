@@ -151,8 +151,11 @@ tc_status tc_get_pressure(const tc_ctx *ctx, void *spec, int where);
  *          is made Hermitian (k > 0 kept); u' is zeroed at the wall nodes and
  *          scaled so that max over the physical grid of |u'| equals amp.
  *   tcoef  host, complex128 [mp+1][2kp+1] or NULL: T' = (1-x^2) x tcoef, scaled
- *          so that max |T'| = amp_T (ignored when Ra == 0 or amp_T <= 0).
- * Requires mp <= M and kp <= K. */
+ *          so that max |T'| = amp_T (ignored when Ra == 0 or amp_T == 0).
+ * A negative amp (amp_T) is taken as the scale factor itself, |amp| times
+ * curl psi, without the max-norm rescaling: this keeps the map from the
+ * coefficients to the state linear, as the gradient of
+ * tc_init_perturbation_adjoint assumes.  Requires mp <= M and kp <= K. */
 tc_status tc_init_perturbation(tc_ctx *ctx, const double *psi, int mp, int kp,
                                double amp, const double *tcoef, double amp_T);
 
@@ -180,6 +183,42 @@ tc_status tc_diagnostics(tc_ctx *ctx, tc_diag *out);
 tc_status tc_nonlinear(tc_ctx *ctx, const void *state_dev, void *n_dev, double *cfl_rate);
 tc_status tc_stage_solve(tc_ctx *ctx, const void *rhs_dev, double dt, void *x_out_dev,
                          void *p_out_dev);
+
+/* Discrete adjoint of one predictor-corrector step at fixed dt (FP64 path only;
+ * TC_ERR_UNSUPPORTED with precision 1).  adj (device, state layout) holds
+ * lambda^{n+1} on entry and lambda^n = P_H J(X^n)^T lambda^{n+1} on return,
+ * where J is the Jacobian of the step at state_n (device, state layout,
+ * caller-owned), transposed in the real Euclidean inner product of the stored
+ * (Re, Im) coefficients, and P_H is the orthogonal projection onto
+ * u(0,-k) = conj u(0,k).  The step's intermediate states are recomputed from
+ * state_n; the context's own state is not changed.  Errors: TC_ERR_ARG,
+ * TC_ERR_TIMEOUT, TC_ERR_OOM, TC_ERR_CUDA. */
+tc_status tc_adjoint_step(tc_ctx *ctx, const void *state_n_dev, double dt, void *adj_dev);
+
+/* Adjoint of the nonlinear stage at state_dev: xbar = (dN/dX)^T nbar (device
+ * buffers of the state layout; nbar holds cotangents of N_r, N_theta, N_z(, N_T)). */
+tc_status tc_nonlinear_adjoint(tc_ctx *ctx, const void *state_dev, const void *nbar_dev,
+                               void *xbar_dev);
+
+/* Adjoint of the linear part of one implicit stage at step dt: rbar (device,
+ * +- form like tc_stage_solve's rhs) = A^T xbar (device, primitive fields). */
+tc_status tc_stage_solve_adjoint(tc_ctx *ctx, const void *xbar_dev, double dt, void *rbar_dev);
+
+/* Objective of the differentiation form: *J = E_pert of the current state
+ * (1/2 int |u - u_base|^2 dV) and, when grad_dev (device, state layout) is
+ * non-NULL, dJ/dX = V w_j r_j c_m (u - u_base) (zero for T). */
+tc_status tc_objective(tc_ctx *ctx, double *J, void *grad_dev);
+
+/* Gradient with respect to the raw coefficients of the last
+ * tc_init_perturbation (the scales that made max|u'| = amp and max|T'| =
+ * amp_T are held fixed): lam_dev (device, state layout) is dJ/dX^0; psi_bar
+ * (host, complex128 [3][mp+1][2kp+1]) and tcoef_bar (host, nullable,
+ * [mp+1][2kp+1]) receive dJ/dRe + i dJ/dIm of each raw coefficient. */
+tc_status tc_init_perturbation_adjoint(tc_ctx *ctx, const void *lam_dev, int mp, int kp,
+                                       double *psi_bar, double *tcoef_bar);
+
+/* Scale factors the last tc_init_perturbation applied to curl psi and to T'. */
+tc_status tc_get_ic_scales(const tc_ctx *ctx, double *s_u, double *s_T);
 
 /* Per-kernel device times recorded while "timing" is on: fills up to cap
  * entries of out (host) and sets *count.  Synchronises the stream. */

@@ -412,13 +412,15 @@ class Model:
                          1j * beta * pr - g.dr(pz),
                          g.dr(r * pt) / r - 1j * m * pr / r])
 
-    def initial_state(self, psi_raw, T_raw=None):
+    def initial_state(self, psi_raw, T_raw=None, scales=None):
         """Basic state + u' = curl(psi) scaled to max|u'| = amp (Sec. 2.1).
 
         psi = (1 - x^2)^2 x raw coefficients; u' is zeroed at the wall nodes
         and scaled by a constant so that the largest Euclidean norm of u' over
         the physical grid equals ``amp``.  With temperature, T' = (1 - x^2) x
-        raw coefficients scaled so that max |T'| = amp_T.
+        raw coefficients scaled so that max |T'| = amp_T.  ``scales`` = (s_u,
+        s_T) applies fixed factors instead (the map is then linear in the
+        coefficients, as the gradient of the differentiation form assumes).
         """
         x = self.g.x
         prof = (1.0 - x * x) ** 2
@@ -426,14 +428,20 @@ class Model:
         u = self.curl(psi)
         u[:, 0] = 0.0
         u[:, -1] = 0.0
-        ph = [self.sp.to_physical(u[c]) for c in range(3)]
-        mag = np.sqrt(ph[0] ** 2 + ph[1] ** 2 + ph[2] ** 2).max()
         X = self.base.copy()
-        X[:3] += (self.wl.amp / mag) * u
-        if self.has_T and T_raw is not None and self.wl.amp_T > 0:
+        if scales is None:
+            ph = [self.sp.to_physical(u[c]) for c in range(3)]
+            mag = np.sqrt(ph[0] ** 2 + ph[1] ** 2 + ph[2] ** 2).max()
+            X[:3] += (self.wl.amp / mag) * u
+        else:
+            X[:3] += scales[0] * u
+        if self.has_T and T_raw is not None and (self.wl.amp_T > 0 or scales is not None):
             t = self.place(T_raw, 1.0 - x * x)
-            tmax = np.abs(self.sp.to_physical(t)).max()
-            X[3] += (self.wl.amp_T / tmax) * t
+            if scales is None:
+                tmax = np.abs(self.sp.to_physical(t)).max()
+                X[3] += (self.wl.amp_T / tmax) * t
+            else:
+                X[3] += scales[1] * t
         return X
 
     # ------------------------------------------------------------ diagnostics

@@ -477,6 +477,12 @@ __device__ __forceinline__ void arm_chunk(unsigned bar, double *dst, const doubl
   }
 }
 
+// TRANS = false: solve A x = b with A = L U (L then U).  TRANS = true: solve
+// A^T x = b = U^T L^T x: forward over U rows (column-oriented: after x_i is
+// known, its products with row i of U are added to the pending sums of rows
+// i+1..i+8), then backward over L rows the same way, so each chunk still only
+// needs its own rows of the factors.
+template <bool TRANS>
 __global__ void __launch_bounds__(4 * kSweepOps)
 k_sweep(SweepArgs a, DevScalars *sc) {
   extern __shared__ __align__(128) double ring_raw[];
@@ -517,11 +523,12 @@ k_sweep(SweepArgs a, DevScalars *sc) {
   const int total = 2 * nch;
   auto arm = [&](int step, int s) {
     if (!a.arm) return;
-    if (step < nch)
-      arm_chunk<kBand>(smem_u32(&bars[s]), ring[s], F.L, a.Nrp, o0, nops, step * kSweepRows);
+    const bool first = step < nch;   // forward pass
+    const int j0 = (first ? step : total - 1 - step) * kSweepRows;
+    if (first != TRANS)   // forward of A, or backward of A^T: L rows
+      arm_chunk<kBand>(smem_u32(&bars[s]), ring[s], F.L, a.Nrp, o0, nops, j0);
     else
-      arm_chunk<kBand + 1>(smem_u32(&bars[s]), ring[s], F.U, a.Nrp, o0, nops,
-                           (total - 1 - step) * kSweepRows);
+      arm_chunk<kBand + 1>(smem_u32(&bars[s]), ring[s], F.U, a.Nrp, o0, nops, j0);
     armed[s] = 1;
   };
   if (threadIdx.x == 0)
@@ -554,7 +561,58 @@ k_sweep(SweepArgs a, DevScalars *sc) {
     }
     __syncthreads();
     if (abort_flag) break;
-    if (active) {
+    if (active && TRANS) {
+      if (fwd) {
+        // U^T y = b: y_i = (b_i - pending_i) / u_ii, then pending_{i+f} += U(i, i+f) y_i
+        const double *Uc = ring[s] + g * kSweepRows * (kBand + 1);
+#pragma unroll
+        for (int r = 0; r < kSweepRows; ++r) {
+          const int j = j0 + r;
+          if (j < a.Nr) {
+            const double *row = Uc + r * (kBand + 1);
+            const double y = (xa[r] - w[0]) * row[0];
+#pragma unroll
+            for (int k = 0; k < kBand - 1; ++k) w[k] = w[k + 1] + row[k + 1] * y;
+            w[kBand - 1] = row[kBand] * y;
+            x[j * xs] = y;
+          }
+        }
+        if (c + 1 < nch) {
+#pragma unroll
+          for (int r = 0; r < kSweepRows; ++r) {
+            const int j = j0 + kSweepRows + r;
+            xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < kBand; ++e) w[e] = 0.0;
+#pragma unroll
+          for (int r = 0; r < kSweepRows; ++r) {
+            const int j = j0 + r;
+            xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
+          }
+        }
+      } else {
+        // L^T x = y: x_j = y_j - pending_j, then pending_{j-8+e} += L(j, j-8+e) x_j
+        const double *Lc = ring[s] + g * kSweepRows * kBand;
+#pragma unroll
+        for (int r = kSweepRows - 1; r >= 0; --r) {
+          const int j = j0 + r;
+          if (j < a.Nr) {
+            const double *row = Lc + r * kBand;
+            const double xj = xa[r] - w[0];
+#pragma unroll
+            for (int k = 0; k < kBand - 1; ++k) w[k] = w[k + 1] + row[kBand - 1 - k] * xj;
+            w[kBand - 1] = row[0] * xj;
+            x[j * xs] = xj;
+          }
+        }
+        if (c > 0) {
+#pragma unroll
+          for (int r = 0; r < kSweepRows; ++r) xa[r] = x[(j0 - kSweepRows + r) * xs];
+        }
+      }
+    } else if (active) {
       if (fwd) {
         const double *Lc = ring[s] + g * kSweepRows * kBand;
 #pragma unroll
@@ -710,6 +768,307 @@ __global__ void k_correct(const double *__restrict__ U, const double *__restrict
   if (bad) atomicOr(&sc->nonfinite, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the implicit stage (its linear part: the wall values are
+// constants) and of the explicit right-hand side, in the real Euclidean inner
+// product of stored (Re, Im) coefficients.  Transposes, in reverse order:
+//   primitive <- +- and influence correction (k_stT_correct, k_stT_alpha),
+//   Helmholtz solves (k_sweep<true>), Helmholtz right-hand side with grad p
+//   (k_stT_hrhs), Poisson solve (k_sweep<true>), div R (k_stT_prhs).
+// Multiplication by a complex constant a transposes to multiplication by
+// conj(a); a radial stencil transposes to the gather over the rows whose
+// stencil contains the node.
+
+// Lbar (primitive) -> cotangent of u0 in the Helmholtz slots (U planes).
+__global__ void k_stT_correct(const double2 *__restrict__ Lb, double *__restrict__ U, Sizes s) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.S) return;
+  const int mode = (int)(i % s.nmode);
+  const long long S = s.S;
+  const double2 xr = Lb[i], xt = Lb[S + i], xz = Lb[2 * S + i];
+  double2 up, um;
+  if (mode == 0) {
+    up = xt;                 // slot 0 carries u_theta
+    um = double2{0.0, 0.0};
+  } else {
+    // X_r = (u+ + u-)/2, X_theta = (u+ - u-)/(2i)
+    up = double2{0.5 * (xr.x - xt.y), 0.5 * (xr.y + xt.x)};
+    um = double2{0.5 * (xr.x + xt.y), 0.5 * (xr.y - xt.x)};
+  }
+  U[i] = up.x;
+  U[S + i] = up.y;
+  U[2 * S + i] = um.x;
+  U[3 * S + i] = um.y;
+  U[4 * S + i] = xz.x;
+  U[5 * S + i] = xz.y;
+  if (s.nf == 4) {
+    const double2 xT = Lb[3 * S + i];
+    U[6 * S + i] = xT.x;
+    U[7 * S + i] = xT.y;
+  }
+}
+
+// Per mode: alphabar = <homogeneous solutions, ubar>, dbar = -Ainv^T alphabar,
+// then the wall-divergence stencils scatter dbar into ubar0 (this thread owns
+// the mode's column).
+__global__ void k_stT_alpha(double *__restrict__ U, LinParams p) {
+  const Sizes &s = p.sz;
+  const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mode >= s.nmode || mode == 0) return;
+  const long long S = s.S;
+  const int m = mode / s.NK, kk = mode % s.NK;
+  const int kv = kval(kk, s.K, s.NK);
+  const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
+  const double beta = p.alpha * kv;
+  const long long fs = (long long)s.Nr * p.nopP;
+  const double *F = p.infl;
+  double2 ab[2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int j = 0; j < s.Nr; ++j) {
+    const long long ii = (long long)j * s.nmode + mode;
+    const long long jo = (long long)j * p.nopP + o;
+    const double2 up = {U[ii], U[S + ii]}, um = {U[2 * S + ii], U[3 * S + ii]};
+    const double2 uz = {U[4 * S + ii], U[5 * S + ii]};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double hp = F[(2 + 2 * q) * fs + jo], hm = F[(3 + 2 * q) * fs + jo];
+      const double zq = F[(6 + q) * fs + jo];
+      // u_z of a homogeneous solution is -i beta zeta: transpose is +i beta zeta
+      ab[q].x += hp * up.x + hm * um.x - beta * zq * uz.y;
+      ab[q].y += hp * up.y + hm * um.y + beta * zq * uz.x;
+    }
+  }
+  const int nop = p.nopP;
+  const double a00 = p.Ainv[o], a01 = p.Ainv[nop + o], a10 = p.Ainv[2 * nop + o],
+               a11 = p.Ainv[3 * nop + o];
+  const double2 d0 = {-(a00 * ab[0].x + a10 * ab[1].x), -(a00 * ab[0].y + a10 * ab[1].y)};
+  const double2 d1 = {-(a01 * ab[0].x + a11 * ab[1].x), -(a01 * ab[0].y + a11 * ab[1].y)};
+  for (int w = 0; w < 2; ++w) {
+    const int j = (w == 0) ? 0 : s.Nr - 1;
+    const int st = p.rad.s0[j];
+    const double2 d = (w == 0) ? d0 : d1;
+    for (int t = 0; t < kStencil; ++t) {
+      const double cf = 0.5 * p.rad.inv_r[j] * p.rad.D1[j * kStencil + t] * p.rad.r[st + t];
+      const long long ii = (long long)(st + t) * s.nmode + mode;
+      U[ii] += cf * d.x;
+      U[S + ii] += cf * d.y;
+      U[2 * S + ii] += cf * d.x;
+      U[3 * S + ii] += cf * d.y;
+    }
+  }
+}
+
+// bbar_H (U planes) -> Rbar (+- form, all slots) and pbar (Ps planes).
+__global__ void k_stT_hrhs(const double *__restrict__ U, double2 *__restrict__ Rb,
+                           double *__restrict__ Ps, LinParams p) {
+  const Sizes &s = p.sz;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.S) return;
+  const int j = (int)(i / s.nmode);
+  const int mode = (int)(i - (long long)j * s.nmode);
+  const long long S = s.S;
+  const bool interior = (j > 0 && j < s.Nr - 1);
+  double2 b[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    b[c] = (c < s.nf && interior) ? double2{U[(2 * c) * S + i], U[(2 * c + 1) * S + i]}
+                                  : double2{0.0, 0.0};
+  double2 pb = {0.0, 0.0};
+  if (mode == 0) {
+    // slot 0 = R_theta = (R+ - R-)/(2i): transpose (i/2) b0, -(i/2) b0
+    Rb[i] = double2{-0.5 * b[0].y, 0.5 * b[0].x};
+    Rb[S + i] = double2{0.5 * b[0].y, -0.5 * b[0].x};
+  } else {
+    Rb[i] = b[0];
+    Rb[S + i] = b[1];
+    const int m = mode / s.NK, kk = mode % s.NK;
+    const double beta = p.alpha * kval(kk, s.K, s.NK);
+    if (interior) {
+      const double mr = m * p.rad.inv_r[j];
+      // slot0: +(m/r) p, slot1: -(m/r) p, slot2: -i beta p (transpose +i beta)
+      pb.x = mr * (b[0].x - b[1].x) - beta * b[2].y;
+      pb.y = mr * (b[0].y - b[1].y) + beta * b[2].x;
+    }
+    // -D1^T (b0 + b1) over the interior rows whose stencil holds node j
+    const int jlo = max(1, j - 2 * kStencil), jhi = min(s.Nr - 2, j + 2 * kStencil);
+    for (int jj = jlo; jj <= jhi; ++jj) {
+      const int t = j - p.rad.s0[jj];
+      if (t < 0 || t >= kStencil) continue;
+      const double w = p.rad.D1[jj * kStencil + t];
+      const long long q = (long long)jj * s.nmode + mode;
+      pb.x -= w * (U[q] + U[2 * S + q]);
+      pb.y -= w * (U[S + q] + U[3 * S + q]);
+    }
+  }
+  Rb[2 * S + i] = b[2];
+  if (s.nf == 4) Rb[3 * S + i] = b[3];
+  Ps[i] = pb.x;
+  Ps[S + i] = pb.y;
+}
+
+// bbar_P (Ps planes) -> Rbar += div^T bbar_P (interior rows only, mode != 0).
+__global__ void k_stT_prhs(const double *__restrict__ Ps, double2 *__restrict__ Rb, LinParams p) {
+  const Sizes &s = p.sz;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.S) return;
+  const int sn = (int)(i / s.nmode);
+  const int mode = (int)(i - (long long)sn * s.nmode);
+  if (mode == 0) return;
+  const long long S = s.S;
+  const int m = mode / s.NK, kk = mode % s.NK;
+  const double beta = p.alpha * kval(kk, s.K, s.NK);
+  double2 rr = {0.0, 0.0}, rt = {0.0, 0.0}, rz = {0.0, 0.0};
+  const int jlo = max(1, sn - 2 * kStencil), jhi = min(s.Nr - 2, sn + 2 * kStencil);
+  for (int j = jlo; j <= jhi; ++j) {
+    const int t = sn - p.rad.s0[j];
+    if (t < 0 || t >= kStencil) continue;
+    const double w = p.rad.inv_r[j] * p.rad.D1[j * kStencil + t] * p.rad.r[sn];
+    const long long q = (long long)j * s.nmode + mode;
+    rr.x += w * Ps[q];
+    rr.y += w * Ps[S + q];
+  }
+  if (sn > 0 && sn < s.Nr - 1) {
+    const double2 bp = {Ps[i], Ps[S + i]};
+    const double mr = m * p.rad.inv_r[sn];
+    rt = double2{mr * bp.y, -mr * bp.x};        // (-i m / r) bp
+    rz = double2{beta * bp.y, -beta * bp.x};    // (-i beta) bp
+  }
+  // R_r = (R+ + R-)/2, R_theta = (R+ - R-)/(2i)
+  double2 a = Rb[i], b = Rb[S + i], z = Rb[2 * S + i];
+  a.x += 0.5 * rr.x - 0.5 * rt.y;
+  a.y += 0.5 * rr.y + 0.5 * rt.x;
+  b.x += 0.5 * rr.x + 0.5 * rt.y;
+  b.y += 0.5 * rr.y - 0.5 * rt.x;
+  z.x += rz.x;
+  z.y += rz.y;
+  Rb[i] = a;
+  Rb[S + i] = b;
+  Rb[2 * S + i] = z;
+}
+
+// R = Y' + c N (+- of primitive N): Ybar (+=) Rbar, Nbar (=, primitive) c N+-^T Rbar.
+__global__ void k_stT_split(const double2 *__restrict__ Rb, double2 *__restrict__ Yb,
+                            double2 *__restrict__ Nb, Sizes s, int accumulate) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.S) return;
+  const long long S = s.S;
+  const double2 rp = Rb[i], rm = Rb[S + i];
+  // N+ = N_r + i N_theta, N- = N_r - i N_theta
+  Nb[i] = double2{kCN * (rp.x + rm.x), kCN * (rp.y + rm.y)};
+  Nb[S + i] = double2{kCN * (rp.y - rm.y), kCN * (rm.x - rp.x)};
+  for (int c = 0; c < s.nf; ++c) {
+    const double2 r = Rb[c * S + i];
+    if (c >= 2) Nb[c * S + i] = double2{kCN * r.x, kCN * r.y};
+    if (accumulate) {
+      const double2 y = Yb[c * S + i];
+      Yb[c * S + i] = double2{y.x + r.x, y.y + r.y};
+    } else {
+      Yb[c * S + i] = r;
+    }
+  }
+}
+
+// Adjoint of Y' = X/dt + (1-c) L X + (1-c) N:  Xbar = transposed operator of
+// Ybar (primitive), Nbar += (1-c) (N+-)^T Ybar.
+__global__ void k_rhsT(const double2 *__restrict__ Yb, double2 *__restrict__ Xb,
+                       double2 *__restrict__ Nb, LinParams p, const DevScalars *sc) {
+  const Sizes &s = p.sz;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.S) return;
+  const int sn = (int)(i / s.nmode);
+  const int mode = (int)(i - (long long)sn * s.nmode);
+  const long long S = s.S;
+  const int m = mode / s.NK, kk = mode % s.NK;
+  const double beta = p.alpha * kval(kk, s.K, s.NK);
+  const double idt = 1.0 / sc->dt;
+  const double om = 1.0 - kCN;
+  const double ir = p.rad.inv_r[sn];
+  const double b2 = beta * beta, ir2 = ir * ir;
+  double2 g[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};   // sum_j (D2 + D1/r_j)[j][sn] Ybar(j)
+  const int jlo = max(0, sn - 2 * kStencil), jhi = min(s.Nr - 1, sn + 2 * kStencil);
+  for (int j = jlo; j <= jhi; ++j) {
+    const int t = sn - p.rad.s0[j];
+    if (t < 0 || t >= kStencil) continue;
+    const double w = p.rad.D2[j * kStencil + t] + p.rad.D1[j * kStencil + t] * p.rad.inv_r[j];
+    const long long q = (long long)j * s.nmode + mode;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (c < s.nf) {
+        const double2 y = Yb[c * S + q];
+        g[c].x += w * y.x;
+        g[c].y += w * y.y;
+      }
+    }
+  }
+  const double qp = (double)(m + 1) * (m + 1), qm = (double)(m - 1) * (m - 1);
+  const double dp = qp * ir2 + b2, dm = qm * ir2 + b2, d0 = (double)m * m * ir2 + b2;
+  double2 xb[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (c >= s.nf) continue;
+    const double2 y = Yb[c * S + i];
+    const double d = (c == 0) ? dp : (c == 1) ? dm : d0;
+    const double kap = (c == 3) ? p.kappaT : 1.0;
+    xb[c] = double2{idt * y.x + om * kap * (g[c].x - d * y.x),
+                    idt * y.y + om * kap * (g[c].y - d * y.y)};
+    // Nbar += (1-c) (N+-)^T Ybar
+    if (c == 0 || c == 1) {
+      const double sg = (c == 0) ? 1.0 : -1.0;
+      double2 nr = Nb[i], nt = Nb[S + i];
+      nr.x += om * y.x;
+      nr.y += om * y.y;
+      nt.x += sg * om * y.y;    // (-i sg) y
+      nt.y -= sg * om * y.x;
+      Nb[i] = nr;
+      Nb[S + i] = nt;
+    } else {
+      double2 n = Nb[c * S + i];
+      n.x += om * y.x;
+      n.y += om * y.y;
+      Nb[c * S + i] = n;
+    }
+  }
+  // X+- = X_r +- i X_theta:  Xbar_r = X+bar + X-bar, Xbar_theta = -i X+bar + i X-bar
+  Xb[i] = double2{xb[0].x + xb[1].x, xb[0].y + xb[1].y};
+  Xb[S + i] = double2{xb[0].y - xb[1].y, xb[1].x - xb[0].x};
+  Xb[2 * S + i] = xb[2];
+  if (s.nf == 4) Xb[3 * S + i] = xb[3];
+}
+
+// Orthogonal projection onto u(0,-k) = conj u(0,k) (and a real (0,0) entry).
+__global__ void k_herm_project(double2 *__restrict__ X, Sizes s) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)s.nf * s.Nr * (s.K + 1);
+  if (t >= n) return;
+  const int k = (int)(t % (s.K + 1));
+  double2 *col = X + (t / (s.K + 1)) * s.nmode;
+  if (k == 0) {
+    col[0].y = 0.0;
+  } else {
+    const double2 a = col[k], b = col[s.NK - k];
+    const double2 h = {0.5 * (a.x + b.x), 0.5 * (a.y - b.y)};
+    col[k] = h;
+    col[s.NK - k] = double2{h.x, -h.y};
+  }
+}
+
+// Gradient of E_pert = (1/2) int |u - u_base|^2 dV: V w_j r_j c_m (u - u_base).
+__global__ void k_objective_grad(const double2 *__restrict__ X, const double2 *__restrict__ base,
+                                 double2 *__restrict__ G, Sizes s, Radial rad, double V) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)s.nf * s.S) return;
+  const int c = (int)(i / s.S);
+  const long long rem = i - (long long)c * s.S;
+  const int j = (int)(rem / s.nmode);
+  const int mode = (int)(rem - (long long)j * s.nmode);
+  if (c >= 3) {
+    G[i] = double2{0.0, 0.0};
+    return;
+  }
+  const double w = V * rad.wr[j] * ((mode / s.NK == 0) ? 1.0 : 2.0);
+  const double2 x = X[i], b = base[i];
+  G[i] = double2{w * (x.x - b.x), w * (x.y - b.y)};
+}
+
 __global__ void k_check_finite(const double2 *__restrict__ X, long long n, DevScalars *sc) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -781,7 +1140,8 @@ SweepArgs sweep_args(const tc_ctx *c) {
 
 void setup_linear(tc_ctx *c) {
   (void)c;
-  cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem);
+  cudaFuncSetAttribute(k_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem);
+  cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem);
 }
 
 void launch_factor_poisson(tc_ctx *c) {
@@ -823,7 +1183,7 @@ void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout) {
     LaunchScope ls(c, KPOIS);
     SweepArgs sa = sweep_args(c);
     sa.f[0] = SweepField{p.LP, p.UP, c->Ps, 0, 1};
-    k_sweep<<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, 1), 4 * kSweepOps, kSweepSmem,
+    k_sweep<false><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, 1), 4 * kSweepOps, kSweepSmem,
               c->stream>>>(
         sa, c->scal);
   }
@@ -838,7 +1198,7 @@ void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout) {
     sa.f[1] = SweepField{p.LH, p.UH, U + 2 * s.S, -1, 0};
     sa.f[2] = SweepField{p.LH, p.UH, U + 4 * s.S, 0, 0};
     if (s.nf == 4) sa.f[3] = SweepField{p.LT, p.UT, U + 6 * s.S, 0, 0};
-    k_sweep<<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, s.nf), 4 * kSweepOps, kSweepSmem,
+    k_sweep<false><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, s.nf), 4 * kSweepOps, kSweepSmem,
               c->stream>>>(
         sa, c->scal);
   }
@@ -861,6 +1221,54 @@ void launch_symmetrise(tc_ctx *c, double2 *X) {
   LaunchScope ls(c, KCHECK);
   k_symmetrise<<<blocks((long long)c->sz.nf * c->sz.Nr * (c->sz.K + 1), 256), 256, 0,
                  c->stream>>>(X, c->sz);
+}
+
+// Adjoint of one implicit stage: Lb (primitive cotangent of the stage output)
+// -> Rb (cotangent of the +- right-hand side).
+void launch_stage_adjoint(tc_ctx *c, const double2 *Lb, double2 *Rb) {
+  const Sizes &s = c->sz;
+  const LinParams &p = c->lin;
+  double *U = reinterpret_cast<double *>(c->U0);
+  LaunchScope ls(c, KADJ);
+  k_stT_correct<<<blocks(s.S, 128), 128, 0, c->stream>>>(Lb, U, s);
+  k_stT_alpha<<<blocks(s.nmode, 64), 64, 0, c->stream>>>(U, p);
+  SweepArgs sa = sweep_args(c);
+  sa.f[0] = SweepField{p.LH, p.UH, U + 0 * s.S, +1, 0};
+  sa.f[1] = SweepField{p.LH, p.UH, U + 2 * s.S, -1, 0};
+  sa.f[2] = SweepField{p.LH, p.UH, U + 4 * s.S, 0, 0};
+  if (s.nf == 4) sa.f[3] = SweepField{p.LT, p.UT, U + 6 * s.S, 0, 0};
+  k_sweep<true><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, s.nf), 4 * kSweepOps, kSweepSmem,
+                  c->stream>>>(sa, c->scal);
+  k_stT_hrhs<<<blocks(s.S, 128), 128, 0, c->stream>>>(U, Rb, c->Ps, p);
+  SweepArgs sp = sweep_args(c);
+  sp.f[0] = SweepField{p.LP, p.UP, c->Ps, 0, 1};
+  k_sweep<true><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, 1), 4 * kSweepOps, kSweepSmem,
+                  c->stream>>>(sp, c->scal);
+  k_stT_prhs<<<blocks(s.S, 128), 128, 0, c->stream>>>(c->Ps, Rb, p);
+  c->launches += 5;
+}
+
+void launch_stage_split_adjoint(tc_ctx *c, const double2 *Rb, double2 *Ybar, double2 *Nb,
+                                int accumulate) {
+  LaunchScope ls(c, KADJ);
+  k_stT_split<<<blocks(c->sz.S, 128), 128, 0, c->stream>>>(Rb, Ybar, Nb, c->sz, accumulate);
+}
+
+void launch_rhs_adjoint(tc_ctx *c, const double2 *Ybar, double2 *Xb, double2 *Nb) {
+  LaunchScope ls(c, KADJ);
+  k_rhsT<<<blocks(c->sz.S, 128), 128, 0, c->stream>>>(Ybar, Xb, Nb, c->lin, c->scal);
+}
+
+void launch_herm_project(tc_ctx *c, double2 *X) {
+  LaunchScope ls(c, KADJ);
+  k_herm_project<<<blocks((long long)c->sz.nf * c->sz.Nr * (c->sz.K + 1), 256), 256, 0,
+                   c->stream>>>(X, c->sz);
+}
+
+void launch_objective_grad(tc_ctx *c, const double2 *X, double2 *G) {
+  LaunchScope ls(c, KADJ);
+  k_objective_grad<<<blocks((long long)c->sz.nf * c->sz.S, 256), 256, 0, c->stream>>>(
+      X, c->base_dev, G, c->sz, c->nl.rad, 2.0 * 3.14159265358979323846 * c->Lz);
 }
 
 void launch_check_finite(tc_ctx *c, const double2 *X, long long n) {

@@ -626,3 +626,301 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
   }
   return TC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Adjoint of the nonlinear stage (FP64): Nbar (primitive cotangents of N) ->
+// Xbar += (dN/dX)^T Nbar at the linearisation point X, in the real Euclidean
+// inner product of stored (Re, Im) coefficients.
+//   * adjoint of the forward transform (scaled by 1/(Ntheta Nz)) is
+//     1/(Ntheta Nz) times the inverse transform of the cotangent with the
+//     m >= 1 entries halved;
+//   * adjoint of the pointwise products (linearised about X's fields);
+//   * adjoint of the inverse transform is the unnormalised forward transform
+//     with the m >= 1 entries doubled; derivative multipliers i m, i beta
+//     become -i m, -i beta, and d/dr becomes the transposed stencil.
+namespace tc {
+namespace {
+
+// z-inverse of the cotangent (values only, m >= 1 halved): V2 [nf][r][l][m]
+__global__ void k_zinv_adj(const double2 *__restrict__ Nb, double2 *__restrict__ Vout,
+                           NLParams p) {
+  const Sizes &s = p.sz;
+  const int m0 = blockIdx.x * p.MB;
+  const int nm = min(p.MB, s.NM - m0);
+  const int r = blockIdx.y;
+  const int Nz = s.Nz;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *A = reinterpret_cast<double2 *>(smem_raw);
+  double2 *B = A + s.nf * p.MB * Nz;
+  double2 *tw = B + s.nf * p.MB * Nz;
+  load_tw<double>(tw, p.twz, Nz);
+  for (int i = threadIdx.x; i < s.nf * nm * Nz; i += blockDim.x) A[i] = double2{0, 0};
+  __syncthreads();
+  for (int t = threadIdx.x; t < s.nf * nm * s.NK; t += blockDim.x) {
+    const int kk = t % s.NK;
+    const int rest = t / s.NK;
+    const int mi = rest % nm;
+    const int g = rest / nm;
+    const int m = m0 + mi;
+    const double h = (m == 0) ? 1.0 : 0.5;
+    const double2 v = Nb[(long long)g * s.S + (long long)r * s.nmode + (long long)m * s.NK + kk];
+    A[(g * nm + mi) * Nz + kpos(kk, s.K, s.NK, Nz)] = double2{h * v.x, h * v.y};
+  }
+  __syncthreads();
+  double2 *res = fft_batch<+1>(A, B, p.pz, s.nf * nm, Nz, tw);
+  for (int t = threadIdx.x; t < s.nf * nm * Nz; t += blockDim.x) {
+    const int mi = t % nm;
+    const int rest = t / nm;
+    const int l = rest % Nz;
+    const int g = rest / Nz;
+    Vout[(((long long)g * s.Nr + r) * Nz + l) * s.NM + m0 + mi] = res[(g * nm + mi) * Nz + l];
+  }
+}
+
+// Per z-row: forward fields of X (from V) and the cotangent (from V2) to the
+// physical grid, pointwise adjoint of the products, forward theta-transform of
+// the 4 nf field cotangents.  Output Wa [3c + d][r][l][m], d = 0: value with
+// the theta part folded in (c'_m (G_val - i m G_theta)), 1: d/dr, 2: d/dz.
+__global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__restrict__ V2,
+                            double2 *__restrict__ Wa, NLParams p) {
+  const Sizes &s = p.sz;
+  const int l0 = blockIdx.x * p.LB;
+  const int nl = min(p.LB, s.Nz - l0);
+  const int r = blockIdx.y;
+  const int Nt = s.Nt;
+  const int nfw = 2 * s.nf;          // forward-field pairs per row
+  const int npair = nfw + 2;         // + cotangent pairs (Nr, Ntheta), (Nz, NT)
+  const int nbuf = p.LB * npair;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *A = reinterpret_cast<double2 *>(smem_raw);
+  double2 *B = A + nbuf * Nt;
+  double2 *tw = B + nbuf * Nt;
+  load_tw<double>(tw, p.twt, Nt);
+  for (int i = threadIdx.x; i < nl * npair * Nt; i += blockDim.x) A[i] = double2{0, 0};
+  __syncthreads();
+  const long long fs = (long long)s.Nr * s.Nz * s.NM;
+  for (int t = threadIdx.x; t < nl * (s.nf + 2) * s.NM; t += blockDim.x) {
+    const int m = t % s.NM;
+    const int rest = t / s.NM;
+    const int c = rest % (s.nf + 2);
+    const int li = rest / (s.nf + 2);
+    const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
+    double2 a, b, e, f;
+    double2 *b0, *b1;
+    if (c < s.nf) {
+      a = Vin[(3 * c + 0) * fs + off];
+      e = Vin[(3 * c + 1) * fs + off];
+      f = Vin[(3 * c + 2) * fs + off];
+      if (m == 0) {
+        a.y = 0.0;
+        e.y = 0.0;
+        f.y = 0.0;
+      }
+      b = double2{-(double)m * a.y, (double)m * a.x};   // i m a
+      b0 = A + (li * npair + 2 * c) * Nt;
+      b1 = b0 + Nt;
+    } else {
+      const int h = c - s.nf;   // 0: (N_r, N_theta), 1: (N_z, N_T)
+      a = V2[(2 * h) * fs + off];
+      b = (2 * h + 1 < s.nf) ? V2[(2 * h + 1) * fs + off] : double2{0.0, 0.0};
+      if (m == 0) {
+        a.y = 0.0;
+        b.y = 0.0;
+      }
+      b0 = A + (li * npair + nfw + h) * Nt;
+      b1 = nullptr;
+    }
+    b0[m] = double2{a.x - b.y, a.y + b.x};
+    if (m > 0) b0[Nt - m] = double2{a.x + b.y, -a.y + b.x};
+    if (b1) {
+      b1[m] = double2{e.x - f.y, e.y + f.x};
+      if (m > 0) b1[Nt - m] = double2{e.x + f.y, -e.y + f.x};
+    }
+  }
+  __syncthreads();
+  double2 *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Nt, tw);
+  double2 *out = (ph == A) ? B : A;
+  const double ir = p.rad.inv_r[r];
+  const double sc = 1.0 / ((double)s.Nt * (double)s.Nz);
+  for (int t = threadIdx.x; t < nl * Nt; t += blockDim.x) {
+    const int j = t % Nt;
+    const int li = t / Nt;
+    const double2 *b = ph + li * npair * Nt + j;
+    const double2 r0 = b[0 * Nt], r1 = b[1 * Nt];   // (ur, ur_t), (ur_r, ur_z)
+    const double2 t0 = b[2 * Nt], t1 = b[3 * Nt];
+    const double2 z0 = b[4 * Nt], z1 = b[5 * Nt];
+    const double2 nb0 = b[nfw * Nt], nb1 = b[(nfw + 1) * Nt];
+    const double ar = sc * nb0.x, at = sc * nb0.y, az = sc * nb1.x, aT = sc * nb1.y;
+    const double ur = r0.x, ut = t0.x, uz = z0.x;
+    const double vt = ut * ir;
+    // cotangents of the 4 nf physical input fields
+    double gur = -(r1.x * ar) - (t1.x + vt) * at - z1.x * az;
+    double gut = -(r0.y * ir) * ar + 2.0 * vt * ar - (t0.y * ir) * at - (ur * ir) * at -
+                 (z0.y * ir) * az;
+    double guz = -(r1.y * ar) - t1.y * at - z1.y * az;
+    const double gurr = -ur * ar, gurt = -vt * ar, gurz = -uz * ar;
+    const double gutr = -ur * at, gutt = -vt * at, gutz = -uz * at;
+    const double guzr = -ur * az, guzt = -vt * az, guzz = -uz * az;
+    double gT = 0.0, gTr = 0.0, gTt = 0.0, gTz = 0.0;
+    if (s.nf == 4) {
+      const double2 T0 = b[6 * Nt], T1 = b[7 * Nt];
+      gur -= T1.x * aT;
+      gut -= (T0.y * ir) * aT;
+      guz -= T1.y * aT;
+      gT = p.Gr * az;
+      gTr = -ur * aT;
+      gTt = -vt * aT;
+      gTz = -uz * aT;
+    }
+    double2 *o = out + li * nfw * Nt + j;
+    o[0 * Nt] = double2{gur, gurt};
+    o[1 * Nt] = double2{gurr, gurz};
+    o[2 * Nt] = double2{gut, gutt};
+    o[3 * Nt] = double2{gutr, gutz};
+    o[4 * Nt] = double2{guz, guzt};
+    o[5 * Nt] = double2{guzr, guzz};
+    if (s.nf == 4) {
+      o[6 * Nt] = double2{gT, gTt};
+      o[7 * Nt] = double2{gTr, gTz};
+    }
+  }
+  __syncthreads();
+  double2 *scratch = (out == A) ? B : A;
+  double2 *sp = fft_batch<-1>(out, scratch, p.pt, nl * nfw, Nt, tw);
+  for (int t = threadIdx.x; t < nl * s.nf * s.NM; t += blockDim.x) {
+    const int m = t % s.NM;
+    const int rest = t / s.NM;
+    const int c = rest % s.nf;
+    const int li = rest / s.nf;
+    const double cm = (m == 0) ? 1.0 : 2.0;
+    const int mm = (Nt - m) % Nt;
+    const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
+    const double2 *z0 = sp + (li * nfw + 2 * c) * Nt;
+    // pair (val, theta): X = value part, Y = theta part
+    const double2 a = z0[m], bq = z0[mm];
+    const double2 Gv = double2{0.5 * (a.x + bq.x), 0.5 * (a.y - bq.y)};
+    const double2 Gt = double2{0.5 * (a.y + bq.y), 0.5 * (bq.x - a.x)};
+    // value cotangent with the theta derivative folded in: c'_m (Gv - i m Gt)
+    Wa[(3 * c + 0) * fs + off] = double2{cm * (Gv.x + m * Gt.y), cm * (Gv.y - m * Gt.x)};
+    const double2 *z1 = z0 + Nt;
+    const double2 a1 = z1[m], b1 = z1[mm];
+    const double2 Gr = double2{0.5 * (a1.x + b1.x), 0.5 * (a1.y - b1.y)};
+    const double2 Gz = double2{0.5 * (a1.y + b1.y), 0.5 * (b1.x - a1.x)};
+    Wa[(3 * c + 1) * fs + off] = double2{cm * Gr.x, cm * Gr.y};
+    Wa[(3 * c + 2) * fs + off] = double2{cm * Gz.x, cm * Gz.y};
+  }
+}
+
+// z-forward (unnormalised) of Wa; Xb += val - i beta z-part; Gr [c][r][mode]
+// holds the d/dr cotangent for the transposed stencil.
+__global__ void k_zfwd_adj(const double2 *__restrict__ Wa, double2 *__restrict__ Xb,
+                           double2 *__restrict__ Gr, NLParams p, int accumulate) {
+  const Sizes &s = p.sz;
+  const int m0 = blockIdx.x * p.MB;
+  const int nm = min(p.MB, s.NM - m0);
+  const int r = blockIdx.y;
+  const int c = blockIdx.z;
+  const int Nz = s.Nz;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *A = reinterpret_cast<double2 *>(smem_raw);
+  double2 *B = A + 3 * p.MB * Nz;
+  double2 *tw = B + 3 * p.MB * Nz;
+  load_tw<double>(tw, p.twz, Nz);
+  const long long fs = (long long)s.Nr * s.Nz * s.NM;
+  for (int t = threadIdx.x; t < 3 * nm * Nz; t += blockDim.x) {
+    const int mi = t % nm;
+    const int rest = t / nm;
+    const int l = rest % Nz;
+    const int d = rest / Nz;
+    A[(3 * mi + d) * Nz + l] = Wa[(3 * c + d) * fs + ((long long)r * Nz + l) * s.NM + m0 + mi];
+  }
+  __syncthreads();
+  double2 *res = fft_batch<-1>(A, B, p.pz, 3 * nm, Nz, tw);
+  for (int t = threadIdx.x; t < nm * s.NK; t += blockDim.x) {
+    const int kk = t % s.NK;
+    const int mi = t / s.NK;
+    const int pos = kpos(kk, s.K, s.NK, Nz);
+    const double beta = p.alpha * kval(kk, s.K, s.NK);
+    const double2 v = res[(3 * mi + 0) * Nz + pos];
+    const double2 gr = res[(3 * mi + 1) * Nz + pos];
+    const double2 gz = res[(3 * mi + 2) * Nz + pos];
+    const long long i = (long long)c * s.S + (long long)r * s.nmode + (long long)(m0 + mi) * s.NK + kk;
+    double2 x = double2{v.x + beta * gz.y, v.y - beta * gz.x};   // v - i beta gz
+    if (accumulate) {
+      const double2 o = Xb[i];
+      x.x += o.x;
+      x.y += o.y;
+    }
+    Xb[i] = x;
+    Gr[i] = gr;
+  }
+}
+
+// Xb(s) += sum_j D1[j][s - s0_j] Gr(j)  (transposed radial stencil)
+__global__ void k_drT(const double2 *__restrict__ Gr, double2 *__restrict__ Xb, Sizes s,
+                      Radial rad) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)s.nf * s.S) return;
+  const int c = (int)(i / s.S);
+  const long long rem = i - (long long)c * s.S;
+  const int sn = (int)(rem / s.nmode);
+  const int mode = (int)(rem - (long long)sn * s.nmode);
+  double2 acc = Xb[i];
+  const int jlo = max(0, sn - 2 * kStencil), jhi = min(s.Nr - 1, sn + 2 * kStencil);
+  for (int j = jlo; j <= jhi; ++j) {
+    const int t = sn - rad.s0[j];
+    if (t < 0 || t >= kStencil) continue;
+    const double w = rad.D1[j * kStencil + t];
+    const double2 g = Gr[(long long)c * s.S + (long long)j * s.nmode + mode];
+    acc.x += w * g.x;
+    acc.y += w * g.y;
+  }
+  Xb[i] = acc;
+}
+
+}  // namespace
+
+void setup_nonlinear_adjoint(tc_ctx *c) {
+  const Sizes &s = c->sz;
+  const NLParams &p = c->nl;
+  const size_t e = sizeof(double2);
+  c->smem_adj_zinv = (size_t)(2 * s.nf * p.MB * s.Nz + s.Nz) * e;
+  c->smem_adj_theta = (size_t)(2 * p.LB * (2 * s.nf + 2) * s.Nt + s.Nt) * e;
+  c->smem_adj_zfwd = (size_t)(2 * 3 * p.MB * s.Nz + s.Nz) * e;
+  cudaFuncSetAttribute(k_zinv_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)c->smem_adj_zinv);
+  cudaFuncSetAttribute(k_theta_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)c->smem_adj_theta);
+  cudaFuncSetAttribute(k_zfwd_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)c->smem_adj_zfwd);
+}
+
+void launch_nonlinear_adjoint(tc_ctx *c, const double2 *X, const double2 *Nb, double2 *Xb,
+                              int accumulate) {
+  const Sizes &s = c->sz;
+  const NLParams &p = c->nl;
+  const int nmb = (s.NM + p.MB - 1) / p.MB;
+  const int nlb = (s.Nz + p.LB - 1) / p.LB;
+  {
+    LaunchScope ls(c, KZINV);
+    k_zinv<double><<<dim3(nmb, s.Nr, s.nf), 256, c->smem_zinv, c->stream>>>(X, c->V, p);
+  }
+  {
+    LaunchScope ls(c, KZINV);
+    k_zinv_adj<<<dim3(nmb, s.Nr), 256, c->smem_adj_zinv, c->stream>>>(Nb, c->W, p);
+  }
+  {
+    LaunchScope ls(c, KTHETA);
+    k_theta_adj<<<dim3(nlb, s.Nr), 256, c->smem_adj_theta, c->stream>>>(c->V, c->W, c->Va, p);
+  }
+  {
+    LaunchScope ls(c, KZFWD);
+    k_zfwd_adj<<<dim3(nmb, s.Nr, s.nf), 256, c->smem_adj_zfwd, c->stream>>>(c->Va, Xb, c->Gdr,
+                                                                            p, accumulate);
+  }
+  LaunchScope ls(c, KZFWD);
+  k_drT<<<(unsigned)(((long long)s.nf * s.S + 255) / 256), 256, 0, c->stream>>>(c->Gdr, Xb, s,
+                                                                                  p.rad);
+}
+
+}  // namespace tc

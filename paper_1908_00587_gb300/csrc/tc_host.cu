@@ -578,7 +578,8 @@ tc_status tc_get_pressure(const tc_ctx *c, void *spec, int where) {
 
 tc_status tc_init_perturbation(tc_ctx *c, const double *psi, int mp, int kp, double amp,
                                const double *tcoef, double amp_T) {
-  if (!c || !psi || mp < 0 || kp < 0 || !(amp >= 0.0)) return TC_ERR_ARG;
+  if (!c || !psi || mp < 0 || kp < 0 || !std::isfinite(amp) || !std::isfinite(amp_T))
+    return TC_ERR_ARG;
   if (c->poisoned) return TC_ERR_CUDA;
   const Sizes &s = c->sz;
   if (mp > s.M || kp > s.K) return TC_ERR_ARG;
@@ -630,7 +631,7 @@ tc_status tc_init_perturbation(tc_ctx *c, const double *psi, int mp, int kp, dou
         u[2 * (2 * s.S + o) + 1] = uz.imag();
       }
   }
-  const bool withT = c->has_T && tcoef && amp_T > 0.0;
+  const bool withT = c->has_T && tcoef && amp_T != 0.0;
   if (withT) {
     std::vector<cplx> tp((size_t)s.S, cplx(0, 0));
     for (int j = 0; j < Nr; ++j) {
@@ -661,8 +662,11 @@ tc_status tc_init_perturbation(tc_ctx *c, const double *psi, int mp, int kp, dou
     double umax, tmax;
     std::memcpy(&umax, &nb[0], sizeof(double));
     std::memcpy(&tmax, &nb[1], sizeof(double));
-    const double su = (umax > 0.0) ? amp / umax : 0.0;
-    const double sT = (withT && tmax > 0.0) ? amp_T / tmax : 0.0;
+    // amp > 0: scale to max|u'| = amp; amp < 0: |amp| is the scale itself
+    const double su = (amp < 0.0) ? -amp : ((umax > 0.0) ? amp / umax : 0.0);
+    const double sT = !withT ? 0.0 : (amp_T < 0.0) ? -amp_T : ((tmax > 0.0) ? amp_T / tmax : 0.0);
+    c->ic_su = su;
+    c->ic_sT = sT;
     std::vector<double> X(c->base);
     for (long long i = 0; i < 2 * 3 * s.S; ++i) X[i] += su * u[i];
     if (s.nf == 4)
@@ -792,6 +796,231 @@ tc_status tc_diagnostics(tc_ctx *c, tc_diag *o) {
   } catch (const CudaError &e) {
     return fail_cuda(c, e.e);
   }
+  return TC_OK;
+}
+
+}  // extern "C"
+
+namespace tc {
+namespace {
+
+void ensure_adjoint(tc_ctx *c) {
+  if (c->Va) return;
+  const Sizes &s = c->sz;
+  c->Va = dalloc<double2>(c, (size_t)3 * s.nf * s.Nr * s.Nz * s.NM);
+  c->Gdr = dalloc<double2>(c, (size_t)s.nf * s.S);
+  c->Rb = dalloc<double2>(c, (size_t)s.nf * s.S);
+  c->Ybar = dalloc<double2>(c, (size_t)s.nf * s.S);
+  c->Nb = dalloc<double2>(c, (size_t)s.nf * s.S);
+  c->Xb = dalloc<double2>(c, (size_t)s.nf * s.S);
+  setup_nonlinear_adjoint(c);
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" {
+
+tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *adj_dev) {
+  if (!c || !state_n_dev || !adj_dev || !(dt > 0.0) || !std::isfinite(dt)) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  if (c->precision != 0) return TC_ERR_UNSUPPORTED;
+  const double2 *Xn = static_cast<const double2 *>(state_n_dev);
+  double2 *lam = static_cast<double2 *>(adj_dev);
+  try {
+    ensure_adjoint(c);
+    int zero = 0;
+    ck(cudaMemcpyAsync(&c->scal->timeout, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    // forward internals of the step at X^n
+    launch_nonlinear(c, Xn, c->N0, nullptr, 0);
+    launch_dt_policy(c, dt, -1);
+    launch_refactor(c);
+    launch_rhs(c, Xn, c->N0);
+    launch_stage(c, c->N0, c->Xp, c->P);
+    launch_nonlinear(c, c->Xp, c->N1, nullptr, 0);
+    // reverse sweep
+    launch_stage_adjoint(c, lam, c->Rb);                    // corrector stage
+    launch_stage_split_adjoint(c, c->Rb, c->Ybar, c->Nb, 0);
+    launch_nonlinear_adjoint(c, c->Xp, c->Nb, c->Xb, 0);    // N(X*)
+    launch_stage_adjoint(c, c->Xb, c->Rb);                  // predictor stage
+    launch_stage_split_adjoint(c, c->Rb, c->Ybar, c->Nb, 1);
+    launch_rhs_adjoint(c, c->Ybar, lam, c->Nb);
+    launch_nonlinear_adjoint(c, Xn, c->Nb, lam, 1);          // N(X^n)
+    launch_herm_project(c, lam);
+    ck(cudaGetLastError());
+    int to = 0;
+    ck(cudaMemcpyAsync(&to, &c->scal->timeout, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    if (to) return TC_ERR_TIMEOUT;
+  } catch (const std::bad_alloc &) {
+    return TC_ERR_OOM;
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  return TC_OK;
+}
+
+tc_status tc_nonlinear_adjoint(tc_ctx *c, const void *state_dev, const void *nbar_dev,
+                               void *xbar_dev) {
+  if (!c || !state_dev || !nbar_dev || !xbar_dev) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  try {
+    ensure_adjoint(c);
+    launch_nonlinear_adjoint(c, static_cast<const double2 *>(state_dev),
+                             static_cast<const double2 *>(nbar_dev),
+                             static_cast<double2 *>(xbar_dev), 0);
+    ck(cudaGetLastError());
+    ck(cudaStreamSynchronize(c->stream));
+  } catch (const std::bad_alloc &) {
+    return TC_ERR_OOM;
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  return TC_OK;
+}
+
+tc_status tc_stage_solve_adjoint(tc_ctx *c, const void *xbar_dev, double dt, void *rbar_dev) {
+  if (!c || !xbar_dev || !rbar_dev || !(dt > 0.0) || !std::isfinite(dt)) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  try {
+    ensure_adjoint(c);
+    int zero = 0;
+    ck(cudaMemcpyAsync(&c->scal->timeout, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    launch_dt_policy(c, dt, -1);
+    launch_refactor(c);
+    launch_stage_adjoint(c, static_cast<const double2 *>(xbar_dev), static_cast<double2 *>(rbar_dev));
+    ck(cudaGetLastError());
+    int to = 0;
+    ck(cudaMemcpyAsync(&to, &c->scal->timeout, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    if (to) return TC_ERR_TIMEOUT;
+  } catch (const std::bad_alloc &) {
+    return TC_ERR_OOM;
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  return TC_OK;
+}
+
+tc_status tc_objective(tc_ctx *c, double *J, void *grad_dev) {
+  if (!c || !J) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  tc_diag d;
+  tc_status st = tc_diagnostics(c, &d);
+  if (st != TC_OK) return st;
+  *J = d.E_pert;
+  if (grad_dev) {
+    try {
+      launch_objective_grad(c, c->X, static_cast<double2 *>(grad_dev));
+      ck(cudaGetLastError());
+      ck(cudaStreamSynchronize(c->stream));
+    } catch (const CudaError &e) {
+      return fail_cuda(c, e.e);
+    }
+  }
+  return TC_OK;
+}
+
+tc_status tc_init_perturbation_adjoint(tc_ctx *c, const void *lam_dev, int mp, int kp,
+                                       double *psi_bar, double *tcoef_bar) {
+  if (!c || !lam_dev || !psi_bar || mp < 0 || kp < 0) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  const Sizes &s = c->sz;
+  if (mp > s.M || kp > s.K) return TC_ERR_ARG;
+  const int Nr = s.Nr, NK = s.NK, nk = 2 * kp + 1;
+  std::vector<cplx> lam((size_t)s.nf * s.S);
+  try {
+    ck(cudaStreamSynchronize(c->stream));
+    ck(cudaMemcpy(lam.data(), lam_dev, sizeof(cplx) * lam.size(), cudaMemcpyDeviceToHost));
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  auto L = [&](int f, int j, int m, int kk) -> cplx {
+    return lam[(size_t)f * s.S + (size_t)j * s.nmode + (size_t)m * NK + kk];
+  };
+  // transpose of u' = s_u Zw curl(psi): psi_bar per component (interior rows)
+  std::vector<cplx> pb((size_t)3 * s.S, cplx(0.0, 0.0));
+  auto PB = [&](int comp, int j, int m, int kk) -> cplx & {
+    return pb[(size_t)comp * s.S + (size_t)j * s.nmode + (size_t)m * NK + kk];
+  };
+  const double alpha = 2.0 * M_PI / c->Lz;
+  const cplx I(0.0, 1.0);
+  const double su = c->ic_su;
+  for (int j = 1; j < Nr - 1; ++j) {
+    const int st = c->s0[j];
+    const double r = c->r[j];
+    for (int m = 0; m < s.NM; ++m)
+      for (int kk = 0; kk < NK; ++kk) {
+        const double beta = alpha * (kk <= s.K ? kk : kk - NK);
+        const cplx ur = su * L(0, j, m, kk), ut = su * L(1, j, m, kk), uz = su * L(2, j, m, kk);
+        // u_r = (i m / r) psi_z - i beta psi_theta
+        PB(2, j, m, kk) += std::conj(I * (double)m / r) * ur;
+        PB(1, j, m, kk) += std::conj(-I * beta) * ur;
+        // u_theta = i beta psi_r - D1 psi_z
+        PB(0, j, m, kk) += std::conj(I * beta) * ut;
+        // u_z = (1/r) D1(r psi_theta) - (i m / r) psi_r
+        PB(0, j, m, kk) += std::conj(-I * (double)m / r) * uz;
+        for (int t = 0; t < kStencil; ++t) {
+          PB(2, st + t, m, kk) -= c->D1[j * kStencil + t] * ut;
+          PB(1, st + t, m, kk) += (c->D1[j * kStencil + t] * c->r[st + t] / r) * uz;
+        }
+      }
+  }
+  // transpose of the Hermitian fix and of the radial profile
+  for (int comp = 0; comp < 3; ++comp)
+    for (int m = 0; m <= mp; ++m)
+      for (int k = -kp; k <= kp; ++k) {
+        cplx acc(0.0, 0.0);
+        for (int j = 0; j < Nr; ++j) {
+          const double x = 2.0 * (c->r[j] - c->r_i) - 1.0;
+          const double prof = (1.0 - x * x) * (1.0 - x * x);
+          cplx v;
+          if (m == 0 && k < 0) {
+            v = 0.0;        // overwritten by the fix: no influence
+          } else if (m == 0 && k > 0) {
+            v = PB(comp, j, 0, k) + std::conj(PB(comp, j, 0, NK - k));
+          } else if (m == 0 && k == 0) {
+            v = cplx(PB(comp, j, 0, 0).real(), 0.0);
+          } else {
+            v = PB(comp, j, m, (k + NK) % NK);
+          }
+          acc += prof * v;
+        }
+        double *o = psi_bar + 2 * (((size_t)comp * (mp + 1) + m) * nk + (k + kp));
+        o[0] = acc.real();
+        o[1] = acc.imag();
+      }
+  if (tcoef_bar) {
+    for (int m = 0; m <= mp; ++m)
+      for (int k = -kp; k <= kp; ++k) {
+        cplx acc(0.0, 0.0);
+        if (s.nf == 4 && c->ic_sT != 0.0) {
+          for (int j = 0; j < Nr; ++j) {
+            const double x = 2.0 * (c->r[j] - c->r_i) - 1.0;
+            cplx v;
+            if (m == 0 && k < 0)
+              v = 0.0;
+            else if (m == 0 && k > 0)
+              v = L(3, j, 0, k) + std::conj(L(3, j, 0, NK - k));
+            else if (m == 0 && k == 0)
+              v = cplx(L(3, j, 0, 0).real(), 0.0);
+            else
+              v = L(3, j, m, (k + NK) % NK);
+            acc += (1.0 - x * x) * c->ic_sT * v;
+          }
+        }
+        double *o = tcoef_bar + 2 * ((size_t)m * nk + (k + kp));
+        o[0] = acc.real();
+        o[1] = acc.imag();
+      }
+  }
+  return TC_OK;
+}
+
+tc_status tc_get_ic_scales(const tc_ctx *c, double *s_u, double *s_T) {
+  if (!c || !s_u || !s_T) return TC_ERR_ARG;
+  *s_u = c->ic_su;
+  *s_T = c->ic_sT;
   return TC_OK;
 }
 

@@ -98,7 +98,7 @@ namespace tc {
 // Kernels with per-launch timing (option "timing").
 enum KernelId {
   KZINV, KTHETA, KZFWD, KDT, KFACTH, KINFL, KRHS, KPRHS, KPOIS, KHRHS, KHELM, KALPHA, KCORR,
-  KDIAG, KCHECK, KNUM
+  KDIAG, KCHECK, KADJ, KNUM
 };
 extern const char *const kKernelNames[KNUM];
 
@@ -141,6 +141,11 @@ struct tc_ctx {
   int precision = 0;            // 0: FP64 everywhere; 1: FP32 transforms/products
   double *prof = nullptr;       // mean-flow profile for the mixed path
   size_t smem32_zinv = 0, smem32_theta = 0, smem32_zfwd = 0;
+  // adjoint buffers (allocated on first use)
+  double2 *Va = nullptr, *Gdr = nullptr, *Rb = nullptr, *Ybar = nullptr, *Nb = nullptr,
+          *Xb = nullptr;
+  size_t smem_adj_zinv = 0, smem_adj_theta = 0, smem_adj_zfwd = 0;
+  double ic_su = 0.0, ic_sT = 0.0;   // scales frozen by tc_init_perturbation
   tc::LinParams lin;
   size_t smem_zinv, smem_theta, smem_zfwd;
   long long launches = 0;        // kernels launched since tc_create
@@ -175,6 +180,15 @@ void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout);
 void launch_check_finite(tc_ctx *c, const double2 *X, long long n);
 void launch_state_check(tc_ctx *c, const double2 *X);
 void setup_linear(tc_ctx *c);
+void launch_stage_adjoint(tc_ctx *c, const double2 *Lb, double2 *Rb);
+void launch_stage_split_adjoint(tc_ctx *c, const double2 *Rb, double2 *Ybar, double2 *Nb,
+                                int accumulate);
+void launch_rhs_adjoint(tc_ctx *c, const double2 *Ybar, double2 *Xb, double2 *Nb);
+void launch_herm_project(tc_ctx *c, double2 *X);
+void launch_objective_grad(tc_ctx *c, const double2 *X, double2 *G);
+void setup_nonlinear_adjoint(tc_ctx *c);
+void launch_nonlinear_adjoint(tc_ctx *c, const double2 *X, const double2 *Nb, double2 *Xb,
+                              int accumulate);
 void launch_symmetrise(tc_ctx *c, double2 *X);
 
 // diag.cu

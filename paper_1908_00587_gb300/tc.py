@@ -72,6 +72,12 @@ _SIGS = {
     "tc_get_timing": [_P, _P, _I, ctypes.POINTER(_I)],
     "tc_reset_timing": [_P],
     "tc_nonlinear_noalloc": [_I, _I, _I, _D, _D, _D, _D, _P, _P, _P, _P],
+    "tc_adjoint_step": [_P, _P, _D, _P],
+    "tc_nonlinear_adjoint": [_P, _P, _P, _P],
+    "tc_stage_solve_adjoint": [_P, _P, _D, _P],
+    "tc_objective": [_P, ctypes.POINTER(_D), _P],
+    "tc_init_perturbation_adjoint": [_P, _P, _I, _I, _P, _P],
+    "tc_get_ic_scales": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -204,6 +210,45 @@ def tc_nonlinear_noalloc(Nr, Ntheta, Nz, eta, Lz, Ra, Pr, state_dev, n_dev, stre
                                      float(Ra), float(Pr), _ptr(state_dev)[0], _ptr(n_dev)[0],
                                      stream_ptr, ctypes.byref(rate)), "tc_nonlinear_noalloc")
     return rate.value
+
+
+def tc_adjoint_step(ctx, state_n_dev, dt, adj_dev):
+    """adj <- P_H J(state_n)^T adj for one step at fixed dt (in place)."""
+    _check(_lib.tc_adjoint_step(ctx, _ptr(state_n_dev)[0], float(dt), _ptr(adj_dev)[0]),
+           "tc_adjoint_step")
+
+
+def tc_nonlinear_adjoint(ctx, state_dev, nbar_dev, xbar_dev):
+    _check(_lib.tc_nonlinear_adjoint(ctx, _ptr(state_dev)[0], _ptr(nbar_dev)[0],
+                                     _ptr(xbar_dev)[0]), "tc_nonlinear_adjoint")
+
+
+def tc_stage_solve_adjoint(ctx, xbar_dev, dt, rbar_dev):
+    _check(_lib.tc_stage_solve_adjoint(ctx, _ptr(xbar_dev)[0], float(dt), _ptr(rbar_dev)[0]),
+           "tc_stage_solve_adjoint")
+
+
+def tc_objective(ctx, grad_dev=None) -> float:
+    J = ctypes.c_double(0.0)
+    _check(_lib.tc_objective(ctx, ctypes.byref(J),
+                             _ptr(grad_dev)[0] if grad_dev is not None else None), "tc_objective")
+    return J.value
+
+
+def tc_init_perturbation_adjoint(ctx, lam_dev, mp, kp, with_T=False):
+    pb = np.zeros((3, mp + 1, 2 * kp + 1), dtype=np.complex128)
+    tb = np.zeros((mp + 1, 2 * kp + 1), dtype=np.complex128) if with_T else None
+    _check(_lib.tc_init_perturbation_adjoint(ctx, _ptr(lam_dev)[0], int(mp), int(kp),
+                                             pb.ctypes.data,
+                                             tb.ctypes.data if tb is not None else None),
+           "tc_init_perturbation_adjoint")
+    return pb, tb
+
+
+def tc_get_ic_scales(ctx):
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib.tc_get_ic_scales(ctx, ctypes.byref(a), ctypes.byref(b)), "tc_get_ic_scales")
+    return a.value, b.value
 
 
 def tc_status_string(s: int) -> str:
