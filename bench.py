@@ -49,6 +49,8 @@ def parse():
                     help="override the workload's precision (0 FP64, 1 mixed)")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="benchmark the batched form: N uneven runs replayed as one graph")
     return ap.parse_args()
 
 
@@ -331,10 +333,76 @@ def run_gb300(args):
     return 0
 
 
+def run_ensemble(args):
+    """Batched form: N uneven runs (every other one mixed precision), one step
+    of all of them captured into a CUDA graph and replayed, against the same
+    runs stepped one after another with plain launches."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from inputs import ensemble_members
+    from paper_1908_00587_gb300 import tc
+    torch.cuda.set_device(0)
+    members = [w.scaled(precision=i % 2) for i, w in enumerate(ensemble_members(args.ensemble))]
+    t0 = time.perf_counter()
+    ens = tc.tc_ensemble_create(members, autotune_tiles=True)
+    setup_s = time.perf_counter() - t0
+    dts = []
+    for i, wl in enumerate(members):
+        ctx = tc.tc_ensemble_member(ens, i)
+        tc.tc_init_perturbation(ctx, psi_coefficients(wl.seed, wl.mp, wl.kp), wl.amp)
+        info = tc.tc_get_info(ctx)
+        X = np.empty((info.nfields, info.Nr, info.M + 1, 2 * info.K + 1), dtype=np.complex128)
+        tc.tc_get_state(ctx, X)
+        out = torch.zeros(X.shape, dtype=torch.complex128, device="cuda")
+        rate = tc.tc_nonlinear(ctx, torch.from_numpy(X).cuda(), out)
+        dts.append(min(1e-3, 0.25 / rate))
+    pts = sum(w.points for w in members)
+    tc.tc_ensemble_step(ens, args.warmup, dts)
+    clocks = Clocks(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tc.tc_ensemble_step(ens, args.steps, dts)
+    torch.cuda.synchronize()
+    graph_s = time.perf_counter() - t0
+    clk = clocks.stop()
+    kps = tc.tc_ensemble_kernels_per_step(ens)
+    # the same members one after another, plain launches (default stream order)
+    seq_s = 0.0
+    for i, wl in enumerate(members):
+        ctx = tc.tc_ensemble_member(ens, i)
+        tc.tc_step(ctx, 1, dts[i])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tc.tc_step(ctx, args.steps, dts[i])
+        seq_s += time.perf_counter() - t0
+    tc.tc_ensemble_destroy(ens)
+    value = pts * args.steps / graph_s
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * graph_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 and f32+f64 members", "data": "synthetic",
+            "config": {"workload": f"ensemble of {len(members)} uneven runs (Nr in 32/48/64, "
+                                   f"N in 32/64/96, eta in 0.5/0.71/0.875, Re_i in [80, 400], "
+                                   f"every other member mixed precision)",
+                       "grid_points_total": pts, "tile_autotune_s": setup_s,
+                       "l2": "working set of all members exceeds L2"},
+            "sequential": {"value": pts * args.steps / seq_s, "ms_per_step": 1e3 * seq_s / args.steps},
+            "speedup_vs_sequential": seq_s / graph_s,
+            "gpu_launches": kps * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ensemble:
+        return run_ensemble(args)
     return run_gb300(args)
 
 

@@ -78,6 +78,7 @@ typedef struct {
   long long state_bytes;        /* nfields * coeffs_per_field * 16 */
   size_t device_bytes;          /* device memory held by the context */
   long long launches;           /* kernels launched since tc_create */
+  int tile_mb, tile_lb;         /* nonlinear-stage tiles in use (see "tile_mb") */
 } tc_info;
 
 /* Device time of one kernel accumulated while option "timing" is 1. */
@@ -113,6 +114,11 @@ tc_status tc_destroy(tc_ctx *ctx);
  *   "check"     1: report NaN/Inf produced by tc_step (default 1)
  *   "timing"    1: bracket every kernel launch with CUDA events on the
  *               context's stream (tc_get_timing); 0: off (default)
+ *   "tile_mb"   m columns per CTA of the axial transform kernels, "tile_lb"
+ *               z rows per CTA of the azimuthal kernel (0: size-based default;
+ *               TC_ERR_UNSUPPORTED if the shared memory would not fit).  The
+ *               tiles change only which CTA computes a transform, not the
+ *               arithmetic, so results are identical for every choice.
  *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
  *               never start their shared-memory copies, so each of their
  *               bounded waits runs out (about 1 s) and tc_step returns
@@ -250,6 +256,40 @@ tc_status tc_reset_timing(tc_ctx *ctx);
 tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta, double Lz, double Ra,
                                double Pr, const void *state_dev, void *n_dev, void *stream,
                                double *cfl_rate);
+
+/* Ensemble of independent runs of uneven size (batching form).  Each member
+ * is an ordinary context on a stream of its own (reach it with
+ * tc_ensemble_member to set its state, options or initial condition; do not
+ * destroy it or change its stream).  Per-member parameters: */
+typedef struct {
+  int Nr, Ntheta, Nz;
+  double eta, Lz, Re_i, Re_o, Ra, Pr;
+  int precision;   /* 0 FP64, 1 mixed (see the "precision" option) */
+} tc_params;
+typedef struct tc_ens tc_ens;
+
+/* Create n members (arguments validated as in tc_create).  autotune_tiles =
+ * 1 times the nonlinear stage for candidate tile shapes once per size class
+ * (Nr, Ntheta, Nz, fields, precision) and keeps the fastest; the choice does
+ * not change any result.  Errors: those of tc_create, TC_ERR_CUDA. */
+tc_status tc_ensemble_create(int n, const tc_params *p, int autotune_tiles, tc_ens **out);
+
+/* The context of member i (owned by the ensemble). */
+tc_status tc_ensemble_member(tc_ens *e, int i, tc_ctx **ctx);
+
+/* Advance every member nsteps steps of its own fixed dt (host array of n
+ * values > 0).  One step of all members is captured once into a CUDA graph
+ * (members are independent branches, run concurrently) and the graph is
+ * replayed nsteps times; it is re-captured when a dt changes.  Returns the
+ * worst member status (TC_ERR_TIMEOUT, TC_ERR_NONFINITE) after a
+ * synchronisation. */
+tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt);
+
+/* Kernel launches one graph replay (one step of every member) contains. */
+tc_status tc_ensemble_kernels_per_step(const tc_ens *e, long long *count);
+
+/* Free the members, streams and graph.  Accepts NULL. */
+tc_status tc_ensemble_destroy(tc_ens *e);
 
 /* Human-readable name of a status. */
 const char *tc_status_string(tc_status s);

@@ -1140,8 +1140,8 @@ SweepArgs sweep_args(const tc_ctx *c) {
 
 void setup_linear(tc_ctx *c) {
   (void)c;
-  cudaFuncSetAttribute(k_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem);
-  cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem);
+  allow_smem(k_sweep<false>);
+  allow_smem(k_sweep<true>);
 }
 
 void launch_factor_poisson(tc_ctx *c) {

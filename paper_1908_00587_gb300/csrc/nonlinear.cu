@@ -354,41 +354,39 @@ void setup_nonlinear(tc_ctx *c) {
   int MB = (int)(3072 / (3 * s.Nz));
   if (MB < 1) MB = 1;
   if (MB > 8) MB = 8;
+  if (c->tile_mb > 0) MB = c->tile_mb;
   if (MB > s.NM) MB = s.NM;
   p.MB = MB;
   int LB = (int)(4096 / (2 * s.nf * s.Nt));
   if (LB < 1) LB = 1;
   if (LB > 8) LB = 8;
+  if (c->tile_lb > 0) LB = c->tile_lb;
   p.LB = LB;
   c->smem_zinv = (size_t)(2 * 3 * MB * s.Nz + s.Nz) * e;
   c->smem_theta = (size_t)(2 * LB * 2 * s.nf * s.Nt + s.Nt) * e;
   c->smem_zfwd = (size_t)(2 * s.nf * MB * s.Nz + s.Nz) * e;
-  cudaFuncSetAttribute(k_zinv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->smem_zinv);
-  cudaFuncSetAttribute(k_theta<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->smem_theta);
-  cudaFuncSetAttribute(k_zfwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->smem_zfwd);
+  allow_smem(k_zinv<double>);
+  allow_smem(k_theta<double>);
+  allow_smem(k_zfwd<double>);
   // FP32 copies of the transforms (mixed precision): same blocking by bytes
   NLParams &q = c->nl32;
   q = p;
   const size_t e32 = sizeof(float2);
   int MB32 = (int)(6144 / (3 * s.Nz));
   MB32 = MB32 < 1 ? 1 : (MB32 > 8 ? 8 : MB32);
+  if (c->tile_mb > 0) MB32 = c->tile_mb;
   if (MB32 > s.NM) MB32 = s.NM;
   int LB32 = (int)(8192 / (2 * s.nf * s.Nt));
   LB32 = LB32 < 1 ? 1 : (LB32 > 8 ? 8 : LB32);
+  if (c->tile_lb > 0) LB32 = c->tile_lb;
   q.MB = MB32;
   q.LB = LB32;
   c->smem32_zinv = (size_t)(2 * 3 * MB32 * s.Nz + s.Nz) * e32;
   c->smem32_theta = (size_t)(2 * LB32 * 2 * s.nf * s.Nt + s.Nt) * e32;
   c->smem32_zfwd = (size_t)(2 * s.nf * MB32 * s.Nz + s.Nz) * e32;
-  cudaFuncSetAttribute(k_zinv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->smem32_zinv);
-  cudaFuncSetAttribute(k_theta<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->smem32_theta);
-  cudaFuncSetAttribute(k_zfwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->smem32_zfwd);
+  allow_smem(k_zinv<float>);
+  allow_smem(k_theta<float>);
+  allow_smem(k_zfwd<float>);
 }
 
 void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long long *rate_bits,
@@ -604,10 +602,9 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
   double2 *W = reinterpret_cast<double2 *>(base + L.W);
   unsigned long long *rate = reinterpret_cast<unsigned long long *>(base + L.rate);
 
-  cudaFuncSetAttribute(k_zinv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_zinv);
-  cudaFuncSetAttribute(k_theta<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sm_theta);
-  cudaFuncSetAttribute(k_zfwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_zfwd);
+  allow_smem(k_zinv<double>);
+  allow_smem(k_theta<double>);
+  allow_smem(k_zfwd<double>);
   const int nmb = (s.NM + MB - 1) / MB;
   const int nlb = (s.Nz + LB - 1) / LB;
   k_zinv<double><<<dim3(nmb, s.Nr, s.nf), 256, sm_zinv, st>>>(
@@ -887,12 +884,9 @@ void setup_nonlinear_adjoint(tc_ctx *c) {
   c->smem_adj_zinv = (size_t)(2 * s.nf * p.MB * s.Nz + s.Nz) * e;
   c->smem_adj_theta = (size_t)(2 * p.LB * (2 * s.nf + 2) * s.Nt + s.Nt) * e;
   c->smem_adj_zfwd = (size_t)(2 * 3 * p.MB * s.Nz + s.Nz) * e;
-  cudaFuncSetAttribute(k_zinv_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->smem_adj_zinv);
-  cudaFuncSetAttribute(k_theta_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->smem_adj_theta);
-  cudaFuncSetAttribute(k_zfwd_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->smem_adj_zfwd);
+  allow_smem(k_zinv_adj);
+  allow_smem(k_theta_adj);
+  allow_smem(k_zfwd_adj);
 }
 
 void launch_nonlinear_adjoint(tc_ctx *c, const double2 *X, const double2 *Nb, double2 *Xb,

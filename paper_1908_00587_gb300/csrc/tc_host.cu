@@ -25,7 +25,7 @@ LaunchScope::LaunchScope(tc_ctx *c_, int id_) : c(c_), id(id_) {
   c->launches++;
   KernelTimer &t = c->timers[id];
   t.launches++;
-  if (!c->timing) return;
+  if (!c->timing || c->capturing) return;
   if ((int)t.ev.size() < 2 * (t.used + 1)) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -37,10 +37,23 @@ LaunchScope::LaunchScope(tc_ctx *c_, int id_) : c(c_), id(id_) {
 }
 
 LaunchScope::~LaunchScope() {
-  if (!c->timing) return;
+  if (!c->timing || c->capturing) return;
   KernelTimer &t = c->timers[id];
   cudaEventRecord(t.ev[2 * t.used + 1], c->stream);
   t.used++;
+}
+
+// All kernels of one predictor-corrector step, enqueued on the context's
+// stream with no host synchronisation (so that a graph can capture it).
+// step_index >= 0 records the step used into dt_hist[step_index].
+void enqueue_step(tc_ctx *c, double dt_fixed, int step_index) {
+  launch_nonlinear(c, c->X, c->N0, &c->scal->rate_bits, 0);
+  launch_dt_policy(c, dt_fixed, step_index);
+  launch_refactor(c);
+  launch_rhs(c, c->X, c->N0);
+  launch_stage(c, c->N0, c->Xp, c->P);
+  launch_nonlinear(c, c->Xp, c->N1, nullptr, 0);
+  launch_stage(c, c->N1, c->X, c->P);
 }
 
 FFTPlan make_plan(int n) {
@@ -483,6 +496,20 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
     c->cfl_limit = v;
   } else if (k == "check") {
     c->check = v != 0.0;
+  } else if (k == "tile_mb" || k == "tile_lb") {
+    if (v < 0.0 || v > 64.0 || v != (double)(int)v) return TC_ERR_ARG;
+    const int old_mb = c->tile_mb, old_lb = c->tile_lb;
+    if (k == "tile_mb") c->tile_mb = (int)v; else c->tile_lb = (int)v;
+    setup_nonlinear(c);
+    const bool fits = (c->precision == 1)
+        ? (c->smem32_zinv <= 227 * 1024 && c->smem32_theta <= 227 * 1024 && c->smem32_zfwd <= 227 * 1024)
+        : (c->smem_zinv <= 227 * 1024 && c->smem_theta <= 227 * 1024 && c->smem_zfwd <= 227 * 1024);
+    if (!fits) {
+      c->tile_mb = old_mb;
+      c->tile_lb = old_lb;
+      setup_nonlinear(c);
+      return TC_ERR_UNSUPPORTED;
+    }
   } else if (k == "precision") {
     if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
     c->precision = (int)v;
@@ -514,6 +541,8 @@ tc_status tc_get_info(const tc_ctx *c, tc_info *o) {
   o->state_bytes = (long long)c->sz.nf * c->sz.S * 16;
   o->device_bytes = c->device_bytes;
   o->launches = c->launches;
+  o->tile_mb = (c->precision == 1) ? c->nl32.MB : c->nl.MB;
+  o->tile_lb = (c->precision == 1) ? c->nl32.LB : c->nl.LB;
   return TC_OK;
 }
 
@@ -560,7 +589,9 @@ tc_status tc_get_state(const tc_ctx *c, void *spec, int where) {
   const size_t bytes = (size_t)16 * c->sz.nf * c->sz.S;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpy(spec, c->X, bytes, where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+    e = cudaMemcpyAsync(spec, c->X, bytes,
+                        where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail_cuda(const_cast<tc_ctx *>(c), e);
   return TC_OK;
 }
@@ -570,8 +601,10 @@ tc_status tc_get_pressure(const tc_ctx *c, void *spec, int where) {
   if (c->poisoned) return TC_ERR_CUDA;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpy(spec, c->P, (size_t)16 * c->sz.S,
-                   where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+    e = cudaMemcpyAsync(spec, c->P, (size_t)16 * c->sz.S,
+                        where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail_cuda(const_cast<tc_ctx *>(c), e);
   return TC_OK;
 }
@@ -652,13 +685,17 @@ tc_status tc_init_perturbation(tc_ctx *c, const double *psi, int mp, int kp, dou
     }
   }
   try {
-    ck(cudaMemcpy(c->Xp, u.data(), u.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // every copy ordered on the context's stream (it may be a non-blocking one)
+    ck(cudaMemcpyAsync(c->Xp, u.data(), u.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
     unsigned long long zero[2] = {0ull, 0ull};
-    ck(cudaMemcpy(c->scal->norm_bits, zero, sizeof(zero), cudaMemcpyHostToDevice));
+    ck(cudaMemcpyAsync(c->scal->norm_bits, zero, sizeof(zero), cudaMemcpyHostToDevice,
+                       c->stream));
     launch_nonlinear(c, c->Xp, nullptr, nullptr, 1);
     ck(cudaGetLastError());
     unsigned long long nb[2];
-    ck(cudaMemcpy(nb, c->scal->norm_bits, sizeof(nb), cudaMemcpyDeviceToHost));
+    ck(cudaMemcpyAsync(nb, c->scal->norm_bits, sizeof(nb), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
     double umax, tmax;
     std::memcpy(&umax, &nb[0], sizeof(double));
     std::memcpy(&tmax, &nb[1], sizeof(double));
@@ -671,9 +708,11 @@ tc_status tc_init_perturbation(tc_ctx *c, const double *psi, int mp, int kp, dou
     for (long long i = 0; i < 2 * 3 * s.S; ++i) X[i] += su * u[i];
     if (s.nf == 4)
       for (long long i = 2 * 3 * s.S; i < 2 * 4 * s.S; ++i) X[i] += sT * u[i];
-    ck(cudaMemcpy(c->X, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice));
+    ck(cudaMemcpyAsync(c->X, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
     DevScalars sc{};
-    ck(cudaMemcpy(c->scal, &sc, sizeof(sc), cudaMemcpyHostToDevice));
+    ck(cudaMemcpyAsync(c->scal, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
   } catch (const CudaError &e) {
     return fail_cuda(c, e.e);
   }
@@ -699,15 +738,7 @@ tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
     int zero = 0;
     ck(cudaMemcpyAsync(&c->scal->nonfinite, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
     const double dt_fixed = dt > 0.0 ? dt : 0.0;
-    for (int n = 0; n < nsteps; ++n) {
-      launch_nonlinear(c, c->X, c->N0, &c->scal->rate_bits, 0);
-      launch_dt_policy(c, dt_fixed, n);
-      launch_refactor(c);
-      launch_rhs(c, c->X, c->N0);
-      launch_stage(c, c->N0, c->Xp, c->P);
-      launch_nonlinear(c, c->Xp, c->N1, nullptr, 0);
-      launch_stage(c, c->N1, c->X, c->P);
-    }
+    for (int n = 0; n < nsteps; ++n) enqueue_step(c, dt_fixed, n);
     ck(cudaGetLastError());
     std::vector<double> hist(nsteps);
     ck(cudaMemcpyAsync(hist.data(), c->dt_hist, sizeof(double) * nsteps, cudaMemcpyDeviceToHost,
@@ -931,7 +962,9 @@ tc_status tc_init_perturbation_adjoint(tc_ctx *c, const void *lam_dev, int mp, i
   std::vector<cplx> lam((size_t)s.nf * s.S);
   try {
     ck(cudaStreamSynchronize(c->stream));
-    ck(cudaMemcpy(lam.data(), lam_dev, sizeof(cplx) * lam.size(), cudaMemcpyDeviceToHost));
+    ck(cudaMemcpyAsync(lam.data(), lam_dev, sizeof(cplx) * lam.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    ck(cudaStreamSynchronize(c->stream));
   } catch (const CudaError &e) {
     return fail_cuda(c, e.e);
   }

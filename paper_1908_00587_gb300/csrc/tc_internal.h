@@ -150,6 +150,8 @@ struct tc_ctx {
   size_t smem_zinv, smem_theta, smem_zfwd;
   long long launches = 0;        // kernels launched since tc_create
   int timing = 0;
+  int capturing = 0;            // a graph is capturing this context's stream
+  int tile_mb = 0, tile_lb = 0; // nonlinear-stage tile overrides (0: default)
   tc::KernelTimer timers[tc::KNUM];
 };
 
@@ -165,6 +167,23 @@ struct LaunchScope {
 }  // namespace tc
 
 namespace tc {
+
+// The dynamic shared-memory limit is a property of the kernel function, shared
+// by every context of the process, so each kernel is opened up to the
+// device's opt-in maximum instead of one context's own need (a smaller launch
+// is unaffected by the larger limit).
+template <typename F>
+inline void allow_smem(F *kernel) {
+  int dev = 0, mx = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) mx -= (int)fa.sharedSizeBytes;
+  if (mx > 0) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
+// tc_host.cu
+void enqueue_step(tc_ctx *c, double dt_fixed, int step_index);
 
 // nonlinear.cu
 void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long long *rate_bits,

@@ -44,7 +44,15 @@ class tc_info(ctypes.Structure):
     _fields_ = [("Nr", ctypes.c_int), ("Ntheta", ctypes.c_int), ("Nz", ctypes.c_int),
                 ("M", ctypes.c_int), ("K", ctypes.c_int), ("nfields", ctypes.c_int),
                 ("coeffs_per_field", ctypes.c_longlong), ("state_bytes", ctypes.c_longlong),
-                ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_longlong)]
+                ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_longlong),
+                ("tile_mb", ctypes.c_int), ("tile_lb", ctypes.c_int)]
+
+
+class tc_params(ctypes.Structure):
+    _fields_ = [("Nr", ctypes.c_int), ("Ntheta", ctypes.c_int), ("Nz", ctypes.c_int),
+                ("eta", ctypes.c_double), ("Lz", ctypes.c_double), ("Re_i", ctypes.c_double),
+                ("Re_o", ctypes.c_double), ("Ra", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("precision", ctypes.c_int)]
 
 
 class tc_kernel_time(ctypes.Structure):
@@ -78,6 +86,11 @@ _SIGS = {
     "tc_objective": [_P, ctypes.POINTER(_D), _P],
     "tc_init_perturbation_adjoint": [_P, _P, _I, _I, _P, _P],
     "tc_get_ic_scales": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "tc_ensemble_create": [_I, _P, _I, ctypes.POINTER(_P)],
+    "tc_ensemble_member": [_P, _I, ctypes.POINTER(_P)],
+    "tc_ensemble_step": [_P, _I, _P],
+    "tc_ensemble_kernels_per_step": [_P, ctypes.POINTER(ctypes.c_longlong)],
+    "tc_ensemble_destroy": [_P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -249,6 +262,39 @@ def tc_get_ic_scales(ctx):
     a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
     _check(_lib.tc_get_ic_scales(ctx, ctypes.byref(a), ctypes.byref(b)), "tc_get_ic_scales")
     return a.value, b.value
+
+
+def tc_ensemble_create(workloads, autotune_tiles=True):
+    n = len(workloads)
+    arr = (tc_params * n)()
+    for i, w in enumerate(workloads):
+        arr[i] = tc_params(w.Nr, w.Ntheta, w.Nz, w.eta, w.Lz, w.Re_i, w.Re_o, w.Ra, w.Pr,
+                           int(getattr(w, "precision", 0)))
+    h = _P()
+    _check(_lib.tc_ensemble_create(n, ctypes.cast(arr, _P), int(bool(autotune_tiles)),
+                                   ctypes.byref(h)), "tc_ensemble_create")
+    return h
+
+
+def tc_ensemble_member(ens, i):
+    h = _P()
+    _check(_lib.tc_ensemble_member(ens, int(i), ctypes.byref(h)), "tc_ensemble_member")
+    return h
+
+
+def tc_ensemble_step(ens, nsteps, dts):
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    _check(_lib.tc_ensemble_step(ens, int(nsteps), d.ctypes.data), "tc_ensemble_step")
+
+
+def tc_ensemble_kernels_per_step(ens):
+    n = ctypes.c_longlong(0)
+    _check(_lib.tc_ensemble_kernels_per_step(ens, ctypes.byref(n)), "tc_ensemble_kernels_per_step")
+    return n.value
+
+
+def tc_ensemble_destroy(ens):
+    _check(_lib.tc_ensemble_destroy(ens), "tc_ensemble_destroy")
 
 
 def tc_status_string(s: int) -> str:

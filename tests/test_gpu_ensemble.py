@@ -1,0 +1,88 @@
+"""Ensemble form: independent runs of uneven size replayed as one CUDA graph.
+
+Each member must give exactly what the same run gives on its own (the graph
+only changes when and where kernels run; the autotuned tiles only change
+which CTA computes a transform), and small FP64 members are pinned to the
+oracle.  Per-member fixed step: dt = min(1e-3, 0.25 / CFL rate of u0).
+"""
+import numpy as np
+import pytest
+
+from inputs import ensemble_members, psi_coefficients
+from oracle import Model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1908_00587_gb300 import tc as mod
+    return mod
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _init(tc, ctx, wl):
+    tc.tc_init_perturbation(ctx, psi_coefficients(wl.seed, wl.mp, wl.kp), wl.amp)
+    info = tc.tc_get_info(ctx)
+    shape = (info.nfields, info.Nr, info.M + 1, 2 * info.K + 1)
+    X = np.empty(shape, dtype=np.complex128)
+    tc.tc_get_state(ctx, X)
+    out = dev(np.zeros_like(X))
+    rate = tc.tc_nonlinear(ctx, dev(X), out)
+    return min(1e-3, 0.25 / rate), shape
+
+
+def test_ensemble_members_match_single_runs_bitwise(tc):
+    members = [w.scaled(precision=i % 2) for i, w in enumerate(ensemble_members(6))]
+    ens = tc.tc_ensemble_create(members, autotune_tiles=True)
+    dts, shapes = [], []
+    for i, wl in enumerate(members):
+        dt, shape = _init(tc, tc.tc_ensemble_member(ens, i), wl)
+        dts.append(dt)
+        shapes.append(shape)
+        info = tc.tc_get_info(tc.tc_ensemble_member(ens, i))
+        assert info.tile_mb >= 1 and info.tile_lb >= 1
+    tc.tc_ensemble_step(ens, 7, dts)
+    tc.tc_ensemble_step(ens, 5, dts)       # replay of the same graph
+    assert tc.tc_ensemble_kernels_per_step(ens) > 18 * len(members) - 1
+    got = []
+    for i in range(len(members)):
+        X = np.empty(shapes[i], dtype=np.complex128)
+        tc.tc_get_state(tc.tc_ensemble_member(ens, i), X)
+        got.append(X)
+    tc.tc_ensemble_destroy(ens)
+    for i, wl in enumerate(members):
+        run = tc.Run.from_workload(wl)       # default tiles, plain launches
+        dt, _ = _init(tc, run.ctx, wl)
+        assert dt == dts[i]
+        run.step(12, dt)
+        ref = run.get_state()
+        run.close()
+        assert np.array_equal(got[i], ref), i
+
+
+def test_ensemble_members_match_oracle(tc):
+    members = [w.scaled(Nr=24, Ntheta=32, Nz=32) for w in ensemble_members(2)]
+    ens = tc.tc_ensemble_create(members, autotune_tiles=True)
+    dts = [_init(tc, tc.tc_ensemble_member(ens, i), wl)[0] for i, wl in enumerate(members)]
+    tc.tc_ensemble_step(ens, 20, dts)
+    for i, wl in enumerate(members):
+        mdl = Model(wl, "fft")
+        X = mdl.initial_state(psi_coefficients(wl.seed, wl.mp, wl.kp))
+        X, _ = mdl.run(X, 20, dts[i])
+        got = np.empty(X.shape, dtype=np.complex128)
+        tc.tc_get_state(tc.tc_ensemble_member(ens, i), got)
+        w = (mdl.g.w * mdl.g.r)[:, None, None] * mdl.sp.cm[None, :, None]
+        err = max(np.sqrt(np.sum(w * np.abs(got[f] - X[f]) ** 2) / np.sum(w * np.abs(X[f]) ** 2))
+                  for f in range(X.shape[0]))
+        assert err <= 1e-10, (i, err)
+    tc.tc_ensemble_destroy(ens)

@@ -246,3 +246,24 @@ def test_sweep_wait_timeout_is_reported(tc):
     run.step(2, 1e-3)
     assert np.all(np.isfinite(run.get_state()))
     run.close()
+
+
+def test_non_blocking_stream_gives_identical_results(tc):
+    """Every host copy is ordered on the context's stream: a run on a
+    non-blocking stream must match a run on the legacy stream bit for bit."""
+    import torch
+    wl = WORKLOADS["tc_fp64T_nr64_n128"].scaled(Nr=20, Ntheta=24, Nz=24, mp=3, kp=3)
+    psi = psi_coefficients(wl.seed, wl.mp, wl.kp)
+    tco = temperature_coefficients(wl.seed, wl.mp, wl.kp)
+    out = []
+    for use_stream in (False, True):
+        run = tc.Run.from_workload(wl)
+        if use_stream:
+            s = torch.cuda.Stream()
+            run.set_stream(s.cuda_stream)
+        run.init_perturbation(psi, wl.amp, tco, wl.amp_T)
+        run.step(5, wl.dt)
+        out.append((run.get_state(), run.get_pressure()))
+        run.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
