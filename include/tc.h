@@ -285,6 +285,12 @@ tc_status tc_ensemble_member(tc_ens *e, int i, tc_ctx **ctx);
  * synchronisation. */
 tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt);
 
+/* Tile autotuner for one context (the one the ensemble runs per size
+ * class): times the nonlinear stage on the context's current state for tile
+ * shapes {1, 2, 4, 8} of "tile_mb", then of "tile_lb", keeps the fastest and
+ * returns them (host, nullable).  Results do not depend on the tiles. */
+tc_status tc_autotune(tc_ctx *ctx, int *tile_mb, int *tile_lb);
+
 /* Kernel launches one graph replay (one step of every member) contains. */
 tc_status tc_ensemble_kernels_per_step(const tc_ens *e, long long *count);
 

@@ -254,6 +254,17 @@ tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt) {
   return worst;
 }
 
+tc_status tc_autotune(tc_ctx *c, int *tile_mb, int *tile_lb) {
+  if (!c) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  int mb = 0, lb = 0;
+  const tc_status st = autotune(c, &mb, &lb);
+  if (st != TC_OK) return st;
+  if (tile_mb) *tile_mb = mb;
+  if (tile_lb) *tile_lb = lb;
+  return TC_OK;
+}
+
 tc_status tc_ensemble_kernels_per_step(const tc_ens *e, long long *count) {
   if (!e || !count) return TC_ERR_ARG;
   *count = 0;

@@ -136,6 +136,13 @@ __device__ __forceinline__ void dftR(V *v) {
   if constexpr (R == 8) dft8<S>(v);
 }
 
+// Shared-memory layout of the transforms: element i of a sequence sits at
+// i + i/8 and a sequence of length n occupies padlen(n) slots, so the
+// stride-R stores of a Stockham pass spread over the banks instead of
+// landing in the same ones.
+__host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 3); }
+__host__ __device__ __forceinline__ int padlen(int n) { return n + (n >> 3) + 1; }
+
 // One Stockham pass over `batch` transforms stored `bstride` apart.
 // tw[t] = exp(-2 pi i t / N).
 template <int R, int S, typename V>
@@ -153,7 +160,7 @@ __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__re
     const int k = j % Ns;
     V v[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = s[j + q * nb];
+    for (int q = 0; q < R; ++q) v[q] = s[spad(j + q * nb)];
     if (Ns > 1) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
@@ -164,7 +171,7 @@ __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__re
     dftR<R, S>(v);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int p = 0; p < R; ++p) d[base + p * Ns] = v[p];
+    for (int p = 0; p < R; ++p) d[spad(base + p * Ns)] = v[p];
   }
 }
 

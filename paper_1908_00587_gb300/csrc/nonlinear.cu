@@ -132,12 +132,13 @@ __global__ void k_zinv(const double2 *__restrict__ X, V2<T> *__restrict__ Vout, 
   const int r = blockIdx.y;
   const int c = blockIdx.z;
   const int Nz = s.Nz;
+  const int Np = padlen(Nz);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V2<T> *A = reinterpret_cast<V2<T> *>(smem_raw);
-  V2<T> *B = A + 3 * p.MB * Nz;
-  V2<T> *tw = B + 3 * p.MB * Nz;
+  V2<T> *B = A + 3 * p.MB * Np;
+  V2<T> *tw = B + 3 * p.MB * Np;
   load_tw<T>(tw, p.twz, Nz);
-  for (int i = threadIdx.x; i < 3 * nm * Nz; i += blockDim.x) A[i] = V2<T>{0, 0};
+  for (int i = threadIdx.x; i < 3 * nm * Np; i += blockDim.x) A[i] = V2<T>{0, 0};
   __syncthreads();
   const int st = p.rad.s0[r];
   const double *d1 = p.rad.D1 + r * kStencil;
@@ -160,18 +161,18 @@ __global__ void k_zinv(const double2 *__restrict__ X, V2<T> *__restrict__ Vout, 
     }
     const double beta = p.alpha * kval(kk, s.K, s.NK);
     const int pos = kpos(kk, s.K, s.NK, Nz);
-    A[(3 * mi + 0) * Nz + pos] = V2<T>{(T)val.x, (T)val.y};
-    A[(3 * mi + 1) * Nz + pos] = V2<T>{(T)dr.x, (T)dr.y};
-    A[(3 * mi + 2) * Nz + pos] = V2<T>{(T)(-beta * val.y), (T)(beta * val.x)};
+    A[(3 * mi + 0) * Np + spad(pos)] = V2<T>{(T)val.x, (T)val.y};
+    A[(3 * mi + 1) * Np + spad(pos)] = V2<T>{(T)dr.x, (T)dr.y};
+    A[(3 * mi + 2) * Np + spad(pos)] = V2<T>{(T)(-beta * val.y), (T)(beta * val.x)};
   }
   __syncthreads();
-  V2<T> *res = fft_batch<+1>(A, B, p.pz, 3 * nm, Nz, tw);
+  V2<T> *res = fft_batch<+1>(A, B, p.pz, 3 * nm, Np, tw);
   for (int t = threadIdx.x; t < 3 * nm * Nz; t += blockDim.x) {
     const int mi = t % nm;
     const int rest = t / nm;
     const int l = rest % Nz;
     const int d = rest / Nz;
-    Vout[(((long long)(3 * c + d) * s.Nr + r) * Nz + l) * s.NM + m0 + mi] = res[(3 * mi + d) * Nz + l];
+    Vout[(((long long)(3 * c + d) * s.Nr + r) * Nz + l) * s.NM + m0 + mi] = res[(3 * mi + d) * Np + spad(l)];
   }
 }
 
@@ -185,14 +186,15 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   const int nl = min(p.LB, s.Nz - l0);
   const int r = blockIdx.y;
   const int Nt = s.Nt;
+  const int Ntp = padlen(Nt);
   const int npair = 2 * s.nf;       // complex transforms per z-row
   const int nbuf = p.LB * npair;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V2<T> *A = reinterpret_cast<V2<T> *>(smem_raw);
-  V2<T> *B = A + nbuf * Nt;
-  V2<T> *tw = B + nbuf * Nt;
+  V2<T> *B = A + nbuf * Ntp;
+  V2<T> *tw = B + nbuf * Ntp;
   load_tw<T>(tw, p.twt, Nt);
-  for (int i = threadIdx.x; i < nl * npair * Nt; i += blockDim.x) A[i] = V2<T>{0, 0};
+  for (int i = threadIdx.x; i < nl * npair * Ntp; i += blockDim.x) A[i] = V2<T>{0, 0};
   __syncthreads();
   // pack: buffer (li, c, 0) = value + i dtheta, (li, c, 1) = d/dr + i d/dz
   for (int t = threadIdx.x; t < nl * s.nf * s.NM; t += blockDim.x) {
@@ -212,18 +214,18 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     }
     const T fm = (T)m;
     const V2<T> dt = V2<T>{-fm * v.y, fm * v.x};  // i m v
-    V2<T> *b0 = A + (li * npair + 2 * c) * Nt;
-    V2<T> *b1 = b0 + Nt;
+    V2<T> *b0 = A + (li * npair + 2 * c) * Ntp;
+    V2<T> *b1 = b0 + Ntp;
     // Z_m = a_m + i b_m ; Z_{-m} = conj(a_m) + i conj(b_m)
-    b0[m] = V2<T>{v.x - dt.y, v.y + dt.x};
-    b1[m] = V2<T>{dr.x - dz.y, dr.y + dz.x};
+    b0[spad(m)] = V2<T>{v.x - dt.y, v.y + dt.x};
+    b1[spad(m)] = V2<T>{dr.x - dz.y, dr.y + dz.x};
     if (m > 0) {
-      b0[Nt - m] = V2<T>{v.x + dt.y, -v.y + dt.x};
-      b1[Nt - m] = V2<T>{dr.x + dz.y, -dr.y + dz.x};
+      b0[spad(Nt - m)] = V2<T>{v.x + dt.y, -v.y + dt.x};
+      b1[spad(Nt - m)] = V2<T>{dr.x + dz.y, -dr.y + dz.x};
     }
   }
   __syncthreads();
-  V2<T> *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Nt, tw);
+  V2<T> *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Ntp, tw);
   V2<T> *out = (ph == A) ? B : A;
   const double rr = p.rad.r[r];
   const T inv_r = (T)p.rad.inv_r[r];
@@ -231,16 +233,16 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   for (int t = threadIdx.x; t < nl * Nt; t += blockDim.x) {
     const int j = t % Nt;
     const int li = t / Nt;
-    const V2<T> *b = ph + li * npair * Nt + j;
-    const V2<T> r0 = b[0 * Nt], r1 = b[1 * Nt];   // (ur, ur_t), (ur_r, ur_z)
-    const V2<T> t0 = b[2 * Nt], t1 = b[3 * Nt];   // (ut, ut_t), (ut_r, ut_z)
-    const V2<T> z0 = b[4 * Nt], z1 = b[5 * Nt];   // (uz, uz_t), (uz_r, uz_z)
+    const V2<T> *b = ph + li * npair * Ntp + spad(j);
+    const V2<T> r0 = b[0 * Ntp], r1 = b[1 * Ntp];   // (ur, ur_t), (ur_r, ur_z)
+    const V2<T> t0 = b[2 * Ntp], t1 = b[3 * Ntp];   // (ut, ut_t), (ut_r, ut_z)
+    const V2<T> z0 = b[4 * Ntp], z1 = b[5 * Ntp];   // (uz, uz_t), (uz_r, uz_z)
     const T ur = r0.x, ut = t0.x, uz = z0.x;
     // full velocity for the CFL bound (mixed: the transforms carry u' only)
     const double Ut = p.mixed ? p.prof[r * 8 + 0] : 0.0, Uz = p.mixed ? p.prof[r * 8 + 1] : 0.0;
     if (mode == 1) {
       nu = fmax(nu, sqrt((double)ur * ur + (double)ut * ut + (double)uz * uz));
-      if (s.nf == 4) nT = fmax(nT, fabs((double)b[6 * Nt].x));
+      if (s.nf == 4) nT = fmax(nT, fabs((double)b[6 * Ntp].x));
       continue;
     }
     const T ut_r = ut * inv_r;
@@ -252,13 +254,13 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     T Nz_ = -adv_z;
     T NT_ = 0;
     if (s.nf == 4) {
-      const V2<T> T0 = b[6 * Nt], T1 = b[7 * Nt];
+      const V2<T> T0 = b[6 * Ntp], T1 = b[7 * Ntp];
       if (!p.mixed) Nz_ += (T)p.Gr * T0.x;   // mixed: buoyancy added in FP64
       NT_ = -(ur * T1.x + ut_r * T0.y + uz * T1.y);
     }
-    V2<T> *o = out + li * 2 * Nt + j;
+    V2<T> *o = out + li * 2 * Ntp + spad(j);
     o[0] = V2<T>{Nr_, Nt_};
-    o[Nt] = V2<T>{Nz_, NT_};
+    o[Ntp] = V2<T>{Nz_, NT_};
     if (rate_bits) {
       const double a = fmax(fabs((double)ur) / p.rad.dr_min[r],
                             fmax(fabs((double)ut + Ut) / (rr * p.dth), fabs((double)uz + Uz) / p.dz));
@@ -282,19 +284,19 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   }
   __syncthreads();
   V2<T> *scratch = (out == A) ? B : A;
-  V2<T> *sp = fft_batch<-1>(out, scratch, p.pt, nl * 2, Nt, tw);
+  V2<T> *sp = fft_batch<-1>(out, scratch, p.pt, nl * 2, Ntp, tw);
   // unpack two real transforms: X_m = (Z_m + conj Z_-m)/2, Y_m = (Z_m - conj Z_-m)/(2i)
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
   for (int t = threadIdx.x; t < nl * s.NM; t += blockDim.x) {
     const int m = t % s.NM;
     const int li = t / s.NM;
-    const V2<T> *z0 = sp + li * 2 * Nt;
+    const V2<T> *z0 = sp + li * 2 * Ntp;
     const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
     const int mm = (Nt - m) % Nt;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const V2<T> a = z0[h * Nt + m];
-      const V2<T> b = z0[h * Nt + mm];
+      const V2<T> a = z0[h * Ntp + spad(m)];
+      const V2<T> b = z0[h * Ntp + spad(mm)];
       const V2<T> x = V2<T>{(T)0.5 * (a.x + b.x), (T)0.5 * (a.y - b.y)};
       const V2<T> y = V2<T>{(T)0.5 * (a.y + b.y), (T)0.5 * (b.x - a.x)};
       W[(2 * h) * fs + off] = x;
@@ -311,11 +313,12 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
   const int nm = min(p.MB, s.NM - m0);
   const int r = blockIdx.y;
   const int Nz = s.Nz;
+  const int Np = padlen(Nz);
   const int nb = s.nf * nm;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V2<T> *A = reinterpret_cast<V2<T> *>(smem_raw);
-  V2<T> *B = A + s.nf * p.MB * Nz;
-  V2<T> *tw = B + s.nf * p.MB * Nz;
+  V2<T> *B = A + s.nf * p.MB * Np;
+  V2<T> *tw = B + s.nf * p.MB * Np;
   load_tw<T>(tw, p.twz, Nz);
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
   for (int t = threadIdx.x; t < nb * Nz; t += blockDim.x) {
@@ -323,17 +326,17 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
     const int rest = t / nm;
     const int l = rest % Nz;
     const int g = rest / Nz;
-    A[(g * nm + mi) * Nz + l] = W[g * fs + ((long long)r * Nz + l) * s.NM + m0 + mi];
+    A[(g * nm + mi) * Np + spad(l)] = W[g * fs + ((long long)r * Nz + l) * s.NM + m0 + mi];
   }
   __syncthreads();
-  V2<T> *res = fft_batch<-1>(A, B, p.pz, nb, Nz, tw);
+  V2<T> *res = fft_batch<-1>(A, B, p.pz, nb, Np, tw);
   const double scale = 1.0 / ((double)s.Nt * (double)s.Nz);
   for (int t = threadIdx.x; t < nb * s.NK; t += blockDim.x) {
     const int kk = t % s.NK;
     const int rest = t / s.NK;
     const int mi = rest % nm;
     const int g = rest / nm;
-    const V2<T> v = res[(g * nm + mi) * Nz + kpos(kk, s.K, s.NK, Nz)];
+    const V2<T> v = res[(g * nm + mi) * Np + spad(kpos(kk, s.K, s.NK, Nz))];
     double2 out = double2{(double)v.x * scale, (double)v.y * scale};
     if (p.mixed) {
       const double2 lin = mean_flow_terms(p, g, r, m0 + mi, kk);
@@ -362,9 +365,9 @@ void setup_nonlinear(tc_ctx *c) {
   if (LB > 8) LB = 8;
   if (c->tile_lb > 0) LB = c->tile_lb;
   p.LB = LB;
-  c->smem_zinv = (size_t)(2 * 3 * MB * s.Nz + s.Nz) * e;
-  c->smem_theta = (size_t)(2 * LB * 2 * s.nf * s.Nt + s.Nt) * e;
-  c->smem_zfwd = (size_t)(2 * s.nf * MB * s.Nz + s.Nz) * e;
+  c->smem_zinv = (size_t)(2 * 3 * MB * padlen(s.Nz) + s.Nz) * e;
+  c->smem_theta = (size_t)(2 * LB * 2 * s.nf * padlen(s.Nt) + s.Nt) * e;
+  c->smem_zfwd = (size_t)(2 * s.nf * MB * padlen(s.Nz) + s.Nz) * e;
   allow_smem(k_zinv<double>);
   allow_smem(k_theta<double>);
   allow_smem(k_zfwd<double>);
@@ -381,9 +384,9 @@ void setup_nonlinear(tc_ctx *c) {
   if (c->tile_lb > 0) LB32 = c->tile_lb;
   q.MB = MB32;
   q.LB = LB32;
-  c->smem32_zinv = (size_t)(2 * 3 * MB32 * s.Nz + s.Nz) * e32;
-  c->smem32_theta = (size_t)(2 * LB32 * 2 * s.nf * s.Nt + s.Nt) * e32;
-  c->smem32_zfwd = (size_t)(2 * s.nf * MB32 * s.Nz + s.Nz) * e32;
+  c->smem32_zinv = (size_t)(2 * 3 * MB32 * padlen(s.Nz) + s.Nz) * e32;
+  c->smem32_theta = (size_t)(2 * LB32 * 2 * s.nf * padlen(s.Nt) + s.Nt) * e32;
+  c->smem32_zfwd = (size_t)(2 * s.nf * MB32 * padlen(s.Nz) + s.Nz) * e32;
   allow_smem(k_zinv<float>);
   allow_smem(k_theta<float>);
   allow_smem(k_zfwd<float>);
@@ -535,9 +538,9 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
   p.MB = MB;
   p.LB = LB;
   const size_t e = sizeof(double2);
-  const size_t sm_zinv = (size_t)(2 * 3 * MB * s.Nz + s.Nz) * e;
-  const size_t sm_theta = (size_t)(2 * LB * 2 * s.nf * s.Nt + s.Nt) * e;
-  const size_t sm_zfwd = (size_t)(2 * s.nf * MB * s.Nz + s.Nz) * e;
+  const size_t sm_zinv = (size_t)(2 * 3 * MB * padlen(s.Nz) + s.Nz) * e;
+  const size_t sm_theta = (size_t)(2 * LB * 2 * s.nf * padlen(s.Nt) + s.Nt) * e;
+  const size_t sm_zfwd = (size_t)(2 * s.nf * MB * padlen(s.Nz) + s.Nz) * e;
   if (sm_zinv > 227 * 1024 || sm_theta > 227 * 1024 || sm_zfwd > 227 * 1024)
     return TC_ERR_UNSUPPORTED;
 
@@ -646,12 +649,13 @@ __global__ void k_zinv_adj(const double2 *__restrict__ Nb, double2 *__restrict__
   const int nm = min(p.MB, s.NM - m0);
   const int r = blockIdx.y;
   const int Nz = s.Nz;
+  const int Np = padlen(Nz);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2 *A = reinterpret_cast<double2 *>(smem_raw);
-  double2 *B = A + s.nf * p.MB * Nz;
-  double2 *tw = B + s.nf * p.MB * Nz;
+  double2 *B = A + s.nf * p.MB * Np;
+  double2 *tw = B + s.nf * p.MB * Np;
   load_tw<double>(tw, p.twz, Nz);
-  for (int i = threadIdx.x; i < s.nf * nm * Nz; i += blockDim.x) A[i] = double2{0, 0};
+  for (int i = threadIdx.x; i < s.nf * nm * Np; i += blockDim.x) A[i] = double2{0, 0};
   __syncthreads();
   for (int t = threadIdx.x; t < s.nf * nm * s.NK; t += blockDim.x) {
     const int kk = t % s.NK;
@@ -661,16 +665,16 @@ __global__ void k_zinv_adj(const double2 *__restrict__ Nb, double2 *__restrict__
     const int m = m0 + mi;
     const double h = (m == 0) ? 1.0 : 0.5;
     const double2 v = Nb[(long long)g * s.S + (long long)r * s.nmode + (long long)m * s.NK + kk];
-    A[(g * nm + mi) * Nz + kpos(kk, s.K, s.NK, Nz)] = double2{h * v.x, h * v.y};
+    A[(g * nm + mi) * Np + spad(kpos(kk, s.K, s.NK, Nz))] = double2{h * v.x, h * v.y};
   }
   __syncthreads();
-  double2 *res = fft_batch<+1>(A, B, p.pz, s.nf * nm, Nz, tw);
+  double2 *res = fft_batch<+1>(A, B, p.pz, s.nf * nm, Np, tw);
   for (int t = threadIdx.x; t < s.nf * nm * Nz; t += blockDim.x) {
     const int mi = t % nm;
     const int rest = t / nm;
     const int l = rest % Nz;
     const int g = rest / Nz;
-    Vout[(((long long)g * s.Nr + r) * Nz + l) * s.NM + m0 + mi] = res[(g * nm + mi) * Nz + l];
+    Vout[(((long long)g * s.Nr + r) * Nz + l) * s.NM + m0 + mi] = res[(g * nm + mi) * Np + spad(l)];
   }
 }
 
@@ -685,15 +689,16 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
   const int nl = min(p.LB, s.Nz - l0);
   const int r = blockIdx.y;
   const int Nt = s.Nt;
+  const int Ntp = padlen(Nt);
   const int nfw = 2 * s.nf;          // forward-field pairs per row
   const int npair = nfw + 2;         // + cotangent pairs (Nr, Ntheta), (Nz, NT)
   const int nbuf = p.LB * npair;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2 *A = reinterpret_cast<double2 *>(smem_raw);
-  double2 *B = A + nbuf * Nt;
-  double2 *tw = B + nbuf * Nt;
+  double2 *B = A + nbuf * Ntp;
+  double2 *tw = B + nbuf * Ntp;
   load_tw<double>(tw, p.twt, Nt);
-  for (int i = threadIdx.x; i < nl * npair * Nt; i += blockDim.x) A[i] = double2{0, 0};
+  for (int i = threadIdx.x; i < nl * npair * Ntp; i += blockDim.x) A[i] = double2{0, 0};
   __syncthreads();
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
   for (int t = threadIdx.x; t < nl * (s.nf + 2) * s.NM; t += blockDim.x) {
@@ -714,8 +719,8 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
         f.y = 0.0;
       }
       b = double2{-(double)m * a.y, (double)m * a.x};   // i m a
-      b0 = A + (li * npair + 2 * c) * Nt;
-      b1 = b0 + Nt;
+      b0 = A + (li * npair + 2 * c) * Ntp;
+      b1 = b0 + Ntp;
     } else {
       const int h = c - s.nf;   // 0: (N_r, N_theta), 1: (N_z, N_T)
       a = V2[(2 * h) * fs + off];
@@ -724,29 +729,29 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
         a.y = 0.0;
         b.y = 0.0;
       }
-      b0 = A + (li * npair + nfw + h) * Nt;
+      b0 = A + (li * npair + nfw + h) * Ntp;
       b1 = nullptr;
     }
-    b0[m] = double2{a.x - b.y, a.y + b.x};
-    if (m > 0) b0[Nt - m] = double2{a.x + b.y, -a.y + b.x};
+    b0[spad(m)] = double2{a.x - b.y, a.y + b.x};
+    if (m > 0) b0[spad(Nt - m)] = double2{a.x + b.y, -a.y + b.x};
     if (b1) {
-      b1[m] = double2{e.x - f.y, e.y + f.x};
-      if (m > 0) b1[Nt - m] = double2{e.x + f.y, -e.y + f.x};
+      b1[spad(m)] = double2{e.x - f.y, e.y + f.x};
+      if (m > 0) b1[spad(Nt - m)] = double2{e.x + f.y, -e.y + f.x};
     }
   }
   __syncthreads();
-  double2 *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Nt, tw);
+  double2 *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Ntp, tw);
   double2 *out = (ph == A) ? B : A;
   const double ir = p.rad.inv_r[r];
   const double sc = 1.0 / ((double)s.Nt * (double)s.Nz);
   for (int t = threadIdx.x; t < nl * Nt; t += blockDim.x) {
     const int j = t % Nt;
     const int li = t / Nt;
-    const double2 *b = ph + li * npair * Nt + j;
-    const double2 r0 = b[0 * Nt], r1 = b[1 * Nt];   // (ur, ur_t), (ur_r, ur_z)
-    const double2 t0 = b[2 * Nt], t1 = b[3 * Nt];
-    const double2 z0 = b[4 * Nt], z1 = b[5 * Nt];
-    const double2 nb0 = b[nfw * Nt], nb1 = b[(nfw + 1) * Nt];
+    const double2 *b = ph + li * npair * Ntp + spad(j);
+    const double2 r0 = b[0 * Ntp], r1 = b[1 * Ntp];   // (ur, ur_t), (ur_r, ur_z)
+    const double2 t0 = b[2 * Ntp], t1 = b[3 * Ntp];
+    const double2 z0 = b[4 * Ntp], z1 = b[5 * Ntp];
+    const double2 nb0 = b[nfw * Ntp], nb1 = b[(nfw + 1) * Ntp];
     const double ar = sc * nb0.x, at = sc * nb0.y, az = sc * nb1.x, aT = sc * nb1.y;
     const double ur = r0.x, ut = t0.x, uz = z0.x;
     const double vt = ut * ir;
@@ -760,7 +765,7 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
     const double guzr = -ur * az, guzt = -vt * az, guzz = -uz * az;
     double gT = 0.0, gTr = 0.0, gTt = 0.0, gTz = 0.0;
     if (s.nf == 4) {
-      const double2 T0 = b[6 * Nt], T1 = b[7 * Nt];
+      const double2 T0 = b[6 * Ntp], T1 = b[7 * Ntp];
       gur -= T1.x * aT;
       gut -= (T0.y * ir) * aT;
       guz -= T1.y * aT;
@@ -769,21 +774,21 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
       gTt = -vt * aT;
       gTz = -uz * aT;
     }
-    double2 *o = out + li * nfw * Nt + j;
-    o[0 * Nt] = double2{gur, gurt};
-    o[1 * Nt] = double2{gurr, gurz};
-    o[2 * Nt] = double2{gut, gutt};
-    o[3 * Nt] = double2{gutr, gutz};
-    o[4 * Nt] = double2{guz, guzt};
-    o[5 * Nt] = double2{guzr, guzz};
+    double2 *o = out + li * nfw * Ntp + spad(j);
+    o[0 * Ntp] = double2{gur, gurt};
+    o[1 * Ntp] = double2{gurr, gurz};
+    o[2 * Ntp] = double2{gut, gutt};
+    o[3 * Ntp] = double2{gutr, gutz};
+    o[4 * Ntp] = double2{guz, guzt};
+    o[5 * Ntp] = double2{guzr, guzz};
     if (s.nf == 4) {
-      o[6 * Nt] = double2{gT, gTt};
-      o[7 * Nt] = double2{gTr, gTz};
+      o[6 * Ntp] = double2{gT, gTt};
+      o[7 * Ntp] = double2{gTr, gTz};
     }
   }
   __syncthreads();
   double2 *scratch = (out == A) ? B : A;
-  double2 *sp = fft_batch<-1>(out, scratch, p.pt, nl * nfw, Nt, tw);
+  double2 *sp = fft_batch<-1>(out, scratch, p.pt, nl * nfw, Ntp, tw);
   for (int t = threadIdx.x; t < nl * s.nf * s.NM; t += blockDim.x) {
     const int m = t % s.NM;
     const int rest = t / s.NM;
@@ -792,15 +797,15 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
     const double cm = (m == 0) ? 1.0 : 2.0;
     const int mm = (Nt - m) % Nt;
     const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
-    const double2 *z0 = sp + (li * nfw + 2 * c) * Nt;
+    const double2 *z0 = sp + (li * nfw + 2 * c) * Ntp;
     // pair (val, theta): X = value part, Y = theta part
-    const double2 a = z0[m], bq = z0[mm];
+    const double2 a = z0[spad(m)], bq = z0[spad(mm)];
     const double2 Gv = double2{0.5 * (a.x + bq.x), 0.5 * (a.y - bq.y)};
     const double2 Gt = double2{0.5 * (a.y + bq.y), 0.5 * (bq.x - a.x)};
     // value cotangent with the theta derivative folded in: c'_m (Gv - i m Gt)
     Wa[(3 * c + 0) * fs + off] = double2{cm * (Gv.x + m * Gt.y), cm * (Gv.y - m * Gt.x)};
-    const double2 *z1 = z0 + Nt;
-    const double2 a1 = z1[m], b1 = z1[mm];
+    const double2 *z1 = z0 + Ntp;
+    const double2 a1 = z1[spad(m)], b1 = z1[spad(mm)];
     const double2 Gr = double2{0.5 * (a1.x + b1.x), 0.5 * (a1.y - b1.y)};
     const double2 Gz = double2{0.5 * (a1.y + b1.y), 0.5 * (b1.x - a1.x)};
     Wa[(3 * c + 1) * fs + off] = double2{cm * Gr.x, cm * Gr.y};
@@ -818,10 +823,11 @@ __global__ void k_zfwd_adj(const double2 *__restrict__ Wa, double2 *__restrict__
   const int r = blockIdx.y;
   const int c = blockIdx.z;
   const int Nz = s.Nz;
+  const int Np = padlen(Nz);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2 *A = reinterpret_cast<double2 *>(smem_raw);
-  double2 *B = A + 3 * p.MB * Nz;
-  double2 *tw = B + 3 * p.MB * Nz;
+  double2 *B = A + 3 * p.MB * Np;
+  double2 *tw = B + 3 * p.MB * Np;
   load_tw<double>(tw, p.twz, Nz);
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
   for (int t = threadIdx.x; t < 3 * nm * Nz; t += blockDim.x) {
@@ -829,18 +835,18 @@ __global__ void k_zfwd_adj(const double2 *__restrict__ Wa, double2 *__restrict__
     const int rest = t / nm;
     const int l = rest % Nz;
     const int d = rest / Nz;
-    A[(3 * mi + d) * Nz + l] = Wa[(3 * c + d) * fs + ((long long)r * Nz + l) * s.NM + m0 + mi];
+    A[(3 * mi + d) * Np + spad(l)] = Wa[(3 * c + d) * fs + ((long long)r * Nz + l) * s.NM + m0 + mi];
   }
   __syncthreads();
-  double2 *res = fft_batch<-1>(A, B, p.pz, 3 * nm, Nz, tw);
+  double2 *res = fft_batch<-1>(A, B, p.pz, 3 * nm, Np, tw);
   for (int t = threadIdx.x; t < nm * s.NK; t += blockDim.x) {
     const int kk = t % s.NK;
     const int mi = t / s.NK;
-    const int pos = kpos(kk, s.K, s.NK, Nz);
+    const int pos = spad(kpos(kk, s.K, s.NK, Nz));
     const double beta = p.alpha * kval(kk, s.K, s.NK);
-    const double2 v = res[(3 * mi + 0) * Nz + pos];
-    const double2 gr = res[(3 * mi + 1) * Nz + pos];
-    const double2 gz = res[(3 * mi + 2) * Nz + pos];
+    const double2 v = res[(3 * mi + 0) * Np + pos];
+    const double2 gr = res[(3 * mi + 1) * Np + pos];
+    const double2 gz = res[(3 * mi + 2) * Np + pos];
     const long long i = (long long)c * s.S + (long long)r * s.nmode + (long long)(m0 + mi) * s.NK + kk;
     double2 x = double2{v.x + beta * gz.y, v.y - beta * gz.x};   // v - i beta gz
     if (accumulate) {
@@ -877,13 +883,19 @@ __global__ void k_drT(const double2 *__restrict__ Gr, double2 *__restrict__ Xb, 
 
 }  // namespace
 
-void setup_nonlinear_adjoint(tc_ctx *c) {
+// The adjoint's azimuthal kernel holds 2 nf + 2 sequences per z-row, so it
+// takes the largest z-row tile not above the forward one that fits.
+static int adjoint_lb(const tc_ctx *c) {
   const Sizes &s = c->sz;
-  const NLParams &p = c->nl;
-  const size_t e = sizeof(double2);
-  c->smem_adj_zinv = (size_t)(2 * s.nf * p.MB * s.Nz + s.Nz) * e;
-  c->smem_adj_theta = (size_t)(2 * p.LB * (2 * s.nf + 2) * s.Nt + s.Nt) * e;
-  c->smem_adj_zfwd = (size_t)(2 * 3 * p.MB * s.Nz + s.Nz) * e;
+  int lb = c->nl.LB;
+  while (lb > 1 && (size_t)(2 * lb * (2 * s.nf + 2) * padlen(s.Nt) + s.Nt) * sizeof(double2) >
+                       (size_t)227 * 1024)
+    --lb;
+  return lb;
+}
+
+void setup_nonlinear_adjoint(tc_ctx *c) {
+  (void)c;
   allow_smem(k_zinv_adj);
   allow_smem(k_theta_adj);
   allow_smem(k_zfwd_adj);
@@ -892,7 +904,12 @@ void setup_nonlinear_adjoint(tc_ctx *c) {
 void launch_nonlinear_adjoint(tc_ctx *c, const double2 *X, const double2 *Nb, double2 *Xb,
                               int accumulate) {
   const Sizes &s = c->sz;
-  const NLParams &p = c->nl;
+  NLParams p = c->nl;
+  p.LB = adjoint_lb(c);
+  const size_t e = sizeof(double2);
+  c->smem_adj_zinv = (size_t)(2 * s.nf * p.MB * padlen(s.Nz) + s.Nz) * e;
+  c->smem_adj_theta = (size_t)(2 * p.LB * (2 * s.nf + 2) * padlen(s.Nt) + s.Nt) * e;
+  c->smem_adj_zfwd = (size_t)(2 * 3 * p.MB * padlen(s.Nz) + s.Nz) * e;
   const int nmb = (s.NM + p.MB - 1) / p.MB;
   const int nlb = (s.Nz + p.LB - 1) / p.LB;
   {

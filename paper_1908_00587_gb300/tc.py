@@ -91,6 +91,7 @@ _SIGS = {
     "tc_ensemble_step": [_P, _I, _P],
     "tc_ensemble_kernels_per_step": [_P, ctypes.POINTER(ctypes.c_longlong)],
     "tc_ensemble_destroy": [_P],
+    "tc_autotune": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -291,6 +292,12 @@ def tc_ensemble_kernels_per_step(ens):
     n = ctypes.c_longlong(0)
     _check(_lib.tc_ensemble_kernels_per_step(ens, ctypes.byref(n)), "tc_ensemble_kernels_per_step")
     return n.value
+
+
+def tc_autotune(ctx):
+    a, b = _I(0), _I(0)
+    _check(_lib.tc_autotune(ctx, ctypes.byref(a), ctypes.byref(b)), "tc_autotune")
+    return a.value, b.value
 
 
 def tc_ensemble_destroy(ens):
