@@ -258,43 +258,37 @@ __global__ void k_rhs(const double2 *__restrict__ X, const double2 *__restrict__
   const double idt = 1.0 / sc->dt;
   const double ir = p.rad.inv_r[j];
   const int st = p.rad.s0[j];
-  const double *d1 = p.rad.D1 + j * kStencil, *d2 = p.rad.D2 + j * kStencil;
+  const double *lw = p.rad.Lw + j * kStencil;   // D2 + D1/r of row j
   const double b2 = beta * beta, ir2 = ir * ir;
   const double om = 1.0 - kCN;
-  // u+, u-
-  {
-    double2 D1p = {0, 0}, D2p = {0, 0}, D1m = {0, 0}, D2m = {0, 0};
+  // L is real, so L(X+-) = L(X_r) +- i L(X_theta): one stencil per primitive field
+  double2 Sx[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
 #pragma unroll
-    for (int t = 0; t < kStencil; ++t) {
-      const long long o = (long long)(st + t) * s.nmode + mode;
-      const double2 xr = X[o], xt = X[s.S + o];
-      const double2 xp = {xr.x - xt.y, xr.y + xt.x}, xm = {xr.x + xt.y, xr.y - xt.x};
-      D1p = D1p + d1[t] * xp;
-      D2p = D2p + d2[t] * xp;
-      D1m = D1m + d1[t] * xm;
-      D2m = D2m + d2[t] * xm;
-    }
+  for (int t = 0; t < kStencil; ++t) {
+    const long long o = (long long)(st + t) * s.nmode + mode;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < s.nf) Sx[c] = Sx[c] + lw[t] * X[c * s.S + o];
+  }
+  {
     const double2 xr = X[i], xt = X[s.S + i];
     const double2 xp = {xr.x - xt.y, xr.y + xt.x}, xm = {xr.x + xt.y, xr.y - xt.x};
+    const double2 Sp = {Sx[0].x - Sx[1].y, Sx[0].y + Sx[1].x};   // S_r + i S_theta
+    const double2 Sm = {Sx[0].x + Sx[1].y, Sx[0].y - Sx[1].x};   // S_r - i S_theta
     const double2 nr = N[i], nt = N[s.S + i];
     const double2 np = {nr.x - nt.y, nr.y + nt.x}, nm = {nr.x + nt.y, nr.y - nt.x};
     const double qp = (double)(m + 1) * (m + 1), qm = (double)(m - 1) * (m - 1);
-    const double2 Lp = D2p + ir * D1p - (qp * ir2 + b2) * xp;
-    const double2 Lm = D2m + ir * D1m - (qm * ir2 + b2) * xm;
+    const double2 Lp = Sp - (qp * ir2 + b2) * xp;
+    const double2 Lm = Sm - (qm * ir2 + b2) * xm;
     Yb[i] = idt * xp + om * Lp + om * np;
     Yb[s.S + i] = idt * xm + om * Lm + om * nm;
   }
-  for (int c = 2; c < s.nf; ++c) {
-    double2 D1x = {0, 0}, D2x = {0, 0};
 #pragma unroll
-    for (int t = 0; t < kStencil; ++t) {
-      const double2 x = X[c * s.S + (long long)(st + t) * s.nmode + mode];
-      D1x = D1x + d1[t] * x;
-      D2x = D2x + d2[t] * x;
-    }
+  for (int c = 2; c < 4; ++c) {
+    if (c >= s.nf) break;
     const double2 x = X[c * s.S + i];
     const double kap = (c == 3) ? p.kappaT : 1.0;
-    const double2 L = kap * (D2x + ir * D1x - ((double)m * m * ir2 + b2) * x);
+    const double2 L = kap * (Sx[c] - ((double)m * m * ir2 + b2) * x);
     Yb[c * s.S + i] = idt * x + om * L + om * N[c * s.S + i];
   }
 }
@@ -331,17 +325,20 @@ __global__ void k_prhs(const double2 *__restrict__ Yb, const double2 *__restrict
     const int m = mode / s.NK, kk = mode % s.NK;
     const double beta = p.alpha * kval(kk, s.K, s.NK);
     const int st = p.rad.s0[j];
+    const double *dw = p.rad.Dw + j * kStencil;   // (1/r_j) D1 r_s
     double2 acc = {0.0, 0.0};
 #pragma unroll
     for (int t = 0; t < kStencil; ++t) {
       const long long ii = (long long)(st + t) * s.nmode + mode;
-      const double2 rr = 0.5 * (rhs_pm(Yb, N, s.S, ii, 0) + rhs_pm(Yb, N, s.S, ii, 1));
-      acc = acc + (p.rad.D1[j * kStencil + t] * p.rad.r[st + t]) * rr;
+      // R_r = (R+ + R-)/2 = (Y+ + Y-)/2 + c N_r
+      const double2 yp = Yb[ii], ym = Yb[s.S + ii], nr = N[ii];
+      const double2 rr = {0.5 * (yp.x + ym.x) + kCN * nr.x, 0.5 * (yp.y + ym.y) + kCN * nr.y};
+      acc = acc + dw[t] * rr;
     }
     const double2 rt = div_2i(rhs_pm(Yb, N, s.S, i, 0) - rhs_pm(Yb, N, s.S, i, 1));
     const double2 rz = rhs_pm(Yb, N, s.S, i, 2);
     const double ir = p.rad.inv_r[j];
-    b = ir * acc + (m * ir) * mul_i(rt) + beta * mul_i(rz);
+    b = acc + (m * ir) * mul_i(rt) + beta * mul_i(rz);
   }
   Ps[i] = b.x;
   Ps[s.S + i] = b.y;
@@ -921,7 +918,7 @@ __global__ void k_stT_prhs(const double *__restrict__ Ps, double2 *__restrict__ 
   for (int j = jlo; j <= jhi; ++j) {
     const int t = sn - p.rad.s0[j];
     if (t < 0 || t >= kStencil) continue;
-    const double w = p.rad.inv_r[j] * p.rad.D1[j * kStencil + t] * p.rad.r[sn];
+    const double w = p.rad.Dw[j * kStencil + t];
     const long long q = (long long)j * s.nmode + mode;
     rr.x += w * Ps[q];
     rr.y += w * Ps[S + q];
@@ -988,7 +985,7 @@ __global__ void k_rhsT(const double2 *__restrict__ Yb, double2 *__restrict__ Xb,
   for (int j = jlo; j <= jhi; ++j) {
     const int t = sn - p.rad.s0[j];
     if (t < 0 || t >= kStencil) continue;
-    const double w = p.rad.D2[j * kStencil + t] + p.rad.D1[j * kStencil + t] * p.rad.inv_r[j];
+    const double w = p.rad.Lw[j * kStencil + t];
     const long long q = (long long)j * s.nmode + mode;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {

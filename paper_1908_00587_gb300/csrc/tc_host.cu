@@ -308,6 +308,8 @@ void allocate(tc_ctx *c) {
   c->d_inv_r = dalloc<double>(c, s.Nr);
   c->d_D1 = dalloc<double>(c, (size_t)s.Nr * kStencil);
   c->d_D2 = dalloc<double>(c, (size_t)s.Nr * kStencil);
+  c->d_Lw = dalloc<double>(c, (size_t)s.Nr * kStencil);
+  c->d_Dw = dalloc<double>(c, (size_t)s.Nr * kStencil);
   c->d_dr = dalloc<double>(c, s.Nr);
   c->d_wr = dalloc<double>(c, s.Nr);
   c->d_s0 = dalloc<int>(c, s.Nr);
@@ -360,7 +362,16 @@ void upload_tables(tc_ctx *c) {
                 cudaMemcpyHostToDevice));
   DevScalars sc{};
   ck(cudaMemcpy(c->scal, &sc, sizeof(sc), cudaMemcpyHostToDevice));
-  Radial rad{c->d_r, c->d_inv_r, c->d_D1, c->d_D2, c->d_dr, c->d_wr, c->d_s0};
+  std::vector<double> Lw((size_t)s.Nr * kStencil), Dw((size_t)s.Nr * kStencil);
+  for (int j = 0; j < s.Nr; ++j)
+    for (int t = 0; t < kStencil; ++t) {
+      const size_t q = (size_t)j * kStencil + t;
+      Lw[q] = c->D2[q] + c->D1[q] * inv_r[j];
+      Dw[q] = inv_r[j] * (c->D1[q] * c->r[c->s0[j] + t]);
+    }
+  ck(cudaMemcpy(c->d_Lw, Lw.data(), Lw.size() * sizeof(double), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(c->d_Dw, Dw.data(), Dw.size() * sizeof(double), cudaMemcpyHostToDevice));
+  Radial rad{c->d_r, c->d_inv_r, c->d_D1, c->d_D2, c->d_dr, c->d_wr, c->d_s0, c->d_Lw, c->d_Dw};
   NLParams &p = c->nl;
   p.sz = s;
   p.rad = rad;

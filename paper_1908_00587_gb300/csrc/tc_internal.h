@@ -42,6 +42,8 @@ struct Sizes {
 struct Radial {
   const double *r, *inv_r, *D1, *D2, *dr_min, *wr;  // wr = quadrature w_j r_j
   const int *s0;                                     // stencil start per node
+  const double *Lw;   // [Nr][9] D2 + D1/r_j: the radial part of L in one stencil
+  const double *Dw;   // [Nr][9] (1/r_j) D1 r_s: the radial part of div
 };
 
 // Scalars shared between kernels on the device.
@@ -129,6 +131,7 @@ struct tc_ctx {
   size_t device_bytes = 0;
   double2 *X, *Xp, *N0, *N1, *Yb, *U0, *P, *V, *W, *alpha_buf, *base_dev;
   double *Ps;   // particular pressure, split planes [2][S]
+  double *d_Lw, *d_Dw;
   double *d_r, *d_inv_r, *d_D1, *d_D2, *d_dr, *d_wr;
   int *d_s0;
   double2 *d_twz, *d_twt;
