@@ -410,7 +410,13 @@ __global__ void k_hrhs(const double2 *__restrict__ Yb, const double2 *__restrict
 // DevScalars::timeout, drains its own copies (bounded again) and returns.
 
 constexpr long long kWaitNs = 1000000000LL;   // 1 s
-constexpr int kSweepStageDoubles = kSweepOps * kSweepRows * (kBand + 1);
+// One operator's chunk in the ring: kSweepRows rows of up to kBand + 1
+// doubles plus 2 doubles of padding, so the 8 operators a warp reads sit in
+// distinct shared-memory banks (unpadded, their blocks are a multiple of
+// 128 bytes apart and every row load is an 8-way bank conflict).  The pad
+// keeps each block 16-byte aligned for the bulk copies.
+constexpr int kSweepOpDoubles = kSweepRows * (kBand + 1) + 2;
+constexpr int kSweepStageDoubles = kSweepOps * kSweepOpDoubles;
 constexpr size_t kSweepSmem = sizeof(double) * kSweepStages * kSweepStageDoubles;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -470,8 +476,91 @@ __device__ __forceinline__ void arm_chunk(unsigned bar, double *dst, const doubl
     const double *s = src + ((long long)(o0 + g) * Nrp + j0) * W;
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        :: "r"(smem_u32(dst + g * kSweepRows * W)), "l"(s), "r"(bytes), "r"(bar) : "memory");
+        :: "r"(smem_u32(dst + g * kSweepOpDoubles)), "l"(s), "r"(bytes), "r"(bar) : "memory");
   }
+}
+
+// Envelope of the factors.  Row j of every radial operator is a 9-point
+// stencil starting at column clamp(j - 4, 0, Nr - 9) (or a boundary row of the
+// same reach), so rows j < Nr - 4 reach at most 4 columns below the diagonal
+// and columns c > 8 at most 4 rows above it.  LU without pivoting keeps that
+// envelope: L rows j < Nr - 4 and U rows j >= 4 hold exact zeros in their 4
+// outermost entries.  The sweeps skip those terms there (subtracting an exact
+// zero changes nothing) and take the full 8 only in the boundary rows.
+constexpr int kNarrowFrom = kBand / 2;   // 4
+
+// Forward substitution row: b - sum_e L(j, j-8+e) w_e, w_7 the newest x.
+template <bool NARROW>
+__device__ __forceinline__ double l_row_value(const double *row, const double (&w)[kBand],
+                                              double b) {
+  double far = b, near = 0.0;
+  if (!NARROW) {
+#pragma unroll
+    for (int e = 0; e < kNarrowFrom; ++e) far -= row[e] * w[e];
+  }
+#pragma unroll
+  for (int e = kNarrowFrom; e < kBand - 2; ++e) far -= row[e] * w[e];
+  near -= row[kBand - 2] * w[kBand - 2];
+  far += near;
+  far -= row[kBand - 1] * w[kBand - 1];
+  return far;
+}
+
+template <bool NARROW>
+__device__ __forceinline__ double l_row(const double *row, double (&w)[kBand], double b) {
+  const double v = l_row_value<NARROW>(row, w, b);
+#pragma unroll
+  for (int e = 0; e < kBand - 1; ++e) w[e] = w[e + 1];
+  w[kBand - 1] = v;
+  return v;
+}
+
+// Backward substitution row: (b - sum_f U(j, j+f) w_{f-1}) / U(j, j), w_0 the newest x.
+template <bool NARROW>
+__device__ __forceinline__ double u_row(const double *row, double (&w)[kBand], double b) {
+  double far = b, near = 0.0;
+  if (!NARROW) {
+#pragma unroll
+    for (int f = kBand; f > kNarrowFrom; --f) far -= row[f] * w[f - 1];
+  }
+#pragma unroll
+  for (int f = kNarrowFrom; f >= 3; --f) far -= row[f] * w[f - 1];
+  near -= row[2] * w[1];
+  far += near;
+  far -= row[1] * w[0];
+  far *= row[0];
+#pragma unroll
+  for (int f = kBand - 1; f > 0; --f) w[f] = w[f - 1];
+  w[0] = far;
+  return far;
+}
+
+// U^T forward row (column-oriented): y = (b - pending_0) / U(i, i), then the
+// pending sums of rows i+1..i+8 take U(i, i+f) y.
+template <bool NARROW>
+__device__ __forceinline__ double ut_row(const double *row, double (&w)[kBand], double b) {
+  const double y = (b - w[0]) * row[0];
+  constexpr int kn = NARROW ? kNarrowFrom : kBand - 1;
+#pragma unroll
+  for (int k = 0; k < kn; ++k) w[k] = w[k + 1] + row[k + 1] * y;
+#pragma unroll
+  for (int k = kn; k < kBand - 1; ++k) w[k] = w[k + 1];
+  w[kBand - 1] = NARROW ? 0.0 : row[kBand] * y;
+  return y;
+}
+
+// L^T backward row: x = b - pending_0, then the pending sums of rows
+// j-1..j-8 take L(j, j-1-k) x.
+template <bool NARROW>
+__device__ __forceinline__ double lt_row(const double *row, double (&w)[kBand], double b) {
+  const double xj = b - w[0];
+  constexpr int kn = NARROW ? kNarrowFrom : kBand - 1;
+#pragma unroll
+  for (int k = 0; k < kn; ++k) w[k] = w[k + 1] + row[kBand - 1 - k] * xj;
+#pragma unroll
+  for (int k = kn; k < kBand - 1; ++k) w[k] = w[k + 1];
+  w[kBand - 1] = NARROW ? 0.0 : row[0] * xj;
+  return xj;
 }
 
 // TRANS = false: solve A x = b with A = L U (L then U).  TRANS = true: solve
@@ -561,17 +650,15 @@ k_sweep(SweepArgs a, DevScalars *sc) {
     if (active && TRANS) {
       if (fwd) {
         // U^T y = b: y_i = (b_i - pending_i) / u_ii, then pending_{i+f} += U(i, i+f) y_i
-        const double *Uc = ring[s] + g * kSweepRows * (kBand + 1);
+        const double *Uc = ring[s] + g * kSweepOpDoubles;
 #pragma unroll
         for (int r = 0; r < kSweepRows; ++r) {
           const int j = j0 + r;
-          if (j < a.Nr) {
-            const double *row = Uc + r * (kBand + 1);
-            const double y = (xa[r] - w[0]) * row[0];
-#pragma unroll
-            for (int k = 0; k < kBand - 1; ++k) w[k] = w[k + 1] + row[k + 1] * y;
-            w[kBand - 1] = row[kBand] * y;
-            x[j * xs] = y;
+          const double *row = Uc + r * (kBand + 1);
+          if (j >= kNarrowFrom && j < a.Nr) {
+            x[j * xs] = ut_row<true>(row, w, xa[r]);
+          } else if (j < a.Nr) {
+            x[j * xs] = ut_row<false>(row, w, xa[r]);
           }
         }
         if (c + 1 < nch) {
@@ -591,17 +678,16 @@ k_sweep(SweepArgs a, DevScalars *sc) {
         }
       } else {
         // L^T x = y: x_j = y_j - pending_j, then pending_{j-8+e} += L(j, j-8+e) x_j
-        const double *Lc = ring[s] + g * kSweepRows * kBand;
+        const double *Lc = ring[s] + g * kSweepOpDoubles;
+        const int narrow_below = a.Nr - kNarrowFrom;
 #pragma unroll
         for (int r = kSweepRows - 1; r >= 0; --r) {
           const int j = j0 + r;
-          if (j < a.Nr) {
-            const double *row = Lc + r * kBand;
-            const double xj = xa[r] - w[0];
-#pragma unroll
-            for (int k = 0; k < kBand - 1; ++k) w[k] = w[k + 1] + row[kBand - 1 - k] * xj;
-            w[kBand - 1] = row[0] * xj;
-            x[j * xs] = xj;
+          const double *row = Lc + r * kBand;
+          if (j < narrow_below) {
+            x[j * xs] = lt_row<true>(row, w, xa[r]);
+          } else if (j < a.Nr) {
+            x[j * xs] = lt_row<false>(row, w, xa[r]);
           }
         }
         if (c > 0) {
@@ -611,22 +697,16 @@ k_sweep(SweepArgs a, DevScalars *sc) {
       }
     } else if (active) {
       if (fwd) {
-        const double *Lc = ring[s] + g * kSweepRows * kBand;
+        const double *Lc = ring[s] + g * kSweepOpDoubles;
+        const int narrow_below = a.Nr - kNarrowFrom;
 #pragma unroll
         for (int r = 0; r < kSweepRows; ++r) {
           const int j = j0 + r;
-          if (j < a.Nr) {
-            const double *row = Lc + r * kBand;
-            double far = xa[r], near = 0.0;
-#pragma unroll
-            for (int e = 0; e < kBand - 2; ++e) far -= row[e] * w[e];
-            near -= row[kBand - 2] * w[kBand - 2];
-            far += near;
-            far -= row[kBand - 1] * w[kBand - 1];
-#pragma unroll
-            for (int e = 0; e < kBand - 1; ++e) w[e] = w[e + 1];
-            w[kBand - 1] = far;
-            x[j * xs] = far;
+          const double *row = Lc + r * kBand;
+          if (j < narrow_below) {
+            x[j * xs] = l_row<true>(row, w, xa[r]);
+          } else if (j < a.Nr) {
+            x[j * xs] = l_row<false>(row, w, xa[r]);
           }
         }
         // prefetch the next forward chunk, or the last chunk for the backward sweep
@@ -646,23 +726,15 @@ k_sweep(SweepArgs a, DevScalars *sc) {
           }
         }
       } else {
-        const double *Uc = ring[s] + g * kSweepRows * (kBand + 1);
+        const double *Uc = ring[s] + g * kSweepOpDoubles;
 #pragma unroll
         for (int r = kSweepRows - 1; r >= 0; --r) {
           const int j = j0 + r;
-          if (j < a.Nr) {
-            const double *row = Uc + r * (kBand + 1);
-            double far = xa[r], near = 0.0;
-#pragma unroll
-            for (int f = kBand; f >= 3; --f) far -= row[f] * w[f - 1];
-            near -= row[2] * w[1];
-            far += near;
-            far -= row[1] * w[0];
-            far *= row[0];
-#pragma unroll
-            for (int f = kBand - 1; f > 0; --f) w[f] = w[f - 1];
-            w[0] = far;
-            x[j * xs] = far;
+          const double *row = Uc + r * (kBand + 1);
+          if (j >= kNarrowFrom && j < a.Nr) {
+            x[j * xs] = u_row<true>(row, w, xa[r]);
+          } else if (j < a.Nr) {
+            x[j * xs] = u_row<false>(row, w, xa[r]);
           }
         }
         if (c > 0) {
