@@ -67,16 +67,11 @@ __device__ __forceinline__ void dft4(V *v) {
   v[3] = csub(t1, t3);
 }
 
+// Second half of the length-8 DFT: a_q = v_q + v_(q+4), b_q = v_q - v_(q+4) given.
 template <int S, typename V>
-__device__ __forceinline__ void dft8(V *v) {
+__device__ __forceinline__ void dft8_tail(V *a, V *b, V *v) {
   using T = decltype(v[0].x);
   const T h = (T)0.70710678118654752440;  // sqrt(2)/2
-  V a[4], b[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    a[q] = cadd(v[q], v[q + 4]);
-    b[q] = csub(v[q], v[q + 4]);
-  }
   // b_q *= exp(S 2 pi i q / 8)
   {
     V x = b[1];
@@ -92,6 +87,34 @@ __device__ __forceinline__ void dft8(V *v) {
     v[2 * p] = a[p];
     v[2 * p + 1] = b[p];
   }
+}
+
+template <int S, typename V>
+__device__ __forceinline__ void dft8(V *v) {
+  V a[4], b[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    a[q] = cadd(v[q], v[q + 4]);
+    b[q] = csub(v[q], v[q + 4]);
+  }
+  dft8_tail<S>(a, b, v);
+}
+
+// Length-8 DFT with v_3 = v_4 = 0 (not read).  This is the first pass of a
+// transform whose input vanishes on the middle band [3N/8, 5N/8), which a
+// dealiased spectrum packed as (0..B, N-B..N-1) does whenever B < 3N/8.
+template <int S, typename V>
+__device__ __forceinline__ void dft8_zmid(V *v) {
+  V a[4], b[4];
+  a[0] = v[0];
+  b[0] = v[0];
+  a[1] = cadd(v[1], v[5]);
+  b[1] = csub(v[1], v[5]);
+  a[2] = cadd(v[2], v[6]);
+  b[2] = csub(v[2], v[6]);
+  a[3] = v[7];
+  b[3] = V{-v[7].x, -v[7].y};
+  dft8_tail<S>(a, b, v);
 }
 
 template <int S, typename V>
@@ -143,9 +166,16 @@ __device__ __forceinline__ void dftR(V *v) {
 __host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 3); }
 __host__ __device__ __forceinline__ int padlen(int n) { return n + (n >> 3) + 1; }
 
+// True when a spectrum packed as entries 0..B and N-B..N-1 of a length-N
+// transform (zeros elsewhere) may use the zero-middle first pass.
+__host__ __device__ __forceinline__ bool zmid_ok(const FFTPlan &pl, int B) {
+  return pl.npass > 0 && pl.radix[0] == 8 && 8 * B < 3 * pl.n;
+}
+
 // One Stockham pass over `batch` transforms stored `bstride` apart.
 // tw[t] = exp(-2 pi i t / N).
-template <int R, int S, typename V>
+// ZMID (radix 8, first pass only): inputs q = 3, 4 are known zeros.
+template <int R, int S, bool ZMID, typename V>
 __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__restrict__ dst,
                                               int N, int Ns, int batch, int bstride,
                                               const V *__restrict__ tw) {
@@ -160,7 +190,15 @@ __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__re
     const int k = j % Ns;
     V v[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = s[spad(j + q * nb)];
+    for (int q = 0; q < R; ++q)
+      if (!ZMID || (q != 3 && q != 4)) v[q] = s[spad(j + q * nb)];
+    if (ZMID) {
+      if constexpr (R == 8) dft8_zmid<S>(v);
+      const int base = j * R;   // Ns = 1
+#pragma unroll
+      for (int p = 0; p < R; ++p) d[spad(base + p)] = v[p];
+      continue;
+    }
     if (Ns > 1) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
@@ -177,19 +215,25 @@ __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__re
 
 // Full transform of `batch` sequences held in buffer a (b is scratch of the
 // same size).  Returns the buffer holding the result.  All threads of the CTA
-// must call it; it ends with a __syncthreads().
+// must call it; it ends with a __syncthreads().  zmid: the caller guarantees
+// that every input vanishes on [3N/8, 5N/8) and the plan starts with radix 8
+// (see zmid_ok); the first pass then skips those inputs.
 template <int S, typename V>
 __device__ V *fft_batch(V *a, V *b, const FFTPlan &pl, int batch, int bstride,
-                        const V *__restrict__ tw) {
+                        const V *__restrict__ tw, bool zmid = false) {
   int Ns = 1;
   for (int p = 0; p < pl.npass; ++p) {
     const int R = pl.radix[p];
-    switch (R) {
-      case 8: stockham_pass<8, S>(a, b, pl.n, Ns, batch, bstride, tw); break;
-      case 4: stockham_pass<4, S>(a, b, pl.n, Ns, batch, bstride, tw); break;
-      case 2: stockham_pass<2, S>(a, b, pl.n, Ns, batch, bstride, tw); break;
-      case 3: stockham_pass<3, S>(a, b, pl.n, Ns, batch, bstride, tw); break;
-      default: stockham_pass<5, S>(a, b, pl.n, Ns, batch, bstride, tw); break;
+    if (p == 0 && zmid) {
+      stockham_pass<8, S, true>(a, b, pl.n, Ns, batch, bstride, tw);
+    } else {
+      switch (R) {
+        case 8: stockham_pass<8, S, false>(a, b, pl.n, Ns, batch, bstride, tw); break;
+        case 4: stockham_pass<4, S, false>(a, b, pl.n, Ns, batch, bstride, tw); break;
+        case 2: stockham_pass<2, S, false>(a, b, pl.n, Ns, batch, bstride, tw); break;
+        case 3: stockham_pass<3, S, false>(a, b, pl.n, Ns, batch, bstride, tw); break;
+        default: stockham_pass<5, S, false>(a, b, pl.n, Ns, batch, bstride, tw); break;
+      }
     }
     __syncthreads();
     V *t = a;

@@ -166,7 +166,7 @@ __global__ void k_zinv(const double2 *__restrict__ X, V2<T> *__restrict__ Vout, 
     A[(3 * mi + 2) * Np + spad(pos)] = V2<T>{(T)(-beta * val.y), (T)(beta * val.x)};
   }
   __syncthreads();
-  V2<T> *res = fft_batch<+1>(A, B, p.pz, 3 * nm, Np, tw);
+  V2<T> *res = fft_batch<+1>(A, B, p.pz, 3 * nm, Np, tw, zmid_ok(p.pz, s.K));
   for (int t = threadIdx.x; t < 3 * nm * Nz; t += blockDim.x) {
     const int mi = t % nm;
     const int rest = t / nm;
@@ -225,11 +225,14 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     }
   }
   __syncthreads();
-  V2<T> *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Ntp, tw);
+  V2<T> *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Ntp, tw, zmid_ok(p.pt, s.M));
   V2<T> *out = (ph == A) ? B : A;
   const double rr = p.rad.r[r];
   const T inv_r = (T)p.rad.inv_r[r];
-  double rate = 0.0, nu = 0.0, nT = 0.0;
+  // CFL: running maxima of |u_r|, |u_theta|, |u_z|; the divisions by the
+  // spacings come once per thread after the loop (division by a positive
+  // constant is monotone, so the max of the quotients is unchanged)
+  double mr = 0.0, mt = 0.0, mz = 0.0, nu = 0.0, nT = 0.0;
   for (int t = threadIdx.x; t < nl * Nt; t += blockDim.x) {
     const int j = t % Nt;
     const int li = t / Nt;
@@ -239,7 +242,9 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     const V2<T> z0 = b[4 * Ntp], z1 = b[5 * Ntp];   // (uz, uz_t), (uz_r, uz_z)
     const T ur = r0.x, ut = t0.x, uz = z0.x;
     // full velocity for the CFL bound (mixed: the transforms carry u' only)
-    const double Ut = p.mixed ? p.prof[r * 8 + 0] : 0.0, Uz = p.mixed ? p.prof[r * 8 + 1] : 0.0;
+    // (only the FP32 instantiation runs the mixed form)
+    const bool mixed = sizeof(T) == 4 && p.mixed;
+    const double Ut = mixed ? p.prof[r * 8 + 0] : 0.0, Uz = mixed ? p.prof[r * 8 + 1] : 0.0;
     if (mode == 1) {
       nu = fmax(nu, sqrt((double)ur * ur + (double)ut * ut + (double)uz * uz));
       if (s.nf == 4) nT = fmax(nT, fabs((double)b[6 * Ntp].x));
@@ -262,9 +267,9 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     o[0] = V2<T>{Nr_, Nt_};
     o[Ntp] = V2<T>{Nz_, NT_};
     if (rate_bits) {
-      const double a = fmax(fabs((double)ur) / p.rad.dr_min[r],
-                            fmax(fabs((double)ut + Ut) / (rr * p.dth), fabs((double)uz + Uz) / p.dz));
-      rate = fmax(rate, a);
+      mr = fmax(mr, fabs((double)ur));
+      mt = fmax(mt, fabs(mixed ? (double)ut + Ut : (double)ut));
+      mz = fmax(mz, fabs(mixed ? (double)uz + Uz : (double)uz));
     }
   }
   if (mode == 1) {
@@ -279,6 +284,7 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     return;
   }
   if (rate_bits) {
+    double rate = fmax(mr / p.rad.dr_min[r], fmax(mt / (rr * p.dth), mz / p.dz));
     for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
     if ((threadIdx.x & 31) == 0) atomic_max_pos(rate_bits, rate);
   }
