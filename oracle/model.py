@@ -9,8 +9,20 @@ Equations (viscous units: length d = r_o - r_i, time d^2/nu, velocity nu/d):
 with u_theta(r_i) = Re_i, u_theta(r_o) = Re_o, T(r_i) = +1/2, T(r_o) = -1/2
 (Sec. 2.1: differentially heated, independently rotating cylinders; a negative
 radial temperature gradient and gravity along z, Boussinesq-like buoyancy).
-Temperature is carried only when Ra != 0.  Centrifugal buoyancy is not
-included.
+Temperature is carried only when Ra != 0.
+
+Options of the scheme (all off by default):
+* ``n_corr`` corrector passes (default 1), each c N(X_prev) + (1-c) N^n with
+  the same explicit part; the last difference max |X_corr - X_prev| over the
+  stored coefficients is kept as ``last_corr_diff``;
+* ``flux_constraint``: a uniform axial pressure gradient G in the (0,0) u_z
+  equation, solved with the stage so that the axial volume flux
+  int u_z r dr (Clenshaw-Curtis quadrature) is zero after every stage;
+* ``eps_c`` (centrifugal buoyancy, Sec. 2.1 cites a Boussinesq-like
+  approximation for rotating flows and leaves other buoyancy set-ups open):
+  the advective acceleration of the momentum equation is weighted by the
+  density factor (1 - eps_c T), so N_u = -(1 - eps_c T)(u.grad u + curvature
+  terms) + Gr T e_z.  The temperature equation is unchanged.
 
 Readings of the scheme (the paper defers its details to other papers):
 * nonlinear term in convective form with the cylindrical curvature terms,
@@ -67,7 +79,14 @@ class _Factored:
 class Model:
     """One run: grid, transforms, operators, base state, step, diagnostics."""
 
-    def __init__(self, wl, transform: str = "naive"):
+    def __init__(self, wl, transform: str = "naive", n_corr: int = 1,
+                 flux_constraint: bool = False, eps_c: float = 0.0):
+        if n_corr < 1:
+            raise ValueError("n_corr >= 1")
+        self.n_corr = int(n_corr)
+        self.flux_constraint = bool(flux_constraint)
+        self.eps_c = float(eps_c)
+        self.last_corr_diff = 0.0
         self.wl = wl
         self.g = Grid(wl.Nr, wl.eta)
         self.sp = Spectral(wl.Ntheta, wl.Nz, wl.Lz, transform)
@@ -75,6 +94,8 @@ class Model:
         self.Gr = wl.Ra / wl.Pr if self.has_T else 0.0
         self.kappa_T = 1.0 / wl.Pr
         self.nf = 4 if self.has_T else 3
+        if self.eps_c != 0.0 and not self.has_T:
+            raise ValueError("centrifugal buoyancy needs the temperature (Ra != 0)")
         self.M, self.K = self.sp.M, self.sp.K
         self.NK = 2 * self.K + 1
         mm, kk = np.meshgrid(self.sp.m, self.sp.kk, indexing="ij")
@@ -239,6 +260,13 @@ class Model:
         Rz00 = self.cols(R[2])[0][None, :].copy()
         Rz00[:, 0] = Rz00[:, -1] = 0.0
         out[2, 0] = ops["H00_z"].solve(Rz00)[0]
+        if self.flux_constraint:
+            # uniform forcing G (interior rows) chosen so that the flux is zero
+            e = np.ones((1, Nr), dtype=complex)
+            e[:, 0] = e[:, -1] = 0.0
+            ug = ops["H00_z"].solve(e)[0]
+            G = -self.axial_flux(out[2, 0]) / self.axial_flux(ug)
+            out[2, 0] = out[2, 0] + G * ug
         if self.has_T:
             RT = self.cols(R[3]).copy()
             RT[:, 0] = RT[:, -1] = 0.0
@@ -286,6 +314,9 @@ class Model:
         Nph = [-(adv("ur") - ut * ut / r),
                -(adv("ut") + ur * ut / r),
                -adv("uz")]
+        if self.eps_c != 0.0:
+            rho = 1.0 - self.eps_c * f["T"]
+            Nph = [rho * a for a in Nph]
         if self.has_T:
             Nph[2] = Nph[2] + self.Gr * f["T"]
             Nph.append(-adv("T"))
@@ -339,10 +370,14 @@ class Model:
         LX = self.explicit_linear(Xpm)
         base = [Xpm[i] / dt + (1.0 - CN) * LX[i] + (1.0 - CN) * Npm0[i]
                 for i in range(self.nf)]
-        Xp, _ = self.stage_solve([base[i] + CN * Npm0[i] for i in range(self.nf)], dt)
-        N1, _ = self.nonlinear(Xp)
-        Npm1 = self.to_pm(N1)
-        Xc, p = self.stage_solve([base[i] + CN * Npm1[i] for i in range(self.nf)], dt)
+        Xc, _ = self.stage_solve([base[i] + CN * Npm0[i] for i in range(self.nf)], dt)
+        for _ in range(self.n_corr):
+            Xprev = Xc
+            N1, _ = self.nonlinear(Xprev)
+            Npm1 = self.to_pm(N1)
+            Xc, p = self.stage_solve([base[i] + CN * Npm1[i] for i in range(self.nf)], dt)
+        self.last_corr_diff = float(max(np.max(np.abs((Xc - Xprev).real)),
+                                        np.max(np.abs((Xc - Xprev).imag))))
         return Xc, p, dt, rate
 
     def run(self, X, nsteps: int, dt: float):
@@ -378,8 +413,17 @@ class Model:
         if self.has_T:
             T = dsolve(0.0, np.zeros(Nr), 0.5, -0.5)
             X[3, :, 0, 0] = T
-            X[2, :, 0, 0] = dsolve(0.0, -self.Gr * T, 0.0, 0.0)
+            uz = dsolve(0.0, -self.Gr * T, 0.0, 0.0)
+            if self.flux_constraint:
+                # L(0) u_z = -Gr T - G with G such that the axial flux is zero
+                ones = dsolve(0.0, -np.ones(Nr), 0.0, 0.0)
+                uz = uz - (self.axial_flux(uz) / self.axial_flux(ones)) * ones
+            X[2, :, 0, 0] = uz
         return X
+
+    def axial_flux(self, uz_profile) -> float:
+        """int u_z r dr over the gap (Clenshaw-Curtis weights), real part."""
+        return float(np.sum(self.g.w * self.g.r * np.real(uz_profile)))
 
     # -------------------------------------------------------- initial states
     def place(self, raw: np.ndarray, profile: np.ndarray) -> np.ndarray:
