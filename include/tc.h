@@ -65,10 +65,14 @@ typedef enum {
  *   div_max    max |div u| over all stored coefficients
  *   div_rms    (int |div u|^2 dV / V)^(1/2)
  *   cfl        CFL number of the last step's start-of-step state times dt
+ *   corr_diff  last step: max |X_corr - X_prev| over the stored coefficients
+ *              (real and imaginary parts) of its last two iterates (the last
+ *              corrector and the one before it, or the predictor)
  */
 typedef struct {
   double t, dt, E, E_pert, torque_i, torque_o, P_wall, eps, buoy_work;
   double Nu_i, Nu_o, div_max, div_rms, cfl;
+  double corr_diff;
 } tc_diag;
 
 /* Sizes derived by tc_create. */
@@ -119,6 +123,23 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               TC_ERR_UNSUPPORTED if the shared memory would not fit).  The
  *               tiles change only which CTA computes a transform, not the
  *               arithmetic, so results are identical for every choice.
+ *   "n_corr"    corrector passes per step, 1..16 (default 1).  Each pass
+ *               solves the stage with c N(X_prev) + (1-c) N^n and the same
+ *               explicit part; diagnostics report the last difference.
+ *   "flux_constraint"  1: a uniform axial pressure gradient in the (0,0)
+ *               u_z equation, solved with every stage, keeps the axial
+ *               volume flux int u_z r dr at zero (default 0).  With
+ *               temperature it also gives the basic state zero axial flux;
+ *               set it before tc_init_perturbation.
+ *   "eps_centrifugal"  centrifugal buoyancy coefficient eps (default 0): the
+ *               momentum advection u.grad u (with its curvature terms) is
+ *               weighted by the density factor 1 - eps T.  Needs the
+ *               temperature (Ra != 0) and precision 0; TC_ERR_UNSUPPORTED
+ *               otherwise.
+ *               The adjoint entry points cover the default scheme only: they
+ *               return TC_ERR_UNSUPPORTED when n_corr != 1, flux_constraint is
+ *               on (tc_stage_solve_adjoint, tc_adjoint_step) or eps != 0
+ *               (tc_nonlinear_adjoint, tc_adjoint_step).
  *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
  *               never start their shared-memory copies, so each of their
  *               bounded waits runs out (about 1 s) and tc_step returns

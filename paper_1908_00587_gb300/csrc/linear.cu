@@ -157,6 +157,12 @@ __global__ void k_factor_helm(LinParams p, const DevScalars *sc) {
     const int q = t / K1, ak = t % K1;
     const double beta = p.alpha * ak;
     band_factor(p.rad, p.sz.Nr, 1, (double)q * q, beta * beta, idt, kCN, p.LH, p.UH, p.Nrp, t);
+    if (t == 0 && p.flux_ug) {
+      // axial-flux constraint: response of the (0,0) u_z operator to a unit
+      // uniform forcing, zero at the walls
+      for (int j = 0; j < p.sz.Nr; ++j) p.flux_ug[j] = (j == 0 || j == p.sz.Nr - 1) ? 0.0 : 1.0;
+      band_solve(p.LH, p.UH, p.Nrp, 0, p.sz.Nr, p.flux_ug, 1);
+    }
   } else {
     const int o = t - p.nopH;
     const int m = o / K1, ak = o % K1;
@@ -230,6 +236,7 @@ __global__ void k_dt_policy(DevScalars *sc, double dt_fixed, double cfl, double 
   const double rate = __longlong_as_double((long long)sc->rate_bits);
   sc->rate_last = rate;
   sc->rate_bits = 0ull;
+  sc->corr_bits = 0ull;
   double dt;
   if (dt_fixed > 0.0) {
     dt = dt_fixed;
@@ -787,54 +794,105 @@ __global__ void k_alpha(const double *__restrict__ U, double2 *__restrict__ alph
 
 __global__ void k_correct(const double *__restrict__ U, const double *__restrict__ Ps,
                           const double2 *__restrict__ alpha, double2 *__restrict__ Xout,
-                          double2 *__restrict__ Pout, LinParams p, DevScalars *sc) {
+                          double2 *__restrict__ Pout, const double2 *__restrict__ Xprev,
+                          LinParams p, DevScalars *sc) {
   const Sizes &s = p.sz;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.S) return;
-  const int j = (int)(i / s.nmode);
-  const int mode = (int)(i - (long long)j * s.nmode);
-  const long long S = s.S;
-  double2 up = {U[i], U[S + i]}, um = {U[2 * S + i], U[3 * S + i]},
-          uz = {U[4 * S + i], U[5 * S + i]};
-  double2 pr = {0.0, 0.0};
-  double2 xr, xt;
-  if (mode == 0) {
-    xr = {0.0, 0.0};   // u_r = 0; slot 0 holds u_theta
-    xt = up;
-  } else {
-    const int m = mode / s.NK, kk = mode % s.NK;
-    const int kv = kval(kk, s.K, s.NK);
-    const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
-    const double beta = p.alpha * kv;
-    const double2 a = alpha[mode], b = alpha[s.nmode + mode];
-    const long long fs = (long long)s.Nr * p.nopP;
-    const long long jo = (long long)j * p.nopP + o;
-    const double *F = p.infl;
-    pr = double2{Ps[i], Ps[S + i]};
-    pr = pr + F[0 * fs + jo] * a;
-    pr = pr + F[1 * fs + jo] * b;
-    up = up + F[2 * fs + jo] * a;
-    um = um + F[3 * fs + jo] * a;
-    up = up + F[4 * fs + jo] * b;
-    um = um + F[5 * fs + jo] * b;
-    // u_z of a homogeneous solution = -i beta zeta
-    uz = uz + (-beta * F[6 * fs + jo]) * mul_i(a);
-    uz = uz + (-beta * F[7 * fs + jo]) * mul_i(b);
-    xr = 0.5 * (up + um);
-    xt = div_2i(up - um);
+  double dmax = 0.0;   // max |Xout - Xprev| over this thread's coefficients
+  if (i < s.S) {
+    const int j = (int)(i / s.nmode);
+    const int mode = (int)(i - (long long)j * s.nmode);
+    const long long S = s.S;
+    double2 up = {U[i], U[S + i]}, um = {U[2 * S + i], U[3 * S + i]},
+            uz = {U[4 * S + i], U[5 * S + i]};
+    double2 pr = {0.0, 0.0};
+    double2 xr, xt;
+    if (mode == 0) {
+      xr = {0.0, 0.0};   // u_r = 0; slot 0 holds u_theta
+      xt = up;
+    } else {
+      const int m = mode / s.NK, kk = mode % s.NK;
+      const int kv = kval(kk, s.K, s.NK);
+      const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
+      const double beta = p.alpha * kv;
+      const double2 a = alpha[mode], b = alpha[s.nmode + mode];
+      const long long fs = (long long)s.Nr * p.nopP;
+      const long long jo = (long long)j * p.nopP + o;
+      const double *F = p.infl;
+      pr = double2{Ps[i], Ps[S + i]};
+      pr = pr + F[0 * fs + jo] * a;
+      pr = pr + F[1 * fs + jo] * b;
+      up = up + F[2 * fs + jo] * a;
+      um = um + F[3 * fs + jo] * a;
+      up = up + F[4 * fs + jo] * b;
+      um = um + F[5 * fs + jo] * b;
+      // u_z of a homogeneous solution = -i beta zeta
+      uz = uz + (-beta * F[6 * fs + jo]) * mul_i(a);
+      uz = uz + (-beta * F[7 * fs + jo]) * mul_i(b);
+      xr = 0.5 * (up + um);
+      xt = div_2i(up - um);
+    }
+    Xout[i] = xr;
+    Xout[S + i] = xt;
+    Xout[2 * S + i] = uz;
+    bool bad = !(isfinite(xr.x) && isfinite(xr.y) && isfinite(xt.x) && isfinite(xt.y) &&
+                 isfinite(uz.x) && isfinite(uz.y));
+    double2 T = {0.0, 0.0};
+    if (s.nf == 4) {
+      T = double2{U[6 * S + i], U[7 * S + i]};
+      Xout[3 * S + i] = T;
+      bad = bad || !(isfinite(T.x) && isfinite(T.y));
+    }
+    if (Pout) Pout[i] = pr;
+    if (bad) atomicOr(&sc->nonfinite, 1);
+    if (Xprev) {
+      auto dm = [&](double2 a, double2 b) {
+        dmax = fmax(dmax, fmax(fabs(a.x - b.x), fabs(a.y - b.y)));
+      };
+      dm(xr, Xprev[i]);
+      dm(xt, Xprev[S + i]);
+      dm(uz, Xprev[2 * S + i]);
+      if (s.nf == 4) dm(T, Xprev[3 * S + i]);
+    }
   }
-  Xout[i] = xr;
-  Xout[S + i] = xt;
-  Xout[2 * S + i] = uz;
-  bool bad = !(isfinite(xr.x) && isfinite(xr.y) && isfinite(xt.x) && isfinite(xt.y) &&
-               isfinite(uz.x) && isfinite(uz.y));
-  if (s.nf == 4) {
-    const double2 T = {U[6 * S + i], U[7 * S + i]};
-    Xout[3 * S + i] = T;
-    bad = bad || !(isfinite(T.x) && isfinite(T.y));
+  if (Xprev) {   // uniform over the grid: every lane of every warp gets here
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0 && dmax > 0.0)
+      atomicMax(&sc->corr_bits, (unsigned long long)__double_as_longlong(dmax));
   }
-  if (Pout) Pout[i] = pr;
-  if (bad) atomicOr(&sc->nonfinite, 1);
+}
+
+// Axial-flux constraint on the (0,0) u_z column (one CTA): the stage's u_z
+// gets G times the response ug to a unit uniform forcing (Dirichlet walls),
+// G = -Q(u_z) / Q(ug) with Q(f) = sum_j w_j r_j f_j the axial volume flux
+// (Clenshaw-Curtis weights), so the flux after the stage is zero.
+__global__ void k_flux(double2 *__restrict__ X, const double *__restrict__ ug, LinParams p) {
+  const Sizes &s = p.sz;
+  __shared__ double red[2][32];
+  double q = 0.0, qg = 0.0;
+  for (int j = threadIdx.x; j < s.Nr; j += blockDim.x) {
+    const double w = p.rad.wr[j];
+    q += w * X[2 * s.S + (long long)j * s.nmode].x;
+    qg += w * ug[j];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+    qg += __shfl_xor_sync(0xffffffffu, qg, o);
+  }
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][wid] = q;
+    red[1][wid] = qg;
+  }
+  __syncthreads();
+  double Q = 0.0, Qg = 0.0;
+  for (int k = 0; k < nw; ++k) {
+    Q += red[0][k];
+    Qg += red[1][k];
+  }
+  const double G = -Q / Qg;
+  for (int j = threadIdx.x; j < s.Nr; j += blockDim.x)
+    X[2 * s.S + (long long)j * s.nmode].x += G * ug[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -1240,7 +1298,8 @@ void launch_rhs(tc_ctx *c, const double2 *X, const double2 *N0) {
   k_rhs<<<blocks(c->sz.S, 128), 128, 0, c->stream>>>(X, N0, c->Yb, c->lin, c->scal);
 }
 
-void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout) {
+void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout,
+                  const double2 *Xprev) {
   const Sizes &s = c->sz;
   const LinParams &p = c->lin;
   double *U = reinterpret_cast<double *>(c->U0);
@@ -1275,9 +1334,15 @@ void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout) {
     LaunchScope ls(c, KALPHA);
     k_alpha<<<blocks(s.nmode, 128), 128, 0, c->stream>>>(U, c->alpha_buf, p);
   }
-  LaunchScope ls(c, KCORR);
-  k_correct<<<blocks(s.S, 128), 128, 0, c->stream>>>(U, c->Ps, c->alpha_buf, Xout, Pout, p,
-                                                      c->scal);
+  {
+    LaunchScope ls(c, KCORR);
+    k_correct<<<blocks(s.S, 128), 128, 0, c->stream>>>(U, c->Ps, c->alpha_buf, Xout, Pout,
+                                                        Xprev, p, c->scal);
+  }
+  if (c->flux) {
+    LaunchScope ls(c, KFLUX);
+    k_flux<<<1, 256, 0, c->stream>>>(Xout, c->flux_ug, p);
+  }
 }
 
 void launch_state_check(tc_ctx *c, const double2 *X) {

@@ -254,12 +254,18 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     const T adv_r = ur * r1.x + ut_r * r0.y + uz * r1.y;
     const T adv_t = ur * t1.x + ut_r * t0.y + uz * t1.y;
     const T adv_z = ur * z1.x + ut_r * z0.y + uz * z1.y;
-    const T Nr_ = -(adv_r - ut * ut_r);
-    const T Nt_ = -(adv_t + ur * ut_r);
+    T Nr_ = -(adv_r - ut * ut_r);
+    T Nt_ = -(adv_t + ur * ut_r);
     T Nz_ = -adv_z;
     T NT_ = 0;
     if (s.nf == 4) {
       const V2<T> T0 = b[6 * Ntp], T1 = b[7 * Ntp];
+      if (p.eps_c != 0.0) {   // centrifugal buoyancy (FP64 form only)
+        const T rho = (T)1 - (T)p.eps_c * T0.x;
+        Nr_ *= rho;
+        Nt_ *= rho;
+        Nz_ *= rho;
+      }
       if (!p.mixed) Nz_ += (T)p.Gr * T0.x;   // mixed: buoyancy added in FP64
       NT_ = -(ur * T1.x + ut_r * T0.y + uz * T1.y);
     }

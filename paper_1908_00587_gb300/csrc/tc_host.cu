@@ -19,7 +19,8 @@ namespace tc {
 
 const char *const kKernelNames[KNUM] = {
     "k_zinv", "k_theta", "k_zfwd", "k_dt_policy", "k_factor", "k_influence",
-    "k_rhs", "k_prhs", "k_psolve", "k_hrhs", "k_hsolve", "k_alpha", "k_correct", "k_diag", "k_check"};
+    "k_rhs", "k_prhs", "k_psolve", "k_hrhs", "k_hsolve", "k_alpha", "k_correct", "k_diag", "k_check",
+    "k_flux"};
 
 LaunchScope::LaunchScope(tc_ctx *c_, int id_) : c(c_), id(id_) {
   c->launches++;
@@ -46,14 +47,24 @@ LaunchScope::~LaunchScope() {
 // All kernels of one predictor-corrector step, enqueued on the context's
 // stream with no host synchronisation (so that a graph can capture it).
 // step_index >= 0 records the step used into dt_hist[step_index].
+// One step: predictor, then n_corr correctors on the same explicit part.
+// The iterates alternate between X and Xp so that the last one lands in X
+// (the predictor may overwrite X: everything that reads X^n -- the first
+// nonlinear evaluation, the CFL rate and the explicit part Yb -- comes first).
+// The last corrector records max |X_corr - X_prev| for tc_diagnostics.
 void enqueue_step(tc_ctx *c, double dt_fixed, int step_index) {
   launch_nonlinear(c, c->X, c->N0, &c->scal->rate_bits, 0);
   launch_dt_policy(c, dt_fixed, step_index);
   launch_refactor(c);
   launch_rhs(c, c->X, c->N0);
-  launch_stage(c, c->N0, c->Xp, c->P);
-  launch_nonlinear(c, c->Xp, c->N1, nullptr, 0);
-  launch_stage(c, c->N1, c->X, c->P);
+  double2 *cur = (c->n_corr % 2) ? c->Xp : c->X;
+  launch_stage(c, c->N0, cur, c->P);
+  for (int i = 0; i < c->n_corr; ++i) {
+    double2 *next = (cur == c->X) ? c->Xp : c->X;
+    launch_nonlinear(c, cur, c->N1, nullptr, 0);
+    launch_stage(c, c->N1, next, c->P, i + 1 == c->n_corr ? cur : nullptr);
+    cur = next;
+  }
 }
 
 FFTPlan make_plan(int n) {
@@ -283,7 +294,21 @@ void build_base(tc_ctx *c) {
     for (int j = 0; j < Nr; ++j) b[j] = -c->Gr * c->Tb_disc[j];
     b[0] = 0.0;
     b[Nr - 1] = 0.0;
-    put(2, dense_solve(dense_lap00(c, 0.0), b, Nr));
+    std::vector<double> uz = dense_solve(dense_lap00(c, 0.0), b, Nr);
+    if (c->flux) {
+      // zero axial flux: L(0) u_z = -Gr T - G, G from the response to -1
+      std::vector<double> one(Nr, -1.0);
+      one[0] = 0.0;
+      one[Nr - 1] = 0.0;
+      const std::vector<double> uc = dense_solve(dense_lap00(c, 0.0), one, Nr);
+      double q = 0.0, qc = 0.0;
+      for (int j = 0; j < Nr; ++j) {
+        q += c->w[j] * c->r[j] * uz[j];
+        qc += c->w[j] * c->r[j] * uc[j];
+      }
+      for (int j = 0; j < Nr; ++j) uz[j] -= (q / qc) * uc[j];
+    }
+    put(2, uz);
   }
 }
 
@@ -523,7 +548,32 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
     }
   } else if (k == "precision") {
     if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
+    if (v == 1.0 && c->eps_c != 0.0) return TC_ERR_UNSUPPORTED;
     c->precision = (int)v;
+  } else if (k == "n_corr") {
+    if (v < 1.0 || v > 16.0 || v != (double)(int)v) return TC_ERR_ARG;
+    c->n_corr = (int)v;
+  } else if (k == "flux_constraint") {
+    if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
+    if ((int)v == c->flux) return TC_OK;
+    try {
+      if (!c->flux_ug) c->flux_ug = dalloc<double>(c, c->sz.Nr);
+      c->flux = (int)v;
+      c->lin.flux_ug = c->flux ? c->flux_ug : nullptr;
+      build_base(c);
+      ck(cudaMemcpyAsync(c->base_dev, c->base.data(), c->base.size() * sizeof(double),
+                         cudaMemcpyHostToDevice, c->stream));
+      // refactor at the next step, which also builds the unit-forcing response
+      char *sb = reinterpret_cast<char *>(c->scal);
+      ck(cudaMemsetAsync(sb + offsetof(DevScalars, dt_factored), 0, sizeof(double), c->stream));
+      ck(cudaStreamSynchronize(c->stream));
+    } catch (const CudaError &e) {
+      return fail_cuda(c, e.e);
+    }
+  } else if (k == "eps_centrifugal") {
+    if (!c->has_T || (v != 0.0 && c->precision == 1)) return TC_ERR_UNSUPPORTED;
+    c->eps_c = v;
+    c->nl.eps_c = v;
   } else if (k == "selftest_no_copy") {
     c->selftest_no_copy = v != 0.0;
   } else if (k == "timing") {
@@ -820,7 +870,10 @@ tc_status tc_diagnostics(tc_ctx *c, tc_diag *o) {
     ck(cudaGetLastError());
     double h[13];
     ck(cudaMemcpyAsync(h, c->diag_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    unsigned long long cb = 0ull;
+    ck(cudaMemcpyAsync(&cb, &c->scal->corr_bits, sizeof(cb), cudaMemcpyDeviceToHost, c->stream));
     ck(cudaStreamSynchronize(c->stream));
+    std::memcpy(&o->corr_diff, &cb, sizeof(double));
     o->t = c->t;
     o->dt = h[0];
     o->E = h[1];
@@ -866,7 +919,10 @@ extern "C" {
 tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *adj_dev) {
   if (!c || !state_n_dev || !adj_dev || !(dt > 0.0) || !std::isfinite(dt)) return TC_ERR_ARG;
   if (c->poisoned) return TC_ERR_CUDA;
-  if (c->precision != 0) return TC_ERR_UNSUPPORTED;
+  // the adjoint is of the default scheme: FP64, one corrector, no flux
+  // constraint, no centrifugal buoyancy
+  if (c->precision != 0 || c->n_corr != 1 || c->flux || c->eps_c != 0.0)
+    return TC_ERR_UNSUPPORTED;
   const double2 *Xn = static_cast<const double2 *>(state_n_dev);
   double2 *lam = static_cast<double2 *>(adj_dev);
   try {
@@ -906,6 +962,7 @@ tc_status tc_nonlinear_adjoint(tc_ctx *c, const void *state_dev, const void *nba
                                void *xbar_dev) {
   if (!c || !state_dev || !nbar_dev || !xbar_dev) return TC_ERR_ARG;
   if (c->poisoned) return TC_ERR_CUDA;
+  if (c->eps_c != 0.0) return TC_ERR_UNSUPPORTED;
   try {
     ensure_adjoint(c);
     launch_nonlinear_adjoint(c, static_cast<const double2 *>(state_dev),
@@ -924,6 +981,7 @@ tc_status tc_nonlinear_adjoint(tc_ctx *c, const void *state_dev, const void *nba
 tc_status tc_stage_solve_adjoint(tc_ctx *c, const void *xbar_dev, double dt, void *rbar_dev) {
   if (!c || !xbar_dev || !rbar_dev || !(dt > 0.0) || !std::isfinite(dt)) return TC_ERR_ARG;
   if (c->poisoned) return TC_ERR_CUDA;
+  if (c->flux) return TC_ERR_UNSUPPORTED;
   try {
     ensure_adjoint(c);
     int zero = 0;

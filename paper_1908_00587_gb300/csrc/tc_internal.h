@@ -58,6 +58,7 @@ struct DevScalars {
   int refactor;         // 1 when the factors must be rebuilt this step
   int nonfinite;        // set when a solve produced NaN/Inf
   int timeout;          // set when a bounded device-side wait gave up
+  unsigned long long corr_bits;   // max |X_corr - X_prev| of the last corrector
 };
 
 // Parameters of the nonlinear stage.
@@ -76,6 +77,7 @@ struct NLParams {
   int mixed;
   const double2 *Xfull;       // state (mixed only)
   const double *prof;         // [r][8]: U_theta, U_z, dU_theta/dr, dU_z/dr, dTbar/dr, T mean
+  double eps_c;               // centrifugal buoyancy: advection weighted by 1 - eps_c T (FP64 only)
 };
 
 // Parameters of the linear stage.
@@ -92,6 +94,7 @@ struct LinParams {
   double *LP, *UP, *LH, *UH, *LT, *UT;
   double *infl;         // influence data [8][Nr][nopP]: pa pb upa uma upb umb za zb
   double *Ainv;         // [4][nopP]
+  double *flux_ug;      // axial-flux constraint: (0,0) u_z response to a unit forcing (Nr), or null
 };
 
 }  // namespace tc
@@ -100,7 +103,7 @@ namespace tc {
 // Kernels with per-launch timing (option "timing").
 enum KernelId {
   KZINV, KTHETA, KZFWD, KDT, KFACTH, KINFL, KRHS, KPRHS, KPOIS, KHRHS, KHELM, KALPHA, KCORR,
-  KDIAG, KCHECK, KADJ, KNUM
+  KDIAG, KCHECK, KFLUX, KADJ, KNUM
 };
 extern const char *const kKernelNames[KNUM];
 
@@ -155,6 +158,10 @@ struct tc_ctx {
   int timing = 0;
   int capturing = 0;            // a graph is capturing this context's stream
   int tile_mb = 0, tile_lb = 0; // nonlinear-stage tile overrides (0: default)
+  int n_corr = 1;               // corrector passes per step
+  int flux = 0;                 // axial-flux constraint on the (0,0) u_z mode
+  double eps_c = 0.0;           // centrifugal buoyancy coefficient
+  double *flux_ug = nullptr;    // device (Nr): unit-forcing response of the (0,0) u_z operator
   tc::KernelTimer timers[tc::KNUM];
 };
 
@@ -198,7 +205,9 @@ void launch_factor_poisson(tc_ctx *c);
 void launch_refactor(tc_ctx *c);
 void launch_dt_policy(tc_ctx *c, double dt_fixed, int step_index);
 void launch_rhs(tc_ctx *c, const double2 *X, const double2 *N0);
-void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout);
+// Xprev (nullable): previous iterate; the stage then records max |Xout - Xprev|.
+void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout,
+                  const double2 *Xprev = nullptr);
 void launch_check_finite(tc_ctx *c, const double2 *X, long long n);
 void launch_state_check(tc_ctx *c, const double2 *X);
 void setup_linear(tc_ctx *c);

@@ -37,7 +37,7 @@ class TCError(RuntimeError):
 class tc_diag(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("t", "dt", "E", "E_pert", "torque_i", "torque_o", "P_wall", "eps",
-                 "buoy_work", "Nu_i", "Nu_o", "div_max", "div_rms", "cfl")]
+                 "buoy_work", "Nu_i", "Nu_o", "div_max", "div_rms", "cfl", "corr_diff")]
 
 
 class tc_info(ctypes.Structure):
