@@ -162,6 +162,23 @@ tc_status tc_get_info(const tc_ctx *ctx, tc_info *out);
  * The simulated time is reset to 0 and the dynamic step forgets its history. */
 tc_status tc_set_state(tc_ctx *ctx, const void *spec, int where);
 
+/* Restart with a change of resolution (Sec. 2.1: resolution may change at a
+ * restart, by interpolation and mode padding).  spec is the state of a run
+ * of the same gap and axial period (eta_src, Lz_src must equal this run's,
+ * else TC_ERR_ARG) on its own grid: complex128 [nfields_src][Nr_src]
+ * [M_src+1][2 K_src+1], k in FFT order (where = 0 host, 1 device; not
+ * retained).  Radial: the degree Nr_src - 1 polynomial through the source's
+ * Chebyshev-Gauss-Lobatto nodal values, evaluated at this run's nodes (wall
+ * values copy exactly).  Fourier: shared modes copied, the rest of this
+ * run's modes zero, source modes beyond M, K dropped.  A source without T
+ * (nfields_src = 3) given to a run with T gets this run's conductive
+ * profile; the reverse drops T.  The result is then checked and committed
+ * as tc_set_state does (same errors; time reset to 0).  Its divergence is
+ * that of an interpolant; the next stage projects it.  Allocates device
+ * scratch for the call (TC_ERR_OOM if that fails). */
+tc_status tc_set_state_regrid(tc_ctx *ctx, const void *spec, int Nr_src, int M_src, int K_src,
+                              int nfields_src, double eta_src, double Lz_src, int where);
+
 /* Copy the current spectral state out (where = 0 host, 1 device). */
 tc_status tc_get_state(const tc_ctx *ctx, void *spec, int where);
 

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtc.so")
 
-SOURCES = ["tc_host.cu", "nonlinear.cu", "linear.cu", "diag.cu", "ensemble.cu"]
+SOURCES = ["tc_host.cu", "nonlinear.cu", "linear.cu", "diag.cu", "ensemble.cu", "restart.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -20,7 +20,7 @@ namespace tc {
 const char *const kKernelNames[KNUM] = {
     "k_zinv", "k_theta", "k_zfwd", "k_dt_policy", "k_factor", "k_influence",
     "k_rhs", "k_prhs", "k_psolve", "k_hrhs", "k_hsolve", "k_alpha", "k_correct", "k_diag", "k_check",
-    "k_flux"};
+    "k_flux", "k_regrid"};
 
 LaunchScope::LaunchScope(tc_ctx *c_, int id_) : c(c_), id(id_) {
   c->launches++;
@@ -426,6 +426,41 @@ void upload_tables(tc_ctx *c) {
 }
 
 }  // namespace
+
+// Validate the state staged in Xp (finite, Hermitian m = 0 column within
+// 1e-12 of its largest entry), symmetrise it and make it the current state.
+// Forgets the dynamic-step history and the flags; the factors stay valid for
+// the step they were built for.
+tc_status commit_staged_state(tc_ctx *c) {
+  const size_t bytes = (size_t)16 * c->sz.nf * c->sz.S;
+  try {
+    DevScalars sc{};
+    char *base = reinterpret_cast<char *>(c->scal);
+    ck(cudaMemsetAsync(base + offsetof(DevScalars, dt_prev), 0, sizeof(double), c->stream));
+    ck(cudaMemsetAsync(base + offsetof(DevScalars, rate_bits), 0,
+                       offsetof(DevScalars, rate_last) - offsetof(DevScalars, rate_bits),
+                       c->stream));
+    ck(cudaMemsetAsync(base + offsetof(DevScalars, nonfinite), 0, sizeof(int), c->stream));
+    launch_state_check(c, c->Xp);
+    ck(cudaGetLastError());
+    ck(cudaMemcpyAsync(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    if (sc.nonfinite) return TC_ERR_NONFINITE;
+    double amax, defect;
+    std::memcpy(&amax, &sc.chk_bits[0], sizeof(double));
+    std::memcpy(&defect, &sc.chk_bits[1], sizeof(double));
+    if (defect > 1e-12 * amax) return TC_ERR_STATE;
+    launch_symmetrise(c, c->Xp);
+    ck(cudaMemcpyAsync(c->X, c->Xp, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    ck(cudaGetLastError());
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  c->t = 0.0;
+  c->dt_last = 0.0;
+  return TC_OK;
+}
+
 }  // namespace tc
 
 using namespace tc;
@@ -615,35 +650,11 @@ tc_status tc_set_state(tc_ctx *c, const void *spec, int where) {
     // stage in Xp, check on the device, commit only a valid state
     ck(cudaMemcpyAsync(c->Xp, spec, bytes,
                        where == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
-    // forget the dynamic-step history and the flags; the factors stay valid
-    // for the step they were built for
-    DevScalars sc{};
-    char *base = reinterpret_cast<char *>(c->scal);
-    ck(cudaMemsetAsync(base + offsetof(DevScalars, dt_prev), 0, sizeof(double), c->stream));
-    ck(cudaMemsetAsync(base + offsetof(DevScalars, rate_bits), 0,
-                       offsetof(DevScalars, rate_last) - offsetof(DevScalars, rate_bits),
-                       c->stream));
-    ck(cudaMemsetAsync(base + offsetof(DevScalars, nonfinite), 0, sizeof(int), c->stream));
-    launch_state_check(c, c->Xp);
-    ck(cudaGetLastError());
-    ck(cudaMemcpyAsync(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
-    ck(cudaStreamSynchronize(c->stream));
-    if (sc.nonfinite) return TC_ERR_NONFINITE;
-    double amax, defect;
-    std::memcpy(&amax, &sc.chk_bits[0], sizeof(double));
-    std::memcpy(&defect, &sc.chk_bits[1], sizeof(double));
-    if (defect > 1e-12 * amax) return TC_ERR_STATE;
-    launch_symmetrise(c, c->Xp);
-    ck(cudaMemcpyAsync(c->X, c->Xp, bytes, cudaMemcpyDeviceToDevice, c->stream));
-    ck(cudaGetLastError());
   } catch (const CudaError &e) {
     return fail_cuda(c, e.e);
   }
-  c->t = 0.0;
-  c->dt_last = 0.0;
-  return TC_OK;
+  return commit_staged_state(c);
 }
-
 tc_status tc_get_state(const tc_ctx *c, void *spec, int where) {
   if (!c || !spec || (where != 0 && where != 1)) return TC_ERR_ARG;
   if (c->poisoned) return TC_ERR_CUDA;

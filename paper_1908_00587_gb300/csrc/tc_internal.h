@@ -103,7 +103,7 @@ namespace tc {
 // Kernels with per-launch timing (option "timing").
 enum KernelId {
   KZINV, KTHETA, KZFWD, KDT, KFACTH, KINFL, KRHS, KPRHS, KPOIS, KHRHS, KHELM, KALPHA, KCORR,
-  KDIAG, KCHECK, KFLUX, KADJ, KNUM
+  KDIAG, KCHECK, KFLUX, KREGRID, KADJ, KNUM
 };
 extern const char *const kKernelNames[KNUM];
 
@@ -194,6 +194,7 @@ inline void allow_smem(F *kernel) {
 
 // tc_host.cu
 void enqueue_step(tc_ctx *c, double dt_fixed, int step_index);
+tc_status commit_staged_state(tc_ctx *c);   // Xp -> X after validation
 
 // nonlinear.cu
 void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long long *rate_bits,

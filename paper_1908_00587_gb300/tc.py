@@ -70,6 +70,7 @@ _SIGS = {
     "tc_set_stream": [_P, _P],
     "tc_get_info": [_P, ctypes.POINTER(tc_info)],
     "tc_set_state": [_P, _P, _I],
+    "tc_set_state_regrid": [_P, _P, _I, _I, _I, _I, _D, _D, _I],
     "tc_get_state": [_P, _P, _I],
     "tc_get_pressure": [_P, _P, _I],
     "tc_init_perturbation": [_P, _P, _I, _I, _D, _P, _D],
@@ -150,6 +151,16 @@ def tc_get_info(ctx) -> tc_info:
 def tc_set_state(ctx, spec):
     p, where = _ptr(spec)
     _check(_lib.tc_set_state(ctx, p, where), "tc_set_state")
+
+
+def tc_set_state_regrid(ctx, spec, eta_src, Lz_src):
+    """spec: state of another resolution, (nfields, Nr, M+1, 2K+1) complex128
+    (numpy array or CUDA tensor); the sizes are read from its shape."""
+    nf, Nr, M1, NK = spec.shape
+    p, where = _ptr(spec)
+    _check(_lib.tc_set_state_regrid(ctx, p, int(Nr), int(M1 - 1), int((NK - 1) // 2), int(nf),
+                                    float(eta_src), float(Lz_src), where),
+           "tc_set_state_regrid")
 
 
 def tc_get_state(ctx, out):
@@ -343,6 +354,9 @@ class Run:
 
     def set_state(self, spec):
         tc_set_state(self.ctx, spec)
+
+    def set_state_regrid(self, spec, eta_src, Lz_src):
+        tc_set_state_regrid(self.ctx, spec, eta_src, Lz_src)
 
     def get_state(self, out=None):
         if out is None:
