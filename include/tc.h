@@ -118,6 +118,10 @@ tc_status tc_destroy(tc_ctx *ctx);
  *   "check"     1: report NaN/Inf produced by tc_step (default 1)
  *   "timing"    1: bracket every kernel launch with CUDA events on the
  *               context's stream (tc_get_timing); 0: off (default)
+ *   "graph"     1 (default): tc_step captures one step as a CUDA graph and
+ *               replays it (re-captured after any option change or a new
+ *               fixed dt); 0, or timing on: kernels launched one by one.
+ *               Results are identical either way.
  *   "tile_mb"   m columns per CTA of the axial transform kernels, "tile_lb"
  *               z rows per CTA of the azimuthal kernel (0: size-based default;
  *               TC_ERR_UNSUPPORTED if the shared memory would not fit).  The

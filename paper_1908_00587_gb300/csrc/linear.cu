@@ -232,7 +232,7 @@ __global__ void k_influence(LinParams p, const DevScalars *sc) {
 }
 
 __global__ void k_dt_policy(DevScalars *sc, double dt_fixed, double cfl, double dt_max,
-                            double *dt_hist, int step) {
+                            double *dt_hist, int hist_cap) {
   const double rate = __longlong_as_double((long long)sc->rate_bits);
   sc->rate_last = rate;
   sc->rate_bits = 0ull;
@@ -249,7 +249,7 @@ __global__ void k_dt_policy(DevScalars *sc, double dt_fixed, double cfl, double 
   sc->dt_prev = dt;
   sc->refactor = (dt != sc->dt_factored) ? 1 : 0;
   if (sc->refactor) sc->dt_factored = dt;
-  if (dt_hist) dt_hist[step] = dt;
+  if (dt_hist && sc->hist_pos < hist_cap) dt_hist[sc->hist_pos++] = dt;
 }
 
 // Y' = X/dt + (1-c) L X + (1-c) N, in +- form, at every node.
@@ -1289,8 +1289,7 @@ void launch_refactor(tc_ctx *c) {
 void launch_dt_policy(tc_ctx *c, double dt_fixed, int step_index) {
   LaunchScope ls(c, KDT);
   k_dt_policy<<<1, 1, 0, c->stream>>>(c->scal, dt_fixed, c->cfl, c->dt_max,
-                                       step_index >= 0 ? c->dt_hist : nullptr,
-                                       step_index >= 0 ? step_index : 0);
+                                       step_index >= 0 ? c->dt_hist : nullptr, c->dt_hist_cap);
 }
 
 void launch_rhs(tc_ctx *c, const double2 *X, const double2 *N0) {

@@ -46,7 +46,8 @@ LaunchScope::~LaunchScope() {
 
 // All kernels of one predictor-corrector step, enqueued on the context's
 // stream with no host synchronisation (so that a graph can capture it).
-// step_index >= 0 records the step used into dt_hist[step_index].
+// step_index >= 0 records the step used into the step history (next slot of
+// a device-side counter that tc_step resets); -1 records nothing.
 // One step: predictor, then n_corr correctors on the same explicit part.
 // The iterates alternate between X and Xp so that the last one lands in X
 // (the predictor may overwrite X: everything that reads X^n -- the first
@@ -461,6 +462,46 @@ tc_status commit_staged_state(tc_ctx *c) {
   return TC_OK;
 }
 
+// Capture one step into a CUDA graph, or keep the one captured before if
+// nothing it depends on has changed: the launch parameters (generation
+// counter, bumped by every option change and buffer reallocation) and the
+// fixed step.  The capture runs on a private stream (the caller's may be the
+// legacy default stream, which cannot be captured); the graph is then
+// launched on the context's stream.
+cudaError_t ensure_step_graph(tc_ctx *c, double dt_fixed) {
+  if (c->step_exec && c->graph_gen == c->gen && c->graph_dt == dt_fixed) return cudaSuccess;
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->step_graph) cudaGraphDestroy(c->step_graph);
+  c->step_exec = nullptr;
+  c->step_graph = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  // the capture stream must not run ahead of work already queued
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  cudaStream_t user = c->stream;
+  const long long l0 = c->launches;
+  c->stream = c->cap_stream;
+  c->capturing = 1;
+  e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue_step(c, dt_fixed, 0);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->step_graph = g;
+  }
+  c->capturing = 0;
+  c->stream = user;
+  c->graph_launches = c->launches - l0;
+  c->launches = l0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_exec, c->step_graph, 0);
+  if (e != cudaSuccess) return e;
+  c->graph_gen = c->gen;
+  c->graph_dt = dt_fixed;
+  return cudaSuccess;
+}
+
 }  // namespace tc
 
 using namespace tc;
@@ -545,6 +586,9 @@ tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz, double Re
 
 tc_status tc_destroy(tc_ctx *c) {
   if (!c) return TC_OK;
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->step_graph) cudaGraphDestroy(c->step_graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void *p : c->allocs) cudaFree(p);
   for (auto &t : c->timers)
     for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
@@ -556,6 +600,7 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
   if (!c || !key) return TC_ERR_ARG;
   const std::string k(key);
   if (!std::isfinite(v)) return TC_ERR_ARG;
+  ++c->gen;   // any option may change a launch parameter of the step
   if (k == "cfl") {
     if (!(v > 0.0)) return TC_ERR_ARG;
     c->cfl = v;
@@ -613,6 +658,8 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
     c->selftest_no_copy = v != 0.0;
   } else if (k == "timing") {
     c->timing = v != 0.0;
+  } else if (k == "graph") {
+    c->use_graph = v != 0.0;
   } else {
     return TC_ERR_ARG;
   }
@@ -806,11 +853,28 @@ tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
         if (p == c->dt_hist) p = h;
       c->dt_hist = h;
       c->dt_hist_cap = nsteps;
+      ++c->gen;   // the history pointer is a kernel argument
     }
-    int zero = 0;
-    ck(cudaMemcpyAsync(&c->scal->nonfinite, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    char *sb = reinterpret_cast<char *>(c->scal);
+    ck(cudaMemsetAsync(sb + offsetof(DevScalars, nonfinite), 0, sizeof(int), c->stream));
+    ck(cudaMemsetAsync(sb + offsetof(DevScalars, hist_pos), 0, sizeof(int), c->stream));
     const double dt_fixed = dt > 0.0 ? dt : 0.0;
-    for (int n = 0; n < nsteps; ++n) enqueue_step(c, dt_fixed, n);
+    if (c->use_graph && !c->timing) {
+      const cudaError_t ge = ensure_step_graph(c, dt_fixed);
+      if (ge != cudaSuccess) {
+        // not capturable here: launch the kernels directly from now on
+        cudaGetLastError();
+        std::fprintf(stderr, "libtc: step graph unavailable (%s), launching directly\n",
+                     cudaGetErrorString(ge));
+        c->use_graph = 0;
+      }
+    }
+    if (c->use_graph && !c->timing) {
+      for (int n = 0; n < nsteps; ++n) ck(cudaGraphLaunch(c->step_exec, c->stream));
+      c->launches += c->graph_launches * nsteps;
+    } else {
+      for (int n = 0; n < nsteps; ++n) enqueue_step(c, dt_fixed, n);
+    }
     ck(cudaGetLastError());
     std::vector<double> hist(nsteps);
     ck(cudaMemcpyAsync(hist.data(), c->dt_hist, sizeof(double) * nsteps, cudaMemcpyDeviceToHost,

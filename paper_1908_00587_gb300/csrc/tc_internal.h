@@ -59,6 +59,7 @@ struct DevScalars {
   int nonfinite;        // set when a solve produced NaN/Inf
   int timeout;          // set when a bounded device-side wait gave up
   unsigned long long corr_bits;   // max |X_corr - X_prev| of the last corrector
+  int hist_pos;         // next slot of the step history of the current tc_step call
 };
 
 // Parameters of the nonlinear stage.
@@ -162,6 +163,15 @@ struct tc_ctx {
   int flux = 0;                 // axial-flux constraint on the (0,0) u_z mode
   double eps_c = 0.0;           // centrifugal buoyancy coefficient
   double *flux_ug = nullptr;    // device (Nr): unit-forcing response of the (0,0) u_z operator
+  // one step captured as a CUDA graph and replayed by tc_step (timing off)
+  int use_graph = 1;
+  long long gen = 0;            // bumped whenever a launch parameter may change
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t step_graph = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  long long graph_gen = -1;
+  double graph_dt = 0.0;
+  long long graph_launches = 0; // kernels in one replay
   tc::KernelTimer timers[tc::KNUM];
 };
 
@@ -195,6 +205,7 @@ inline void allow_smem(F *kernel) {
 // tc_host.cu
 void enqueue_step(tc_ctx *c, double dt_fixed, int step_index);
 tc_status commit_staged_state(tc_ctx *c);   // Xp -> X after validation
+cudaError_t ensure_step_graph(tc_ctx *c, double dt_fixed);
 
 // nonlinear.cu
 void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long long *rate_bits,
