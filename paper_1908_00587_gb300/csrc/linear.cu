@@ -320,38 +320,73 @@ __device__ __forceinline__ double2 rhs_pm(const double2 *Yb, const double2 *N, l
 // so one thread owns one real system and its loads coalesce across modes.
 
 // Poisson right-hand side: div R inside, 0 on the Neumann rows and for (0,0).
-__global__ void k_prhs(const double2 *__restrict__ Yb, const double2 *__restrict__ N,
-                       double *__restrict__ Ps, LinParams p) {
+// A CTA takes kPrW consecutive modes x kPrL consecutive rows.  The radial
+// component R_r = (R+ + R-)/2 that the divergence stencil reads is formed once
+// per node of the window [j0 - 8, j0 + kPrL + 8) into shared memory (every
+// stencil of the tile lies inside: it starts at clamp(j - 4, 0, Nr - 9), which
+// is within 8 rows below j), instead of once per tap.
+// With temperature the same kernel writes the T Helmholtz right-hand side
+// (it needs no pressure), so the T solve can run with the pressure solve.
+constexpr int kPrW = 32, kPrL = 32, kPrThreads = 256;
+__global__ void __launch_bounds__(kPrThreads)
+k_prhs(const double2 *__restrict__ Yb, const double2 *__restrict__ N, double *__restrict__ Ps,
+       double *__restrict__ UT, LinParams p) {
   const Sizes &s = p.sz;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.S) return;
-  const int j = (int)(i / s.nmode);
-  const int mode = (int)(i - (long long)j * s.nmode);
-  double2 b = {0.0, 0.0};
-  if (mode != 0 && j > 0 && j < s.Nr - 1) {
-    const int m = mode / s.NK, kk = mode % s.NK;
-    const double beta = p.alpha * kval(kk, s.K, s.NK);
-    const int st = p.rad.s0[j];
-    const double *dw = p.rad.Dw + j * kStencil;   // (1/r_j) D1 r_s
-    double2 acc = {0.0, 0.0};
-#pragma unroll
-    for (int t = 0; t < kStencil; ++t) {
-      const long long ii = (long long)(st + t) * s.nmode + mode;
+  constexpr int kWin = kPrL + 16;
+  __shared__ double2 Rr[kWin * kPrW];
+  const int tx = threadIdx.x % kPrW, ty = threadIdx.x / kPrW;
+  constexpr int kRowsT = kPrThreads / kPrW;
+  const int mode = blockIdx.x * kPrW + tx;
+  const int j0 = blockIdx.y * kPrL;
+  const long long S = s.S;
+  for (int q = ty; q < kWin; q += kRowsT) {
+    const int jw = j0 - 8 + q;
+    double2 rr = {0.0, 0.0};
+    if (mode < s.nmode && jw >= 0 && jw < s.Nr) {
+      const long long ii = (long long)jw * s.nmode + mode;
       // R_r = (R+ + R-)/2 = (Y+ + Y-)/2 + c N_r
-      const double2 yp = Yb[ii], ym = Yb[s.S + ii], nr = N[ii];
-      const double2 rr = {0.5 * (yp.x + ym.x) + kCN * nr.x, 0.5 * (yp.y + ym.y) + kCN * nr.y};
-      acc = acc + dw[t] * rr;
+      const double2 yp = Yb[ii], ym = Yb[S + ii], nr = N[ii];
+      rr = double2{0.5 * (yp.x + ym.x) + kCN * nr.x, 0.5 * (yp.y + ym.y) + kCN * nr.y};
     }
-    const double2 rt = div_2i(rhs_pm(Yb, N, s.S, i, 0) - rhs_pm(Yb, N, s.S, i, 1));
-    const double2 rz = rhs_pm(Yb, N, s.S, i, 2);
-    const double ir = p.rad.inv_r[j];
-    b = acc + (m * ir) * mul_i(rt) + beta * mul_i(rz);
+    Rr[q * kPrW + tx] = rr;
   }
-  Ps[i] = b.x;
-  Ps[s.S + i] = b.y;
+  __syncthreads();
+  if (mode >= s.nmode) return;
+  for (int r = ty; r < kPrL; r += kRowsT) {
+    const int j = j0 + r;
+    if (j >= s.Nr) break;
+    const long long i = (long long)j * s.nmode + mode;
+    double2 b = {0.0, 0.0};
+    if (mode != 0 && j > 0 && j < s.Nr - 1) {
+      const int m = mode / s.NK, kk = mode % s.NK;
+      const double beta = p.alpha * kval(kk, s.K, s.NK);
+      const int q0 = p.rad.s0[j] - (j0 - 8);
+      const double *dw = p.rad.Dw + j * kStencil;   // (1/r_j) D1 r_s
+      double2 acc = {0.0, 0.0};
+#pragma unroll
+      for (int t = 0; t < kStencil; ++t) acc = acc + dw[t] * Rr[(q0 + t) * kPrW + tx];
+      const double2 rt = div_2i(rhs_pm(Yb, N, S, i, 0) - rhs_pm(Yb, N, S, i, 1));
+      const double2 rz = rhs_pm(Yb, N, S, i, 2);
+      const double ir = p.rad.inv_r[j];
+      b = acc + (m * ir) * mul_i(rt) + beta * mul_i(rz);
+    }
+    Ps[i] = b.x;
+    Ps[S + i] = b.y;
+    if (UT) {   // T: Dirichlet rows (wall temperatures in the (0,0) mode)
+      double2 bt = {0.0, 0.0};
+      if (j == 0 || j == s.Nr - 1) {
+        if (mode == 0) bt.x = (j == 0) ? 0.5 : -0.5;
+      } else {
+        bt = rhs_pm(Yb, N, S, i, 3);
+      }
+      UT[i] = bt.x;
+      UT[S + i] = bt.y;
+    }
+  }
 }
 
-// Helmholtz right-hand sides of u+, u-, u_z (, T), wall values on the wall rows.
+// Helmholtz right-hand sides of u+, u-, u_z, wall values on the wall rows (the
+// T right-hand side comes from k_prhs).
 // Mode (0,0): slot 0 carries u_theta's equation (u_r = 0), slot 1 is unused.
 __global__ void k_hrhs(const double2 *__restrict__ Yb, const double2 *__restrict__ N,
                        const double *__restrict__ Ps, double *__restrict__ U, LinParams p) {
@@ -362,21 +397,19 @@ __global__ void k_hrhs(const double2 *__restrict__ Yb, const double2 *__restrict
   const int mode = (int)(i - (long long)j * s.nmode);
   const long long S = s.S;
   const bool wall = (j == 0 || j == s.Nr - 1);
-  double2 b[4] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+  double2 b[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
   if (mode == 0) {
     const bool lo = (j == 0);
     if (wall) {
       b[0] = {lo ? p.Re_i : p.Re_o, 0.0};
       b[2] = {0.0, 0.0};
-      b[3] = {lo ? 0.5 : -0.5, 0.0};
     } else {
       b[0] = div_2i(rhs_pm(Yb, N, S, i, 0) - rhs_pm(Yb, N, S, i, 1));
       b[2] = rhs_pm(Yb, N, S, i, 2);
-      if (s.nf == 4) b[3] = rhs_pm(Yb, N, S, i, 3);
     }
     b[1] = {0.0, 0.0};
   } else if (wall) {
-    b[0] = b[1] = b[2] = b[3] = double2{0.0, 0.0};
+    b[0] = b[1] = b[2] = double2{0.0, 0.0};
   } else {
     const int m = mode / s.NK, kk = mode % s.NK;
     const double beta = p.alpha * kval(kk, s.K, s.NK);
@@ -392,14 +425,11 @@ __global__ void k_hrhs(const double2 *__restrict__ Yb, const double2 *__restrict
     b[0] = rhs_pm(Yb, N, S, i, 0) - (d1p - mp);
     b[1] = rhs_pm(Yb, N, S, i, 1) - (d1p + mp);
     b[2] = rhs_pm(Yb, N, S, i, 2) - beta * mul_i(pj);
-    if (s.nf == 4) b[3] = rhs_pm(Yb, N, S, i, 3);
   }
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    if (c < s.nf) {
-      U[(2 * c) * S + i] = b[c].x;
-      U[(2 * c + 1) * S + i] = b[c].y;
-    }
+  for (int c = 0; c < 3; ++c) {
+    U[(2 * c) * S + i] = b[c].x;
+    U[(2 * c + 1) * S + i] = b[c].y;
   }
 }
 
@@ -762,34 +792,43 @@ k_sweep(SweepArgs a, DevScalars *sc) {
 }
 
 // Influence coefficients per mode: alpha = -Ainv [div u0 (r_i), div u0 (r_o)].
+// Two lanes per mode: lane w forms the wall divergence at wall w, the pair
+// swaps them, and lane w writes row w of alpha.
 __global__ void k_alpha(const double *__restrict__ U, double2 *__restrict__ alpha, LinParams p) {
   const Sizes &s = p.sz;
-  const int mode = blockIdx.x * blockDim.x + threadIdx.x;
-  if (mode >= s.nmode || mode == 0) return;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int mode = (int)(t >> 1);
+  const int w = (int)(t & 1);
+  const bool live = mode < s.nmode && mode != 0;
   const long long S = s.S;
-  const int m = mode / s.NK, kk = mode % s.NK;
-  const int kv = kval(kk, s.K, s.NK);
-  const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
-  double2 d[2];
-  for (int w = 0; w < 2; ++w) {
+  double2 d = {0.0, 0.0};
+  int o = 0;
+  if (live) {
+    const int m = mode / s.NK, kk = mode % s.NK;
+    const int kv = kval(kk, s.K, s.NK);
+    o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
     const int j = (w == 0) ? 0 : s.Nr - 1;
     const int st = p.rad.s0[j];
     double2 acc = {0.0, 0.0};
 #pragma unroll
-    for (int t = 0; t < kStencil; ++t) {
-      const long long ii = (long long)(st + t) * s.nmode + mode;
+    for (int q = 0; q < kStencil; ++q) {
+      const long long ii = (long long)(st + q) * s.nmode + mode;
       const double2 up = {U[ii], U[S + ii]}, um = {U[2 * S + ii], U[3 * S + ii]};
       const double2 ur = 0.5 * (up + um);
-      acc = acc + p.rad.D1[j * kStencil + t] * (p.rad.r[st + t] * ur);
+      acc = acc + p.rad.D1[j * kStencil + q] * (p.rad.r[st + q] * ur);
     }
-    d[w] = p.rad.inv_r[j] * acc;
+    d = p.rad.inv_r[j] * acc;
   }
+  // lanes 2i, 2i+1 hold the two walls of one mode (the grid is whole warps)
+  const double ox = __shfl_xor_sync(0xffffffffu, d.x, 1);
+  const double oy = __shfl_xor_sync(0xffffffffu, d.y, 1);
+  if (!live) return;
+  const double2 d0 = w == 0 ? d : double2{ox, oy};
+  const double2 d1 = w == 0 ? double2{ox, oy} : d;
   const int nop = p.nopP;
-  const double a00 = p.Ainv[o], a01 = p.Ainv[nop + o], a10 = p.Ainv[2 * nop + o],
-               a11 = p.Ainv[3 * nop + o];
-  alpha[mode] = double2{-(a00 * d[0].x + a01 * d[1].x), -(a00 * d[0].y + a01 * d[1].y)};
-  alpha[s.nmode + mode] =
-      double2{-(a10 * d[0].x + a11 * d[1].x), -(a10 * d[0].y + a11 * d[1].y)};
+  const double a0 = p.Ainv[(2 * w) * nop + o], a1 = p.Ainv[(2 * w + 1) * nop + o];
+  alpha[(long long)w * s.nmode + mode] =
+      double2{-(a0 * d0.x + a1 * d1.x), -(a0 * d0.y + a1 * d1.y)};
 }
 
 __global__ void k_correct(const double *__restrict__ U, const double *__restrict__ Ps,
@@ -798,7 +837,10 @@ __global__ void k_correct(const double *__restrict__ U, const double *__restrict
                           LinParams p, DevScalars *sc) {
   const Sizes &s = p.sz;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double dmax = 0.0;   // max |Xout - Xprev| over this thread's coefficients
+  // max |Xout - Xprev| over this thread's coefficients, kept as the bit
+  // pattern (non-negative doubles order like their bits), so only the
+  // subtractions use the FP64 pipe
+  unsigned long long dbits = 0ull;
   if (i < s.S) {
     const int j = (int)(i / s.nmode);
     const int mode = (int)(i - (long long)j * s.nmode);
@@ -847,7 +889,9 @@ __global__ void k_correct(const double *__restrict__ U, const double *__restrict
     if (bad) atomicOr(&sc->nonfinite, 1);
     if (Xprev) {
       auto dm = [&](double2 a, double2 b) {
-        dmax = fmax(dmax, fmax(fabs(a.x - b.x), fabs(a.y - b.y)));
+        const unsigned long long u = (unsigned long long)__double_as_longlong(fabs(a.x - b.x));
+        const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(a.y - b.y));
+        dbits = max(dbits, max(u, v));
       };
       dm(xr, Xprev[i]);
       dm(xt, Xprev[S + i]);
@@ -855,10 +899,17 @@ __global__ void k_correct(const double *__restrict__ U, const double *__restrict
       if (s.nf == 4) dm(T, Xprev[3 * S + i]);
     }
   }
-  if (Xprev) {   // uniform over the grid: every lane of every warp gets here
-    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    if ((threadIdx.x & 31) == 0 && dmax > 0.0)
-      atomicMax(&sc->corr_bits, (unsigned long long)__double_as_longlong(dmax));
+  if (Xprev) {   // uniform over the grid: every thread of every block gets here
+    __shared__ unsigned long long wmax[32];
+    for (int o = 16; o > 0; o >>= 1) dbits = max(dbits, __shfl_xor_sync(0xffffffffu, dbits, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = dbits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) dbits = max(dbits, wmax[w]);
+      // one atomic per block, and none once a larger value is in place
+      if (dbits > *reinterpret_cast<volatile unsigned long long *>(&sc->corr_bits))
+        atomicMax(&sc->corr_bits, dbits);
+    }
   }
 }
 
@@ -1302,17 +1353,20 @@ void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout,
   const Sizes &s = c->sz;
   const LinParams &p = c->lin;
   double *U = reinterpret_cast<double *>(c->U0);
+  double *UT = (s.nf == 4) ? U + 6 * s.S : nullptr;
   {
     LaunchScope ls(c, KPRHS);
-    k_prhs<<<blocks(s.S, 128), 128, 0, c->stream>>>(c->Yb, N, c->Ps, p);
+    k_prhs<<<dim3(blocks(s.nmode, kPrW), blocks(s.Nr, kPrL)), kPrThreads, 0, c->stream>>>(
+        c->Yb, N, c->Ps, UT, p);
   }
   {
+    // the pressure and (independent of it) the temperature
     LaunchScope ls(c, KPOIS);
     SweepArgs sa = sweep_args(c);
     sa.f[0] = SweepField{p.LP, p.UP, c->Ps, 0, 1};
-    k_sweep<false><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, 1), 4 * kSweepOps, kSweepSmem,
-              c->stream>>>(
-        sa, c->scal);
+    if (UT) sa.f[1] = SweepField{p.LT, p.UT, UT, 0, 0};
+    k_sweep<false><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, UT ? 2 : 1), 4 * kSweepOps,
+                     kSweepSmem, c->stream>>>(sa, c->scal);
   }
   {
     LaunchScope ls(c, KHRHS);
@@ -1324,14 +1378,12 @@ void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout,
     sa.f[0] = SweepField{p.LH, p.UH, U + 0 * s.S, +1, 0};
     sa.f[1] = SweepField{p.LH, p.UH, U + 2 * s.S, -1, 0};
     sa.f[2] = SweepField{p.LH, p.UH, U + 4 * s.S, 0, 0};
-    if (s.nf == 4) sa.f[3] = SweepField{p.LT, p.UT, U + 6 * s.S, 0, 0};
-    k_sweep<false><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, s.nf), 4 * kSweepOps, kSweepSmem,
-              c->stream>>>(
-        sa, c->scal);
+    k_sweep<false><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, 3), 4 * kSweepOps, kSweepSmem,
+                     c->stream>>>(sa, c->scal);
   }
   {
     LaunchScope ls(c, KALPHA);
-    k_alpha<<<blocks(s.nmode, 128), 128, 0, c->stream>>>(U, c->alpha_buf, p);
+    k_alpha<<<blocks(2LL * s.nmode, 64), 64, 0, c->stream>>>(U, c->alpha_buf, p);
   }
   {
     LaunchScope ls(c, KCORR);

@@ -229,10 +229,13 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   V2<T> *out = (ph == A) ? B : A;
   const double rr = p.rad.r[r];
   const T inv_r = (T)p.rad.inv_r[r];
-  // CFL: running maxima of |u_r|, |u_theta|, |u_z|; the divisions by the
-  // spacings come once per thread after the loop (division by a positive
-  // constant is monotone, so the max of the quotients is unchanged)
-  double mr = 0.0, mt = 0.0, mz = 0.0, nu = 0.0, nT = 0.0;
+  // CFL: running maxima of |u_r|, |u_theta|, |u_z|, kept as bit patterns
+  // (non-negative doubles order like their bits: integer max, no FP64 issue
+  // slot); the divisions by the spacings come once per thread after the loop
+  // (division by a positive constant is monotone, so the max is unchanged)
+  unsigned long long mr = 0ull, mt = 0ull, mz = 0ull;
+  double nu = 0.0, nT = 0.0;
+  auto bits = [](double v) { return (unsigned long long)__double_as_longlong(fabs(v)); };
   for (int t = threadIdx.x; t < nl * Nt; t += blockDim.x) {
     const int j = t % Nt;
     const int li = t / Nt;
@@ -273,9 +276,9 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     o[0] = V2<T>{Nr_, Nt_};
     o[Ntp] = V2<T>{Nz_, NT_};
     if (rate_bits) {
-      mr = fmax(mr, fabs((double)ur));
-      mt = fmax(mt, fabs(mixed ? (double)ut + Ut : (double)ut));
-      mz = fmax(mz, fabs(mixed ? (double)uz + Uz : (double)uz));
+      mr = max(mr, bits((double)ur));
+      mt = max(mt, bits(mixed ? (double)ut + Ut : (double)ut));
+      mz = max(mz, bits(mixed ? (double)uz + Uz : (double)uz));
     }
   }
   if (mode == 1) {
@@ -290,7 +293,8 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     return;
   }
   if (rate_bits) {
-    double rate = fmax(mr / p.rad.dr_min[r], fmax(mt / (rr * p.dth), mz / p.dz));
+    auto val = [](unsigned long long b) { return __longlong_as_double((long long)b); };
+    double rate = fmax(val(mr) / p.rad.dr_min[r], fmax(val(mt) / (rr * p.dth), val(mz) / p.dz));
     for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
     if ((threadIdx.x & 31) == 0) atomic_max_pos(rate_bits, rate);
   }
