@@ -989,32 +989,59 @@ __global__ void k_stT_correct(const double2 *__restrict__ Lb, double *__restrict
 // Per mode: alphabar = <homogeneous solutions, ubar>, dbar = -Ainv^T alphabar,
 // then the wall-divergence stencils scatter dbar into ubar0 (this thread owns
 // the mode's column).
-__global__ void k_stT_alpha(double *__restrict__ U, LinParams p) {
+// A CTA takes kAlW modes (lanes) x kAlR row groups (warps): each thread sums
+// its rows' share of the homogeneous-solution products, the row groups are
+// reduced in shared memory, and one lane per mode forms the wall
+// divergence cotangents and scatters them back through the transposed stencil
+// (sequentially per mode: with Nr < 18 the two walls' stencils overlap).
+constexpr int kAlW = 32, kAlR = 8;
+__global__ void __launch_bounds__(kAlW * kAlR) k_stT_alpha(double *__restrict__ U, LinParams p) {
   const Sizes &s = p.sz;
-  const int mode = blockIdx.x * blockDim.x + threadIdx.x;
-  if (mode >= s.nmode || mode == 0) return;
+  __shared__ double red[kAlR][4][kAlW];
+  const int tx = threadIdx.x % kAlW, ty = threadIdx.x / kAlW;
+  const int mode = blockIdx.x * kAlW + tx;
+  const bool live = mode < s.nmode && mode != 0;
   const long long S = s.S;
-  const int m = mode / s.NK, kk = mode % s.NK;
-  const int kv = kval(kk, s.K, s.NK);
-  const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
-  const double beta = p.alpha * kv;
+  int o = 0;
+  double beta = 0.0;
+  if (live) {
+    const int m = mode / s.NK, kk = mode % s.NK;
+    const int kv = kval(kk, s.K, s.NK);
+    o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
+    beta = p.alpha * kv;
+  }
   const long long fs = (long long)s.Nr * p.nopP;
   const double *F = p.infl;
   double2 ab[2] = {{0.0, 0.0}, {0.0, 0.0}};
-  for (int j = 0; j < s.Nr; ++j) {
-    const long long ii = (long long)j * s.nmode + mode;
-    const long long jo = (long long)j * p.nopP + o;
-    const double2 up = {U[ii], U[S + ii]}, um = {U[2 * S + ii], U[3 * S + ii]};
-    const double2 uz = {U[4 * S + ii], U[5 * S + ii]};
+  if (live) {
+    for (int j = ty; j < s.Nr; j += kAlR) {
+      const long long ii = (long long)j * s.nmode + mode;
+      const long long jo = (long long)j * p.nopP + o;
+      const double2 up = {U[ii], U[S + ii]}, um = {U[2 * S + ii], U[3 * S + ii]};
+      const double2 uz = {U[4 * S + ii], U[5 * S + ii]};
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const double hp = F[(2 + 2 * q) * fs + jo], hm = F[(3 + 2 * q) * fs + jo];
-      const double zq = F[(6 + q) * fs + jo];
-      // u_z of a homogeneous solution is -i beta zeta: transpose is +i beta zeta
-      ab[q].x += hp * up.x + hm * um.x - beta * zq * uz.y;
-      ab[q].y += hp * up.y + hm * um.y + beta * zq * uz.x;
+      for (int q = 0; q < 2; ++q) {
+        const double hp = F[(2 + 2 * q) * fs + jo], hm = F[(3 + 2 * q) * fs + jo];
+        const double zq = F[(6 + q) * fs + jo];
+        // u_z of a homogeneous solution is -i beta zeta: transpose is +i beta zeta
+        ab[q].x += hp * up.x + hm * um.x - beta * zq * uz.y;
+        ab[q].y += hp * up.y + hm * um.y + beta * zq * uz.x;
+      }
     }
   }
+  red[ty][0][tx] = ab[0].x;
+  red[ty][1][tx] = ab[0].y;
+  red[ty][2][tx] = ab[1].x;
+  red[ty][3][tx] = ab[1].y;
+  __syncthreads();
+  if (ty != 0 || !live) return;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int g = 0; g < kAlR; ++g)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] += red[g][c][tx];
+  ab[0] = double2{v[0], v[1]};
+  ab[1] = double2{v[2], v[3]};
   const int nop = p.nopP;
   const double a00 = p.Ainv[o], a01 = p.Ainv[nop + o], a10 = p.Ainv[2 * nop + o],
                a11 = p.Ainv[3 * nop + o];
@@ -1024,6 +1051,7 @@ __global__ void k_stT_alpha(double *__restrict__ U, LinParams p) {
     const int j = (w == 0) ? 0 : s.Nr - 1;
     const int st = p.rad.s0[j];
     const double2 d = (w == 0) ? d0 : d1;
+#pragma unroll
     for (int t = 0; t < kStencil; ++t) {
       const double cf = 0.5 * p.rad.inv_r[j] * p.rad.D1[j * kStencil + t] * p.rad.r[st + t];
       const long long ii = (long long)(st + t) * s.nmode + mode;
@@ -1067,10 +1095,11 @@ __global__ void k_stT_hrhs(const double *__restrict__ U, double2 *__restrict__ R
       pb.y = mr * (b[0].y - b[1].y) + beta * b[2].x;
     }
     // -D1^T (b0 + b1) over the interior rows whose stencil holds node j
-    const int jlo = max(1, j - 2 * kStencil), jhi = min(s.Nr - 2, j + 2 * kStencil);
-    for (int jj = jlo; jj <= jhi; ++jj) {
+    for (int e = 0; e < kTrans; ++e) {
+      const int jj = p.rad.tj[j * kTrans + e];
+      if (jj < 0) break;
+      if (jj < 1 || jj > s.Nr - 2) continue;
       const int t = j - p.rad.s0[jj];
-      if (t < 0 || t >= kStencil) continue;
       const double w = p.rad.D1[jj * kStencil + t];
       const long long q = (long long)jj * s.nmode + mode;
       pb.x -= w * (U[q] + U[2 * S + q]);
@@ -1095,10 +1124,11 @@ __global__ void k_stT_prhs(const double *__restrict__ Ps, double2 *__restrict__ 
   const int m = mode / s.NK, kk = mode % s.NK;
   const double beta = p.alpha * kval(kk, s.K, s.NK);
   double2 rr = {0.0, 0.0}, rt = {0.0, 0.0}, rz = {0.0, 0.0};
-  const int jlo = max(1, sn - 2 * kStencil), jhi = min(s.Nr - 2, sn + 2 * kStencil);
-  for (int j = jlo; j <= jhi; ++j) {
+  for (int e = 0; e < kTrans; ++e) {
+    const int j = p.rad.tj[sn * kTrans + e];
+    if (j < 0) break;
+    if (j < 1 || j > s.Nr - 2) continue;
     const int t = sn - p.rad.s0[j];
-    if (t < 0 || t >= kStencil) continue;
     const double w = p.rad.Dw[j * kStencil + t];
     const long long q = (long long)j * s.nmode + mode;
     rr.x += w * Ps[q];
@@ -1162,10 +1192,10 @@ __global__ void k_rhsT(const double2 *__restrict__ Yb, double2 *__restrict__ Xb,
   const double ir = p.rad.inv_r[sn];
   const double b2 = beta * beta, ir2 = ir * ir;
   double2 g[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};   // sum_j (D2 + D1/r_j)[j][sn] Ybar(j)
-  const int jlo = max(0, sn - 2 * kStencil), jhi = min(s.Nr - 1, sn + 2 * kStencil);
-  for (int j = jlo; j <= jhi; ++j) {
+  for (int e = 0; e < kTrans; ++e) {
+    const int j = p.rad.tj[sn * kTrans + e];
+    if (j < 0) break;
     const int t = sn - p.rad.s0[j];
-    if (t < 0 || t >= kStencil) continue;
     const double w = p.rad.Lw[j * kStencil + t];
     const long long q = (long long)j * s.nmode + mode;
 #pragma unroll
@@ -1416,7 +1446,7 @@ void launch_stage_adjoint(tc_ctx *c, const double2 *Lb, double2 *Rb) {
   double *U = reinterpret_cast<double *>(c->U0);
   LaunchScope ls(c, KADJ);
   k_stT_correct<<<blocks(s.S, 128), 128, 0, c->stream>>>(Lb, U, s);
-  k_stT_alpha<<<blocks(s.nmode, 64), 64, 0, c->stream>>>(U, p);
+  k_stT_alpha<<<blocks(s.nmode, kAlW), kAlW * kAlR, 0, c->stream>>>(U, p);
   SweepArgs sa = sweep_args(c);
   sa.f[0] = SweepField{p.LH, p.UH, U + 0 * s.S, +1, 0};
   sa.f[1] = SweepField{p.LH, p.UH, U + 2 * s.S, -1, 0};

@@ -885,10 +885,10 @@ __global__ void k_drT(const double2 *__restrict__ Gr, double2 *__restrict__ Xb, 
   const int sn = (int)(rem / s.nmode);
   const int mode = (int)(rem - (long long)sn * s.nmode);
   double2 acc = Xb[i];
-  const int jlo = max(0, sn - 2 * kStencil), jhi = min(s.Nr - 1, sn + 2 * kStencil);
-  for (int j = jlo; j <= jhi; ++j) {
+  for (int e = 0; e < kTrans; ++e) {
+    const int j = rad.tj[sn * kTrans + e];
+    if (j < 0) break;
     const int t = sn - rad.s0[j];
-    if (t < 0 || t >= kStencil) continue;
     const double w = rad.D1[j * kStencil + t];
     const double2 g = Gr[(long long)c * s.S + (long long)j * s.nmode + mode];
     acc.x += w * g.x;

@@ -336,6 +336,7 @@ void allocate(tc_ctx *c) {
   c->d_D2 = dalloc<double>(c, (size_t)s.Nr * kStencil);
   c->d_Lw = dalloc<double>(c, (size_t)s.Nr * kStencil);
   c->d_Dw = dalloc<double>(c, (size_t)s.Nr * kStencil);
+  c->d_tj = dalloc<int>(c, (size_t)s.Nr * kTrans);
   c->d_dr = dalloc<double>(c, s.Nr);
   c->d_wr = dalloc<double>(c, s.Nr);
   c->d_s0 = dalloc<int>(c, s.Nr);
@@ -397,7 +398,19 @@ void upload_tables(tc_ctx *c) {
     }
   ck(cudaMemcpy(c->d_Lw, Lw.data(), Lw.size() * sizeof(double), cudaMemcpyHostToDevice));
   ck(cudaMemcpy(c->d_Dw, Dw.data(), Dw.size() * sizeof(double), cudaMemcpyHostToDevice));
-  Radial rad{c->d_r, c->d_inv_r, c->d_D1, c->d_D2, c->d_dr, c->d_wr, c->d_s0, c->d_Lw, c->d_Dw};
+  std::vector<int> tj((size_t)s.Nr * kTrans, -1);
+  for (int n = 0; n < s.Nr; ++n) {
+    int k = 0;
+    for (int j = 0; j < s.Nr; ++j)
+      if (c->s0[j] <= n && n < c->s0[j] + kStencil) {
+        if (k < kTrans) tj[(size_t)n * kTrans + k] = j;
+        ++k;
+      }
+    if (k > kTrans) throw CudaError{cudaErrorInvalidValue};   // cannot happen (at most 17)
+  }
+  ck(cudaMemcpy(c->d_tj, tj.data(), tj.size() * sizeof(int), cudaMemcpyHostToDevice));
+  Radial rad{c->d_r,  c->d_inv_r, c->d_D1, c->d_D2, c->d_dr,
+             c->d_wr, c->d_s0,    c->d_Lw, c->d_Dw, c->d_tj};
   NLParams &p = c->nl;
   p.sz = s;
   p.rad = rad;

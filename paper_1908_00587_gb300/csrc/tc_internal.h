@@ -44,7 +44,13 @@ struct Radial {
   const int *s0;                                     // stencil start per node
   const double *Lw;   // [Nr][9] D2 + D1/r_j: the radial part of L in one stencil
   const double *Dw;   // [Nr][9] (1/r_j) D1 r_s: the radial part of div
+  // transposed stencils: [Nr][kTrans] the rows j whose stencil holds node n,
+  // ascending, -1 after the last.  At most 13 for Nr >= 18 (the 5 rows whose
+  // stencil is clamped to a wall plus 8 centred ones); with Nr <= 17 every row
+  // can hold node n, so at most 17.
+  const int *tj;
 };
+constexpr int kTrans = 20;
 
 // Scalars shared between kernels on the device.
 struct DevScalars {
@@ -136,6 +142,7 @@ struct tc_ctx {
   double2 *X, *Xp, *N0, *N1, *Yb, *U0, *P, *V, *W, *alpha_buf, *base_dev;
   double *Ps;   // particular pressure, split planes [2][S]
   double *d_Lw, *d_Dw;
+  int *d_tj;
   double *d_r, *d_inv_r, *d_D1, *d_D2, *d_dr, *d_wr;
   int *d_s0;
   double2 *d_twz, *d_twt;
