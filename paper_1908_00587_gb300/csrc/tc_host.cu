@@ -1017,13 +1017,15 @@ tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *a
     ensure_adjoint(c);
     int zero = 0;
     ck(cudaMemcpyAsync(&c->scal->timeout, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    // forward internals of the step at X^n
+    // forward internals of the step at X^n: only the predictor state X* is
+    // needed (the linearisation point of N(X*)); N(X*) itself is not, since
+    // the corrector stage is linear in its right-hand side and the adjoint
+    // of the nonlinear stage recomputes its own transforms of X*
     launch_nonlinear(c, Xn, c->N0, nullptr, 0);
     launch_dt_policy(c, dt, -1);
     launch_refactor(c);
     launch_rhs(c, Xn, c->N0);
     launch_stage(c, c->N0, c->Xp, c->P);
-    launch_nonlinear(c, c->Xp, c->N1, nullptr, 0);
     // reverse sweep
     launch_stage_adjoint(c, lam, c->Rb);                    // corrector stage
     launch_stage_split_adjoint(c, c->Rb, c->Ybar, c->Nb, 0);
