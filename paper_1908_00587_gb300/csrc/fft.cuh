@@ -172,22 +172,31 @@ __host__ __device__ __forceinline__ bool zmid_ok(const FFTPlan &pl, int B) {
   return pl.npass > 0 && pl.radix[0] == 8 && 8 * B < 3 * pl.n;
 }
 
-// One Stockham pass over `batch` transforms stored `bstride` apart.
-// tw[t] = exp(-2 pi i t / N).
+__device__ __forceinline__ int fdiv(int n, FastDiv f) {
+  const unsigned u = (unsigned)n;
+  const unsigned t = __umulhi(f.m, u);
+  return (int)((t + ((u - t) >> f.s1)) >> f.s2);
+}
+
+// One Stockham pass (pass p of plan pl, stride Ns) over `batch` transforms
+// stored `bstride` apart.  twp: this pass's twiddles, w^(q k) at (q-1) Ns + k,
+// so the threads of a warp (consecutive k) read consecutive entries.  The
+// index arithmetic divides by the plan's fixed divisors with FastDiv.
 // ZMID (radix 8, first pass only): inputs q = 3, 4 are known zeros.
 template <int R, int S, bool ZMID, typename V>
 __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__restrict__ dst,
-                                              int N, int Ns, int batch, int bstride,
-                                              const V *__restrict__ tw) {
+                                              const FFTPlan &pl, int p, int Ns, int batch,
+                                              int bstride, const V *__restrict__ twp) {
+  const int N = pl.n;
   const int nb = N / R;
   const int total = nb * batch;
-  const int twstep = N / (Ns * R);
+  const FastDiv dnb = pl.div_nb[p], dns = pl.div_ns[p];
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int b = t / nb;
+    const int b = fdiv(t, dnb);
     const int j = t - b * nb;
     const V *s = src + b * bstride;
     V *d = dst + b * bstride;
-    const int k = j % Ns;
+    const int k = j - fdiv(j, dns) * Ns;
     V v[R];
 #pragma unroll
     for (int q = 0; q < R; ++q)
@@ -202,7 +211,7 @@ __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__re
     if (Ns > 1) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        const V w = tw[q * k * twstep];
+        const V w = twp[(q - 1) * Ns + k];
         v[q] = (S < 0) ? cmul(v[q], w) : cmulc(v[q], w);
       }
     }
@@ -214,7 +223,7 @@ __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__re
 }
 
 // Full transform of `batch` sequences held in buffer a (b is scratch of the
-// same size).  Returns the buffer holding the result.  All threads of the CTA
+// same size); tw: the plan's pass-major twiddle table (fill_plan_twiddles).  Returns the buffer holding the result.  All threads of the CTA
 // must call it; it ends with a __syncthreads().  zmid: the caller guarantees
 // that every input vanishes on [3N/8, 5N/8) and the plan starts with radix 8
 // (see zmid_ok); the first pass then skips those inputs.
@@ -224,15 +233,16 @@ __device__ V *fft_batch(V *a, V *b, const FFTPlan &pl, int batch, int bstride,
   int Ns = 1;
   for (int p = 0; p < pl.npass; ++p) {
     const int R = pl.radix[p];
+    const V *twp = tw + pl.tw_off[p];
     if (p == 0 && zmid) {
-      stockham_pass<8, S, true>(a, b, pl.n, Ns, batch, bstride, tw);
+      stockham_pass<8, S, true>(a, b, pl, p, Ns, batch, bstride, twp);
     } else {
       switch (R) {
-        case 8: stockham_pass<8, S, false>(a, b, pl.n, Ns, batch, bstride, tw); break;
-        case 4: stockham_pass<4, S, false>(a, b, pl.n, Ns, batch, bstride, tw); break;
-        case 2: stockham_pass<2, S, false>(a, b, pl.n, Ns, batch, bstride, tw); break;
-        case 3: stockham_pass<3, S, false>(a, b, pl.n, Ns, batch, bstride, tw); break;
-        default: stockham_pass<5, S, false>(a, b, pl.n, Ns, batch, bstride, tw); break;
+        case 8: stockham_pass<8, S, false>(a, b, pl, p, Ns, batch, bstride, twp); break;
+        case 4: stockham_pass<4, S, false>(a, b, pl, p, Ns, batch, bstride, twp); break;
+        case 2: stockham_pass<2, S, false>(a, b, pl, p, Ns, batch, bstride, twp); break;
+        case 3: stockham_pass<3, S, false>(a, b, pl, p, Ns, batch, bstride, twp); break;
+        default: stockham_pass<5, S, false>(a, b, pl, p, Ns, batch, bstride, twp); break;
       }
     }
     __syncthreads();

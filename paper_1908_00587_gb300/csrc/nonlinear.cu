@@ -34,6 +34,12 @@ __device__ __forceinline__ int kpos(int kk, int K, int NK, int Nz) {
   return kk <= K ? kk : Nz - NK + kk;
 }
 
+// n / d and n % d for a divisor with a precomputed FastDiv.
+__device__ __forceinline__ int2 divmod(int n, int d, FastDiv f) {
+  const int q = fdiv(n, f);
+  return int2{q, n - q * d};
+}
+
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *p, double v) {
   // non-negative doubles order like their bit patterns
   atomicMax(p, (unsigned long long)__double_as_longlong(v));
@@ -142,8 +148,9 @@ __global__ void k_zinv(const double2 *__restrict__ X, V2<T> *__restrict__ Vout, 
   __syncthreads();
   const int st = p.rad.s0[r];
   const double *d1 = p.rad.D1 + r * kStencil;
+  const FastDiv fnm = (nm == p.MB) ? p.fMB : p.fMBl;
   for (int t = threadIdx.x; t < nm * s.NK; t += blockDim.x) {
-    const int mi = t / s.NK;
+    const int mi = fdiv(t, p.fNK);
     const int kk = t - mi * s.NK;
     const long long col = (long long)(m0 + mi) * s.NK + kk;
     const double2 *Xc = X + (long long)c * s.S;
@@ -168,10 +175,11 @@ __global__ void k_zinv(const double2 *__restrict__ X, V2<T> *__restrict__ Vout, 
   __syncthreads();
   V2<T> *res = fft_batch<+1>(A, B, p.pz, 3 * nm, Np, tw, zmid_ok(p.pz, s.K));
   for (int t = threadIdx.x; t < 3 * nm * Nz; t += blockDim.x) {
-    const int mi = t % nm;
-    const int rest = t / nm;
-    const int l = rest % Nz;
-    const int d = rest / Nz;
+    const int2 a = divmod(t, nm, fnm);
+    const int mi = a.y;
+    const int2 b = divmod(a.x, Nz, p.fNz);
+    const int l = b.y;
+    const int d = b.x;
     Vout[(((long long)(3 * c + d) * s.Nr + r) * Nz + l) * s.NM + m0 + mi] = res[(3 * mi + d) * Np + spad(l)];
   }
 }
@@ -198,10 +206,11 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   __syncthreads();
   // pack: buffer (li, c, 0) = value + i dtheta, (li, c, 1) = d/dr + i d/dz
   for (int t = threadIdx.x; t < nl * s.nf * s.NM; t += blockDim.x) {
-    const int m = t % s.NM;
-    const int rest = t / s.NM;
-    const int c = rest % s.nf;
-    const int li = rest / s.nf;
+    const int2 a = divmod(t, s.NM, p.fNM);
+    const int m = a.y;
+    const int2 b = divmod(a.x, s.nf, p.fnf);
+    const int c = b.y;
+    const int li = b.x;
     const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
     const long long fs = (long long)s.Nr * s.Nz * s.NM;
     V2<T> v = Vin[(3 * c + 0) * fs + off];
@@ -237,8 +246,9 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   double nu = 0.0, nT = 0.0;
   auto bits = [](double v) { return (unsigned long long)__double_as_longlong(fabs(v)); };
   for (int t = threadIdx.x; t < nl * Nt; t += blockDim.x) {
-    const int j = t % Nt;
-    const int li = t / Nt;
+    const int2 a = divmod(t, Nt, p.fNt);
+    const int j = a.y;
+    const int li = a.x;
     const V2<T> *b = ph + li * npair * Ntp + spad(j);
     const V2<T> r0 = b[0 * Ntp], r1 = b[1 * Ntp];   // (ur, ur_t), (ur_r, ur_z)
     const V2<T> t0 = b[2 * Ntp], t1 = b[3 * Ntp];   // (ut, ut_t), (ut_r, ut_z)
@@ -304,11 +314,12 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   // unpack two real transforms: X_m = (Z_m + conj Z_-m)/2, Y_m = (Z_m - conj Z_-m)/(2i)
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
   for (int t = threadIdx.x; t < nl * s.NM; t += blockDim.x) {
-    const int m = t % s.NM;
-    const int li = t / s.NM;
+    const int2 a = divmod(t, s.NM, p.fNM);
+    const int m = a.y;
+    const int li = a.x;
     const V2<T> *z0 = sp + li * 2 * Ntp;
     const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
-    const int mm = (Nt - m) % Nt;
+    const int mm = m == 0 ? 0 : Nt - m;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const V2<T> a = z0[h * Ntp + spad(m)];
@@ -337,21 +348,24 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
   V2<T> *tw = B + s.nf * p.MB * Np;
   load_tw<T>(tw, p.twz, Nz);
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
+  const FastDiv fnm = (nm == p.MB) ? p.fMB : p.fMBl;
   for (int t = threadIdx.x; t < nb * Nz; t += blockDim.x) {
-    const int mi = t % nm;
-    const int rest = t / nm;
-    const int l = rest % Nz;
-    const int g = rest / Nz;
+    const int2 a = divmod(t, nm, fnm);
+    const int mi = a.y;
+    const int2 b = divmod(a.x, Nz, p.fNz);
+    const int l = b.y;
+    const int g = b.x;
     A[(g * nm + mi) * Np + spad(l)] = W[g * fs + ((long long)r * Nz + l) * s.NM + m0 + mi];
   }
   __syncthreads();
   V2<T> *res = fft_batch<-1>(A, B, p.pz, nb, Np, tw);
   const double scale = 1.0 / ((double)s.Nt * (double)s.Nz);
   for (int t = threadIdx.x; t < nb * s.NK; t += blockDim.x) {
-    const int kk = t % s.NK;
-    const int rest = t / s.NK;
-    const int mi = rest % nm;
-    const int g = rest / nm;
+    const int2 a = divmod(t, s.NK, p.fNK);
+    const int kk = a.y;
+    const int2 b = divmod(a.x, nm, fnm);
+    const int mi = b.y;
+    const int g = b.x;
     const V2<T> v = res[(g * nm + mi) * Np + spad(kpos(kk, s.K, s.NK, Nz))];
     double2 out = double2{(double)v.x * scale, (double)v.y * scale};
     if (p.mixed) {
@@ -364,6 +378,18 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
 }
 
 }  // namespace
+
+void set_divisors(NLParams &p) {
+  const Sizes &s = p.sz;
+  p.fNK = make_fastdiv((unsigned)s.NK);
+  p.fNM = make_fastdiv((unsigned)s.NM);
+  p.fNt = make_fastdiv((unsigned)s.Nt);
+  p.fNz = make_fastdiv((unsigned)s.Nz);
+  p.fnf = make_fastdiv((unsigned)s.nf);
+  p.fMB = make_fastdiv((unsigned)p.MB);
+  const int last = s.NM - ((s.NM - 1) / p.MB) * p.MB;   // width of the last m-block
+  p.fMBl = make_fastdiv((unsigned)last);
+}
 
 void setup_nonlinear(tc_ctx *c) {
   NLParams &p = c->nl;
@@ -400,6 +426,8 @@ void setup_nonlinear(tc_ctx *c) {
   if (c->tile_lb > 0) LB32 = c->tile_lb;
   q.MB = MB32;
   q.LB = LB32;
+  set_divisors(p);
+  set_divisors(q);
   c->smem32_zinv = (size_t)(2 * 3 * MB32 * padlen(s.Nz) + s.Nz) * e32;
   c->smem32_theta = (size_t)(2 * LB32 * 2 * s.nf * padlen(s.Nt) + s.Nt) * e32;
   c->smem32_zfwd = (size_t)(2 * s.nf * MB32 * padlen(s.Nz) + s.Nz) * e32;
@@ -553,6 +581,7 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
   LB = LB < 1 ? 1 : (LB > 8 ? 8 : LB);
   p.MB = MB;
   p.LB = LB;
+  set_divisors(p);
   const size_t e = sizeof(double2);
   const size_t sm_zinv = (size_t)(2 * 3 * MB * padlen(s.Nz) + s.Nz) * e;
   const size_t sm_theta = (size_t)(2 * LB * 2 * s.nf * padlen(s.Nt) + s.Nt) * e;
@@ -595,8 +624,8 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
     const double hi = j < Nr - 1 ? r[j + 1] - r[j] : 1e300;
     drm[j] = std::min(lo, hi);
   }
-  fill_twiddles(Nz, reinterpret_cast<double2 *>(host + L.twz));
-  fill_twiddles(Ntheta, reinterpret_cast<double2 *>(host + L.twt));
+  fill_plan_twiddles(make_plan(Nz), reinterpret_cast<double2 *>(host + L.twz));
+  fill_plan_twiddles(make_plan(Ntheta), reinterpret_cast<double2 *>(host + L.twt));
   *reinterpret_cast<unsigned long long *>(host + L.rate) = 0ull;   // CFL slot starts at zero
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -761,8 +790,9 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
   const double ir = p.rad.inv_r[r];
   const double sc = 1.0 / ((double)s.Nt * (double)s.Nz);
   for (int t = threadIdx.x; t < nl * Nt; t += blockDim.x) {
-    const int j = t % Nt;
-    const int li = t / Nt;
+    const int2 a = divmod(t, Nt, p.fNt);
+    const int j = a.y;
+    const int li = a.x;
     const double2 *b = ph + li * npair * Ntp + spad(j);
     const double2 r0 = b[0 * Ntp], r1 = b[1 * Ntp];   // (ur, ur_t), (ur_r, ur_z)
     const double2 t0 = b[2 * Ntp], t1 = b[3 * Ntp];
@@ -806,10 +836,11 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
   double2 *scratch = (out == A) ? B : A;
   double2 *sp = fft_batch<-1>(out, scratch, p.pt, nl * nfw, Ntp, tw);
   for (int t = threadIdx.x; t < nl * s.nf * s.NM; t += blockDim.x) {
-    const int m = t % s.NM;
-    const int rest = t / s.NM;
-    const int c = rest % s.nf;
-    const int li = rest / s.nf;
+    const int2 q1 = divmod(t, s.NM, p.fNM);
+    const int m = q1.y;
+    const int2 q2 = divmod(q1.x, s.nf, p.fnf);
+    const int c = q2.y;
+    const int li = q2.x;
     const double cm = (m == 0) ? 1.0 : 2.0;
     const int mm = (Nt - m) % Nt;
     const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;

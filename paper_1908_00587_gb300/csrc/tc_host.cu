@@ -99,8 +99,26 @@ FFTPlan make_plan(int n) {
     m /= 5;
   }
   p.npass = (int)rs.size();
-  for (int i = 0; i < p.npass; ++i) p.radix[i] = rs[i];
+  int Ns = 1, off = 0;
+  for (int i = 0; i < p.npass; ++i) {
+    p.radix[i] = rs[i];
+    p.tw_off[i] = off;
+    if (Ns > 1) off += (rs[i] - 1) * Ns;
+    p.div_nb[i] = make_fastdiv((unsigned)(n / rs[i]));
+    p.div_ns[i] = make_fastdiv((unsigned)Ns);
+    Ns *= rs[i];
+  }
   return p;
+}
+
+FastDiv make_fastdiv(unsigned d) {
+  int l = 0;   // ceil(log2 d)
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l - 1 > 0 ? l - 1 : 0;
+  return f;
 }
 
 // Finite-difference weights at x0 on nodes x[0..n-1] for derivatives 0..2
@@ -130,12 +148,25 @@ void fd_weights(double x0, const double *x, int n, double w[3][kStencil]) {
   }
 }
 
-// exp(-2 pi i t / n), t = 0..n-1, evaluated in long double.
-void fill_twiddles(int n, double2 *out) {
+// Pass-major twiddles of a plan, each exp(-2 pi i t / n) with t = q k n/(Ns R)
+// evaluated in long double.
+void fill_plan_twiddles(const FFTPlan &pl, double2 *out) {
   const long double pi = 3.141592653589793238462643383279502884L;
-  for (int i = 0; i < n; ++i) {
-    const long double a = 2.0L * pi * (long double)i / (long double)n;
-    out[i] = double2{(double)cosl(a), (double)(-sinl(a))};
+  const int n = pl.n;
+  for (int i = 0; i < n; ++i) out[i] = double2{0.0, 0.0};
+  int Ns = 1;
+  for (int p = 0; p < pl.npass; ++p) {
+    const int R = pl.radix[p];
+    if (Ns > 1) {
+      const int step = n / (Ns * R);
+      for (int q = 1; q < R; ++q)
+        for (int k = 0; k < Ns; ++k) {
+          const long long t = (long long)q * k * step;
+          const long double a = 2.0L * pi * (long double)(t % n) / (long double)n;
+          out[pl.tw_off[p] + (q - 1) * Ns + k] = double2{(double)cosl(a), (double)(-sinl(a))};
+        }
+    }
+    Ns *= R;
   }
 }
 
@@ -194,9 +225,9 @@ std::vector<double> dense_solve(std::vector<double> A, std::vector<double> b, in
   return x;
 }
 
-std::vector<double2> twiddles(int n) {
-  std::vector<double2> t(n);
-  fill_twiddles(n, t.data());
+std::vector<double2> twiddles(const FFTPlan &pl) {
+  std::vector<double2> t(pl.n);
+  fill_plan_twiddles(pl, t.data());
   return t;
 }
 
@@ -380,7 +411,7 @@ void upload_tables(tc_ctx *c) {
   ck(cudaMemcpy(c->d_dr, c->dr_min.data(), s.Nr * sizeof(double), cudaMemcpyHostToDevice));
   ck(cudaMemcpy(c->d_wr, wr.data(), s.Nr * sizeof(double), cudaMemcpyHostToDevice));
   ck(cudaMemcpy(c->d_s0, c->s0.data(), s.Nr * sizeof(int), cudaMemcpyHostToDevice));
-  std::vector<double2> tz = twiddles(s.Nz), tt = twiddles(s.Nt);
+  std::vector<double2> tz = twiddles(make_plan(s.Nz)), tt = twiddles(make_plan(s.Nt));
   ck(cudaMemcpy(c->d_twz, tz.data(), s.Nz * sizeof(double2), cudaMemcpyHostToDevice));
   ck(cudaMemcpy(c->d_twt, tt.data(), s.Nt * sizeof(double2), cudaMemcpyHostToDevice));
   ck(cudaMemcpy(c->diag_part + (size_t)s.Nr * 6, c->Tb_disc.data(), s.Nr * sizeof(double),

@@ -20,17 +20,32 @@ constexpr int kSweepRows = 16;    // rows per staged chunk of band factors
 constexpr int kSweepOps = 16;     // operators (|k| values) per sweep CTA
 constexpr int kSweepStages = 3;   // depth of the shared-memory ring
 
+// Division by a divisor fixed at set-up: q = (t + ((n - t) >> s1)) >> s2 with
+// t = umulhi(m, n) (Granlund & Montgomery, "Division by invariant integers
+// using multiplication", 1994), exact for every 32-bit n.
+struct FastDiv {
+  unsigned m;
+  int s1, s2;
+};
+
 struct FFTPlan {
   int n;
   int npass;
   int radix[16];
+  // twiddles of pass p (Ns > 1): w^(q k) for q = 1..R-1, k = 0..Ns-1 at
+  // tw_off[p] + (q - 1) Ns + k, w = exp(-2 pi i / (Ns R)); n - 1 entries in all
+  int tw_off[16];
+  FastDiv div_nb[16];   // division by n / radix[p]
+  FastDiv div_ns[16];   // division by Ns of pass p
 };
 
+FastDiv make_fastdiv(unsigned d);
 FFTPlan make_plan(int n);
+// Pass-major twiddle table of a plan: n entries (the last one unused).
+void fill_plan_twiddles(const FFTPlan &pl, double2 *out);
 
 // Host helpers shared by the set-up code (tc_host.cu).
 void fd_weights(double x0, const double *x, int n, double w[3][kStencil]);
-void fill_twiddles(int n, double2 *out);
 
 // Problem sizes.
 struct Sizes {
@@ -78,14 +93,18 @@ struct NLParams {
   int MB;               // m columns per CTA in the z kernels
   int LB;               // z rows per CTA in the theta kernel
   FFTPlan pz, pt;
-  const double2 *twz, *twt;   // exp(-2 pi i t / N) tables (FP64 master copy)
+  const double2 *twz, *twt;   // pass-major twiddle tables of pz, pt (FP64 master copy)
   // mixed precision: the transforms carry only the perturbation u' = u - U(r)
   // (FP32); the products with the mean mode U are added in FP64 in k_zfwd
   int mixed;
   const double2 *Xfull;       // state (mixed only)
   const double *prof;         // [r][8]: U_theta, U_z, dU_theta/dr, dU_z/dr, dTbar/dr, T mean
   double eps_c;               // centrifugal buoyancy: advection weighted by 1 - eps_c T (FP64 only)
+  // fixed divisors of the element loops (set_divisors): NK, NM, Nt, Nz, nf,
+  // MB and the last m-block's width
+  FastDiv fNK, fNM, fNt, fNz, fnf, fMB, fMBl;
 };
+void set_divisors(NLParams &p);
 
 // Parameters of the linear stage.
 struct LinParams {
