@@ -50,6 +50,8 @@ def parse():
                     help="override the workload's precision (0 FP64, 1 mixed)")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the differentiation-form measurement")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="benchmark the batched form: N uneven runs replayed as one graph")
     return ap.parse_args()
@@ -344,6 +346,8 @@ def run_gb300(args):
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
             "kernels": kernels}
     run.close()
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_throughput(tc, torch, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, el, cores, sample = oracle_throughput(wl, budget_s=15.0)
         line["cpu_baseline"] = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
@@ -353,6 +357,62 @@ def run_gb300(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def adjoint_throughput(tc, torch, flush, steps=200, checkpoint=20, timed_adj=50):
+    """Differentiation form on its own workload (64^3, FP64, fixed dt).
+
+    (1) the discrete adjoint step alone: tc_adjoint_step from a stored state,
+    CUDA events per step on the context's stream, L2 flushed between steps;
+    (2) one whole gradient of J = E_pert(T) over `steps` steps: forward with
+    a checkpoint every `checkpoint` steps, then per segment recompute and
+    adjoint steps back (the autograd.Function path), wall clock with a device
+    synchronisation at both ends.  Both in grid-point-steps/s, the second
+    counting the `steps` steps of the differentiated window."""
+    from paper_1908_00587_gb300.autograd import perturbation_energy
+
+    wl = WORKLOADS["tc_adjoint_nr64_n64"]
+    run = tc.Run.from_workload(wl)
+    stream = torch.cuda.current_stream()
+    run.set_stream(stream.cuda_stream)
+    run.init_perturbation(psi_coefficients(wl.seed, wl.mp, wl.kp), wl.amp)
+    X = torch.empty(run.shape, dtype=torch.complex128, device="cuda")
+    tc.tc_get_state(run.ctx, X)
+    lam = torch.empty_like(X)
+    tc.tc_objective(run.ctx, lam)
+    for _ in range(3):
+        tc.tc_adjoint_step(run.ctx, X, wl.dt, lam)
+    ks = [torch.cuda.Event(enable_timing=True) for _ in range(timed_adj)]
+    ke = [torch.cuda.Event(enable_timing=True) for _ in range(timed_adj)]
+    torch.cuda.synchronize()
+    for i in range(timed_adj):
+        flush.fill_(i & 0xFF)
+        ks[i].record(stream)
+        tc.tc_adjoint_step(run.ctx, X, wl.dt, lam)
+        ke[i].record(stream)
+    torch.cuda.synchronize()
+    adj_ms = sum(a.elapsed_time(b) for a, b in zip(ks, ke)) / timed_adj
+    # whole gradient through the autograd.Function
+    psi = torch.from_numpy(psi_coefficients(wl.seed, wl.mp, wl.kp)).requires_grad_(True)
+    J = perturbation_energy(run, psi, 2, wl.dt, wl.amp, checkpoint=checkpoint)
+    J.backward()                          # warm-up of the whole path
+    psi.grad = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = perturbation_energy(run, psi, steps, wl.dt, wl.amp, checkpoint=checkpoint)
+    J.backward()
+    torch.cuda.synchronize()
+    grad_s = time.perf_counter() - t0
+    run.close()
+    return {"workload": f"{wl.name}: Nr={wl.Nr} Ntheta={wl.Ntheta} Nz={wl.Nz} eta={wl.eta} "
+                        f"Re_i={wl.Re_i} dt={wl.dt}",
+            "adjoint_step": {"value": wl.points / (adj_ms * 1e-3), "unit": METRIC,
+                             "ms_per_step": adj_ms, "steps": timed_adj,
+                             "l2": "flushed between timed steps"},
+            "gradient": {"value": wl.points * steps / grad_s, "unit": METRIC,
+                         "seconds": grad_s, "steps": steps, "checkpoint_every": checkpoint,
+                         "includes": "forward with checkpoints, per-segment recompute, "
+                                     "adjoint steps, host-side psi marshalling"}}
 
 
 def run_ensemble(args):

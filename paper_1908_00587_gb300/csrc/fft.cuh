@@ -183,42 +183,47 @@ __device__ __forceinline__ int fdiv(int n, FastDiv f) {
 // so the threads of a warp (consecutive k) read consecutive entries.  The
 // index arithmetic divides by the plan's fixed divisors with FastDiv.
 // ZMID (radix 8, first pass only): inputs q = 3, 4 are known zeros.
+// Butterfly j of one transform, s -> d (both the transform's own storage).
+template <int R, int S, bool ZMID, typename V>
+__device__ __forceinline__ void butterfly(const V *__restrict__ s, V *__restrict__ d, int j,
+                                          int nb, int Ns, FastDiv dns,
+                                          const V *__restrict__ twp) {
+  const int k = j - fdiv(j, dns) * Ns;
+  V v[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q)
+    if (!ZMID || (q != 3 && q != 4)) v[q] = s[spad(j + q * nb)];
+  if (ZMID) {
+    if constexpr (R == 8) dft8_zmid<S>(v);
+    const int base = j * R;   // Ns = 1
+#pragma unroll
+    for (int p = 0; p < R; ++p) d[spad(base + p)] = v[p];
+    return;
+  }
+  if (Ns > 1) {
+#pragma unroll
+    for (int q = 1; q < R; ++q) {
+      const V w = twp[(q - 1) * Ns + k];
+      v[q] = (S < 0) ? cmul(v[q], w) : cmulc(v[q], w);
+    }
+  }
+  dftR<R, S>(v);
+  const int base = (j - k) * R + k;
+#pragma unroll
+  for (int p = 0; p < R; ++p) d[spad(base + p * Ns)] = v[p];
+}
+
 template <int R, int S, bool ZMID, typename V>
 __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__restrict__ dst,
                                               const FFTPlan &pl, int p, int Ns, int batch,
                                               int bstride, const V *__restrict__ twp) {
-  const int N = pl.n;
-  const int nb = N / R;
+  const int nb = pl.n / R;
   const int total = nb * batch;
   const FastDiv dnb = pl.div_nb[p], dns = pl.div_ns[p];
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int b = fdiv(t, dnb);
     const int j = t - b * nb;
-    const V *s = src + b * bstride;
-    V *d = dst + b * bstride;
-    const int k = j - fdiv(j, dns) * Ns;
-    V v[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q)
-      if (!ZMID || (q != 3 && q != 4)) v[q] = s[spad(j + q * nb)];
-    if (ZMID) {
-      if constexpr (R == 8) dft8_zmid<S>(v);
-      const int base = j * R;   // Ns = 1
-#pragma unroll
-      for (int p = 0; p < R; ++p) d[spad(base + p)] = v[p];
-      continue;
-    }
-    if (Ns > 1) {
-#pragma unroll
-      for (int q = 1; q < R; ++q) {
-        const V w = twp[(q - 1) * Ns + k];
-        v[q] = (S < 0) ? cmul(v[q], w) : cmulc(v[q], w);
-      }
-    }
-    dftR<R, S>(v);
-    const int base = (j - k) * R + k;
-#pragma unroll
-    for (int p = 0; p < R; ++p) d[spad(base + p * Ns)] = v[p];
+    butterfly<R, S, ZMID>(src + b * bstride, dst + b * bstride, j, nb, Ns, dns, twp);
   }
 }
 
