@@ -57,6 +57,16 @@ def parse():
     return ap.parse_args()
 
 
+def measured_hbm_peak():
+    """Copy bandwidth measured on the GB300s (GB/s), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def config_of(wl, extra=None):
     cfg = {"workload": f"{wl.name}: Nr={wl.Nr} Ntheta={wl.Ntheta} Nz={wl.Nz} eta={wl.eta} "
                        f"Re_i={wl.Re_i} Re_o={wl.Re_o} Ra={wl.Ra} Pr={wl.Pr} "
@@ -330,6 +340,17 @@ def run_gb300(args):
         roof.update({"achieved": None, "frac": None})
     tr = traffic_for(dom)
     roof["traffic"] = tr
+    # the whole step against HBM: algorithmic bytes per grid-point-step (every
+    # spectral field pass read or written once: 44 passes with T, 33 without,
+    # of 16 B per stored coefficient, S/P coefficients per grid point)
+    S = wl.Nr * ((wl.Ntheta - 1) // 3 + 1) * (2 * ((wl.Nz - 1) // 3) + 1)
+    passes = 44 if wl.Ra else 33
+    alg_b = passes * 16.0 * S / wl.points
+    hbm_peak = measured_hbm_peak()
+    hbm = {"alg_bytes_per_point_step": alg_b, "achieved_GBs": alg_b * value / 1e9,
+           "peak_GBs": hbm_peak,
+           "frac": alg_b * value / 1e9 / hbm_peak if hbm_peak else None,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
     kernels = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in sorted(timing.items())}
     kernels["_pass"] = {"steps": kt_steps, "ms": round(kt_total_ms, 4)}
 
@@ -343,7 +364,8 @@ def run_gb300(args):
                                      "tiles_mb_lb": list(tiles),
                                      "launch": "one step captured as a CUDA graph, replayed per step",
                                      "stated_error": "rel L2 <= 1e-10 vs FP64 oracle"}),
-            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "hbm_of_step": hbm,
+            "clocks": clk,
             "kernels": kernels}
     run.close()
     if not args.no_adjoint:
