@@ -300,28 +300,31 @@ def run_gb300(args):
     value = wl.points * args.steps * world / (total_ms * 1e-3)
 
     # end to end through the public API with host buffers: state in from pinned
-    # host memory, one step, state out to pinned host memory
-    host = torch.empty(run.shape, dtype=torch.complex128, pin_memory=True).numpy()
-    run.get_state(host)
+    # host memory, one step, state out to pinned host memory (--e2e-steps 0
+    # skips it, for states too large to pin on the host)
+    e2e = None
     ne = min(args.e2e_steps, args.steps)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(ne):
-        run.set_state(host)
-        run.step(1, wl.dt)
+    if ne > 0:
+        host = torch.empty(run.shape, dtype=torch.complex128, pin_memory=True).numpy()
         run.get_state(host)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    state_bytes = int(np.prod(run.shape)) * 16
-    e2e = {"value": wl.points * ne * world / e2e_s, "unit": METRIC,
-           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-           "steps": ne}
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            run.set_state(host)
+            run.step(1, wl.dt)
+            run.get_state(host)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        state_bytes = int(np.prod(run.shape)) * 16
+        e2e = {"value": wl.points * ne * world / e2e_s, "unit": METRIC,
+               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+               "steps": ne}
 
     # roofline of the dominant kernel (FP64-ALU bound: see the design doc)
     dom = max(timing, key=lambda k: timing[k][1])
