@@ -98,6 +98,10 @@ typedef struct {
  * 0 < eta < 1; Lz > 0; Pr > 0 when Ra != 0.  Temperature is carried only when
  * Ra != 0.  The state starts as the discrete basic state: circular Couette
  * flow, and with Ra != 0 the conductive temperature and its steady axial flow.
+ * Each transform kernel holds a whole batch of sequences in shared memory
+ * (two buffers of 16 B per padded point, at most 227 KB per CTA), so the
+ * largest azimuthal size is 1000 without temperature and 750 with it (FP64,
+ * one z-row per CTA); larger sizes return TC_ERR_UNSUPPORTED.
  * Errors: TC_ERR_ARG, TC_ERR_UNSUPPORTED, TC_ERR_OOM, TC_ERR_CUDA. */
 tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz,
                     double Re_i, double Re_o, double Ra, double Pr, tc_ctx **out);
