@@ -250,6 +250,12 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     const int j = a.y;
     const int li = a.x;
     const V2<T> *b = ph + li * npair * Ntp + spad(j);
+    if constexpr (sizeof(T) == 8) {
+      if (p.phys_out) {   // keep the physical fields for the adjoint of this stage
+        double2 *o = p.phys_out + ((long long)r * s.Nz + l0 + li) * npair * Nt + j;
+        for (int q = 0; q < npair; ++q) o[q * Nt] = b[q * Ntp];
+      }
+    }
     const V2<T> r0 = b[0 * Ntp], r1 = b[1 * Ntp];   // (ur, ur_t), (ur_r, ur_z)
     const V2<T> t0 = b[2 * Ntp], t1 = b[3 * Ntp];   // (ut, ut_t), (ut_r, ut_z)
     const V2<T> z0 = b[4 * Ntp], z1 = b[5 * Ntp];   // (uz, uz_t), (uz_r, uz_z)
@@ -437,7 +443,7 @@ void setup_nonlinear(tc_ctx *c) {
 }
 
 void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long long *rate_bits,
-                      int mode) {
+                      int mode, double2 *phys_out) {
   const Sizes &s = c->sz;
   if (c->precision == 1 && mode == 0) {
     NLParams q = c->nl32;
@@ -462,7 +468,8 @@ void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long lon
         W, N, q);
     return;
   }
-  const NLParams &p = c->nl;
+  NLParams p = c->nl;
+  p.phys_out = phys_out;
   const int nmb = (s.NM + p.MB - 1) / p.MB;
   {
     LaunchScope ls(c, KZINV);
@@ -736,8 +743,12 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
   const int Nt = s.Nt;
   const int Ntp = padlen(Nt);
   const int nfw = 2 * s.nf;          // forward-field pairs per row
-  const int npair = nfw + 2;         // + cotangent pairs (Nr, Ntheta), (Nz, NT)
-  const int nbuf = p.LB * npair;
+  // transformed here per row: the forward pairs (unless phys_in holds them)
+  // and the cotangent pairs (N_r, N_theta), (N_z, N_T)
+  const bool cached = p.phys_in != nullptr;
+  const int npair = cached ? 2 : nfw + 2;
+  const int cot0 = cached ? 0 : nfw;   // first cotangent pair of a row
+  const int nbuf = p.LB * (nfw + 2);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2 *A = reinterpret_cast<double2 *>(smem_raw);
   double2 *B = A + nbuf * Ntp;
@@ -746,11 +757,12 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
   for (int i = threadIdx.x; i < nl * npair * Ntp; i += blockDim.x) A[i] = double2{0, 0};
   __syncthreads();
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
-  for (int t = threadIdx.x; t < nl * (s.nf + 2) * s.NM; t += blockDim.x) {
-    const int m = t % s.NM;
-    const int rest = t / s.NM;
-    const int c = rest % (s.nf + 2);
-    const int li = rest / (s.nf + 2);
+  const int nin = cached ? 2 : s.nf + 2;   // inputs per row: components, then 2 cotangent pairs
+  for (int t = threadIdx.x; t < nl * nin * s.NM; t += blockDim.x) {
+    const int2 q1 = divmod(t, s.NM, p.fNM);
+    const int m = q1.y;
+    const int li = q1.x / nin;
+    const int c = q1.x - li * nin + (cached ? s.nf : 0);
     const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
     double2 a, b, e, f;
     double2 *b0, *b1;
@@ -774,7 +786,7 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
         a.y = 0.0;
         b.y = 0.0;
       }
-      b0 = A + (li * npair + nfw + h) * Ntp;
+      b0 = A + (li * npair + cot0 + h) * Ntp;
       b1 = nullptr;
     }
     b0[spad(m)] = double2{a.x - b.y, a.y + b.x};
@@ -794,10 +806,13 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
     const int j = a.y;
     const int li = a.x;
     const double2 *b = ph + li * npair * Ntp + spad(j);
-    const double2 r0 = b[0 * Ntp], r1 = b[1 * Ntp];   // (ur, ur_t), (ur_r, ur_z)
-    const double2 t0 = b[2 * Ntp], t1 = b[3 * Ntp];
-    const double2 z0 = b[4 * Ntp], z1 = b[5 * Ntp];
-    const double2 nb0 = b[nfw * Ntp], nb1 = b[(nfw + 1) * Ntp];
+    // forward pairs: from this kernel's transforms, or the stored physical fields
+    const double2 *f = cached ? p.phys_in + ((long long)r * s.Nz + l0 + li) * nfw * Nt + j : b;
+    const int fst = cached ? Nt : Ntp;
+    const double2 r0 = f[0 * fst], r1 = f[1 * fst];   // (ur, ur_t), (ur_r, ur_z)
+    const double2 t0 = f[2 * fst], t1 = f[3 * fst];
+    const double2 z0 = f[4 * fst], z1 = f[5 * fst];
+    const double2 nb0 = b[cot0 * Ntp], nb1 = b[(cot0 + 1) * Ntp];
     const double ar = sc * nb0.x, at = sc * nb0.y, az = sc * nb1.x, aT = sc * nb1.y;
     const double ur = r0.x, ut = t0.x, uz = z0.x;
     const double vt = ut * ir;
@@ -811,7 +826,7 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
     const double guzr = -ur * az, guzt = -vt * az, guzz = -uz * az;
     double gT = 0.0, gTr = 0.0, gTt = 0.0, gTz = 0.0;
     if (s.nf == 4) {
-      const double2 T0 = b[6 * Ntp], T1 = b[7 * Ntp];
+      const double2 T0 = f[6 * fst], T1 = f[7 * fst];
       gur -= T1.x * aT;
       gut -= (T0.y * ir) * aT;
       guz -= T1.y * aT;
@@ -949,17 +964,18 @@ void setup_nonlinear_adjoint(tc_ctx *c) {
 }
 
 void launch_nonlinear_adjoint(tc_ctx *c, const double2 *X, const double2 *Nb, double2 *Xb,
-                              int accumulate) {
+                              int accumulate, const double2 *phys_in) {
   const Sizes &s = c->sz;
   NLParams p = c->nl;
   p.LB = adjoint_lb(c);
+  p.phys_in = phys_in;
   const size_t e = sizeof(double2);
   c->smem_adj_zinv = (size_t)(2 * s.nf * p.MB * padlen(s.Nz) + s.Nz) * e;
   c->smem_adj_theta = (size_t)(2 * p.LB * (2 * s.nf + 2) * padlen(s.Nt) + s.Nt) * e;
   c->smem_adj_zfwd = (size_t)(2 * 3 * p.MB * padlen(s.Nz) + s.Nz) * e;
   const int nmb = (s.NM + p.MB - 1) / p.MB;
   const int nlb = (s.Nz + p.LB - 1) / p.LB;
-  {
+  if (!phys_in) {   // the forward fields of X, unless stored by the forward pass
     LaunchScope ls(c, KZINV);
     k_zinv<double><<<dim3(nmb, s.Nr, s.nf), 256, c->smem_zinv, c->stream>>>(X, c->V, p);
   }

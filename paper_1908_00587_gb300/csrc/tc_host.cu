@@ -1027,6 +1027,7 @@ void ensure_adjoint(tc_ctx *c) {
   c->Ybar = dalloc<double2>(c, (size_t)s.nf * s.S);
   c->Nb = dalloc<double2>(c, (size_t)s.nf * s.S);
   c->Xb = dalloc<double2>(c, (size_t)s.nf * s.S);
+  c->Phys = dalloc<double2>(c, (size_t)s.Nr * s.Nz * 2 * s.nf * s.Nt);
   setup_nonlinear_adjoint(c);
 }
 
@@ -1052,7 +1053,7 @@ tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *a
     // needed (the linearisation point of N(X*)); N(X*) itself is not, since
     // the corrector stage is linear in its right-hand side and the adjoint
     // of the nonlinear stage recomputes its own transforms of X*
-    launch_nonlinear(c, Xn, c->N0, nullptr, 0);
+    launch_nonlinear(c, Xn, c->N0, nullptr, 0, c->Phys);   // keeps the physical fields of X^n
     launch_dt_policy(c, dt, -1);
     launch_refactor(c);
     launch_rhs(c, Xn, c->N0);
@@ -1064,7 +1065,7 @@ tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *a
     launch_stage_adjoint(c, c->Xb, c->Rb);                  // predictor stage
     launch_stage_split_adjoint(c, c->Rb, c->Ybar, c->Nb, 1);
     launch_rhs_adjoint(c, c->Ybar, lam, c->Nb);
-    launch_nonlinear_adjoint(c, Xn, c->Nb, lam, 1);          // N(X^n)
+    launch_nonlinear_adjoint(c, Xn, c->Nb, lam, 1, c->Phys);  // N(X^n)
     launch_herm_project(c, lam);
     ck(cudaGetLastError());
     int to = 0;

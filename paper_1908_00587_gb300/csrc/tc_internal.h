@@ -103,6 +103,12 @@ struct NLParams {
   // fixed divisors of the element loops (set_divisors): NK, NM, Nt, Nz, nf,
   // MB and the last m-block's width
   FastDiv fNK, fNM, fNt, fNz, fnf, fMB, fMBl;
+  // physical-grid fields of the forward transforms, [r][z][2 nf][Nt] complex
+  // pairs (value + i d/dtheta, d/dr + i d/dz per component): k_theta writes
+  // them when phys_out is set, the adjoint theta kernel reads them instead of
+  // transforming the state again when phys_in is set (FP64 only)
+  double2 *phys_out;
+  const double2 *phys_in;
 };
 void set_divisors(NLParams &p);
 
@@ -176,7 +182,7 @@ struct tc_ctx {
   size_t smem32_zinv = 0, smem32_theta = 0, smem32_zfwd = 0;
   // adjoint buffers (allocated on first use)
   double2 *Va = nullptr, *Gdr = nullptr, *Rb = nullptr, *Ybar = nullptr, *Nb = nullptr,
-          *Xb = nullptr;
+          *Xb = nullptr, *Phys = nullptr;
   size_t smem_adj_zinv = 0, smem_adj_theta = 0, smem_adj_zfwd = 0;
   double ic_su = 0.0, ic_sT = 0.0;   // scales frozen by tc_init_perturbation
   tc::LinParams lin;
@@ -235,7 +241,7 @@ cudaError_t ensure_step_graph(tc_ctx *c, double dt_fixed);
 
 // nonlinear.cu
 void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long long *rate_bits,
-                      int mode);
+                      int mode, double2 *phys_out = nullptr);
 void setup_nonlinear(tc_ctx *c);
 
 // linear.cu
@@ -256,8 +262,10 @@ void launch_rhs_adjoint(tc_ctx *c, const double2 *Ybar, double2 *Xb, double2 *Nb
 void launch_herm_project(tc_ctx *c, double2 *X);
 void launch_objective_grad(tc_ctx *c, const double2 *X, double2 *G);
 void setup_nonlinear_adjoint(tc_ctx *c);
+// phys_in (nullable): the forward physical fields of X written by
+// launch_nonlinear(..., phys_out) on the same X.
 void launch_nonlinear_adjoint(tc_ctx *c, const double2 *X, const double2 *Nb, double2 *Xb,
-                              int accumulate);
+                              int accumulate, const double2 *phys_in = nullptr);
 void launch_symmetrise(tc_ctx *c, double2 *X);
 
 // diag.cu

@@ -267,3 +267,21 @@ def test_non_blocking_stream_gives_identical_results(tc):
         run.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_create_size_limits(tc):
+    """The azimuthal size limit that the shared-memory transforms impose."""
+    st = {v: k for k, v in tc.STATUS.items()}
+
+    def create(Nt, Ra):
+        h = tc.ctypes.c_void_p()
+        code = tc._lib.tc_create(9, Nt, 8, 0.5, 1.0, 10.0, 0.0, Ra, 1.0, tc.ctypes.byref(h))
+        if code == 0:
+            tc._lib.tc_destroy(h)
+        return code
+
+    assert create(1000, 0.0) == 0
+    assert create(750, 100.0) == 0
+    assert create(1024, 0.0) == st["TC_ERR_UNSUPPORTED"]
+    assert create(768, 100.0) == st["TC_ERR_UNSUPPORTED"]
+    assert create(1030, 0.0) == st["TC_ERR_ARG"]          # not 2^a 3^b 5^c / above 1024
