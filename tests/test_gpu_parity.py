@@ -285,3 +285,40 @@ def test_create_size_limits(tc):
     assert create(1024, 0.0) == st["TC_ERR_UNSUPPORTED"]
     assert create(768, 100.0) == st["TC_ERR_UNSUPPORTED"]
     assert create(1030, 0.0) == st["TC_ERR_ARG"]          # not 2^a 3^b 5^c / above 1024
+
+
+@pytest.mark.parametrize("Nr,Nt,Nz,Ra", [(9, 750, 8, 400.0),     # largest azimuthal size with T
+                                         (11, 1000, 6, 0.0),      # largest without T
+                                         (9, 4, 4, 300.0)])       # smallest: M = K = 1
+def test_nonlinear_extreme_sizes(tc, Nr, Nt, Nz, Ra):
+    wl = _wl(Nr, Nt, Nz, Ra)
+    mdl = Model(wl, "fft")
+    X = random_state(200 + Nt, mdl.nf, Nr, mdl.M, mdl.K)
+    ref, rate = mdl.nonlinear(X)
+    run = tc.Run.from_workload(wl)
+    out = dev(np.zeros_like(X))
+    got_rate = tc.tc_nonlinear(run.ctx, dev(X), out)
+    run.close()
+    got = out.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert abs(got_rate - rate) <= 1e-13 * rate
+
+
+def test_step_parity_smallest_grid(tc):
+    """Nr = 9 (one stencil spans the gap), Ntheta = Nz = 4 (M = K = 1), with T."""
+    wl = Workload("tiny", Nr=9, Ntheta=4, Nz=4, eta=0.5, Lz=2.0, Re_i=40.0, Ra=200.0, Pr=1.0,
+                  amp=1e-2, mp=1, kp=1, amp_T=1e-2, seed=9, dt=1e-3)
+    mdl, got, ref, *_ = _run_both(tc, wl, 30, "fft")
+    assert rel_l2(mdl, got, ref) <= 1e-10
+
+
+def test_quiescent_state_stays_at_rest(tc):
+    """Re_i = Re_o = 0, no heating: the basic state is zero and stays exactly zero."""
+    wl = Workload("rest", Nr=12, Ntheta=12, Nz=12, eta=0.5, Lz=2.0, Re_i=0.0)
+    run = tc.Run.from_workload(wl)
+    run.step(10, 1e-3)
+    X = run.get_state()
+    d = run.diagnostics()
+    run.close()
+    assert np.abs(X).max() == 0.0
+    assert d["E"] == 0.0 and d["corr_diff"] == 0.0
