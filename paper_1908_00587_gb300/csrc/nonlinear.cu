@@ -129,9 +129,23 @@ __global__ void k_meanprof(const double2 *__restrict__ X, double *__restrict__ p
   prof[r * 8 + 5] = (s.nf == 4) ? X[3 * s.S + o].x : 0.0;
 }
 
-// V layout: [3*c + d][r][l][m], d = 0 value, 1 d/dr, 2 d/dz.
+// Mixed precision: the perturbation part of the state in FP32 for the axial
+// kernel (one rounding per coefficient instead of FP64 stencil arithmetic):
+// the (0,0) modes of u_theta, u_z and T are the FP64 mean profiles and are
+// left out (zero), as everything that involves them is formed in FP64.
+__global__ void k_tofloat(const double2 *__restrict__ X, float2 *__restrict__ X32, Sizes s) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)s.nf * s.S) return;
+  const int f = (int)(i / s.S);
+  const long long mode = (i - (long long)f * s.S) % s.nmode;
+  const double2 x = X[i];
+  X32[i] = (f != 0 && mode == 0) ? float2{0.0f, 0.0f} : float2{(float)x.x, (float)x.y};
+}
+
+// V layout: [3*c + d][r][l][m], d = 0 value, 1 d/dr, 2 d/dz.  X is the state
+// in the transform's precision (FP32: k_tofloat's copy, mean profiles removed).
 template <typename T>
-__global__ void k_zinv(const double2 *__restrict__ X, V2<T> *__restrict__ Vout, NLParams p) {
+__global__ void k_zinv(const V2<T> *__restrict__ X, V2<T> *__restrict__ Vout, NLParams p) {
   const Sizes &s = p.sz;
   const int m0 = blockIdx.x * p.MB;
   const int nm = min(p.MB, s.NM - m0);
@@ -147,30 +161,28 @@ __global__ void k_zinv(const double2 *__restrict__ X, V2<T> *__restrict__ Vout, 
   for (int i = threadIdx.x; i < 3 * nm * Np; i += blockDim.x) A[i] = V2<T>{0, 0};
   __syncthreads();
   const int st = p.rad.s0[r];
-  const double *d1 = p.rad.D1 + r * kStencil;
+  T d1[kStencil];
+#pragma unroll
+  for (int q = 0; q < kStencil; ++q) d1[q] = (T)p.rad.D1[r * kStencil + q];
   const FastDiv fnm = (nm == p.MB) ? p.fMB : p.fMBl;
   for (int t = threadIdx.x; t < nm * s.NK; t += blockDim.x) {
     const int mi = fdiv(t, p.fNK);
     const int kk = t - mi * s.NK;
     const long long col = (long long)(m0 + mi) * s.NK + kk;
-    const double2 *Xc = X + (long long)c * s.S;
-    double2 val = Xc[(long long)r * s.nmode + col];
-    double2 dr = {0.0, 0.0};
+    const V2<T> *Xc = X + (long long)c * s.S;
+    const V2<T> val = Xc[(long long)r * s.nmode + col];
+    V2<T> dr = {0, 0};
 #pragma unroll
     for (int q = 0; q < kStencil; ++q) {
-      const double2 x = Xc[(long long)(st + q) * s.nmode + col];
+      const V2<T> x = Xc[(long long)(st + q) * s.nmode + col];
       dr.x += d1[q] * x.x;
       dr.y += d1[q] * x.y;
     }
-    if (p.mixed && col == 0 && c != 0) {   // U_theta, U_z, Tbar stay out of FP32
-      val = double2{0.0, 0.0};
-      dr = double2{0.0, 0.0};
-    }
-    const double beta = p.alpha * kval(kk, s.K, s.NK);
+    const T beta = (T)(p.alpha * kval(kk, s.K, s.NK));
     const int pos = kpos(kk, s.K, s.NK, Nz);
-    A[(3 * mi + 0) * Np + spad(pos)] = V2<T>{(T)val.x, (T)val.y};
-    A[(3 * mi + 1) * Np + spad(pos)] = V2<T>{(T)dr.x, (T)dr.y};
-    A[(3 * mi + 2) * Np + spad(pos)] = V2<T>{(T)(-beta * val.y), (T)(beta * val.x)};
+    A[(3 * mi + 0) * Np + spad(pos)] = val;
+    A[(3 * mi + 1) * Np + spad(pos)] = dr;
+    A[(3 * mi + 2) * Np + spad(pos)] = V2<T>{-beta * val.y, beta * val.x};
   }
   __syncthreads();
   V2<T> *res = fft_batch<+1>(A, B, p.pz, 3 * nm, Np, tw, zmid_ok(p.pz, s.K));
@@ -455,8 +467,10 @@ void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long lon
     {
       LaunchScope ls(c, KZINV);
       k_meanprof<<<(s.Nr + 63) / 64, 64, 0, c->stream>>>(X, c->prof, s, q.rad);
+      k_tofloat<<<(unsigned)(((long long)s.nf * s.S + 255) / 256), 256, 0, c->stream>>>(
+          X, c->X32, s);
       k_zinv<float><<<dim3((s.NM + q.MB - 1) / q.MB, s.Nr, s.nf), 256, c->smem32_zinv,
-                      c->stream>>>(X, V, q);
+                      c->stream>>>(c->X32, V, q);
     }
     {
       LaunchScope ls(c, KTHETA);

@@ -673,6 +673,14 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
   } else if (k == "precision") {
     if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
     if (v == 1.0 && c->eps_c != 0.0) return TC_ERR_UNSUPPORTED;
+    if (v == 1.0 && !c->X32) {
+      try {
+        c->X32 = dalloc<float2>(c, (size_t)c->sz.nf * c->sz.S);
+      } catch (const CudaError &e) {
+        cudaGetLastError();
+        return e.e == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA;
+      }
+    }
     c->precision = (int)v;
   } else if (k == "n_corr") {
     if (v < 1.0 || v > 16.0 || v != (double)(int)v) return TC_ERR_ARG;

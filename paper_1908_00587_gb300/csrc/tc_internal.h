@@ -179,6 +179,7 @@ struct tc_ctx {
   tc::NLParams nl, nl32;
   int precision = 0;            // 0: FP64 everywhere; 1: FP32 transforms/products
   double *prof = nullptr;       // mean-flow profile for the mixed path
+  float2 *X32 = nullptr;        // mixed path: FP32 copy of the perturbation state
   size_t smem32_zinv = 0, smem32_theta = 0, smem32_zfwd = 0;
   // adjoint buffers (allocated on first use)
   double2 *Va = nullptr, *Gdr = nullptr, *Rb = nullptr, *Ybar = nullptr, *Nb = nullptr,
