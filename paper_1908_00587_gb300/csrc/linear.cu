@@ -76,7 +76,10 @@ __device__ __forceinline__ void build_row(const Radial &rad, int Nr, int j, int 
 
 // In-place band LU (Doolittle, no pivoting) of one operator, rows built on the
 // fly.  Operator-major storage: L row j at L[(o*Nrp + j)*8], U row j at
-// U[(o*Nrp + j)*9] (inverse diagonal first, then the 8 super-diagonals).
+// U[(o*Nrp + j)*9]: the inverse diagonal 1/u_jj first, then the 8
+// super-diagonals divided by u_jj (U = D U' with U' unit upper triangular),
+// so a backward row is x_j = b_j/u_jj - sum_f U'(j, j+f) x_(j+f): one FMA
+// behind the newest x on the sweeps' critical path.
 __device__ void band_factor(const Radial &rad, int Nr, int kind, double q2, double beta2,
                             double idt, double ck, double *L, double *U, int Nrp, int o) {
   const long long base = (long long)o * Nrp;
@@ -88,20 +91,22 @@ __device__ void band_factor(const Radial &rad, int Nr, int kind, double q2, doub
       const int i = j - kBand + e;
       if (i < 0) continue;
       const double *Ui = U + (base + i) * (kBand + 1);
-      const double l = a[e] * Ui[0];
-      a[e] = l;
+      // l = a_e / u_ii; l U(i, i+f) = a_e U'(i, i+f)
+      const double ae = a[e];
+      a[e] = ae * Ui[0];
 #pragma unroll
       for (int f = 1; f <= kBand; ++f) {
-        if (e + f < kBandW) a[e + f] -= l * Ui[f];
+        if (e + f < kBandW) a[e + f] -= ae * Ui[f];
       }
     }
-    a[kBand] = 1.0 / a[kBand];
+    const double inv = 1.0 / a[kBand];
     double *Lj = L + (base + j) * kBand;
     double *Uj = U + (base + j) * (kBand + 1);
 #pragma unroll
     for (int e = 0; e < kBand; ++e) Lj[e] = a[e];
+    Uj[0] = inv;
 #pragma unroll
-    for (int f = 0; f <= kBand; ++f) Uj[f] = a[kBand + f];
+    for (int f = 1; f <= kBand; ++f) Uj[f] = a[kBand + f] * inv;
   }
 }
 
@@ -128,10 +133,9 @@ __device__ void band_solve(const double *__restrict__ L, const double *__restric
   for (int e = 0; e < kBand; ++e) w[e] = V{};
   for (int j = Nr - 1; j >= 0; --j) {
     const double *row = U + (base + j) * (kBand + 1);
-    V acc = x[j * xs];
+    V acc = scale(x[j * xs], row[0]);
 #pragma unroll
-    for (int f = 1; f <= kBand; ++f) axpy(acc, row[f], w[f - 1]);
-    acc = scale(acc, row[0]);
+    for (int f = kBand; f >= 1; --f) axpy(acc, row[f], w[f - 1]);
 #pragma unroll
     for (int f = kBand - 1; f > 0; --f) w[f] = w[f - 1];
     w[0] = acc;
@@ -526,64 +530,49 @@ __device__ __forceinline__ void arm_chunk(unsigned bar, double *dst, const doubl
 // zero changes nothing) and take the full 8 only in the boundary rows.
 constexpr int kNarrowFrom = kBand / 2;   // 4
 
+// Each row is one FMA chain ordered oldest to newest, so the newest solution
+// value enters last and the recurrence costs one FMA latency per row (a
+// separate partial sum for the second-newest term would put an add on that
+// path).
+
 // Forward substitution row: b - sum_e L(j, j-8+e) w_e, w_7 the newest x.
 template <bool NARROW>
-__device__ __forceinline__ double l_row_value(const double *row, const double (&w)[kBand],
-                                              double b) {
-  double far = b, near = 0.0;
-  if (!NARROW) {
-#pragma unroll
-    for (int e = 0; e < kNarrowFrom; ++e) far -= row[e] * w[e];
-  }
-#pragma unroll
-  for (int e = kNarrowFrom; e < kBand - 2; ++e) far -= row[e] * w[e];
-  near -= row[kBand - 2] * w[kBand - 2];
-  far += near;
-  far -= row[kBand - 1] * w[kBand - 1];
-  return far;
-}
-
-template <bool NARROW>
 __device__ __forceinline__ double l_row(const double *row, double (&w)[kBand], double b) {
-  const double v = l_row_value<NARROW>(row, w, b);
+  double v = b;
+#pragma unroll
+  for (int e = NARROW ? kNarrowFrom : 0; e < kBand; ++e) v -= row[e] * w[e];
 #pragma unroll
   for (int e = 0; e < kBand - 1; ++e) w[e] = w[e + 1];
   w[kBand - 1] = v;
   return v;
 }
 
-// Backward substitution row: (b - sum_f U(j, j+f) w_{f-1}) / U(j, j), w_0 the newest x.
+// Backward substitution row with U = D U': b / u_jj - sum_f U'(j, j+f) w_{f-1},
+// w_0 the newest x (row[0] = 1/u_jj, row[f] = U'(j, j+f)).
 template <bool NARROW>
 __device__ __forceinline__ double u_row(const double *row, double (&w)[kBand], double b) {
-  double far = b, near = 0.0;
-  if (!NARROW) {
+  double v = b * row[0];
 #pragma unroll
-    for (int f = kBand; f > kNarrowFrom; --f) far -= row[f] * w[f - 1];
-  }
-#pragma unroll
-  for (int f = kNarrowFrom; f >= 3; --f) far -= row[f] * w[f - 1];
-  near -= row[2] * w[1];
-  far += near;
-  far -= row[1] * w[0];
-  far *= row[0];
+  for (int f = NARROW ? kNarrowFrom : kBand; f >= 1; --f) v -= row[f] * w[f - 1];
 #pragma unroll
   for (int f = kBand - 1; f > 0; --f) w[f] = w[f - 1];
-  w[0] = far;
-  return far;
+  w[0] = v;
+  return v;
 }
 
-// U^T forward row (column-oriented): y = (b - pending_0) / U(i, i), then the
-// pending sums of rows i+1..i+8 take U(i, i+f) y.
+// U^T forward row (column-oriented), U^T = U'^T D: z = b - pending_0 solves
+// the unit factor, y = z / u_ii, and the pending sums of rows i+1..i+8 take
+// U'(i, i+f) z.
 template <bool NARROW>
 __device__ __forceinline__ double ut_row(const double *row, double (&w)[kBand], double b) {
-  const double y = (b - w[0]) * row[0];
+  const double z = b - w[0];
   constexpr int kn = NARROW ? kNarrowFrom : kBand - 1;
 #pragma unroll
-  for (int k = 0; k < kn; ++k) w[k] = w[k + 1] + row[k + 1] * y;
+  for (int k = 0; k < kn; ++k) w[k] = w[k + 1] + row[k + 1] * z;
 #pragma unroll
   for (int k = kn; k < kBand - 1; ++k) w[k] = w[k + 1];
-  w[kBand - 1] = NARROW ? 0.0 : row[kBand] * y;
-  return y;
+  w[kBand - 1] = NARROW ? 0.0 : row[kBand] * z;
+  return z * row[0];
 }
 
 // L^T backward row: x = b - pending_0, then the pending sums of rows
