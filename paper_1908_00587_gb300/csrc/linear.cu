@@ -598,9 +598,7 @@ template <bool TRANS>
 __global__ void __launch_bounds__(4 * kSweepOps)
 k_sweep(SweepArgs a, DevScalars *sc) {
   extern __shared__ __align__(128) double ring_raw[];
-  double *ring[kSweepStages];
-#pragma unroll
-  for (int s = 0; s < kSweepStages; ++s) ring[s] = ring_raw + s * kSweepStageDoubles;
+  auto ring = [&](int st) { return ring_raw + st * kSweepStageDoubles; };
   __shared__ __align__(8) unsigned long long bars[kSweepStages];
   __shared__ int abort_flag;
   const SweepField F = a.f[blockIdx.z];
@@ -629,8 +627,8 @@ k_sweep(SweepArgs a, DevScalars *sc) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  unsigned phase[kSweepStages] = {0, 0, 0};
-  int armed[kSweepStages] = {0, 0, 0};   // meaningful on thread 0
+  // per-stage bits: current mbarrier phase, and copies in flight (thread 0)
+  unsigned phase = 0u, armed = 0u;
   // chunk sequence: forward L chunks 0..nch-1, then backward U chunks nch-1..0
   const int total = 2 * nch;
   auto arm = [&](int step, int s) {
@@ -638,10 +636,10 @@ k_sweep(SweepArgs a, DevScalars *sc) {
     const bool first = step < nch;   // forward pass
     const int j0 = (first ? step : total - 1 - step) * kSweepRows;
     if (first != TRANS)   // forward of A, or backward of A^T: L rows
-      arm_chunk<kBand>(smem_u32(&bars[s]), ring[s], F.L, a.Nrp, o0, nops, j0);
+      arm_chunk<kBand>(smem_u32(&bars[s]), ring(s), F.L, a.Nrp, o0, nops, j0);
     else
-      arm_chunk<kBand + 1>(smem_u32(&bars[s]), ring[s], F.U, a.Nrp, o0, nops, j0);
-    armed[s] = 1;
+      arm_chunk<kBand + 1>(smem_u32(&bars[s]), ring(s), F.U, a.Nrp, o0, nops, j0);
+    armed |= 1u << s;
   };
   if (threadIdx.x == 0)
     for (int s = 0; s < kSweepStages && s < total; ++s) arm(s, s);
@@ -663,86 +661,94 @@ k_sweep(SweepArgs a, DevScalars *sc) {
     if (fwd && step == nch - 1) {
       // backward sweep starts from the chunk just finished: nothing to prefetch
     }
-    const bool done = mbar_wait(smem_u32(&bars[s]), phase[s]);
+    const bool done = mbar_wait(smem_u32(&bars[s]), (phase >> s) & 1u);
     if (!done) {
       ok = false;
       atomicOr(&abort_flag, 1);
     } else {
-      phase[s] ^= 1u;
-      if (threadIdx.x == 0) armed[s] = 0;   // its copies have landed
+      phase ^= 1u << s;
+      if (threadIdx.x == 0) armed &= ~(1u << s);   // its copies have landed
     }
     __syncthreads();
     if (abort_flag) break;
-    if (active && TRANS) {
-      if (fwd) {
-        // U^T y = b: y_i = (b_i - pending_i) / u_ii, then pending_{i+f} += U(i, i+f) y_i
-        const double *Uc = ring[s] + g * kSweepOpDoubles;
+    if (active) {
+      // The narrow/wide choice is made per chunk (a chunk with any boundary
+      // row takes the wide form for all its rows: the extra terms are exact
+      // zeros), so a full chunk is straight-line code in which the sliding
+      // window w[] lives in renamed registers; only a chunk past the last row
+      // guards each row.
+      const bool full = j0 + kSweepRows <= a.Nr;
+      const bool low_narrow = j0 + kSweepRows <= a.Nr - kNarrowFrom;   // L rows, L^T rows
+      const bool up_narrow = j0 >= kNarrowFrom;                        // U rows, U^T rows
+      const double *Lc = ring(s) + g * kSweepOpDoubles;                // stage holds L or U
+      if (TRANS && fwd) {
+        // U^T y = b: z_i = b_i - pending_i, y_i = z_i / u_ii, pending += U'(i, i+f) z_i
+        if (full && up_narrow) {
 #pragma unroll
-        for (int r = 0; r < kSweepRows; ++r) {
-          const int j = j0 + r;
-          const double *row = Uc + r * (kBand + 1);
-          if (j >= kNarrowFrom && j < a.Nr) {
-            x[j * xs] = ut_row<true>(row, w, xa[r]);
-          } else if (j < a.Nr) {
-            x[j * xs] = ut_row<false>(row, w, xa[r]);
-          }
-        }
-        if (c + 1 < nch) {
+          for (int r = 0; r < kSweepRows; ++r)
+            x[(j0 + r) * xs] = ut_row<true>(Lc + r * (kBand + 1), w, xa[r]);
+        } else if (full) {
 #pragma unroll
-          for (int r = 0; r < kSweepRows; ++r) {
-            const int j = j0 + kSweepRows + r;
-            xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
-          }
+          for (int r = 0; r < kSweepRows; ++r)
+            x[(j0 + r) * xs] = ut_row<false>(Lc + r * (kBand + 1), w, xa[r]);
         } else {
 #pragma unroll
-          for (int e = 0; e < kBand; ++e) w[e] = 0.0;
+          for (int r = 0; r < kSweepRows; ++r)
+            if (j0 + r < a.Nr) x[(j0 + r) * xs] = ut_row<false>(Lc + r * (kBand + 1), w, xa[r]);
+        }
+      } else if (TRANS) {
+        // L^T x = y: x_j = y_j - pending_j, then pending_{j-8+e} += L(j, j-8+e) x_j
+        if (full && low_narrow) {
 #pragma unroll
-          for (int r = 0; r < kSweepRows; ++r) {
-            const int j = j0 + r;
-            xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
-          }
+          for (int r = kSweepRows - 1; r >= 0; --r)
+            x[(j0 + r) * xs] = lt_row<true>(Lc + r * kBand, w, xa[r]);
+        } else if (full) {
+#pragma unroll
+          for (int r = kSweepRows - 1; r >= 0; --r)
+            x[(j0 + r) * xs] = lt_row<false>(Lc + r * kBand, w, xa[r]);
+        } else {
+#pragma unroll
+          for (int r = kSweepRows - 1; r >= 0; --r)
+            if (j0 + r < a.Nr) x[(j0 + r) * xs] = lt_row<false>(Lc + r * kBand, w, xa[r]);
+        }
+      } else if (fwd) {
+        if (full && low_narrow) {
+#pragma unroll
+          for (int r = 0; r < kSweepRows; ++r)
+            x[(j0 + r) * xs] = l_row<true>(Lc + r * kBand, w, xa[r]);
+        } else if (full) {
+#pragma unroll
+          for (int r = 0; r < kSweepRows; ++r)
+            x[(j0 + r) * xs] = l_row<false>(Lc + r * kBand, w, xa[r]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < kSweepRows; ++r)
+            if (j0 + r < a.Nr) x[(j0 + r) * xs] = l_row<false>(Lc + r * kBand, w, xa[r]);
         }
       } else {
-        // L^T x = y: x_j = y_j - pending_j, then pending_{j-8+e} += L(j, j-8+e) x_j
-        const double *Lc = ring[s] + g * kSweepOpDoubles;
-        const int narrow_below = a.Nr - kNarrowFrom;
+        if (full && up_narrow) {
 #pragma unroll
-        for (int r = kSweepRows - 1; r >= 0; --r) {
-          const int j = j0 + r;
-          const double *row = Lc + r * kBand;
-          if (j < narrow_below) {
-            x[j * xs] = lt_row<true>(row, w, xa[r]);
-          } else if (j < a.Nr) {
-            x[j * xs] = lt_row<false>(row, w, xa[r]);
-          }
-        }
-        if (c > 0) {
+          for (int r = kSweepRows - 1; r >= 0; --r)
+            x[(j0 + r) * xs] = u_row<true>(Lc + r * (kBand + 1), w, xa[r]);
+        } else if (full) {
 #pragma unroll
-          for (int r = 0; r < kSweepRows; ++r) xa[r] = x[(j0 - kSweepRows + r) * xs];
+          for (int r = kSweepRows - 1; r >= 0; --r)
+            x[(j0 + r) * xs] = u_row<false>(Lc + r * (kBand + 1), w, xa[r]);
+        } else {
+#pragma unroll
+          for (int r = kSweepRows - 1; r >= 0; --r)
+            if (j0 + r < a.Nr) x[(j0 + r) * xs] = u_row<false>(Lc + r * (kBand + 1), w, xa[r]);
         }
       }
-    } else if (active) {
+      // prefetch the right-hand sides of the next chunk
       if (fwd) {
-        const double *Lc = ring[s] + g * kSweepOpDoubles;
-        const int narrow_below = a.Nr - kNarrowFrom;
-#pragma unroll
-        for (int r = 0; r < kSweepRows; ++r) {
-          const int j = j0 + r;
-          const double *row = Lc + r * kBand;
-          if (j < narrow_below) {
-            x[j * xs] = l_row<true>(row, w, xa[r]);
-          } else if (j < a.Nr) {
-            x[j * xs] = l_row<false>(row, w, xa[r]);
-          }
-        }
-        // prefetch the next forward chunk, or the last chunk for the backward sweep
         if (c + 1 < nch) {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r) {
             const int j = j0 + kSweepRows + r;
             xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
           }
-        } else {
+        } else {   // the backward sweep starts from the chunk just finished
 #pragma unroll
           for (int e = 0; e < kBand; ++e) w[e] = 0.0;
 #pragma unroll
@@ -751,22 +757,9 @@ k_sweep(SweepArgs a, DevScalars *sc) {
             xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
           }
         }
-      } else {
-        const double *Uc = ring[s] + g * kSweepOpDoubles;
+      } else if (c > 0) {
 #pragma unroll
-        for (int r = kSweepRows - 1; r >= 0; --r) {
-          const int j = j0 + r;
-          const double *row = Uc + r * (kBand + 1);
-          if (j >= kNarrowFrom && j < a.Nr) {
-            x[j * xs] = u_row<true>(row, w, xa[r]);
-          } else if (j < a.Nr) {
-            x[j * xs] = u_row<false>(row, w, xa[r]);
-          }
-        }
-        if (c > 0) {
-#pragma unroll
-          for (int r = 0; r < kSweepRows; ++r) xa[r] = x[(j0 - kSweepRows + r) * xs];
-        }
+        for (int r = 0; r < kSweepRows; ++r) xa[r] = x[(j0 - kSweepRows + r) * xs];
       }
     }
     __syncthreads();   // every thread is done with stage s
@@ -776,7 +769,7 @@ k_sweep(SweepArgs a, DevScalars *sc) {
   if (abort_flag && threadIdx.x == 0) {
     // drain the copies still in flight into this CTA's ring, bounded again
     for (int s = 0; s < kSweepStages; ++s)
-      if (armed[s]) mbar_wait(smem_u32(&bars[s]), phase[s]);
+      if ((armed >> s) & 1u) mbar_wait(smem_u32(&bars[s]), (phase >> s) & 1u);
   }
 }
 
