@@ -238,6 +238,7 @@ __global__ void k_influence(LinParams p, const DevScalars *sc) {
 __global__ void k_dt_policy(DevScalars *sc, double dt_fixed, double cfl, double dt_max,
                             double *dt_hist, int hist_cap) {
   const double rate = __longlong_as_double((long long)sc->rate_bits);
+  sc->dt_old = sc->dt;
   sc->rate_last = rate;
   sc->rate_bits = 0ull;
   sc->corr_bits = 0ull;
@@ -256,54 +257,6 @@ __global__ void k_dt_policy(DevScalars *sc, double dt_fixed, double cfl, double 
   if (dt_hist && sc->hist_pos < hist_cap) dt_hist[sc->hist_pos++] = dt;
 }
 
-// Y' = X/dt + (1-c) L X + (1-c) N, in +- form, at every node.
-__global__ void k_rhs(const double2 *__restrict__ X, const double2 *__restrict__ N,
-                      double2 *__restrict__ Yb, LinParams p, const DevScalars *sc) {
-  const Sizes &s = p.sz;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.S) return;
-  const int j = (int)(i / s.nmode);
-  const int mode = (int)(i - (long long)j * s.nmode);
-  const int m = mode / s.NK, kk = mode % s.NK;
-  const double beta = p.alpha * kval(kk, s.K, s.NK);
-  const double idt = 1.0 / sc->dt;
-  const double ir = p.rad.inv_r[j];
-  const int st = p.rad.s0[j];
-  const double *lw = p.rad.Lw + j * kStencil;   // D2 + D1/r of row j
-  const double b2 = beta * beta, ir2 = ir * ir;
-  const double om = 1.0 - kCN;
-  // L is real, so L(X+-) = L(X_r) +- i L(X_theta): one stencil per primitive field
-  double2 Sx[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-#pragma unroll
-  for (int t = 0; t < kStencil; ++t) {
-    const long long o = (long long)(st + t) * s.nmode + mode;
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-      if (c < s.nf) Sx[c] = Sx[c] + lw[t] * X[c * s.S + o];
-  }
-  {
-    const double2 xr = X[i], xt = X[s.S + i];
-    const double2 xp = {xr.x - xt.y, xr.y + xt.x}, xm = {xr.x + xt.y, xr.y - xt.x};
-    const double2 Sp = {Sx[0].x - Sx[1].y, Sx[0].y + Sx[1].x};   // S_r + i S_theta
-    const double2 Sm = {Sx[0].x + Sx[1].y, Sx[0].y - Sx[1].x};   // S_r - i S_theta
-    const double2 nr = N[i], nt = N[s.S + i];
-    const double2 np = {nr.x - nt.y, nr.y + nt.x}, nm = {nr.x + nt.y, nr.y - nt.x};
-    const double qp = (double)(m + 1) * (m + 1), qm = (double)(m - 1) * (m - 1);
-    const double2 Lp = Sp - (qp * ir2 + b2) * xp;
-    const double2 Lm = Sm - (qm * ir2 + b2) * xm;
-    Yb[i] = idt * xp + om * Lp + om * np;
-    Yb[s.S + i] = idt * xm + om * Lm + om * nm;
-  }
-#pragma unroll
-  for (int c = 2; c < 4; ++c) {
-    if (c >= s.nf) break;
-    const double2 x = X[c * s.S + i];
-    const double kap = (c == 3) ? p.kappaT : 1.0;
-    const double2 L = kap * (Sx[c] - ((double)m * m * ir2 + b2) * x);
-    Yb[c * s.S + i] = idt * x + om * L + om * N[c * s.S + i];
-  }
-}
-
 // Explicit right-hand side R = Y' + c N of component comp at flat index i.
 __device__ __forceinline__ double2 rhs_pm(const double2 *Yb, const double2 *N, long long S,
                                           long long i, int comp) {
@@ -318,6 +271,96 @@ __device__ __forceinline__ double2 rhs_pm(const double2 *Yb, const double2 *N, l
   }
   return y + kCN * N[comp * S + i];
 }
+
+// Y' = X/dt + (1-c) L X + (1-c) N, in +- form, at every node.
+//
+// L X from the previous stage: at interior nodes of modes other than (0,0)
+// the last corrector solved (1/dt' - c kappa L) X = R - G(p) for the current
+// X (R = Y'_prev + c N1 its right-hand side, G the pressure gradient of the
+// total pressure p, dt' that stage's step), so (1 - c) kappa L X =
+// ((1 - c)/c) (X/dt' - R + G).  When that stage is known to have produced
+// the current state (sc->rhs_ident), those nodes use it: one D1 stencil on p
+// instead of the Laplacian stencil on every field.  The wall rows (Dirichlet
+// rows of the stage), the (0,0) mode (solved without pressure, with the wall
+// values and, with the flux constraint, an extra forcing) and every other
+// case take the stencil.
+__global__ void k_rhs(const double2 *__restrict__ X, const double2 *__restrict__ N,
+                      double2 *__restrict__ Yb, const double2 *__restrict__ N1,
+                      const double2 *__restrict__ P, LinParams p, const DevScalars *sc) {
+  const Sizes &s = p.sz;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.S) return;
+  const int j = (int)(i / s.nmode);
+  const int mode = (int)(i - (long long)j * s.nmode);
+  const int m = mode / s.NK, kk = mode % s.NK;
+  const double beta = p.alpha * kval(kk, s.K, s.NK);
+  const double idt = 1.0 / sc->dt;
+  const double ir = p.rad.inv_r[j];
+  const int st = p.rad.s0[j];
+  const double om = 1.0 - kCN;
+  const long long S = s.S;
+  if (sc->rhs_ident && mode != 0 && j > 0 && j < s.Nr - 1) {
+    const double q = om / kCN;
+    const double idt_old = 1.0 / sc->dt_old;
+    const double *d1 = p.rad.D1 + j * kStencil;
+    double2 d1p = {0.0, 0.0};
+#pragma unroll
+    for (int t = 0; t < kStencil; ++t) d1p = d1p + d1[t] * P[(long long)(st + t) * s.nmode + mode];
+    const double2 pj = P[i];
+    const double2 mp = (m * ir) * pj;
+    const double2 xr = X[i], xt = X[S + i];
+    const double2 xp = {xr.x - xt.y, xr.y + xt.x}, xm = {xr.x + xt.y, xr.y - xt.x};
+    const double2 nr = N[i], nt = N[S + i];
+    const double2 np = {nr.x - nt.y, nr.y + nt.x}, nm = {nr.x + nt.y, nr.y - nt.x};
+    const double2 rp = rhs_pm(Yb, N1, S, i, 0), rm = rhs_pm(Yb, N1, S, i, 1);
+    Yb[i] = idt * xp + q * (idt_old * xp - rp + (d1p - mp)) + om * np;
+    Yb[S + i] = idt * xm + q * (idt_old * xm - rm + (d1p + mp)) + om * nm;
+    {
+      const double2 x = X[2 * S + i];
+      const double2 rz = rhs_pm(Yb, N1, S, i, 2);
+      Yb[2 * S + i] = idt * x + q * (idt_old * x - rz + beta * mul_i(pj)) + om * N[2 * S + i];
+    }
+    if (s.nf == 4) {
+      const double2 x = X[3 * S + i];
+      const double2 rT = rhs_pm(Yb, N1, S, i, 3);
+      Yb[3 * S + i] = idt * x + q * (idt_old * x - rT) + om * N[3 * S + i];
+    }
+    return;
+  }
+  const double *lw = p.rad.Lw + j * kStencil;   // D2 + D1/r of row j
+  const double b2 = beta * beta, ir2 = ir * ir;
+  // L is real, so L(X+-) = L(X_r) +- i L(X_theta): one stencil per primitive field
+  double2 Sx[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+#pragma unroll
+  for (int t = 0; t < kStencil; ++t) {
+    const long long o = (long long)(st + t) * s.nmode + mode;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < s.nf) Sx[c] = Sx[c] + lw[t] * X[c * S + o];
+  }
+  {
+    const double2 xr = X[i], xt = X[S + i];
+    const double2 xp = {xr.x - xt.y, xr.y + xt.x}, xm = {xr.x + xt.y, xr.y - xt.x};
+    const double2 Sp = {Sx[0].x - Sx[1].y, Sx[0].y + Sx[1].x};   // S_r + i S_theta
+    const double2 Sm = {Sx[0].x + Sx[1].y, Sx[0].y - Sx[1].x};   // S_r - i S_theta
+    const double2 nr = N[i], nt = N[S + i];
+    const double2 np = {nr.x - nt.y, nr.y + nt.x}, nm = {nr.x + nt.y, nr.y - nt.x};
+    const double qp = (double)(m + 1) * (m + 1), qm = (double)(m - 1) * (m - 1);
+    const double2 Lp = Sp - (qp * ir2 + b2) * xp;
+    const double2 Lm = Sm - (qm * ir2 + b2) * xm;
+    Yb[i] = idt * xp + om * Lp + om * np;
+    Yb[S + i] = idt * xm + om * Lm + om * nm;
+  }
+#pragma unroll
+  for (int c = 2; c < 4; ++c) {
+    if (c >= s.nf) break;
+    const double2 x = X[c * S + i];
+    const double kap = (c == 3) ? p.kappaT : 1.0;
+    const double2 L = kap * (Sx[c] - ((double)m * m * ir2 + b2) * x);
+    Yb[c * S + i] = idt * x + om * L + om * N[c * S + i];
+  }
+}
+
 
 // The radial solves work on split real / imaginary planes (the operators are
 // real): plane q of a field holds part q (0 re, 1 im) as [r][mode] doubles,
@@ -882,6 +925,8 @@ __global__ void k_correct(const double *__restrict__ U, const double *__restrict
     }
   }
   if (Xprev) {   // uniform over the grid: every thread of every block gets here
+    // the last corrector: X, Yb, N1 and P now belong to one stage
+    if (i == 0) sc->rhs_ident = 1;
     __shared__ unsigned long long wmax[32];
     for (int o = 16; o > 0; o >>= 1) dbits = max(dbits, __shfl_xor_sync(0xffffffffu, dbits, o));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = dbits;
@@ -1357,7 +1402,13 @@ void launch_dt_policy(tc_ctx *c, double dt_fixed, int step_index) {
 
 void launch_rhs(tc_ctx *c, const double2 *X, const double2 *N0) {
   LaunchScope ls(c, KRHS);
-  k_rhs<<<blocks(c->sz.S, 128), 128, 0, c->stream>>>(X, N0, c->Yb, c->lin, c->scal);
+  k_rhs<<<blocks(c->sz.S, 128), 128, 0, c->stream>>>(X, N0, c->Yb, c->N1, c->P, c->lin,
+                                                      c->scal);
+}
+
+void invalidate_rhs_identity(tc_ctx *c) {
+  cudaMemsetAsync(reinterpret_cast<char *>(c->scal) + offsetof(DevScalars, rhs_ident), 0,
+                  sizeof(int), c->stream);
 }
 
 void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout,

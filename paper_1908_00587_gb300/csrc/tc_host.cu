@@ -479,6 +479,7 @@ void upload_tables(tc_ctx *c) {
 tc_status commit_staged_state(tc_ctx *c) {
   const size_t bytes = (size_t)16 * c->sz.nf * c->sz.S;
   try {
+    invalidate_rhs_identity(c);
     DevScalars sc{};
     char *base = reinterpret_cast<char *>(c->scal);
     ck(cudaMemsetAsync(base + offsetof(DevScalars, dt_prev), 0, sizeof(double), c->stream));
@@ -879,6 +880,7 @@ tc_status tc_init_perturbation(tc_ctx *c, const double *psi, int mp, int kp, dou
     for (long long i = 0; i < 2 * 3 * s.S; ++i) X[i] += su * u[i];
     if (s.nf == 4)
       for (long long i = 2 * 3 * s.S; i < 2 * 4 * s.S; ++i) X[i] += sT * u[i];
+    invalidate_rhs_identity(c);
     ck(cudaMemcpyAsync(c->X, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice,
                        c->stream));
     DevScalars sc{};
@@ -973,6 +975,7 @@ tc_status tc_stage_solve(tc_ctx *c, const void *rhs_dev, double dt, void *x_out_
   if (c->poisoned) return TC_ERR_CUDA;
   const Sizes &s = c->sz;
   try {
+    invalidate_rhs_identity(c);
     ck(cudaMemcpyAsync(c->Yb, rhs_dev, (size_t)16 * s.nf * s.S, cudaMemcpyDeviceToDevice,
                        c->stream));
     ck(cudaMemsetAsync(c->N1, 0, (size_t)16 * s.nf * s.S, c->stream));
@@ -1055,6 +1058,7 @@ tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *a
   double2 *lam = static_cast<double2 *>(adj_dev);
   try {
     ensure_adjoint(c);
+    invalidate_rhs_identity(c);
     int zero = 0;
     ck(cudaMemcpyAsync(&c->scal->timeout, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
     // forward internals of the step at X^n: only the predictor state X* is
@@ -1114,6 +1118,7 @@ tc_status tc_stage_solve_adjoint(tc_ctx *c, const void *xbar_dev, double dt, voi
   if (c->flux) return TC_ERR_UNSUPPORTED;
   try {
     ensure_adjoint(c);
+    invalidate_rhs_identity(c);
     int zero = 0;
     ck(cudaMemcpyAsync(&c->scal->timeout, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
     launch_dt_policy(c, dt, -1);

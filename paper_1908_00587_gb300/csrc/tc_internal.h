@@ -81,6 +81,12 @@ struct DevScalars {
   int timeout;          // set when a bounded device-side wait gave up
   unsigned long long corr_bits;   // max |X_corr - X_prev| of the last corrector
   int hist_pos;         // next slot of the step history of the current tc_step call
+  // 1 while X, Yb, N1 and P are the last corrector's state, right-hand side,
+  // nonlinear term and pressure (k_correct sets it; every entry point that
+  // changes one of them outside a step clears it): k_rhs may then take L X
+  // from that stage's equation instead of the stencil
+  int rhs_ident;
+  double dt_old;        // step of the stage that produced the current state
 };
 
 // Parameters of the nonlinear stage.
@@ -250,6 +256,7 @@ void launch_factor_poisson(tc_ctx *c);
 void launch_refactor(tc_ctx *c);
 void launch_dt_policy(tc_ctx *c, double dt_fixed, int step_index);
 void launch_rhs(tc_ctx *c, const double2 *X, const double2 *N0);
+void invalidate_rhs_identity(tc_ctx *c);   // enqueued on the context's stream
 // Xprev (nullable): previous iterate; the stage then records max |Xout - Xprev|.
 void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout,
                   const double2 *Xprev = nullptr);

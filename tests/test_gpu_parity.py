@@ -322,3 +322,34 @@ def test_quiescent_state_stays_at_rest(tc):
     run.close()
     assert np.abs(X).max() == 0.0
     assert d["E"] == 0.0 and d["corr_diff"] == 0.0
+
+
+def test_rhs_from_stage_equation_matches_stencil(tc):
+    """After a corrector, the explicit part takes L X from that stage's
+    equation; with the state re-entered before every step (which forgets the
+    stage) it takes the 9-point stencil.  Both runs must agree to round-off,
+    and both stay on the oracle."""
+    # fixed dt near the CFL step of this flow (its dynamic step is about 5e-5)
+    wl = WORKLOADS["tc_fp64T_nr64_n128"].scaled(Nr=24, Ntheta=24, Nz=30, mp=4, kp=4, dt=5e-5)
+    psi = psi_coefficients(wl.seed, wl.mp, wl.kp)
+    tco = temperature_coefficients(wl.seed, wl.mp, wl.kp)
+    a = tc.Run.from_workload(wl)
+    a.init_perturbation(psi, wl.amp, tco, wl.amp_T)
+    a.step(20, wl.dt)
+    Xa = a.get_state()
+    a.close()
+    b = tc.Run.from_workload(wl)
+    b.init_perturbation(psi, wl.amp, tco, wl.amp_T)
+    for _ in range(20):
+        b.step(1, wl.dt)
+        b.set_state(b.get_state())
+    Xb = b.get_state()
+    b.close()
+    mdl = Model(wl, "fft")
+    # the two forms of L X differ by round-off of the stage solve divided by
+    # c dt: ~1e-16 |X| / dt per step, against a perturbation ~1e-5 of |X|
+    assert rel_l2(mdl, Xa, Xb) <= 1e-11
+    assert rel_l2(mdl, Xa - mdl.base, Xb - mdl.base) <= 1e-9
+    X = mdl.initial_state(psi, tco)
+    X, _ = mdl.run(X, 20, wl.dt)
+    assert rel_l2(mdl, Xa, X) <= 1e-10
