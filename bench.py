@@ -57,6 +57,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(dist, value, device):
+    """The largest of each rank's value (all ranks get it); value itself alone."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(points, steps, world, slowest_ms):
+    """Whole-job grid-point-steps/s: every rank's points and steps over the
+    slowest rank's time (replicas run the same workload)."""
+    return points * steps * world / (slowest_ms * 1e-3)
+
+
 def measured_hbm_peak():
     """Copy bandwidth measured on the GB300s (GB/s), else the fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -293,11 +309,8 @@ def run_gb300(args):
     kt_total_ms = sum(a.elapsed_time(b) for a, b in zip(ks, ke))
     timing = tc.tc_get_timing(run.ctx)
     tc.tc_set_option(run.ctx, "timing", 0)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = wl.points * args.steps * world / (total_ms * 1e-3)
+    total_ms = max_over_ranks(dist, total_ms, "cuda")
+    value = replica_throughput(wl.points, args.steps, world, total_ms)
 
     # end to end through the public API with host buffers: state in from pinned
     # host memory, one step, state out to pinned host memory (--e2e-steps 0
@@ -316,13 +329,9 @@ def run_gb300(args):
             run.step(1, wl.dt)
             run.get_state(host)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
         state_bytes = int(np.prod(run.shape)) * 16
-        e2e = {"value": wl.points * ne * world / e2e_s, "unit": METRIC,
+        e2e = {"value": replica_throughput(wl.points, ne, world, e2e_s * 1e3), "unit": METRIC,
                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                "steps": ne}
 
