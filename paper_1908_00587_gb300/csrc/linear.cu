@@ -902,13 +902,17 @@ __global__ void k_correct(const double *__restrict__ U, const double *__restrict
     Xout[i] = xr;
     Xout[S + i] = xt;
     Xout[2 * S + i] = uz;
-    bool bad = !(isfinite(xr.x) && isfinite(xr.y) && isfinite(xt.x) && isfinite(xt.y) &&
-                 isfinite(uz.x) && isfinite(uz.y));
+    // NaN/Inf test on the exponent bits (integer ops, off the FP64 pipe)
+    auto exp_all = [](double2 v) {
+      return (__double2hiint(v.x) & 0x7ff00000) == 0x7ff00000 ||
+             (__double2hiint(v.y) & 0x7ff00000) == 0x7ff00000;
+    };
+    bool bad = exp_all(xr) || exp_all(xt) || exp_all(uz);
     double2 T = {0.0, 0.0};
     if (s.nf == 4) {
       T = double2{U[6 * S + i], U[7 * S + i]};
       Xout[3 * S + i] = T;
-      bad = bad || !(isfinite(T.x) && isfinite(T.y));
+      bad = bad || exp_all(T);
     }
     if (Pout) Pout[i] = pr;
     if (bad) atomicOr(&sc->nonfinite, 1);
