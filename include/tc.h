@@ -247,6 +247,28 @@ tc_status tc_stage_solve(tc_ctx *ctx, const void *rhs_dev, double dt, void *x_ou
  * TC_ERR_TIMEOUT, TC_ERR_OOM, TC_ERR_CUDA. */
 tc_status tc_adjoint_step(tc_ctx *ctx, const void *state_n_dev, double dt, void *adj_dev);
 
+/* Recorded steps for the reverse sweep (checkpoint segments).
+ * tc_record_bytes_per_step: bytes one recorded step takes: X^n and the
+ *   predictor state X* (state layout each), then the physical-grid fields of
+ *   X^n (complex128 [Nr][Nz][2 nfields][Ntheta]: per component the pairs
+ *   value + i d/dtheta and d/dr + i d/dz).
+ * tc_step_record: advances nsteps steps of fixed dt > 0 like tc_step and
+ *   writes step n's record at record_dev + n * that size (device,
+ *   caller-owned, record_bytes long; TC_ERR_ARG if too short).
+ * tc_adjoint_steps: lambda (adj, device) from step n0 + nsteps back to n0
+ *   over nsteps records written by tc_step_record with the same dt, last
+ *   first -- the same map as nsteps calls of tc_adjoint_step on the recorded
+ *   states, without recomputing any forward stage.  The context's state is
+ *   not changed.
+ * Both cover the default scheme only (TC_ERR_UNSUPPORTED otherwise, as for
+ * tc_adjoint_step).  Errors: TC_ERR_ARG, TC_ERR_NONFINITE (record),
+ * TC_ERR_TIMEOUT, TC_ERR_OOM, TC_ERR_CUDA. */
+tc_status tc_record_bytes_per_step(const tc_ctx *ctx, long long *bytes);
+tc_status tc_step_record(tc_ctx *ctx, int nsteps, double dt, void *record_dev,
+                         long long record_bytes);
+tc_status tc_adjoint_steps(tc_ctx *ctx, int nsteps, const void *record_dev, double dt,
+                           void *adj_dev);
+
 /* Adjoint of the nonlinear stage at state_dev: xbar = (dN/dX)^T nbar (device
  * buffers of the state layout; nbar holds cotangents of N_r, N_theta, N_z(, N_T)). */
 tc_status tc_nonlinear_adjoint(tc_ctx *ctx, const void *state_dev, const void *nbar_dev,

@@ -1047,13 +1047,44 @@ void ensure_adjoint(tc_ctx *c) {
 
 extern "C" {
 
-tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *adj_dev) {
-  if (!c || !state_n_dev || !adj_dev || !(dt > 0.0) || !std::isfinite(dt)) return TC_ERR_ARG;
-  if (c->poisoned) return TC_ERR_CUDA;
+namespace {
+
+// Reverse sweep of one step given its linearisation points: X^n, the
+// predictor state X* and the physical-grid fields of X^n.  lam: lambda^(n+1)
+// in, lambda^n out.  The factors and influence data must be those of dt.
+void enqueue_adjoint_sweep(tc_ctx *c, const double2 *Xn, const double2 *Xs,
+                           const double2 *phys, double2 *lam) {
+  launch_stage_adjoint(c, lam, c->Rb);                      // corrector stage
+  launch_stage_split_adjoint(c, c->Rb, c->Ybar, c->Nb, 0);
+  launch_nonlinear_adjoint(c, Xs, c->Nb, c->Xb, 0);         // N(X*)
+  launch_stage_adjoint(c, c->Xb, c->Rb);                    // predictor stage
+  launch_stage_split_adjoint(c, c->Rb, c->Ybar, c->Nb, 1);
+  launch_rhs_adjoint(c, c->Ybar, lam, c->Nb);
+  launch_nonlinear_adjoint(c, Xn, c->Nb, lam, 1, phys);     // N(X^n)
+  launch_herm_project(c, lam);
+}
+
+tc_status adjoint_supported(const tc_ctx *c) {
   // the adjoint is of the default scheme: FP64, one corrector, no flux
   // constraint, no centrifugal buoyancy
   if (c->precision != 0 || c->n_corr != 1 || c->flux || c->eps_c != 0.0)
     return TC_ERR_UNSUPPORTED;
+  return TC_OK;
+}
+
+// Record of one step: X^n, X* (nf S complex each), then the physical fields
+// of X^n (Nr Nz 2 nf Nt complex).
+long long record_doubles2(const tc_ctx *c) {
+  const Sizes &s = c->sz;
+  return 2LL * s.nf * s.S + (long long)s.Nr * s.Nz * 2 * s.nf * s.Nt;
+}
+
+}  // namespace
+
+tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *adj_dev) {
+  if (!c || !state_n_dev || !adj_dev || !(dt > 0.0) || !std::isfinite(dt)) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  if (adjoint_supported(c) != TC_OK) return TC_ERR_UNSUPPORTED;
   const double2 *Xn = static_cast<const double2 *>(state_n_dev);
   double2 *lam = static_cast<double2 *>(adj_dev);
   try {
@@ -1070,15 +1101,95 @@ tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *a
     launch_refactor(c);
     launch_rhs(c, Xn, c->N0);
     launch_stage(c, c->N0, c->Xp, c->P);
-    // reverse sweep
-    launch_stage_adjoint(c, lam, c->Rb);                    // corrector stage
-    launch_stage_split_adjoint(c, c->Rb, c->Ybar, c->Nb, 0);
-    launch_nonlinear_adjoint(c, c->Xp, c->Nb, c->Xb, 0);    // N(X*)
-    launch_stage_adjoint(c, c->Xb, c->Rb);                  // predictor stage
-    launch_stage_split_adjoint(c, c->Rb, c->Ybar, c->Nb, 1);
-    launch_rhs_adjoint(c, c->Ybar, lam, c->Nb);
-    launch_nonlinear_adjoint(c, Xn, c->Nb, lam, 1, c->Phys);  // N(X^n)
-    launch_herm_project(c, lam);
+    enqueue_adjoint_sweep(c, Xn, c->Xp, c->Phys, lam);
+    ck(cudaGetLastError());
+    int to = 0;
+    ck(cudaMemcpyAsync(&to, &c->scal->timeout, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    if (to) return TC_ERR_TIMEOUT;
+  } catch (const std::bad_alloc &) {
+    return TC_ERR_OOM;
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  return TC_OK;
+}
+
+tc_status tc_record_bytes_per_step(const tc_ctx *c, long long *bytes) {
+  if (!c || !bytes) return TC_ERR_ARG;
+  *bytes = 16 * record_doubles2(c);
+  return TC_OK;
+}
+
+tc_status tc_step_record(tc_ctx *c, int nsteps, double dt, void *record_dev,
+                         long long record_bytes) {
+  if (!c || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return TC_ERR_ARG;
+  if (nsteps > 0 && (!record_dev || record_bytes < 16 * record_doubles2(c) * nsteps))
+    return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  if (adjoint_supported(c) != TC_OK) return TC_ERR_UNSUPPORTED;
+  if (nsteps == 0) return TC_OK;
+  const Sizes &s = c->sz;
+  const long long S = s.S;
+  try {
+    ensure_adjoint(c);
+    char *sb = reinterpret_cast<char *>(c->scal);
+    ck(cudaMemsetAsync(sb + offsetof(DevScalars, nonfinite), 0, sizeof(int), c->stream));
+    double2 *rec = static_cast<double2 *>(record_dev);
+    for (int n = 0; n < nsteps; ++n) {
+      double2 *rX = rec + (long long)n * record_doubles2(c);
+      double2 *rXs = rX + (long long)s.nf * S;
+      double2 *rP = rXs + (long long)s.nf * S;
+      ck(cudaMemcpyAsync(rX, c->X, 16 * (size_t)s.nf * S, cudaMemcpyDeviceToDevice, c->stream));
+      // one step (the default scheme: one corrector), its predictor state
+      // written straight into the record
+      launch_nonlinear(c, c->X, c->N0, &c->scal->rate_bits, 0, rP);
+      launch_dt_policy(c, dt, -1);
+      launch_refactor(c);
+      launch_rhs(c, c->X, c->N0);
+      launch_stage(c, c->N0, rXs, c->P);
+      launch_nonlinear(c, rXs, c->N1, nullptr, 0);
+      launch_stage(c, c->N1, c->X, c->P, rXs);
+    }
+    ck(cudaGetLastError());
+    DevScalars sc;
+    ck(cudaMemcpyAsync(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaStreamSynchronize(c->stream));
+    c->t += dt * nsteps;
+    c->dt_last = dt;
+    if (sc.timeout) return TC_ERR_TIMEOUT;
+    if (c->check && sc.nonfinite) return TC_ERR_NONFINITE;
+  } catch (const std::bad_alloc &) {
+    return TC_ERR_OOM;
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  return TC_OK;
+}
+
+tc_status tc_adjoint_steps(tc_ctx *c, int nsteps, const void *record_dev, double dt,
+                           void *adj_dev) {
+  if (!c || nsteps < 0 || !adj_dev || !(dt > 0.0) || !std::isfinite(dt)) return TC_ERR_ARG;
+  if (nsteps > 0 && !record_dev) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  if (adjoint_supported(c) != TC_OK) return TC_ERR_UNSUPPORTED;
+  if (nsteps == 0) return TC_OK;
+  const Sizes &s = c->sz;
+  const double2 *rec = static_cast<const double2 *>(record_dev);
+  double2 *lam = static_cast<double2 *>(adj_dev);
+  try {
+    ensure_adjoint(c);
+    invalidate_rhs_identity(c);
+    int zero = 0;
+    ck(cudaMemcpyAsync(&c->scal->timeout, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    launch_dt_policy(c, dt, -1);   // the factors of dt
+    launch_refactor(c);
+    for (int n = nsteps - 1; n >= 0; --n) {
+      const double2 *rX = rec + (long long)n * record_doubles2(c);
+      const double2 *rXs = rX + (long long)s.nf * s.S;
+      const double2 *rP = rXs + (long long)s.nf * s.S;
+      enqueue_adjoint_sweep(c, rX, rXs, rP, lam);
+    }
     ck(cudaGetLastError());
     int to = 0;
     ck(cudaMemcpyAsync(&to, &c->scal->timeout, sizeof(int), cudaMemcpyDeviceToHost, c->stream));

@@ -82,6 +82,9 @@ _SIGS = {
     "tc_reset_timing": [_P],
     "tc_nonlinear_noalloc": [_I, _I, _I, _D, _D, _D, _D, _P, _P, _P, _P],
     "tc_adjoint_step": [_P, _P, _D, _P],
+    "tc_record_bytes_per_step": [_P, ctypes.POINTER(ctypes.c_longlong)],
+    "tc_step_record": [_P, _I, _D, _P, ctypes.c_longlong],
+    "tc_adjoint_steps": [_P, _I, _P, _D, _P],
     "tc_nonlinear_adjoint": [_P, _P, _P, _P],
     "tc_stage_solve_adjoint": [_P, _P, _D, _P],
     "tc_objective": [_P, ctypes.POINTER(_D), _P],
@@ -241,6 +244,24 @@ def tc_adjoint_step(ctx, state_n_dev, dt, adj_dev):
     """adj <- P_H J(state_n)^T adj for one step at fixed dt (in place)."""
     _check(_lib.tc_adjoint_step(ctx, _ptr(state_n_dev)[0], float(dt), _ptr(adj_dev)[0]),
            "tc_adjoint_step")
+
+
+def tc_record_bytes_per_step(ctx) -> int:
+    b = ctypes.c_longlong(0)
+    _check(_lib.tc_record_bytes_per_step(ctx, ctypes.byref(b)), "tc_record_bytes_per_step")
+    return b.value
+
+
+def tc_step_record(ctx, nsteps, dt, record_dev):
+    """record_dev: CUDA tensor of at least nsteps * tc_record_bytes_per_step bytes."""
+    nbytes = record_dev.numel() * record_dev.element_size()
+    _check(_lib.tc_step_record(ctx, int(nsteps), float(dt), _ptr(record_dev)[0], int(nbytes)),
+           "tc_step_record")
+
+
+def tc_adjoint_steps(ctx, nsteps, record_dev, dt, adj_dev):
+    _check(_lib.tc_adjoint_steps(ctx, int(nsteps), _ptr(record_dev)[0], float(dt),
+                                 _ptr(adj_dev)[0]), "tc_adjoint_steps")
 
 
 def tc_nonlinear_adjoint(ctx, state_dev, nbar_dev, xbar_dev):

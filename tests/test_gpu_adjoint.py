@@ -182,3 +182,60 @@ def test_gradient_vs_central_differences_adjoint_workload(tc):
     print("adjoint 64^3 200 steps: worst rel diff vs central FD over 16 directions:",
           {k: f"{v:.2e}" for k, v in worst.items()})
     assert worst[1e-3] <= 1e-6
+
+
+def test_recorded_segment_matches_step_by_step(tc):
+    """tc_adjoint_steps over tc_step_record's records equals chained
+    tc_adjoint_step calls on the same states (the records hold the forward
+    run's own predictor states; the single-step entry point recomputes them,
+    which differs only by round-off)."""
+    import torch
+    wl = TINY.scaled(Nr=20, Ntheta=24, Nz=24, mp=3, kp=3)
+    run = tc.Run.from_workload(wl)
+    run.init_perturbation(psi_coefficients(wl.seed, wl.mp, wl.kp), wl.amp,
+                          temperature_coefficients(wl.seed, wl.mp, wl.kp), wl.amp_T)
+    n = 6
+    per = tc.tc_record_bytes_per_step(run.ctx)
+    rec = torch.empty(n * per, dtype=torch.uint8, device="cuda")
+    X0 = run.get_state()
+    tc.tc_step_record(run.ctx, n, wl.dt, rec)
+    X_rec = run.get_state()
+    # the recorded run advanced the state like tc_step
+    ref = tc.Run.from_workload(wl)
+    ref.set_state(X0)
+    ref.step(n, wl.dt)
+    X_plain = ref.get_state()
+    ref.close()
+    assert np.abs(X_rec - X_plain).max() <= 1e-12 * np.abs(X_plain).max()
+    lam0 = hermitian_projection(random_state(71, run.nf, wl.Nr, run.M, run.K))
+    lam_a = dev(lam0)
+    tc.tc_adjoint_steps(run.ctx, n, rec, wl.dt, lam_a)
+    nstate = int(np.prod(run.shape)) * 16
+    states = [rec[k * per:k * per + nstate].view(torch.complex128).reshape(run.shape)
+              for k in range(n)]
+    lam_b = dev(lam0)
+    for k in reversed(range(n)):
+        tc.tc_adjoint_step(run.ctx, states[k], wl.dt, lam_b)
+    run.close()
+    a, b = host(lam_a), host(lam_b)
+    assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
+    np.testing.assert_array_equal(host(states[0]), X0)
+
+
+def test_gradient_recorded_and_recomputed_agree(tc):
+    import torch
+    from paper_1908_00587_gb300.autograd import perturbation_energy
+    wl = TINY.scaled(Nr=20, Ntheta=24, Nz=24, mp=3, kp=3)
+    psi = psi_coefficients(wl.seed, wl.mp, wl.kp)
+    grads = []
+    for budget in (4 << 30, 0):
+        run = tc.Run.from_workload(wl)
+        run.init_perturbation(psi, wl.amp)
+        su, _ = tc.tc_get_ic_scales(run.ctx)
+        pt = torch.from_numpy(psi.copy()).requires_grad_(True)
+        J = perturbation_energy(run, pt, 9, wl.dt, -su, None, 0.0, checkpoint=4,
+                                record_budget=budget)
+        J.backward()
+        grads.append(pt.grad.numpy().copy())
+        run.close()
+    assert np.abs(grads[0] - grads[1]).max() <= 1e-9 * np.abs(grads[1]).max()
