@@ -250,8 +250,8 @@ tc_status tc_adjoint_step(tc_ctx *ctx, const void *state_n_dev, double dt, void 
 /* Recorded steps for the reverse sweep (checkpoint segments).
  * tc_record_bytes_per_step: bytes one recorded step takes: X^n and the
  *   predictor state X* (state layout each), then the physical-grid fields of
- *   X^n (complex128 [Nr][Nz][2 nfields][Ntheta]: per component the pairs
- *   value + i d/dtheta and d/dr + i d/dz).
+ *   X^n and of X* (complex128 [Nr][Nz][2 nfields][Ntheta] each: per component
+ *   the pairs value + i d/dtheta and d/dr + i d/dz).
  * tc_step_record: advances nsteps steps of fixed dt > 0 like tc_step and
  *   writes step n's record at record_dev + n * that size (device,
  *   caller-owned, record_bytes long; TC_ERR_ARG if too short).

@@ -1050,13 +1050,14 @@ extern "C" {
 namespace {
 
 // Reverse sweep of one step given its linearisation points: X^n, the
-// predictor state X* and the physical-grid fields of X^n.  lam: lambda^(n+1)
-// in, lambda^n out.  The factors and influence data must be those of dt.
+// predictor state X* and the physical-grid fields of X^n and (nullable) of X*.
+// lam: lambda^(n+1) in, lambda^n out.  The factors and influence data must be
+// those of dt.
 void enqueue_adjoint_sweep(tc_ctx *c, const double2 *Xn, const double2 *Xs,
-                           const double2 *phys, double2 *lam) {
+                           const double2 *phys, const double2 *phys_s, double2 *lam) {
   launch_stage_adjoint(c, lam, c->Rb);                      // corrector stage
   launch_stage_split_adjoint(c, c->Rb, c->Ybar, c->Nb, 0);
-  launch_nonlinear_adjoint(c, Xs, c->Nb, c->Xb, 0);         // N(X*)
+  launch_nonlinear_adjoint(c, Xs, c->Nb, c->Xb, 0, phys_s); // N(X*)
   launch_stage_adjoint(c, c->Xb, c->Rb);                    // predictor stage
   launch_stage_split_adjoint(c, c->Rb, c->Ybar, c->Nb, 1);
   launch_rhs_adjoint(c, c->Ybar, lam, c->Nb);
@@ -1073,10 +1074,13 @@ tc_status adjoint_supported(const tc_ctx *c) {
 }
 
 // Record of one step: X^n, X* (nf S complex each), then the physical fields
-// of X^n (Nr Nz 2 nf Nt complex).
-long long record_doubles2(const tc_ctx *c) {
+// of X^n and of X* (Nr Nz 2 nf Nt complex each).
+long long phys_doubles2(const tc_ctx *c) {
   const Sizes &s = c->sz;
-  return 2LL * s.nf * s.S + (long long)s.Nr * s.Nz * 2 * s.nf * s.Nt;
+  return (long long)s.Nr * s.Nz * 2 * s.nf * s.Nt;
+}
+long long record_doubles2(const tc_ctx *c) {
+  return 2LL * c->sz.nf * c->sz.S + 2 * phys_doubles2(c);
 }
 
 }  // namespace
@@ -1101,7 +1105,7 @@ tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *a
     launch_refactor(c);
     launch_rhs(c, Xn, c->N0);
     launch_stage(c, c->N0, c->Xp, c->P);
-    enqueue_adjoint_sweep(c, Xn, c->Xp, c->Phys, lam);
+    enqueue_adjoint_sweep(c, Xn, c->Xp, c->Phys, nullptr, lam);
     ck(cudaGetLastError());
     int to = 0;
     ck(cudaMemcpyAsync(&to, &c->scal->timeout, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -1140,15 +1144,17 @@ tc_status tc_step_record(tc_ctx *c, int nsteps, double dt, void *record_dev,
       double2 *rX = rec + (long long)n * record_doubles2(c);
       double2 *rXs = rX + (long long)s.nf * S;
       double2 *rP = rXs + (long long)s.nf * S;
+      double2 *rPs = rP + phys_doubles2(c);
       ck(cudaMemcpyAsync(rX, c->X, 16 * (size_t)s.nf * S, cudaMemcpyDeviceToDevice, c->stream));
-      // one step (the default scheme: one corrector), its predictor state
-      // written straight into the record
+      // one step (the default scheme: one corrector), its predictor state and
+      // both nonlinear evaluations' physical fields written straight into
+      // the record
       launch_nonlinear(c, c->X, c->N0, &c->scal->rate_bits, 0, rP);
       launch_dt_policy(c, dt, -1);
       launch_refactor(c);
       launch_rhs(c, c->X, c->N0);
       launch_stage(c, c->N0, rXs, c->P);
-      launch_nonlinear(c, rXs, c->N1, nullptr, 0);
+      launch_nonlinear(c, rXs, c->N1, nullptr, 0, rPs);
       launch_stage(c, c->N1, c->X, c->P, rXs);
     }
     ck(cudaGetLastError());
@@ -1188,7 +1194,7 @@ tc_status tc_adjoint_steps(tc_ctx *c, int nsteps, const void *record_dev, double
       const double2 *rX = rec + (long long)n * record_doubles2(c);
       const double2 *rXs = rX + (long long)s.nf * s.S;
       const double2 *rP = rXs + (long long)s.nf * s.S;
-      enqueue_adjoint_sweep(c, rX, rXs, rP, lam);
+      enqueue_adjoint_sweep(c, rX, rXs, rP, rP + phys_doubles2(c), lam);
     }
     ck(cudaGetLastError());
     int to = 0;
