@@ -547,6 +547,63 @@ cudaError_t ensure_step_graph(tc_ctx *c, double dt_fixed) {
   return cudaSuccess;
 }
 
+
+// Capture `enqueue` (kernels and device copies on c->stream) into cg, or keep
+// the graph captured before for the same key; then launch it on c->stream.
+// Direct launches when timing is on, graphs are off, or the capture fails.
+template <typename F>
+void run_cached(tc_ctx *c, tc_ctx::CachedGraph &cg, const void *a, const void *b, int n,
+                double dt, F enqueue) {
+  if (!c->use_graph || c->timing) {
+    enqueue();
+    return;
+  }
+  const bool same = cg.exec && cg.gen == c->gen && cg.a == a && cg.b == b && cg.n == n &&
+                    cg.dt == dt;
+  if (!same) {
+    if (cg.exec) cudaGraphExecDestroy(cg.exec);
+    if (cg.g) cudaGraphDestroy(cg.g);
+    cg.exec = nullptr;
+    cg.g = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) {
+      cudaStream_t user = c->stream;
+      const long long l0 = c->launches;
+      c->stream = c->cap_stream;
+      c->capturing = 1;
+      e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        enqueue();
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->cap_stream, &g);
+        cg.g = g;
+      }
+      c->capturing = 0;
+      c->stream = user;
+      cg.launches = c->launches - l0;
+      c->launches = l0;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&cg.exec, cg.g, 0);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (cg.g) cudaGraphDestroy(cg.g);
+      cg.g = nullptr;
+      cg.exec = nullptr;
+      enqueue();
+      return;
+    }
+    cg.gen = c->gen;
+    cg.a = a;
+    cg.b = b;
+    cg.n = n;
+    cg.dt = dt;
+  }
+  ck(cudaGraphLaunch(cg.exec, c->stream));
+  c->launches += cg.launches;
+}
+
 }  // namespace tc
 
 using namespace tc;
@@ -633,6 +690,10 @@ tc_status tc_destroy(tc_ctx *c) {
   if (!c) return TC_OK;
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   if (c->step_graph) cudaGraphDestroy(c->step_graph);
+  for (tc_ctx::CachedGraph *cg : {&c->rec_graph, &c->adj_graph}) {
+    if (cg->exec) cudaGraphExecDestroy(cg->exec);
+    if (cg->g) cudaGraphDestroy(cg->g);
+  }
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void *p : c->allocs) cudaFree(p);
   for (auto &t : c->timers)
@@ -1119,6 +1180,7 @@ tc_status tc_adjoint_step(tc_ctx *c, const void *state_n_dev, double dt, void *a
   return TC_OK;
 }
 
+
 tc_status tc_record_bytes_per_step(const tc_ctx *c, long long *bytes) {
   if (!c || !bytes) return TC_ERR_ARG;
   *bytes = 16 * record_doubles2(c);
@@ -1140,12 +1202,13 @@ tc_status tc_step_record(tc_ctx *c, int nsteps, double dt, void *record_dev,
     char *sb = reinterpret_cast<char *>(c->scal);
     ck(cudaMemsetAsync(sb + offsetof(DevScalars, nonfinite), 0, sizeof(int), c->stream));
     double2 *rec = static_cast<double2 *>(record_dev);
+    run_cached(c, c->rec_graph, record_dev, nullptr, nsteps, dt, [&]() {
     for (int n = 0; n < nsteps; ++n) {
       double2 *rX = rec + (long long)n * record_doubles2(c);
       double2 *rXs = rX + (long long)s.nf * S;
       double2 *rP = rXs + (long long)s.nf * S;
       double2 *rPs = rP + phys_doubles2(c);
-      ck(cudaMemcpyAsync(rX, c->X, 16 * (size_t)s.nf * S, cudaMemcpyDeviceToDevice, c->stream));
+      cudaMemcpyAsync(rX, c->X, 16 * (size_t)s.nf * S, cudaMemcpyDeviceToDevice, c->stream);
       // one step (the default scheme: one corrector), its predictor state and
       // both nonlinear evaluations' physical fields written straight into
       // the record
@@ -1157,6 +1220,7 @@ tc_status tc_step_record(tc_ctx *c, int nsteps, double dt, void *record_dev,
       launch_nonlinear(c, rXs, c->N1, nullptr, 0, rPs);
       launch_stage(c, c->N1, c->X, c->P, rXs);
     }
+    });
     ck(cudaGetLastError());
     DevScalars sc;
     ck(cudaMemcpyAsync(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
@@ -1188,14 +1252,16 @@ tc_status tc_adjoint_steps(tc_ctx *c, int nsteps, const void *record_dev, double
     invalidate_rhs_identity(c);
     int zero = 0;
     ck(cudaMemcpyAsync(&c->scal->timeout, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    launch_dt_policy(c, dt, -1);   // the factors of dt
-    launch_refactor(c);
-    for (int n = nsteps - 1; n >= 0; --n) {
-      const double2 *rX = rec + (long long)n * record_doubles2(c);
-      const double2 *rXs = rX + (long long)s.nf * s.S;
-      const double2 *rP = rXs + (long long)s.nf * s.S;
-      enqueue_adjoint_sweep(c, rX, rXs, rP, rP + phys_doubles2(c), lam);
-    }
+    run_cached(c, c->adj_graph, record_dev, adj_dev, nsteps, dt, [&]() {
+      launch_dt_policy(c, dt, -1);   // the factors of dt
+      launch_refactor(c);
+      for (int n = nsteps - 1; n >= 0; --n) {
+        const double2 *rX = rec + (long long)n * record_doubles2(c);
+        const double2 *rXs = rX + (long long)s.nf * s.S;
+        const double2 *rP = rXs + (long long)s.nf * s.S;
+        enqueue_adjoint_sweep(c, rX, rXs, rP, rP + phys_doubles2(c), lam);
+      }
+    });
     ck(cudaGetLastError());
     int to = 0;
     ck(cudaMemcpyAsync(&to, &c->scal->timeout, sizeof(int), cudaMemcpyDeviceToHost, c->stream));

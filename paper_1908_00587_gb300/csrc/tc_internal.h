@@ -211,6 +211,16 @@ struct tc_ctx {
   long long graph_gen = -1;
   double graph_dt = 0.0;
   long long graph_launches = 0; // kernels in one replay
+  // recorded-segment graphs (tc_step_record, tc_adjoint_steps), keyed by
+  // their buffers, length, step and the generation counter
+  struct CachedGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long gen = -1, launches = 0;
+    const void *a = nullptr, *b = nullptr;
+    int n = 0;
+    double dt = 0.0;
+  } rec_graph, adj_graph;
   tc::KernelTimer timers[tc::KNUM];
 };
 
