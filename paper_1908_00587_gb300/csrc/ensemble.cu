@@ -4,10 +4,11 @@
 // member is captured once into a CUDA graph: the members are independent
 // branches between a fork and a join, so one graph launch replays all of them
 // and the GPU runs the branches concurrently, filling the SMs that a single
-// small run leaves idle.  The graph is rebuilt only when a member's step
-// changes.  A persistent kernel was not used: every stage of a run depends on
-// the previous one, which inside one launch would need grid-wide barriers on
-// a shared GPU; graph replay removes the same per-launch host overhead.
+// small run leaves idle.  The graph is rebuilt only when a member's step or
+// options change.  A persistent kernel was not used: every stage of a run
+// depends on the previous one, which inside one launch would need grid-wide
+// barriers on a shared GPU; graph replay removes the same per-launch host
+// overhead.
 //
 // Tiles: before the first step, each size class (Nr, Ntheta, Nz, fields,
 // precision) is tuned once by timing the nonlinear stage for candidate tile
@@ -35,6 +36,7 @@ struct tc_ens {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<double> graph_dt;
+  std::vector<long long> graph_gen;   // members' launch-parameter generations at capture
 };
 
 namespace tc {
@@ -193,8 +195,9 @@ tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt) {
     if (e->m[i]->timing) tc_set_option(e->m[i], "timing", 0);
   }
   if (nsteps == 0) return TC_OK;
-  const bool same = e->exec && (int)e->graph_dt.size() == n &&
-                    std::equal(e->graph_dt.begin(), e->graph_dt.end(), dt);
+  bool same = e->exec && (int)e->graph_dt.size() == n &&
+              std::equal(e->graph_dt.begin(), e->graph_dt.end(), dt);
+  for (int i = 0; same && i < n; ++i) same = e->graph_gen[i] == e->m[i]->gen;
   if (!same) {
     drop_graph(e);
     // capture one step of every member as independent branches
@@ -223,6 +226,8 @@ tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt) {
       return TC_ERR_CUDA;
     }
     e->graph_dt.assign(dt, dt + n);
+    e->graph_gen.resize(n);
+    for (int i = 0; i < n; ++i) e->graph_gen[i] = e->m[i]->gen;
   }
   for (int i = 0; i < n; ++i) {
     tc_ctx *c = e->m[i];

@@ -86,3 +86,29 @@ def test_ensemble_members_match_oracle(tc):
                   for f in range(X.shape[0]))
         assert err <= 1e-10, (i, err)
     tc.tc_ensemble_destroy(ens)
+
+
+def test_ensemble_graph_follows_member_options(tc):
+    """Changing a member's option after the graph was captured re-captures it:
+    the member then steps exactly like a run with that option."""
+    members = [w.scaled(Nr=20, Ntheta=24, Nz=24) for w in ensemble_members(2)]
+    ens = tc.tc_ensemble_create(members, autotune_tiles=False)
+    dts, shapes = [], []
+    for i, wl in enumerate(members):
+        dt, shape = _init(tc, tc.tc_ensemble_member(ens, i), wl)
+        dts.append(dt)
+        shapes.append(shape)
+    tc.tc_ensemble_step(ens, 2, dts)
+    tc.tc_set_option(tc.tc_ensemble_member(ens, 0), "n_corr", 2)
+    tc.tc_ensemble_step(ens, 3, dts)
+    X = np.empty(shapes[0], dtype=np.complex128)
+    tc.tc_get_state(tc.tc_ensemble_member(ens, 0), X)
+    tc.tc_ensemble_destroy(ens)
+    run = tc.Run.from_workload(members[0])
+    _init(tc, run.ctx, members[0])
+    run.step(2, dts[0])
+    run.set_option("n_corr", 2)
+    run.step(3, dts[0])
+    ref = run.get_state()
+    run.close()
+    np.testing.assert_array_equal(X, ref)
