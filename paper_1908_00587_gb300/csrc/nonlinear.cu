@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 
 #include "fft.cuh"
 #include "tc_internal.h"
@@ -57,53 +58,13 @@ __device__ __forceinline__ void load_tw(V2<T> *dst, const double2 *src, int n) {
 // the (0,0) mode of u_theta, u_z, T; u_b (everything else, including the
 // (0,0) mode of u_r) goes through the FP32 transforms, which supply
 // u_b.grad u_b with its curvature terms.  The products in which U or Tbar
-// takes part are diagonal in (m, k) and are formed here in FP64:
+// takes part are diagonal in (m, k) and are formed in FP64 in k_zfwd:
 //   N_r = -(a u_r - 2 (U_theta/r) u_theta) + [U_theta^2 / r]_(0,0)
 //   N_theta = -(a u_theta + (U_theta/r + U_theta') u_r)
 //   N_z = -(a u_z + U_z' u_r) + Gr T          N_T = -(a T + Tbar' u_r)
 // with a = i (m U_theta / r + beta U_z) and (u, T) the u_b coefficients, the
 // buoyancy Gr T on the full temperature.  In exact arithmetic the sum equals
 // the dealiased product: multiplying by a function of r creates no new modes.
-__device__ double2 mean_flow_terms(const NLParams &p, int g, int r, int m, int kk) {
-  const Sizes &s = p.sz;
-  const double *pr = p.prof + r * 8;
-  const double Ut = pr[0], Uz = pr[1], dUt = pr[2], dUz = pr[3], dTb = pr[4];
-  const double ir = p.rad.inv_r[r];
-  const long long i = (long long)r * s.nmode + (long long)m * s.NK + kk;
-  const bool mean = (m == 0 && kk == 0);
-  const double beta = p.alpha * kval(kk, s.K, s.NK);
-  const double al = m * Ut * ir + beta * Uz;              // a = i al (0 for the mean)
-  const double2 zero = {0.0, 0.0};
-  const double2 ur = p.Xfull[i];
-  auto ia = [&](double2 v) { return double2{-al * v.y, al * v.x}; };
-  if (g == 0) {
-    const double2 ut = mean ? zero : p.Xfull[s.S + i];
-    const double2 t = ia(ur);
-    double2 o = double2{-(t.x - 2.0 * Ut * ir * ut.x), -(t.y - 2.0 * Ut * ir * ut.y)};
-    if (mean) o.x += Ut * Ut * ir;
-    return o;
-  }
-  if (g == 1) {
-    const double2 ut = mean ? zero : p.Xfull[s.S + i];
-    const double2 t = ia(ut);
-    const double c = Ut * ir + dUt;
-    return double2{-(t.x + c * ur.x), -(t.y + c * ur.y)};
-  }
-  if (g == 2) {
-    const double2 uz = mean ? zero : p.Xfull[2 * s.S + i];
-    const double2 t = ia(uz);
-    double2 o = double2{-(t.x + dUz * ur.x), -(t.y + dUz * ur.y)};
-    if (s.nf == 4) {
-      const double2 T = p.Xfull[3 * s.S + i];
-      o.x += p.Gr * T.x;
-      o.y += p.Gr * T.y;
-    }
-    return o;
-  }
-  const double2 T = mean ? zero : p.Xfull[3 * s.S + i];
-  const double2 t = ia(T);
-  return double2{-(t.x + dTb * ur.x), -(t.y + dTb * ur.y)};
-}
 
 // Mean profiles of the (0,0) mode and their radial derivatives, one thread per r.
 __global__ void k_meanprof(const double2 *__restrict__ X, double *__restrict__ prof, Sizes s,
@@ -250,13 +211,24 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   V2<T> *out = (ph == A) ? B : A;
   const double rr = p.rad.r[r];
   const T inv_r = (T)p.rad.inv_r[r];
-  // CFL: running maxima of |u_r|, |u_theta|, |u_z|, kept as bit patterns
-  // (non-negative doubles order like their bits: integer max, no FP64 issue
-  // slot); the divisions by the spacings come once per thread after the loop
-  // (division by a positive constant is monotone, so the max is unchanged)
-  unsigned long long mr = 0ull, mt = 0ull, mz = 0ull;
+  // CFL: running maxima of |u_r|, |u_theta|, |u_z| in the transforms'
+  // precision, kept as bit patterns (non-negative floating-point values order
+  // like their bits: integer max, no FP64 issue slot); the divisions by the
+  // spacings come once per thread after the loop (division by a positive
+  // constant is monotone, so the max is unchanged).  The FP32 form adds the
+  // mean profile in FP32: the CFL step then carries FP32 rounding, like the
+  // rest of that form's nonlinear stage.
+  using CflBits = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned>::type;
+  CflBits mr = 0, mt = 0, mz = 0;
   double nu = 0.0, nT = 0.0;
-  auto bits = [](double v) { return (unsigned long long)__double_as_longlong(fabs(v)); };
+  auto bits = [](T v) -> CflBits {
+    if constexpr (sizeof(T) == 8) return (CflBits)__double_as_longlong(fabs(v));
+    else return (CflBits)__float_as_uint(fabsf(v));
+  };
+  auto val = [](CflBits b) -> double {
+    if constexpr (sizeof(T) == 8) return __longlong_as_double((long long)b);
+    else return (double)__uint_as_float(b);
+  };
   for (int t = threadIdx.x; t < nl * Nt; t += blockDim.x) {
     const int2 a = divmod(t, Nt, p.fNt);
     const int j = a.y;
@@ -275,7 +247,7 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     // full velocity for the CFL bound (mixed: the transforms carry u' only)
     // (only the FP32 instantiation runs the mixed form)
     const bool mixed = sizeof(T) == 4 && p.mixed;
-    const double Ut = mixed ? p.prof[r * 8 + 0] : 0.0, Uz = mixed ? p.prof[r * 8 + 1] : 0.0;
+    const T Ut = mixed ? (T)p.prof[r * 8 + 0] : (T)0, Uz = mixed ? (T)p.prof[r * 8 + 1] : (T)0;
     if (mode == 1) {
       nu = fmax(nu, sqrt((double)ur * ur + (double)ut * ut + (double)uz * uz));
       if (s.nf == 4) nT = fmax(nT, fabs((double)b[6 * Ntp].x));
@@ -304,9 +276,9 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     o[0] = V2<T>{Nr_, Nt_};
     o[Ntp] = V2<T>{Nz_, NT_};
     if (rate_bits) {
-      mr = max(mr, bits((double)ur));
-      mt = max(mt, bits(mixed ? (double)ut + Ut : (double)ut));
-      mz = max(mz, bits(mixed ? (double)uz + Uz : (double)uz));
+      mr = max(mr, bits(ur));
+      mt = max(mt, bits(mixed ? ut + Ut : ut));
+      mz = max(mz, bits(mixed ? uz + Uz : uz));
     }
   }
   if (mode == 1) {
@@ -321,7 +293,6 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     return;
   }
   if (rate_bits) {
-    auto val = [](unsigned long long b) { return __longlong_as_double((long long)b); };
     double rate = fmax(val(mr) / p.rad.dr_min[r], fmax(val(mt) / (rr * p.dth), val(mz) / p.dz));
     for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
     if ((threadIdx.x & 31) == 0) atomic_max_pos(rate_bits, rate);
@@ -378,20 +349,85 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
   __syncthreads();
   V2<T> *res = fft_batch<-1>(A, B, p.pz, nb, Np, tw);
   const double scale = 1.0 / ((double)s.Nt * (double)s.Nz);
+  if (!p.mixed) {
+    for (int t = threadIdx.x; t < nb * s.NK; t += blockDim.x) {
+      const int2 a = divmod(t, s.NK, p.fNK);
+      const int kk = a.y;
+      const int2 b = divmod(a.x, nm, fnm);
+      const int mi = b.y;
+      const int g = b.x;
+      const V2<T> v = res[(g * nm + mi) * Np + spad(kpos(kk, s.K, s.NK, Nz))];
+      N[(long long)g * s.S + (long long)r * s.nmode + (long long)(m0 + mi) * s.NK + kk] =
+          double2{(double)v.x * scale, (double)v.y * scale};
+    }
+    return;
+  }
+  // Mixed precision: the FP32 transform (scaled in FP32: 1/(Ntheta Nz), exact
+  // for power-of-two sizes) plus the FP64 products with the mean profiles of
+  // this radial level,
+  //   N_r += -(a u_r - 2 (U_theta/r) u_theta) (+ U_theta^2/r for the mean)
+  //   N_theta += -(a u_theta + (U_theta/r + U_theta') u_r)
+  //   N_z += -(a u_z + U_z' u_r) + Gr T      N_T += -(a T + Tbar' u_r)
+  // with a = i al, al = m U_theta/r + beta U_z from a table built once per
+  // CTA (it serves every field of a mode).
+  V2<T> *scratch = (res == A) ? B : A;
+  double *alt = reinterpret_cast<double *>(scratch);   // [mi][kk], MB NK <= 2 nf MB Np
+  const double *pr = p.prof + r * 8;
+  const double ir = p.rad.inv_r[r];
+  const double Utr = pr[0] * ir, Uz = pr[1], dUt = pr[2], dUz = pr[3], dTb = pr[4];
+  const double c0 = 2.0 * Utr, c1 = Utr + dUt;
+  for (int t = threadIdx.x; t < nm * s.NK; t += blockDim.x) {
+    const int2 a = divmod(t, s.NK, p.fNK);
+    alt[t] = (double)(m0 + a.x) * Utr + p.alpha * kval(a.y, s.K, s.NK) * Uz;
+  }
+  __syncthreads();
+  const T fscale = (T)scale;
   for (int t = threadIdx.x; t < nb * s.NK; t += blockDim.x) {
     const int2 a = divmod(t, s.NK, p.fNK);
     const int kk = a.y;
     const int2 b = divmod(a.x, nm, fnm);
     const int mi = b.y;
     const int g = b.x;
+    const int m = m0 + mi;
     const V2<T> v = res[(g * nm + mi) * Np + spad(kpos(kk, s.K, s.NK, Nz))];
-    double2 out = double2{(double)v.x * scale, (double)v.y * scale};
-    if (p.mixed) {
-      const double2 lin = mean_flow_terms(p, g, r, m0 + mi, kk);
-      out.x += lin.x;
-      out.y += lin.y;
+    double2 out = double2{(double)(v.x * fscale), (double)(v.y * fscale)};
+    const long long i = (long long)r * s.nmode + (long long)m * s.NK + kk;
+    const bool mean = (m == 0 && kk == 0);
+    const double al = alt[mi * s.NK + kk];
+    const double2 ur = p.Xfull[i];
+    const double2 zero = {0.0, 0.0};
+    // w: the field a multiplies; c, x: the coefficient and field of the other term
+    double2 w, x;
+    double c;
+    if (g == 0) {
+      w = ur;
+      x = mean ? zero : p.Xfull[s.S + i];
+      c = -c0;
+    } else if (g == 1) {
+      w = mean ? zero : p.Xfull[s.S + i];
+      x = ur;
+      c = c1;
+    } else if (g == 2) {
+      w = mean ? zero : p.Xfull[2 * s.S + i];
+      x = ur;
+      c = dUz;
+    } else {
+      w = mean ? zero : p.Xfull[3 * s.S + i];
+      x = ur;
+      c = dTb;
     }
-    N[(long long)g * s.S + (long long)r * s.nmode + (long long)(m0 + mi) * s.NK + kk] = out;
+    // out -= i al w + c x
+    out.x = fma(al, w.y, out.x);
+    out.y = fma(-al, w.x, out.y);
+    out.x = fma(-c, x.x, out.x);
+    out.y = fma(-c, x.y, out.y);
+    if (g == 0 && mean) out.x += Utr * pr[0];
+    if (g == 2 && s.nf == 4) {
+      const double2 T2 = p.Xfull[3 * s.S + i];
+      out.x = fma(p.Gr, T2.x, out.x);
+      out.y = fma(p.Gr, T2.y, out.y);
+    }
+    N[(long long)g * s.S + i] = out;
   }
 }
 
