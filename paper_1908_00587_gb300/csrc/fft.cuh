@@ -67,21 +67,89 @@ __device__ __forceinline__ void dft4(V *v) {
   v[3] = csub(t1, t3);
 }
 
+// Cosine-tangent form of a twiddle w = c (1 + i t), c = cos, t = tan of its
+// angle: w v = c (v + i t v).  Forming v + i t v takes two FMAs and applying c
+// while adding into a butterfly output one FMA per component, so a twiddled
+// radix-2 step costs 6 FMAs instead of a complex product (4) plus 4 additions
+// (Linzer and Feig, "Modified FFTs for fused multiply-add architectures",
+// Math. Comp. 60, 1993).  With FMA the result carries the usual complex-product
+// error for every angle: c t = sin to rounding, and the rounding of v + i t v
+// is scaled back by c.  The tables keep |c| >= 2^-60 so that t stays finite.
+template <typename T>
+__device__ __forceinline__ T fmat(T a, T b, T c) {
+  if constexpr (sizeof(T) == 8) return __fma_rn(a, b, c);
+  else return __fmaf_rn(a, b, c);
+}
+
+// v + i t v
+template <typename V, typename T>
+__device__ __forceinline__ V ct_u(V v, T t) {
+  return V{fmat(-t, v.y, v.x), fmat(t, v.x, v.y)};
+}
+
+// a + c u and a - c u
+template <typename V, typename T>
+__device__ __forceinline__ void ct_pm(V a, T c, V u, V &plus, V &minus) {
+  plus = V{fmat(c, u.x, a.x), fmat(c, u.y, a.y)};
+  minus = V{fmat(-c, u.x, a.x), fmat(-c, u.y, a.y)};
+}
+
+// Twiddled length-4 DFT, out_p = sum_q w^q v_q exp(S 2 pi i p q / 4), in place,
+// with w = c1 (1 + i t1) and w^2 = c2 (1 + i t2).  Decimation in time:
+// v_0 +- w^2 v_2 and v_1 +- w^2 v_3, then w times the latter: 24 FMAs.
+template <int S, typename V, typename T>
+__device__ __forceinline__ void dft4_ct(V *v, T c1, T t1, T c2, T t2) {
+  V y0, y1, p0, p1;
+  ct_pm(v[0], c2, ct_u(v[2], t2), y0, y1);
+  ct_pm(v[1], c2, ct_u(v[3], t2), p0, p1);
+  ct_pm(y0, c1, ct_u(p0, t1), v[0], v[2]);
+  // y1 +- (S i) w p1
+  const V u = ct_u(p1, t1);
+  const T sc = (T)S * c1;
+  v[1] = V{fmat(-sc, u.y, y1.x), fmat(sc, u.x, y1.y)};
+  v[3] = V{fmat(sc, u.y, y1.x), fmat(-sc, u.x, y1.y)};
+}
+
+// Twiddled length-8 DFT, out_p = sum_q w^q v_q exp(S 2 pi i p q / 8), in place.
+// ct[0..4] = w^4, w, w^2, g, g^2 with g = w exp(S i pi / 4), each (c, t).
+// Pairs q, q + 4 first (v_q +- w^4 v_(q+4)); the even outputs are then the
+// twiddled length-4 DFT of the sums with w, the odd ones that of the
+// differences with g: 72 FMAs.
+template <int S, typename V, typename T>
+__device__ __forceinline__ void dft8_ct(V *v, const V *ct) {
+  V P[4], Q[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ct_pm(v[q], (T)ct[0].x, ct_u(v[q + 4], (T)ct[0].y), P[q], Q[q]);
+  dft4_ct<S>(P, (T)ct[1].x, (T)ct[1].y, (T)ct[2].x, (T)ct[2].y);
+  dft4_ct<S>(Q, (T)ct[3].x, (T)ct[3].y, (T)ct[4].x, (T)ct[4].y);
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    v[2 * p] = P[p];
+    v[2 * p + 1] = Q[p];
+  }
+}
+
 // Second half of the length-8 DFT: a_q = v_q + v_(q+4), b_q = v_q - v_(q+4) given.
+// The odd outputs are the length-4 DFT of g^q b_q with g = exp(S i pi / 4) =
+// h (1 + S i): g^2 = S i is a swap, g is the cosine-tangent form with c = h,
+// t = S (v + i t v is two additions).
 template <int S, typename V>
 __device__ __forceinline__ void dft8_tail(V *a, V *b, V *v) {
   using T = decltype(v[0].x);
   const T h = (T)0.70710678118654752440;  // sqrt(2)/2
-  // b_q *= exp(S 2 pi i q / 8)
-  {
-    V x = b[1];
-    b[1] = V{h * (x.x - (T)S * x.y), h * ((T)S * x.x + x.y)};
-    b[2] = mul_si<S>(b[2]);
-    x = b[3];
-    b[3] = V{h * (-x.x - (T)S * x.y), h * ((T)S * x.x - x.y)};
-  }
   dft4<S>(a);
-  dft4<S>(b);
+  {
+    const V s2 = mul_si<S>(b[2]), s3 = mul_si<S>(b[3]);
+    const V y0 = cadd(b[0], s2), y1 = csub(b[0], s2);
+    const V p0 = cadd(b[1], s3), p1 = csub(b[1], s3);
+    // v + S i v
+    const V u0 = V{p0.x - (T)S * p0.y, p0.y + (T)S * p0.x};
+    const V u1 = V{p1.x - (T)S * p1.y, p1.y + (T)S * p1.x};
+    ct_pm(y0, h, u0, b[0], b[2]);
+    const T sh = (T)S * h;
+    b[1] = V{fmat(-sh, u1.y, y1.x), fmat(sh, u1.x, y1.y)};
+    b[3] = V{fmat(sh, u1.y, y1.x), fmat(-sh, u1.x, y1.y)};
+  }
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
     v[2 * p] = a[p];
@@ -179,8 +247,10 @@ __device__ __forceinline__ int fdiv(int n, FastDiv f) {
 }
 
 // One Stockham pass (pass p of plan pl, stride Ns) over `batch` transforms
-// stored `bstride` apart.  twp: this pass's twiddles, w^(q k) at (q-1) Ns + k,
-// so the threads of a warp (consecutive k) read consecutive entries.  The
+// stored `bstride` apart.  twp: this pass's twiddles, slot i at i Ns + k, so the
+// threads of a warp (consecutive k) read consecutive entries: for radix 4 and
+// 8 the cosine-tangent slots named in butterfly(), for radix 2, 3 and 5
+// w^(q k) as (cos, sin) in slot q - 1.  The
 // index arithmetic divides by the plan's fixed divisors with FastDiv.
 // ZMID (radix 8, first pass only): inputs q = 3, 4 are known zeros.
 // Butterfly j of one transform, s -> d (both the transform's own storage).
@@ -200,14 +270,33 @@ __device__ __forceinline__ void butterfly(const V *__restrict__ s, V *__restrict
     for (int p = 0; p < R; ++p) d[spad(base + p)] = v[p];
     return;
   }
-  if (Ns > 1) {
+  using T = decltype(v[0].x);
+  if constexpr (R == 4 || R == 8) {
+    // cosine-tangent twiddles: slots w, w^2 (radix 4); w^4, w, w^2, g, g^2
+    // (radix 8); the inverse conjugates them, t -> -t
+    if (Ns > 1) {
+      constexpr int NT = R == 4 ? 2 : 5;
+      V ct[NT];
 #pragma unroll
-    for (int q = 1; q < R; ++q) {
-      const V w = twp[(q - 1) * Ns + k];
-      v[q] = (S < 0) ? cmul(v[q], w) : cmulc(v[q], w);
+      for (int i = 0; i < NT; ++i) {
+        const V w = twp[i * Ns + k];
+        ct[i] = V{w.x, (S < 0) ? w.y : -w.y};
+      }
+      if constexpr (R == 4) dft4_ct<S>(v, (T)ct[0].x, (T)ct[0].y, (T)ct[1].x, (T)ct[1].y);
+      else dft8_ct<S, V, T>(v, ct);
+    } else {
+      dftR<R, S>(v);
     }
+  } else {
+    if (Ns > 1) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        const V w = twp[(q - 1) * Ns + k];
+        v[q] = (S < 0) ? cmul(v[q], w) : cmulc(v[q], w);
+      }
+    }
+    dftR<R, S>(v);
   }
-  dftR<R, S>(v);
   const int base = (j - k) * R + k;
 #pragma unroll
   for (int p = 0; p < R; ++p) d[spad(base + p * Ns)] = v[p];

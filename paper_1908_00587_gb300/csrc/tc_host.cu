@@ -154,17 +154,40 @@ void fill_plan_twiddles(const FFTPlan &pl, double2 *out) {
   const long double pi = 3.141592653589793238462643383279502884L;
   const int n = pl.n;
   for (int i = 0; i < n; ++i) out[i] = double2{0.0, 0.0};
+  // w = exp(-i a) as (cos a, -sin a), or in cosine-tangent form (c, t) with
+  // w = c (1 + i t); |c| is kept >= 2^-60 so that t is finite (the product
+  // c t still rounds to -sin a)
+  auto angle = [&](long long q) { return 2.0L * pi * (long double)(q % n) / (long double)n; };
+  auto ct = [](long double a) {
+    long double c = cosl(a);
+    const long double lo = 8.6736173798840354720596224069595337e-19L;   // 2^-60
+    if (fabsl(c) < lo) c = c < 0 ? -lo : lo;
+    return double2{(double)c, (double)(-sinl(a) / c)};
+  };
   int Ns = 1;
   for (int p = 0; p < pl.npass; ++p) {
     const int R = pl.radix[p];
+    double2 *o = out + pl.tw_off[p];
     if (Ns > 1) {
       const int step = n / (Ns * R);
-      for (int q = 1; q < R; ++q)
-        for (int k = 0; k < Ns; ++k) {
-          const long long t = (long long)q * k * step;
-          const long double a = 2.0L * pi * (long double)(t % n) / (long double)n;
-          out[pl.tw_off[p] + (q - 1) * Ns + k] = double2{(double)cosl(a), (double)(-sinl(a))};
+      for (int k = 0; k < Ns; ++k) {
+        const long long e = (long long)k * step;
+        if (R == 4) {            // w, w^2
+          o[k] = ct(angle(e));
+          o[Ns + k] = ct(angle(2 * e));
+        } else if (R == 8) {     // w^4, w, w^2, g = w exp(-i pi/4), g^2
+          o[k] = ct(angle(4 * e));
+          o[Ns + k] = ct(angle(e));
+          o[2 * Ns + k] = ct(angle(2 * e));
+          o[3 * Ns + k] = ct(angle(e) + pi / 4);
+          o[4 * Ns + k] = ct(angle(2 * e) + pi / 2);
+        } else {
+          for (int q = 1; q < R; ++q) {
+            const long double a = angle(q * e);
+            o[(q - 1) * Ns + k] = double2{(double)cosl(a), (double)(-sinl(a))};
+          }
         }
+      }
     }
     Ns *= R;
   }

@@ -32,8 +32,10 @@ struct FFTPlan {
   int n;
   int npass;
   int radix[16];
-  // twiddles of pass p (Ns > 1): w^(q k) for q = 1..R-1, k = 0..Ns-1 at
-  // tw_off[p] + (q - 1) Ns + k, w = exp(-2 pi i / (Ns R)); n - 1 entries in all
+  // twiddles of pass p (Ns > 1), w = exp(-2 pi i / (Ns R)), slot i of k at
+  // tw_off[p] + i Ns + k: radix 2, 3, 5 w^(q k) in slot q - 1; radix 4 and 8
+  // cosine-tangent forms of w^k, w^2k (and w^4k, w^k e^(-i pi/4), its square);
+  // (R - 1) Ns slots reserved per pass, n - 1 in all
   int tw_off[16];
   FastDiv div_nb[16];   // division by n / radix[p]
   FastDiv div_ns[16];   // division by Ns of pass p
