@@ -300,6 +300,15 @@ tc_status tc_get_timing(tc_ctx *ctx, tc_kernel_time *out, int cap, int *count);
 /* Forget the recorded times. */
 tc_status tc_reset_timing(tc_ctx *ctx);
 
+/* Sustained FP64 FMA rate of the current device, the peak of the ALU
+ * roofline of the FP64 kernels (the paper has no counterpart; it is a
+ * measurement aid).  Runs 4 independent FMA chains per thread, 32 warps on
+ * every SM, for about target_ms milliseconds (0 < target_ms <= 10000) on
+ * `stream` (NULL: default stream), after one untimed launch that also lets
+ * the clock settle, and writes the rate in TFLOP/s to *tflops (host).
+ * Allocates and frees a small device buffer; synchronises the stream. */
+tc_status tc_measure_fp64_rate(double target_ms, void *stream, double *tflops);
+
 /* Nonlinear terms without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc
  * -- code embedded in a host application that owns all device memory through

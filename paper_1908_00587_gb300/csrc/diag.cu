@@ -9,6 +9,8 @@
 // deterministic run to run.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "tc_internal.h"
 
 namespace tc {
@@ -154,3 +156,81 @@ void launch_diagnostics(tc_ctx *c) {
 }
 
 }  // namespace tc
+
+// ---------------------------------------------------------------------------
+// FP64 FMA rate of the device, for the ALU roofline of the FP64 kernels.
+// Every thread runs 4 independent dependent chains x <- fma(x, a, b) (a, b
+// kernel arguments, so nothing folds), 32 warps on every SM: the FP64 unit
+// of every SM sub-partition is kept busy whatever its latency.
+namespace tc {
+namespace {
+
+constexpr int kProbeThreads = 1024;
+constexpr int kProbeChains = 4;
+
+__global__ void __launch_bounds__(kProbeThreads) k_fp64_rate(double *out, int iters, double a,
+                                                              double b) {
+  double x[kProbeChains];
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) x[k] = 1e-3 * (threadIdx.x + k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) s += x[k];
+  out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" tc_status tc_measure_fp64_rate(double target_ms, void *stream, double *tflops) {
+  if (!tflops || !(target_ms > 0.0) || target_ms > 10000.0) return TC_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+    return TC_ERR_CUDA;
+  double *buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * (size_t)nsm * tc::kProbeThreads) != cudaSuccess) {
+    cudaGetLastError();
+    return TC_ERR_OOM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double total_ms = 0.0, total_flops = 0.0;
+  // one calibration launch, then launches of about a tenth of the target each
+  int iters = 4000;
+  const double a = 0.999999, b = 1e-7;
+  for (int rep = 0; e == cudaSuccess && rep < 12 && total_ms < target_ms; ++rep) {
+    e = cudaEventRecord(e0, st);
+    if (e != cudaSuccess) break;
+    tc::k_fp64_rate<<<nsm, tc::kProbeThreads, 0, st>>>(buf, iters, a, b);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess || ms <= 0.0f) break;
+    if (rep > 0) {   // the calibration launch also settles the clock
+      total_ms += ms;
+      total_flops += 2.0 * tc::kProbeChains * (double)iters * nsm * tc::kProbeThreads;
+    }
+    const double want = target_ms / 10.0;
+    const double next = iters * want / ms;
+    iters = (int)std::min(4.0e5, std::max(1000.0, next));   // at most ~0.5 s per launch
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TC_ERR_CUDA;
+  }
+  if (total_ms <= 0.0) return TC_ERR_CUDA;
+  *tflops = total_flops / (total_ms * 1e-3) / 1e12;
+  return TC_OK;
+}

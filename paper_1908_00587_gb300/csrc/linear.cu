@@ -239,6 +239,7 @@ __global__ void k_dt_policy(DevScalars *sc, double dt_fixed, double cfl, double 
                             double *dt_hist, int hist_cap) {
   const double rate = __longlong_as_double((long long)sc->rate_bits);
   sc->dt_old = sc->dt;
+  sc->idt_old = sc->idt;
   sc->rate_last = rate;
   sc->rate_bits = 0ull;
   sc->corr_bits = 0ull;
@@ -251,6 +252,7 @@ __global__ void k_dt_policy(DevScalars *sc, double dt_fixed, double cfl, double 
     dt = (prev <= 0.0 || dt_star < prev || dt_star > 1.1 * prev) ? dt_star : prev;
   }
   sc->dt = dt;
+  sc->idt = 1.0 / dt;
   sc->dt_prev = dt;
   sc->refactor = (dt != sc->dt_factored) ? 1 : 0;
   if (sc->refactor) sc->dt_factored = dt;
@@ -290,18 +292,18 @@ __global__ void k_rhs(const double2 *__restrict__ X, const double2 *__restrict__
   const Sizes &s = p.sz;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.S) return;
-  const int j = (int)(i / s.nmode);
+  const int j = (int)i / s.nmode;
   const int mode = (int)(i - (long long)j * s.nmode);
   const int m = mode / s.NK, kk = mode % s.NK;
   const double beta = p.alpha * kval(kk, s.K, s.NK);
-  const double idt = 1.0 / sc->dt;
+  const double idt = sc->idt;
   const double ir = p.rad.inv_r[j];
   const int st = p.rad.s0[j];
   const double om = 1.0 - kCN;
   const long long S = s.S;
   if (sc->rhs_ident && mode != 0 && j > 0 && j < s.Nr - 1) {
     const double q = om / kCN;
-    const double idt_old = 1.0 / sc->dt_old;
+    const double idt_old = sc->idt_old;
     const double *d1 = p.rad.D1 + j * kStencil;
     double2 d1p = {0.0, 0.0};
 #pragma unroll
@@ -440,7 +442,7 @@ __global__ void k_hrhs(const double2 *__restrict__ Yb, const double2 *__restrict
   const Sizes &s = p.sz;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.S) return;
-  const int j = (int)(i / s.nmode);
+  const int j = (int)i / s.nmode;
   const int mode = (int)(i - (long long)j * s.nmode);
   const long long S = s.S;
   const bool wall = (j == 0 || j == s.Nr - 1);
@@ -603,6 +605,38 @@ __device__ __forceinline__ double u_row(const double *row, double (&w)[kBand], d
   return v;
 }
 
+// The same rows with the narrow/wide choice made per row (uniform across the
+// CTA): the outer terms, the oldest, come first in the chain when present.
+__device__ __forceinline__ double l_row_sel(const double *row, double (&w)[kBand], double b,
+                                            bool wide) {
+  double v = b;
+  if (wide) {
+#pragma unroll
+    for (int e = 0; e < kNarrowFrom; ++e) v -= row[e] * w[e];
+  }
+#pragma unroll
+  for (int e = kNarrowFrom; e < kBand; ++e) v -= row[e] * w[e];
+#pragma unroll
+  for (int e = 0; e < kBand - 1; ++e) w[e] = w[e + 1];
+  w[kBand - 1] = v;
+  return v;
+}
+
+__device__ __forceinline__ double u_row_sel(const double *row, double (&w)[kBand], double b,
+                                            bool wide) {
+  double v = b * row[0];
+  if (wide) {
+#pragma unroll
+    for (int f = kBand; f > kNarrowFrom; --f) v -= row[f] * w[f - 1];
+  }
+#pragma unroll
+  for (int f = kNarrowFrom; f >= 1; --f) v -= row[f] * w[f - 1];
+#pragma unroll
+  for (int f = kBand - 1; f > 0; --f) w[f] = w[f - 1];
+  w[0] = v;
+  return v;
+}
+
 // U^T forward row (column-oriented), U^T = U'^T D: z = b - pending_0 solves
 // the unit factor, y = z / u_ii, and the pending sums of rows i+1..i+8 take
 // U'(i, i+f) z.
@@ -660,7 +694,7 @@ k_sweep(SweepArgs a, DevScalars *sc) {
   const int kk = neg ? a.NK - ak : ak;
   bool active = (g < nops) && !(neg && ak == 0) && !(F.skip00 && m == 0 && ak == 0);
   double *x = F.x + part * a.S + (long long)m * a.NK + (active ? kk : 0);
-  const long long xs = a.nmode;
+  const int xs = a.nmode;   // row stride; Nr * nmode < 2^31
   const int nch = (a.Nr + kSweepRows - 1) / kSweepRows;
 
   if (threadIdx.x == 0) {
@@ -690,19 +724,26 @@ k_sweep(SweepArgs a, DevScalars *sc) {
   double w[kBand];
 #pragma unroll
   for (int e = 0; e < kBand; ++e) w[e] = 0.0;
-  double xa[kSweepRows];
-  {
+  // xa: the current chunk's right-hand sides, overwritten by its results; xn:
+  // the next chunk's, loaded while the current one is swept.  Results are
+  // stored once per chunk, so no global access sits on a row's recurrence.
+  // The forward results of the last chunk stay in registers: they are the
+  // right-hand sides of the first backward chunk.
+  double xa[kSweepRows], xn[kSweepRows];
 #pragma unroll
-    for (int r = 0; r < kSweepRows; ++r) xa[r] = (active && r < a.Nr) ? x[r * xs] : 0.0;
-  }
+  for (int r = 0; r < kSweepRows; ++r) xa[r] = (active && r < a.Nr) ? x[r * xs] : 0.0;
   bool ok = true;
   for (int step = 0; step < total; ++step) {
     const int s = step % kSweepStages;
     const bool fwd = step < nch;
     const int c = fwd ? step : total - 1 - step;
     const int j0 = c * kSweepRows;
-    if (fwd && step == nch - 1) {
-      // backward sweep starts from the chunk just finished: nothing to prefetch
+    const bool turn = step == nch - 1;   // the backward sweep starts from this chunk
+    // right-hand sides of the next chunk (forward c + 1, backward c - 1)
+    if (active && !turn && step + 1 < total) {
+      const int jn = fwd ? j0 + kSweepRows : j0 - kSweepRows;
+#pragma unroll
+      for (int r = 0; r < kSweepRows; ++r) xn[r] = (jn + r < a.Nr) ? x[(jn + r) * xs] : 0.0;
     }
     const bool done = mbar_wait(smem_u32(&bars[s]), (phase >> s) & 1u);
     if (!done) {
@@ -715,11 +756,12 @@ k_sweep(SweepArgs a, DevScalars *sc) {
     __syncthreads();
     if (abort_flag) break;
     if (active) {
-      // The narrow/wide choice is made per chunk (a chunk with any boundary
-      // row takes the wide form for all its rows: the extra terms are exact
-      // zeros), so a full chunk is straight-line code in which the sliding
-      // window w[] lives in renamed registers; only a chunk past the last row
-      // guards each row.
+      // A full chunk is straight-line code in which the sliding window w[]
+      // lives in renamed registers.  Its rows take the narrow form (4
+      // off-diagonal terms) except the 4 boundary rows of each factor, which
+      // take all 8 (for a chunk that holds one, the choice is made per row;
+      // the extra terms elsewhere would be exact zeros).  Only a chunk past
+      // the last row guards each row.
       const bool full = j0 + kSweepRows <= a.Nr;
       const bool low_narrow = j0 + kSweepRows <= a.Nr - kNarrowFrom;   // L rows, L^T rows
       const bool up_narrow = j0 >= kNarrowFrom;                        // U rows, U^T rows
@@ -729,80 +771,69 @@ k_sweep(SweepArgs a, DevScalars *sc) {
         if (full && up_narrow) {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            x[(j0 + r) * xs] = ut_row<true>(Lc + r * (kBand + 1), w, xa[r]);
+            xa[r] = ut_row<true>(Lc + r * (kBand + 1), w, xa[r]);
         } else if (full) {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            x[(j0 + r) * xs] = ut_row<false>(Lc + r * (kBand + 1), w, xa[r]);
+            xa[r] = ut_row<false>(Lc + r * (kBand + 1), w, xa[r]);
         } else {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            if (j0 + r < a.Nr) x[(j0 + r) * xs] = ut_row<false>(Lc + r * (kBand + 1), w, xa[r]);
+            if (j0 + r < a.Nr) xa[r] = ut_row<false>(Lc + r * (kBand + 1), w, xa[r]);
         }
       } else if (TRANS) {
         // L^T x = y: x_j = y_j - pending_j, then pending_{j-8+e} += L(j, j-8+e) x_j
         if (full && low_narrow) {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            x[(j0 + r) * xs] = lt_row<true>(Lc + r * kBand, w, xa[r]);
+            xa[r] = lt_row<true>(Lc + r * kBand, w, xa[r]);
         } else if (full) {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            x[(j0 + r) * xs] = lt_row<false>(Lc + r * kBand, w, xa[r]);
+            xa[r] = lt_row<false>(Lc + r * kBand, w, xa[r]);
         } else {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            if (j0 + r < a.Nr) x[(j0 + r) * xs] = lt_row<false>(Lc + r * kBand, w, xa[r]);
+            if (j0 + r < a.Nr) xa[r] = lt_row<false>(Lc + r * kBand, w, xa[r]);
         }
       } else if (fwd) {
         if (full && low_narrow) {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            x[(j0 + r) * xs] = l_row<true>(Lc + r * kBand, w, xa[r]);
-        } else if (full) {
+            xa[r] = l_row<true>(Lc + r * kBand, w, xa[r]);
+        } else if (full) {   // the last 4 rows of L are the wide ones
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            x[(j0 + r) * xs] = l_row<false>(Lc + r * kBand, w, xa[r]);
+            xa[r] = l_row_sel(Lc + r * kBand, w, xa[r], j0 + r >= a.Nr - kNarrowFrom);
         } else {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            if (j0 + r < a.Nr) x[(j0 + r) * xs] = l_row<false>(Lc + r * kBand, w, xa[r]);
+            if (j0 + r < a.Nr) xa[r] = l_row<false>(Lc + r * kBand, w, xa[r]);
         }
       } else {
         if (full && up_narrow) {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            x[(j0 + r) * xs] = u_row<true>(Lc + r * (kBand + 1), w, xa[r]);
-        } else if (full) {
+            xa[r] = u_row<true>(Lc + r * (kBand + 1), w, xa[r]);
+        } else if (full) {   // the first 4 rows of U are the wide ones
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            x[(j0 + r) * xs] = u_row<false>(Lc + r * (kBand + 1), w, xa[r]);
+            xa[r] = u_row_sel(Lc + r * (kBand + 1), w, xa[r], j0 + r < kNarrowFrom);
         } else {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            if (j0 + r < a.Nr) x[(j0 + r) * xs] = u_row<false>(Lc + r * (kBand + 1), w, xa[r]);
+            if (j0 + r < a.Nr) xa[r] = u_row<false>(Lc + r * (kBand + 1), w, xa[r]);
         }
       }
-      // prefetch the right-hand sides of the next chunk
-      if (fwd) {
-        if (c + 1 < nch) {
+      if (turn) {
 #pragma unroll
-          for (int r = 0; r < kSweepRows; ++r) {
-            const int j = j0 + kSweepRows + r;
-            xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
-          }
-        } else {   // the backward sweep starts from the chunk just finished
+        for (int e = 0; e < kBand; ++e) w[e] = 0.0;
+      } else {
 #pragma unroll
-          for (int e = 0; e < kBand; ++e) w[e] = 0.0;
+        for (int r = 0; r < kSweepRows; ++r)
+          if (full || j0 + r < a.Nr) x[(j0 + r) * xs] = xa[r];
 #pragma unroll
-          for (int r = 0; r < kSweepRows; ++r) {
-            const int j = j0 + r;
-            xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
-          }
-        }
-      } else if (c > 0) {
-#pragma unroll
-        for (int r = 0; r < kSweepRows; ++r) xa[r] = x[(j0 - kSweepRows + r) * xs];
+        for (int r = 0; r < kSweepRows; ++r) xa[r] = xn[r];
       }
     }
     __syncthreads();   // every thread is done with stage s
@@ -867,7 +898,7 @@ __global__ void k_correct(const double *__restrict__ U, const double *__restrict
   // subtractions use the FP64 pipe
   unsigned long long dbits = 0ull;
   if (i < s.S) {
-    const int j = (int)(i / s.nmode);
+    const int j = (int)i / s.nmode;
     const int mode = (int)(i - (long long)j * s.nmode);
     const long long S = s.S;
     double2 up = {U[i], U[S + i]}, um = {U[2 * S + i], U[3 * S + i]},
@@ -1100,7 +1131,7 @@ __global__ void k_stT_hrhs(const double *__restrict__ U, double2 *__restrict__ R
   const Sizes &s = p.sz;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.S) return;
-  const int j = (int)(i / s.nmode);
+  const int j = (int)i / s.nmode;
   const int mode = (int)(i - (long long)j * s.nmode);
   const long long S = s.S;
   const bool interior = (j > 0 && j < s.Nr - 1);
@@ -1148,7 +1179,7 @@ __global__ void k_stT_prhs(const double *__restrict__ Ps, double2 *__restrict__ 
   const Sizes &s = p.sz;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.S) return;
-  const int sn = (int)(i / s.nmode);
+  const int sn = (int)i / s.nmode;
   const int mode = (int)(i - (long long)sn * s.nmode);
   if (mode == 0) return;
   const long long S = s.S;
@@ -1213,7 +1244,7 @@ __global__ void k_rhsT(const double2 *__restrict__ Yb, double2 *__restrict__ Xb,
   const Sizes &s = p.sz;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.S) return;
-  const int sn = (int)(i / s.nmode);
+  const int sn = (int)i / s.nmode;
   const int mode = (int)(i - (long long)sn * s.nmode);
   const long long S = s.S;
   const int m = mode / s.NK, kk = mode % s.NK;
@@ -1297,7 +1328,7 @@ __global__ void k_objective_grad(const double2 *__restrict__ X, const double2 *_
   if (i >= (long long)s.nf * s.S) return;
   const int c = (int)(i / s.S);
   const long long rem = i - (long long)c * s.S;
-  const int j = (int)(rem / s.nmode);
+  const int j = (int)rem / s.nmode;
   const int mode = (int)(rem - (long long)j * s.nmode);
   if (c >= 3) {
     G[i] = double2{0.0, 0.0};

@@ -52,7 +52,7 @@ void fd_weights(double x0, const double *x, int n, double w[3][kStencil]);
 // Problem sizes.
 struct Sizes {
   int Nr, Nt, Nz, M, K, NM, NK, nmode, nf;
-  long long S;  // Nr * nmode coefficients per field
+  long long S;  // Nr * nmode coefficients per field (< 2^31: Nr <= 1024, Nt, Nz <= 1024)
 };
 
 // Device-side radial tables (device pointers).
@@ -89,6 +89,7 @@ struct DevScalars {
   // from that stage's equation instead of the stencil
   int rhs_ident;
   double dt_old;        // step of the stage that produced the current state
+  double idt, idt_old;  // 1/dt and 1/dt_old, set with them by the step policy
 };
 
 // Parameters of the nonlinear stage.

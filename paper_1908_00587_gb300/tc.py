@@ -81,6 +81,7 @@ _SIGS = {
     "tc_get_timing": [_P, _P, _I, ctypes.POINTER(_I)],
     "tc_reset_timing": [_P],
     "tc_nonlinear_noalloc": [_I, _I, _I, _D, _D, _D, _D, _P, _P, _P, _P],
+    "tc_measure_fp64_rate": [_D, _P, ctypes.POINTER(_D)],
     "tc_adjoint_step": [_P, _P, _D, _P],
     "tc_record_bytes_per_step": [_P, ctypes.POINTER(ctypes.c_longlong)],
     "tc_step_record": [_P, _I, _D, _P, ctypes.c_longlong],
@@ -238,6 +239,15 @@ def tc_nonlinear_noalloc(Nr, Ntheta, Nz, eta, Lz, Ra, Pr, state_dev, n_dev, stre
                                      float(Ra), float(Pr), _ptr(state_dev)[0], _ptr(n_dev)[0],
                                      stream_ptr, ctypes.byref(rate)), "tc_nonlinear_noalloc")
     return rate.value
+
+
+def tc_measure_fp64_rate(target_ms=250.0, stream_ptr=None):
+    """Sustained FP64 FMA rate of the current device in TFLOP/s (a measurement
+    aid for the ALU roofline; see include/tc.h)."""
+    out = ctypes.c_double(0.0)
+    _check(_lib.tc_measure_fp64_rate(float(target_ms), stream_ptr, ctypes.byref(out)),
+           "tc_measure_fp64_rate")
+    return out.value
 
 
 def tc_adjoint_step(ctx, state_n_dev, dt, adj_dev):

@@ -66,3 +66,16 @@ def test_status_strings(tc):
     for s in range(9):
         assert tc.tc_status_string(s)
     assert "unknown" in tc.tc_status_string(42)
+
+
+def test_fp64_rate_rejects_bad_arguments(tc):
+    """The measurement aid validates its arguments before touching the device."""
+    import ctypes
+    lib = ctypes.CDLL(tc.LIB_PATH)
+    lib.tc_measure_fp64_rate.argtypes = [ctypes.c_double, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_double)]
+    out = ctypes.c_double(0.0)
+    assert lib.tc_measure_fp64_rate(0.0, None, ctypes.byref(out)) == 1
+    assert lib.tc_measure_fp64_rate(-5.0, None, ctypes.byref(out)) == 1
+    assert lib.tc_measure_fp64_rate(2e4, None, ctypes.byref(out)) == 1
+    assert lib.tc_measure_fp64_rate(100.0, None, None) == 1

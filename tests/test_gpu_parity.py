@@ -50,6 +50,7 @@ SIZES = [
     (9, 48, 40, 0.0),
     (16, 20, 12, 800.0),
     (33, 36, 18, 0.0),
+    (10, 64, 64, 300.0),   # twiddled radix-8 passes (plan 8 x 8) in both directions
 ]
 
 
@@ -269,6 +270,14 @@ def test_non_blocking_stream_gives_identical_results(tc):
     assert np.array_equal(out[0][1], out[1][1])
 
 
+def test_fp64_rate_probe(tc):
+    """The FP64 FMA rate the roofline quotes: positive, and not above the
+    nominal 4 flop/clk/SM of 152 SMs at the 2.07 GHz maximum clock (a probe
+    that read above it would not be doing the work)."""
+    r = tc.tc_measure_fp64_rate(50.0)
+    assert 0.2 < r <= 152 * 2.07e9 * 4 / 1e12
+
+
 def test_create_size_limits(tc):
     """The azimuthal size limit that the shared-memory transforms impose."""
     st = {v: k for k, v in tc.STATUS.items()}
@@ -289,6 +298,7 @@ def test_create_size_limits(tc):
 
 @pytest.mark.parametrize("Nr,Nt,Nz,Ra", [(9, 750, 8, 400.0),     # largest azimuthal size with T
                                          (11, 1000, 6, 0.0),      # largest without T
+                                         (9, 512, 16, 0.0),       # plan 8 x 8 x 8 in theta
                                          (9, 4, 4, 300.0)])       # smallest: M = K = 1
 def test_nonlinear_extreme_sizes(tc, Nr, Nt, Nz, Ra):
     wl = _wl(Nr, Nt, Nz, Ra)
