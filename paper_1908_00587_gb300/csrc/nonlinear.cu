@@ -195,14 +195,14 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
       dz.y = 0;
     }
     const T fm = (T)m;
-    const V2<T> dt = V2<T>{-fm * v.y, fm * v.x};  // i m v
     V2<T> *b0 = A + (li * npair + 2 * c) * Ntp;
     V2<T> *b1 = b0 + Ntp;
-    // Z_m = a_m + i b_m ; Z_{-m} = conj(a_m) + i conj(b_m)
-    b0[spad(m)] = V2<T>{v.x - dt.y, v.y + dt.x};
+    // Z_m = a_m + i b_m ; Z_{-m} = conj(a_m) + i conj(b_m).  For the value
+    // and its theta derivative b = i m a: Z_m = (1 - m) a, Z_{-m} = (1 + m) conj(a)
+    b0[spad(m)] = V2<T>{fmat(-fm, v.x, v.x), fmat(-fm, v.y, v.y)};
     b1[spad(m)] = V2<T>{dr.x - dz.y, dr.y + dz.x};
     if (m > 0) {
-      b0[spad(Nt - m)] = V2<T>{v.x + dt.y, -v.y + dt.x};
+      b0[spad(Nt - m)] = V2<T>{fmat(fm, v.x, v.x), fmat(-fm, v.y, -v.y)};
       b1[spad(Nt - m)] = V2<T>{dr.x + dz.y, -dr.y + dz.x};
     }
   }
@@ -300,7 +300,8 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   __syncthreads();
   V2<T> *scratch = (out == A) ? B : A;
   V2<T> *sp = fft_batch<-1>(out, scratch, p.pt, nl * 2, Ntp, tw);
-  // unpack two real transforms: X_m = (Z_m + conj Z_-m)/2, Y_m = (Z_m - conj Z_-m)/(2i)
+  // unpack two real transforms: X_m = (Z_m + conj Z_-m)/2, Y_m = (Z_m - conj Z_-m)/(2i);
+  // the factor 1/2 is left to k_zfwd's final scaling (exact: a power of two)
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
   for (int t = threadIdx.x; t < nl * s.NM; t += blockDim.x) {
     const int2 a = divmod(t, s.NM, p.fNM);
@@ -313,8 +314,8 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     for (int h = 0; h < 2; ++h) {
       const V2<T> a = z0[h * Ntp + spad(m)];
       const V2<T> b = z0[h * Ntp + spad(mm)];
-      const V2<T> x = V2<T>{(T)0.5 * (a.x + b.x), (T)0.5 * (a.y - b.y)};
-      const V2<T> y = V2<T>{(T)0.5 * (a.y + b.y), (T)0.5 * (b.x - a.x)};
+      const V2<T> x = V2<T>{a.x + b.x, a.y - b.y};
+      const V2<T> y = V2<T>{a.y + b.y, b.x - a.x};
       W[(2 * h) * fs + off] = x;
       if (2 * h + 1 < s.nf) W[(2 * h + 1) * fs + off] = y;
     }
@@ -348,7 +349,8 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
   }
   __syncthreads();
   V2<T> *res = fft_batch<-1>(A, B, p.pz, nb, Np, tw);
-  const double scale = 1.0 / ((double)s.Nt * (double)s.Nz);
+  // 1/(Ntheta Nz), times the 1/2 of k_theta's unpacking of paired transforms
+  const double scale = 0.5 / ((double)s.Nt * (double)s.Nz);
   if (!p.mixed) {
     for (int t = threadIdx.x; t < nb * s.NK; t += blockDim.x) {
       const int2 a = divmod(t, s.NK, p.fNK);
@@ -362,8 +364,8 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
     }
     return;
   }
-  // Mixed precision: the FP32 transform (scaled in FP32: 1/(Ntheta Nz), exact
-  // for power-of-two sizes) plus the FP64 products with the mean profiles of
+  // Mixed precision: the FP32 transform (scaled in FP32: 1/(2 Ntheta Nz),
+  // exact for power-of-two sizes) plus the FP64 products with the mean profiles of
   // this radial level,
   //   N_r += -(a u_r - 2 (U_theta/r) u_theta) (+ U_theta^2/r for the mean)
   //   N_theta += -(a u_theta + (U_theta/r + U_theta') u_r)
