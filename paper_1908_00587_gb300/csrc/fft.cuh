@@ -316,14 +316,102 @@ __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__re
   }
 }
 
+// The same passes for a length known at compile time (powers of two 64..512,
+// with the plans make_plan gives them: radix 8 first, then 8s, or two 4s, or
+// one 4).  The divisions by nb and Ns become shifts and masks, and the padded
+// addresses of a butterfly's inputs and outputs become one base plus constant
+// offsets: spad(x + c) = spad(x) + c + c/8 whenever c is a multiple of 8.
+template <int R, int S, bool ZMID, int N, int NS, typename V>
+__device__ __forceinline__ void stockham_pass_fixed(const V *__restrict__ src, V *__restrict__ dst,
+                                                    int batch, int bstride,
+                                                    const V *__restrict__ twp) {
+  using T = decltype(src[0].x);
+  constexpr int nb = N / R;
+  static_assert((nb & (nb - 1)) == 0 && nb % 8 == 0, "power-of-two stride, multiple of 8");
+  constexpr int in_step = nb + nb / 8;   // spad distance between inputs q and q + 1
+  const int total = nb * batch;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bi = t / nb;
+    const int j = t - bi * nb;
+    const V *s = src + bi * bstride;
+    V *d = dst + bi * bstride;
+    const int k = j % NS;
+    const int sj = spad(j);
+    V v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+      if (!ZMID || (q != 3 && q != 4)) v[q] = s[sj + q * in_step];
+    if constexpr (ZMID) {
+      dft8_zmid<S>(v);
+    } else if constexpr (NS == 1) {
+      dftR<R, S>(v);
+    } else {
+      constexpr int NT = R == 4 ? 2 : 5;
+      V ct[NT];
+#pragma unroll
+      for (int i = 0; i < NT; ++i) {
+        const V w = twp[i * NS + k];
+        ct[i] = V{w.x, (S < 0) ? w.y : -w.y};
+      }
+      if constexpr (R == 4) dft4_ct<S>(v, (T)ct[0].x, (T)ct[0].y, (T)ct[1].x, (T)ct[1].y);
+      else dft8_ct<S, V, T>(v, ct);
+    }
+    const int base = (j - k) * R + k;
+    if constexpr (NS % 8 == 0) {
+      const int sb = spad(base);
+#pragma unroll
+      for (int p = 0; p < R; ++p) d[sb + p * (NS + NS / 8)] = v[p];
+    } else if constexpr (NS == 1) {
+      // base = j R and R <= 8: the R outputs share base / 8
+      const int sb = base + j * R / 8;
+#pragma unroll
+      for (int p = 0; p < R; ++p) d[sb + p] = v[p];
+    } else {
+#pragma unroll
+      for (int p = 0; p < R; ++p) d[spad(base + p * NS)] = v[p];
+    }
+  }
+}
+
+template <int S, int N, typename V>
+__device__ V *fft_batch_fixed(V *a, V *b, const FFTPlan &pl, int batch, int bstride,
+                              const V *__restrict__ tw, bool zmid) {
+  // plans of make_plan: 64 = 8 8, 128 = 8 4 4, 256 = 8 8 4, 512 = 8 8 8
+  constexpr int R1 = (N == 128) ? 4 : 8;
+  constexpr int R2 = (N == 64) ? 0 : (N == 512 ? 8 : 4);
+  if (zmid) stockham_pass_fixed<8, S, true, N, 1>(a, b, batch, bstride, tw);
+  else stockham_pass_fixed<8, S, false, N, 1>(a, b, batch, bstride, tw);
+  __syncthreads();
+  stockham_pass_fixed<R1, S, false, N, 8>(b, a, batch, bstride, tw + pl.tw_off[1]);
+  __syncthreads();
+  if constexpr (R2 == 0) {
+    return a;
+  } else {
+    stockham_pass_fixed<R2, S, false, N, 8 * R1>(a, b, batch, bstride, tw + pl.tw_off[2]);
+    __syncthreads();
+    return b;
+  }
+}
+
 // Full transform of `batch` sequences held in buffer a (b is scratch of the
 // same size); tw: the plan's pass-major twiddle table (fill_plan_twiddles).  Returns the buffer holding the result.  All threads of the CTA
 // must call it; it ends with a __syncthreads().  zmid: the caller guarantees
 // that every input vanishes on [3N/8, 5N/8) and the plan starts with radix 8
-// (see zmid_ok); the first pass then skips those inputs.
-template <int S, typename V>
+// (see zmid_ok); the first pass then skips those inputs.  FIXED: lengths
+// 64..512 take the compile-time passes above (a kernel that does not gain
+// from them, measured, passes false and keeps only the generic passes).
+template <int S, bool FIXED = true, typename V>
 __device__ V *fft_batch(V *a, V *b, const FFTPlan &pl, int batch, int bstride,
                         const V *__restrict__ tw, bool zmid = false) {
+  if constexpr (FIXED) {
+    switch (pl.n) {
+      case 64: return fft_batch_fixed<S, 64>(a, b, pl, batch, bstride, tw, zmid);
+      case 128: return fft_batch_fixed<S, 128>(a, b, pl, batch, bstride, tw, zmid);
+      case 256: return fft_batch_fixed<S, 256>(a, b, pl, batch, bstride, tw, zmid);
+      case 512: return fft_batch_fixed<S, 512>(a, b, pl, batch, bstride, tw, zmid);
+      default: break;
+    }
+  }
   int Ns = 1;
   for (int p = 0; p < pl.npass; ++p) {
     const int R = pl.radix[p];

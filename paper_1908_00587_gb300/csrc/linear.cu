@@ -605,38 +605,6 @@ __device__ __forceinline__ double u_row(const double *row, double (&w)[kBand], d
   return v;
 }
 
-// The same rows with the narrow/wide choice made per row (uniform across the
-// CTA): the outer terms, the oldest, come first in the chain when present.
-__device__ __forceinline__ double l_row_sel(const double *row, double (&w)[kBand], double b,
-                                            bool wide) {
-  double v = b;
-  if (wide) {
-#pragma unroll
-    for (int e = 0; e < kNarrowFrom; ++e) v -= row[e] * w[e];
-  }
-#pragma unroll
-  for (int e = kNarrowFrom; e < kBand; ++e) v -= row[e] * w[e];
-#pragma unroll
-  for (int e = 0; e < kBand - 1; ++e) w[e] = w[e + 1];
-  w[kBand - 1] = v;
-  return v;
-}
-
-__device__ __forceinline__ double u_row_sel(const double *row, double (&w)[kBand], double b,
-                                            bool wide) {
-  double v = b * row[0];
-  if (wide) {
-#pragma unroll
-    for (int f = kBand; f > kNarrowFrom; --f) v -= row[f] * w[f - 1];
-  }
-#pragma unroll
-  for (int f = kNarrowFrom; f >= 1; --f) v -= row[f] * w[f - 1];
-#pragma unroll
-  for (int f = kBand - 1; f > 0; --f) w[f] = w[f - 1];
-  w[0] = v;
-  return v;
-}
-
 // U^T forward row (column-oriented), U^T = U'^T D: z = b - pending_0 solves
 // the unit factor, y = z / u_ii, and the pending sums of rows i+1..i+8 take
 // U'(i, i+f) z.
@@ -694,7 +662,7 @@ k_sweep(SweepArgs a, DevScalars *sc) {
   const int kk = neg ? a.NK - ak : ak;
   bool active = (g < nops) && !(neg && ak == 0) && !(F.skip00 && m == 0 && ak == 0);
   double *x = F.x + part * a.S + (long long)m * a.NK + (active ? kk : 0);
-  const int xs = a.nmode;   // row stride; Nr * nmode < 2^31
+  const long long xs = a.nmode;
   const int nch = (a.Nr + kSweepRows - 1) / kSweepRows;
 
   if (threadIdx.x == 0) {
@@ -724,26 +692,19 @@ k_sweep(SweepArgs a, DevScalars *sc) {
   double w[kBand];
 #pragma unroll
   for (int e = 0; e < kBand; ++e) w[e] = 0.0;
-  // xa: the current chunk's right-hand sides, overwritten by its results; xn:
-  // the next chunk's, loaded while the current one is swept.  Results are
-  // stored once per chunk, so no global access sits on a row's recurrence.
-  // The forward results of the last chunk stay in registers: they are the
-  // right-hand sides of the first backward chunk.
-  double xa[kSweepRows], xn[kSweepRows];
+  double xa[kSweepRows];
+  {
 #pragma unroll
-  for (int r = 0; r < kSweepRows; ++r) xa[r] = (active && r < a.Nr) ? x[r * xs] : 0.0;
+    for (int r = 0; r < kSweepRows; ++r) xa[r] = (active && r < a.Nr) ? x[r * xs] : 0.0;
+  }
   bool ok = true;
   for (int step = 0; step < total; ++step) {
     const int s = step % kSweepStages;
     const bool fwd = step < nch;
     const int c = fwd ? step : total - 1 - step;
     const int j0 = c * kSweepRows;
-    const bool turn = step == nch - 1;   // the backward sweep starts from this chunk
-    // right-hand sides of the next chunk (forward c + 1, backward c - 1)
-    if (active && !turn && step + 1 < total) {
-      const int jn = fwd ? j0 + kSweepRows : j0 - kSweepRows;
-#pragma unroll
-      for (int r = 0; r < kSweepRows; ++r) xn[r] = (jn + r < a.Nr) ? x[(jn + r) * xs] : 0.0;
+    if (fwd && step == nch - 1) {
+      // backward sweep starts from the chunk just finished: nothing to prefetch
     }
     const bool done = mbar_wait(smem_u32(&bars[s]), (phase >> s) & 1u);
     if (!done) {
@@ -756,12 +717,11 @@ k_sweep(SweepArgs a, DevScalars *sc) {
     __syncthreads();
     if (abort_flag) break;
     if (active) {
-      // A full chunk is straight-line code in which the sliding window w[]
-      // lives in renamed registers.  Its rows take the narrow form (4
-      // off-diagonal terms) except the 4 boundary rows of each factor, which
-      // take all 8 (for a chunk that holds one, the choice is made per row;
-      // the extra terms elsewhere would be exact zeros).  Only a chunk past
-      // the last row guards each row.
+      // The narrow/wide choice is made per chunk (a chunk with any boundary
+      // row takes the wide form for all its rows: the extra terms are exact
+      // zeros), so a full chunk is straight-line code in which the sliding
+      // window w[] lives in renamed registers; only a chunk past the last row
+      // guards each row.
       const bool full = j0 + kSweepRows <= a.Nr;
       const bool low_narrow = j0 + kSweepRows <= a.Nr - kNarrowFrom;   // L rows, L^T rows
       const bool up_narrow = j0 >= kNarrowFrom;                        // U rows, U^T rows
@@ -771,69 +731,80 @@ k_sweep(SweepArgs a, DevScalars *sc) {
         if (full && up_narrow) {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            xa[r] = ut_row<true>(Lc + r * (kBand + 1), w, xa[r]);
+            x[(j0 + r) * xs] = ut_row<true>(Lc + r * (kBand + 1), w, xa[r]);
         } else if (full) {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            xa[r] = ut_row<false>(Lc + r * (kBand + 1), w, xa[r]);
+            x[(j0 + r) * xs] = ut_row<false>(Lc + r * (kBand + 1), w, xa[r]);
         } else {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            if (j0 + r < a.Nr) xa[r] = ut_row<false>(Lc + r * (kBand + 1), w, xa[r]);
+            if (j0 + r < a.Nr) x[(j0 + r) * xs] = ut_row<false>(Lc + r * (kBand + 1), w, xa[r]);
         }
       } else if (TRANS) {
         // L^T x = y: x_j = y_j - pending_j, then pending_{j-8+e} += L(j, j-8+e) x_j
         if (full && low_narrow) {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            xa[r] = lt_row<true>(Lc + r * kBand, w, xa[r]);
+            x[(j0 + r) * xs] = lt_row<true>(Lc + r * kBand, w, xa[r]);
         } else if (full) {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            xa[r] = lt_row<false>(Lc + r * kBand, w, xa[r]);
+            x[(j0 + r) * xs] = lt_row<false>(Lc + r * kBand, w, xa[r]);
         } else {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            if (j0 + r < a.Nr) xa[r] = lt_row<false>(Lc + r * kBand, w, xa[r]);
+            if (j0 + r < a.Nr) x[(j0 + r) * xs] = lt_row<false>(Lc + r * kBand, w, xa[r]);
         }
       } else if (fwd) {
         if (full && low_narrow) {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            xa[r] = l_row<true>(Lc + r * kBand, w, xa[r]);
-        } else if (full) {   // the last 4 rows of L are the wide ones
+            x[(j0 + r) * xs] = l_row<true>(Lc + r * kBand, w, xa[r]);
+        } else if (full) {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            xa[r] = l_row_sel(Lc + r * kBand, w, xa[r], j0 + r >= a.Nr - kNarrowFrom);
+            x[(j0 + r) * xs] = l_row<false>(Lc + r * kBand, w, xa[r]);
         } else {
 #pragma unroll
           for (int r = 0; r < kSweepRows; ++r)
-            if (j0 + r < a.Nr) xa[r] = l_row<false>(Lc + r * kBand, w, xa[r]);
+            if (j0 + r < a.Nr) x[(j0 + r) * xs] = l_row<false>(Lc + r * kBand, w, xa[r]);
         }
       } else {
         if (full && up_narrow) {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            xa[r] = u_row<true>(Lc + r * (kBand + 1), w, xa[r]);
-        } else if (full) {   // the first 4 rows of U are the wide ones
+            x[(j0 + r) * xs] = u_row<true>(Lc + r * (kBand + 1), w, xa[r]);
+        } else if (full) {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            xa[r] = u_row_sel(Lc + r * (kBand + 1), w, xa[r], j0 + r < kNarrowFrom);
+            x[(j0 + r) * xs] = u_row<false>(Lc + r * (kBand + 1), w, xa[r]);
         } else {
 #pragma unroll
           for (int r = kSweepRows - 1; r >= 0; --r)
-            if (j0 + r < a.Nr) xa[r] = u_row<false>(Lc + r * (kBand + 1), w, xa[r]);
+            if (j0 + r < a.Nr) x[(j0 + r) * xs] = u_row<false>(Lc + r * (kBand + 1), w, xa[r]);
         }
       }
-      if (turn) {
+      // prefetch the right-hand sides of the next chunk
+      if (fwd) {
+        if (c + 1 < nch) {
 #pragma unroll
-        for (int e = 0; e < kBand; ++e) w[e] = 0.0;
-      } else {
+          for (int r = 0; r < kSweepRows; ++r) {
+            const int j = j0 + kSweepRows + r;
+            xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
+          }
+        } else {   // the backward sweep starts from the chunk just finished
 #pragma unroll
-        for (int r = 0; r < kSweepRows; ++r)
-          if (full || j0 + r < a.Nr) x[(j0 + r) * xs] = xa[r];
+          for (int e = 0; e < kBand; ++e) w[e] = 0.0;
 #pragma unroll
-        for (int r = 0; r < kSweepRows; ++r) xa[r] = xn[r];
+          for (int r = 0; r < kSweepRows; ++r) {
+            const int j = j0 + r;
+            xa[r] = (j < a.Nr) ? x[j * xs] : 0.0;
+          }
+        }
+      } else if (c > 0) {
+#pragma unroll
+        for (int r = 0; r < kSweepRows; ++r) xa[r] = x[(j0 - kSweepRows + r) * xs];
       }
     }
     __syncthreads();   // every thread is done with stage s
