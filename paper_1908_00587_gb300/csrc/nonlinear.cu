@@ -49,9 +49,15 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *p, double v) 
 template <typename T>
 using V2 = typename V2t<T>::type;
 
+// Twiddle table into shared memory: the FP64 table, or for the FP32 kernels
+// its FP32 copy (no conversion on the FP64 unit).
 template <typename T>
-__device__ __forceinline__ void load_tw(V2<T> *dst, const double2 *src, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = V2<T>{(T)src[i].x, (T)src[i].y};
+__device__ __forceinline__ void load_tw(V2<T> *dst, const double2 *src, const float2 *src32, int n) {
+  if constexpr (sizeof(T) == 4) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src32[i];
+  } else {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  }
 }
 
 // Mixed precision: u = U + u_b with U = (0, U_theta(r), U_z(r)) and Tbar(r)
@@ -67,8 +73,8 @@ __device__ __forceinline__ void load_tw(V2<T> *dst, const double2 *src, int n) {
 // the dealiased product: multiplying by a function of r creates no new modes.
 
 // Mean profiles of the (0,0) mode and their radial derivatives, one thread per r.
-__global__ void k_meanprof(const double2 *__restrict__ X, double *__restrict__ prof, Sizes s,
-                           Radial rad) {
+__global__ void k_meanprof(const double2 *__restrict__ X, double *__restrict__ prof,
+                           float *__restrict__ prof32, Sizes s, Radial rad) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= s.Nr) return;
   const int st = rad.s0[r];
@@ -88,6 +94,8 @@ __global__ void k_meanprof(const double2 *__restrict__ X, double *__restrict__ p
   prof[r * 8 + 3] = dUz;
   prof[r * 8 + 4] = dTb;
   prof[r * 8 + 5] = (s.nf == 4) ? X[3 * s.S + o].x : 0.0;
+  prof32[2 * r + 0] = (float)X[s.S + o].x;
+  prof32[2 * r + 1] = (float)X[2 * s.S + o].x;
 }
 
 // Mixed precision: the perturbation part of the state in FP32 for the axial
@@ -118,13 +126,16 @@ __global__ void k_zinv(const V2<T> *__restrict__ X, V2<T> *__restrict__ Vout, NL
   V2<T> *A = reinterpret_cast<V2<T> *>(smem_raw);
   V2<T> *B = A + 3 * p.MB * Np;
   V2<T> *tw = B + 3 * p.MB * Np;
-  load_tw<T>(tw, p.twz, Nz);
+  load_tw<T>(tw, p.twz, p.twz32, Nz);
   for (int i = threadIdx.x; i < 3 * nm * Np; i += blockDim.x) A[i] = V2<T>{0, 0};
   __syncthreads();
   const int st = p.rad.s0[r];
   T d1[kStencil];
 #pragma unroll
-  for (int q = 0; q < kStencil; ++q) d1[q] = (T)p.rad.D1[r * kStencil + q];
+  for (int q = 0; q < kStencil; ++q) {
+    if constexpr (sizeof(T) == 4) d1[q] = p.d1_32[r * kStencil + q];
+    else d1[q] = p.rad.D1[r * kStencil + q];
+  }
   const FastDiv fnm = (nm == p.MB) ? p.fMB : p.fMBl;
   for (int t = threadIdx.x; t < nm * s.NK; t += blockDim.x) {
     const int mi = fdiv(t, p.fNK);
@@ -139,7 +150,9 @@ __global__ void k_zinv(const V2<T> *__restrict__ X, V2<T> *__restrict__ Vout, NL
       dr.x += d1[q] * x.x;
       dr.y += d1[q] * x.y;
     }
-    const T beta = (T)(p.alpha * kval(kk, s.K, s.NK));
+    T beta;
+    if constexpr (sizeof(T) == 4) beta = p.beta32[kk];
+    else beta = p.alpha * kval(kk, s.K, s.NK);
     const int pos = kpos(kk, s.K, s.NK, Nz);
     A[(3 * mi + 0) * Np + spad(pos)] = val;
     A[(3 * mi + 1) * Np + spad(pos)] = dr;
@@ -175,8 +188,11 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   V2<T> *A = reinterpret_cast<V2<T> *>(smem_raw);
   V2<T> *B = A + nbuf * Ntp;
   V2<T> *tw = B + nbuf * Ntp;
-  load_tw<T>(tw, p.twt, Nt);
+  using CflBits = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned>::type;
+  __shared__ CflBits cfl_cta[3];   // CTA maxima of |u_r|, |u_theta|, |u_z| (bit patterns)
+  load_tw<T>(tw, p.twt, p.twt32, Nt);
   for (int i = threadIdx.x; i < nl * npair * Ntp; i += blockDim.x) A[i] = V2<T>{0, 0};
+  if (threadIdx.x < 3) cfl_cta[threadIdx.x] = 0;
   __syncthreads();
   // pack: buffer (li, c, 0) = value + i dtheta, (li, c, 1) = d/dr + i d/dz
   for (int t = threadIdx.x; t < nl * s.nf * s.NM; t += blockDim.x) {
@@ -211,25 +227,38 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   V2<T> *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Ntp, tw, zmid_ok(p.pt, s.M));
   V2<T> *out = (ph == A) ? B : A;
   const double rr = p.rad.r[r];
-  const T inv_r = (T)p.rad.inv_r[r];
+  T inv_r;
+  if constexpr (sizeof(T) == 4) inv_r = p.inv_r32[r];
+  else inv_r = p.rad.inv_r[r];
   // CFL: running maxima of |u_r|, |u_theta|, |u_z| in the transforms'
   // precision, kept as bit patterns (non-negative floating-point values order
   // like their bits: integer max, no FP64 issue slot); the divisions by the
-  // spacings come once per thread after the loop (division by a positive
+  // spacings come once per CTA after the loop (division by a positive
   // constant is monotone, so the max is unchanged).  The FP32 form adds the
   // mean profile in FP32: the CFL step then carries FP32 rounding, like the
   // rest of that form's nonlinear stage.
-  using CflBits = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned>::type;
   CflBits mr = 0, mt = 0, mz = 0;
   double nu = 0.0, nT = 0.0;
+  // |v| as its bit pattern: the sign bit cleared with an integer mask
   auto bits = [](T v) -> CflBits {
-    if constexpr (sizeof(T) == 8) return (CflBits)__double_as_longlong(fabs(v));
-    else return (CflBits)__float_as_uint(fabsf(v));
+    if constexpr (sizeof(T) == 8) return (CflBits)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    else return (CflBits)__float_as_uint(v) & 0x7fffffffu;
   };
   auto val = [](CflBits b) -> double {
     if constexpr (sizeof(T) == 8) return __longlong_as_double((long long)b);
     else return (double)__uint_as_float(b);
   };
+  // full velocity for the CFL bound (mixed: the transforms carry u' only;
+  // only the FP32 instantiation runs the mixed form)
+  const bool mixed = sizeof(T) == 4 && p.mixed;
+  T Ut = (T)0, Uz = (T)0;
+  if constexpr (sizeof(T) == 4) {
+    if (mixed) {
+      Ut = p.prof32[2 * r + 0];
+      Uz = p.prof32[2 * r + 1];
+    }
+  }
+  const bool centrifugal = p.eps_c != 0.0;   // FP64 form only
   for (int t = threadIdx.x; t < nl * Nt; t += blockDim.x) {
     const int2 a = divmod(t, Nt, p.fNt);
     const int j = a.y;
@@ -245,10 +274,6 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     const V2<T> t0 = b[2 * Ntp], t1 = b[3 * Ntp];   // (ut, ut_t), (ut_r, ut_z)
     const V2<T> z0 = b[4 * Ntp], z1 = b[5 * Ntp];   // (uz, uz_t), (uz_r, uz_z)
     const T ur = r0.x, ut = t0.x, uz = z0.x;
-    // full velocity for the CFL bound (mixed: the transforms carry u' only)
-    // (only the FP32 instantiation runs the mixed form)
-    const bool mixed = sizeof(T) == 4 && p.mixed;
-    const T Ut = mixed ? (T)p.prof[r * 8 + 0] : (T)0, Uz = mixed ? (T)p.prof[r * 8 + 1] : (T)0;
     if (mode == 1) {
       nu = fmax(nu, sqrt((double)ur * ur + (double)ut * ut + (double)uz * uz));
       if (s.nf == 4) nT = fmax(nT, fabs((double)b[6 * Ntp].x));
@@ -264,13 +289,15 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     T NT_ = 0;
     if (s.nf == 4) {
       const V2<T> T0 = b[6 * Ntp], T1 = b[7 * Ntp];
-      if (p.eps_c != 0.0) {   // centrifugal buoyancy (FP64 form only)
-        const T rho = (T)1 - (T)p.eps_c * T0.x;
-        Nr_ *= rho;
-        Nt_ *= rho;
-        Nz_ *= rho;
+      if constexpr (sizeof(T) == 8) {
+        if (centrifugal) {   // centrifugal buoyancy (FP64 form only)
+          const T rho = (T)1 - (T)p.eps_c * T0.x;
+          Nr_ *= rho;
+          Nt_ *= rho;
+          Nz_ *= rho;
+        }
+        Nz_ += (T)p.Gr * T0.x;   // mixed: buoyancy added in FP64 in k_zfwd
       }
-      if (!p.mixed) Nz_ += (T)p.Gr * T0.x;   // mixed: buoyancy added in FP64
       NT_ = -(ur * T1.x + ut_r * T0.y + uz * T1.y);
     }
     V2<T> *o = out + li * 2 * Ntp + spad(j);
@@ -293,12 +320,27 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     }
     return;
   }
+  // CTA maxima of the bit patterns (integer operations only), then one thread
+  // divides by the spacings: the same rate as the max over points of the
+  // per-point rates, since division by a positive constant is monotone
   if (rate_bits) {
-    double rate = fmax(val(mr) / p.rad.dr_min[r], fmax(val(mt) / (rr * p.dth), val(mz) / p.dz));
-    for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_pos(rate_bits, rate);
+    for (int o = 16; o > 0; o >>= 1) {
+      mr = max(mr, (CflBits)__shfl_xor_sync(0xffffffffu, mr, o));
+      mt = max(mt, (CflBits)__shfl_xor_sync(0xffffffffu, mt, o));
+      mz = max(mz, (CflBits)__shfl_xor_sync(0xffffffffu, mz, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&cfl_cta[0], mr);
+      atomicMax(&cfl_cta[1], mt);
+      atomicMax(&cfl_cta[2], mz);
+    }
   }
   __syncthreads();
+  if (rate_bits && threadIdx.x == 0) {
+    const double rate = fmax(val(cfl_cta[0]) / p.rad.dr_min[r],
+                             fmax(val(cfl_cta[1]) / (rr * p.dth), val(cfl_cta[2]) / p.dz));
+    atomic_max_pos(rate_bits, rate);
+  }
   V2<T> *scratch = (out == A) ? B : A;
   V2<T> *sp = fft_batch<-1>(out, scratch, p.pt, nl * 2, Ntp, tw);
   // unpack two real transforms: X_m = (Z_m + conj Z_-m)/2, Y_m = (Z_m - conj Z_-m)/(2i);
@@ -337,7 +379,7 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
   V2<T> *A = reinterpret_cast<V2<T> *>(smem_raw);
   V2<T> *B = A + s.nf * p.MB * Np;
   V2<T> *tw = B + s.nf * p.MB * Np;
-  load_tw<T>(tw, p.twz, Nz);
+  load_tw<T>(tw, p.twz, p.twz32, Nz);
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
   const FastDiv fnm = (nm == p.MB) ? p.fMB : p.fMBl;
   for (int t = threadIdx.x; t < nb * Nz; t += blockDim.x) {
@@ -505,7 +547,7 @@ void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long lon
     float2 *W = reinterpret_cast<float2 *>(c->W);
     {
       LaunchScope ls(c, KZINV);
-      k_meanprof<<<(s.Nr + 63) / 64, 64, 0, c->stream>>>(X, c->prof, s, q.rad);
+      k_meanprof<<<(s.Nr + 63) / 64, 64, 0, c->stream>>>(X, c->prof, c->d_prof32, s, q.rad);
       k_tofloat<<<(unsigned)(((long long)s.nf * s.S + 255) / 256), 256, 0, c->stream>>>(
           X, c->X32, s);
       k_zinv<float><<<dim3((s.NM + q.MB - 1) / q.MB, s.Nr, s.nf), 256, c->smem32_zinv,
@@ -759,7 +801,7 @@ __global__ void k_zinv_adj(const double2 *__restrict__ Nb, double2 *__restrict__
   double2 *A = reinterpret_cast<double2 *>(smem_raw);
   double2 *B = A + s.nf * p.MB * Np;
   double2 *tw = B + s.nf * p.MB * Np;
-  load_tw<double>(tw, p.twz, Nz);
+  load_tw<double>(tw, p.twz, nullptr, Nz);
   for (int i = threadIdx.x; i < s.nf * nm * Np; i += blockDim.x) A[i] = double2{0, 0};
   __syncthreads();
   for (int t = threadIdx.x; t < s.nf * nm * s.NK; t += blockDim.x) {
@@ -806,7 +848,7 @@ __global__ void k_theta_adj(const double2 *__restrict__ Vin, const double2 *__re
   double2 *A = reinterpret_cast<double2 *>(smem_raw);
   double2 *B = A + nbuf * Ntp;
   double2 *tw = B + nbuf * Ntp;
-  load_tw<double>(tw, p.twt, Nt);
+  load_tw<double>(tw, p.twt, nullptr, Nt);
   for (int i = threadIdx.x; i < nl * npair * Ntp; i += blockDim.x) A[i] = double2{0, 0};
   __syncthreads();
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
@@ -943,7 +985,7 @@ __global__ void k_zfwd_adj(const double2 *__restrict__ Wa, double2 *__restrict__
   double2 *A = reinterpret_cast<double2 *>(smem_raw);
   double2 *B = A + 3 * p.MB * Np;
   double2 *tw = B + 3 * p.MB * Np;
-  load_tw<double>(tw, p.twz, Nz);
+  load_tw<double>(tw, p.twz, nullptr, Nz);
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
   for (int t = threadIdx.x; t < 3 * nm * Nz; t += blockDim.x) {
     const int mi = t % nm;

@@ -396,6 +396,8 @@ void allocate(tc_ctx *c) {
   c->d_s0 = dalloc<int>(c, s.Nr);
   c->d_twz = dalloc<double2>(c, s.Nz);
   c->d_twt = dalloc<double2>(c, s.Nt);
+  c->d_f32 = dalloc<float>(c, (size_t)2 * s.Nz + 2 * s.Nt + (size_t)kStencil * s.Nr + s.NK + s.Nr);
+  c->d_prof32 = dalloc<float>(c, (size_t)2 * s.Nr);
   const int K1 = s.K + 1;
   c->lin.nopP = s.NM * K1;
   c->lin.nopH = (s.NM + 1) * K1;
@@ -476,6 +478,32 @@ void upload_tables(tc_ctx *c) {
   p.pt = make_plan(s.Nt);
   p.twz = c->d_twz;
   p.twt = c->d_twt;
+  {
+    // FP32 tables: twiddles (z, theta), d/dr weights, beta per stored k, 1/r
+    std::vector<float> f((size_t)2 * s.Nz + 2 * s.Nt + (size_t)kStencil * s.Nr + s.NK + s.Nr);
+    size_t o = 0;
+    for (int i = 0; i < s.Nz; ++i) {
+      f[o++] = (float)tz[i].x;
+      f[o++] = (float)tz[i].y;
+    }
+    for (int i = 0; i < s.Nt; ++i) {
+      f[o++] = (float)tt[i].x;
+      f[o++] = (float)tt[i].y;
+    }
+    const size_t od1 = o;
+    for (size_t q = 0; q < (size_t)kStencil * s.Nr; ++q) f[o++] = (float)c->D1[q];
+    const size_t obeta = o;
+    for (int kk = 0; kk < s.NK; ++kk) f[o++] = (float)(p.alpha * (kk <= s.K ? kk : kk - s.NK));
+    const size_t oir = o;
+    for (int j = 0; j < s.Nr; ++j) f[o++] = (float)inv_r[j];
+    ck(cudaMemcpy(c->d_f32, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    p.twz32 = reinterpret_cast<const float2 *>(c->d_f32);
+    p.twt32 = reinterpret_cast<const float2 *>(c->d_f32 + 2 * s.Nz);
+    p.d1_32 = c->d_f32 + od1;
+    p.beta32 = c->d_f32 + obeta;
+    p.inv_r32 = c->d_f32 + oir;
+    p.prof32 = c->d_prof32;
+  }
   LinParams &l = c->lin;
   l.sz = s;
   l.rad = rad;

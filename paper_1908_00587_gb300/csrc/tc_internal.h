@@ -118,6 +118,16 @@ struct NLParams {
   // transforming the state again when phys_in is set (FP64 only)
   double2 *phys_out;
   const double2 *phys_in;
+  // FP32 copies for the mixed form's transform kernels, each entry the FP32
+  // rounding of its FP64 counterpart made once on the host: the twiddle
+  // tables, the 9-point d/dr weights [r][9], beta = alpha k per stored axial
+  // index, 1/r; prof32 [r][2] = U_theta, U_z (written by k_meanprof).  An FP64
+  // instruction costs a warp's turn on the FP64 unit (about 64 cycles)
+  // however few of its lanes are active, so the FP32 kernels take these
+  // values instead of converting per thread.
+  const float2 *twz32, *twt32;
+  const float *d1_32, *beta32, *inv_r32;
+  float *prof32;
 };
 void set_divisors(NLParams &p);
 
@@ -180,6 +190,8 @@ struct tc_ctx {
   double *d_r, *d_inv_r, *d_D1, *d_D2, *d_dr, *d_wr;
   int *d_s0;
   double2 *d_twz, *d_twt;
+  float *d_f32;          // FP32 tables of NLParams (twiddles, d/dr weights, beta, 1/r)
+  float *d_prof32;       // [Nr][2] FP32 mean profiles (mixed form)
   double *LP, *UP, *LH, *UH, *LT, *UT, *infl, *Ainv;
   double *dt_hist;
   int dt_hist_cap = 0;
