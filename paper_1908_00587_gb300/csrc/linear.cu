@@ -295,7 +295,7 @@ __global__ void k_rhs(const double2 *__restrict__ X, const double2 *__restrict__
   const int j = (int)i / s.nmode;
   const int mode = (int)(i - (long long)j * s.nmode);
   const int m = mode / s.NK, kk = mode % s.NK;
-  const double beta = p.alpha * kval(kk, s.K, s.NK);
+  const double beta = p.betak[kk];
   const double idt = sc->idt;
   const double ir = p.rad.inv_r[j];
   const int st = p.rad.s0[j];
@@ -309,7 +309,7 @@ __global__ void k_rhs(const double2 *__restrict__ X, const double2 *__restrict__
 #pragma unroll
     for (int t = 0; t < kStencil; ++t) d1p = d1p + d1[t] * P[(long long)(st + t) * s.nmode + mode];
     const double2 pj = P[i];
-    const double2 mp = (m * ir) * pj;
+    const double2 mp = (p.mval[m] * ir) * pj;
     const double2 xr = X[i], xt = X[S + i];
     const double2 xp = {xr.x - xt.y, xr.y + xt.x}, xm = {xr.x + xt.y, xr.y - xt.x};
     const double2 nr = N[i], nt = N[S + i];
@@ -408,7 +408,7 @@ k_prhs(const double2 *__restrict__ Yb, const double2 *__restrict__ N, double *__
     double2 b = {0.0, 0.0};
     if (mode != 0 && j > 0 && j < s.Nr - 1) {
       const int m = mode / s.NK, kk = mode % s.NK;
-      const double beta = p.alpha * kval(kk, s.K, s.NK);
+      const double beta = p.betak[kk];
       const int q0 = p.rad.s0[j] - (j0 - 8);
       const double *dw = p.rad.Dw + j * kStencil;   // (1/r_j) D1 r_s
       double2 acc = {0.0, 0.0};
@@ -417,7 +417,7 @@ k_prhs(const double2 *__restrict__ Yb, const double2 *__restrict__ N, double *__
       const double2 rt = div_2i(rhs_pm(Yb, N, S, i, 0) - rhs_pm(Yb, N, S, i, 1));
       const double2 rz = rhs_pm(Yb, N, S, i, 2);
       const double ir = p.rad.inv_r[j];
-      b = acc + (m * ir) * mul_i(rt) + beta * mul_i(rz);
+      b = acc + (p.mval[m] * ir) * mul_i(rt) + beta * mul_i(rz);
     }
     Ps[i] = b.x;
     Ps[S + i] = b.y;
@@ -461,7 +461,7 @@ __global__ void k_hrhs(const double2 *__restrict__ Yb, const double2 *__restrict
     b[0] = b[1] = b[2] = double2{0.0, 0.0};
   } else {
     const int m = mode / s.NK, kk = mode % s.NK;
-    const double beta = p.alpha * kval(kk, s.K, s.NK);
+    const double beta = p.betak[kk];
     const int st = p.rad.s0[j];
     double2 d1p = {0.0, 0.0};
 #pragma unroll
@@ -470,7 +470,7 @@ __global__ void k_hrhs(const double2 *__restrict__ Yb, const double2 *__restrict
       d1p = d1p + p.rad.D1[j * kStencil + q] * double2{Ps[o], Ps[S + o]};
     }
     const double2 pj = {Ps[i], Ps[S + i]};
-    const double2 mp = (m * p.rad.inv_r[j]) * pj;
+    const double2 mp = (p.mval[m] * p.rad.inv_r[j]) * pj;
     b[0] = rhs_pm(Yb, N, S, i, 0) - (d1p - mp);
     b[1] = rhs_pm(Yb, N, S, i, 1) - (d1p + mp);
     b[2] = rhs_pm(Yb, N, S, i, 2) - beta * mul_i(pj);
@@ -883,7 +883,7 @@ __global__ void k_correct(const double *__restrict__ U, const double *__restrict
       const int m = mode / s.NK, kk = mode % s.NK;
       const int kv = kval(kk, s.K, s.NK);
       const int o = m * (s.K + 1) + (kv < 0 ? -kv : kv);
-      const double beta = p.alpha * kv;
+      const double beta = p.betak[kk];
       const double2 a = alpha[mode], b = alpha[s.nmode + mode];
       const long long fs = (long long)s.Nr * p.nopP;
       const long long jo = (long long)j * p.nopP + o;
@@ -1120,9 +1120,9 @@ __global__ void k_stT_hrhs(const double *__restrict__ U, double2 *__restrict__ R
     Rb[i] = b[0];
     Rb[S + i] = b[1];
     const int m = mode / s.NK, kk = mode % s.NK;
-    const double beta = p.alpha * kval(kk, s.K, s.NK);
+    const double beta = p.betak[kk];
     if (interior) {
-      const double mr = m * p.rad.inv_r[j];
+      const double mr = p.mval[m] * p.rad.inv_r[j];
       // slot0: +(m/r) p, slot1: -(m/r) p, slot2: -i beta p (transpose +i beta)
       pb.x = mr * (b[0].x - b[1].x) - beta * b[2].y;
       pb.y = mr * (b[0].y - b[1].y) + beta * b[2].x;
@@ -1155,7 +1155,7 @@ __global__ void k_stT_prhs(const double *__restrict__ Ps, double2 *__restrict__ 
   if (mode == 0) return;
   const long long S = s.S;
   const int m = mode / s.NK, kk = mode % s.NK;
-  const double beta = p.alpha * kval(kk, s.K, s.NK);
+  const double beta = p.betak[kk];
   double2 rr = {0.0, 0.0}, rt = {0.0, 0.0}, rz = {0.0, 0.0};
   for (int e = 0; e < kTrans; ++e) {
     const int j = p.rad.tj[sn * kTrans + e];
@@ -1169,7 +1169,7 @@ __global__ void k_stT_prhs(const double *__restrict__ Ps, double2 *__restrict__ 
   }
   if (sn > 0 && sn < s.Nr - 1) {
     const double2 bp = {Ps[i], Ps[S + i]};
-    const double mr = m * p.rad.inv_r[sn];
+    const double mr = p.mval[m] * p.rad.inv_r[sn];
     rt = double2{mr * bp.y, -mr * bp.x};        // (-i m / r) bp
     rz = double2{beta * bp.y, -beta * bp.x};    // (-i beta) bp
   }
@@ -1219,7 +1219,7 @@ __global__ void k_rhsT(const double2 *__restrict__ Yb, double2 *__restrict__ Xb,
   const int mode = (int)(i - (long long)sn * s.nmode);
   const long long S = s.S;
   const int m = mode / s.NK, kk = mode % s.NK;
-  const double beta = p.alpha * kval(kk, s.K, s.NK);
+  const double beta = p.betak[kk];
   const double idt = 1.0 / sc->dt;
   const double om = 1.0 - kCN;
   const double ir = p.rad.inv_r[sn];

@@ -393,7 +393,8 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
   __syncthreads();
   V2<T> *res = fft_batch<-1>(A, B, p.pz, nb, Np, tw);
   // 1/(Ntheta Nz), times the 1/2 of k_theta's unpacking of paired transforms
-  const double scale = 0.5 / ((double)s.Nt * (double)s.Nz);
+  // (set on the host: a division here would cost every warp FP64 turns)
+  const double scale = p.zscale;
   if (!p.mixed) {
     for (int t = threadIdx.x; t < nb * s.NK; t += blockDim.x) {
       const int2 a = divmod(t, s.NK, p.fNK);
@@ -744,6 +745,7 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
   p.Gr = (Ra != 0.0) ? Ra / Pr : 0.0;
   p.dth = 2.0 * M_PI / s.Nt;
   p.dz = Lz / s.Nz;
+  p.zscale = 0.5 / ((double)s.Nt * (double)s.Nz);
   p.pz = make_plan(s.Nz);
   p.pt = make_plan(s.Nt);
   p.twz = reinterpret_cast<const double2 *>(base + L.twz);

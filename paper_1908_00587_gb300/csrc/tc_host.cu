@@ -398,6 +398,7 @@ void allocate(tc_ctx *c) {
   c->d_twt = dalloc<double2>(c, s.Nt);
   c->d_f32 = dalloc<float>(c, (size_t)2 * s.Nz + 2 * s.Nt + (size_t)kStencil * s.Nr + s.NK + s.Nr);
   c->d_prof32 = dalloc<float>(c, (size_t)2 * s.Nr);
+  c->d_kmtab = dalloc<double>(c, (size_t)s.NK + s.NM);
   const int K1 = s.K + 1;
   c->lin.nopP = s.NM * K1;
   c->lin.nopH = (s.NM + 1) * K1;
@@ -474,6 +475,7 @@ void upload_tables(tc_ctx *c) {
   p.Gr = c->Gr;
   p.dth = 2.0 * M_PI / s.Nt;
   p.dz = c->Lz / s.Nz;
+  p.zscale = 0.5 / ((double)s.Nt * (double)s.Nz);
   p.pz = make_plan(s.Nz);
   p.pt = make_plan(s.Nt);
   p.twz = c->d_twz;
@@ -519,6 +521,14 @@ void upload_tables(tc_ctx *c) {
   l.UT = c->UT;
   l.infl = c->infl;
   l.Ainv = c->Ainv;
+  {
+    std::vector<double> km((size_t)s.NK + s.NM);
+    for (int kk = 0; kk < s.NK; ++kk) km[kk] = p.alpha * (double)(kk <= s.K ? kk : kk - s.NK);
+    for (int m = 0; m < s.NM; ++m) km[s.NK + m] = (double)m;
+    ck(cudaMemcpy(c->d_kmtab, km.data(), km.size() * sizeof(double), cudaMemcpyHostToDevice));
+    l.betak = c->d_kmtab;
+    l.mval = c->d_kmtab + s.NK;
+  }
 }
 
 }  // namespace

@@ -99,6 +99,7 @@ struct NLParams {
   double alpha;         // 2 pi / Lz
   double Gr;            // Ra / Pr
   double dth, dz;       // grid spacings in theta and z
+  double zscale;        // 1/(2 Ntheta Nz): forward scale with the 1/2 of k_theta's unpacking
   int MB;               // m columns per CTA in the z kernels
   int LB;               // z rows per CTA in the theta kernel
   FFTPlan pz, pt;
@@ -146,6 +147,9 @@ struct LinParams {
   double *infl;         // influence data [8][Nr][nopP]: pa pb upa uma upb umb za zb
   double *Ainv;         // [4][nopP]
   double *flux_ug;      // axial-flux constraint: (0,0) u_z response to a unit forcing (Nr), or null
+  // beta = alpha k per stored axial index (NK) and m as a double (NM), so the
+  // per-coefficient kernels convert no integer on the FP64 unit
+  const double *betak, *mval;
 };
 
 }  // namespace tc
@@ -192,6 +196,7 @@ struct tc_ctx {
   double2 *d_twz, *d_twt;
   float *d_f32;          // FP32 tables of NLParams (twiddles, d/dr weights, beta, 1/r)
   float *d_prof32;       // [Nr][2] FP32 mean profiles (mixed form)
+  double *d_kmtab;       // LinParams::betak (NK) then mval (NM)
   double *LP, *UP, *LH, *UH, *LT, *UT, *infl, *Ainv;
   double *dt_hist;
   int dt_hist_cap = 0;
