@@ -37,9 +37,10 @@ def rel_l2(mdl, a, b):
                for f in range(a.shape[0]))
 
 
-@pytest.mark.parametrize("Ra", [0.0, 700.0])
-def test_mixed_nonlinear_random_state(tc, Ra):
-    wl = Workload("mx", Nr=20, Ntheta=36, Nz=40, eta=0.6, Lz=1.5, Re_i=80.0, Ra=Ra, Pr=0.9,
+@pytest.mark.parametrize("Nr,Nt,Nz,Ra", [(20, 36, 40, 0.0), (20, 36, 40, 700.0),
+                                         (10, 128, 256, 300.0)])   # compile-time plans 128, 256
+def test_mixed_nonlinear_random_state(tc, Nr, Nt, Nz, Ra):
+    wl = Workload("mx", Nr=Nr, Ntheta=Nt, Nz=Nz, eta=0.6, Lz=1.5, Re_i=80.0, Ra=Ra, Pr=0.9,
                   precision=1)
     mdl = Model(wl)
     X = random_state(900, mdl.nf, wl.Nr, mdl.M, mdl.K)

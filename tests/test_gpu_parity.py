@@ -299,6 +299,8 @@ def test_create_size_limits(tc):
 @pytest.mark.parametrize("Nr,Nt,Nz,Ra", [(9, 750, 8, 400.0),     # largest azimuthal size with T
                                          (11, 1000, 6, 0.0),      # largest without T
                                          (9, 512, 16, 0.0),       # plan 8 x 8 x 8 in theta
+                                         (9, 256, 16, 300.0),     # plan 8 x 8 x 4 in theta
+                                         (10, 16, 256, 0.0),      # plan 8 x 8 x 4 in z
                                          (9, 4, 4, 300.0)])       # smallest: M = K = 1
 def test_nonlinear_extreme_sizes(tc, Nr, Nt, Nz, Ra):
     wl = _wl(Nr, Nt, Nz, Ra)
