@@ -83,6 +83,7 @@ typedef struct {
   size_t device_bytes;          /* device memory held by the context */
   long long launches;           /* kernels launched since tc_create */
   int tile_mb, tile_lb;         /* nonlinear-stage tiles in use (see "tile_mb") */
+  int tile_mbf;                 /* m columns per CTA of the forward axial kernel */
 } tc_info;
 
 /* Device time of one kernel accumulated while option "timing" is 1. */
@@ -126,8 +127,10 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               replays it (re-captured after any option change or a new
  *               fixed dt); 0, or timing on: kernels launched one by one.
  *               Results are identical either way.
- *   "tile_mb"   m columns per CTA of the axial transform kernels, "tile_lb"
- *               z rows per CTA of the azimuthal kernel (0: size-based default;
+ *   "tile_mb"   m columns per CTA of the inverse axial kernel (and, unless
+ *               "tile_mbf" is set, of the forward one), "tile_mbf" m columns
+ *               per CTA of the forward axial kernel, "tile_lb" z rows per
+ *               CTA of the azimuthal kernel (0: size-based default;
  *               TC_ERR_UNSUPPORTED if the shared memory would not fit).  The
  *               tiles change only which CTA computes a transform, not the
  *               arithmetic, so results are identical for every choice.
@@ -364,8 +367,10 @@ tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt);
 
 /* Tile autotuner for one context (the one the ensemble runs per size
  * class): times the nonlinear stage on the context's current state for tile
- * shapes {1, 2, 4, 8} of "tile_mb", then of "tile_lb", keeps the fastest and
- * returns them (host, nullable).  Results do not depend on the tiles. */
+ * shapes {1, 2, 3, 4, 5, 6, 8} of "tile_mb", then {1, 2, 3, 4, 8} of
+ * "tile_lb", then {1, 2, 3, 4, 5, 6, 8} of "tile_mbf", keeps the fastest and
+ * returns the first two (host, nullable; tc_get_info reports all three).
+ * Results do not depend on the tiles. */
 tc_status tc_autotune(tc_ctx *ctx, int *tile_mb, int *tile_lb);
 
 /* Kernel launches one graph replay (one step of every member) contains. */

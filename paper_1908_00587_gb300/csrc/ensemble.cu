@@ -68,10 +68,15 @@ tc_status autotune(tc_ctx *c, int *best_mb, int *best_lb) {
     cudaEventDestroy(a);
     return TC_ERR_CUDA;
   }
-  const int cand[] = {1, 2, 4, 8};
+  // widths that are not powers of two change how the grids fill the 152 SMs
+  const int cand_mb[] = {1, 2, 3, 4, 5, 6, 8};
+  const int cand_lb[] = {1, 2, 3, 4, 8};
+  // the forward axial kernel's width stays at its default while tile_mb is
+  // searched, so that search sees only the inverse kernel change
+  tc_set_option(c, "tile_mbf", (c->precision == 1) ? c->nl32.MBf : c->nl.MBf);
   float best = 1e30f;
   int bm = 0;
-  for (int mb : cand) {
+  for (int mb : cand_mb) {
     if (mb > c->sz.NM) break;
     if (tc_set_option(c, "tile_mb", mb) != TC_OK) continue;
     const float t = time_nonlinear(c, a, b, 3);
@@ -83,7 +88,7 @@ tc_status autotune(tc_ctx *c, int *best_mb, int *best_lb) {
   if (bm) tc_set_option(c, "tile_mb", bm);
   best = 1e30f;
   int bl = 0;
-  for (int lb : cand) {
+  for (int lb : cand_lb) {
     if (tc_set_option(c, "tile_lb", lb) != TC_OK) continue;
     const float t = time_nonlinear(c, a, b, 3);
     if (t < best) {
@@ -92,6 +97,19 @@ tc_status autotune(tc_ctx *c, int *best_mb, int *best_lb) {
     }
   }
   if (bl) tc_set_option(c, "tile_lb", bl);
+  // the forward axial kernel's own width (its grid fills the SMs differently)
+  best = 1e30f;
+  int bf = 0;
+  for (int mb : cand_mb) {
+    if (mb > c->sz.NM) break;
+    if (tc_set_option(c, "tile_mbf", mb) != TC_OK) continue;
+    const float t = time_nonlinear(c, a, b, 3);
+    if (t < best) {
+      best = t;
+      bf = mb;
+    }
+  }
+  if (bf) tc_set_option(c, "tile_mbf", bf);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   const cudaError_t err = cudaGetLastError();
@@ -161,7 +179,8 @@ tc_status tc_ensemble_create(int n, const tc_params *p, int autotune_tiles, tc_e
     tc_set_stream(c, s);
   }
   if (autotune_tiles) {
-    std::map<ClassKey, std::pair<int, int>> tuned;
+    // tuned (tile_mb, tile_lb, tile_mbf) per size class
+    std::map<ClassKey, std::tuple<int, int, int>> tuned;
     for (tc_ctx *c : e->m) {
       const ClassKey k = class_of(c);
       auto it = tuned.find(k);
@@ -169,10 +188,12 @@ tc_status tc_ensemble_create(int n, const tc_params *p, int autotune_tiles, tc_e
         int mb = 0, lb = 0;
         tc_status st = autotune(c, &mb, &lb);
         if (st != TC_OK) return fail(st);
-        tuned[k] = {mb, lb};
+        tuned[k] = std::make_tuple(mb, lb, c->tile_mbf);
       } else {
-        if (it->second.first) tc_set_option(c, "tile_mb", it->second.first);
-        if (it->second.second) tc_set_option(c, "tile_lb", it->second.second);
+        const auto [mb, lb, mbf] = it->second;
+        if (mb) tc_set_option(c, "tile_mb", mb);
+        if (lb) tc_set_option(c, "tile_lb", lb);
+        if (mbf) tc_set_option(c, "tile_mbf", mbf);
       }
     }
   }

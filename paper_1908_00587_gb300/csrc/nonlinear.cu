@@ -369,19 +369,19 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
 template <typename T>
 __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLParams p) {
   const Sizes &s = p.sz;
-  const int m0 = blockIdx.x * p.MB;
-  const int nm = min(p.MB, s.NM - m0);
+  const int m0 = blockIdx.x * p.MBf;
+  const int nm = min(p.MBf, s.NM - m0);
   const int r = blockIdx.y;
   const int Nz = s.Nz;
   const int Np = padlen(Nz);
   const int nb = s.nf * nm;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V2<T> *A = reinterpret_cast<V2<T> *>(smem_raw);
-  V2<T> *B = A + s.nf * p.MB * Np;
-  V2<T> *tw = B + s.nf * p.MB * Np;
+  V2<T> *B = A + s.nf * p.MBf * Np;
+  V2<T> *tw = B + s.nf * p.MBf * Np;
   load_tw<T>(tw, p.twz, p.twz32, Nz);
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
-  const FastDiv fnm = (nm == p.MB) ? p.fMB : p.fMBl;
+  const FastDiv fnm = (nm == p.MBf) ? p.fMBf : p.fMBfl;
   for (int t = threadIdx.x; t < nb * Nz; t += blockDim.x) {
     const int2 a = divmod(t, nm, fnm);
     const int mi = a.y;
@@ -417,7 +417,7 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
   // with a = i al, al = m U_theta/r + beta U_z from a table built once per
   // CTA (it serves every field of a mode).
   V2<T> *scratch = (res == A) ? B : A;
-  double *alt = reinterpret_cast<double *>(scratch);   // [mi][kk], MB NK <= 2 nf MB Np
+  double *alt = reinterpret_cast<double *>(scratch);   // [mi][kk], MBf NK <= 2 nf MBf Np
   const double *pr = p.prof + r * 8;
   const double ir = p.rad.inv_r[r];
   const double Utr = pr[0] * ir, Uz = pr[1], dUt = pr[2], dUz = pr[3], dTb = pr[4];
@@ -489,6 +489,9 @@ void set_divisors(NLParams &p) {
   p.fMB = make_fastdiv((unsigned)p.MB);
   const int last = s.NM - ((s.NM - 1) / p.MB) * p.MB;   // width of the last m-block
   p.fMBl = make_fastdiv((unsigned)last);
+  p.fMBf = make_fastdiv((unsigned)p.MBf);
+  const int lastf = s.NM - ((s.NM - 1) / p.MBf) * p.MBf;
+  p.fMBfl = make_fastdiv((unsigned)lastf);
 }
 
 void setup_nonlinear(tc_ctx *c) {
@@ -502,6 +505,7 @@ void setup_nonlinear(tc_ctx *c) {
   if (c->tile_mb > 0) MB = c->tile_mb;
   if (MB > s.NM) MB = s.NM;
   p.MB = MB;
+  p.MBf = (c->tile_mbf > 0) ? std::min(c->tile_mbf, s.NM) : MB;
   int LB = (int)(4096 / (2 * s.nf * s.Nt));
   if (LB < 1) LB = 1;
   if (LB > 8) LB = 8;
@@ -509,7 +513,7 @@ void setup_nonlinear(tc_ctx *c) {
   p.LB = LB;
   c->smem_zinv = (size_t)(2 * 3 * MB * padlen(s.Nz) + s.Nz) * e;
   c->smem_theta = (size_t)(2 * LB * 2 * s.nf * padlen(s.Nt) + s.Nt) * e;
-  c->smem_zfwd = (size_t)(2 * s.nf * MB * padlen(s.Nz) + s.Nz) * e;
+  c->smem_zfwd = (size_t)(2 * s.nf * p.MBf * padlen(s.Nz) + s.Nz) * e;
   allow_smem(k_zinv<double>);
   allow_smem(k_theta<double>);
   allow_smem(k_zfwd<double>);
@@ -525,12 +529,13 @@ void setup_nonlinear(tc_ctx *c) {
   LB32 = LB32 < 1 ? 1 : (LB32 > 8 ? 8 : LB32);
   if (c->tile_lb > 0) LB32 = c->tile_lb;
   q.MB = MB32;
+  q.MBf = (c->tile_mbf > 0) ? std::min(c->tile_mbf, s.NM) : MB32;
   q.LB = LB32;
   set_divisors(p);
   set_divisors(q);
   c->smem32_zinv = (size_t)(2 * 3 * MB32 * padlen(s.Nz) + s.Nz) * e32;
   c->smem32_theta = (size_t)(2 * LB32 * 2 * s.nf * padlen(s.Nt) + s.Nt) * e32;
-  c->smem32_zfwd = (size_t)(2 * s.nf * MB32 * padlen(s.Nz) + s.Nz) * e32;
+  c->smem32_zfwd = (size_t)(2 * s.nf * q.MBf * padlen(s.Nz) + s.Nz) * e32;
   allow_smem(k_zinv<float>);
   allow_smem(k_theta<float>);
   allow_smem(k_zfwd<float>);
@@ -560,7 +565,7 @@ void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long lon
                        c->stream>>>(V, W, q, rate_bits, c->scal->norm_bits, 0);
     }
     LaunchScope ls(c, KZFWD);
-    k_zfwd<float><<<dim3((s.NM + q.MB - 1) / q.MB, s.Nr), 256, c->smem32_zfwd, c->stream>>>(
+    k_zfwd<float><<<dim3((s.NM + q.MBf - 1) / q.MBf, s.Nr), 256, c->smem32_zfwd, c->stream>>>(
         W, N, q);
     return;
   }
@@ -579,7 +584,8 @@ void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long lon
   }
   if (mode == 1) return;
   LaunchScope ls(c, KZFWD);
-  k_zfwd<double><<<dim3(nmb, s.Nr), 256, c->smem_zfwd, c->stream>>>(c->W, N, p);
+  k_zfwd<double><<<dim3((s.NM + p.MBf - 1) / p.MBf, s.Nr), 256, c->smem_zfwd, c->stream>>>(
+      c->W, N, p);
 }
 
 }  // namespace tc
@@ -683,6 +689,7 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
   int LB = (int)(4096 / (2 * s.nf * s.Nt));
   LB = LB < 1 ? 1 : (LB > 8 ? 8 : LB);
   p.MB = MB;
+  p.MBf = MB;
   p.LB = LB;
   set_divisors(p);
   const size_t e = sizeof(double2);

@@ -779,10 +779,12 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
     c->cfl_limit = v;
   } else if (k == "check") {
     c->check = v != 0.0;
-  } else if (k == "tile_mb" || k == "tile_lb") {
+  } else if (k == "tile_mb" || k == "tile_lb" || k == "tile_mbf") {
     if (v < 0.0 || v > 64.0 || v != (double)(int)v) return TC_ERR_ARG;
-    const int old_mb = c->tile_mb, old_lb = c->tile_lb;
-    if (k == "tile_mb") c->tile_mb = (int)v; else c->tile_lb = (int)v;
+    const int old_mb = c->tile_mb, old_lb = c->tile_lb, old_mbf = c->tile_mbf;
+    if (k == "tile_mb") c->tile_mb = (int)v;
+    else if (k == "tile_lb") c->tile_lb = (int)v;
+    else c->tile_mbf = (int)v;
     setup_nonlinear(c);
     const bool fits = (c->precision == 1)
         ? (c->smem32_zinv <= 227 * 1024 && c->smem32_theta <= 227 * 1024 && c->smem32_zfwd <= 227 * 1024)
@@ -790,6 +792,7 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
     if (!fits) {
       c->tile_mb = old_mb;
       c->tile_lb = old_lb;
+      c->tile_mbf = old_mbf;
       setup_nonlinear(c);
       return TC_ERR_UNSUPPORTED;
     }
@@ -861,6 +864,7 @@ tc_status tc_get_info(const tc_ctx *c, tc_info *o) {
   o->launches = c->launches;
   o->tile_mb = (c->precision == 1) ? c->nl32.MB : c->nl.MB;
   o->tile_lb = (c->precision == 1) ? c->nl32.LB : c->nl.LB;
+  o->tile_mbf = (c->precision == 1) ? c->nl32.MBf : c->nl.MBf;
   return TC_OK;
 }
 

@@ -100,7 +100,8 @@ struct NLParams {
   double Gr;            // Ra / Pr
   double dth, dz;       // grid spacings in theta and z
   double zscale;        // 1/(2 Ntheta Nz): forward scale with the 1/2 of k_theta's unpacking
-  int MB;               // m columns per CTA in the z kernels
+  int MB;               // m columns per CTA in k_zinv (and the adjoint z kernels)
+  int MBf;              // m columns per CTA in k_zfwd
   int LB;               // z rows per CTA in the theta kernel
   FFTPlan pz, pt;
   const double2 *twz, *twt;   // pass-major twiddle tables of pz, pt (FP64 master copy)
@@ -111,8 +112,8 @@ struct NLParams {
   const double *prof;         // [r][8]: U_theta, U_z, dU_theta/dr, dU_z/dr, dTbar/dr, T mean
   double eps_c;               // centrifugal buoyancy: advection weighted by 1 - eps_c T (FP64 only)
   // fixed divisors of the element loops (set_divisors): NK, NM, Nt, Nz, nf,
-  // MB and the last m-block's width
-  FastDiv fNK, fNM, fNt, fNz, fnf, fMB, fMBl;
+  // MB and the last m-block's width, MBf and its last block's width
+  FastDiv fNK, fNM, fNt, fNz, fnf, fMB, fMBl, fMBf, fMBfl;
   // physical-grid fields of the forward transforms, [r][z][2 nf][Nt] complex
   // pairs (value + i d/dtheta, d/dr + i d/dz per component): k_theta writes
   // them when phys_out is set, the adjoint theta kernel reads them instead of
@@ -217,7 +218,7 @@ struct tc_ctx {
   long long launches = 0;        // kernels launched since tc_create
   int timing = 0;
   int capturing = 0;            // a graph is capturing this context's stream
-  int tile_mb = 0, tile_lb = 0; // nonlinear-stage tile overrides (0: default)
+  int tile_mb = 0, tile_lb = 0, tile_mbf = 0;   // nonlinear-stage tile overrides (0: default)
   int n_corr = 1;               // corrector passes per step
   int flux = 0;                 // axial-flux constraint on the (0,0) u_z mode
   double eps_c = 0.0;           // centrifugal buoyancy coefficient

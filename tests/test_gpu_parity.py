@@ -270,6 +270,30 @@ def test_non_blocking_stream_gives_identical_results(tc):
     assert np.array_equal(out[0][1], out[1][1])
 
 
+def test_nonlinear_identical_for_every_tile(tc):
+    """Tiles change only which CTA computes a transform: the nonlinear terms
+    are bitwise the same for every (tile_mb, tile_lb, tile_mbf), including
+    widths that are not powers of two and a ragged last block."""
+    wl = _wl(12, 24, 30, 500.0)
+    mdl = Model(wl)
+    X = random_state(321, mdl.nf, wl.Nr, mdl.M, mdl.K)
+    outs = []
+    for mb, lb, mbf in [(0, 0, 0), (1, 1, 1), (3, 2, 5), (2, 3, 1), (5, 4, 3), (8, 8, 8)]:
+        run = tc.Run.from_workload(wl)
+        tc.tc_set_option(run.ctx, "tile_mb", mb)
+        tc.tc_set_option(run.ctx, "tile_lb", lb)
+        tc.tc_set_option(run.ctx, "tile_mbf", mbf)
+        info = tc.tc_get_info(run.ctx)
+        if mbf:
+            assert info.tile_mbf == min(mbf, mdl.M + 1)
+        out = dev(np.zeros_like(X))
+        tc.tc_nonlinear(run.ctx, dev(X), out)
+        outs.append(out.cpu().numpy())
+        run.close()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
 def test_fp64_rate_probe(tc):
     """The FP64 FMA rate the roofline quotes: positive, and not above the
     nominal 4 flop/clk/SM of 152 SMs at the 2.07 GHz maximum clock (a probe
