@@ -49,6 +49,26 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *p, double v) 
 template <typename T>
 using V2 = typename V2t<T>::type;
 
+// Zero the entries of ntr padded length-n spectra (stride ld) that the
+// packing leaves unwritten, the dealiasing gap B+1 .. n-B-1, except the part
+// [3n/8, 5n/8) that a dealiased first pass (zmid) never reads.
+template <typename V>
+__device__ __forceinline__ void zero_gap(V *A, int ntr, int ld, int n, int B, bool zmid) {
+  const int lo = B + 1, hi = n - B - 1;
+  if (hi < lo) return;
+  int s0 = hi + 1, s1 = hi + 1;   // skipped part [s0, s1)
+  if (zmid) {   // zmid_ok: 8 B < 3 n, so lo <= 3n/8 and 5n/8 <= hi + 1
+    s0 = 3 * n / 8;
+    s1 = 5 * n / 8;
+  }
+  const int L1 = s0 - lo, L = L1 + (hi + 1 - s1);
+  for (int t = threadIdx.x; t < ntr * L; t += blockDim.x) {
+    const int tr = t / L, u = t - tr * L;
+    const int i = (u < L1) ? lo + u : s1 + (u - L1);
+    A[tr * ld + spad(i)] = V{0, 0};
+  }
+}
+
 // Twiddle table into shared memory: the FP64 table, or for the FP32 kernels
 // its FP32 copy (no conversion on the FP64 unit).
 template <typename T>
@@ -127,7 +147,7 @@ __global__ void k_zinv(const V2<T> *__restrict__ X, V2<T> *__restrict__ Vout, NL
   V2<T> *B = A + 3 * p.MB * Np;
   V2<T> *tw = B + 3 * p.MB * Np;
   load_tw<T>(tw, p.twz, p.twz32, Nz);
-  for (int i = threadIdx.x; i < 3 * nm * Np; i += blockDim.x) A[i] = V2<T>{0, 0};
+  zero_gap(A, 3 * nm, Np, Nz, s.K, zmid_ok(p.pz, s.K));
   __syncthreads();
   const int st = p.rad.s0[r];
   T d1[kStencil];
@@ -191,7 +211,7 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
   using CflBits = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned>::type;
   __shared__ CflBits cfl_cta[3];   // CTA maxima of |u_r|, |u_theta|, |u_z| (bit patterns)
   load_tw<T>(tw, p.twt, p.twt32, Nt);
-  for (int i = threadIdx.x; i < nl * npair * Ntp; i += blockDim.x) A[i] = V2<T>{0, 0};
+  zero_gap(A, nl * npair, Ntp, Nt, s.M, zmid_ok(p.pt, s.M));
   if (threadIdx.x < 3) cfl_cta[threadIdx.x] = 0;
   __syncthreads();
   // pack: buffer (li, c, 0) = value + i dtheta, (li, c, 1) = d/dr + i d/dz
