@@ -397,20 +397,17 @@ __device__ V *fft_batch_fixed(V *a, V *b, const FFTPlan &pl, int batch, int bstr
 // same size); tw: the plan's pass-major twiddle table (fill_plan_twiddles).  Returns the buffer holding the result.  All threads of the CTA
 // must call it; it ends with a __syncthreads().  zmid: the caller guarantees
 // that every input vanishes on [3N/8, 5N/8) and the plan starts with radix 8
-// (see zmid_ok); the first pass then skips those inputs.  FIXED: lengths
-// 64..512 take the compile-time passes above (a kernel that does not gain
-// from them, measured, passes false and keeps only the generic passes).
-template <int S, bool FIXED = true, typename V>
+// (see zmid_ok); the first pass then skips those inputs.  Lengths 64..512
+// take the compile-time passes above.
+template <int S, typename V>
 __device__ V *fft_batch(V *a, V *b, const FFTPlan &pl, int batch, int bstride,
                         const V *__restrict__ tw, bool zmid = false) {
-  if constexpr (FIXED) {
-    switch (pl.n) {
-      case 64: return fft_batch_fixed<S, 64>(a, b, pl, batch, bstride, tw, zmid);
-      case 128: return fft_batch_fixed<S, 128>(a, b, pl, batch, bstride, tw, zmid);
-      case 256: return fft_batch_fixed<S, 256>(a, b, pl, batch, bstride, tw, zmid);
-      case 512: return fft_batch_fixed<S, 512>(a, b, pl, batch, bstride, tw, zmid);
-      default: break;
-    }
+  switch (pl.n) {
+    case 64: return fft_batch_fixed<S, 64>(a, b, pl, batch, bstride, tw, zmid);
+    case 128: return fft_batch_fixed<S, 128>(a, b, pl, batch, bstride, tw, zmid);
+    case 256: return fft_batch_fixed<S, 256>(a, b, pl, batch, bstride, tw, zmid);
+    case 512: return fft_batch_fixed<S, 512>(a, b, pl, batch, bstride, tw, zmid);
+    default: break;
   }
   int Ns = 1;
   for (int p = 0; p < pl.npass; ++p) {

@@ -179,8 +179,7 @@ __global__ void k_zinv(const V2<T> *__restrict__ X, V2<T> *__restrict__ Vout, NL
     A[(3 * mi + 2) * Np + spad(pos)] = V2<T>{-beta * val.y, beta * val.x};
   }
   __syncthreads();
-  // generic passes: the compile-time ones measured slower in this kernel
-  V2<T> *res = fft_batch<+1, false>(A, B, p.pz, 3 * nm, Np, tw, zmid_ok(p.pz, s.K));
+  V2<T> *res = fft_batch<+1>(A, B, p.pz, 3 * nm, Np, tw, zmid_ok(p.pz, s.K));
   for (int t = threadIdx.x; t < 3 * nm * Nz; t += blockDim.x) {
     const int2 a = divmod(t, nm, fnm);
     const int mi = a.y;
