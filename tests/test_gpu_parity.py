@@ -384,6 +384,24 @@ def test_fp64_rate_probe(tc):
     assert 0.2 < r <= 152 * 2.07e9 * 4 / 1e12
 
 
+def test_zero_and_negative_step_counts(tc):
+    """tc_step with no steps is a no-op that leaves the state bit for bit;
+    a negative count is an argument error that changes nothing."""
+    wl = WORKLOADS["tc_fp64_nr32_n32"].scaled(Nr=12, Ntheta=12, Nz=12, mp=2, kp=2)
+    run = tc.Run.from_workload(wl)
+    run.init_perturbation(psi_coefficients(wl.seed, wl.mp, wl.kp), wl.amp)
+    before = run.get_state()
+    assert len(run.step(0, wl.dt)) == 0
+    assert np.array_equal(run.get_state(), before)
+    with pytest.raises(tc.TCError) as e:
+        run.step(-1, wl.dt)
+    assert e.value.name == "TC_ERR_ARG"
+    assert np.array_equal(run.get_state(), before)
+    run.step(1, wl.dt)                      # the context is still usable
+    assert not np.array_equal(run.get_state(), before)
+    run.close()
+
+
 def test_create_size_limits(tc):
     """The azimuthal size limit that the shared-memory transforms impose."""
     st = {v: k for k, v in tc.STATUS.items()}
@@ -407,6 +425,7 @@ def test_create_size_limits(tc):
                                          (9, 512, 16, 0.0),       # plan 8 x 8 x 8 in theta
                                          (9, 256, 16, 300.0),     # plan 8 x 8 x 4 in theta
                                          (10, 16, 256, 0.0),      # plan 8 x 8 x 4 in z
+                                         (9, 8, 1024, 300.0),     # largest axial size
                                          (9, 4, 4, 300.0)])       # smallest: M = K = 1
 def test_nonlinear_extreme_sizes(tc, Nr, Nt, Nz, Ra):
     wl = _wl(Nr, Nt, Nz, Ra)
