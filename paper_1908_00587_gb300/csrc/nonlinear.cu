@@ -1070,13 +1070,27 @@ __global__ void k_drT(const double2 *__restrict__ Gr, double2 *__restrict__ Xb, 
 
 // The adjoint's azimuthal kernel holds 2 nf + 2 sequences per z-row, so it
 // takes the largest z-row tile not above the forward one that fits.
+// Tiles of the adjoint's nonlinear kernels: the largest not above the forward
+// ones (at most 2 m-columns) whose shared memory lets three CTAs share an SM,
+// so that small runs still spread over every SM (the forward tiles are tuned
+// for the forward kernels, whose buffers are smaller).
+static const size_t kAdjSmemPerCta = (size_t)74 * 1024;
+static size_t adj_theta_smem(const Sizes &s, int lb) {
+  return (size_t)(2 * lb * (2 * s.nf + 2) * padlen(s.Nt) + s.Nt) * sizeof(double2);
+}
+static size_t adj_z_smem(const Sizes &s, int mb) {   // the larger of k_zinv_adj, k_zfwd_adj, k_zinv
+  const int w = s.nf > 3 ? s.nf : 3;
+  return (size_t)(2 * w * mb * padlen(s.Nz) + s.Nz) * sizeof(double2);
+}
 static int adjoint_lb(const tc_ctx *c) {
-  const Sizes &s = c->sz;
   int lb = c->nl.LB;
-  while (lb > 1 && (size_t)(2 * lb * (2 * s.nf + 2) * padlen(s.Nt) + s.Nt) * sizeof(double2) >
-                       (size_t)227 * 1024)
-    --lb;
+  while (lb > 1 && adj_theta_smem(c->sz, lb) > kAdjSmemPerCta) --lb;
   return lb;
+}
+static int adjoint_mb(const tc_ctx *c) {
+  int mb = c->nl.MB < 2 ? c->nl.MB : 2;
+  while (mb > 1 && adj_z_smem(c->sz, mb) > kAdjSmemPerCta) --mb;
+  return mb;
 }
 
 void setup_nonlinear_adjoint(tc_ctx *c) {
@@ -1091,16 +1105,19 @@ void launch_nonlinear_adjoint(tc_ctx *c, const double2 *X, const double2 *Nb, do
   const Sizes &s = c->sz;
   NLParams p = c->nl;
   p.LB = adjoint_lb(c);
+  p.MB = adjoint_mb(c);
+  set_divisors(p);
   p.phys_in = phys_in;
   const size_t e = sizeof(double2);
   c->smem_adj_zinv = (size_t)(2 * s.nf * p.MB * padlen(s.Nz) + s.Nz) * e;
-  c->smem_adj_theta = (size_t)(2 * p.LB * (2 * s.nf + 2) * padlen(s.Nt) + s.Nt) * e;
+  c->smem_adj_theta = adj_theta_smem(s, p.LB);
   c->smem_adj_zfwd = (size_t)(2 * 3 * p.MB * padlen(s.Nz) + s.Nz) * e;
+  const size_t smem_zinv = (size_t)(2 * 3 * p.MB * padlen(s.Nz) + s.Nz) * e;
   const int nmb = (s.NM + p.MB - 1) / p.MB;
   const int nlb = (s.Nz + p.LB - 1) / p.LB;
   if (!phys_in) {   // the forward fields of X, unless stored by the forward pass
     LaunchScope ls(c, KZINV);
-    k_zinv<double><<<dim3(nmb, s.Nr, s.nf), 256, c->smem_zinv, c->stream>>>(X, c->V, p);
+    k_zinv<double><<<dim3(nmb, s.Nr, s.nf), 256, smem_zinv, c->stream>>>(X, c->V, p);
   }
   {
     LaunchScope ls(c, KZINV);
