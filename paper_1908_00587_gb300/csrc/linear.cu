@@ -1027,7 +1027,7 @@ __global__ void k_stT_correct(const double2 *__restrict__ Lb, double *__restrict
 // reduced in shared memory, and one lane per mode forms the wall
 // divergence cotangents and scatters them back through the transposed stencil
 // (sequentially per mode: with Nr < 18 the two walls' stencils overlap).
-constexpr int kAlW = 32, kAlR = 8;
+constexpr int kAlW = 8, kAlR = 32;   // 8 modes x 32 row groups: small runs still fill the SMs
 __global__ void __launch_bounds__(kAlW * kAlR) k_stT_alpha(double *__restrict__ U, LinParams p) {
   const Sizes &s = p.sz;
   __shared__ double red[kAlR][4][kAlW];
