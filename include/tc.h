@@ -309,7 +309,11 @@ tc_status tc_reset_timing(tc_ctx *ctx);
  * every SM, for about target_ms milliseconds (0 < target_ms <= 10000) on
  * `stream` (NULL: default stream), after one untimed launch that also lets
  * the clock settle, and writes the rate in TFLOP/s to *tflops (host).
- * Allocates and frees a small device buffer; synchronises the stream. */
+ * Allocates and frees a small device buffer (SMs x 1024 doubles) and
+ * synchronises the stream.  Errors: TC_ERR_ARG for a null tflops or a
+ * target_ms out of range (checked before any device call), TC_ERR_OOM if the
+ * buffer cannot be allocated, TC_ERR_CUDA for any other CUDA failure (the
+ * calling thread's CUDA error state is cleared; no context is involved). */
 tc_status tc_measure_fp64_rate(double target_ms, void *stream, double *tflops);
 
 /* Nonlinear terms without any device allocation.  The paper has no
