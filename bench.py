@@ -339,19 +339,24 @@ def run_gb300(args):
 
     # end to end through the public API with host buffers: state in from pinned
     # host memory, one step, state out to pinned host memory (--e2e-steps 0
-    # skips it, for states too large to pin on the host)
+    # skips it, for states too large to pin on the host).  Each step is a
+    # restart from host memory: the state and its clock go back in, so the
+    # dynamic step continues the run as it would on the device
     e2e = None
     ne = min(args.e2e_steps, args.steps)
     if ne > 0:
         host = torch.empty(run.shape, dtype=torch.complex128, pin_memory=True).numpy()
         run.get_state(host)
+        t_sim, dt_prev = run.get_clock()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(ne):
             run.set_state(host)
-            run.step(1, wl.dt)
+            run.set_clock(t_sim, dt_prev)
+            dt_prev = float(run.step(1, wl.dt)[-1])
+            t_sim += dt_prev
             run.get_state(host)
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")

@@ -222,6 +222,22 @@ tc_status tc_init_perturbation(tc_ctx *ctx, const double *psi, int mp, int kp,
  * Errors: TC_ERR_ARG, TC_ERR_NONFINITE, TC_ERR_CFL, TC_ERR_CUDA. */
 tc_status tc_step(tc_ctx *ctx, int nsteps, double dt, double *dt_used);
 
+/* Clock of the run: the simulated time t of the current state and dt_prev,
+ * the step that the next dynamic step is compared with (Sec. 2.1, dynamic
+ * time-step control).  dt_prev is 0 after tc_create, tc_set_state,
+ * tc_set_state_regrid and tc_init_perturbation (the next dynamic step is
+ * then dt* itself), and the last step taken after tc_step.  A restart that
+ * puts a saved state back with tc_set_state and then its saved clock with
+ * tc_set_clock continues that run: the next dynamic step keeps dt_prev under
+ * the rule of tc_step, and the Helmholtz factors are reused when that step is
+ * the one they were last built for.  tc_get_clock synchronises the context's
+ * stream and reads dt_prev from the device (8 bytes); either output pointer
+ * (host) may be NULL.  tc_set_clock enqueues the dt_prev write on the
+ * context's stream.  Errors: TC_ERR_ARG for a NULL context, a non-finite t or
+ * dt_prev, or dt_prev < 0; TC_ERR_CUDA. */
+tc_status tc_get_clock(const tc_ctx *ctx, double *t, double *dt_prev);
+tc_status tc_set_clock(tc_ctx *ctx, double t, double dt_prev);
+
 /* Diagnostics of the current state (one small device->host copy). */
 tc_status tc_diagnostics(tc_ctx *ctx, tc_diag *out);
 

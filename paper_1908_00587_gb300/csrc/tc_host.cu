@@ -1074,6 +1074,38 @@ tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
   return TC_OK;
 }
 
+tc_status tc_get_clock(const tc_ctx *c, double *t, double *dt_prev) {
+  if (!c) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  if (dt_prev) {
+    // the device value: tc_stage_solve and the adjoint entry points also run
+    // the step policy
+    double v = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&v, &c->scal->dt_prev, sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail_cuda(const_cast<tc_ctx *>(c), e);
+    *dt_prev = v;
+  }
+  if (t) *t = c->t;
+  return TC_OK;
+}
+
+tc_status tc_set_clock(tc_ctx *c, double t, double dt_prev) {
+  if (!c || !std::isfinite(t) || !std::isfinite(dt_prev) || dt_prev < 0.0) return TC_ERR_ARG;
+  if (c->poisoned) return TC_ERR_CUDA;
+  try {
+    // a pageable source: the copy is staged before the call returns
+    ck(cudaMemcpyAsync(&c->scal->dt_prev, &dt_prev, sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+  } catch (const CudaError &e) {
+    return fail_cuda(c, e.e);
+  }
+  c->t = t;
+  c->dt_last = dt_prev;
+  return TC_OK;
+}
+
 tc_status tc_nonlinear(tc_ctx *c, const void *state_dev, void *n_dev, double *cfl_rate) {
   if (!c || !state_dev || !n_dev) return TC_ERR_ARG;
   if (c->poisoned) return TC_ERR_CUDA;

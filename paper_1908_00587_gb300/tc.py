@@ -76,6 +76,8 @@ _SIGS = {
     "tc_get_pressure": [_P, _P, _I],
     "tc_init_perturbation": [_P, _P, _I, _I, _D, _P, _D],
     "tc_step": [_P, _I, _D, _P],
+    "tc_get_clock": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "tc_set_clock": [_P, _D, _D],
     "tc_diagnostics": [_P, ctypes.POINTER(tc_diag)],
     "tc_nonlinear": [_P, _P, _P, _P],
     "tc_stage_solve": [_P, _P, _D, _P, _P],
@@ -195,6 +197,18 @@ def tc_step(ctx, nsteps: int, dt: float):
     used = np.zeros(max(nsteps, 1), dtype=np.float64)
     _check(_lib.tc_step(ctx, int(nsteps), float(dt), used.ctypes.data), "tc_step")
     return used[:nsteps]
+
+
+def tc_get_clock(ctx):
+    """(t, dt_prev): simulated time and the step the next dynamic step is
+    compared with."""
+    t, dtp = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib.tc_get_clock(ctx, ctypes.byref(t), ctypes.byref(dtp)), "tc_get_clock")
+    return t.value, dtp.value
+
+
+def tc_set_clock(ctx, t: float, dt_prev: float):
+    _check(_lib.tc_set_clock(ctx, float(t), float(dt_prev)), "tc_set_clock")
 
 
 def tc_diagnostics(ctx) -> dict:
@@ -405,6 +419,12 @@ class Run:
 
     def step(self, nsteps, dt):
         return tc_step(self.ctx, nsteps, dt)
+
+    def get_clock(self):
+        return tc_get_clock(self.ctx)
+
+    def set_clock(self, t, dt_prev):
+        tc_set_clock(self.ctx, t, dt_prev)
 
     def diagnostics(self):
         return tc_diagnostics(self.ctx)

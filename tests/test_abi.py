@@ -60,6 +60,10 @@ def test_null_handles(tc):
     assert lib.tc_step(None, 1, 1e-3, None) == 1
     lib.tc_diagnostics.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     assert lib.tc_diagnostics(None, None) == 1
+    lib.tc_get_clock.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.tc_get_clock(None, None, None) == 1
+    lib.tc_set_clock.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+    assert lib.tc_set_clock(None, 0.0, 1e-4) == 1
 
 
 def test_status_strings(tc):
