@@ -69,3 +69,24 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
         gpus = 2
 
     assert bench.run_reference(Args()) == 0
+
+
+def test_reference_arm_line_on_rank0(monkeypatch, capsys):
+    """Rank 0 times the oracle after the requested warm-up steps and prints
+    one JSON line with the reference arm's keys."""
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+
+    class Args:
+        workload = "tc_fp64_nr32_n32"
+        steps = 2
+        warmup = 1
+        gpus = 1
+
+    assert bench.run_reference(Args()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["warmup"] == 1 and line["steps"] == 2
+    assert line["value"] > 0 and line["e2e"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert "after 1 untimed steps" in line["cpu_baseline"]["sample"]
