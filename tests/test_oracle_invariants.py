@@ -138,8 +138,9 @@ def test_energy_budget():
         assert abs(dEdt - rhs[n]) < 1e-5 * mdl.diagnostics(mdl.base)["eps"]
 
 
-def test_taylor_onset_eigenvalue():
-    gold = _golden("taylor_onset_eta05.txt")
+@pytest.mark.parametrize("fixture", ["taylor_onset_eta05.txt", "taylor_onset_eta0875.txt"])
+def test_taylor_onset_eigenvalue(fixture):
+    gold = _golden(fixture)
     beta = gold["beta_c"]
     lo = leading_eigenvalue(32, gold["eta"], gold["Re_stable"], 0.0, 0, beta).real
     hi = leading_eigenvalue(32, gold["eta"], gold["Re_unstable"], 0.0, 0, beta).real
@@ -147,6 +148,11 @@ def test_taylor_onset_eigenvalue():
     rec = critical_reynolds(32, gold["eta"], beta, gold["Re_stable"], gold["Re_unstable"],
                             tol=1e-3)
     assert abs(rec - gold["Re_c"]) < 0.02
+    # beta_c is the minimum of the neutral curve: 0.1 to either side needs a
+    # larger Reynolds number
+    for b in (beta - 0.1, beta + 0.1):
+        assert critical_reynolds(32, gold["eta"], b, gold["Re_stable"], gold["Re_unstable"],
+                                 tol=1e-3) > rec + 0.02
 
 
 def _growth_rate(mdl, dt, t_end=0.8, t_fit=0.2):
