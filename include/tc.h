@@ -230,9 +230,9 @@ tc_status tc_step(tc_ctx *ctx, int nsteps, double dt, double *dt_used);
  * puts a saved state back with tc_set_state and then its saved clock with
  * tc_set_clock continues that run: the next dynamic step keeps dt_prev under
  * the rule of tc_step, and the Helmholtz factors are reused when that step is
- * the one they were last built for.  tc_get_clock synchronises the context's
- * stream and reads dt_prev from the device (8 bytes); either output pointer
- * (host) may be NULL.  tc_set_clock enqueues the dt_prev write on the
+ * the one they were last built for.  Either output pointer of tc_get_clock
+ * (host) may be NULL; for a non-NULL dt_prev it synchronises the context's
+ * stream and reads the value from the device (8 bytes).  tc_set_clock enqueues the dt_prev write on the
  * context's stream.  Errors: TC_ERR_ARG for a NULL context, a non-finite t or
  * dt_prev, or dt_prev < 0; TC_ERR_CUDA. */
 tc_status tc_get_clock(const tc_ctx *ctx, double *t, double *dt_prev);
