@@ -273,7 +273,6 @@ tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt) {
     if (cudaMemcpy(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost) != cudaSuccess)
       return TC_ERR_CUDA;
     c->t += dt[i] * nsteps;
-    c->dt_last = dt[i];
     if (sc.timeout) worst = TC_ERR_TIMEOUT;
     else if (c->check && sc.nonfinite && worst == TC_OK) worst = TC_ERR_NONFINITE;
   }

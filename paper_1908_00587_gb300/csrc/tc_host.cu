@@ -564,7 +564,6 @@ tc_status commit_staged_state(tc_ctx *c) {
     return fail_cuda(c, e.e);
   }
   c->t = 0.0;
-  c->dt_last = 0.0;
   return TC_OK;
 }
 
@@ -1016,7 +1015,6 @@ tc_status tc_init_perturbation(tc_ctx *c, const double *psi, int mp, int kp, dou
     return fail_cuda(c, e.e);
   }
   c->t = 0.0;
-  c->dt_last = 0.0;
   return TC_OK;
 }
 
@@ -1064,7 +1062,6 @@ tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
     ck(cudaStreamSynchronize(c->stream));
     for (int n = 0; n < nsteps; ++n) c->t += hist[n];
     if (dt_used) std::memcpy(dt_used, hist.data(), sizeof(double) * nsteps);
-    c->dt_last = hist[nsteps - 1];
     if (sc.timeout) return TC_ERR_TIMEOUT;
     if (c->check && sc.nonfinite) return TC_ERR_NONFINITE;
     if (c->cfl_limit > 0.0 && sc.rate_last * sc.dt > c->cfl_limit) return TC_ERR_CFL;
@@ -1102,7 +1099,6 @@ tc_status tc_set_clock(tc_ctx *c, double t, double dt_prev) {
     return fail_cuda(c, e.e);
   }
   c->t = t;
-  c->dt_last = dt_prev;
   return TC_OK;
 }
 
@@ -1323,7 +1319,6 @@ tc_status tc_step_record(tc_ctx *c, int nsteps, double dt, void *record_dev,
     ck(cudaMemcpyAsync(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
     ck(cudaStreamSynchronize(c->stream));
     c->t += dt * nsteps;
-    c->dt_last = dt;
     if (sc.timeout) return TC_ERR_TIMEOUT;
     if (c->check && sc.nonfinite) return TC_ERR_NONFINITE;
   } catch (const std::bad_alloc &) {

@@ -179,7 +179,7 @@ struct tc_ctx {
   int selftest_no_copy = 0;   // test hook: sweeps never start their copies
   cudaStream_t stream = nullptr;
   bool poisoned = false;
-  double t = 0.0, dt_last = 0.0;
+  double t = 0.0;
   // host tables
   std::vector<double> r, D1, D2, w, dr_min;
   std::vector<int> s0;
