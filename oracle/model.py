@@ -456,6 +456,36 @@ class Model:
                          1j * beta * pr - g.dr(pz),
                          g.dr(r * pt) / r - 1j * m * pr / r])
 
+    def _perturbation_shapes(self, psi_raw, T_raw=None):
+        """Unscaled u' = curl(psi) (zeroed at the wall nodes) and T' (Sec. 2.1).
+
+        psi = (1 - x^2)^2 x raw coefficients, T' = (1 - x^2) x raw
+        coefficients (None without temperature or raw T draws).
+        """
+        x = self.g.x
+        prof = (1.0 - x * x) ** 2
+        psi = np.stack([self.place(psi_raw[c], prof) for c in range(3)])
+        u = self.curl(psi)
+        u[:, 0] = 0.0
+        u[:, -1] = 0.0
+        t = None
+        if self.has_T and T_raw is not None:
+            t = self.place(T_raw, 1.0 - x * x)
+        return u, t
+
+    def ic_scales(self, psi_raw, T_raw=None):
+        """The constants s_u, s_T that scale curl(psi) to max|u'| = amp and T'
+        to max |T'| = amp_T on the physical grid (Sec. 2.1 initial conditions;
+        s_T = 0 without temperature draws or with amp_T = 0)."""
+        u, t = self._perturbation_shapes(psi_raw, T_raw)
+        ph = [self.sp.to_physical(u[c]) for c in range(3)]
+        mag = np.sqrt(ph[0] ** 2 + ph[1] ** 2 + ph[2] ** 2).max()
+        s_u = self.wl.amp / mag
+        s_T = 0.0
+        if t is not None and self.wl.amp_T > 0:
+            s_T = self.wl.amp_T / np.abs(self.sp.to_physical(t)).max()
+        return s_u, s_T
+
     def initial_state(self, psi_raw, T_raw=None, scales=None):
         """Basic state + u' = curl(psi) scaled to max|u'| = amp (Sec. 2.1).
 
@@ -466,26 +496,15 @@ class Model:
         s_T) applies fixed factors instead (the map is then linear in the
         coefficients, as the gradient of the differentiation form assumes).
         """
-        x = self.g.x
-        prof = (1.0 - x * x) ** 2
-        psi = np.stack([self.place(psi_raw[c], prof) for c in range(3)])
-        u = self.curl(psi)
-        u[:, 0] = 0.0
-        u[:, -1] = 0.0
+        u, t = self._perturbation_shapes(psi_raw, T_raw)
         X = self.base.copy()
         if scales is None:
-            ph = [self.sp.to_physical(u[c]) for c in range(3)]
-            mag = np.sqrt(ph[0] ** 2 + ph[1] ** 2 + ph[2] ** 2).max()
-            X[:3] += (self.wl.amp / mag) * u
-        else:
-            X[:3] += scales[0] * u
-        if self.has_T and T_raw is not None and (self.wl.amp_T > 0 or scales is not None):
-            t = self.place(T_raw, 1.0 - x * x)
-            if scales is None:
-                tmax = np.abs(self.sp.to_physical(t)).max()
-                X[3] += (self.wl.amp_T / tmax) * t
-            else:
-                X[3] += scales[1] * t
+            scales = self.ic_scales(psi_raw, T_raw)
+            if self.wl.amp_T <= 0:
+                t = None
+        X[:3] += scales[0] * u
+        if t is not None:
+            X[3] += scales[1] * t
         return X
 
     # ------------------------------------------------------------ diagnostics
