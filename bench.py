@@ -56,6 +56,8 @@ def parse():
                     help="skip the differentiation-form measurement")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="benchmark the batched form: N uneven runs replayed as one graph")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the mixed-precision and ensemble forms (N = 1 only)")
     return ap.parse_args()
 
 
@@ -340,6 +342,18 @@ def run_gb300(args):
     kt_total_ms = sum(a.elapsed_time(b) for a, b in zip(ks, ke))
     timing = tc.tc_get_timing(run.ctx)
     tc.tc_set_option(run.ctx, "timing", 0)
+    # production form of the same steps: one tc_step call of K steps (the
+    # graph replayed back to back, one host round trip per call; no L2 flush
+    # can sit between the steps of one call, and the 15 MB state fits in L2)
+    ms_a = torch.cuda.Event(enable_timing=True)
+    ms_b = torch.cuda.Event(enable_timing=True)
+    flush.fill_(7)
+    torch.cuda.synchronize()
+    ms_a.record(stream)
+    run.step(args.steps, wl.dt)
+    ms_b.record(stream)
+    torch.cuda.synchronize()
+    multi_ms = ms_a.elapsed_time(ms_b) / args.steps
     total_ms = max_over_ranks(dist, total_ms, "cuda")
     value = replica_throughput(wl.points, args.steps, world, total_ms)
 
@@ -445,6 +459,10 @@ def run_gb300(args):
                                          "rel L2 <= 1.3e-11 vs the FP64 path after 50 steps at "
                                          "256x512x512 (<= 2e-6 of max|N| on a random O(1) state)"
                                          if mixed else "rel L2 <= 1e-10 vs FP64 oracle")}),
+            "multistep": {"value": wl.points / (multi_ms * 1e-3), "unit": METRIC,
+                          "ms_per_step": multi_ms,
+                          "how": f"one tc_step call of {args.steps} steps, CUDA events around "
+                                 "it; L2 flushed once before the call, not between its steps"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "hbm_of_step": hbm,
             "fp64_of_step": fp64,
             "clocks": clk,
@@ -452,6 +470,11 @@ def run_gb300(args):
     run.close()
     if not args.no_adjoint:
         line["adjoint"] = adjoint_throughput(tc, torch, flush)
+    if world == 1 and not args.no_forms:
+        del flush
+        torch.cuda.empty_cache()
+        line["forms"] = {"mixed": forms_mixed(tc, torch),
+                         "ensemble": ensemble_form(tc, torch, 64, 20, 3)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, el, cores, sample = oracle_throughput(wl, budget_s=15.0)
         line["cpu_baseline"] = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
@@ -540,19 +563,100 @@ def adjoint_throughput(tc, torch, flush, steps=200, checkpoint=20, timed_adj=50)
                                      "host-side psi marshalling"}}
 
 
-def run_ensemble(args):
-    """Batched form: N uneven runs (every other one mixed precision), one step
-    of all of them captured into a CUDA graph and replayed, against the same
-    runs stepped one after another with plain launches."""
+def cc_radial_weights(Nr):
+    """Clenshaw-Curtis weights of the Nr Chebyshev-Gauss-Lobatto nodes mapped
+    to a gap of width 1 (the quadrature of the S14 parity norm; a measurement
+    helper, checked against the oracle's weights by the tests)."""
     import numpy as np
-    import torch
+    n = Nr - 1
+    theta = np.pi * np.arange(Nr) / n
+    w = np.zeros(Nr)
+    for j in range(Nr):
+        s = 0.0
+        for k in range(1, n // 2 + 1):
+            b = 1.0 if 2 * k == n else 2.0
+            s += b * np.cos(2 * k * theta[j]) / (4 * k * k - 1)
+        c = 1.0 if j in (0, n) else 2.0
+        w[j] = c / n * (1.0 - s)
+    return 0.5 * w
 
-    import __graft_entry__ as g
-    g.build()
+
+def weighted_rel_l2(a, b, r, w):
+    """Per-field relative L2 of a against b (torch complex tensors of the state
+    layout), weights c_m w_j r_j with c_0 = 1, c_m>0 = 2."""
+    import torch
+    nf, Nr, NM, _ = b.shape
+    wr = torch.as_tensor(w * r, dtype=torch.float64, device=b.device).view(Nr, 1, 1)
+    cm = torch.full((NM,), 2.0, dtype=torch.float64, device=b.device)
+    cm[0] = 1.0
+    wt = wr * cm.view(1, NM, 1)
+    out = []
+    for f in range(nf):
+        num = torch.sum(wt * (a[f] - b[f]).abs() ** 2)
+        den = torch.sum(wt * b[f].abs() ** 2)
+        out.append(float(torch.sqrt(num / den)))
+    return out
+
+
+def forms_mixed(tc, torch, steps=10, total=50):
+    """Mixed precision against FP64 on the same GPU at 256 x 512 x 512 (eta =
+    0.875, Re_i = 1e4, amplitude 0.1, dt = 2e-6): both forms run `total`
+    steps from the same seeded state; `steps` of them (after 3 untimed) are
+    timed with CUDA events on the context's stream (the 717 MB state exceeds
+    L2), and the per-field relative L2 of the mixed state against the FP64
+    state after `total` steps is the mixed form's stated error."""
+    import numpy as np
+    wl = WORKLOADS["tc_mixed_nr256_n512"]
+    psi = psi_coefficients(wl.seed, wl.mp, wl.kp)
+    stream = torch.cuda.current_stream()
+    res, final = {}, {}
+    for prec in (1, 0):
+        w = wl.scaled(precision=prec)
+        run = tc.Run.from_workload(w)
+        run.set_stream(stream.cuda_stream)
+        run.init_perturbation(psi, w.amp)
+        tc.tc_autotune(run.ctx)
+        info = tc.tc_get_info(run.ctx)
+        run.step(3, w.dt)
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        run.step(steps, w.dt)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = ev[0].elapsed_time(ev[1]) / steps
+        run.step(total - 3 - steps, w.dt)
+        X = torch.empty(run.shape, dtype=torch.complex128, device="cuda")
+        tc.tc_get_state(run.ctx, X)
+        final[prec] = X
+        res[prec] = {"value": w.points / (ms * 1e-3), "unit": METRIC, "ms_per_step": ms,
+                     "steps_timed": steps, "clocks": clk,
+                     "tiles_mb_lb_mbf": [info.tile_mb, info.tile_lb, info.tile_mbf]}
+        run.close()
+    g = 0.5 * (1.0 - np.cos(np.pi * np.arange(wl.Nr) / (wl.Nr - 1)))
+    r = wl.eta / (1.0 - wl.eta) + g
+    err = weighted_rel_l2(final[1], final[0], r, cc_radial_weights(wl.Nr))
+    del final
+    torch.cuda.empty_cache()
+    return {"workload": f"{wl.name}: Nr={wl.Nr} Ntheta={wl.Ntheta} Nz={wl.Nz} eta={wl.eta} "
+                        f"Re_i={wl.Re_i} amp={wl.amp} dt={wl.dt}",
+            "mixed": res[1], "fp64": res[0],
+            "speedup_vs_fp64": res[1]["value"] / res[0]["value"],
+            "stated_error": {"rel_l2_vs_fp64_per_field": dict(zip(("u_r", "u_theta", "u_z"), err)),
+                             "after_steps": total,
+                             "norm": "c_m w_j r_j weighted (Clenshaw-Curtis w_j)"}}
+
+
+def ensemble_form(tc, torch, n=64, steps=20, warmup=3):
+    """Batched form: n uneven runs (every other one mixed precision), one step
+    of all of them captured into one CUDA graph and replayed, against the same
+    runs stepped one after another (each replaying its own step graph)."""
+    import numpy as np
     from inputs import ensemble_members
-    from paper_1908_00587_gb300 import tc
-    torch.cuda.set_device(0)
-    members = [w.scaled(precision=i % 2) for i, w in enumerate(ensemble_members(args.ensemble))]
+    members = [w.scaled(precision=i % 2) for i, w in enumerate(ensemble_members(n))]
     t0 = time.perf_counter()
     ens = tc.tc_ensemble_create(members, autotune_tiles=True)
     setup_s = time.perf_counter() - t0
@@ -561,45 +665,63 @@ def run_ensemble(args):
         ctx = tc.tc_ensemble_member(ens, i)
         tc.tc_init_perturbation(ctx, psi_coefficients(wl.seed, wl.mp, wl.kp), wl.amp)
         info = tc.tc_get_info(ctx)
-        X = np.empty((info.nfields, info.Nr, info.M + 1, 2 * info.K + 1), dtype=np.complex128)
+        X = torch.empty((info.nfields, info.Nr, info.M + 1, 2 * info.K + 1),
+                        dtype=torch.complex128, device="cuda")
         tc.tc_get_state(ctx, X)
-        out = torch.zeros(X.shape, dtype=torch.complex128, device="cuda")
-        rate = tc.tc_nonlinear(ctx, torch.from_numpy(X).cuda(), out)
+        out = torch.zeros_like(X)
+        rate = tc.tc_nonlinear(ctx, X, out)
         dts.append(min(1e-3, 0.25 / rate))
     pts = sum(w.points for w in members)
-    tc.tc_ensemble_step(ens, args.warmup, dts)
-    clocks = Clocks(0)
+    tc.tc_ensemble_step(ens, warmup, dts)
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tc.tc_ensemble_step(ens, args.steps, dts)
+    tc.tc_ensemble_step(ens, steps, dts)
     torch.cuda.synchronize()
     graph_s = time.perf_counter() - t0
     clk = clocks.stop()
     kps = tc.tc_ensemble_kernels_per_step(ens)
-    # the same members one after another, plain launches (default stream order)
     seq_s = 0.0
     for i, wl in enumerate(members):
         ctx = tc.tc_ensemble_member(ens, i)
         tc.tc_step(ctx, 1, dts[i])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tc.tc_step(ctx, args.steps, dts[i])
+        tc.tc_step(ctx, steps, dts[i])
         seq_s += time.perf_counter() - t0
     tc.tc_ensemble_destroy(ens)
-    value = pts * args.steps / graph_s
-    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * graph_s / args.steps,
+    return {"workload": f"ensemble of {len(members)} uneven runs (Nr in 32/48/64, "
+                        f"N in 32/64/96, eta in 0.5/0.71/0.875, Re_i in [80, 400], "
+                        f"every other member mixed precision), fixed dt per member",
+            "grid_points_total": pts, "steps": steps, "warmup": warmup,
+            "value": pts * steps / graph_s, "unit": METRIC,
+            "ms_per_step": 1e3 * graph_s / steps,
+            "sequential": {"value": pts * steps / seq_s, "ms_per_step": 1e3 * seq_s / steps},
+            "speedup_vs_sequential": seq_s / graph_s,
+            "kernels_per_step": kps, "tile_autotune_s": setup_s,
+            "timing": "wall clock around tc_ensemble_step with a device synchronisation "
+                      "at both ends", "clocks": clk}
+
+
+def run_ensemble(args):
+    """Batched form on its own line (--ensemble N)."""
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_1908_00587_gb300 import tc
+    torch.cuda.set_device(0)
+    f = ensemble_form(tc, torch, args.ensemble, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": f["value"], "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 and f32+f64 members", "data": "synthetic",
-            "config": {"workload": f"ensemble of {len(members)} uneven runs (Nr in 32/48/64, "
-                                   f"N in 32/64/96, eta in 0.5/0.71/0.875, Re_i in [80, 400], "
-                                   f"every other member mixed precision)",
-                       "grid_points_total": pts, "tile_autotune_s": setup_s,
+            "config": {"workload": f["workload"], "grid_points_total": f["grid_points_total"],
+                       "tile_autotune_s": f["tile_autotune_s"],
                        "l2": "working set of all members exceeds L2"},
-            "sequential": {"value": pts * args.steps / seq_s, "ms_per_step": 1e3 * seq_s / args.steps},
-            "speedup_vs_sequential": seq_s / graph_s,
-            "gpu_launches": kps * args.steps, "clocks": clk}
+            "sequential": f["sequential"], "speedup_vs_sequential": f["speedup_vs_sequential"],
+            "gpu_launches": f["kernels_per_step"] * args.steps, "clocks": f["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -151,6 +151,15 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               return TC_ERR_UNSUPPORTED when n_corr != 1, flux_constraint is
  *               on (tc_stage_solve_adjoint, tc_adjoint_step) or eps != 0
  *               (tc_nonlinear_adjoint, tc_adjoint_step).
+ *   "memory_budget"  largest device memory, in bytes, the context may hold
+ *               (0: no limit, the default).  Every allocation made after
+ *               tc_create -- the FP32 state copy of precision 1, the buffers
+ *               of the first adjoint call, a longer step history in tc_step,
+ *               the flux-constraint response, the scratch of
+ *               tc_set_state_regrid -- that would take tc_get_info's
+ *               device_bytes above it returns TC_ERR_OOM instead, with the
+ *               context unchanged and usable.  A failed device allocation
+ *               returns TC_ERR_OOM the same way.
  *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
  *               never start their shared-memory copies, so each of their
  *               bounded waits runs out (about 1 s) and tc_step returns
@@ -348,7 +357,10 @@ tc_status tc_measure_fp64_rate(double target_ms, void *stream, double *tflops);
  * in the 32 MiB (3 nfields + nfields planes of Nr * Nz * (M+1) complex128);
  * larger sizes return TC_ERR_UNSUPPORTED, other invalid sizes TC_ERR_ARG.
  * The first call on a device looks up the array's device address for that
- * device (make it before any stream capture).  All calls share the array and
+ * device (make it before any stream capture); the address is kept for the
+ * life of the process, so do not call this entry point on a device after
+ * cudaDeviceReset of that device.  Each call copies its small radial and
+ * twiddle tables in from a host buffer of its own on `stream`.  All calls share the array and
  * each call overwrites the previous call's contents (the CFL slot is cleared
  * every call), so calls that overlap on the GPU race: serialise them.  Work
  * runs on `stream` (NULL: default stream); *cfl_rate (host, nullable) as in

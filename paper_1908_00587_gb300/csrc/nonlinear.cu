@@ -15,6 +15,8 @@
 //   k_zfwd   per (m-block, r): forward FFT along z, keep |k| <= K, scale.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -630,7 +632,10 @@ constexpr int kNoAllocMaxN = 512;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
-unsigned char *g_scratch_addr[kMaxDevices] = {};   // device address per device
+// device address of the array per device, looked up once per device; atomic
+// so that host threads calling at the same time do not race (they would
+// store the same address)
+std::atomic<unsigned char *> g_scratch_addr[kMaxDevices] = {};
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -721,15 +726,16 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
   // once per device, with that device current: the device address of the array
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TC_ERR_CUDA;
-  if (!g_scratch_addr[dev]) {
+  unsigned char *base = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!base) {
     void *ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
       cudaGetLastError();
       return TC_ERR_CUDA;
     }
-    g_scratch_addr[dev] = static_cast<unsigned char *>(ptr);
+    base = static_cast<unsigned char *>(ptr);
+    g_scratch_addr[dev].store(base, std::memory_order_release);
   }
-  unsigned char *base = g_scratch_addr[dev];
 
   // radial tables and twiddles, staged on the host stack and copied in
   alignas(256) unsigned char host[kTableMaxBytes];

@@ -112,6 +112,8 @@ extern "C" tc_status tc_set_state_regrid(tc_ctx *c, const void *spec, int Nr_src
     if (where == 0 && src_dev) cudaFree(src_dev);
     if (P_dev) cudaFree(P_dev);
   };
+  if (over_budget(c, (where == 0 ? src_bytes : 0) + P.size() * sizeof(double)))
+    return TC_ERR_OOM;
   cudaError_t e = cudaSuccess;
   if (where == 0) {
     e = cudaMalloc(&src_dev, src_bytes);

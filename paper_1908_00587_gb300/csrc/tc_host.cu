@@ -266,6 +266,7 @@ template <typename T>
 T *dalloc(tc_ctx *c, size_t count) {
   void *p = nullptr;
   const size_t bytes = count * sizeof(T);
+  if (over_budget(c, bytes)) throw std::bad_alloc();
   cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -801,9 +802,8 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
     if (v == 1.0 && !c->X32) {
       try {
         c->X32 = dalloc<float2>(c, (size_t)c->sz.nf * c->sz.S);
-      } catch (const CudaError &e) {
-        cudaGetLastError();
-        return e.e == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA;
+      } catch (const std::bad_alloc &) {
+        return TC_ERR_OOM;
       }
     }
     c->precision = (int)v;
@@ -813,8 +813,14 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
   } else if (k == "flux_constraint") {
     if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
     if ((int)v == c->flux) return TC_OK;
+    if (!c->flux_ug) {
+      try {
+        c->flux_ug = dalloc<double>(c, c->sz.Nr);
+      } catch (const std::bad_alloc &) {
+        return TC_ERR_OOM;
+      }
+    }
     try {
-      if (!c->flux_ug) c->flux_ug = dalloc<double>(c, c->sz.Nr);
       c->flux = (int)v;
       c->lin.flux_ug = c->flux ? c->flux_ug : nullptr;
       build_base(c);
@@ -831,6 +837,9 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
     if (!c->has_T || (v != 0.0 && c->precision == 1)) return TC_ERR_UNSUPPORTED;
     c->eps_c = v;
     c->nl.eps_c = v;
+  } else if (k == "memory_budget") {
+    if (v < 0.0 || v != std::floor(v) || v > 9.0e15) return TC_ERR_ARG;
+    c->mem_budget = (size_t)v;
   } else if (k == "selftest_no_copy") {
     c->selftest_no_copy = v != 0.0;
   } else if (k == "timing") {
@@ -1024,12 +1033,19 @@ tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
   if (nsteps == 0) return TC_OK;
   try {
     if (nsteps > c->dt_hist_cap) {
+      const size_t grow = sizeof(double) * (size_t)(nsteps - c->dt_hist_cap);
+      if (over_budget(c, grow)) return TC_ERR_OOM;
       double *h = nullptr;
-      ck(cudaMalloc(&h, sizeof(double) * nsteps));
+      if (cudaMalloc(&h, sizeof(double) * nsteps) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ERR_OOM;
+      }
+      ck(cudaStreamSynchronize(c->stream));   // the old history may still be in use
       cudaFree(c->dt_hist);
       for (auto &p : c->allocs)
         if (p == c->dt_hist) p = h;
       c->dt_hist = h;
+      c->device_bytes += grow;
       c->dt_hist_cap = nsteps;
       ++c->gen;   // the history pointer is a kernel argument
     }
@@ -1184,8 +1200,12 @@ namespace tc {
 namespace {
 
 void ensure_adjoint(tc_ctx *c) {
-  if (c->Va) return;
+  if (c->Phys) return;
   const Sizes &s = c->sz;
+  // all or nothing: the buffers count as present once the last one exists
+  const size_t need = 16 * ((size_t)3 * s.nf * s.Nr * s.Nz * s.NM + (size_t)5 * s.nf * s.S +
+                            (size_t)s.Nr * s.Nz * 2 * s.nf * s.Nt);
+  if (over_budget(c, need)) throw std::bad_alloc();
   c->Va = dalloc<double2>(c, (size_t)3 * s.nf * s.Nr * s.Nz * s.NM);
   c->Gdr = dalloc<double2>(c, (size_t)s.nf * s.S);
   c->Rb = dalloc<double2>(c, (size_t)s.nf * s.S);

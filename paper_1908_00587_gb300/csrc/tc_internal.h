@@ -188,6 +188,9 @@ struct tc_ctx {
   // device memory
   std::vector<void *> allocs;
   size_t device_bytes = 0;
+  // largest device_bytes allowed for allocations made after tc_create
+  // (option "memory_budget"; 0: no limit)
+  size_t mem_budget = 0;
   double2 *X, *Xp, *N0, *N1, *Yb, *U0, *P, *V, *W, *alpha_buf, *base_dev;
   double *Ps;   // particular pressure, split planes [2][S]
   double *d_Lw, *d_Dw;
@@ -273,6 +276,11 @@ inline void allow_smem(F *kernel) {
 }
 
 // tc_host.cu
+// True when `extra` more device bytes would take the context past its
+// memory budget (option "memory_budget").
+inline bool over_budget(const tc_ctx *c, size_t extra) {
+  return c->mem_budget && c->device_bytes + extra > c->mem_budget;
+}
 void enqueue_step(tc_ctx *c, double dt_fixed, int step_index);
 tc_status commit_staged_state(tc_ctx *c);   // Xp -> X after validation
 cudaError_t ensure_step_graph(tc_ctx *c, double dt_fixed);

@@ -129,6 +129,35 @@ def _ptr(a):
     raise TypeError("expected a NumPy array or a CUDA tensor")
 
 
+def _sized(a, n: int, what: str, device_only: bool = False):
+    """(pointer, where) of a complex128 array or tensor holding at least n
+    entries; raises ValueError before any call when it does not, so a short
+    or mistyped buffer never reaches a kernel or a host copy."""
+    p, where = _ptr(a)
+    if device_only and where != 1:
+        raise ValueError(f"{what}: expected a CUDA tensor (device pointer)")
+    dt = a.dtype
+    ok = (dt == np.complex128) if isinstance(a, np.ndarray) else (str(dt) == "torch.complex128")
+    if not ok:
+        raise ValueError(f"{what}: expected complex128, got {dt}")
+    numel = a.size if isinstance(a, np.ndarray) else a.numel()
+    if numel < n:
+        raise ValueError(f"{what}: {numel} entries, {n} needed")
+    return p, where
+
+
+def _state_len(ctx) -> int:
+    i = tc_info()
+    _check(_lib.tc_get_info(ctx, ctypes.byref(i)), "tc_get_info")
+    return int(i.nfields) * int(i.coeffs_per_field)
+
+
+def _plane_len(ctx) -> int:
+    i = tc_info()
+    _check(_lib.tc_get_info(ctx, ctypes.byref(i)), "tc_get_info")
+    return int(i.coeffs_per_field)
+
+
 # -- C names ------------------------------------------------------------------
 def tc_create(Nr, Ntheta, Nz, eta, Lz, Re_i, Re_o=0.0, Ra=0.0, Pr=1.0):
     h = _P()
@@ -156,7 +185,7 @@ def tc_get_info(ctx) -> tc_info:
 
 
 def tc_set_state(ctx, spec):
-    p, where = _ptr(spec)
+    p, where = _sized(spec, _state_len(ctx), "tc_set_state")
     _check(_lib.tc_set_state(ctx, p, where), "tc_set_state")
 
 
@@ -164,20 +193,20 @@ def tc_set_state_regrid(ctx, spec, eta_src, Lz_src):
     """spec: state of another resolution, (nfields, Nr, M+1, 2K+1) complex128
     (numpy array or CUDA tensor); the sizes are read from its shape."""
     nf, Nr, M1, NK = spec.shape
-    p, where = _ptr(spec)
+    p, where = _sized(spec, nf * Nr * M1 * NK, "tc_set_state_regrid")
     _check(_lib.tc_set_state_regrid(ctx, p, int(Nr), int(M1 - 1), int((NK - 1) // 2), int(nf),
                                     float(eta_src), float(Lz_src), where),
            "tc_set_state_regrid")
 
 
 def tc_get_state(ctx, out):
-    p, where = _ptr(out)
+    p, where = _sized(out, _state_len(ctx), "tc_get_state")
     _check(_lib.tc_get_state(ctx, p, where), "tc_get_state")
     return out
 
 
 def tc_get_pressure(ctx, out):
-    p, where = _ptr(out)
+    p, where = _sized(out, _plane_len(ctx), "tc_get_pressure")
     _check(_lib.tc_get_pressure(ctx, p, where), "tc_get_pressure")
     return out
 
@@ -219,15 +248,20 @@ def tc_diagnostics(ctx) -> dict:
 
 def tc_nonlinear(ctx, state_dev, n_dev) -> float:
     rate = ctypes.c_double(0.0)
-    _check(_lib.tc_nonlinear(ctx, _ptr(state_dev)[0], _ptr(n_dev)[0], ctypes.byref(rate)),
+    n = _state_len(ctx)
+    _check(_lib.tc_nonlinear(ctx, _sized(state_dev, n, "tc_nonlinear state", True)[0],
+                             _sized(n_dev, n, "tc_nonlinear out", True)[0], ctypes.byref(rate)),
            "tc_nonlinear")
     return rate.value
 
 
 def tc_stage_solve(ctx, rhs_dev, dt, x_out_dev, p_out_dev=None):
-    pp = _ptr(p_out_dev)[0] if p_out_dev is not None else None
-    _check(_lib.tc_stage_solve(ctx, _ptr(rhs_dev)[0], float(dt), _ptr(x_out_dev)[0], pp),
-           "tc_stage_solve")
+    n = _state_len(ctx)
+    pp = (_sized(p_out_dev, _plane_len(ctx), "tc_stage_solve p_out", True)[0]
+          if p_out_dev is not None else None)
+    _check(_lib.tc_stage_solve(ctx, _sized(rhs_dev, n, "tc_stage_solve rhs", True)[0],
+                               float(dt), _sized(x_out_dev, n, "tc_stage_solve x_out", True)[0],
+                               pp), "tc_stage_solve")
 
 
 def tc_get_timing(ctx) -> dict:
@@ -250,8 +284,12 @@ def tc_nonlinear_noalloc(Nr, Ntheta, Nz, eta, Lz, Ra, Pr, state_dev, n_dev, stre
     and for why overlapping calls must be serialised.  Returns the CFL rate.
     """
     rate = ctypes.c_double(0.0)
+    nf = 4 if Ra != 0.0 else 3
+    n = nf * int(Nr) * ((int(Ntheta) - 1) // 3 + 1) * (2 * ((int(Nz) - 1) // 3) + 1)
     _check(_lib.tc_nonlinear_noalloc(int(Nr), int(Ntheta), int(Nz), float(eta), float(Lz),
-                                     float(Ra), float(Pr), _ptr(state_dev)[0], _ptr(n_dev)[0],
+                                     float(Ra), float(Pr),
+                                     _sized(state_dev, n, "tc_nonlinear_noalloc state", True)[0],
+                                     _sized(n_dev, n, "tc_nonlinear_noalloc out", True)[0],
                                      stream_ptr, ctypes.byref(rate)), "tc_nonlinear_noalloc")
     return rate.value
 
@@ -267,7 +305,9 @@ def tc_measure_fp64_rate(target_ms=250.0, stream_ptr=None):
 
 def tc_adjoint_step(ctx, state_n_dev, dt, adj_dev):
     """adj <- P_H J(state_n)^T adj for one step at fixed dt (in place)."""
-    _check(_lib.tc_adjoint_step(ctx, _ptr(state_n_dev)[0], float(dt), _ptr(adj_dev)[0]),
+    n = _state_len(ctx)
+    _check(_lib.tc_adjoint_step(ctx, _sized(state_n_dev, n, "tc_adjoint_step state", True)[0],
+                                float(dt), _sized(adj_dev, n, "tc_adjoint_step adj", True)[0]),
            "tc_adjoint_step")
 
 
@@ -279,37 +319,51 @@ def tc_record_bytes_per_step(ctx) -> int:
 
 def tc_step_record(ctx, nsteps, dt, record_dev):
     """record_dev: CUDA tensor of at least nsteps * tc_record_bytes_per_step bytes."""
+    if not getattr(record_dev, "is_cuda", False):
+        raise ValueError("tc_step_record: record_dev must be a CUDA tensor")
     nbytes = record_dev.numel() * record_dev.element_size()
     _check(_lib.tc_step_record(ctx, int(nsteps), float(dt), _ptr(record_dev)[0], int(nbytes)),
            "tc_step_record")
 
 
 def tc_adjoint_steps(ctx, nsteps, record_dev, dt, adj_dev):
+    need = int(nsteps) * tc_record_bytes_per_step(ctx)
+    if not getattr(record_dev, "is_cuda", False) or \
+            record_dev.numel() * record_dev.element_size() < need:
+        raise ValueError(f"tc_adjoint_steps: a CUDA tensor of at least {need} bytes needed")
     _check(_lib.tc_adjoint_steps(ctx, int(nsteps), _ptr(record_dev)[0], float(dt),
-                                 _ptr(adj_dev)[0]), "tc_adjoint_steps")
+                                 _sized(adj_dev, _state_len(ctx), "tc_adjoint_steps adj",
+                                        True)[0]), "tc_adjoint_steps")
 
 
 def tc_nonlinear_adjoint(ctx, state_dev, nbar_dev, xbar_dev):
-    _check(_lib.tc_nonlinear_adjoint(ctx, _ptr(state_dev)[0], _ptr(nbar_dev)[0],
-                                     _ptr(xbar_dev)[0]), "tc_nonlinear_adjoint")
+    n = _state_len(ctx)
+    _check(_lib.tc_nonlinear_adjoint(ctx, _sized(state_dev, n, "state", True)[0],
+                                     _sized(nbar_dev, n, "nbar", True)[0],
+                                     _sized(xbar_dev, n, "xbar", True)[0]),
+           "tc_nonlinear_adjoint")
 
 
 def tc_stage_solve_adjoint(ctx, xbar_dev, dt, rbar_dev):
-    _check(_lib.tc_stage_solve_adjoint(ctx, _ptr(xbar_dev)[0], float(dt), _ptr(rbar_dev)[0]),
+    n = _state_len(ctx)
+    _check(_lib.tc_stage_solve_adjoint(ctx, _sized(xbar_dev, n, "xbar", True)[0], float(dt),
+                                       _sized(rbar_dev, n, "rbar", True)[0]),
            "tc_stage_solve_adjoint")
 
 
 def tc_objective(ctx, grad_dev=None) -> float:
     J = ctypes.c_double(0.0)
-    _check(_lib.tc_objective(ctx, ctypes.byref(J),
-                             _ptr(grad_dev)[0] if grad_dev is not None else None), "tc_objective")
+    gp = (_sized(grad_dev, _state_len(ctx), "tc_objective grad", True)[0]
+          if grad_dev is not None else None)
+    _check(_lib.tc_objective(ctx, ctypes.byref(J), gp), "tc_objective")
     return J.value
 
 
 def tc_init_perturbation_adjoint(ctx, lam_dev, mp, kp, with_T=False):
     pb = np.zeros((3, mp + 1, 2 * kp + 1), dtype=np.complex128)
     tb = np.zeros((mp + 1, 2 * kp + 1), dtype=np.complex128) if with_T else None
-    _check(_lib.tc_init_perturbation_adjoint(ctx, _ptr(lam_dev)[0], int(mp), int(kp),
+    lp = _sized(lam_dev, _state_len(ctx), "tc_init_perturbation_adjoint lam", True)[0]
+    _check(_lib.tc_init_perturbation_adjoint(ctx, lp, int(mp), int(kp),
                                              pb.ctypes.data,
                                              tb.ctypes.data if tb is not None else None),
            "tc_init_perturbation_adjoint")

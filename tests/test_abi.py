@@ -83,3 +83,20 @@ def test_fp64_rate_rejects_bad_arguments(tc):
     assert lib.tc_measure_fp64_rate(-5.0, None, ctypes.byref(out)) == 1
     assert lib.tc_measure_fp64_rate(2e4, None, ctypes.byref(out)) == 1
     assert lib.tc_measure_fp64_rate(100.0, None, None) == 1
+
+
+def test_binding_rejects_short_or_host_buffers(tc):
+    """The binding checks dtype, size and device placement of state buffers
+    before any library call, so a short or host buffer never reaches a kernel
+    (these raise before touching the GPU)."""
+    import numpy as np
+    nf, Nr, M1, NK = 3, 16, 4, 7    # Ntheta = Nz = 12: M = K = 3
+    good = np.zeros((nf, Nr, M1, NK), dtype=np.complex128)
+    with pytest.raises(ValueError):            # host arrays are not device pointers
+        tc.tc_nonlinear_noalloc(Nr, 12, 12, 0.5, 1.0, 0.0, 1.0, good, good)
+    with pytest.raises((ValueError, TypeError)):
+        tc._sized(good[:, :8], good.size, "short", False)
+    with pytest.raises(ValueError):
+        tc._sized(good.real.copy(), good.size, "float64", False)
+    p, where = tc._sized(good, good.size, "ok", False)
+    assert where == 0 and p == good.ctypes.data

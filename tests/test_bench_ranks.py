@@ -90,3 +90,34 @@ def test_reference_arm_line_on_rank0(monkeypatch, capsys):
     assert line["value"] > 0 and line["e2e"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert "after 1 untimed steps" in line["cpu_baseline"]["sample"]
+
+
+@pytest.mark.parametrize("Nr", [9, 32, 64, 256])
+def test_bench_norm_weights_match_oracle(Nr):
+    """The bench's stated-error norm uses its own Clenshaw-Curtis weights; they
+    are the oracle's quadrature (the S14 parity norm) to round-off."""
+    import numpy as np
+    import bench
+    from oracle.grid import Grid
+    g = Grid(Nr, 0.875)
+    w = bench.cc_radial_weights(Nr)
+    assert np.abs(w - g.w).max() <= 1e-14
+    assert abs(w.sum() - 1.0) <= 1e-14
+
+
+def test_bench_weighted_norm_matches_oracle_metric():
+    import numpy as np
+    import torch
+    import bench
+    from inputs import Workload, random_state
+    from oracle import Model
+    wl = Workload("n", Nr=12, Ntheta=12, Nz=12, eta=0.6, Lz=1.0, Re_i=10.0)
+    mdl = Model(wl)
+    a = random_state(1, 3, 12, mdl.M, mdl.K)
+    b = random_state(2, 3, 12, mdl.M, mdl.K)
+    w = (mdl.g.w * mdl.g.r)[:, None, None] * mdl.sp.cm[None, :, None]
+    ref = [float(np.sqrt(np.sum(w * np.abs(a[f] - b[f]) ** 2) / np.sum(w * np.abs(b[f]) ** 2)))
+           for f in range(3)]
+    got = bench.weighted_rel_l2(torch.from_numpy(a), torch.from_numpy(b), mdl.g.r,
+                                bench.cc_radial_weights(12))
+    assert np.allclose(got, ref, rtol=1e-13)

@@ -96,16 +96,27 @@ def test_mixed_run_error_vs_oracle(tc):
 
 
 def test_mixed_shrunken_large_workload_vs_oracle(tc):
-    """The 256 x 512^2 mixed workload's parameters at 48 x 64^2, 5 steps."""
+    """The 256 x 512^2 mixed workload's parameters (eta = 0.875, Re_i = 1e4,
+    amplitude 0.1, dt = 2e-6) at 48 x 64^2, 50 steps, against the FP64
+    oracle at the FP64 path's own gate, relative L2 <= 1e-10 per field.
+
+    Why the gate holds for the mixed form: only u'.grad u' of the
+    perturbation goes through FP32; its rounding, about 2^-24 of |N'| per
+    evaluation, enters the state multiplied by dt.  With |N'| ~ |u'|^2 / gap
+    ~ 1e-2 .. 1 here, 50 steps of dt = 2e-6 move the state by at most
+    ~1e-4 |N'| and the FP32 part of that is ~1e-11 of |u'| ~ 0.1."""
     wl = WORKLOADS["tc_mixed_nr256_n512"].scaled(Nr=48, Ntheta=64, Nz=64, mp=8, kp=8)
-    got, psi, _ = _run(tc, wl, 5)
+    got, psi, _ = _run(tc, wl, 50)
     mdl = Model(wl, "fft")
-    X, _ = mdl.run(mdl.initial_state(psi), 5, wl.dt)
-    err = rel_l2(mdl, got, X)
+    X, _ = mdl.run(mdl.initial_state(psi), 50, wl.dt)
+    w = (mdl.g.w * mdl.g.r)[:, None, None] * mdl.sp.cm[None, :, None]
+    per_field = [float(np.sqrt(np.sum(w * np.abs(got[f] - X[f]) ** 2) / np.sum(w * np.abs(X[f]) ** 2)))
+                 for f in range(got.shape[0])]
     pert = rel_l2(mdl, got - mdl.base, X - mdl.base)
-    print(f"mixed eta=0.875 Re=1e4 48x64x64 5 steps: rel L2 {err:.3e}, perturbation {pert:.3e}")
-    assert err < 1e-9
-    assert pert < 1e-4
+    print(f"mixed eta=0.875 Re=1e4 48x64x64 50 steps: rel L2 per field {per_field}, "
+          f"perturbation {pert:.3e}")
+    assert max(per_field) <= 1e-10, per_field
+    assert pert < 1e-6
 
 
 def test_mixed_vs_fp64_full_size(tc):

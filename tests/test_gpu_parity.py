@@ -282,6 +282,43 @@ def test_bench_workload_parity(tc):
     assert rel_l2(mdl, got - mdl.base, ref - mdl.base) <= 1e-6
 
 
+# Whole runs of the configured workloads at their own sizes, element by
+# element against the oracle in the weighted relative L2 of each field
+# (c_m w_j r_j weights), gate 1e-10:
+#   64 x 128 x 128 with temperature and the dynamic CFL step, 200 steps (the
+#     two step sequences compared separately to 1e-8);
+#   64^3, eta = 0.5, Re_i = 120, dt = 2e-4, 100 steps (the forward run of the
+#     differentiation workload);
+#   the 256 x 512^2 mixed workload's physics (eta = 0.875, Re_i = 1e4,
+#     amplitude 0.1, modes up to 16, dt = 2e-6) shrunk to 64 x 128^2 and run
+#     in FP64 for 50 steps.
+FULL_RUNS = [
+    ("tc_fp64T_nr64_n128", {}, 200),
+    ("tc_adjoint_nr64_n64", {}, 100),
+    ("tc_mixed_nr256_n512", dict(Nr=64, Ntheta=128, Nz=128, precision=0), 50),
+]
+
+
+@pytest.mark.parametrize("name,shrink,nsteps", FULL_RUNS,
+                         ids=["fp64T_64x128x128_200", "adjoint_fwd_64cubed_100",
+                              "eta0875_Re1e4_64x128x128_fp64_50"])
+def test_workload_full_run_parity(tc, name, shrink, nsteps):
+    wl = WORKLOADS[name].scaled(**shrink)
+    mdl, got, ref, dts, rdts, dg, dr, _, _ = _run_both(tc, wl, nsteps, "fft")
+    per_field = []
+    w = (mdl.g.w * mdl.g.r)[:, None, None] * mdl.sp.cm[None, :, None]
+    for f in range(got.shape[0]):
+        per_field.append(float(np.sqrt(np.sum(w * np.abs(got[f] - ref[f]) ** 2)
+                                       / np.sum(w * np.abs(ref[f]) ** 2))))
+    pert = rel_l2(mdl, got - mdl.base, ref - mdl.base)
+    print(f"{name} {shrink} {nsteps} steps: rel L2 per field {per_field}, "
+          f"perturbation {pert:.2e}, dt range {rdts.min():.4e}..{rdts.max():.4e}")
+    assert np.all(np.abs(dts - rdts) <= 1e-8 * rdts)
+    assert max(per_field) <= 1e-10, per_field
+    for k in ("E", "E_pert", "eps", "P_wall"):
+        assert abs(dg[k] - dr[k]) <= 1e-9 * abs(dr[k]) + 1e-300, (k, dg[k], dr[k])
+
+
 def test_set_state_validation(tc):
     wl = WORKLOADS["tc_fp64_nr32_n32"]
     run = tc.Run.from_workload(wl)
