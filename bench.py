@@ -214,9 +214,18 @@ def step_flops(wl):
     nf = 4 if wl.Ra else 3
     M, K = (wl.Ntheta - 1) // 3, (wl.Nz - 1) // 3
     S = wl.Nr * (M + 1) * (2 * K + 1)
+    nonlinear, linear = stage_flops(wl)
+    return 2 * (nonlinear + linear)
+
+
+def stage_flops(wl):
+    """(nonlinear, linear) algorithmic flops of one stage (see step_flops)."""
+    nf = 4 if wl.Ra else 3
+    M, K = (wl.Ntheta - 1) // 3, (wl.Nz - 1) // 3
+    S = wl.Nr * (M + 1) * (2 * K + 1)
     nonlinear = sum(kernel_flops(k, wl) for k in ("k_theta", "k_zinv", "k_zfwd"))
     linear = nf * 9 * 4 * S / 2 + (2 * 9 * 4 + (2 * nf + 2) * 2 * 10 + 50) * S
-    return 2 * (nonlinear + linear)
+    return nonlinear, linear
 
 
 def source_hash(names):
@@ -691,6 +700,27 @@ def ensemble_form(tc, torch, n=64, steps=20, warmup=3):
         tc.tc_step(ctx, steps, dts[i])
         seq_s += time.perf_counter() - t0
     tc.tc_ensemble_destroy(ens)
+    # how much of the FP64 unit one ensemble step keeps busy: the FP64
+    # members' whole steps and the mixed members' FP64 linear stages
+    fp64_flops = 0.0
+    fp32_flops = 0.0
+    for wl in members:
+        nl, lin = stage_flops(wl)
+        if wl.precision:
+            fp64_flops += 2 * lin
+            fp32_flops += 2 * nl
+        else:
+            fp64_flops += 2 * (nl + lin)
+    step_s = graph_s / steps
+    try:
+        fp64_peak = tc.tc_measure_fp64_rate(250.0, torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        fp64_peak = FP64_PEAK_TFLOPS
+    fp64_use = {"fp64_flops_per_step": fp64_flops, "fp32_flops_per_step": fp32_flops,
+                "achieved_fp64_tflops": fp64_flops / step_s / 1e12,
+                "fp64_peak_tflops": fp64_peak,
+                "frac": fp64_flops / step_s / 1e12 / fp64_peak,
+                "peak_source": "tc_measure_fp64_rate (measured FP64 FMA rate of this GPU)"}
     return {"workload": f"ensemble of {len(members)} uneven runs (Nr in 32/48/64, "
                         f"N in 32/64/96, eta in 0.5/0.71/0.875, Re_i in [80, 400], "
                         f"every other member mixed precision), fixed dt per member",
@@ -700,6 +730,7 @@ def ensemble_form(tc, torch, n=64, steps=20, warmup=3):
             "sequential": {"value": pts * steps / seq_s, "ms_per_step": 1e3 * seq_s / steps},
             "speedup_vs_sequential": seq_s / graph_s,
             "kernels_per_step": kps, "tile_autotune_s": setup_s,
+            "fp64_of_step": fp64_use,
             "timing": "wall clock around tc_ensemble_step with a device synchronisation "
                       "at both ends", "clocks": clk}
 

@@ -411,6 +411,19 @@ tc_status tc_ensemble_kernels_per_step(const tc_ens *e, long long *count);
 /* Free the members, streams and graph.  Accepts NULL. */
 tc_status tc_ensemble_destroy(tc_ens *e);
 
+/* Index checks of the debug build (libtc_debug.so, compiled with
+ * -DTC_DEBUG; the paper's quality assurance runs short tests with runtime
+ * checks and the compilers' tightest debug settings, Sec. 2.5).  In that build the step kernels check the indices
+ * of their global and shared-memory accesses (state, nonlinear intermediates,
+ * transform buffers, right-hand sides, radial sweeps and their factor copies,
+ * influence data); an index out of range sets one bit per check site in a
+ * device word and the access is skipped -- nothing traps.  *flags (host)
+ * receives the bits set since the last clear (0: every index was in range);
+ * clear != 0 resets them.  Synchronises the device.  Errors: TC_ERR_ARG for a
+ * NULL flags, TC_ERR_UNSUPPORTED in the normal build (libtc.so, where the
+ * checks compile away), TC_ERR_CUDA. */
+tc_status tc_debug_flags(unsigned *flags, int clear);
+
 /* Human-readable name of a status. */
 const char *tc_status_string(tc_status s);
 

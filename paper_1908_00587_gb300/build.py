@@ -18,6 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtc.so")
+# the same sources with -DTC_DEBUG: index checks that record, never trap
+LIB_DEBUG = os.path.join(PKG, "libtc_debug.so")
 
 SOURCES = ["tc_host.cu", "nonlinear.cu", "linear.cu", "diag.cu", "ensemble.cu", "restart.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,18 +41,22 @@ def _newer(target: str, deps) -> bool:
     return all(os.path.getmtime(d) <= t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, extra: tuple = ()) -> str:
+def build(verbose: bool = False, force: bool = False, extra: tuple = (),
+          debug: bool = True) -> str:
+    """Compile libtc.so and (debug=True) libtc_debug.so; returns libtc.so's path."""
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "tc.h"))
     cc = nvcc()
+    variants = [("", LIB, ())] + ([("_debug", LIB_DEBUG, ("-DTC_DEBUG",))] if debug else [])
 
-    def compile_one(src):
+    def compile_one(job):
+        src, suffix, defs = job
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, src.replace(".cu", suffix + ".o"))
         if not force and _newer(o, [s] + headers):
             return o
-        cmd = [cc, "-c", s, "-o", o] + ARCH + FLAGS + list(extra)
+        cmd = [cc, "-c", s, "-o", o] + ARCH + FLAGS + list(defs) + list(extra)
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         res = subprocess.run(cmd, capture_output=True, text=True)
@@ -60,13 +66,16 @@ def build(verbose: bool = False, force: bool = False, extra: tuple = ()) -> str:
             print(res.stderr, file=sys.stderr)
         return o
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    if force or not _newer(LIB, objs):
-        cmd = [cc, "-shared", "-o", LIB] + objs + ARCH
-        res = subprocess.run(cmd, capture_output=True, text=True)
-        if res.returncode != 0:
-            raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
+    jobs = [(src, suffix, defs) for suffix, _, defs in variants for src in SOURCES]
+    with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for k, (suffix, lib, _) in enumerate(variants):
+        vobjs = objs[k * len(SOURCES):(k + 1) * len(SOURCES)]
+        if force or not _newer(lib, vobjs):
+            cmd = [cc, "-shared", "-o", lib] + vobjs + ARCH
+            res = subprocess.run(cmd, capture_output=True, text=True)
+            if res.returncode != 0:
+                raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
     return LIB
 
 

@@ -260,14 +260,17 @@ __device__ __forceinline__ void butterfly(const V *__restrict__ s, V *__restrict
                                           const V *__restrict__ twp) {
   const int k = j - fdiv(j, dns) * Ns;
   V v[R];
+  const int npad = padlen(nb * R);
 #pragma unroll
   for (int q = 0; q < R; ++q)
-    if (!ZMID || (q != 3 && q != 4)) v[q] = s[spad(j + q * nb)];
+    if (!ZMID || (q != 3 && q != 4))
+      v[q] = dbg_in(spad(j + q * nb), npad, DBG_FFT_SMEM) ? s[spad(j + q * nb)] : V{0, 0};
   if (ZMID) {
     if constexpr (R == 8) dft8_zmid<S>(v);
     const int base = j * R;   // Ns = 1
 #pragma unroll
-    for (int p = 0; p < R; ++p) d[spad(base + p)] = v[p];
+    for (int p = 0; p < R; ++p)
+      if (dbg_in(spad(base + p), npad, DBG_FFT_SMEM)) d[spad(base + p)] = v[p];
     return;
   }
   using T = decltype(v[0].x);
@@ -299,7 +302,8 @@ __device__ __forceinline__ void butterfly(const V *__restrict__ s, V *__restrict
   }
   const int base = (j - k) * R + k;
 #pragma unroll
-  for (int p = 0; p < R; ++p) d[spad(base + p * Ns)] = v[p];
+  for (int p = 0; p < R; ++p)
+    if (dbg_in(spad(base + p * Ns), npad, DBG_FFT_SMEM)) d[spad(base + p * Ns)] = v[p];
 }
 
 template <int R, int S, bool ZMID, typename V>
@@ -340,7 +344,8 @@ __device__ __forceinline__ void stockham_pass_fixed(const V *__restrict__ src, V
     V v[R];
 #pragma unroll
     for (int q = 0; q < R; ++q)
-      if (!ZMID || (q != 3 && q != 4)) v[q] = s[sj + q * in_step];
+      if (!ZMID || (q != 3 && q != 4))
+        v[q] = dbg_in(sj + q * in_step, padlen(N), DBG_FFT_SMEM) ? s[sj + q * in_step] : V{0, 0};
     if constexpr (ZMID) {
       dft8_zmid<S>(v);
     } else if constexpr (NS == 1) {
@@ -360,15 +365,18 @@ __device__ __forceinline__ void stockham_pass_fixed(const V *__restrict__ src, V
     if constexpr (NS % 8 == 0) {
       const int sb = spad(base);
 #pragma unroll
-      for (int p = 0; p < R; ++p) d[sb + p * (NS + NS / 8)] = v[p];
+      for (int p = 0; p < R; ++p)
+        if (dbg_in(sb + p * (NS + NS / 8), padlen(N), DBG_FFT_SMEM)) d[sb + p * (NS + NS / 8)] = v[p];
     } else if constexpr (NS == 1) {
       // base = j R and R <= 8: the R outputs share base / 8
       const int sb = base + j * R / 8;
 #pragma unroll
-      for (int p = 0; p < R; ++p) d[sb + p] = v[p];
+      for (int p = 0; p < R; ++p)
+        if (dbg_in(sb + p, padlen(N), DBG_FFT_SMEM)) d[sb + p] = v[p];
     } else {
 #pragma unroll
-      for (int p = 0; p < R; ++p) d[spad(base + p * NS)] = v[p];
+      for (int p = 0; p < R; ++p)
+        if (dbg_in(spad(base + p * NS), padlen(N), DBG_FFT_SMEM)) d[spad(base + p * NS)] = v[p];
     }
   }
 }

@@ -307,7 +307,9 @@ __global__ void k_rhs(const double2 *__restrict__ X, const double2 *__restrict__
     const double *d1 = p.rad.D1 + j * kStencil;
     double2 d1p = {0.0, 0.0};
 #pragma unroll
-    for (int t = 0; t < kStencil; ++t) d1p = d1p + d1[t] * P[(long long)(st + t) * s.nmode + mode];
+    for (int t = 0; t < kStencil; ++t)
+      if (dbg_in((long long)(st + t) * s.nmode + mode, S, DBG_RHS))
+        d1p = d1p + d1[t] * P[(long long)(st + t) * s.nmode + mode];
     const double2 pj = P[i];
     const double2 mp = (p.mval[m] * ir) * pj;
     const double2 xr = X[i], xt = X[S + i];
@@ -336,6 +338,7 @@ __global__ void k_rhs(const double2 *__restrict__ X, const double2 *__restrict__
 #pragma unroll
   for (int t = 0; t < kStencil; ++t) {
     const long long o = (long long)(st + t) * s.nmode + mode;
+    if (!dbg_in(o, S, DBG_RHS)) continue;
 #pragma unroll
     for (int c = 0; c < 4; ++c)
       if (c < s.nf) Sx[c] = Sx[c] + lw[t] * X[c * S + o];
@@ -413,12 +416,15 @@ k_prhs(const double2 *__restrict__ Yb, const double2 *__restrict__ N, double *__
       const double *dw = p.rad.Dw + j * kStencil;   // (1/r_j) D1 r_s
       double2 acc = {0.0, 0.0};
 #pragma unroll
-      for (int t = 0; t < kStencil; ++t) acc = acc + dw[t] * Rr[(q0 + t) * kPrW + tx];
+      for (int t = 0; t < kStencil; ++t)
+        if (dbg_in((q0 + t) * kPrW + tx, kWin * kPrW, DBG_PRHS))
+          acc = acc + dw[t] * Rr[(q0 + t) * kPrW + tx];
       const double2 rt = div_2i(rhs_pm(Yb, N, S, i, 0) - rhs_pm(Yb, N, S, i, 1));
       const double2 rz = rhs_pm(Yb, N, S, i, 2);
       const double ir = p.rad.inv_r[j];
       b = acc + (p.mval[m] * ir) * mul_i(rt) + beta * mul_i(rz);
     }
+    if (!dbg_in(i, S, DBG_PRHS)) continue;
     Ps[i] = b.x;
     Ps[S + i] = b.y;
     if (UT) {   // T: Dirichlet rows (wall temperatures in the (0,0) mode)
@@ -467,7 +473,8 @@ __global__ void k_hrhs(const double2 *__restrict__ Yb, const double2 *__restrict
 #pragma unroll
     for (int q = 0; q < kStencil; ++q) {
       const long long o = (long long)(st + q) * s.nmode + mode;
-      d1p = d1p + p.rad.D1[j * kStencil + q] * double2{Ps[o], Ps[S + o]};
+      if (dbg_in(o, S, DBG_HRHS))
+        d1p = d1p + p.rad.D1[j * kStencil + q] * double2{Ps[o], Ps[S + o]};
     }
     const double2 pj = {Ps[i], Ps[S + i]};
     const double2 mp = (p.mval[m] * p.rad.inv_r[j]) * pj;
@@ -543,6 +550,7 @@ struct SweepField {
   double *x;             // re plane; the im plane follows at x + S
   int qshift;            // operator row q = m + qshift (|.|, 0 -> 1 when m = 0 for u-)
   int skip00;            // 1: mode (0,0) has no system (pressure)
+  int nop;               // operators stored in L and U (index checks of the debug build)
 };
 
 struct SweepArgs {
@@ -554,11 +562,17 @@ struct SweepArgs {
 
 template <int W>   // 8: L blocks (forward), 9: U blocks (backward)
 __device__ __forceinline__ void arm_chunk(unsigned bar, double *dst, const double *src, int Nrp,
-                                          int o0, int nops, int j0) {
+                                          int o0, int nops, int j0, int nop_total) {
   const unsigned bytes = (unsigned)(kSweepRows * W * sizeof(double));
+  // debug build: a chunk past the stored operators is not copied and the
+  // barrier expects only the copies made (the wait still completes)
+  int ncopy = nops;
+  if (!dbg_in((long long)(o0 + nops - 1) * Nrp + j0 + kSweepRows - 1, (long long)nop_total * Nrp,
+              DBG_SWEEP_COPY))
+    ncopy = 0;
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-               :: "r"(bar), "r"(bytes * (unsigned)nops) : "memory");
-  for (int g = 0; g < nops; ++g) {
+               :: "r"(bar), "r"(bytes * (unsigned)ncopy) : "memory");
+  for (int g = 0; g < ncopy; ++g) {
     const double *s = src + ((long long)(o0 + g) * Nrp + j0) * W;
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -661,6 +675,10 @@ k_sweep(SweepArgs a, DevScalars *sc) {
   const int ak = g0 + g;
   const int kk = neg ? a.NK - ak : ak;
   bool active = (g < nops) && !(neg && ak == 0) && !(F.skip00 && m == 0 && ak == 0);
+  // debug build: the system's last row must lie inside its plane
+  if (active && !dbg_in((long long)(a.Nr - 1) * a.nmode + (long long)m * a.NK + kk, a.S,
+                        DBG_SWEEP_X))
+    active = false;
   double *x = F.x + part * a.S + (long long)m * a.NK + (active ? kk : 0);
   const long long xs = a.nmode;
   const int nch = (a.Nr + kSweepRows - 1) / kSweepRows;
@@ -681,9 +699,9 @@ k_sweep(SweepArgs a, DevScalars *sc) {
     const bool first = step < nch;   // forward pass
     const int j0 = (first ? step : total - 1 - step) * kSweepRows;
     if (first != TRANS)   // forward of A, or backward of A^T: L rows
-      arm_chunk<kBand>(smem_u32(&bars[s]), ring(s), F.L, a.Nrp, o0, nops, j0);
+      arm_chunk<kBand>(smem_u32(&bars[s]), ring(s), F.L, a.Nrp, o0, nops, j0, F.nop);
     else
-      arm_chunk<kBand + 1>(smem_u32(&bars[s]), ring(s), F.U, a.Nrp, o0, nops, j0);
+      arm_chunk<kBand + 1>(smem_u32(&bars[s]), ring(s), F.U, a.Nrp, o0, nops, j0, F.nop);
     armed |= 1u << s;
   };
   if (threadIdx.x == 0)
@@ -840,6 +858,7 @@ __global__ void k_alpha(const double *__restrict__ U, double2 *__restrict__ alph
 #pragma unroll
     for (int q = 0; q < kStencil; ++q) {
       const long long ii = (long long)(st + q) * s.nmode + mode;
+      if (!dbg_in(ii, S, DBG_ALPHA)) continue;
       const double2 up = {U[ii], U[S + ii]}, um = {U[2 * S + ii], U[3 * S + ii]};
       const double2 ur = 0.5 * (up + um);
       acc = acc + p.rad.D1[j * kStencil + q] * (p.rad.r[st + q] * ur);
@@ -853,6 +872,7 @@ __global__ void k_alpha(const double *__restrict__ U, double2 *__restrict__ alph
   const double2 d0 = w == 0 ? d : double2{ox, oy};
   const double2 d1 = w == 0 ? double2{ox, oy} : d;
   const int nop = p.nopP;
+  if (!dbg_in(o, nop, DBG_ALPHA)) return;
   const double a0 = p.Ainv[(2 * w) * nop + o], a1 = p.Ainv[(2 * w + 1) * nop + o];
   alpha[(long long)w * s.nmode + mode] =
       double2{-(a0 * d0.x + a1 * d1.x), -(a0 * d0.y + a1 * d1.y)};
@@ -886,7 +906,7 @@ __global__ void k_correct(const double *__restrict__ U, const double *__restrict
       const double beta = p.betak[kk];
       const double2 a = alpha[mode], b = alpha[s.nmode + mode];
       const long long fs = (long long)s.Nr * p.nopP;
-      const long long jo = (long long)j * p.nopP + o;
+      const long long jo = dbg_in(o, p.nopP, DBG_CORRECT) ? (long long)j * p.nopP + o : 0;
       const double *F = p.infl;
       pr = double2{Ps[i], Ps[S + i]};
       pr = pr + F[0 * fs + jo] * a;
@@ -1385,6 +1405,20 @@ void setup_linear(tc_ctx *c) {
   allow_smem(k_sweep<true>);
 }
 
+unsigned debug_word_linear(int clear) {
+  unsigned v = 0;
+#ifdef TC_DEBUG
+  if (cudaMemcpyFromSymbol(&v, g_dbg_word, sizeof(v)) != cudaSuccess) cudaGetLastError();
+  if (clear) {
+    const unsigned z = 0;
+    if (cudaMemcpyToSymbol(g_dbg_word, &z, sizeof(z)) != cudaSuccess) cudaGetLastError();
+  }
+#else
+  (void)clear;
+#endif
+  return v;
+}
+
 void launch_factor_poisson(tc_ctx *c) {
   LaunchScope ls(c, KFACTH);
   k_factor_poisson<<<blocks(c->lin.nopP, 128), 128, 0, c->stream>>>(c->lin);
@@ -1432,8 +1466,8 @@ void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout,
     // the pressure and (independent of it) the temperature
     LaunchScope ls(c, KPOIS);
     SweepArgs sa = sweep_args(c);
-    sa.f[0] = SweepField{p.LP, p.UP, c->Ps, 0, 1};
-    if (UT) sa.f[1] = SweepField{p.LT, p.UT, UT, 0, 0};
+    sa.f[0] = SweepField{p.LP, p.UP, c->Ps, 0, 1, p.nopP};
+    if (UT) sa.f[1] = SweepField{p.LT, p.UT, UT, 0, 0, p.nopT};
     k_sweep<false><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, UT ? 2 : 1), 4 * kSweepOps,
                      kSweepSmem, c->stream>>>(sa, c->scal);
   }
@@ -1444,9 +1478,9 @@ void launch_stage(tc_ctx *c, const double2 *N, double2 *Xout, double2 *Pout,
   {
     LaunchScope ls(c, KHELM);
     SweepArgs sa = sweep_args(c);
-    sa.f[0] = SweepField{p.LH, p.UH, U + 0 * s.S, +1, 0};
-    sa.f[1] = SweepField{p.LH, p.UH, U + 2 * s.S, -1, 0};
-    sa.f[2] = SweepField{p.LH, p.UH, U + 4 * s.S, 0, 0};
+    sa.f[0] = SweepField{p.LH, p.UH, U + 0 * s.S, +1, 0, p.nopH};
+    sa.f[1] = SweepField{p.LH, p.UH, U + 2 * s.S, -1, 0, p.nopH};
+    sa.f[2] = SweepField{p.LH, p.UH, U + 4 * s.S, 0, 0, p.nopH};
     k_sweep<false><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, 3), 4 * kSweepOps, kSweepSmem,
                      c->stream>>>(sa, c->scal);
   }
@@ -1487,15 +1521,15 @@ void launch_stage_adjoint(tc_ctx *c, const double2 *Lb, double2 *Rb) {
   k_stT_correct<<<blocks(s.S, 128), 128, 0, c->stream>>>(Lb, U, s);
   k_stT_alpha<<<blocks(s.nmode, kAlW), kAlW * kAlR, 0, c->stream>>>(U, p);
   SweepArgs sa = sweep_args(c);
-  sa.f[0] = SweepField{p.LH, p.UH, U + 0 * s.S, +1, 0};
-  sa.f[1] = SweepField{p.LH, p.UH, U + 2 * s.S, -1, 0};
-  sa.f[2] = SweepField{p.LH, p.UH, U + 4 * s.S, 0, 0};
-  if (s.nf == 4) sa.f[3] = SweepField{p.LT, p.UT, U + 6 * s.S, 0, 0};
+  sa.f[0] = SweepField{p.LH, p.UH, U + 0 * s.S, +1, 0, p.nopH};
+  sa.f[1] = SweepField{p.LH, p.UH, U + 2 * s.S, -1, 0, p.nopH};
+  sa.f[2] = SweepField{p.LH, p.UH, U + 4 * s.S, 0, 0, p.nopH};
+  if (s.nf == 4) sa.f[3] = SweepField{p.LT, p.UT, U + 6 * s.S, 0, 0, p.nopT};
   k_sweep<true><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, s.nf), 4 * kSweepOps, kSweepSmem,
                   c->stream>>>(sa, c->scal);
   k_stT_hrhs<<<blocks(s.S, 128), 128, 0, c->stream>>>(U, Rb, c->Ps, p);
   SweepArgs sp = sweep_args(c);
-  sp.f[0] = SweepField{p.LP, p.UP, c->Ps, 0, 1};
+  sp.f[0] = SweepField{p.LP, p.UP, c->Ps, 0, 1, p.nopP};
   k_sweep<true><<<dim3((s.K + kSweepOps) / kSweepOps, s.NM, 1), 4 * kSweepOps, kSweepSmem,
                   c->stream>>>(sp, c->scal);
   k_stT_prhs<<<blocks(s.S, 128), 128, 0, c->stream>>>(c->Ps, Rb, p);

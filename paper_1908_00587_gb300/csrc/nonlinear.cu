@@ -164,11 +164,14 @@ __global__ void k_zinv(const V2<T> *__restrict__ X, V2<T> *__restrict__ Vout, NL
     const int kk = t - mi * s.NK;
     const long long col = (long long)(m0 + mi) * s.NK + kk;
     const V2<T> *Xc = X + (long long)c * s.S;
-    const V2<T> val = Xc[(long long)r * s.nmode + col];
+    const long long nX = (long long)(s.nf - c) * s.S;   // entries of X from Xc on
+    const long long iv = (long long)r * s.nmode + col;
+    const V2<T> val = dbg_in(iv, nX, DBG_ZINV_X) ? Xc[iv] : V2<T>{0, 0};
     V2<T> dr = {0, 0};
 #pragma unroll
     for (int q = 0; q < kStencil; ++q) {
-      const V2<T> x = Xc[(long long)(st + q) * s.nmode + col];
+      const long long ix = (long long)(st + q) * s.nmode + col;
+      const V2<T> x = dbg_in(ix, nX, DBG_ZINV_X) ? Xc[ix] : V2<T>{0, 0};
       dr.x += d1[q] * x.x;
       dr.y += d1[q] * x.y;
     }
@@ -176,9 +179,11 @@ __global__ void k_zinv(const V2<T> *__restrict__ X, V2<T> *__restrict__ Vout, NL
     if constexpr (sizeof(T) == 4) beta = p.beta32[kk];
     else beta = p.alpha * kval(kk, s.K, s.NK);
     const int pos = kpos(kk, s.K, s.NK, Nz);
-    A[(3 * mi + 0) * Np + spad(pos)] = val;
-    A[(3 * mi + 1) * Np + spad(pos)] = dr;
-    A[(3 * mi + 2) * Np + spad(pos)] = V2<T>{-beta * val.y, beta * val.x};
+    if (dbg_in((3 * mi + 2) * Np + spad(pos), 3 * p.MB * Np, DBG_FFT_SMEM)) {
+      A[(3 * mi + 0) * Np + spad(pos)] = val;
+      A[(3 * mi + 1) * Np + spad(pos)] = dr;
+      A[(3 * mi + 2) * Np + spad(pos)] = V2<T>{-beta * val.y, beta * val.x};
+    }
   }
   __syncthreads();
   V2<T> *res = fft_batch<+1>(A, B, p.pz, 3 * nm, Np, tw, zmid_ok(p.pz, s.K));
@@ -188,7 +193,9 @@ __global__ void k_zinv(const V2<T> *__restrict__ X, V2<T> *__restrict__ Vout, NL
     const int2 b = divmod(a.x, Nz, p.fNz);
     const int l = b.y;
     const int d = b.x;
-    Vout[(((long long)(3 * c + d) * s.Nr + r) * Nz + l) * s.NM + m0 + mi] = res[(3 * mi + d) * Np + spad(l)];
+    const long long io = (((long long)(3 * c + d) * s.Nr + r) * Nz + l) * s.NM + m0 + mi;
+    if (dbg_in(io, 3LL * s.nf * s.Nr * Nz * s.NM, DBG_ZINV_V))
+      Vout[io] = res[(3 * mi + d) * Np + spad(l)];
   }
 }
 
@@ -224,6 +231,9 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     const int li = b.x;
     const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
     const long long fs = (long long)s.Nr * s.Nz * s.NM;
+    if (!dbg_in((3 * c + 2) * fs + off, 3LL * s.nf * fs, DBG_THETA_V) ||
+        !dbg_in((li * npair + 2 * c + 1) * Ntp + spad(Nt - 1), nbuf * Ntp, DBG_FFT_SMEM))
+      continue;
     V2<T> v = Vin[(3 * c + 0) * fs + off];
     V2<T> dr = Vin[(3 * c + 1) * fs + off];
     V2<T> dz = Vin[(3 * c + 2) * fs + off];
@@ -287,8 +297,11 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
     const V2<T> *b = ph + li * npair * Ntp + spad(j);
     if constexpr (sizeof(T) == 8) {
       if (p.phys_out) {   // keep the physical fields for the adjoint of this stage
-        double2 *o = p.phys_out + ((long long)r * s.Nz + l0 + li) * npair * Nt + j;
-        for (int q = 0; q < npair; ++q) o[q * Nt] = b[q * Ntp];
+        const long long io = ((long long)r * s.Nz + l0 + li) * npair * Nt + j;
+        double2 *o = p.phys_out + io;
+        if (dbg_in(io + (long long)(npair - 1) * Nt, (long long)s.Nr * s.Nz * npair * Nt,
+                   DBG_THETA_PHYS))
+          for (int q = 0; q < npair; ++q) o[q * Nt] = b[q * Ntp];
       }
     }
     const V2<T> r0 = b[0 * Ntp], r1 = b[1 * Ntp];   // (ur, ur_t), (ur_r, ur_z)
@@ -380,8 +393,9 @@ __global__ void k_theta(const V2<T> *__restrict__ Vin, V2<T> *__restrict__ W, NL
       const V2<T> b = z0[h * Ntp + spad(mm)];
       const V2<T> x = V2<T>{a.x + b.x, a.y - b.y};
       const V2<T> y = V2<T>{a.y + b.y, b.x - a.x};
-      W[(2 * h) * fs + off] = x;
-      if (2 * h + 1 < s.nf) W[(2 * h + 1) * fs + off] = y;
+      if (dbg_in((2 * h) * fs + off, (long long)s.nf * fs, DBG_THETA_W)) W[(2 * h) * fs + off] = x;
+      if (2 * h + 1 < s.nf && dbg_in((2 * h + 1) * fs + off, (long long)s.nf * fs, DBG_THETA_W))
+        W[(2 * h + 1) * fs + off] = y;
     }
   }
 }
@@ -409,7 +423,10 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
     const int2 b = divmod(a.x, Nz, p.fNz);
     const int l = b.y;
     const int g = b.x;
-    A[(g * nm + mi) * Np + spad(l)] = W[g * fs + ((long long)r * Nz + l) * s.NM + m0 + mi];
+    const long long iw = g * fs + ((long long)r * Nz + l) * s.NM + m0 + mi;
+    if (dbg_in(iw, (long long)s.nf * fs, DBG_ZFWD_W) &&
+        dbg_in((g * nm + mi) * Np + spad(l), (long long)s.nf * p.MBf * Np, DBG_FFT_SMEM))
+      A[(g * nm + mi) * Np + spad(l)] = W[iw];
   }
   __syncthreads();
   V2<T> *res = fft_batch<-1>(A, B, p.pz, nb, Np, tw);
@@ -424,8 +441,9 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
       const int mi = b.y;
       const int g = b.x;
       const V2<T> v = res[(g * nm + mi) * Np + spad(kpos(kk, s.K, s.NK, Nz))];
-      N[(long long)g * s.S + (long long)r * s.nmode + (long long)(m0 + mi) * s.NK + kk] =
-          double2{(double)v.x * scale, (double)v.y * scale};
+      const long long in = (long long)g * s.S + (long long)r * s.nmode + (long long)(m0 + mi) * s.NK + kk;
+      if (dbg_in(in, (long long)s.nf * s.S, DBG_ZFWD_N))
+        N[in] = double2{(double)v.x * scale, (double)v.y * scale};
     }
     return;
   }
@@ -494,11 +512,25 @@ __global__ void k_zfwd(const V2<T> *__restrict__ W, double2 *__restrict__ N, NLP
       out.x = fma(p.Gr, T2.x, out.x);
       out.y = fma(p.Gr, T2.y, out.y);
     }
-    N[(long long)g * s.S + i] = out;
+    if (dbg_in((long long)g * s.S + i, (long long)s.nf * s.S, DBG_ZFWD_N)) N[(long long)g * s.S + i] = out;
   }
 }
 
 }  // namespace
+
+unsigned debug_word_nonlinear(int clear) {
+  unsigned v = 0;
+#ifdef TC_DEBUG
+  if (cudaMemcpyFromSymbol(&v, g_dbg_word, sizeof(v)) != cudaSuccess) cudaGetLastError();
+  if (clear) {
+    const unsigned z = 0;
+    if (cudaMemcpyToSymbol(g_dbg_word, &z, sizeof(z)) != cudaSuccess) cudaGetLastError();
+  }
+#else
+  (void)clear;
+#endif
+  return v;
+}
 
 void set_divisors(NLParams &p) {
   const Sizes &s = p.sz;

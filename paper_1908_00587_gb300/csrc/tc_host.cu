@@ -1556,6 +1556,22 @@ tc_status tc_get_ic_scales(const tc_ctx *c, double *s_u, double *s_T) {
   return TC_OK;
 }
 
+tc_status tc_debug_flags(unsigned *flags, int clear) {
+  if (!flags) return TC_ERR_ARG;
+  *flags = 0;
+#ifndef TC_DEBUG
+  (void)clear;
+  return TC_ERR_UNSUPPORTED;
+#else
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return TC_ERR_CUDA;
+  }
+  *flags = debug_word_nonlinear(clear) | debug_word_linear(clear);
+  return TC_OK;
+#endif
+}
+
 tc_status tc_get_timing(tc_ctx *c, tc_kernel_time *out, int cap, int *count) {
   if (!c || (!out && cap > 0) || !count) return TC_ERR_ARG;
   if (c->poisoned) return TC_ERR_CUDA;

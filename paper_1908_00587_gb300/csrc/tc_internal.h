@@ -12,6 +12,33 @@
 
 namespace tc {
 
+// Index checks of the debug build (compiled with -DTC_DEBUG; libtc_debug.so).
+// dbg_in(i, n, site) is true when 0 <= i < n.  In the debug build an index
+// out of that range sets bit `site` of a device word of this translation unit
+// and returns false, and the caller skips the access: a bad index is
+// recorded, never dereferenced, and never traps.  tc_debug_flags reads the
+// words.  In the normal build dbg_in is the constant true and the checks
+// compile away.
+enum DbgSite {
+  DBG_ZINV_X, DBG_ZINV_V, DBG_THETA_V, DBG_THETA_W, DBG_THETA_PHYS, DBG_ZFWD_W, DBG_ZFWD_N,
+  DBG_FFT_SMEM, DBG_RHS, DBG_PRHS, DBG_HRHS, DBG_SWEEP_X, DBG_SWEEP_COPY, DBG_ALPHA,
+  DBG_CORRECT, DBG_NSITES
+};
+#ifdef TC_DEBUG
+static __device__ unsigned int g_dbg_word;
+__device__ __forceinline__ bool dbg_in(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(&g_dbg_word, 1u << site);
+  return false;
+}
+#else
+__device__ __forceinline__ constexpr bool dbg_in(long long, long long, int) { return true; }
+#endif
+// Host side: this translation unit's word (0 in the normal build); clear != 0
+// resets it.  One reader per .cu file that checks indices.
+unsigned debug_word_nonlinear(int clear);
+unsigned debug_word_linear(int clear);
+
 constexpr int kStencil = 9;   // radial FD stencil (Sec. 2.1: 9 points by default)
 constexpr int kBand = 8;      // half bandwidth of the radial operators
 constexpr int kBandW = 17;    // stored band entries per row (8 lower, diag, 8 upper)

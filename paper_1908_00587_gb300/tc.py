@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtc.so")
+# TC_LIB=debug loads the debug build (index checks, tc_debug_flags)
+LIB_PATH = os.path.join(_HERE, "libtc_debug.so" if os.environ.get("TC_LIB") == "debug"
+                        else "libtc.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libtc.so is not built ({LIB_PATH}); run __graft_entry__.build()")
@@ -100,6 +102,7 @@ _SIGS = {
     "tc_ensemble_kernels_per_step": [_P, ctypes.POINTER(ctypes.c_longlong)],
     "tc_ensemble_destroy": [_P],
     "tc_autotune": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "tc_debug_flags": [ctypes.POINTER(ctypes.c_uint), _I],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -413,6 +416,14 @@ def tc_autotune(ctx):
 
 def tc_ensemble_destroy(ens):
     _check(_lib.tc_ensemble_destroy(ens), "tc_ensemble_destroy")
+
+
+def tc_debug_flags(clear=False) -> int:
+    """Check-site bits of the debug build's index checks (see include/tc.h);
+    raises TCError (TC_ERR_UNSUPPORTED) in the normal build."""
+    f = ctypes.c_uint(0)
+    _check(_lib.tc_debug_flags(ctypes.byref(f), int(bool(clear))), "tc_debug_flags")
+    return f.value
 
 
 def tc_status_string(s: int) -> str:

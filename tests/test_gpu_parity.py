@@ -315,8 +315,30 @@ def test_workload_full_run_parity(tc, name, shrink, nsteps):
           f"perturbation {pert:.2e}, dt range {rdts.min():.4e}..{rdts.max():.4e}")
     assert np.all(np.abs(dts - rdts) <= 1e-8 * rdts)
     assert max(per_field) <= 1e-10, per_field
-    for k in ("E", "E_pert", "eps", "P_wall"):
+    for k in ("E", "E_pert", "eps"):
         assert abs(dg[k] - dr[k]) <= 1e-9 * abs(dr[k]) + 1e-300, (k, dg[k], dr[k])
+    # the wall power is a wall derivative of the O(Re) mean flow: the 9-point
+    # one-sided stencil at the first Chebyshev node amplifies a relative state
+    # difference by kappa = (|D1| |u| + |u|/r) / |D1 u - u/r| (about 1e4 at
+    # eta = 0.875, Re_i = 1e4); gate it at that conditioning times the field
+    # difference
+    kappa = _wall_shear_condition(mdl, ref)
+    tol = max(1e-9, 10.0 * kappa * max(per_field))
+    assert abs(dg["P_wall"] - dr["P_wall"]) <= tol * abs(dr["P_wall"]), (dg["P_wall"], dr["P_wall"],
+                                                                        kappa)
+
+
+def _wall_shear_condition(mdl, X):
+    """Relative condition number of the wall shear d u_theta/dr - u_theta/r of
+    the (0,0) mode with respect to the nodal values (worst wall)."""
+    g = mdl.g
+    u = X[1][:, 0, 0].real
+    worst = 1.0
+    for w in (0, -1):
+        row = g.D1[w]
+        sig = row @ u - u[w] / g.r[w]
+        worst = max(worst, float((np.abs(row) @ np.abs(u) + abs(u[w]) / g.r[w]) / abs(sig)))
+    return worst
 
 
 def test_set_state_validation(tc):
