@@ -76,6 +76,11 @@ void fill_plan_twiddles(const FFTPlan &pl, double2 *out);
 // Host helpers shared by the set-up code (tc_host.cu).
 void fd_weights(double x0, const double *x, int n, double w[3][kStencil]);
 
+// Axial wavenumber index k of stored index kk (FFT order: 0..K, then -K..-1).
+__host__ __device__ __forceinline__ int kval(int kk, int K, int NK) {
+  return kk <= K ? kk : kk - NK;
+}
+
 // Problem sizes.
 struct Sizes {
   int Nr, Nt, Nz, M, K, NM, NK, nmode, nf;
