@@ -390,12 +390,33 @@ tc_status tc_ensemble_create(int n, const tc_params *p, int autotune_tiles, tc_e
 tc_status tc_ensemble_member(tc_ens *e, int i, tc_ctx **ctx);
 
 /* Advance every member nsteps steps of its own fixed dt (host array of n
- * values > 0).  One step of all members is captured once into a CUDA graph
- * (members are independent branches, run concurrently) and the graph is
- * replayed nsteps times; it is re-captured when a dt changes.  Returns the
- * worst member status (TC_ERR_TIMEOUT, TC_ERR_NONFINITE) after a
- * synchronisation. */
+ * values > 0), in the ensemble's launch mode (tc_ensemble_set_mode):
+ *   1 (default) one persistent cooperative kernel launch runs all nsteps
+ *     steps of every member: the work items are the CTA tiles of the step's
+ *     kernels, numbered member after member for each stage of the
+ *     predictor-corrector step; resident CTAs pull items from a per-stage
+ *     counter and a grid barrier separates the stages.  Every wait in it is
+ *     bounded (2 s for the barrier, 1 s for the sweeps' copies); a wait that
+ *     runs out makes the call return TC_ERR_TIMEOUT without a fault.  It runs
+ *     the default scheme: while any member has n_corr != 1, the flux
+ *     constraint or the sweep test hook, the call steps in mode 0 instead.
+ *     It shrinks transform tiles that do not fit its shared-memory budget
+ *     (results do not depend on tiles).
+ *   0 one step of all members captured once into a CUDA graph (independent
+ *     branches run concurrently) and replayed nsteps times; re-captured when a
+ *     dt or a member option changes.
+ * Results are bit-identical in both modes and to each member stepped alone.
+ * Returns the worst member status (TC_ERR_TIMEOUT, TC_ERR_NONFINITE) after
+ * a synchronisation. */
 tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt);
+
+/* Launch mode of tc_ensemble_step: 1 persistent kernel (default), 0 graph of
+ * per-member kernels, 2 persistent kernel with its test hook -- CTA 0 leaves
+ * before the first grid barrier, so every other CTA's bounded wait runs out
+ * and tc_ensemble_step returns TC_ERR_TIMEOUT (the members' states are then
+ * those before the call's first corrector).  Errors: TC_ERR_ARG. */
+tc_status tc_ensemble_set_mode(tc_ens *e, int mode);
+tc_status tc_ensemble_get_mode(const tc_ens *e, int *mode);
 
 /* Tile autotuner for one context (the one the ensemble runs per size
  * class): times the nonlinear stage on the context's current state for tile
@@ -405,7 +426,9 @@ tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt);
  * Results do not depend on the tiles. */
 tc_status tc_autotune(tc_ctx *ctx, int *tile_mb, int *tile_lb);
 
-/* Kernel launches one graph replay (one step of every member) contains. */
+/* Kernel launches per tc_ensemble_step step: the kernels one graph replay
+ * (one step of every member) contains in mode 0; 1 in the persistent modes
+ * (one launch covers every step of a call). */
 tc_status tc_ensemble_kernels_per_step(const tc_ens *e, long long *count);
 
 /* Free the members, streams and graph.  Accepts NULL. */

@@ -1,20 +1,21 @@
-// Ensemble of independent runs of uneven size on one GPU.
+// Ensemble of independent runs of uneven size on one GPU (batching form).
 //
-// Each member is an ordinary context on its own stream.  One step of every
-// member is captured once into a CUDA graph: the members are independent
-// branches between a fork and a join, so one graph launch replays all of them
-// and the GPU runs the branches concurrently, filling the SMs that a single
-// small run leaves idle.  The graph is rebuilt only when a member's step or
-// options change.  A persistent kernel was not used: every stage of a run
-// depends on the previous one, which inside one launch would need grid-wide
-// barriers on a shared GPU; graph replay removes the same per-launch host
-// overhead.
+// Each member is an ordinary context.  Two ways to step them all:
+//   mode 1 (default): one persistent cooperative kernel (k_ensemble) runs
+//     every step of every member; work items are single CTA tiles of the
+//     step's kernels, pulled stage by stage from per-stage counters, with a
+//     bounded grid barrier between stages;
+//   mode 0: one step of every member captured once into a CUDA graph, the
+//     members as independent branches between a fork and a join, replayed
+//     once per step.
+// Both run exactly the arithmetic of the member stepped alone.
 //
 // Tiles: before the first step, each size class (Nr, Ntheta, Nz, fields,
 // precision) is tuned once by timing the nonlinear stage for candidate tile
 // shapes (m columns per CTA of the axial kernels, z rows per CTA of the
-// azimuthal kernel) and keeping the fastest.  Tiles do not change the
-// arithmetic, so results are bit-identical for every choice.
+// azimuthal kernel) and keeping the fastest; the persistent kernel then
+// shrinks any tile whose shared memory exceeds its per-CTA budget.  Tiles do
+// not change the arithmetic, so results are bit-identical for every choice.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +26,8 @@
 #include <tuple>
 #include <vector>
 
+#include "lin_body.cuh"
+#include "nl_body.cuh"
 #include "tc_internal.h"
 
 struct tc_ens {
@@ -37,6 +40,16 @@ struct tc_ens {
   cudaGraphExec_t exec = nullptr;
   std::vector<double> graph_dt;
   std::vector<long long> graph_gen;   // members' launch-parameter generations at capture
+  // persistent launch (mode 1): member table, item offsets, grid-barrier state
+  int mode = 1;
+  void *d_mem = nullptr;     // EnsMember[n] (device)
+  int *d_offs = nullptr;     // item offsets [stage][n + 1] (device)
+  void *d_sync = nullptr;    // EnsSync (device)
+  size_t smem = 0;
+  int grid = 0;
+  std::vector<double> plan_dt;
+  std::vector<long long> plan_gen;
+  long long items_per_step = 0;
 };
 
 namespace tc {
@@ -122,6 +135,471 @@ tc_status autotune(tc_ctx *c, int *best_mb, int *best_lb) {
   return TC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Persistent ensemble kernel (mode 1).
+//
+// One cooperative launch runs every step of every member.  A step is the
+// fixed sequence of stages of enqueue_step (n_corr = 1): for each stage the
+// work items of all members -- one CTA tile of that stage's kernel each -- are
+// numbered consecutively, and the resident CTAs pull items from a per-stage
+// counter until the stage is exhausted; a grid barrier then separates it from
+// the next stage.  Members are independent, so the barrier is the only
+// dependency: stage s of every member needs stage s - 1 of the same member,
+// and the barrier provides exactly that (and a little more).  A cooperative
+// launch makes every CTA resident, so the barrier cannot wait for a CTA that
+// is not running; its spin is still bounded (kEnsBarrierNs): a CTA that gives
+// up raises the failure flag, every other CTA leaves at its next barrier, and
+// tc_ensemble_step reports TC_ERR_TIMEOUT.  Each item runs the same device
+// body on the same tile as the member's own kernels, so every member stays
+// bit-identical to the run stepped alone.
+enum EnsKind : int {
+  EK_PREP, EK_ZINV, EK_THETA, EK_ZFWD, EK_DT, EK_FACTH, EK_INFL, EK_RHS, EK_PRHS, EK_SWEEP_P,
+  EK_HRHS, EK_SWEEP_H, EK_ALPHA, EK_CORRECT
+};
+struct EnsStageDef {
+  int kind, pass;   // pass 0: predictor (X -> Xp, with N0), 1: corrector (Xp -> X, with N1)
+};
+__constant__ EnsStageDef c_ens_stages[] = {
+    {EK_PREP, 0},  {EK_ZINV, 0},    {EK_THETA, 0}, {EK_ZFWD, 0},    {EK_DT, 0},
+    {EK_FACTH, 0}, {EK_INFL, 0},    {EK_RHS, 0},   {EK_PRHS, 0},    {EK_SWEEP_P, 0},
+    {EK_HRHS, 0},  {EK_SWEEP_H, 0}, {EK_ALPHA, 0}, {EK_CORRECT, 0}, {EK_PREP, 1},
+    {EK_ZINV, 1},  {EK_THETA, 1},   {EK_ZFWD, 1},  {EK_PRHS, 1},    {EK_SWEEP_P, 1},
+    {EK_HRHS, 1},  {EK_SWEEP_H, 1}, {EK_ALPHA, 1}, {EK_CORRECT, 1}};
+constexpr int kEnsStages = 24;
+const int h_ens_kind[kEnsStages] = {EK_PREP,  EK_ZINV,  EK_THETA,   EK_ZFWD,  EK_DT,
+                                    EK_FACTH, EK_INFL,  EK_RHS,     EK_PRHS,  EK_SWEEP_P,
+                                    EK_HRHS,  EK_SWEEP_H, EK_ALPHA, EK_CORRECT, EK_PREP,
+                                    EK_ZINV,  EK_THETA, EK_ZFWD,    EK_PRHS,  EK_SWEEP_P,
+                                    EK_HRHS,  EK_SWEEP_H, EK_ALPHA, EK_CORRECT};
+constexpr int kEnsThreads = 256;
+constexpr int kEnsSweepGroups = 2;    // sweep tiles per item, 64 threads each
+constexpr int kEnsSweepStages = 2;    // factor ring depth of those tiles
+constexpr size_t kEnsSweepRing = sizeof(double) * kEnsSweepStages * kSweepStageDoubles;
+constexpr size_t kEnsSweepGroupBytes = kEnsSweepRing + 64;   // + mbarriers and abort flag
+constexpr size_t kEnsSmemBudget = 110 * 1024;   // two CTAs per SM
+constexpr long long kEnsBarrierNs = 2000000000LL;   // 2 s
+
+// Launch parameters of one member (device copy; see ens_item).
+struct EnsMember {
+  NLParams nl[2];     // transform parameters of the two passes (mixed: Xfull differs)
+  LinParams lin;
+  SweepArgs swP, swH;
+  double2 *X, *Xp, *N0, *N1, *Yb, *P, *alpha;
+  void *V, *W;
+  double *Ps, *U, *UT, *prof;
+  float2 *X32;
+  float *prof32;
+  DevScalars *sc;
+  double dt, cfl, dt_max;
+  int mixed, nmb, nlb, nmbf, nprx, nprof, nsw_p, nsw_h, swx;
+};
+
+struct EnsSync {
+  unsigned count, gen;
+  int fail;
+  unsigned ctr[kEnsStages];
+};
+
+struct GroupSync {
+  int id;   // named barrier of one 64-thread group
+  __device__ void operator()() const {
+    asm volatile("bar.sync %0, 64;" :: "r"(id) : "memory");
+  }
+};
+
+// Grid barrier of the cooperative launch; the last CTA to arrive also resets
+// the item counter of the stage just finished.  False when the wait ran out
+// or another CTA gave up.
+__device__ bool ens_grid_barrier(EnsSync *g, int st) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned *vgen = &g->gen;
+    const unsigned gen0 = *vgen;
+    __threadfence();
+    if (atomicAdd(&g->count, 1u) == gridDim.x - 1) {
+      g->count = 0;
+      g->ctr[st] = 0;
+      __threadfence();
+      atomicAdd(&g->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == gen0) {
+        if (*reinterpret_cast<volatile int *>(&g->fail)) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+        if ((long long)(global_ns() - t0) > kEnsBarrierNs) {
+          atomicExch(&g->fail, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// One work item: tile `t` of stage `d` of member `m`.
+__device__ __forceinline__ void ens_item(const EnsMember &m, EnsStageDef d, int t,
+                                         unsigned char *smem) {
+  const Sizes &s = m.lin.sz;
+  const int tid = threadIdx.x;
+  const long long i = (long long)t * kEnsThreads + tid;
+  const NLParams &p = m.nl[d.pass];
+  const double2 *Xin = d.pass ? m.Xp : m.X;
+  double2 *Nout = d.pass ? m.N1 : m.N0;
+  switch (d.kind) {
+    case EK_PREP:
+      if (t < m.nprof) meanprof_body(Xin, m.prof, m.prof32, s, m.lin.rad, t * kEnsThreads + tid);
+      else tofloat_body(Xin, m.X32, s, (long long)(t - m.nprof) * kEnsThreads + tid);
+      break;
+    case EK_ZINV: {
+      const int bx = t % m.nmb, r = t / m.nmb;
+      if (m.mixed)
+        zinv_body<float>(m.X32, static_cast<float2 *>(m.V), p, smem, bx, r % s.Nr, r / s.Nr);
+      else
+        zinv_body<double>(Xin, static_cast<double2 *>(m.V), p, smem, bx, r % s.Nr, r / s.Nr);
+      break;
+    }
+    case EK_THETA: {
+      unsigned long long *rate = d.pass ? nullptr : &m.sc->rate_bits;
+      if (m.mixed)
+        theta_body<float>(static_cast<const float2 *>(m.V), static_cast<float2 *>(m.W), p, rate,
+                          m.sc->norm_bits, 0, smem, t % m.nlb, t / m.nlb);
+      else
+        theta_body<double>(static_cast<const double2 *>(m.V), static_cast<double2 *>(m.W), p,
+                           rate, m.sc->norm_bits, 0, smem, t % m.nlb, t / m.nlb);
+      break;
+    }
+    case EK_ZFWD:
+      if (m.mixed)
+        zfwd_body<float>(static_cast<const float2 *>(m.W), Nout, p, smem, t % m.nmbf,
+                         t / m.nmbf);
+      else
+        zfwd_body<double>(static_cast<const double2 *>(m.W), Nout, p, smem, t % m.nmbf,
+                          t / m.nmbf);
+      break;
+    case EK_DT:
+      if (tid == 0) dt_policy_body(m.sc, m.dt, m.cfl, m.dt_max, nullptr, 0);
+      break;
+    case EK_FACTH:
+      factor_helm_body(m.lin, m.sc, (int)i);
+      break;
+    case EK_INFL:
+      influence_body(m.lin, m.sc, (int)i);
+      break;
+    case EK_RHS:
+      rhs_body(m.X, m.N0, m.Yb, m.N1, m.P, m.lin, m.sc, i);
+      break;
+    case EK_PRHS:
+      prhs_body(m.Yb, Nout, m.Ps, m.UT, m.lin, reinterpret_cast<double2 *>(smem), t % m.nprx,
+                t / m.nprx);
+      break;
+    case EK_SWEEP_P:
+    case EK_SWEEP_H: {
+      const int grp = tid >> 6;
+      const int nt = d.kind == EK_SWEEP_P ? m.nsw_p : m.nsw_h;
+      const int u = t * kEnsSweepGroups + grp;
+      if (grp < kEnsSweepGroups && u < nt) {
+        unsigned char *base = smem + grp * kEnsSweepGroupBytes;
+        unsigned long long *bars = reinterpret_cast<unsigned long long *>(base + kEnsSweepRing);
+        int *abort_flag = reinterpret_cast<int *>(bars + kEnsSweepStages);
+        const int bx = u % m.swx, r = u / m.swx;
+        sweep_body<false, kEnsSweepStages>(d.kind == EK_SWEEP_P ? m.swP : m.swH, m.sc, bx,
+                                           r % s.NM, r / s.NM, tid & 63,
+                                           reinterpret_cast<double *>(base), bars, abort_flag,
+                                           GroupSync{1 + grp});
+      }
+      break;
+    }
+    case EK_HRHS:
+      hrhs_body(m.Yb, Nout, m.Ps, m.U, m.lin, i);
+      break;
+    case EK_ALPHA:
+      alpha_body(m.U, m.alpha, m.lin, i);
+      break;
+    case EK_CORRECT:
+      if (d.pass) correct_body(m.U, m.Ps, m.alpha, m.X, m.P, m.Xp, m.lin, m.sc, i);
+      else correct_body(m.U, m.Ps, m.alpha, m.Xp, m.P, nullptr, m.lin, m.sc, i);
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(kEnsThreads, 2)
+k_ensemble(const EnsMember *__restrict__ mem, const int *__restrict__ offs, int nmem, int nsteps,
+           EnsSync *gs, int selftest) {
+  extern __shared__ __align__(128) unsigned char ens_smem[];
+  __shared__ int item_s;
+  for (int step = 0; step < nsteps; ++step) {
+    for (int st = 0; st < kEnsStages; ++st) {
+      const int *o = offs + st * (nmem + 1);
+      const int total = o[nmem];
+      const EnsStageDef d = c_ens_stages[st];
+      while (true) {
+        if (threadIdx.x == 0) item_s = atomicAdd(&gs->ctr[st], 1u);
+        __syncthreads();
+        const int it = item_s;
+        __syncthreads();
+        if (it >= total) break;
+        int lo = 0, hi = nmem;   // the member m with o[m] <= it < o[m + 1]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (o[mid] <= it) lo = mid;
+          else hi = mid;
+        }
+        ens_item(mem[lo], d, it - o[lo], ens_smem);
+        __syncthreads();
+      }
+      if (selftest && blockIdx.x == 0) return;   // test hook: never arrive
+      if (!ens_grid_barrier(gs, st)) return;
+    }
+  }
+}
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+SweepArgs sweep_args_of(const tc_ctx *c) {
+  SweepArgs a{};
+  a.Nr = c->sz.Nr;
+  a.Nrp = c->lin.Nrp;
+  a.K = c->sz.K;
+  a.NK = c->sz.NK;
+  a.nmode = c->sz.nmode;
+  a.S = c->sz.S;
+  a.arm = 1;
+  return a;
+}
+
+// Items of stage kind k for one member (host).
+int ens_items(const EnsMember &m, const tc_ctx *c, int k) {
+  const Sizes &s = c->sz;
+  switch (k) {
+    case EK_PREP: return m.mixed ? m.nprof + cdiv((long long)s.nf * s.S, kEnsThreads) : 0;
+    case EK_ZINV: return m.nmb * s.Nr * s.nf;
+    case EK_THETA: return m.nlb * s.Nr;
+    case EK_ZFWD: return m.nmbf * s.Nr;
+    case EK_DT: return 1;
+    case EK_FACTH: return cdiv(c->lin.nopH + c->lin.nopT, kEnsThreads);
+    case EK_INFL: return cdiv(c->lin.nopP, kEnsThreads);
+    case EK_RHS:
+    case EK_HRHS:
+    case EK_CORRECT: return cdiv(s.S, kEnsThreads);
+    case EK_PRHS: return m.nprx * cdiv(s.Nr, kPrL);
+    case EK_SWEEP_P: return cdiv(m.nsw_p, kEnsSweepGroups);
+    case EK_SWEEP_H: return cdiv(m.nsw_h, kEnsSweepGroups);
+    case EK_ALPHA: return cdiv(2LL * s.nmode, kEnsThreads);
+  }
+  return 0;
+}
+
+// Largest transform-tile shared memory of a context in its precision.
+size_t transform_smem(const tc_ctx *c) {
+  return c->precision == 1 ? std::max({c->smem32_zinv, c->smem32_theta, c->smem32_zfwd})
+                           : std::max({c->smem_zinv, c->smem_theta, c->smem_zfwd});
+}
+
+// Shrink a member's tiles until they fit the persistent kernel's budget
+// (tiles do not change the arithmetic).
+void fit_tiles(tc_ctx *c, size_t budget) {
+  for (int guard = 0; guard < 64 && transform_smem(c) > budget; ++guard) {
+    const NLParams &q = (c->precision == 1) ? c->nl32 : c->nl;
+    const size_t zi = c->precision == 1 ? c->smem32_zinv : c->smem_zinv;
+    const size_t th = c->precision == 1 ? c->smem32_theta : c->smem_theta;
+    if (th > budget && q.LB > 1) tc_set_option(c, "tile_lb", q.LB - 1);
+    else if (zi > budget && q.MB > 1) tc_set_option(c, "tile_mb", q.MB - 1);
+    else if (q.MBf > 1) tc_set_option(c, "tile_mbf", q.MBf - 1);
+    else break;
+  }
+}
+
+void drop_plan(tc_ens *e) {
+  if (e->d_mem) cudaFree(e->d_mem);
+  if (e->d_offs) cudaFree(e->d_offs);
+  if (e->d_sync) cudaFree(e->d_sync);
+  e->d_mem = nullptr;
+  e->d_offs = nullptr;
+  e->d_sync = nullptr;
+  e->plan_dt.clear();
+  e->plan_gen.clear();
+}
+
+// Member table and item offsets for the persistent kernel (rebuilt when a
+// member's step or launch parameters change).
+tc_status build_plan(tc_ens *e, const double *dt) {
+  const int n = (int)e->m.size();
+  drop_plan(e);
+  std::vector<EnsMember> mem(n);
+  size_t smem = std::max<size_t>((size_t)kPrWin * kPrW * sizeof(double2),
+                                 kEnsSweepGroups * kEnsSweepGroupBytes);
+  for (int i = 0; i < n; ++i) {
+    tc_ctx *c = e->m[i];
+    if (c->n_corr != 1 || c->flux || c->selftest_no_copy) return TC_ERR_UNSUPPORTED;
+    fit_tiles(c, kEnsSmemBudget);
+    if (transform_smem(c) > kEnsSmemBudget) return TC_ERR_UNSUPPORTED;
+    smem = std::max(smem, transform_smem(c));
+    const Sizes &s = c->sz;
+    EnsMember &m = mem[i];
+    m.mixed = c->precision == 1;
+    for (int pass = 0; pass < 2; ++pass) {
+      NLParams q = m.mixed ? c->nl32 : c->nl;
+      if (m.mixed) {
+        q.mixed = 1;
+        q.Xfull = pass ? c->Xp : c->X;
+        q.prof = c->prof;
+      }
+      q.phys_out = nullptr;
+      m.nl[pass] = q;
+    }
+    const NLParams &q = m.nl[0];
+    m.lin = c->lin;
+    double *U = reinterpret_cast<double *>(c->U0);
+    m.U = U;
+    m.UT = (s.nf == 4) ? U + 6 * s.S : nullptr;
+    m.swP = sweep_args_of(c);
+    m.swP.f[0] = SweepField{c->lin.LP, c->lin.UP, c->Ps, 0, 1, c->lin.nopP};
+    if (m.UT) m.swP.f[1] = SweepField{c->lin.LT, c->lin.UT, m.UT, 0, 0, c->lin.nopT};
+    m.swH = sweep_args_of(c);
+    m.swH.f[0] = SweepField{c->lin.LH, c->lin.UH, U + 0 * s.S, +1, 0, c->lin.nopH};
+    m.swH.f[1] = SweepField{c->lin.LH, c->lin.UH, U + 2 * s.S, -1, 0, c->lin.nopH};
+    m.swH.f[2] = SweepField{c->lin.LH, c->lin.UH, U + 4 * s.S, 0, 0, c->lin.nopH};
+    m.X = c->X;
+    m.Xp = c->Xp;
+    m.N0 = c->N0;
+    m.N1 = c->N1;
+    m.Yb = c->Yb;
+    m.P = c->P;
+    m.alpha = c->alpha_buf;
+    m.V = c->V;
+    m.W = c->W;
+    m.Ps = c->Ps;
+    m.prof = c->prof;
+    m.X32 = c->X32;
+    m.prof32 = c->d_prof32;
+    m.sc = c->scal;
+    m.dt = dt[i];
+    m.cfl = c->cfl;
+    m.dt_max = c->dt_max;
+    m.nmb = cdiv(s.NM, q.MB);
+    m.nlb = cdiv(s.Nz, q.LB);
+    m.nmbf = cdiv(s.NM, q.MBf);
+    m.nprx = cdiv(s.nmode, kPrW);
+    m.nprof = cdiv(s.Nr, kEnsThreads);
+    m.swx = (s.K + kSweepOps) / kSweepOps;
+    m.nsw_p = m.swx * s.NM * (m.UT ? 2 : 1);
+    m.nsw_h = m.swx * s.NM * 3;
+  }
+  std::vector<int> offs((size_t)kEnsStages * (n + 1), 0);
+  long long items = 0;
+  for (int st = 0; st < kEnsStages; ++st) {
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+      offs[(size_t)st * (n + 1) + i] = acc;
+      acc += ens_items(mem[i], e->m[i], h_ens_kind[st]);
+    }
+    offs[(size_t)st * (n + 1) + n] = acc;
+    items += acc;
+  }
+  e->items_per_step = items;
+  // kernel attributes and a grid of every CTA that can be resident
+  if (cudaFuncSetAttribute(k_ensemble, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return TC_ERR_UNSUPPORTED;
+  }
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ensemble, kEnsThreads, smem) !=
+          cudaSuccess || per < 1) {
+    cudaGetLastError();
+    return TC_ERR_UNSUPPORTED;
+  }
+  e->grid = nsm * per;
+  e->smem = smem;
+  if (cudaMalloc(&e->d_mem, sizeof(EnsMember) * n) != cudaSuccess ||
+      cudaMalloc(&e->d_offs, sizeof(int) * offs.size()) != cudaSuccess ||
+      cudaMalloc(&e->d_sync, sizeof(EnsSync)) != cudaSuccess) {
+    cudaGetLastError();
+    drop_plan(e);
+    return TC_ERR_OOM;
+  }
+  if (cudaMemcpy(e->d_mem, mem.data(), sizeof(EnsMember) * n, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(e->d_offs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    drop_plan(e);
+    return TC_ERR_CUDA;
+  }
+  e->plan_dt.assign(dt, dt + n);
+  e->plan_gen.resize(n);
+  for (int i = 0; i < n; ++i) e->plan_gen[i] = e->m[i]->gen;
+  return TC_OK;
+}
+
+// nsteps steps of every member in one cooperative launch on e->s0.
+// selftest != 0: CTA 0 leaves before the first grid barrier (test hook of the
+// bounded wait: every other CTA's wait runs out and the step reports
+// TC_ERR_TIMEOUT, without a fault).
+tc_status persistent_steps(tc_ens *e, int nsteps, const double *dt, int selftest) {
+  const int n = (int)e->m.size();
+  bool same = e->d_mem && (int)e->plan_dt.size() == n &&
+              std::equal(e->plan_dt.begin(), e->plan_dt.end(), dt);
+  for (int i = 0; same && i < n; ++i) same = e->plan_gen[i] == e->m[i]->gen;
+  if (!same) {
+    const tc_status st = build_plan(e, dt);
+    if (st != TC_OK) return st;
+  }
+  if (cudaMemsetAsync(e->d_sync, 0, sizeof(EnsSync), e->s0) != cudaSuccess) {
+    cudaGetLastError();
+    return TC_ERR_CUDA;
+  }
+  int nm = n;
+  const EnsMember *dm = static_cast<const EnsMember *>(e->d_mem);
+  EnsSync *ds = static_cast<EnsSync *>(e->d_sync);
+  void *args[] = {&dm, &e->d_offs, &nm, &nsteps, &ds, &selftest};
+  if (cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_ensemble), dim3(e->grid),
+                                  dim3(kEnsThreads), args, e->smem, e->s0) != cudaSuccess) {
+    std::fprintf(stderr, "libtc: ensemble launch: %s\n", cudaGetErrorString(cudaGetLastError()));
+    return TC_ERR_CUDA;
+  }
+  for (tc_ctx *c : e->m) c->launches += 1;
+  return TC_OK;
+}
+
+// Wait for the steps and collect the members' status flags.
+tc_status finish_steps(tc_ens *e, int nsteps, const double *dt, bool persistent) {
+  const int n = (int)e->m.size();
+  if (cudaStreamSynchronize(e->s0) != cudaSuccess) {
+    cudaGetLastError();
+    for (tc_ctx *c : e->m) c->poisoned = true;
+    return TC_ERR_CUDA;
+  }
+  tc_status worst = TC_OK;
+  if (persistent) {
+    EnsSync gs;
+    if (cudaMemcpy(&gs, e->d_sync, sizeof(gs), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return TC_ERR_CUDA;
+    if (gs.fail) worst = TC_ERR_TIMEOUT;
+  }
+  for (int i = 0; i < n; ++i) {
+    tc_ctx *c = e->m[i];
+    DevScalars sc;
+    if (cudaMemcpy(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return TC_ERR_CUDA;
+    c->t += dt[i] * nsteps;
+    if (sc.timeout) worst = TC_ERR_TIMEOUT;
+    else if (c->check && sc.nonfinite && worst == TC_OK) worst = TC_ERR_NONFINITE;
+  }
+  return worst;
+}
+
 void drop_graph(tc_ens *e) {
   if (e->exec) cudaGraphExecDestroy(e->exec);
   if (e->graph) cudaGraphDestroy(e->graph);
@@ -139,6 +617,7 @@ extern "C" {
 tc_status tc_ensemble_destroy(tc_ens *e) {
   if (!e) return TC_OK;
   drop_graph(e);
+  drop_plan(e);
   for (tc_ctx *c : e->m) tc_destroy(c);
   for (cudaStream_t s : e->streams) cudaStreamDestroy(s);
   for (cudaEvent_t ev : e->joins) cudaEventDestroy(ev);
@@ -216,6 +695,19 @@ tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt) {
     if (e->m[i]->timing) tc_set_option(e->m[i], "timing", 0);
   }
   if (nsteps == 0) return TC_OK;
+  bool persistent = e->mode >= 1;
+  for (int i = 0; persistent && i < n; ++i)   // the persistent kernel runs the default scheme
+    persistent = e->m[i]->n_corr == 1 && !e->m[i]->flux && !e->m[i]->selftest_no_copy;
+  if (persistent) {
+    for (int i = 0; i < n; ++i) {
+      tc_ctx *c = e->m[i];
+      cudaMemsetAsync(reinterpret_cast<char *>(c->scal) + offsetof(DevScalars, nonfinite), 0,
+                      2 * sizeof(int), e->s0);
+    }
+    const tc_status st = persistent_steps(e, nsteps, dt, e->mode == 2);
+    if (st != TC_OK) return st;
+    return finish_steps(e, nsteps, dt, true);
+  }
   bool same = e->exec && (int)e->graph_dt.size() == n &&
               std::equal(e->graph_dt.begin(), e->graph_dt.end(), dt);
   for (int i = 0; same && i < n; ++i) same = e->graph_gen[i] == e->m[i]->gen;
@@ -261,22 +753,19 @@ tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt) {
       return TC_ERR_CUDA;
     }
   }
-  if (cudaStreamSynchronize(e->s0) != cudaSuccess) {
-    cudaGetLastError();
-    for (tc_ctx *c : e->m) c->poisoned = true;
-    return TC_ERR_CUDA;
-  }
-  tc_status worst = TC_OK;
-  for (int i = 0; i < n; ++i) {
-    tc_ctx *c = e->m[i];
-    DevScalars sc;
-    if (cudaMemcpy(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost) != cudaSuccess)
-      return TC_ERR_CUDA;
-    c->t += dt[i] * nsteps;
-    if (sc.timeout) worst = TC_ERR_TIMEOUT;
-    else if (c->check && sc.nonfinite && worst == TC_OK) worst = TC_ERR_NONFINITE;
-  }
-  return worst;
+  return finish_steps(e, nsteps, dt, false);
+}
+
+tc_status tc_ensemble_set_mode(tc_ens *e, int mode) {
+  if (!e || mode < 0 || mode > 2) return TC_ERR_ARG;
+  e->mode = mode;
+  return TC_OK;
+}
+
+tc_status tc_ensemble_get_mode(const tc_ens *e, int *mode) {
+  if (!e || !mode) return TC_ERR_ARG;
+  *mode = e->mode;
+  return TC_OK;
 }
 
 tc_status tc_autotune(tc_ctx *c, int *tile_mb, int *tile_lb) {
@@ -293,6 +782,10 @@ tc_status tc_autotune(tc_ctx *c, int *tile_mb, int *tile_lb) {
 tc_status tc_ensemble_kernels_per_step(const tc_ens *e, long long *count) {
   if (!e || !count) return TC_ERR_ARG;
   *count = 0;
+  if (e->mode >= 1) {   // one cooperative launch per tc_ensemble_step call
+    *count = e->d_mem ? 1 : 0;
+    return TC_OK;
+  }
   if (!e->graph) return TC_OK;
   size_t nodes = 0;
   if (cudaGraphGetNodes(e->graph, nullptr, &nodes) != cudaSuccess) return TC_ERR_CUDA;

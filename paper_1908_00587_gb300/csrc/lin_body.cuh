@@ -638,9 +638,10 @@ __device__ __forceinline__ double lt_row(const double *row, double (&w)[kBand], 
 // One sweep tile run by the 4 kSweepOps threads tid = 0.. of a group that
 // synchronises with sync() (the whole CTA in k_sweep; a named barrier of the
 // group in the persistent ensemble kernel).  ring_raw: kSweepSmem bytes of
-// shared memory, bars: kSweepStages mbarriers, abort_flag: one shared int,
-// all private to the group.
-template <bool TRANS, typename Sync>
+// shared memory, bars: NST mbarriers, abort_flag: one shared int, all
+// private to the group.  NST: depth of the factor ring (NST in
+// k_sweep; ring_raw holds NST stages of kSweepStageDoubles).
+template <bool TRANS, int NST, typename Sync>
 __device__ __forceinline__ void sweep_body(const SweepArgs &a, DevScalars *sc, int bx, int by,
                                            int bz, int tid, double *ring_raw,
                                            unsigned long long *bars, int *abort_flag,
@@ -671,7 +672,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, DevScalars *sc, i
 
   if (tid == 0) {
     *abort_flag = 0;
-    for (int s = 0; s < kSweepStages; ++s)
+    for (int s = 0; s < NST; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bars[s])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -691,7 +692,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, DevScalars *sc, i
     armed |= 1u << s;
   };
   if (tid == 0)
-    for (int s = 0; s < kSweepStages && s < total; ++s) arm(s, s);
+    for (int s = 0; s < NST && s < total; ++s) arm(s, s);
 
   double w[kBand];
 #pragma unroll
@@ -703,7 +704,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, DevScalars *sc, i
   }
   bool ok = true;
   for (int step = 0; step < total; ++step) {
-    const int s = step % kSweepStages;
+    const int s = step % NST;
     const bool fwd = step < nch;
     const int c = fwd ? step : total - 1 - step;
     const int j0 = c * kSweepRows;
@@ -812,14 +813,20 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, DevScalars *sc, i
       }
     }
     sync();   // every thread is done with stage s
-    if (tid == 0 && step + kSweepStages < total) arm(step + kSweepStages, s);
+    if (tid == 0 && step + NST < total) arm(step + NST, s);
   }
   if (!ok) atomicOr(&sc->timeout, 1);
   if (*abort_flag && tid == 0) {
     // drain the copies still in flight into this CTA's ring, bounded again
-    for (int s = 0; s < kSweepStages; ++s)
+    for (int s = 0; s < NST; ++s)
       if ((armed >> s) & 1u) mbar_wait(smem_u32(&bars[s]), (phase >> s) & 1u);
   }
+  // the barriers are invalidated so that their shared memory can be reused
+  // (the persistent ensemble kernel runs many tiles in the same CTA)
+  sync();
+  if (tid == 0)
+    for (int s = 0; s < NST; ++s)
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(smem_u32(&bars[s])) : "memory");
 }
 
 // Influence coefficients per mode: alpha = -Ainv [div u0 (r_i), div u0 (r_o)].

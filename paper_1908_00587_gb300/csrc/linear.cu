@@ -77,8 +77,8 @@ k_sweep(SweepArgs a, DevScalars *sc) {
   extern __shared__ __align__(128) double ring_raw[];
   __shared__ __align__(8) unsigned long long bars[kSweepStages];
   __shared__ int abort_flag;
-  sweep_body<TRANS>(a, sc, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, ring_raw, bars,
-                    &abort_flag, CtaSync{});
+  sweep_body<TRANS, kSweepStages>(a, sc, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x,
+                                  ring_raw, bars, &abort_flag, CtaSync{});
 }
 
 __global__ void k_alpha(const double *__restrict__ U, double2 *__restrict__ alpha, LinParams p) {

@@ -100,6 +100,8 @@ _SIGS = {
     "tc_ensemble_member": [_P, _I, ctypes.POINTER(_P)],
     "tc_ensemble_step": [_P, _I, _P],
     "tc_ensemble_kernels_per_step": [_P, ctypes.POINTER(ctypes.c_longlong)],
+    "tc_ensemble_set_mode": [_P, _I],
+    "tc_ensemble_get_mode": [_P, ctypes.POINTER(_I)],
     "tc_ensemble_destroy": [_P],
     "tc_autotune": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "tc_debug_flags": [ctypes.POINTER(ctypes.c_uint), _I],
@@ -400,6 +402,18 @@ def tc_ensemble_member(ens, i):
 def tc_ensemble_step(ens, nsteps, dts):
     d = np.ascontiguousarray(dts, dtype=np.float64)
     _check(_lib.tc_ensemble_step(ens, int(nsteps), d.ctypes.data), "tc_ensemble_step")
+
+
+def tc_ensemble_set_mode(ens, mode: int):
+    """1 persistent kernel (default), 0 graph of per-member kernels, 2 the
+    persistent kernel's timeout test hook (see include/tc.h)."""
+    _check(_lib.tc_ensemble_set_mode(ens, int(mode)), "tc_ensemble_set_mode")
+
+
+def tc_ensemble_get_mode(ens) -> int:
+    m = _I(0)
+    _check(_lib.tc_ensemble_get_mode(ens, ctypes.byref(m)), "tc_ensemble_get_mode")
+    return m.value
 
 
 def tc_ensemble_kernels_per_step(ens):

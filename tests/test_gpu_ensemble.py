@@ -1,9 +1,10 @@
-"""Ensemble form: independent runs of uneven size replayed as one CUDA graph.
+"""Ensemble form: independent runs of uneven size in one persistent launch
+(mode 1, default) or replayed as one CUDA graph (mode 0).
 
-Each member must give exactly what the same run gives on its own (the graph
-only changes when and where kernels run; the autotuned tiles only change
-which CTA computes a transform), and small FP64 members are pinned to the
-oracle.  Per-member fixed step: dt = min(1e-3, 0.25 / CFL rate of u0).
+Each member must give exactly what the same run gives on its own (the launch
+mode only changes when and where each CTA tile runs; the autotuned tiles only
+change which CTA computes a transform), and small FP64 members are pinned to
+the oracle.  Per-member fixed step: dt = min(1e-3, 0.25 / CFL rate of u0).
 """
 import numpy as np
 import pytest
@@ -41,9 +42,12 @@ def _init(tc, ctx, wl):
     return min(1e-3, 0.25 / rate), shape
 
 
-def test_ensemble_members_match_single_runs_bitwise(tc):
+@pytest.mark.parametrize("mode", [1, 0], ids=["persistent", "graph"])
+def test_ensemble_members_match_single_runs_bitwise(tc, mode):
     members = [w.scaled(precision=i % 2) for i, w in enumerate(ensemble_members(6))]
     ens = tc.tc_ensemble_create(members, autotune_tiles=True)
+    tc.tc_ensemble_set_mode(ens, mode)
+    assert tc.tc_ensemble_get_mode(ens) == mode
     dts, shapes = [], []
     for i, wl in enumerate(members):
         dt, shape = _init(tc, tc.tc_ensemble_member(ens, i), wl)
@@ -52,8 +56,11 @@ def test_ensemble_members_match_single_runs_bitwise(tc):
         info = tc.tc_get_info(tc.tc_ensemble_member(ens, i))
         assert info.tile_mb >= 1 and info.tile_lb >= 1
     tc.tc_ensemble_step(ens, 7, dts)
-    tc.tc_ensemble_step(ens, 5, dts)       # replay of the same graph
-    assert tc.tc_ensemble_kernels_per_step(ens) > 18 * len(members) - 1
+    tc.tc_ensemble_step(ens, 5, dts)       # the same plan (graph) again
+    if mode == 1:
+        assert tc.tc_ensemble_kernels_per_step(ens) == 1
+    else:
+        assert tc.tc_ensemble_kernels_per_step(ens) > 18 * len(members) - 1
     got = []
     for i in range(len(members)):
         X = np.empty(shapes[i], dtype=np.complex128)
@@ -112,3 +119,25 @@ def test_ensemble_graph_follows_member_options(tc):
     ref = run.get_state()
     run.close()
     np.testing.assert_array_equal(X, ref)
+
+
+def test_persistent_barrier_timeout_is_reported(tc):
+    """Mode 2: CTA 0 of the persistent kernel never arrives at the first grid
+    barrier, so every other CTA's bounded wait (2 s) runs out, the kernel
+    ends and the step reports TC_ERR_TIMEOUT -- no hang, no fault.  The
+    ensemble then steps normally in mode 1."""
+    members = [w.scaled(Nr=20, Ntheta=24, Nz=24) for w in ensemble_members(3)]
+    ens = tc.tc_ensemble_create(members, autotune_tiles=False)
+    dts = [_init(tc, tc.tc_ensemble_member(ens, i), wl)[0] for i, wl in enumerate(members)]
+    tc.tc_ensemble_set_mode(ens, 2)
+    with pytest.raises(tc.TCError) as e:
+        tc.tc_ensemble_step(ens, 1, dts)
+    assert e.value.name == "TC_ERR_TIMEOUT"
+    tc.tc_ensemble_set_mode(ens, 1)
+    tc.tc_ensemble_step(ens, 2, dts)
+    for i in range(len(members)):
+        info = tc.tc_get_info(tc.tc_ensemble_member(ens, i))
+        X = np.empty((info.nfields, info.Nr, info.M + 1, 2 * info.K + 1), dtype=np.complex128)
+        tc.tc_get_state(tc.tc_ensemble_member(ens, i), X)
+        assert np.all(np.isfinite(X))
+    tc.tc_ensemble_destroy(ens)
