@@ -1,10 +1,9 @@
 // Ensemble of independent runs of uneven size on one GPU (batching form).
 //
 // Each member is an ordinary context.  Two ways to step them all:
-//   mode 1 (default): one persistent cooperative kernel (k_ensemble) runs
-//     every step of every member; work items are single CTA tiles of the
-//     step's kernels, pulled stage by stage from per-stage counters, with a
-//     bounded grid barrier between stages;
+//   mode 1 (default): one persistent kernel (k_ensemble) runs every step of
+//     every member; work items are single CTA tiles of the step's kernels,
+//     and each member advances through its stages on its own;
 //   mode 0: one step of every member captured once into a CUDA graph, the
 //     members as independent branches between a fork and a join, replayed
 //     once per step.
@@ -42,9 +41,10 @@ struct tc_ens {
   std::vector<long long> graph_gen;   // members' launch-parameter generations at capture
   // persistent launch (mode 1): member table, item offsets, grid-barrier state
   int mode = 1;
-  void *d_mem = nullptr;     // EnsMember[n] (device)
-  int *d_offs = nullptr;     // item offsets [stage][n + 1] (device)
-  void *d_sync = nullptr;    // EnsSync (device)
+  void *d_mem = nullptr;       // EnsMember[n] (device)
+  int *d_ntiles = nullptr;     // tiles [n][stage] (device)
+  unsigned *d_sched = nullptr; // stage [n], claim and done [n][G] of one launch (device)
+  int *d_fail = nullptr;       // failure flag of the last launch (device)
   size_t smem = 0;
   int grid = 0;
   std::vector<double> plan_dt;
@@ -138,20 +138,22 @@ tc_status autotune(tc_ctx *c, int *best_mb, int *best_lb) {
 // ---------------------------------------------------------------------------
 // Persistent ensemble kernel (mode 1).
 //
-// One cooperative launch runs every step of every member.  A step is the
-// fixed sequence of stages of enqueue_step (n_corr = 1): for each stage the
-// work items of all members -- one CTA tile of that stage's kernel each -- are
-// numbered consecutively, and the resident CTAs pull items from a per-stage
-// counter until the stage is exhausted; a grid barrier then separates it from
-// the next stage.  Members are independent, so the barrier is the only
-// dependency: stage s of every member needs stage s - 1 of the same member,
-// and the barrier provides exactly that (and a little more).  A cooperative
-// launch makes every CTA resident, so the barrier cannot wait for a CTA that
-// is not running; its spin is still bounded (kEnsBarrierNs): a CTA that gives
-// up raises the failure flag, every other CTA leaves at its next barrier, and
-// tc_ensemble_step reports TC_ERR_TIMEOUT.  Each item runs the same device
-// body on the same tile as the member's own kernels, so every member stays
-// bit-identical to the run stepped alone.
+// One launch runs a chunk of steps of every member.  Each member's step is
+// the fixed sequence of stages of enqueue_step (n_corr = 1), and every stage
+// is a set of work items, one CTA tile of that stage's kernel each.  The
+// members advance independently: member m's stage counter g (a global stage
+// index over the chunk's steps) moves to g + 1 when the last tile of stage g
+// is done, and a CTA looking for work scans the members (one lane of warp 0
+// per member) for one whose current stage still has unclaimed tiles, claims
+// the next tile with an atomic counter and runs it.  Nothing waits on a
+// dependency: a tile is only claimed once its stage is current, i.e. once
+// every earlier stage of its member is complete, so latency-bound stages of
+// one member (the radial sweeps) overlap with the transforms of others, as
+// independent kernels would.  A CTA that finds no ready work sleeps and scans
+// again; if that lasts kEnsIdleNs it raises the failure flag, every CTA
+// leaves, and tc_ensemble_step reports TC_ERR_TIMEOUT (a stage that is never
+// published -- the test hook -- ends that way, without a fault).  Each tile
+// runs the same device body as the member's own kernel.
 enum EnsKind : int {
   EK_PREP, EK_ZINV, EK_THETA, EK_ZFWD, EK_DT, EK_FACTH, EK_INFL, EK_RHS, EK_PRHS, EK_SWEEP_P,
   EK_HRHS, EK_SWEEP_H, EK_ALPHA, EK_CORRECT
@@ -177,7 +179,8 @@ constexpr int kEnsSweepStages = 2;    // factor ring depth of those tiles
 constexpr size_t kEnsSweepRing = sizeof(double) * kEnsSweepStages * kSweepStageDoubles;
 constexpr size_t kEnsSweepGroupBytes = kEnsSweepRing + 64;   // + mbarriers and abort flag
 constexpr size_t kEnsSmemBudget = 110 * 1024;   // two CTAs per SM
-constexpr long long kEnsBarrierNs = 2000000000LL;   // 2 s
+constexpr long long kEnsIdleNs = 2000000000LL;   // 2 s without ready work
+constexpr int kEnsMaxChunk = 50;                   // steps per launch
 
 // Launch parameters of one member (device copy; see ens_item).
 struct EnsMember {
@@ -194,10 +197,12 @@ struct EnsMember {
   int mixed, nmb, nlb, nmbf, nprx, nprof, nsw_p, nsw_h, swx;
 };
 
-struct EnsSync {
-  unsigned count, gen;
-  int fail;
-  unsigned ctr[kEnsStages];
+// Scheduler state of one launch (zeroed before it): per member its current
+// global stage, and per (member, global stage) the claimed and done tiles.
+struct EnsSched {
+  unsigned *stage;   // [n]
+  unsigned *claim;   // [n][G]
+  unsigned *done;    // [n][G]
 };
 
 struct GroupSync {
@@ -207,42 +212,8 @@ struct GroupSync {
   }
 };
 
-// Grid barrier of the cooperative launch; the last CTA to arrive also resets
-// the item counter of the stage just finished.  False when the wait ran out
-// or another CTA gave up.
-__device__ bool ens_grid_barrier(EnsSync *g, int st) {
-  __shared__ int ok_s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned *vgen = &g->gen;
-    const unsigned gen0 = *vgen;
-    __threadfence();
-    if (atomicAdd(&g->count, 1u) == gridDim.x - 1) {
-      g->count = 0;
-      g->ctr[st] = 0;
-      __threadfence();
-      atomicAdd(&g->gen, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (*vgen == gen0) {
-        if (*reinterpret_cast<volatile int *>(&g->fail)) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(128);
-        if ((long long)(global_ns() - t0) > kEnsBarrierNs) {
-          atomicExch(&g->fail, 1);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    ok_s = ok;
-  }
-  __syncthreads();
-  return ok_s != 0;
+__device__ __forceinline__ unsigned ld_volatile(const unsigned *p) {
+  return *reinterpret_cast<const volatile unsigned *>(p);
 }
 
 // One work item: tile `t` of stage `d` of member `m`.
@@ -332,33 +303,92 @@ __device__ __forceinline__ void ens_item(const EnsMember &m, EnsStageDef d, int 
 }
 
 __global__ void __launch_bounds__(kEnsThreads, 2)
-k_ensemble(const EnsMember *__restrict__ mem, const int *__restrict__ offs, int nmem, int nsteps,
-           EnsSync *gs, int selftest) {
+k_ensemble(const EnsMember *__restrict__ mem, const int *__restrict__ ntiles, int nmem,
+           int nsteps, EnsSched sch, int *fail, int selftest) {
   extern __shared__ __align__(128) unsigned char ens_smem[];
-  __shared__ int item_s;
-  for (int step = 0; step < nsteps; ++step) {
-    for (int st = 0; st < kEnsStages; ++st) {
-      const int *o = offs + st * (nmem + 1);
-      const int total = o[nmem];
-      const EnsStageDef d = c_ens_stages[st];
-      while (true) {
-        if (threadIdx.x == 0) item_s = atomicAdd(&gs->ctr[st], 1u);
-        __syncthreads();
-        const int it = item_s;
-        __syncthreads();
-        if (it >= total) break;
-        int lo = 0, hi = nmem;   // the member m with o[m] <= it < o[m + 1]
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (o[mid] <= it) lo = mid;
-          else hi = mid;
+  __shared__ int pick_m, pick_t;
+  __shared__ unsigned pick_g;
+  const unsigned G = (unsigned)nsteps * kEnsStages;
+  int start = blockIdx.x % nmem;          // first member this CTA looks at (warp 0, uniform)
+  unsigned long long idle_since = 0ull;   // thread 0: start of the current idle spell
+  while (true) {
+    if (threadIdx.x < 32) {
+      // warp 0 scans 32 members at a time for a current stage with tiles left
+      const int lane = threadIdx.x;
+      int found = -1, nfin = 0;
+      unsigned fg = 0u, ft = 0u;
+      for (int base = 0; base < nmem && found < 0; base += 32) {
+        const int k = base + lane;
+        int m = 0, nt = 0;
+        unsigned g = 0u;
+        bool cand = false, fin = false;
+        if (k < nmem) {
+          m = (start + k) % nmem;
+          g = ld_volatile(&sch.stage[m]);
+          if (g >= G) {
+            fin = true;
+          } else {
+            nt = ntiles[m * kEnsStages + (int)(g % kEnsStages)];
+            if (nt == 0) atomicCAS(&sch.stage[m], g, g + 1u);   // an empty stage passes at once
+            else cand = ld_volatile(&sch.claim[(size_t)m * G + g]) < (unsigned)nt;
+          }
         }
-        ens_item(mem[lo], d, it - o[lo], ens_smem);
-        __syncthreads();
+        nfin += __popc(__ballot_sync(0xffffffffu, fin));
+        unsigned mask = __ballot_sync(0xffffffffu, cand);
+        while (mask && found < 0) {   // try the candidates in lane order
+          const int l = __ffs(mask) - 1;
+          unsigned t = 0u;
+          if (lane == l) t = atomicAdd(&sch.claim[(size_t)m * G + g], 1u);
+          t = __shfl_sync(0xffffffffu, t, l);
+          const int ntl = __shfl_sync(0xffffffffu, nt, l);
+          if (t < (unsigned)ntl) {
+            found = __shfl_sync(0xffffffffu, m, l);
+            fg = __shfl_sync(0xffffffffu, g, l);
+            ft = t;
+          }
+          mask &= mask - 1u;
+        }
       }
-      if (selftest && blockIdx.x == 0) return;   // test hook: never arrive
-      if (!ens_grid_barrier(gs, st)) return;
+      if (found >= 0) start = found;   // every lane: the next scan starts there
+      if (lane == 0) {
+        __threadfence();   // acquire: the claimed stage's inputs are complete
+        pick_m = found >= 0 ? found : (nfin == nmem ? -2 : -1);
+        pick_g = fg;
+        pick_t = (int)ft;
+        if (found >= 0) {
+          idle_since = 0ull;
+        } else if (nfin < nmem) {
+          const unsigned long long now = global_ns();
+          if (idle_since == 0ull) idle_since = now;
+          if (*reinterpret_cast<volatile int *>(fail) ||
+              (long long)(now - idle_since) > kEnsIdleNs) {
+            atomicExch(fail, 1);
+            pick_m = -2;
+          } else {
+            __nanosleep(256);
+          }
+        }
+      }
     }
+    __syncthreads();
+    const int m = pick_m;
+    if (m == -2) break;
+    if (m >= 0) {
+      const unsigned g = pick_g;
+      ens_item(mem[m], c_ens_stages[g % kEnsStages], pick_t, ens_smem);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();   // release: this tile's results before the count
+        const unsigned nt = (unsigned)ntiles[m * kEnsStages + (int)(g % kEnsStages)];
+        const unsigned d = atomicAdd(&sch.done[(size_t)m * G + g], 1u) + 1u;
+        const bool hold = selftest && m == 0 && g == 0u;   // test hook: never publish
+        if (d == nt && !hold) {
+          __threadfence();
+          atomicExch(&sch.stage[m], g + 1u);
+        }
+      }
+    }
+    __syncthreads();   // pick_* is rewritten by the next scan
   }
 }
 
@@ -420,16 +450,18 @@ void fit_tiles(tc_ctx *c, size_t budget) {
 
 void drop_plan(tc_ens *e) {
   if (e->d_mem) cudaFree(e->d_mem);
-  if (e->d_offs) cudaFree(e->d_offs);
-  if (e->d_sync) cudaFree(e->d_sync);
+  if (e->d_ntiles) cudaFree(e->d_ntiles);
+  if (e->d_sched) cudaFree(e->d_sched);
+  if (e->d_fail) cudaFree(e->d_fail);
   e->d_mem = nullptr;
-  e->d_offs = nullptr;
-  e->d_sync = nullptr;
+  e->d_ntiles = nullptr;
+  e->d_sched = nullptr;
+  e->d_fail = nullptr;
   e->plan_dt.clear();
   e->plan_gen.clear();
 }
 
-// Member table and item offsets for the persistent kernel (rebuilt when a
+// Member table and tile counts for the persistent kernel (rebuilt when a
 // member's step or launch parameters change).
 tc_status build_plan(tc_ens *e, const double *dt) {
   const int n = (int)e->m.size();
@@ -494,17 +526,13 @@ tc_status build_plan(tc_ens *e, const double *dt) {
     m.nsw_p = m.swx * s.NM * (m.UT ? 2 : 1);
     m.nsw_h = m.swx * s.NM * 3;
   }
-  std::vector<int> offs((size_t)kEnsStages * (n + 1), 0);
+  std::vector<int> ntiles((size_t)n * kEnsStages, 0);
   long long items = 0;
-  for (int st = 0; st < kEnsStages; ++st) {
-    int acc = 0;
-    for (int i = 0; i < n; ++i) {
-      offs[(size_t)st * (n + 1) + i] = acc;
-      acc += ens_items(mem[i], e->m[i], h_ens_kind[st]);
+  for (int i = 0; i < n; ++i)
+    for (int st = 0; st < kEnsStages; ++st) {
+      ntiles[(size_t)i * kEnsStages + st] = ens_items(mem[i], e->m[i], h_ens_kind[st]);
+      items += ntiles[(size_t)i * kEnsStages + st];
     }
-    offs[(size_t)st * (n + 1) + n] = acc;
-    items += acc;
-  }
   e->items_per_step = items;
   // kernel attributes and a grid of every CTA that can be resident
   if (cudaFuncSetAttribute(k_ensemble, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -522,17 +550,19 @@ tc_status build_plan(tc_ens *e, const double *dt) {
   }
   e->grid = nsm * per;
   e->smem = smem;
+  const size_t words = (size_t)n * (1 + 2 * (size_t)kEnsMaxChunk * kEnsStages);
   if (cudaMalloc(&e->d_mem, sizeof(EnsMember) * n) != cudaSuccess ||
-      cudaMalloc(&e->d_offs, sizeof(int) * offs.size()) != cudaSuccess ||
-      cudaMalloc(&e->d_sync, sizeof(EnsSync)) != cudaSuccess) {
+      cudaMalloc(&e->d_ntiles, sizeof(int) * ntiles.size()) != cudaSuccess ||
+      cudaMalloc(&e->d_sched, sizeof(unsigned) * words) != cudaSuccess ||
+      cudaMalloc(&e->d_fail, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     drop_plan(e);
     return TC_ERR_OOM;
   }
   if (cudaMemcpy(e->d_mem, mem.data(), sizeof(EnsMember) * n, cudaMemcpyHostToDevice) !=
           cudaSuccess ||
-      cudaMemcpy(e->d_offs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess) {
+      cudaMemcpy(e->d_ntiles, ntiles.data(), sizeof(int) * ntiles.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
     drop_plan(e);
     return TC_ERR_CUDA;
@@ -544,9 +574,9 @@ tc_status build_plan(tc_ens *e, const double *dt) {
 }
 
 // nsteps steps of every member in one cooperative launch on e->s0.
-// selftest != 0: CTA 0 leaves before the first grid barrier (test hook of the
-// bounded wait: every other CTA's wait runs out and the step reports
-// TC_ERR_TIMEOUT, without a fault).
+// selftest != 0: the last tile of member 0's first stage is never published
+// (test hook of the bounded idle wait: the other members finish, then every
+// CTA runs out of ready work, and the step reports TC_ERR_TIMEOUT).
 tc_status persistent_steps(tc_ens *e, int nsteps, const double *dt, int selftest) {
   const int n = (int)e->m.size();
   bool same = e->d_mem && (int)e->plan_dt.size() == n &&
@@ -556,20 +586,29 @@ tc_status persistent_steps(tc_ens *e, int nsteps, const double *dt, int selftest
     const tc_status st = build_plan(e, dt);
     if (st != TC_OK) return st;
   }
-  if (cudaMemsetAsync(e->d_sync, 0, sizeof(EnsSync), e->s0) != cudaSuccess) {
+  if (cudaMemsetAsync(e->d_fail, 0, sizeof(int), e->s0) != cudaSuccess) {
     cudaGetLastError();
     return TC_ERR_CUDA;
   }
-  int nm = n;
   const EnsMember *dm = static_cast<const EnsMember *>(e->d_mem);
-  EnsSync *ds = static_cast<EnsSync *>(e->d_sync);
-  void *args[] = {&dm, &e->d_offs, &nm, &nsteps, &ds, &selftest};
-  if (cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_ensemble), dim3(e->grid),
-                                  dim3(kEnsThreads), args, e->smem, e->s0) != cudaSuccess) {
-    std::fprintf(stderr, "libtc: ensemble launch: %s\n", cudaGetErrorString(cudaGetLastError()));
-    return TC_ERR_CUDA;
+  for (int done = 0; done < nsteps;) {
+    const int chunk = std::min(kEnsMaxChunk, nsteps - done);
+    const size_t G = (size_t)chunk * kEnsStages;
+    EnsSched sch{};
+    sch.stage = e->d_sched;
+    sch.claim = e->d_sched + n;
+    sch.done = sch.claim + (size_t)n * G;
+    const size_t words = (size_t)n * (1 + 2 * G);
+    if (cudaMemsetAsync(e->d_sched, 0, sizeof(unsigned) * words, e->s0) != cudaSuccess) {
+      cudaGetLastError();
+      return TC_ERR_CUDA;
+    }
+    k_ensemble<<<e->grid, kEnsThreads, e->smem, e->s0>>>(dm, e->d_ntiles, n, chunk, sch,
+                                                         e->d_fail, selftest);
+    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+    for (tc_ctx *c : e->m) c->launches += 1;
+    done += chunk;
   }
-  for (tc_ctx *c : e->m) c->launches += 1;
   return TC_OK;
 }
 
@@ -583,10 +622,10 @@ tc_status finish_steps(tc_ens *e, int nsteps, const double *dt, bool persistent)
   }
   tc_status worst = TC_OK;
   if (persistent) {
-    EnsSync gs;
-    if (cudaMemcpy(&gs, e->d_sync, sizeof(gs), cudaMemcpyDeviceToHost) != cudaSuccess)
+    int fail = 0;
+    if (cudaMemcpy(&fail, e->d_fail, sizeof(fail), cudaMemcpyDeviceToHost) != cudaSuccess)
       return TC_ERR_CUDA;
-    if (gs.fail) worst = TC_ERR_TIMEOUT;
+    if (fail) worst = TC_ERR_TIMEOUT;
   }
   for (int i = 0; i < n; ++i) {
     tc_ctx *c = e->m[i];
@@ -782,7 +821,7 @@ tc_status tc_autotune(tc_ctx *c, int *tile_mb, int *tile_lb) {
 tc_status tc_ensemble_kernels_per_step(const tc_ens *e, long long *count) {
   if (!e || !count) return TC_ERR_ARG;
   *count = 0;
-  if (e->mode >= 1) {   // one cooperative launch per tc_ensemble_step call
+  if (e->mode >= 1) {   // one persistent launch per tc_ensemble_step call (up to 50 steps)
     *count = e->d_mem ? 1 : 0;
     return TC_OK;
   }
