@@ -391,13 +391,14 @@ tc_status tc_ensemble_member(tc_ens *e, int i, tc_ctx **ctx);
 
 /* Advance every member nsteps steps of its own fixed dt (host array of n
  * values > 0), in the ensemble's launch mode (tc_ensemble_set_mode):
- *   1 (default) one persistent cooperative kernel launch runs all nsteps
- *     steps of every member: the work items are the CTA tiles of the step's
- *     kernels, numbered member after member for each stage of the
- *     predictor-corrector step; resident CTAs pull items from a per-stage
- *     counter and a grid barrier separates the stages.  Every wait in it is
- *     bounded (2 s for the barrier, 1 s for the sweeps' copies); a wait that
- *     runs out makes the call return TC_ERR_TIMEOUT without a fault.  It runs
+ *   1 (default) one persistent kernel launch (per 50 steps) runs the steps
+ *     of every member: the work items are the CTA tiles of the step's
+ *     kernels; each member moves to its next stage of the predictor-corrector
+ *     step when its current stage's tiles are done, and resident CTAs claim
+ *     ready tiles of any member, so the members proceed independently.
+ *     Nothing in it waits on another CTA; a CTA that finds no ready work for
+ *     2 s, or a sweep copy that does not land within 1 s, makes the call
+ *     return TC_ERR_TIMEOUT without a fault.  It runs
  *     the default scheme: while any member has n_corr != 1, the flux
  *     constraint or the sweep test hook, the call steps in mode 0 instead.
  *     It shrinks transform tiles that do not fit its shared-memory budget
@@ -415,10 +416,12 @@ tc_status tc_ensemble_member(tc_ens *e, int i, tc_ctx **ctx);
 tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt);
 
 /* Launch mode of tc_ensemble_step: 1 persistent kernel (default), 0 graph of
- * per-member kernels, 2 persistent kernel with its test hook -- CTA 0 leaves
- * before the first grid barrier, so every other CTA's bounded wait runs out
- * and tc_ensemble_step returns TC_ERR_TIMEOUT (the members' states are then
- * those before the call's first corrector).  Errors: TC_ERR_ARG. */
+ * per-member kernels, 2 persistent kernel with its test hook -- the end of
+ * member 0's first transform stage is never published, so that member never
+ * becomes ready again; the others finish, every CTA's bounded idle wait (2 s)
+ * runs out and tc_ensemble_step returns TC_ERR_TIMEOUT (member 0's state is
+ * then the one before the call, the others have stepped).  Errors:
+ * TC_ERR_ARG. */
 tc_status tc_ensemble_set_mode(tc_ens *e, int mode);
 tc_status tc_ensemble_get_mode(const tc_ens *e, int *mode);
 

@@ -381,7 +381,9 @@ k_ensemble(const EnsMember *__restrict__ mem, const int *__restrict__ ntiles, in
         __threadfence();   // release: this tile's results before the count
         const unsigned nt = (unsigned)ntiles[m * kEnsStages + (int)(g % kEnsStages)];
         const unsigned d = atomicAdd(&sch.done[(size_t)m * G + g], 1u) + 1u;
-        const bool hold = selftest && m == 0 && g == 0u;   // test hook: never publish
+        // test hook: member 0's first transform stage (global stage 1, never
+        // empty) is never published
+        const bool hold = selftest && m == 0 && g == 1u;
         if (d == nt && !hold) {
           __threadfence();
           atomicExch(&sch.stage[m], g + 1u);
@@ -574,7 +576,7 @@ tc_status build_plan(tc_ens *e, const double *dt) {
 }
 
 // nsteps steps of every member in one cooperative launch on e->s0.
-// selftest != 0: the last tile of member 0's first stage is never published
+// selftest != 0: member 0's first transform stage is never published
 // (test hook of the bounded idle wait: the other members finish, then every
 // CTA runs out of ready work, and the step reports TC_ERR_TIMEOUT).
 tc_status persistent_steps(tc_ens *e, int nsteps, const double *dt, int selftest) {

@@ -130,11 +130,12 @@ def test_ensemble_graph_follows_member_options(tc):
     np.testing.assert_array_equal(X, ref)
 
 
-def test_persistent_barrier_timeout_is_reported(tc):
-    """Mode 2: CTA 0 of the persistent kernel never arrives at the first grid
-    barrier, so every other CTA's bounded wait (2 s) runs out, the kernel
-    ends and the step reports TC_ERR_TIMEOUT -- no hang, no fault.  The
-    ensemble then steps normally in mode 1."""
+def test_persistent_unpublished_stage_times_out(tc):
+    """Mode 2: the end of member 0's first transform stage is never published,
+    so that member never has ready work again; the others finish, every CTA's
+    bounded idle wait (2 s) runs out, the kernel ends and the step reports
+    TC_ERR_TIMEOUT -- no hang, no fault.  The ensemble then steps normally
+    in mode 1."""
     members = [w.scaled(Nr=20, Ntheta=24, Nz=24) for w in ensemble_members(3)]
     ens = tc.tc_ensemble_create(members, autotune_tiles=False)
     dts = [_init(tc, tc.tc_ensemble_member(ens, i), wl)[0] for i, wl in enumerate(members)]
