@@ -216,7 +216,36 @@ __device__ __forceinline__ unsigned ld_volatile(const unsigned *p) {
   return *reinterpret_cast<const volatile unsigned *>(p);
 }
 
-// One work item: tile `t` of stage `d` of member `m`.
+// Tiles per claim, by stage kind: a claim covers that many consecutive tiles
+// (the scan and the counters cost about as much as a small tile).
+__constant__ int c_ens_batch[] = {8, 4, 2, 4, 1, 1, 1, 8, 2, 1, 8, 1, 8, 8};
+const int h_ens_batch[] = {8, 4, 2, 4, 1, 1, 1, 8, 2, 1, 8, 1, 8, 8};
+
+// Tiles of a stage kind for one member (one CTA tile of that kind's kernel
+// each; the sweeps count tile pairs).
+__host__ __device__ __forceinline__ int ens_tiles(const EnsMember &m, int kind) {
+  const Sizes &s = m.lin.sz;
+  auto cd = [](long long a, long long b) { return (int)((a + b - 1) / b); };
+  switch (kind) {
+    case EK_PREP: return m.mixed ? m.nprof + cd((long long)s.nf * s.S, kEnsThreads) : 0;
+    case EK_ZINV: return m.nmb * s.Nr * s.nf;
+    case EK_THETA: return m.nlb * s.Nr;
+    case EK_ZFWD: return m.nmbf * s.Nr;
+    case EK_DT: return 1;
+    case EK_FACTH: return cd(m.lin.nopH + m.lin.nopT, kEnsThreads);
+    case EK_INFL: return cd(m.lin.nopP, kEnsThreads);
+    case EK_RHS:
+    case EK_HRHS:
+    case EK_CORRECT: return cd(s.S, kEnsThreads);
+    case EK_PRHS: return m.nprx * cd(s.Nr, kPrL);
+    case EK_SWEEP_P: return cd(m.nsw_p, kEnsSweepGroups);
+    case EK_SWEEP_H: return cd(m.nsw_h, kEnsSweepGroups);
+    case EK_ALPHA: return cd(2LL * s.nmode, kEnsThreads);
+  }
+  return 0;
+}
+
+// One tile: tile `t` of stage `d` of member `m`.
 __device__ __forceinline__ void ens_item(const EnsMember &m, EnsStageDef d, int t,
                                          unsigned char *smem) {
   const Sizes &s = m.lin.sz;
@@ -375,8 +404,13 @@ k_ensemble(const EnsMember *__restrict__ mem, const int *__restrict__ ntiles, in
     if (m == -2) break;
     if (m >= 0) {
       const unsigned g = pick_g;
-      ens_item(mem[m], c_ens_stages[g % kEnsStages], pick_t, ens_smem);
-      __syncthreads();
+      const EnsStageDef d = c_ens_stages[g % kEnsStages];
+      const int B = c_ens_batch[d.kind];
+      const int t1 = min((pick_t + 1) * B, ens_tiles(mem[m], d.kind));
+      for (int t = pick_t * B; t < t1; ++t) {
+        ens_item(mem[m], d, t, ens_smem);
+        __syncthreads();   // the tile's shared memory is free for the next one
+      }
       if (threadIdx.x == 0) {
         __threadfence();   // release: this tile's results before the count
         const unsigned nt = (unsigned)ntiles[m * kEnsStages + (int)(g % kEnsStages)];
@@ -408,26 +442,10 @@ SweepArgs sweep_args_of(const tc_ctx *c) {
   return a;
 }
 
-// Items of stage kind k for one member (host).
-int ens_items(const EnsMember &m, const tc_ctx *c, int k) {
-  const Sizes &s = c->sz;
-  switch (k) {
-    case EK_PREP: return m.mixed ? m.nprof + cdiv((long long)s.nf * s.S, kEnsThreads) : 0;
-    case EK_ZINV: return m.nmb * s.Nr * s.nf;
-    case EK_THETA: return m.nlb * s.Nr;
-    case EK_ZFWD: return m.nmbf * s.Nr;
-    case EK_DT: return 1;
-    case EK_FACTH: return cdiv(c->lin.nopH + c->lin.nopT, kEnsThreads);
-    case EK_INFL: return cdiv(c->lin.nopP, kEnsThreads);
-    case EK_RHS:
-    case EK_HRHS:
-    case EK_CORRECT: return cdiv(s.S, kEnsThreads);
-    case EK_PRHS: return m.nprx * cdiv(s.Nr, kPrL);
-    case EK_SWEEP_P: return cdiv(m.nsw_p, kEnsSweepGroups);
-    case EK_SWEEP_H: return cdiv(m.nsw_h, kEnsSweepGroups);
-    case EK_ALPHA: return cdiv(2LL * s.nmode, kEnsThreads);
-  }
-  return 0;
+// Claims of stage kind k for one member (host): its tiles in batches.
+int ens_items(const EnsMember &m, int k) {
+  const int tiles = ens_tiles(m, k);
+  return (tiles + h_ens_batch[k] - 1) / h_ens_batch[k];
 }
 
 // Largest transform-tile shared memory of a context in its precision.
@@ -532,7 +550,7 @@ tc_status build_plan(tc_ens *e, const double *dt) {
   long long items = 0;
   for (int i = 0; i < n; ++i)
     for (int st = 0; st < kEnsStages; ++st) {
-      ntiles[(size_t)i * kEnsStages + st] = ens_items(mem[i], e->m[i], h_ens_kind[st]);
+      ntiles[(size_t)i * kEnsStages + st] = ens_items(mem[i], h_ens_kind[st]);
       items += ntiles[(size_t)i * kEnsStages + st];
     }
   e->items_per_step = items;
