@@ -391,7 +391,7 @@ tc_status tc_ensemble_member(tc_ens *e, int i, tc_ctx **ctx);
 
 /* Advance every member nsteps steps of its own fixed dt (host array of n
  * values > 0), in the ensemble's launch mode (tc_ensemble_set_mode):
- *   1 (default) one persistent kernel launch (per 50 steps) runs the steps
+ *   1 one persistent kernel launch (per 50 steps) runs the steps
  *     of every member: the work items are the CTA tiles of the step's
  *     kernels; each member moves to its next stage of the predictor-corrector
  *     step when its current stage's tiles are done, and resident CTAs claim
@@ -403,9 +403,12 @@ tc_status tc_ensemble_member(tc_ens *e, int i, tc_ctx **ctx);
  *     constraint or the sweep test hook, the call steps in mode 0 instead.
  *     It shrinks transform tiles that do not fit its shared-memory budget
  *     (results do not depend on tiles).
- *   0 one step of all members captured once into a CUDA graph (independent
- *     branches run concurrently) and replayed nsteps times; re-captured when a
- *     dt or a member option changes.
+ *   0 (default) one step of all members captured once into a CUDA graph
+ *     (independent branches run concurrently) and replayed nsteps times;
+ *     re-captured when a dt or a member option changes.  It is the default
+ *     because it is faster: the persistent kernel is compiled for the
+ *     register demand of its largest body (16 warps per SM), the members'
+ *     own kernels run with more warps.
  * Mode 0 is bit-identical to each member stepped alone.  Mode 1 computes the
  * same tiles with the same device code, but compiled into one kernel, where
  * the compiler may fuse multiplies and adds differently: it agrees with the
@@ -415,8 +418,8 @@ tc_status tc_ensemble_member(tc_ens *e, int i, tc_ctx **ctx);
  * a synchronisation. */
 tc_status tc_ensemble_step(tc_ens *e, int nsteps, const double *dt);
 
-/* Launch mode of tc_ensemble_step: 1 persistent kernel (default), 0 graph of
- * per-member kernels, 2 persistent kernel with its test hook -- the end of
+/* Launch mode of tc_ensemble_step: 0 graph of per-member kernels (default),
+ * 1 persistent kernel, 2 persistent kernel with its test hook -- the end of
  * member 0's first transform stage is never published, so that member never
  * becomes ready again; the others finish, every CTA's bounded idle wait (2 s)
  * runs out and tc_ensemble_step returns TC_ERR_TIMEOUT (member 0's state is

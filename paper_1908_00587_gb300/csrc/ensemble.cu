@@ -1,12 +1,16 @@
 // Ensemble of independent runs of uneven size on one GPU (batching form).
 //
 // Each member is an ordinary context.  Two ways to step them all:
-//   mode 1 (default): one persistent kernel (k_ensemble) runs every step of
-//     every member; work items are single CTA tiles of the step's kernels,
-//     and each member advances through its stages on its own;
-//   mode 0: one step of every member captured once into a CUDA graph, the
-//     members as independent branches between a fork and a join, replayed
-//     once per step.
+//   mode 0 (default): one step of every member captured once into a CUDA
+//     graph, the members as independent branches between a fork and a join,
+//     replayed once per step;
+//   mode 1: one persistent kernel (k_ensemble) runs every step of every
+//     member; work items are single CTA tiles of the step's kernels, and each
+//     member advances through its stages on its own.
+// Mode 0 is the default because it is faster: the persistent kernel is one
+// function compiled for the register demand of its largest body (128 per
+// thread, 16 warps per SM), while the members' own kernels run at 24 to 64
+// warps per SM, and its sweep tiles leave half of a CTA idle.
 // Both run exactly the arithmetic of the member stepped alone.
 //
 // Tiles: before the first step, each size class (Nr, Ntheta, Nz, fields,
@@ -40,7 +44,7 @@ struct tc_ens {
   std::vector<double> graph_dt;
   std::vector<long long> graph_gen;   // members' launch-parameter generations at capture
   // persistent launch (mode 1): member table, item offsets, grid-barrier state
-  int mode = 1;
+  int mode = 0;
   void *d_mem = nullptr;       // EnsMember[n] (device)
   int *d_ntiles = nullptr;     // tiles [n][stage] (device)
   unsigned *d_sched = nullptr; // stage [n], claim and done [n][G] of one launch (device)

@@ -405,7 +405,7 @@ def tc_ensemble_step(ens, nsteps, dts):
 
 
 def tc_ensemble_set_mode(ens, mode: int):
-    """1 persistent kernel (default), 0 graph of per-member kernels, 2 the
+    """0 graph of per-member kernels (default), 1 persistent kernel, 2 the
     persistent kernel's timeout test hook (see include/tc.h)."""
     _check(_lib.tc_ensemble_set_mode(ens, int(mode)), "tc_ensemble_set_mode")
 

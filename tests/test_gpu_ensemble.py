@@ -1,5 +1,5 @@
-"""Ensemble form: independent runs of uneven size in one persistent launch
-(mode 1, default) or replayed as one CUDA graph (mode 0).
+"""Ensemble form: independent runs of uneven size replayed as one CUDA graph
+(mode 0, default) or in one persistent launch (mode 1).
 
 Each member must give exactly what the same run gives on its own (the launch
 mode only changes when and where each CTA tile runs; the autotuned tiles only
@@ -155,11 +155,12 @@ def test_persistent_unpublished_stage_times_out(tc):
 
 def test_persistent_mode_steps_unsupported_schemes_as_graph(tc):
     """With a member on a scheme the persistent kernel does not run (n_corr =
-    2), the default mode steps that call as the graph of member kernels:
+    2), the persistent mode steps that call as the graph of member kernels:
     the member then equals the run alone bit for bit."""
     members = [w.scaled(Nr=20, Ntheta=24, Nz=24) for w in ensemble_members(2)]
     ens = tc.tc_ensemble_create(members, autotune_tiles=False)
-    assert tc.tc_ensemble_get_mode(ens) == 1
+    assert tc.tc_ensemble_get_mode(ens) == 0
+    tc.tc_ensemble_set_mode(ens, 1)
     dts, shapes = [], []
     for i, wl in enumerate(members):
         dt, shape = _init(tc, tc.tc_ensemble_member(ens, i), wl)
