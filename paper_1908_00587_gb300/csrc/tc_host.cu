@@ -725,6 +725,13 @@ tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz, double Re
     upload_tables(c);
     setup_nonlinear(c);
     setup_linear(c);
+    if (theta_tc_supported(s)) {   // the DFT matrix's slices for the tensor-core transforms
+      std::vector<unsigned short> tab;
+      build_theta_dft(s.Nt, s.M, tab);
+      c->d_dft_tc = dalloc<unsigned char>(c, theta_tc_table_bytes());
+      ck(cudaMemcpy(c->d_dft_tc, tab.data(), theta_tc_table_bytes(), cudaMemcpyHostToDevice));
+      setup_theta_tc();
+    }
     if (c->smem_zinv > 227 * 1024 || c->smem_theta > 227 * 1024 || c->smem_zfwd > 227 * 1024 ||
         c->smem32_zinv > 227 * 1024 || c->smem32_theta > 227 * 1024 ||
         c->smem32_zfwd > 227 * 1024) {
@@ -840,6 +847,9 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
   } else if (k == "memory_budget") {
     if (v < 0.0 || v != std::floor(v) || v > 9.0e15) return TC_ERR_ARG;
     c->mem_budget = (size_t)v;
+  } else if (k == "tensor_theta") {
+    if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
+    c->tensor_theta = (int)v;
   } else if (k == "selftest_no_copy") {
     c->selftest_no_copy = v != 0.0;
   } else if (k == "timing") {

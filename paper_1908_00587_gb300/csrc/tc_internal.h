@@ -255,6 +255,10 @@ struct tc_ctx {
   int capturing = 0;            // a graph is capturing this context's stream
   int tile_mb = 0, tile_lb = 0, tile_mbf = 0;   // nonlinear-stage tile overrides (0: default)
   int n_corr = 1;               // corrector passes per step
+  // azimuthal transforms on the tensor cores (theta_tc.cu): the DFT matrix's
+  // BF16 slices (device, null when the size is not supported) and the option
+  unsigned char *d_dft_tc = nullptr;
+  int tensor_theta = 1;
   int flux = 0;                 // axial-flux constraint on the (0,0) u_z mode
   double eps_c = 0.0;           // centrifugal buoyancy coefficient
   double *flux_ug = nullptr;    // device (Nr): unit-forcing response of the (0,0) u_z operator
@@ -349,5 +353,15 @@ void launch_symmetrise(tc_ctx *c, double2 *X);
 
 // diag.cu
 void launch_diagnostics(tc_ctx *c);
+
+// theta_tc.cu: the inverse azimuthal transforms of the FP64 nonlinear stage
+// as BF16 slice products on the tensor cores (FP64-accurate), then the
+// products and the forward transform as in k_theta
+bool theta_tc_supported(const Sizes &s);
+size_t theta_tc_table_bytes();
+void build_theta_dft(int Nt, int M, std::vector<unsigned short> &out);
+void setup_theta_tc();
+void launch_theta_tc(cudaStream_t st, const double2 *V, double2 *W, const NLParams &p,
+                     const unsigned char *dft, unsigned long long *rate_bits, int *timeout);
 
 }  // namespace tc

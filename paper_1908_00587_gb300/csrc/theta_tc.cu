@@ -1,0 +1,524 @@
+// Azimuthal transforms of the FP64 nonlinear stage on the tensor cores.
+//
+// The inverse theta transform of k_theta (Sec. 2.1: Fourier-Galerkin in
+// theta) is a dense contraction: for every radial level and z row, the
+// physical values of each real field are u(theta_j) = sum_k F_jk x_k with
+// x = (Re a_0, Re a_1..Re a_M, Im a_1..Im a_M) and F_j0 = 1,
+// F_jm = 2 cos(m theta_j), F_j(M+m) = -2 sin(m theta_j).  k_theta_tc forms
+// these products with tcgen05.mma in BF16 at FP64 accuracy by splitting both
+// operands into 7 slices of 8 significant bits (Ozaki et al., "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication", Numer. Algorithms 59, 2012):
+//   F/2      = sum_i A_i 2^-8,  A_i = a_i 2^-8i,  a_i integers in [-256, 256]
+//   x/2^E    = sum_j B_j 2^-8,  B_j = b_j 2^-8j  (E: exponent of the column)
+// Every product A_i B_j is exact in BF16 x BF16 -> FP32, and the sum over the
+// at most 96 coefficients of all pairs with i + j = L is exact in an FP32
+// accumulator for L <= 3 (at most 4 pairs x 96 terms of at most 2^16);
+// levels 4..6 share one accumulator whose rounding is 2^-24 of a term that
+// is itself below 2^-32 of the result.  The pairs with i + j > 6 are below
+// 2^-56 of the result and are not formed (28 of the 49 slice products).  The
+// five accumulators are combined exactly in 64-bit integers and rounded once
+// to FP64.  The theta derivative is the same product applied to i m a_m.
+//
+// The rest of the stage is k_theta's: the products u.grad u (with curvature
+// terms, buoyancy and the CFL rate) in FP64 on the physical grid, then the
+// forward theta FFT in FP64 and the unpacking into W.
+//
+// Data path of one CTA (LB z rows of one radial level, 48 data columns):
+//   1. all threads: read V, slice the 48 columns into 7 BF16 operand tiles in
+//      shared memory (K-major core-matrix layout, no swizzle), one exponent
+//      per column;
+//   2. thread 0: stream the 14 half-slices of the DFT matrix (each 128 rows x
+//      48 coefficients, 12 KB, already in the operand layout) with 1-D bulk
+//      copies into a two-deep ring and issue the 28 x 6 MMAs (M 128, N 48,
+//      K 16) into five TMEM accumulators of 48 columns;
+//   3. warps 0-3: read the accumulators (lane = theta row), combine them and
+//      write the physical fields (FP64) to shared memory;
+//   4. all threads: products, forward FFT, unpack (as k_theta).
+// Every wait is bounded (1 s); a wait that runs out sets the timeout flag of
+// the context and the CTA frees its tensor memory and returns.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "fft.cuh"
+#include "nl_body.cuh"
+#include "tc_internal.h"
+
+namespace tc {
+namespace {
+
+constexpr int kTcM = 128;      // theta rows per MMA (Ntheta <= 128; zero rows beyond)
+constexpr int kTcK = 96;       // real coefficients per data column, padded (2M + 1 <= 96)
+constexpr int kTcN = 48;       // data columns per CTA: LB z rows x 4 nf real fields
+constexpr int kTcS = 7;        // slices of each operand
+constexpr int kTcAcc = 5;      // accumulators: levels 0..3 exact, levels 4..6 together
+constexpr int kTcHalfK = 48;   // coefficients per streamed half-slice of the DFT matrix
+constexpr int kTcStages = 2 * kTcS;
+constexpr int kTcThreads = 256;
+// Operand layouts in shared memory (K-major, no swizzle): core matrices of 8
+// rows x 16 bytes (8 BF16), the K-neighbour of a core matrix 128 B further,
+// the next group of 8 rows one K extent further.
+constexpr int kTcBSlice = (kTcN / 8) * (kTcK / 8) * 128;       // 9216 B per data slice
+constexpr int kTcBBytes = kTcS * kTcBSlice;                     // 64512
+constexpr int kTcAHalf = (kTcM / 8) * (kTcHalfK / 8) * 128;    // 12288 B per half-slice
+constexpr int kTcSmem = kTcBBytes + 2 * kTcAHalf;               // 89088
+constexpr int kTcTmemCols = 256;
+constexpr long long kTcWaitNs = 1000000000LL;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int b_off(int n, int k) {   // data operand, one slice
+  return ((n >> 3) * (kTcK / 8) + (k >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr & 0x3FFFFu) >> 4) |
+         ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned phase) {
+  unsigned ok = 0;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+    if (ok) return true;
+    if ((long long)(global_ns() - t0) > kTcWaitNs) return false;
+  }
+}
+
+// BF16 bits of d * 2^(-8 s) for an integer |d| <= 256 (exact).
+__device__ __forceinline__ unsigned short bf16_digit(int d, int s) {
+  if (d == 0) return 0;
+  const unsigned sgn = d < 0 ? 0x8000u : 0u;
+  const unsigned a = (unsigned)(d < 0 ? -d : d);
+  const int e = 31 - __clz(a);                     // 0..8
+  const unsigned mant = e >= 7 ? (a >> (e - 7)) & 0x7Fu : (a << (7 - e)) & 0x7Fu;
+  return (unsigned short)(sgn | ((unsigned)(127 + e - 8 * s) << 7) | mant);
+}
+
+// round(|x| * 2^(56 - E)) with the sign of x, exactly (x finite, |x| < 2^E).
+__device__ __forceinline__ long long scaled_int(double x, int E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int be = (int)((b >> 52) & 0x7FF);
+  unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  if (be == 0 && mant == 0) return 0;
+  int ex;
+  if (be == 0) {
+    ex = -1022;
+  } else {
+    mant |= 1ull << 52;
+    ex = be - 1023;
+  }
+  const int sh = ex + 4 - E;   // x = mant 2^(ex - 52): result = mant 2^(ex + 4 - E)
+  unsigned long long q;
+  if (sh >= 0) {
+    q = mant << sh;            // sh <= 3 since |x| < 2^E
+  } else if (sh < -60) {
+    q = 0;
+  } else {
+    const int r = -sh;
+    q = mant >> r;
+    const unsigned long long rem = mant & ((1ull << r) - 1ull);
+    const unsigned long long half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+  }
+  return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+// Nearest double to a 64-bit integer, as bits (round to nearest even).
+__device__ __forceinline__ unsigned long long ll_to_double_bits(long long v) {
+  if (v == 0) return 0ull;
+  const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll(u);
+  u <<= lz;                                             // bit 63 set
+  unsigned long long frac = (u >> 11) & 0xFFFFFFFFFFFFFull;
+  const unsigned long long rb = (u >> 10) & 1ull, st = u & 0x3FFull;
+  unsigned long long bits = ((unsigned long long)(63 - lz + 1023) << 52) + frac;
+  if (rb && (st || (frac & 1ull))) ++bits;              // carries into the exponent if needed
+  return sgn | bits;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 2)
+k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
+           const unsigned char *__restrict__ dft, unsigned long long *__restrict__ rate_bits,
+           int *__restrict__ timeout, int LB) {
+  const Sizes &s = p.sz;
+  const int l0 = blockIdx.x * LB;
+  const int nl = min(LB, s.Nz - l0);
+  const int r = blockIdx.y;
+  const int Nt = s.Nt;
+  const int Ntp = padlen(Nt);
+  const int M = s.M;
+  const int ncol = 4 * s.nf;                      // data columns per z row
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char *sB = sm;
+  unsigned char *sA = sm + kTcBBytes;
+  __shared__ __align__(8) unsigned long long bars[5];   // full[2], free[2], done
+  __shared__ unsigned tmem_s;
+  __shared__ int colE[kTcN];
+  __shared__ int abort_s;
+  __shared__ unsigned long long cfl_cta[3];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_s)), "r"(kTcTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    abort_s = 0;
+    for (int i = 0; i < 5; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bars[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < 3) cfl_cta[tid] = 0ull;
+  __syncthreads();
+  // the first two half-slices of the DFT matrix
+  auto load_a = [&](int st) {
+    const unsigned bar = smem_u32(&bars[st & 1]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(bar), "r"((unsigned)kTcAHalf) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(smem_u32(sA + (st & 1) * kTcAHalf)), "l"(dft + (size_t)st * kTcAHalf),
+           "r"((unsigned)kTcAHalf), "r"(bar)
+        : "memory");
+  };
+  if (tid == 0) {
+    load_a(0);
+    load_a(1);
+  }
+
+  // 1. the data columns of this tile, sliced.  Column n = li ncol + 4 c + q:
+  // z row li, field c, q = 0 value, 1 theta derivative, 2 d/dr, 3 d/dz.
+  // Coefficient k: 0 -> Re a_0, 1..M -> Re a_k, M+1..2M -> Im a_(k-M).
+  const long long fs = (long long)s.Nr * s.Nz * s.NM;
+  for (int n = warp; n < kTcN; n += kTcThreads / 32) {
+    const int li = n / ncol, cq = n - li * ncol, c = cq >> 2, q = cq & 3;
+    double x[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int k = lane + 32 * u;
+      double v = 0.0;
+      if (li < nl && k <= 2 * M) {
+        const int m = k <= M ? k : k - M;
+        const bool im = k > M;
+        const int d = q <= 1 ? 0 : q - 1;
+        const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
+        const long long iv = (3 * c + d) * fs + off;
+        if (dbg_in(iv, 3LL * s.nf * fs, DBG_THETA_V)) {
+          const double2 a = Vin[iv];
+          if (q == 1)   // i m a_m: Re = -m Im a_m, Im = m Re a_m
+            v = im ? (double)m * a.x : -(double)m * a.y;
+          else
+            v = im ? a.y : a.x;
+        }
+      }
+      x[u] = v;
+    }
+    // exponent of the column: E with max |x| < 2^E
+    unsigned long long mb = 0ull;
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      mb = max(mb, (unsigned long long)__double_as_longlong(x[u]) & 0x7FFFFFFFFFFFFFFFull);
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    const int E = mb ? (int)((mb >> 52) & 0x7FF) - 1022 : 0;   // 2^(e) <= max < 2^(e+1) = 2^E
+    if (lane == 0) colE[n] = E;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int k = lane + 32 * u;
+      long long y = scaled_int(x[u], E);
+      int dig[kTcS];
+#pragma unroll
+      for (int sl = kTcS - 1; sl >= 1; --sl) {
+        int lo = (int)(y & 255ll);
+        if (lo >= 128) lo -= 256;
+        dig[sl] = lo;
+        y = (y - lo) >> 8;
+      }
+      dig[0] = (int)y;
+#pragma unroll
+      for (int sl = 0; sl < kTcS; ++sl)
+        *reinterpret_cast<unsigned short *>(sB + sl * kTcBSlice + b_off(n, k)) =
+            bf16_digit(dig[sl], sl);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_s;
+
+  // 2. the slice products (thread 0 issues them)
+  if (tid == 0) {
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                           ((unsigned)(kTcN >> 3) << 17) | ((unsigned)(kTcM >> 4) << 24);
+    unsigned inited = 0u;
+    bool ok = true;
+    for (int st = 0; st < kTcStages && ok; ++st) {
+      const int i = st >> 1, h = st & 1, buf = st & 1;
+      if (!tc_wait(smem_u32(&bars[buf]), (unsigned)(st >> 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned abase = smem_u32(sA + buf * kTcAHalf);
+      for (int j = 0; j + i < kTcS; ++j) {
+        const int L = i + j;
+        const int acc = L < kTcAcc - 1 ? L : kTcAcc - 1;
+        const unsigned dcol = tmem + (unsigned)(acc * kTcN);
+        const unsigned bbase = smem_u32(sB + j * kTcBSlice);
+#pragma unroll
+        for (int t = 0; t < kTcHalfK / 16; ++t) {
+          const unsigned long long ad = tc_desc(abase + t * 256, 128, (kTcHalfK / 8) * 128);
+          const unsigned long long bd =
+              tc_desc(bbase + (h * (kTcHalfK / 8) + 2 * t) * 128, 128, (kTcK / 8) * 128);
+          const unsigned en = (inited >> acc) & 1u;
+          inited |= 1u << acc;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+              :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(en) : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&bars[2 + buf])) : "memory");
+      // refill the buffer of the previous stage once its products are done
+      if (st >= 1 && st + 1 < kTcStages) {
+        const int pb = (st - 1) & 1;
+        if (!tc_wait(smem_u32(&bars[2 + pb]), (unsigned)((st - 1) >> 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        load_a(st + 1);
+      }
+    }
+    if (ok)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&bars[4])) : "memory");
+    else
+      abort_s = 1;
+  }
+  __syncthreads();
+  bool done = abort_s == 0 && tc_wait(smem_u32(&bars[4]), 0u);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!done) {
+    if (tid == 0) atomicOr(timeout, 1);
+    // drain the copies still in flight into this CTA (bounded)
+    if (tid == 0) {
+      tc_wait(smem_u32(&bars[0]), 0u);
+      tc_wait(smem_u32(&bars[1]), 0u);
+    }
+  }
+  // 3. accumulators -> physical fields P[n][j] (FP64), lane = theta row
+  double *P = reinterpret_cast<double *>(sm);   // over the data slices: the products are done
+  if (done && warp < 4) {
+    const int j = warp * 32 + lane;
+    for (int cb = 0; cb < kTcN / 16; ++cb) {
+      unsigned v[kTcAcc][16];
+#pragma unroll
+      for (int a = 0; a < kTcAcc; ++a) {
+        const unsigned ta = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(a * kTcN + cb * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]),
+              "=r"(v[a][5]), "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]),
+              "=r"(v[a][10]), "=r"(v[a][11]), "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]),
+              "=r"(v[a][15])
+            : "r"(ta));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int n = cb * 16 + t;
+        // level L holds (integer) x 2^(-8L); in units of 2^-36 of level 0
+        long long I = (long long)__float2int_rn(__uint_as_float(v[0][t])) << 36;
+        I += (long long)__float2int_rn(__uint_as_float(v[1][t]) * 256.0f) << 28;
+        I += (long long)__float2int_rn(__uint_as_float(v[2][t]) * 65536.0f) << 20;
+        I += (long long)__float2int_rn(__uint_as_float(v[3][t]) * 16777216.0f) << 12;
+        I += (long long)__float2int_rn(__uint_as_float(v[4][t]) * 68719476736.0f);
+        // value = I 2^-36 2^-16 2^(E+1): F/2 and x/2^E each carry a 2^-8
+        unsigned long long bits = ll_to_double_bits(I);
+        if (bits & 0x7FFFFFFFFFFFFFFFull) bits += (unsigned long long)(long long)(colE[n] - 51) << 52;
+        P[n * kTcM + j] = __longlong_as_double((long long)bits);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(tmem), "r"(kTcTmemCols) : "memory");
+  if (!done) return;
+
+  // 4. products on the physical grid (as k_theta), forward FFT, unpack
+  double2 *out = reinterpret_cast<double2 *>(sm + kTcN * kTcM * sizeof(double));
+  double2 *scratch = out + 2 * LB * Ntp;
+  double2 *tw = scratch + 2 * LB * Ntp;
+  load_tw<double>(tw, p.twt, p.twt32, Nt);
+  const double rr = p.rad.r[r];
+  const double inv_r = p.rad.inv_r[r];
+  unsigned long long mr = 0ull, mt = 0ull, mz = 0ull;
+  const bool centrifugal = p.eps_c != 0.0;
+  auto bitsabs = [](double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+  };
+  for (int t = tid; t < nl * Nt; t += blockDim.x) {
+    const int li = t / Nt, j = t - li * Nt;
+    const double *f = P + (li * ncol) * kTcM + j;   // field c, q at f[(4c + q) kTcM]
+    const double ur = f[0], ur_t = f[kTcM], ur_r = f[2 * kTcM], ur_z = f[3 * kTcM];
+    const double ut = f[4 * kTcM], ut_t = f[5 * kTcM], ut_r_ = f[6 * kTcM], ut_z = f[7 * kTcM];
+    const double uz = f[8 * kTcM], uz_t = f[9 * kTcM], uz_r = f[10 * kTcM], uz_z = f[11 * kTcM];
+    const double ut_r = ut * inv_r;
+    const double adv_r = ur * ur_r + ut_r * ur_t + uz * ur_z;
+    const double adv_t = ur * ut_r_ + ut_r * ut_t + uz * ut_z;
+    const double adv_z = ur * uz_r + ut_r * uz_t + uz * uz_z;
+    double Nr_ = -(adv_r - ut * ut_r);
+    double Nt_ = -(adv_t + ur * ut_r);
+    double Nz_ = -adv_z;
+    double NT_ = 0.0;
+    if (s.nf == 4) {
+      const double T = f[12 * kTcM], T_t = f[13 * kTcM], T_r = f[14 * kTcM], T_z = f[15 * kTcM];
+      if (centrifugal) {
+        const double rho = 1.0 - p.eps_c * T;
+        Nr_ *= rho;
+        Nt_ *= rho;
+        Nz_ *= rho;
+      }
+      Nz_ += p.Gr * T;
+      NT_ = -(ur * T_r + ut_r * T_t + uz * T_z);
+    }
+    double2 *o = out + li * 2 * Ntp + spad(j);
+    o[0] = double2{Nr_, Nt_};
+    o[Ntp] = double2{Nz_, NT_};
+    if (rate_bits) {
+      mr = max(mr, bitsabs(ur));
+      mt = max(mt, bitsabs(ut));
+      mz = max(mz, bitsabs(uz));
+    }
+  }
+  if (rate_bits) {
+    for (int o = 16; o > 0; o >>= 1) {
+      mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+      mt = max(mt, __shfl_xor_sync(0xffffffffu, mt, o));
+      mz = max(mz, __shfl_xor_sync(0xffffffffu, mz, o));
+    }
+    if (lane == 0) {
+      atomicMax(&cfl_cta[0], mr);
+      atomicMax(&cfl_cta[1], mt);
+      atomicMax(&cfl_cta[2], mz);
+    }
+  }
+  __syncthreads();
+  if (rate_bits && tid == 0) {
+    auto val = [](unsigned long long b) { return __longlong_as_double((long long)b); };
+    const double rate = fmax(val(cfl_cta[0]) / p.rad.dr_min[r],
+                             fmax(val(cfl_cta[1]) / (rr * p.dth), val(cfl_cta[2]) / p.dz));
+    atomicMax(rate_bits, (unsigned long long)__double_as_longlong(rate));
+  }
+  double2 *sp = fft_batch<-1>(out, scratch, p.pt, nl * 2, Ntp, tw);
+  // unpack two real transforms: X_m = (Z_m + conj Z_-m)/2, Y_m = (Z_m - conj Z_-m)/(2i);
+  // the factor 1/2 is left to k_zfwd's final scaling (as in k_theta)
+  for (int t = tid; t < nl * s.NM; t += blockDim.x) {
+    const int li = t / s.NM, m = t - li * s.NM;
+    const double2 *z0 = sp + li * 2 * Ntp;
+    const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
+    const int mm = m == 0 ? 0 : Nt - m;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const double2 a = z0[h * Ntp + spad(m)];
+      const double2 b = z0[h * Ntp + spad(mm)];
+      const double2 x = double2{a.x + b.x, a.y - b.y};
+      const double2 y = double2{a.y + b.y, b.x - a.x};
+      if (dbg_in((2 * h) * fs + off, (long long)s.nf * fs, DBG_THETA_W)) W[(2 * h) * fs + off] = x;
+      if (2 * h + 1 < s.nf && dbg_in((2 * h + 1) * fs + off, (long long)s.nf * fs, DBG_THETA_W))
+        W[(2 * h + 1) * fs + off] = y;
+    }
+  }
+}
+
+// Host copy of scaled_int and of the digit split: the DFT matrix's slices.
+long long host_scaled_int(long double y) {   // round(y 2^56), |y| <= 1
+  return std::llround(std::ldexp(y, 56));
+}
+
+}  // namespace
+
+// The DFT matrix F/2 for Ntheta = Nt, M = Mmax, in 14 half-slices of the A
+// operand layout (slice i, half h at (2 i + h) * kTcAHalf bytes).
+void build_theta_dft(int Nt, int Mm, std::vector<unsigned short> &out) {
+  out.assign((size_t)kTcStages * kTcAHalf / 2, 0);
+  auto bf16 = [](int d, int sl) -> unsigned short {
+    if (d == 0) return 0;
+    const unsigned sgn = d < 0 ? 0x8000u : 0u;
+    const unsigned a = (unsigned)(d < 0 ? -d : d);
+    int e = 0;
+    while ((a >> (e + 1)) != 0u) ++e;
+    const unsigned mant = e >= 7 ? (a >> (e - 7)) & 0x7Fu : (a << (7 - e)) & 0x7Fu;
+    return (unsigned short)(sgn | ((unsigned)(127 + e - 8 * sl) << 7) | mant);
+  };
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int j = 0; j < kTcM; ++j)
+    for (int k = 0; k < kTcK; ++k) {
+      long double y = 0.0L;   // F/2
+      if (j < Nt && k <= 2 * Mm) {
+        if (k == 0) {
+          y = 0.5L;
+        } else {
+          const int m = k <= Mm ? k : k - Mm;
+          const long double ang = 2.0L * pi * (long double)((long long)m * j % Nt) / Nt;
+          y = k <= Mm ? std::cos(ang) : -std::sin(ang);
+        }
+      }
+      long long Y = host_scaled_int(y);
+      int dig[kTcS];
+      for (int sl = kTcS - 1; sl >= 1; --sl) {
+        int lo = (int)(Y & 255ll);
+        if (lo >= 128) lo -= 256;
+        dig[sl] = lo;
+        Y = (Y - lo) / 256;
+      }
+      dig[0] = (int)Y;
+      const int h = k / kTcHalfK, kl = k - h * kTcHalfK;
+      const int off = ((j >> 3) * (kTcHalfK / 8) + (kl >> 3)) * 128 + (j & 7) * 16 + (kl & 7) * 2;
+      for (int sl = 0; sl < kTcS; ++sl)
+        out[((size_t)(2 * sl + h) * kTcAHalf + off) / 2] = bf16(dig[sl], sl);
+    }
+}
+
+bool theta_tc_supported(const Sizes &s) {
+  return s.Nt <= kTcM && 2 * s.M + 1 <= kTcK && (kTcN % (4 * s.nf)) == 0;
+}
+
+size_t theta_tc_table_bytes() { return (size_t)kTcStages * kTcAHalf; }
+
+void setup_theta_tc() {
+  allow_smem(k_theta_tc);
+}
+
+void launch_theta_tc(cudaStream_t st, const double2 *V, double2 *W, const NLParams &p,
+                     const unsigned char *dft, unsigned long long *rate_bits, int *timeout) {
+  const Sizes &s = p.sz;
+  const int LB = kTcN / (4 * s.nf);
+  k_theta_tc<<<dim3((s.Nz + LB - 1) / LB, s.Nr), kTcThreads, kTcSmem, st>>>(V, W, p, dft,
+                                                                            rate_bits, timeout, LB);
+}
+
+}  // namespace tc

@@ -1,0 +1,84 @@
+"""The azimuthal transforms on the tensor cores (k_theta_tc) against the FP64
+FFT path (k_theta) of the same library and against the oracle.
+
+k_theta_tc forms the inverse theta transforms as DFT-matrix products of BF16
+slices (7 per operand, exact FP32 partial sums, exact integer combination),
+so it must agree with the FP64 transforms to FP64 round-off: 1e-13 of the
+largest nonlinear term here, at the benchmark's size and at ragged sizes.
+The oracle parity of every stage and run test also runs through it (it is
+on by default where the size allows: Ntheta <= 128)."""
+import numpy as np
+import pytest
+
+from inputs import WORKLOADS, Workload, psi_coefficients, random_state, temperature_coefficients
+from oracle import Model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1908_00587_gb300 import tc as mod
+    return mod
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+CASES = [
+    WORKLOADS["tc_fp64T_nr64_n128"],
+    Workload("tt1", Nr=17, Ntheta=96, Nz=40, eta=0.6, Lz=1.3, Re_i=70.0, Ra=0.0),
+    Workload("tt2", Nr=12, Ntheta=30, Nz=24, eta=0.7, Lz=2.1, Re_i=40.0, Re_o=-9.0, Ra=400.0,
+             Pr=0.9),
+    Workload("tt3", Nr=9, Ntheta=8, Nz=10, eta=0.5, Lz=1.0, Re_i=20.0, Ra=0.0),
+]
+
+
+@pytest.mark.parametrize("wl", CASES, ids=[w.name for w in CASES])
+def test_tensor_theta_matches_fft_theta(tc, wl):
+    run = tc.Run.from_workload(wl)
+    X = random_state(900 + wl.Nr, run.nf, wl.Nr, run.M, run.K)
+    outs, rates = [], []
+    for flag in (1, 0):
+        tc.tc_set_option(run.ctx, "tensor_theta", flag)
+        out = dev(np.zeros_like(X))
+        rates.append(tc.tc_nonlinear(run.ctx, dev(X), out))
+        outs.append(out.cpu().numpy())
+    run.close()
+    a, b = outs
+    rel = np.abs(a - b).max() / np.abs(b).max()
+    print(f"{wl.name}: tensor vs FFT theta transforms, max rel difference {rel:.2e}")
+    assert rel <= 1e-13, rel
+    assert abs(rates[0] - rates[1]) <= 1e-13 * rates[1]
+
+
+def test_tensor_theta_step_matches_oracle(tc):
+    """A whole heated run with the dynamic step, tensor-core transforms on,
+    against the oracle (the default path; checked explicitly here)."""
+    wl = WORKLOADS["tc_fp64T_nr64_n128"].scaled(Nr=24, Ntheta=48, Nz=36, mp=4, kp=4)
+    mdl = Model(wl, "fft")
+    psi = psi_coefficients(wl.seed, wl.mp, wl.kp)
+    tco = temperature_coefficients(wl.seed, wl.mp, wl.kp)
+    run = tc.Run.from_workload(wl)
+    tc.tc_set_option(run.ctx, "tensor_theta", 1)
+    run.init_perturbation(psi, wl.amp, tco, wl.amp_T)
+    dts = run.step(30, wl.dt)
+    got = run.get_state()
+    run.close()
+    X = mdl.initial_state(psi, tco)
+    dtp, ref_dts = 0.0, []
+    for _ in range(30):
+        X, _, dtp, _ = mdl.step(X, wl.dt, dtp)
+        ref_dts.append(dtp)
+    assert np.all(np.abs(dts - np.array(ref_dts)) <= 1e-8 * np.array(ref_dts))
+    w = (mdl.g.w * mdl.g.r)[:, None, None] * mdl.sp.cm[None, :, None]
+    err = max(float(np.sqrt(np.sum(w * np.abs(got[f] - X[f]) ** 2) / np.sum(w * np.abs(X[f]) ** 2)))
+              for f in range(X.shape[0]))
+    assert err <= 1e-10, err
