@@ -160,6 +160,16 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               device_bytes above it returns TC_ERR_OOM instead, with the
  *               context unchanged and usable.  A failed device allocation
  *               returns TC_ERR_OOM the same way.
+ *   "tensor_theta"  1: the inverse azimuthal transforms of the FP64
+ *               nonlinear stage run as DFT-matrix products on the tensor
+ *               cores (tcgen05), each operand split into 7 BF16 slices of 8
+ *               significant bits, the level sums exact in FP32 and combined
+ *               exactly in 64-bit integers: FP64-accurate (agrees with the FFT
+ *               path to ~4e-16 of the largest term).  Needs Ntheta <= 128 and
+ *               precision 0 (otherwise the FFT path runs).  0 (default): the
+ *               FP64 FFT.  The default is the FFT because it is faster on this
+ *               GPU at the sizes measured (64 x 128 x 128 with T: 0.47 against
+ *               0.41 ms a launch of the azimuthal kernel).
  *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
  *               never start their shared-memory copies, so each of their
  *               bounded waits runs out (about 1 s) and tc_step returns

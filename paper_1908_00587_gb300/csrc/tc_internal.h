@@ -258,7 +258,7 @@ struct tc_ctx {
   // azimuthal transforms on the tensor cores (theta_tc.cu): the DFT matrix's
   // BF16 slices (device, null when the size is not supported) and the option
   unsigned char *d_dft_tc = nullptr;
-  int tensor_theta = 1;
+  int tensor_theta = 0;
   int flux = 0;                 // axial-flux constraint on the (0,0) u_z mode
   double eps_c = 0.0;           // centrifugal buoyancy coefficient
   double *flux_ug = nullptr;    // device (Nr): unit-forcing response of the (0,0) u_z operator

@@ -4,9 +4,9 @@ FFT path (k_theta) of the same library and against the oracle.
 k_theta_tc forms the inverse theta transforms as DFT-matrix products of BF16
 slices (7 per operand, exact FP32 partial sums, exact integer combination),
 so it must agree with the FP64 transforms to FP64 round-off: 1e-13 of the
-largest nonlinear term here, at the benchmark's size and at ragged sizes.
-The oracle parity of every stage and run test also runs through it (it is
-on by default where the size allows: Ntheta <= 128)."""
+largest nonlinear term here, at the benchmark's size and at ragged sizes,
+and a whole run through it must meet the oracle gate (option tensor_theta;
+the default path is the FP64 FFT)."""
 import numpy as np
 import pytest
 
