@@ -24,14 +24,14 @@
 // terms, buoyancy and the CFL rate) in FP64 on the physical grid, then the
 // forward theta FFT in FP64 and the unpacking into W.
 //
-// Data path of one CTA (LB z rows of one radial level, 48 data columns):
+// Data path of one CTA (2 z rows of one radial level, 32 data columns):
 //   1. all threads: read V, slice the 48 columns into 7 BF16 operand tiles in
 //      shared memory (K-major core-matrix layout, no swizzle), one exponent
 //      per column;
-//   2. thread 0: stream the 14 half-slices of the DFT matrix (each 128 rows x
-//      48 coefficients, 12 KB, already in the operand layout) with 1-D bulk
-//      copies into a two-deep ring and issue the 28 x 6 MMAs (M 128, N 48,
-//      K 16) into five TMEM accumulators of 48 columns;
+//   2. thread 0: stream the 21 chunks of the DFT matrix's slices (each 128
+//      rows x 32 coefficients, 8 KB, already in the operand layout) with 1-D
+//      bulk copies into a four-deep ring and issue the 28 x 6 MMAs (M 128,
+//      N 32, K 16) into five TMEM accumulators of 32 columns;
 //   3. warps 0-3: read the accumulators (lane = theta row), combine them and
 //      write the physical fields (FP64) to shared memory;
 //   4. all threads: products, forward FFT, unpack (as k_theta).
@@ -53,19 +53,22 @@ namespace {
 
 constexpr int kTcM = 128;      // theta rows per MMA (Ntheta <= 128; zero rows beyond)
 constexpr int kTcK = 96;       // real coefficients per data column, padded (2M + 1 <= 96)
-constexpr int kTcN = 48;       // data columns per CTA: LB z rows x 4 nf real fields
+constexpr int kTcN = 32;       // data columns per CTA: 2 z rows x 4 nf real fields (+ zeros)
+constexpr int kTcLB = 2;       // z rows per CTA
 constexpr int kTcS = 7;        // slices of each operand
 constexpr int kTcAcc = 5;      // accumulators: levels 0..3 exact, levels 4..6 together
-constexpr int kTcHalfK = 48;   // coefficients per streamed half-slice of the DFT matrix
-constexpr int kTcStages = 2 * kTcS;
+constexpr int kTcKc = 32;      // coefficients per streamed chunk of a DFT-matrix slice
+constexpr int kTcChunks = kTcK / kTcKc;   // 3 per slice
+constexpr int kTcStages = kTcChunks * kTcS;   // 21
+constexpr int kTcRing = 4;     // chunks in flight
 constexpr int kTcThreads = 256;
 // Operand layouts in shared memory (K-major, no swizzle): core matrices of 8
 // rows x 16 bytes (8 BF16), the K-neighbour of a core matrix 128 B further,
 // the next group of 8 rows one K extent further.
-constexpr int kTcBSlice = (kTcN / 8) * (kTcK / 8) * 128;       // 9216 B per data slice
-constexpr int kTcBBytes = kTcS * kTcBSlice;                     // 64512
-constexpr int kTcAHalf = (kTcM / 8) * (kTcHalfK / 8) * 128;    // 12288 B per half-slice
-constexpr int kTcSmem = kTcBBytes + 2 * kTcAHalf;               // 89088
+constexpr int kTcBSlice = (kTcN / 8) * (kTcK / 8) * 128;       // 6144 B per data slice
+constexpr int kTcBBytes = kTcS * kTcBSlice;                     // 43008
+constexpr int kTcAChunk = (kTcM / 8) * (kTcKc / 8) * 128;      // 8192 B per chunk
+constexpr int kTcSmem = kTcBBytes + kTcRing * kTcAChunk;        // 75776: three CTAs per SM
 constexpr int kTcTmemCols = 256;
 constexpr long long kTcWaitNs = 1000000000LL;
 
@@ -155,10 +158,11 @@ __device__ __forceinline__ unsigned long long ll_to_double_bits(long long v) {
   return sgn | bits;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2)
+__global__ void __launch_bounds__(kTcThreads, 3)
 k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
            const unsigned char *__restrict__ dft, unsigned long long *__restrict__ rate_bits,
-           int *__restrict__ timeout, int LB) {
+           int *__restrict__ timeout) {
+  constexpr int LB = kTcLB;
   const Sizes &s = p.sz;
   const int l0 = blockIdx.x * LB;
   const int nl = min(LB, s.Nz - l0);
@@ -167,10 +171,10 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
   const int Ntp = padlen(Nt);
   const int M = s.M;
   const int ncol = 4 * s.nf;                      // data columns per z row
-  extern __shared__ __align__(1024) unsigned char sm[];
+  extern __shared__ __align__(128) unsigned char sm[];
   unsigned char *sB = sm;
   unsigned char *sA = sm + kTcBBytes;
-  __shared__ __align__(8) unsigned long long bars[5];   // full[2], free[2], done
+  __shared__ __align__(8) unsigned long long bars[2 * kTcRing + 1];   // full, free, done
   __shared__ unsigned tmem_s;
   __shared__ int colE[kTcN];
   __shared__ int abort_s;
@@ -184,40 +188,42 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
   }
   if (tid == 0) {
     abort_s = 0;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 2 * kTcRing + 1; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bars[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < 3) cfl_cta[tid] = 0ull;
   __syncthreads();
-  // the first two half-slices of the DFT matrix
+  // the first kTcRing chunks of the DFT matrix
   auto load_a = [&](int st) {
-    const unsigned bar = smem_u32(&bars[st & 1]);
+    const int b = st % kTcRing;
+    const unsigned bar = smem_u32(&bars[b]);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(bar), "r"((unsigned)kTcAHalf) : "memory");
+                 :: "r"(bar), "r"((unsigned)kTcAChunk) : "memory");
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        :: "r"(smem_u32(sA + (st & 1) * kTcAHalf)), "l"(dft + (size_t)st * kTcAHalf),
-           "r"((unsigned)kTcAHalf), "r"(bar)
+        :: "r"(smem_u32(sA + b * kTcAChunk)), "l"(dft + (size_t)st * kTcAChunk),
+           "r"((unsigned)kTcAChunk), "r"(bar)
         : "memory");
   };
-  if (tid == 0) {
-    load_a(0);
-    load_a(1);
-  }
+  if (tid == 0)
+    for (int st = 0; st < kTcRing; ++st) load_a(st);
 
   // 1. the data columns of this tile, sliced.  Column n = li ncol + 4 c + q:
   // z row li, field c, q = 0 value, 1 theta derivative, 2 d/dr, 3 d/dz.
   // Coefficient k: 0 -> Re a_0, 1..M -> Re a_k, M+1..2M -> Im a_(k-M).
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
-  for (int n = warp; n < kTcN; n += kTcThreads / 32) {
+  constexpr int kColsPerWarp = kTcN / (kTcThreads / 32);   // 4
+  double xs[kColsPerWarp][3];
+#pragma unroll
+  for (int cw = 0; cw < kColsPerWarp; ++cw) {   // all loads first
+    const int n = warp + cw * (kTcThreads / 32);
     const int li = n / ncol, cq = n - li * ncol, c = cq >> 2, q = cq & 3;
-    double x[3];
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
       const int k = lane + 32 * u;
       double v = 0.0;
-      if (li < nl && k <= 2 * M) {
+      if (li < nl && cq < ncol && k <= 2 * M) {
         const int m = k <= M ? k : k - M;
         const bool im = k > M;
         const int d = q <= 1 ? 0 : q - 1;
@@ -231,20 +237,24 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
             v = im ? a.y : a.x;
         }
       }
-      x[u] = v;
+      xs[cw][u] = v;
     }
+  }
+#pragma unroll
+  for (int cw = 0; cw < kColsPerWarp; ++cw) {
+    const int n = warp + cw * (kTcThreads / 32);
     // exponent of the column: E with max |x| < 2^E
     unsigned long long mb = 0ull;
 #pragma unroll
     for (int u = 0; u < 3; ++u)
-      mb = max(mb, (unsigned long long)__double_as_longlong(x[u]) & 0x7FFFFFFFFFFFFFFFull);
+      mb = max(mb, (unsigned long long)__double_as_longlong(xs[cw][u]) & 0x7FFFFFFFFFFFFFFFull);
     for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
     const int E = mb ? (int)((mb >> 52) & 0x7FF) - 1022 : 0;   // 2^(e) <= max < 2^(e+1) = 2^E
     if (lane == 0) colE[n] = E;
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
       const int k = lane + 32 * u;
-      long long y = scaled_int(x[u], E);
+      long long y = scaled_int(xs[cw][u], E);
       int dig[kTcS];
 #pragma unroll
       for (int sl = kTcS - 1; sl >= 1; --sl) {
@@ -273,23 +283,23 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
     unsigned inited = 0u;
     bool ok = true;
     for (int st = 0; st < kTcStages && ok; ++st) {
-      const int i = st >> 1, h = st & 1, buf = st & 1;
-      if (!tc_wait(smem_u32(&bars[buf]), (unsigned)(st >> 1) & 1u)) {
+      const int i = st / kTcChunks, ch = st - i * kTcChunks, buf = st % kTcRing;
+      if (!tc_wait(smem_u32(&bars[buf]), (unsigned)(st / kTcRing) & 1u)) {
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned abase = smem_u32(sA + buf * kTcAHalf);
+      const unsigned abase = smem_u32(sA + buf * kTcAChunk);
       for (int j = 0; j + i < kTcS; ++j) {
         const int L = i + j;
         const int acc = L < kTcAcc - 1 ? L : kTcAcc - 1;
         const unsigned dcol = tmem + (unsigned)(acc * kTcN);
         const unsigned bbase = smem_u32(sB + j * kTcBSlice);
 #pragma unroll
-        for (int t = 0; t < kTcHalfK / 16; ++t) {
-          const unsigned long long ad = tc_desc(abase + t * 256, 128, (kTcHalfK / 8) * 128);
+        for (int t = 0; t < kTcKc / 16; ++t) {
+          const unsigned long long ad = tc_desc(abase + t * 256, 128, (kTcKc / 8) * 128);
           const unsigned long long bd =
-              tc_desc(bbase + (h * (kTcHalfK / 8) + 2 * t) * 128, 128, (kTcK / 8) * 128);
+              tc_desc(bbase + (ch * (kTcKc / 8) + 2 * t) * 128, 128, (kTcK / 8) * 128);
           const unsigned en = (inited >> acc) & 1u;
           inited |= 1u << acc;
           asm volatile(
@@ -299,55 +309,46 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&bars[2 + buf])) : "memory");
+                   :: "r"(smem_u32(&bars[kTcRing + buf])) : "memory");
       // refill the buffer of the previous stage once its products are done
-      if (st >= 1 && st + 1 < kTcStages) {
-        const int pb = (st - 1) & 1;
-        if (!tc_wait(smem_u32(&bars[2 + pb]), (unsigned)((st - 1) >> 1) & 1u)) {
+      if (st >= 1 && st - 1 + kTcRing < kTcStages) {
+        const int pb = (st - 1) % kTcRing;
+        if (!tc_wait(smem_u32(&bars[kTcRing + pb]), (unsigned)((st - 1) / kTcRing) & 1u)) {
           ok = false;
           break;
         }
-        load_a(st + 1);
+        load_a(st - 1 + kTcRing);
       }
     }
     if (ok)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&bars[4])) : "memory");
+                   :: "r"(smem_u32(&bars[2 * kTcRing])) : "memory");
     else
       abort_s = 1;
   }
   __syncthreads();
-  bool done = abort_s == 0 && tc_wait(smem_u32(&bars[4]), 0u);
+  bool done = abort_s == 0 && tc_wait(smem_u32(&bars[2 * kTcRing]), 0u);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!done) {
-    if (tid == 0) atomicOr(timeout, 1);
-    // drain the copies still in flight into this CTA (bounded)
-    if (tid == 0) {
-      tc_wait(smem_u32(&bars[0]), 0u);
-      tc_wait(smem_u32(&bars[1]), 0u);
-    }
-  }
+  if (!done && tid == 0) atomicOr(timeout, 1);
   // 3. accumulators -> physical fields P[n][j] (FP64), lane = theta row
   double *P = reinterpret_cast<double *>(sm);   // over the data slices: the products are done
   if (done && warp < 4) {
     const int j = warp * 32 + lane;
-    for (int cb = 0; cb < kTcN / 16; ++cb) {
-      unsigned v[kTcAcc][16];
+    for (int cb = 0; cb < kTcN / 8; ++cb) {
+      unsigned v[kTcAcc][8];
 #pragma unroll
       for (int a = 0; a < kTcAcc; ++a) {
-        const unsigned ta = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(a * kTcN + cb * 16);
+        const unsigned ta = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(a * kTcN + cb * 8);
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
             : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]),
-              "=r"(v[a][5]), "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]),
-              "=r"(v[a][10]), "=r"(v[a][11]), "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]),
-              "=r"(v[a][15])
+              "=r"(v[a][5]), "=r"(v[a][6]), "=r"(v[a][7])
             : "r"(ta));
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int n = cb * 16 + t;
+      for (int t = 0; t < 8; ++t) {
+        const int n = cb * 8 + t;
         // level L holds (integer) x 2^(-8L); in units of 2^-36 of level 0
         long long I = (long long)__float2int_rn(__uint_as_float(v[0][t])) << 36;
         I += (long long)__float2int_rn(__uint_as_float(v[1][t]) * 256.0f) << 28;
@@ -461,10 +462,11 @@ long long host_scaled_int(long double y) {   // round(y 2^56), |y| <= 1
 
 }  // namespace
 
-// The DFT matrix F/2 for Ntheta = Nt, M = Mmax, in 14 half-slices of the A
-// operand layout (slice i, half h at (2 i + h) * kTcAHalf bytes).
+// The DFT matrix F/2 for Ntheta = Nt, M = Mmax, in 21 chunks of the A operand
+// layout (slice i, coefficients 32 ch .. 32 ch + 31 at (3 i + ch) * kTcAChunk
+// bytes).
 void build_theta_dft(int Nt, int Mm, std::vector<unsigned short> &out) {
-  out.assign((size_t)kTcStages * kTcAHalf / 2, 0);
+  out.assign((size_t)kTcStages * kTcAChunk / 2, 0);
   auto bf16 = [](int d, int sl) -> unsigned short {
     if (d == 0) return 0;
     const unsigned sgn = d < 0 ? 0x8000u : 0u;
@@ -496,18 +498,18 @@ void build_theta_dft(int Nt, int Mm, std::vector<unsigned short> &out) {
         Y = (Y - lo) / 256;
       }
       dig[0] = (int)Y;
-      const int h = k / kTcHalfK, kl = k - h * kTcHalfK;
-      const int off = ((j >> 3) * (kTcHalfK / 8) + (kl >> 3)) * 128 + (j & 7) * 16 + (kl & 7) * 2;
+      const int ch = k / kTcKc, kl = k - ch * kTcKc;
+      const int off = ((j >> 3) * (kTcKc / 8) + (kl >> 3)) * 128 + (j & 7) * 16 + (kl & 7) * 2;
       for (int sl = 0; sl < kTcS; ++sl)
-        out[((size_t)(2 * sl + h) * kTcAHalf + off) / 2] = bf16(dig[sl], sl);
+        out[((size_t)(kTcChunks * sl + ch) * kTcAChunk + off) / 2] = bf16(dig[sl], sl);
     }
 }
 
 bool theta_tc_supported(const Sizes &s) {
-  return s.Nt <= kTcM && 2 * s.M + 1 <= kTcK && (kTcN % (4 * s.nf)) == 0;
+  return s.Nt <= kTcM && 2 * s.M + 1 <= kTcK && kTcLB * 4 * s.nf <= kTcN;
 }
 
-size_t theta_tc_table_bytes() { return (size_t)kTcStages * kTcAHalf; }
+size_t theta_tc_table_bytes() { return (size_t)kTcStages * kTcAChunk; }
 
 void setup_theta_tc() {
   allow_smem(k_theta_tc);
@@ -516,9 +518,8 @@ void setup_theta_tc() {
 void launch_theta_tc(cudaStream_t st, const double2 *V, double2 *W, const NLParams &p,
                      const unsigned char *dft, unsigned long long *rate_bits, int *timeout) {
   const Sizes &s = p.sz;
-  const int LB = kTcN / (4 * s.nf);
-  k_theta_tc<<<dim3((s.Nz + LB - 1) / LB, s.Nr), kTcThreads, kTcSmem, st>>>(V, W, p, dft,
-                                                                            rate_bits, timeout, LB);
+  k_theta_tc<<<dim3((s.Nz + kTcLB - 1) / kTcLB, s.Nr), kTcThreads, kTcSmem, st>>>(
+      V, W, p, dft, rate_bits, timeout);
 }
 
 }  // namespace tc
