@@ -9,16 +9,17 @@
 // operands into 7 slices of 8 significant bits (Ozaki et al., "Error-free
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication", Numer. Algorithms 59, 2012):
-//   F/2      = sum_i A_i 2^-8,  A_i = a_i 2^-8i,  a_i integers in [-256, 256]
-//   x/2^E    = sum_j B_j 2^-8,  B_j = b_j 2^-8j  (E: exponent of the column)
-// Every product A_i B_j is exact in BF16 x BF16 -> FP32, and the sum over the
-// at most 96 coefficients of all pairs with i + j = L is exact in an FP32
-// accumulator for L <= 3 (at most 4 pairs x 96 terms of at most 2^16);
-// levels 4..6 share one accumulator whose rounding is 2^-24 of a term that
-// is itself below 2^-32 of the result.  The pairs with i + j > 6 are below
-// 2^-56 of the result and are not formed (28 of the 49 slice products).  The
-// five accumulators are combined exactly in 64-bit integers and rounded once
-// to FP64.  The theta derivative is the same product applied to i m a_m.
+//   F/2   = 2^-8 sum_i a_i 2^-8i,   x/2^E = 2^-8 sum_j b_j 2^-8j,
+// a_i, b_j integers in [-256, 256] (E: exponent of the data column).  The
+// products a_i b_j are exact in BF16 x BF16 -> FP32, and so is the sum of all
+// pairs of one level L = i + j over the at most 96 coefficients (at most 7
+// pairs x 96 terms, below 2^24).  The slices of the data sit one above the
+// other along N, so one MMA with A = a_i and B = (b_0 .. b_(6-i)) adds a_i b_j
+// to TMEM column block i + j: seven level blocks, each exact.  Levels above 6
+// are below 2^-56 of the result and are not formed (28 of the 49 slice
+// products).  The level sums are combined exactly in 64-bit integers and
+// rounded once to FP64.  The theta derivative is the same product applied to
+// i m a_m.
 //
 // The rest of the stage is k_theta's: the products u.grad u (with curvature
 // terms, buoyancy and the CFL rate) in FP64 on the physical grid, then the
@@ -30,8 +31,8 @@
 //      per column;
 //   2. thread 0: stream the 21 chunks of the DFT matrix's slices (each 128
 //      rows x 32 coefficients, 8 KB, already in the operand layout) with 1-D
-//      bulk copies into a four-deep ring and issue the 28 x 6 MMAs (M 128,
-//      N 32, K 16) into five TMEM accumulators of 32 columns;
+//      bulk copies into a four-deep ring and issue 7 x 6 MMAs (M 128,
+//      N 32 (7 - i), K 16) into the seven level blocks of 32 TMEM columns;
 //   3. warps 0-3: read the accumulators (lane = theta row), combine them and
 //      write the physical fields (FP64) to shared memory;
 //   4. all threads: products, forward FFT, unpack (as k_theta).
@@ -56,7 +57,7 @@ constexpr int kTcK = 96;       // real coefficients per data column, padded (2M 
 constexpr int kTcN = 32;       // data columns per CTA: 2 z rows x 4 nf real fields (+ zeros)
 constexpr int kTcLB = 2;       // z rows per CTA
 constexpr int kTcS = 7;        // slices of each operand
-constexpr int kTcAcc = 5;      // accumulators: levels 0..3 exact, levels 4..6 together
+constexpr int kTcLev = 7;      // level blocks of kTcN TMEM columns each
 constexpr int kTcKc = 32;      // coefficients per streamed chunk of a DFT-matrix slice
 constexpr int kTcChunks = kTcK / kTcKc;   // 3 per slice
 constexpr int kTcStages = kTcChunks * kTcS;   // 21
@@ -105,14 +106,14 @@ __device__ __forceinline__ bool tc_wait(unsigned bar, unsigned phase) {
   }
 }
 
-// BF16 bits of d * 2^(-8 s) for an integer |d| <= 256 (exact).
-__device__ __forceinline__ unsigned short bf16_digit(int d, int s) {
+// BF16 bits of an integer |d| <= 256 (exact).
+__device__ __forceinline__ unsigned short bf16_digit(int d) {
   if (d == 0) return 0;
   const unsigned sgn = d < 0 ? 0x8000u : 0u;
   const unsigned a = (unsigned)(d < 0 ? -d : d);
   const int e = 31 - __clz(a);                     // 0..8
   const unsigned mant = e >= 7 ? (a >> (e - 7)) & 0x7Fu : (a << (7 - e)) & 0x7Fu;
-  return (unsigned short)(sgn | ((unsigned)(127 + e - 8 * s) << 7) | mant);
+  return (unsigned short)(sgn | ((unsigned)(127 + e) << 7) | mant);
 }
 
 // round(|x| * 2^(56 - E)) with the sign of x, exactly (x finite, |x| < 2^E).
@@ -181,11 +182,6 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
   __shared__ unsigned long long cfl_cta[3];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_s)), "r"(kTcTmemCols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
   if (tid == 0) {
     abort_s = 0;
     for (int i = 0; i < 2 * kTcRing + 1; ++i)
@@ -267,10 +263,17 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
 #pragma unroll
       for (int sl = 0; sl < kTcS; ++sl)
         *reinterpret_cast<unsigned short *>(sB + sl * kTcBSlice + b_off(n, k)) =
-            bf16_digit(dig[sl], sl);
+            bf16_digit(dig[sl]);
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  // tensor memory only now, for the products and the read-back (another CTA
+  // on this SM may hold it meanwhile: the allocation waits for it)
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_s)), "r"(kTcTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -278,9 +281,6 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
 
   // 2. the slice products (thread 0 issues them)
   if (tid == 0) {
-    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                           ((unsigned)(kTcN >> 3) << 17) | ((unsigned)(kTcM >> 4) << 24);
-    unsigned inited = 0u;
     bool ok = true;
     for (int st = 0; st < kTcStages && ok; ++st) {
       const int i = st / kTcChunks, ch = st - i * kTcChunks, buf = st % kTcRing;
@@ -289,24 +289,24 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // A = slice i of the DFT matrix (this chunk), B = data slices 0 .. 6 - i
+      // stacked along N, D = level blocks i .. 6
+      const int nB = (kTcLev - i) * kTcN;
+      const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                             ((unsigned)(nB >> 3) << 17) | ((unsigned)(kTcM >> 4) << 24);
       const unsigned abase = smem_u32(sA + buf * kTcAChunk);
-      for (int j = 0; j + i < kTcS; ++j) {
-        const int L = i + j;
-        const int acc = L < kTcAcc - 1 ? L : kTcAcc - 1;
-        const unsigned dcol = tmem + (unsigned)(acc * kTcN);
-        const unsigned bbase = smem_u32(sB + j * kTcBSlice);
+      const unsigned dcol = tmem + (unsigned)(i * kTcN);
 #pragma unroll
-        for (int t = 0; t < kTcKc / 16; ++t) {
-          const unsigned long long ad = tc_desc(abase + t * 256, 128, (kTcKc / 8) * 128);
-          const unsigned long long bd =
-              tc_desc(bbase + (ch * (kTcKc / 8) + 2 * t) * 128, 128, (kTcK / 8) * 128);
-          const unsigned en = (inited >> acc) & 1u;
-          inited |= 1u << acc;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-              :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(en) : "memory");
-        }
+      for (int t = 0; t < kTcKc / 16; ++t) {
+        const unsigned long long ad = tc_desc(abase + t * 256, 128, (kTcKc / 8) * 128);
+        const unsigned long long bd =
+            tc_desc(smem_u32(sB) + (ch * (kTcKc / 8) + 2 * t) * 128, 128, (kTcK / 8) * 128);
+        // the first product (slice 0, coefficients 0..15) initialises every block
+        const unsigned en = (st == 0 && t == 0) ? 0u : 1u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(en) : "memory");
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    :: "r"(smem_u32(&bars[kTcRing + buf])) : "memory");
@@ -335,29 +335,29 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
   if (done && warp < 4) {
     const int j = warp * 32 + lane;
     for (int cb = 0; cb < kTcN / 8; ++cb) {
-      unsigned v[kTcAcc][8];
+      unsigned v[kTcLev][8];
 #pragma unroll
-      for (int a = 0; a < kTcAcc; ++a) {
-        const unsigned ta = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(a * kTcN + cb * 8);
+      for (int L = 0; L < kTcLev; ++L) {
+        const unsigned ta = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(L * kTcN + cb * 8);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-            : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]),
-              "=r"(v[a][5]), "=r"(v[a][6]), "=r"(v[a][7])
+            : "=r"(v[L][0]), "=r"(v[L][1]), "=r"(v[L][2]), "=r"(v[L][3]), "=r"(v[L][4]),
+              "=r"(v[L][5]), "=r"(v[L][6]), "=r"(v[L][7])
             : "r"(ta));
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int n = cb * 8 + t;
-        // level L holds (integer) x 2^(-8L); in units of 2^-36 of level 0
-        long long I = (long long)__float2int_rn(__uint_as_float(v[0][t])) << 36;
-        I += (long long)__float2int_rn(__uint_as_float(v[1][t]) * 256.0f) << 28;
-        I += (long long)__float2int_rn(__uint_as_float(v[2][t]) * 65536.0f) << 20;
-        I += (long long)__float2int_rn(__uint_as_float(v[3][t]) * 16777216.0f) << 12;
-        I += (long long)__float2int_rn(__uint_as_float(v[4][t]) * 68719476736.0f);
-        // value = I 2^-36 2^-16 2^(E+1): F/2 and x/2^E each carry a 2^-8
+        // level L holds the integer S_L of weight 2^(-8L); in units of 2^-40
+        long long I = 0;
+#pragma unroll
+        for (int L = 0; L < kTcLev - 1; ++L)
+          I += (long long)__float2int_rn(__uint_as_float(v[L][t])) << (40 - 8 * L);
+        I += (long long)__float2int_rn(__uint_as_float(v[kTcLev - 1][t]) * 0.00390625f);
+        // value = I 2^-40 2^-16 2^(E+1): F/2 and x/2^E each carry a 2^-8
         unsigned long long bits = ll_to_double_bits(I);
-        if (bits & 0x7FFFFFFFFFFFFFFFull) bits += (unsigned long long)(long long)(colE[n] - 51) << 52;
+        if (bits & 0x7FFFFFFFFFFFFFFFull) bits += (unsigned long long)(long long)(colE[n] - 55) << 52;
         P[n * kTcM + j] = __longlong_as_double((long long)bits);
       }
     }
@@ -474,7 +474,8 @@ void build_theta_dft(int Nt, int Mm, std::vector<unsigned short> &out) {
     int e = 0;
     while ((a >> (e + 1)) != 0u) ++e;
     const unsigned mant = e >= 7 ? (a >> (e - 7)) & 0x7Fu : (a << (7 - e)) & 0x7Fu;
-    return (unsigned short)(sgn | ((unsigned)(127 + e - 8 * sl) << 7) | mant);
+    (void)sl;
+    return (unsigned short)(sgn | ((unsigned)(127 + e) << 7) | mant);
   };
   const long double pi = 3.141592653589793238462643383279502884L;
   for (int j = 0; j < kTcM; ++j)
