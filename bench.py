@@ -77,6 +77,16 @@ def replica_throughput(points, steps, world, slowest_ms):
     return points * steps * world / (slowest_ms * 1e-3)
 
 
+def measured_bf16_peak():
+    """Dense BF16 tensor rate measured on the GB300s (TFLOP/s, burst)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def measured_hbm_peak():
     """Copy bandwidth measured on the GB300s (GB/s), else the fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -189,9 +199,11 @@ def kernel_flops(name, wl):
     nf = 4 if wl.Ra else 3
     M, K = (wl.Ntheta - 1) // 3, (wl.Nz - 1) // 3
     NM, NK = M + 1, 2 * K + 1
-    if name == "k_theta":
+    if name in ("k_theta", "k_theta_tc"):
         # per z-row: 2 nf inverse + 2 forward complex FFTs along theta (two real
-        # fields each), ~30 flops of products and curvature terms per point
+        # fields each), ~30 flops of products and curvature terms per point.
+        # The tensor-core kernel does the same stage (its inverse transforms
+        # as DFT-matrix products): the stage's algorithmic count is the same
         return wl.Nr * wl.Nz * ((2 * nf + 2) * fft_flops(wl.Ntheta) + 30 * wl.Ntheta)
     if name == "k_zinv":
         # 3 fields per component and m column, plus the 9-point d/dr (72 flops/coeff)
@@ -199,6 +211,14 @@ def kernel_flops(name, wl):
     if name == "k_zfwd":
         return wl.Nr * nf * NM * fft_flops(wl.Nz)
     return None
+
+
+def theta_tc_tensor_flops(wl):
+    """BF16 tensor flops one launch of k_theta_tc issues: per CTA (2 z rows,
+    32 data columns, 128 theta rows, 96 coefficients) the products of DFT
+    slice i with data slices 0..6-i, 28 slice pairs of 128 x 32 x 96."""
+    ctas = wl.Nr * ((wl.Nz + 1) // 2)
+    return ctas * 28 * 2.0 * 128 * 32 * 96
 
 
 def step_flops(wl):
@@ -306,6 +326,8 @@ def run_gb300(args):
     tc.tc_autotune(run.ctx)                 # tile shapes of the nonlinear stage
     info = tc.tc_get_info(run.ctx)
     tiles = (info.tile_mb, info.tile_lb, info.tile_mbf)
+    azimuthal = ("tensor cores: DFT-matrix products of 7 BF16 slices (k_theta_tc)"
+                 if info.tensor_theta else "FP64 FFT (k_theta)")
 
     for _ in range(args.warmup):
         run.step(1, wl.dt)                  # the first one also captures the step graph
@@ -402,6 +424,7 @@ def run_gb300(args):
     nl, ms = timing[dom]
     fl = kernel_flops(dom, wl)
     fp32_dom = mixed and dom in ("k_theta", "k_zinv", "k_zfwd")
+    tensor_dom = dom == "k_theta_tc"
     peak = FP32_PEAK_TFLOPS if fp32_dom else FP64_PEAK_TFLOPS
     roof = {"kernel": dom, "bound": "alu", "unit": "TFLOP/s", "peak": peak,
             "peak_source": ("derived: 152 SMs x 2.07 GHz x 256 FP32 flop/clk/SM" if fp32_dom
@@ -415,6 +438,19 @@ def run_gb300(args):
                      "flops_per_launch": fl})
     else:
         roof.update({"achieved": None, "frac": None})
+    if tensor_dom:
+        # the azimuthal stage with its inverse transforms on the tensor cores:
+        # achieved counts the stage's algorithmic FP64 flops (FFT count), as
+        # for k_theta; the BF16 slice products it issues are reported beside
+        tf = theta_tc_tensor_flops(wl)
+        bf16 = measured_bf16_peak()
+        roof["how"] = ("algorithmic FP64 flops of the azimuthal stage (its FFT count) over "
+                       "the tensor-core kernel's time")
+        roof["tensor"] = {"bf16_flops_per_launch": tf,
+                          "achieved_tflops": tf / (ms / nl * 1e-3) / 1e12,
+                          "peak_tflops": bf16,
+                          "frac": (tf / (ms / nl * 1e-3) / 1e12 / bf16) if bf16 else None,
+                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16, burst)"}
     # the FP64 FMA rate this GPU sustains, measured after the timed regions
     # (the derived peak above counts 4 flop/clk/SM; the FP64 units deliver less)
     fp64_meas = None
@@ -463,6 +499,7 @@ def run_gb300(args):
             "config": config_of(wl, {"l2": "flushed between timed steps (512 MiB write)",
                                      "parallelism": f"replicas x{world}",
                                      "tiles_mb_lb_mbf": list(tiles),
+                                     "azimuthal_transforms": azimuthal,
                                      "launch": "one step captured as a CUDA graph, replayed per step",
                                      "stated_error": (
                                          "rel L2 <= 1.3e-11 vs the FP64 path after 50 steps at "

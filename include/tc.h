@@ -84,6 +84,7 @@ typedef struct {
   long long launches;           /* kernels launched since tc_create */
   int tile_mb, tile_lb;         /* nonlinear-stage tiles in use (see "tile_mb") */
   int tile_mbf;                 /* m columns per CTA of the forward axial kernel */
+  int tensor_theta;             /* 1: the azimuthal stage runs on the tensor cores */
 } tc_info;
 
 /* Device time of one kernel accumulated while option "timing" is 1. */
@@ -167,9 +168,11 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               exactly in 64-bit integers: FP64-accurate (agrees with the FFT
  *               path to ~4e-16 of the largest term).  Needs Ntheta <= 128 and
  *               precision 0 (otherwise the FFT path runs).  0 (default): the
- *               FP64 FFT.  The default is the FFT because it is faster on this
- *               GPU at the sizes measured (64 x 128 x 128 with T: 0.47 against
- *               0.41 ms a launch of the azimuthal kernel).
+ *               FP64 FFT.  Which one is faster depends on the size (measured
+ *               on GB300: 0.38 against 0.41 ms a launch at 64 x 128 x 128 with
+ *               temperature, 0.16 against 0.09 ms at 64 x 64 x 64, where most
+ *               of the 128 rows of each product are padding); tc_autotune
+ *               times both and keeps the faster.
  *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
  *               never start their shared-memory copies, so each of their
  *               bounded waits runs out (about 1 s) and tc_step returns
@@ -441,9 +444,11 @@ tc_status tc_ensemble_get_mode(const tc_ens *e, int *mode);
 /* Tile autotuner for one context (the one the ensemble runs per size
  * class): times the nonlinear stage on the context's current state for tile
  * shapes {1, 2, 3, 4, 5, 6, 8} of "tile_mb", then {1, 2, 3, 4, 8} of
- * "tile_lb", then {1, 2, 3, 4, 5, 6, 8} of "tile_mbf", keeps the fastest and
- * returns the first two (host, nullable; tc_get_info reports all three).
- * Results do not depend on the tiles. */
+ * "tile_lb", then (precision 0, Ntheta <= 128) "tensor_theta" 1 against 0,
+ * then {1, 2, 3, 4, 5, 6, 8} of "tile_mbf", keeps the fastest and returns the
+ * first two (host, nullable; tc_get_info reports all four).  Results do not
+ * depend on the tiles; the tensor-core azimuthal stage changes them only at
+ * round-off (see "tensor_theta"). */
 tc_status tc_autotune(tc_ctx *ctx, int *tile_mb, int *tile_lb);
 
 /* Kernel launches per tc_ensemble_step step: the kernels one graph replay

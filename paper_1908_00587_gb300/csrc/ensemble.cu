@@ -91,6 +91,7 @@ tc_status autotune(tc_ctx *c, int *best_mb, int *best_lb) {
   // the forward axial kernel's width stays at its default while tile_mb is
   // searched, so that search sees only the inverse kernel change
   tc_set_option(c, "tile_mbf", (c->precision == 1) ? c->nl32.MBf : c->nl.MBf);
+  tc_set_option(c, "tensor_theta", 0);
   float best = 1e30f;
   int bm = 0;
   for (int mb : cand_mb) {
@@ -114,6 +115,12 @@ tc_status autotune(tc_ctx *c, int *best_mb, int *best_lb) {
     }
   }
   if (bl) tc_set_option(c, "tile_lb", bl);
+  // the azimuthal stage on the tensor cores, where it applies, against the
+  // FFT kernel with the tile just chosen
+  if (c->precision == 0 && c->d_dft_tc) {
+    tc_set_option(c, "tensor_theta", 1);
+    if (time_nonlinear(c, a, b, 3) >= best) tc_set_option(c, "tensor_theta", 0);
+  }
   // the forward axial kernel's own width (its grid fills the SMs differently)
   best = 1e30f;
   int bf = 0;
@@ -721,8 +728,8 @@ tc_status tc_ensemble_create(int n, const tc_params *p, int autotune_tiles, tc_e
     tc_set_stream(c, s);
   }
   if (autotune_tiles) {
-    // tuned (tile_mb, tile_lb, tile_mbf) per size class
-    std::map<ClassKey, std::tuple<int, int, int>> tuned;
+    // tuned (tile_mb, tile_lb, tile_mbf, tensor_theta) per size class
+    std::map<ClassKey, std::tuple<int, int, int, int>> tuned;
     for (tc_ctx *c : e->m) {
       const ClassKey k = class_of(c);
       auto it = tuned.find(k);
@@ -730,12 +737,13 @@ tc_status tc_ensemble_create(int n, const tc_params *p, int autotune_tiles, tc_e
         int mb = 0, lb = 0;
         tc_status st = autotune(c, &mb, &lb);
         if (st != TC_OK) return fail(st);
-        tuned[k] = std::make_tuple(mb, lb, c->tile_mbf);
+        tuned[k] = std::make_tuple(mb, lb, c->tile_mbf, c->tensor_theta);
       } else {
-        const auto [mb, lb, mbf] = it->second;
+        const auto [mb, lb, mbf, tt] = it->second;
         if (mb) tc_set_option(c, "tile_mb", mb);
         if (lb) tc_set_option(c, "tile_lb", lb);
         if (mbf) tc_set_option(c, "tile_mbf", mbf);
+        tc_set_option(c, "tensor_theta", tt);
       }
     }
   }

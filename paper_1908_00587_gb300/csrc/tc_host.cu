@@ -883,6 +883,7 @@ tc_status tc_get_info(const tc_ctx *c, tc_info *o) {
   o->tile_mb = (c->precision == 1) ? c->nl32.MB : c->nl.MB;
   o->tile_lb = (c->precision == 1) ? c->nl32.LB : c->nl.LB;
   o->tile_mbf = (c->precision == 1) ? c->nl32.MBf : c->nl.MBf;
+  o->tensor_theta = (c->precision == 0 && c->tensor_theta && c->d_dft_tc) ? 1 : 0;
   return TC_OK;
 }
 
