@@ -3,8 +3,8 @@
 // The inverse theta transform of k_theta (Sec. 2.1: Fourier-Galerkin in
 // theta) is a dense contraction: for every radial level and z row, the
 // physical values of each real field are u(theta_j) = sum_k F_jk x_k with
-// x = (Re a_0, Re a_1..Re a_M, Im a_1..Im a_M) and F_j0 = 1,
-// F_jm = 2 cos(m theta_j), F_j(M+m) = -2 sin(m theta_j).  k_theta_tc forms
+// x_2m = Re a_m, x_2m+1 = Im a_m (Im a_0 = 0) and F_j0 = 1, F_j1 = 0,
+// F_j,2m = 2 cos(m theta_j), F_j,2m+1 = -2 sin(m theta_j).  k_theta_tc forms
 // these products with tcgen05.mma in BF16 at FP64 accuracy by splitting both
 // operands into 7 slices of 8 significant bits (Ozaki et al., "Error-free
 // transformations of matrix multiplication by using fast routines of matrix
@@ -26,14 +26,14 @@
 // forward theta FFT in FP64 and the unpacking into W.
 //
 // Data path of one CTA (2 z rows of one radial level, 32 data columns):
-//   1. all threads: read V, slice the 48 columns into 7 BF16 operand tiles in
-//      shared memory (K-major core-matrix layout, no swizzle), one exponent
-//      per column;
+//   1. all threads (8 per column): read V, slice the 32 columns into 7 BF16
+//      operand tiles in shared memory (K-major core-matrix layout, no
+//      swizzle), one exponent per column;
 //   2. thread 0: stream the 21 chunks of the DFT matrix's slices (each 128
 //      rows x 32 coefficients, 8 KB, already in the operand layout) with 1-D
 //      bulk copies into a four-deep ring and issue 7 x 6 MMAs (M 128,
 //      N 32 (7 - i), K 16) into the seven level blocks of 32 TMEM columns;
-//   3. warps 0-3: read the accumulators (lane = theta row), combine them and
+//   3. all warps: read the accumulators (lane = theta row), combine them and
 //      write the physical fields (FP64) to shared memory;
 //   4. all threads: products, forward FFT, unpack (as k_theta).
 // Every wait is bounded (1 s); a wait that runs out sets the timeout flag of
@@ -53,7 +53,7 @@ namespace tc {
 namespace {
 
 constexpr int kTcM = 128;      // theta rows per MMA (Ntheta <= 128; zero rows beyond)
-constexpr int kTcK = 96;       // real coefficients per data column, padded (2M + 1 <= 96)
+constexpr int kTcK = 96;       // real coefficients per data column, padded (2 (M + 1) <= 96)
 constexpr int kTcN = 32;       // data columns per CTA: 2 z rows x 4 nf real fields (+ zeros)
 constexpr int kTcLB = 2;       // z rows per CTA
 constexpr int kTcS = 7;        // slices of each operand
@@ -106,43 +106,42 @@ __device__ __forceinline__ bool tc_wait(unsigned bar, unsigned phase) {
   }
 }
 
-// BF16 bits of an integer |d| <= 256 (exact).
-__device__ __forceinline__ unsigned short bf16_digit(int d) {
-  if (d == 0) return 0;
-  const unsigned sgn = d < 0 ? 0x8000u : 0u;
-  const unsigned a = (unsigned)(d < 0 ? -d : d);
-  const int e = 31 - __clz(a);                     // 0..8
-  const unsigned mant = e >= 7 ? (a >> (e - 7)) & 0x7Fu : (a << (7 - e)) & 0x7Fu;
-  return (unsigned short)(sgn | ((unsigned)(127 + e) << 7) | mant);
-}
-
-// round(|x| * 2^(56 - E)) with the sign of x, exactly (x finite, |x| < 2^E).
-__device__ __forceinline__ long long scaled_int(double x, int E) {
+// round(|x| 2^(56 - E)) for finite x with |x| < 2^E (ties away from zero).
+__device__ __forceinline__ unsigned long long scaled_mag(double x, int E) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int be = (int)((b >> 52) & 0x7FF);
   unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-  if (be == 0 && mant == 0) return 0;
-  int ex;
-  if (be == 0) {
-    ex = -1022;
-  } else {
-    mant |= 1ull << 52;
-    ex = be - 1023;
-  }
-  const int sh = ex + 4 - E;   // x = mant 2^(ex - 52): result = mant 2^(ex + 4 - E)
-  unsigned long long q;
-  if (sh >= 0) {
-    q = mant << sh;            // sh <= 3 since |x| < 2^E
-  } else if (sh < -60) {
-    q = 0;
-  } else {
-    const int r = -sh;
-    q = mant >> r;
-    const unsigned long long rem = mant & ((1ull << r) - 1ull);
-    const unsigned long long half = 1ull << (r - 1);
-    if (rem > half || (rem == half && (q & 1ull))) ++q;
-  }
-  return (b >> 63) ? -(long long)q : (long long)q;
+  if (be) mant |= 1ull << 52;
+  // |x| = mant 2^(ex - 52), ex = max(be, 1) - 1023: result mant 2^(ex + 4 - E)
+  const int sh = max(be, 1) - 1023 + 4 - E;
+  if (sh >= 0) return mant << sh;            // sh <= 3 since |x| < 2^E
+  const int rs = -sh;
+  if (rs >= 54) return 0ull;                 // mant + 2^(rs-1) < 2^rs
+  return (mant + (1ull << (rs - 1))) >> rs;
+}
+
+// The 7 slices of x / 2^E as FP32 bit patterns of integers (slice 0 the most
+// significant): q = round(|x| 2^(56 - E)) = sum_j d_j 256^(6 - j) with
+// balanced digits d_1..d_6 in [-128, 127] and d_0 in [-128, 256].  Adding
+// 0x80 to each of the 7 low bytes of q carries exactly where a digit borrows,
+// so the bytes t_b of t = q + 0x0080808080808080 give d = t_b - 128 (the top
+// digit t_6 + 256 t_7 - 128).  Each digit is formed in FP32 from the pattern
+// 0x4B4000tt = 1.5 2^23 + tt, scaled by the sign of x: exact, and exact in
+// BF16 (at most 8 significant bits).
+__device__ __forceinline__ void slice_value(double x, int E, unsigned out[kTcS]) {
+  const unsigned long long t = scaled_mag(x, E) + 0x0080808080808080ull;
+  const unsigned lo = (unsigned)t, hi = (unsigned)(t >> 32);
+  const float sg = __uint_as_float(0x3F800000u |
+                                   ((unsigned)((unsigned long long)__double_as_longlong(x) >> 32) &
+                                    0x80000000u));   // -1 or 1: the sign bit of x
+  const float c0 = -12583040.0f * sg;        // -(1.5 2^23 + 128)
+#pragma unroll
+  for (int b = 0; b < 4; ++b)   // bytes 0..3 -> slices 6..3
+    out[kTcS - 1 - b] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(lo, 0x4B40u, 0x5460 | b)), sg, c0));
+#pragma unroll
+  for (int b = 0; b < 2; ++b)   // bytes 4, 5 -> slices 2, 1
+    out[2 - b] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(hi, 0x4B40u, 0x5460 | b)), sg, c0));
+  out[0] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(hi, 0x4B40u, 0x5432)), sg, c0));
 }
 
 // Nearest double to a 64-bit integer, as bits (round to nearest even).
@@ -205,65 +204,58 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
   if (tid == 0)
     for (int st = 0; st < kTcRing; ++st) load_a(st);
 
-  // 1. the data columns of this tile, sliced.  Column n = li ncol + 4 c + q:
-  // z row li, field c, q = 0 value, 1 theta derivative, 2 d/dr, 3 d/dz.
-  // Coefficient k: 0 -> Re a_0, 1..M -> Re a_k, M+1..2M -> Im a_(k-M).
+  // 1. the data columns of this tile, sliced.  Thread t: column n = t / 8,
+  // part s8 = t % 8.  Column n = li ncol + 4 c + q: z row li, field c, q = 0
+  // value, 1 theta derivative, 2 d/dr, 3 d/dz.  Coefficient k = 2 m + h:
+  // h = 0 Re a_m, h = 1 Im a_m (Im a_0 taken as 0, as the real inverse FFT
+  // does); the thread holds m = 16 g + 2 s8 + {0, 1}, g = 0..2, so that one
+  // group g is four adjacent coefficients (one 8-byte store per slice).
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
-  constexpr int kColsPerWarp = kTcN / (kTcThreads / 32);   // 4
-  double xs[kColsPerWarp][3];
-#pragma unroll
-  for (int cw = 0; cw < kColsPerWarp; ++cw) {   // all loads first
-    const int n = warp + cw * (kTcThreads / 32);
+  {
+    const int n = tid >> 3, s8 = tid & 7;
     const int li = n / ncol, cq = n - li * ncol, c = cq >> 2, q = cq & 3;
+    const bool col = li < nl && cq < ncol;
+    const int d = q <= 1 ? 0 : q - 1;
+    const long long base = (3LL * c + d) * fs + ((long long)r * s.Nz + l0 + li) * s.NM;
+    double2 a[6];
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      const int k = lane + 32 * u;
-      double v = 0.0;
-      if (li < nl && cq < ncol && k <= 2 * M) {
-        const int m = k <= M ? k : k - M;
-        const bool im = k > M;
-        const int d = q <= 1 ? 0 : q - 1;
-        const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
-        const long long iv = (3 * c + d) * fs + off;
-        if (dbg_in(iv, 3LL * s.nf * fs, DBG_THETA_V)) {
-          const double2 a = Vin[iv];
-          if (q == 1)   // i m a_m: Re = -m Im a_m, Im = m Re a_m
-            v = im ? (double)m * a.x : -(double)m * a.y;
-          else
-            v = im ? a.y : a.x;
-        }
+    for (int u = 0; u < 6; ++u) {   // all loads first
+      const int m = 16 * (u >> 1) + 2 * s8 + (u & 1);
+      double2 v = double2{0.0, 0.0};
+      if (col && m <= M && dbg_in(base + m, 3LL * s.nf * fs, DBG_THETA_V)) {
+        v = Vin[base + m];
+        if (m == 0) v.y = 0.0;
+        if (q == 1) v = double2{-(double)m * v.y, (double)m * v.x};   // i m a_m
       }
-      xs[cw][u] = v;
+      a[u] = v;
     }
-  }
-#pragma unroll
-  for (int cw = 0; cw < kColsPerWarp; ++cw) {
-    const int n = warp + cw * (kTcThreads / 32);
-    // exponent of the column: E with max |x| < 2^E
+    // exponent of the column: E with max |x| < 2^E (the 8 threads of a column
+    // are 8 adjacent lanes)
     unsigned long long mb = 0ull;
 #pragma unroll
-    for (int u = 0; u < 3; ++u)
-      mb = max(mb, (unsigned long long)__double_as_longlong(xs[cw][u]) & 0x7FFFFFFFFFFFFFFFull);
-    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    for (int u = 0; u < 6; ++u) {
+      mb = max(mb, (unsigned long long)__double_as_longlong(a[u].x) & 0x7FFFFFFFFFFFFFFFull);
+      mb = max(mb, (unsigned long long)__double_as_longlong(a[u].y) & 0x7FFFFFFFFFFFFFFFull);
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
     const int E = mb ? (int)((mb >> 52) & 0x7FF) - 1022 : 0;   // 2^(e) <= max < 2^(e+1) = 2^E
-    if (lane == 0) colE[n] = E;
+    if (s8 == 0) colE[n] = E;
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      const int k = lane + 32 * u;
-      long long y = scaled_int(xs[cw][u], E);
-      int dig[kTcS];
+    for (int g = 0; g < 3; ++g) {
+      const double xv[4] = {a[2 * g].x, a[2 * g].y, a[2 * g + 1].x, a[2 * g + 1].y};
+      unsigned f[4][kTcS];
 #pragma unroll
-      for (int sl = kTcS - 1; sl >= 1; --sl) {
-        int lo = (int)(y & 255ll);
-        if (lo >= 128) lo -= 256;
-        dig[sl] = lo;
-        y = (y - lo) >> 8;
+      for (int v = 0; v < 4; ++v) slice_value(xv[v], E, f[v]);
+      const int k0 = 32 * g + 4 * s8;
+#pragma unroll
+      for (int sl = 0; sl < kTcS; ++sl) {
+        // BF16 = top half of the FP32 digit; the lower k in the lower half
+        uint2 w;
+        w.x = __byte_perm(f[0][sl], f[1][sl], 0x7632);
+        w.y = __byte_perm(f[2][sl], f[3][sl], 0x7632);
+        *reinterpret_cast<uint2 *>(sB + sl * kTcBSlice + b_off(n, k0)) = w;
       }
-      dig[0] = (int)y;
-#pragma unroll
-      for (int sl = 0; sl < kTcS; ++sl)
-        *reinterpret_cast<unsigned short *>(sB + sl * kTcBSlice + b_off(n, k)) =
-            bf16_digit(dig[sl]);
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -330,15 +322,20 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
   bool done = abort_s == 0 && tc_wait(smem_u32(&bars[2 * kTcRing]), 0u);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!done && tid == 0) atomicOr(timeout, 1);
-  // 3. accumulators -> physical fields P[n][j] (FP64), lane = theta row
+  // 3. accumulators -> physical fields P[n][j] (FP64), lane = theta row.
+  // Warp w reads TMEM lanes 32 (w % 4) ..; warps 0-3 take columns 0-15,
+  // warps 4-7 columns 16-31.
   double *P = reinterpret_cast<double *>(sm);   // over the data slices: the products are done
-  if (done && warp < 4) {
-    const int j = warp * 32 + lane;
-    for (int cb = 0; cb < kTcN / 8; ++cb) {
+  if (done) {
+    const int wq = warp & 3;
+    const int j = wq * 32 + lane;
+#pragma unroll 1
+    for (int cc = 0; cc < kTcN / 16; ++cc) {
+      const int cb = (warp >> 2) * (kTcN / 16) + cc;
       unsigned v[kTcLev][8];
 #pragma unroll
       for (int L = 0; L < kTcLev; ++L) {
-        const unsigned ta = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(L * kTcN + cb * 8);
+        const unsigned ta = tmem + ((unsigned)(wq * 32) << 16) + (unsigned)(L * kTcN + cb * 8);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
             : "=r"(v[L][0]), "=r"(v[L][1]), "=r"(v[L][2]), "=r"(v[L][3]), "=r"(v[L][4]),
@@ -349,11 +346,12 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int n = cb * 8 + t;
-        // level L holds the integer S_L of weight 2^(-8L); in units of 2^-40
-        long long I = 0;
+        // level L holds the integer S_L of weight 2^(-8L): Horner in units of
+        // 2^-40, the last level rounded to that unit
+        long long I = (long long)__float2int_rn(__uint_as_float(v[0][t]));
 #pragma unroll
-        for (int L = 0; L < kTcLev - 1; ++L)
-          I += (long long)__float2int_rn(__uint_as_float(v[L][t])) << (40 - 8 * L);
+        for (int L = 1; L < kTcLev - 1; ++L)
+          I = I * 256 + (long long)__float2int_rn(__uint_as_float(v[L][t]));
         I += (long long)__float2int_rn(__uint_as_float(v[kTcLev - 1][t]) * 0.00390625f);
         // value = I 2^-40 2^-16 2^(E+1): F/2 and x/2^E each carry a 2^-8
         unsigned long long bits = ll_to_double_bits(I);
@@ -480,14 +478,14 @@ void build_theta_dft(int Nt, int Mm, std::vector<unsigned short> &out) {
   const long double pi = 3.141592653589793238462643383279502884L;
   for (int j = 0; j < kTcM; ++j)
     for (int k = 0; k < kTcK; ++k) {
-      long double y = 0.0L;   // F/2
-      if (j < Nt && k <= 2 * Mm) {
-        if (k == 0) {
-          y = 0.5L;
+      long double y = 0.0L;   // F/2; column k = 2 m + h
+      const int m = k >> 1, h = k & 1;
+      if (j < Nt && m <= Mm) {
+        if (m == 0) {
+          y = h ? 0.0L : 0.5L;
         } else {
-          const int m = k <= Mm ? k : k - Mm;
           const long double ang = 2.0L * pi * (long double)((long long)m * j % Nt) / Nt;
-          y = k <= Mm ? std::cos(ang) : -std::sin(ang);
+          y = h ? -std::sin(ang) : std::cos(ang);
         }
       }
       long long Y = host_scaled_int(y);
@@ -507,7 +505,7 @@ void build_theta_dft(int Nt, int Mm, std::vector<unsigned short> &out) {
 }
 
 bool theta_tc_supported(const Sizes &s) {
-  return s.Nt <= kTcM && 2 * s.M + 1 <= kTcK && kTcLB * 4 * s.nf <= kTcN;
+  return s.Nt <= kTcM && 2 * (s.M + 1) <= kTcK && kTcLB * 4 * s.nf <= kTcN;
 }
 
 size_t theta_tc_table_bytes() { return (size_t)kTcStages * kTcAChunk; }
