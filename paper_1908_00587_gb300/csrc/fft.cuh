@@ -306,14 +306,28 @@ __device__ __forceinline__ void butterfly(const V *__restrict__ s, V *__restrict
     if (dbg_in(spad(base + p * Ns), npad, DBG_FFT_SMEM)) d[spad(base + p * Ns)] = v[p];
 }
 
+// Thread index rotated by rot (0 <= rot < blockDim.x): the loops below hand
+// butterfly t to thread (t - rot) mod blockDim.x, so that a pass with fewer
+// butterflies than threads does not always land on the first warps (the
+// warps of one index share a scheduler partition in every CTA of the SM).
+__device__ __forceinline__ int rot_tid(int rot) {
+  const int t = (int)threadIdx.x + rot;
+  return t >= (int)blockDim.x ? t - (int)blockDim.x : t;
+}
+
+// rot for the tile (bx, by): one warp further per tile, mod 4 warps
+__device__ __forceinline__ int tile_rot(int bx, int by) {
+  return (((bx + by) & 3) * 32) % (int)blockDim.x;
+}
+
 template <int R, int S, bool ZMID, typename V>
 __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__restrict__ dst,
                                               const FFTPlan &pl, int p, int Ns, int batch,
-                                              int bstride, const V *__restrict__ twp) {
+                                              int bstride, const V *__restrict__ twp, int rot) {
   const int nb = pl.n / R;
   const int total = nb * batch;
   const FastDiv dnb = pl.div_nb[p], dns = pl.div_ns[p];
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+  for (int t = rot_tid(rot); t < total; t += blockDim.x) {
     const int b = fdiv(t, dnb);
     const int j = t - b * nb;
     butterfly<R, S, ZMID>(src + b * bstride, dst + b * bstride, j, nb, Ns, dns, twp);
@@ -328,13 +342,13 @@ __device__ __forceinline__ void stockham_pass(const V *__restrict__ src, V *__re
 template <int R, int S, bool ZMID, int N, int NS, typename V>
 __device__ __forceinline__ void stockham_pass_fixed(const V *__restrict__ src, V *__restrict__ dst,
                                                     int batch, int bstride,
-                                                    const V *__restrict__ twp) {
+                                                    const V *__restrict__ twp, int rot) {
   using T = decltype(src[0].x);
   constexpr int nb = N / R;
   static_assert((nb & (nb - 1)) == 0 && nb % 8 == 0, "power-of-two stride, multiple of 8");
   constexpr int in_step = nb + nb / 8;   // spad distance between inputs q and q + 1
   const int total = nb * batch;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+  for (int t = rot_tid(rot); t < total; t += blockDim.x) {
     const int bi = t / nb;
     const int j = t - bi * nb;
     const V *s = src + bi * bstride;
@@ -383,19 +397,19 @@ __device__ __forceinline__ void stockham_pass_fixed(const V *__restrict__ src, V
 
 template <int S, int N, typename V>
 __device__ V *fft_batch_fixed(V *a, V *b, const FFTPlan &pl, int batch, int bstride,
-                              const V *__restrict__ tw, bool zmid) {
+                              const V *__restrict__ tw, bool zmid, int rot) {
   // plans of make_plan: 64 = 8 8, 128 = 8 4 4, 256 = 8 8 4, 512 = 8 8 8
   constexpr int R1 = (N == 128) ? 4 : 8;
   constexpr int R2 = (N == 64) ? 0 : (N == 512 ? 8 : 4);
-  if (zmid) stockham_pass_fixed<8, S, true, N, 1>(a, b, batch, bstride, tw);
-  else stockham_pass_fixed<8, S, false, N, 1>(a, b, batch, bstride, tw);
+  if (zmid) stockham_pass_fixed<8, S, true, N, 1>(a, b, batch, bstride, tw, rot);
+  else stockham_pass_fixed<8, S, false, N, 1>(a, b, batch, bstride, tw, rot);
   __syncthreads();
-  stockham_pass_fixed<R1, S, false, N, 8>(b, a, batch, bstride, tw + pl.tw_off[1]);
+  stockham_pass_fixed<R1, S, false, N, 8>(b, a, batch, bstride, tw + pl.tw_off[1], rot);
   __syncthreads();
   if constexpr (R2 == 0) {
     return a;
   } else {
-    stockham_pass_fixed<R2, S, false, N, 8 * R1>(a, b, batch, bstride, tw + pl.tw_off[2]);
+    stockham_pass_fixed<R2, S, false, N, 8 * R1>(a, b, batch, bstride, tw + pl.tw_off[2], rot);
     __syncthreads();
     return b;
   }
@@ -406,15 +420,17 @@ __device__ V *fft_batch_fixed(V *a, V *b, const FFTPlan &pl, int batch, int bstr
 // must call it; it ends with a __syncthreads().  zmid: the caller guarantees
 // that every input vanishes on [3N/8, 5N/8) and the plan starts with radix 8
 // (see zmid_ok); the first pass then skips those inputs.  Lengths 64..512
-// take the compile-time passes above.
+// take the compile-time passes above.  rot: thread rotation of the passes
+// (rot_tid; 0 <= rot < blockDim.x), which changes only which thread computes
+// a butterfly.
 template <int S, typename V>
 __device__ V *fft_batch(V *a, V *b, const FFTPlan &pl, int batch, int bstride,
-                        const V *__restrict__ tw, bool zmid = false) {
+                        const V *__restrict__ tw, bool zmid = false, int rot = 0) {
   switch (pl.n) {
-    case 64: return fft_batch_fixed<S, 64>(a, b, pl, batch, bstride, tw, zmid);
-    case 128: return fft_batch_fixed<S, 128>(a, b, pl, batch, bstride, tw, zmid);
-    case 256: return fft_batch_fixed<S, 256>(a, b, pl, batch, bstride, tw, zmid);
-    case 512: return fft_batch_fixed<S, 512>(a, b, pl, batch, bstride, tw, zmid);
+    case 64: return fft_batch_fixed<S, 64>(a, b, pl, batch, bstride, tw, zmid, rot);
+    case 128: return fft_batch_fixed<S, 128>(a, b, pl, batch, bstride, tw, zmid, rot);
+    case 256: return fft_batch_fixed<S, 256>(a, b, pl, batch, bstride, tw, zmid, rot);
+    case 512: return fft_batch_fixed<S, 512>(a, b, pl, batch, bstride, tw, zmid, rot);
     default: break;
   }
   int Ns = 1;
@@ -422,14 +438,14 @@ __device__ V *fft_batch(V *a, V *b, const FFTPlan &pl, int batch, int bstride,
     const int R = pl.radix[p];
     const V *twp = tw + pl.tw_off[p];
     if (p == 0 && zmid) {
-      stockham_pass<8, S, true>(a, b, pl, p, Ns, batch, bstride, twp);
+      stockham_pass<8, S, true>(a, b, pl, p, Ns, batch, bstride, twp, rot);
     } else {
       switch (R) {
-        case 8: stockham_pass<8, S, false>(a, b, pl, p, Ns, batch, bstride, twp); break;
-        case 4: stockham_pass<4, S, false>(a, b, pl, p, Ns, batch, bstride, twp); break;
-        case 2: stockham_pass<2, S, false>(a, b, pl, p, Ns, batch, bstride, twp); break;
-        case 3: stockham_pass<3, S, false>(a, b, pl, p, Ns, batch, bstride, twp); break;
-        default: stockham_pass<5, S, false>(a, b, pl, p, Ns, batch, bstride, twp); break;
+        case 8: stockham_pass<8, S, false>(a, b, pl, p, Ns, batch, bstride, twp, rot); break;
+        case 4: stockham_pass<4, S, false>(a, b, pl, p, Ns, batch, bstride, twp, rot); break;
+        case 2: stockham_pass<2, S, false>(a, b, pl, p, Ns, batch, bstride, twp, rot); break;
+        case 3: stockham_pass<3, S, false>(a, b, pl, p, Ns, batch, bstride, twp, rot); break;
+        default: stockham_pass<5, S, false>(a, b, pl, p, Ns, batch, bstride, twp, rot); break;
       }
     }
     __syncthreads();

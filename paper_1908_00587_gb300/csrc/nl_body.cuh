@@ -174,7 +174,7 @@ __device__ __forceinline__ void zinv_body(const V2<T> *__restrict__ X, V2<T> *__
     }
   }
   __syncthreads();
-  V2<T> *res = fft_batch<+1>(A, B, p.pz, 3 * nm, Np, tw, zmid_ok(p.pz, s.K));
+  V2<T> *res = fft_batch<+1>(A, B, p.pz, 3 * nm, Np, tw, zmid_ok(p.pz, s.K), tile_rot(bx, by + bz));
   for (int t = threadIdx.x; t < 3 * nm * Nz; t += blockDim.x) {
     const int2 a = divmod(t, nm, fnm);
     const int mi = a.y;
@@ -244,7 +244,7 @@ __device__ __forceinline__ void theta_body(const V2<T> *__restrict__ Vin, V2<T> 
     }
   }
   __syncthreads();
-  V2<T> *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Ntp, tw, zmid_ok(p.pt, s.M));
+  V2<T> *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Ntp, tw, zmid_ok(p.pt, s.M), tile_rot(bx, by));
   V2<T> *out = (ph == A) ? B : A;
   const double rr = p.rad.r[r];
   T inv_r;
@@ -365,7 +365,7 @@ __device__ __forceinline__ void theta_body(const V2<T> *__restrict__ Vin, V2<T> 
     atomic_max_pos(rate_bits, rate);
   }
   V2<T> *scratch = (out == A) ? B : A;
-  V2<T> *sp = fft_batch<-1>(out, scratch, p.pt, nl * 2, Ntp, tw);
+  V2<T> *sp = fft_batch<-1>(out, scratch, p.pt, nl * 2, Ntp, tw, false, tile_rot(bx, by));
   // unpack two real transforms: X_m = (Z_m + conj Z_-m)/2, Y_m = (Z_m - conj Z_-m)/(2i);
   // the factor 1/2 is left to k_zfwd's final scaling (exact: a power of two)
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
@@ -419,7 +419,7 @@ __device__ __forceinline__ void zfwd_body(const V2<T> *__restrict__ W, double2 *
       A[(g * nm + mi) * Np + spad(l)] = W[iw];
   }
   __syncthreads();
-  V2<T> *res = fft_batch<-1>(A, B, p.pz, nb, Np, tw);
+  V2<T> *res = fft_batch<-1>(A, B, p.pz, nb, Np, tw, false, tile_rot(bx, by));
   // 1/(Ntheta Nz), times the 1/2 of k_theta's unpacking of paired transforms
   // (set on the host: a division here would cost every warp FP64 turns)
   const double scale = p.zscale;

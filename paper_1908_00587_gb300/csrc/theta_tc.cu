@@ -1,52 +1,41 @@
 // Azimuthal transforms of the FP64 nonlinear stage on the tensor cores.
 //
-// Both theta transforms of k_theta (Sec. 2.1: Fourier-Galerkin in theta,
-// products on the physical grid) are dense contractions.  Inverse: for every
-// radial level and z row, the physical values of each real field are
-// u(theta_j) = sum_k F_jk x_k with x_2m = Re a_m, x_2m+1 = Im a_m (Im a_0 = 0)
-// and F_j0 = 1, F_j1 = 0, F_j,2m = 2 cos(m theta_j), F_j,2m+1 =
-// -2 sin(m theta_j).  Forward: the products P_j (u.grad u with curvature
-// terms, buoyancy) go back as W_2m + i W_2m+1 = 2 sum_j P_j e^(-i m theta_j),
-// i.e. W = G P with G_2m,j = 2 cos(m theta_j), G_2m+1,j = -2 sin(m theta_j)
-// (the unnormalised DFT doubled, which is what k_theta's packed FFT and its
-// unpacking leave for k_zfwd's final scaling).  k_theta_tc forms both
-// products with tcgen05.mma in BF16 at FP64 accuracy by splitting both
+// The inverse theta transform of k_theta (Sec. 2.1: Fourier-Galerkin in
+// theta) is a dense contraction: for every radial level and z row, the
+// physical values of each real field are u(theta_j) = sum_k F_jk x_k with
+// x_2m = Re a_m, x_2m+1 = Im a_m (Im a_0 = 0) and F_j0 = 1, F_j1 = 0,
+// F_j,2m = 2 cos(m theta_j), F_j,2m+1 = -2 sin(m theta_j).  k_theta_tc forms
+// these products with tcgen05.mma in BF16 at FP64 accuracy by splitting both
 // operands into 7 slices of 8 significant bits (Ozaki et al., "Error-free
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication", Numer. Algorithms 59, 2012):
 //   F/2   = 2^-8 sum_i a_i 2^-8i,   x/2^E = 2^-8 sum_j b_j 2^-8j,
-// a_i, b_j integers, |a_0|, |b_0| <= 256, the others <= 128 (E: exponent of
-// the data column).  The products a_i b_j are exact in BF16 x BF16 -> FP32.
-// The data slices sit one above the other along N, so one MMA with A = a_i
-// and B = (b_0 .. b_(6-i)) adds a_i b_j to TMEM column block i + j: seven
-// level blocks.  Level L sums at most K (2 256 128 + (L - 1) 128^2) =
-// K 2^14 (L + 3) in magnitude: below 2^24, so exact, for every level of the
-// inverse (K = 96) and levels 0..5 of the forward (K = 128); level 6 of the
-// forward may round, at 2^-48 of level 0 (below 2^-60 of the result).
-// Levels above 6 are below 2^-56 of the result and are not formed (28 of the
-// 49 slice products).  The level sums are combined exactly in 64-bit
-// integers and rounded once to FP64.  The theta derivative is the inverse
-// product applied to i m a_m.
+// a_i, b_j integers in [-256, 256] (E: exponent of the data column).  The
+// products a_i b_j are exact in BF16 x BF16 -> FP32, and so is the sum of all
+// pairs of one level L = i + j over the at most 96 coefficients (at most 7
+// pairs x 96 terms, below 2^24).  The slices of the data sit one above the
+// other along N, so one MMA with A = a_i and B = (b_0 .. b_(6-i)) adds a_i b_j
+// to TMEM column block i + j: seven level blocks, each exact.  Levels above 6
+// are below 2^-56 of the result and are not formed (28 of the 49 slice
+// products).  The level sums are combined exactly in 64-bit integers and
+// rounded once to FP64.  The theta derivative is the same product applied to
+// i m a_m.
 //
-// Data path of one CTA (2 z rows of one radial level):
-//   1. all threads (8 per column): read V, slice the 32 columns (4 per field:
-//      value, d/dtheta, d/dr, d/dz) into 7 BF16 operand tiles in shared
-//      memory (K-major core-matrix layout, no swizzle), one exponent per
-//      column;
-//   2. thread 0: stream the 21 chunks of the inverse matrix's slices (128
-//      rows x 32 coefficients, already in the operand layout) with 1-D bulk
-//      copies into a four-deep ring and issue 7 x 6 MMAs (M 128, N 32 (7 - i),
-//      K 16) into the seven level blocks of 32 TMEM columns;
+// The rest of the stage is k_theta's: the products u.grad u (with curvature
+// terms, buoyancy and the CFL rate) in FP64 on the physical grid, then the
+// forward theta FFT in FP64 and the unpacking into W.
+//
+// Data path of one CTA (2 z rows of one radial level, 32 data columns):
+//   1. all threads (8 per column): read V, slice the 32 columns into 7 BF16
+//      operand tiles in shared memory (K-major core-matrix layout, no
+//      swizzle), one exponent per column;
+//   2. thread 0: stream the 21 chunks of the DFT matrix's slices (each 128
+//      rows x 32 coefficients, 8 KB, already in the operand layout) with 1-D
+//      bulk copies into a four-deep ring and issue 7 x 6 MMAs (M 128,
+//      N 32 (7 - i), K 16) into the seven level blocks of 32 TMEM columns;
 //   3. all warps: read the accumulators (lane = theta row), combine them and
 //      write the physical fields (FP64) to shared memory;
-//   4. all threads: the products on the physical grid in FP64 (as k_theta),
-//      the CFL rate, one exponent per product column;
-//   5. all threads: slice the 8 product columns (2 z rows x 4) into 8-column
-//      blocks;
-//   6. thread 0: the 28 chunks of the forward matrix's slices through the
-//      same ring (the first ones already fetched during step 2), 7 x 8 MMAs
-//      (M 128, N 8 (7 - i) rounded up to 16, K 16) into 8-column level
-//      blocks; all warps read them back (lane = coefficient row) and write W.
+//   4. all threads: products, forward FFT, unpack (as k_theta).
 // Every wait is bounded (1 s); a wait that runs out sets the timeout flag of
 // the context, and the CTA waits (bounded) for its copies in flight, frees
 // its tensor memory and returns.
@@ -57,24 +46,22 @@
 #include <cstring>
 #include <vector>
 
+#include "fft.cuh"
 #include "nl_body.cuh"
 #include "tc_internal.h"
 
 namespace tc {
 namespace {
 
-constexpr int kTcM = 128;      // rows per MMA: theta points (inverse), coefficients (forward)
+constexpr int kTcM = 128;      // theta rows per MMA (Ntheta <= 128; zero rows beyond)
 constexpr int kTcK = 96;       // real coefficients per data column, padded (2 (M + 1) <= 96)
 constexpr int kTcN = 32;       // data columns per CTA: 2 z rows x 4 nf real fields (+ zeros)
 constexpr int kTcLB = 2;       // z rows per CTA
 constexpr int kTcS = 7;        // slices of each operand
-constexpr int kTcLev = 7;      // level blocks (kTcN TMEM columns each in the inverse)
-constexpr int kTcKc = 32;      // contraction elements per streamed chunk of a DFT-matrix slice
-constexpr int kTcChunks = kTcK / kTcKc;       // 3 per slice of the inverse matrix
-constexpr int kTcStages = kTcChunks * kTcS;   // 21 inverse chunks
-constexpr int kTcFChunks = kTcM / kTcKc;      // 4 per slice of the forward matrix (Ntheta <= 128)
-constexpr int kTcFStages = kTcFChunks * kTcS; // 28 forward chunks
-constexpr int kTcAll = kTcStages + kTcFStages;
+constexpr int kTcLev = 7;      // level blocks of kTcN TMEM columns each
+constexpr int kTcKc = 32;      // coefficients per streamed chunk of a DFT-matrix slice
+constexpr int kTcChunks = kTcK / kTcKc;   // 3 per slice
+constexpr int kTcStages = kTcChunks * kTcS;   // 21
 constexpr int kTcRing = 4;     // chunks in flight
 constexpr int kTcThreads = 256;
 // Operand layouts in shared memory (K-major, no swizzle): core matrices of 8
@@ -85,13 +72,6 @@ constexpr int kTcBBytes = kTcS * kTcBSlice;                     // 43008
 constexpr int kTcAChunk = (kTcM / 8) * (kTcKc / 8) * 128;      // 8192 B per chunk
 constexpr int kTcSmem = kTcBBytes + kTcRing * kTcAChunk;        // 75776: three CTAs per SM
 constexpr int kTcTmemCols = 256;
-// forward transform: 8 data columns (2 z rows x 4 products) per slice block,
-// 8 blocks (the 7 slices and one zero block, so that every stacked N is a
-// multiple of 16), 8 level blocks of 8 TMEM columns
-constexpr int kTcFN = 8;
-constexpr int kTcFBlock = kTcFN * kTcM * 2;                     // 2048 B
-constexpr int kTcFTmemCols = 64;
-constexpr int kTcPfOff = 32768;   // FP64 products [8][128] (after the physical fields)
 constexpr long long kTcWaitNs = 1000000000LL;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -189,19 +169,15 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
   const int nl = min(LB, s.Nz - l0);
   const int r = blockIdx.y;
   const int Nt = s.Nt;
+  const int Ntp = padlen(Nt);
   const int M = s.M;
   const int ncol = 4 * s.nf;                      // data columns per z row
-  // bytes streamed per chunk: the rows that are not zero (theta points of
-  // the inverse matrix, coefficients of the forward one), in groups of 8
-  const unsigned inv_bytes = (unsigned)((Nt + 7) >> 3) * 512u;
-  const unsigned fwd_bytes = (unsigned)((2 * (M + 1) + 7) >> 3) * 512u;
   extern __shared__ __align__(128) unsigned char sm[];
   unsigned char *sB = sm;
   unsigned char *sA = sm + kTcBBytes;
   __shared__ __align__(8) unsigned long long bars[2 * kTcRing + 1];   // full, free, done
   __shared__ unsigned tmem_s;
   __shared__ int colE[kTcN];
-  __shared__ unsigned colMax[kTcLB * 4];          // high words of max |product| per column
   __shared__ int abort_s;
   __shared__ unsigned long long cfl_cta[3];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -213,90 +189,21 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < 3) cfl_cta[tid] = 0ull;
-  if (tid < kTcLB * 4) colMax[tid] = 0u;
   __syncthreads();
   // thread 0's count of chunks whose copies were started / waited for
   int loaded = 0, consumed = 0;
-  // chunk st of the DFT matrices: 0..20 inverse (slice st / 3), 21..48
-  // forward (slice (st - 21) / 4), into ring buffer st % 4
+  // chunk st of the DFT matrix into ring buffer st % kTcRing
   auto load_a = [&](int st) {
     loaded = st + 1;
     const int b = st % kTcRing;
     const unsigned bar = smem_u32(&bars[b]);
-    const unsigned bytes = st < kTcStages ? inv_bytes : fwd_bytes;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(bar), "r"(bytes) : "memory");
+                 :: "r"(bar), "r"((unsigned)kTcAChunk) : "memory");
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
         :: "r"(smem_u32(sA + b * kTcAChunk)), "l"(dft + (size_t)st * kTcAChunk),
-           "r"(bytes), "r"(bar)
+           "r"((unsigned)kTcAChunk), "r"(bar)
         : "memory");
-  };
-  // thread 0: the products of chunks st0 .. st1-1 (bounded waits; false if
-  // one ran out), refilling each buffer once its products are done; the
-  // done barrier is signalled either way, once the products issued are done
-  auto issue = [&](int st0, int st1, unsigned tm, unsigned bbase, bool fwd) -> bool {
-    bool ok = true;
-    for (int st = st0; st < st1 && ok; ++st) {
-      const int u = st - st0;
-      const int i = fwd ? u / kTcFChunks : u / kTcChunks;
-      const int ch = fwd ? u - i * kTcFChunks : u - i * kTcChunks;
-      const int buf = st % kTcRing;
-      if (!tc_wait(smem_u32(&bars[buf]), (unsigned)(st / kTcRing) & 1u)) {
-        ok = false;
-        break;
-      }
-      consumed = st + 1;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // A = slice i of the DFT matrix (this chunk), B = data slices 0 .. 6 - i
-      // stacked along N, D = level blocks i .. 6 (forward: N rounded up to a
-      // multiple of 16 with the next block, whose products land in level 7)
-      const int nB = fwd ? ((kTcLev - i) * kTcFN + 15) & ~15 : (kTcLev - i) * kTcN;
-      const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                             ((unsigned)(nB >> 3) << 17) | ((unsigned)(kTcM >> 4) << 24);
-      const unsigned abase = smem_u32(sA + buf * kTcAChunk);
-      const unsigned dcol = tm + (unsigned)(i * (fwd ? kTcFN : kTcN));
-      const unsigned bsbo = fwd ? (kTcM / 8) * 128 : (kTcK / 8) * 128;
-#pragma unroll
-      for (int t = 0; t < kTcKc / 16; ++t) {
-        const unsigned long long ad = tc_desc(abase + t * 256, 128, (kTcKc / 8) * 128);
-        const unsigned long long bd = tc_desc(bbase + (ch * (kTcKc / 8) + 2 * t) * 128, 128, bsbo);
-        // the first product (slice 0, elements 0..15) initialises every block
-        const unsigned en = (u == 0 && t == 0) ? 0u : 1u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-            :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(en) : "memory");
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&bars[kTcRing + buf])) : "memory");
-      // refill the buffer of the previous chunk once its products are done
-      if (st >= 1 && st - 1 + kTcRing < kTcAll) {
-        const int pb = (st - 1) % kTcRing;
-        if (!tc_wait(smem_u32(&bars[kTcRing + pb]), (unsigned)((st - 1) / kTcRing) & 1u)) {
-          ok = false;
-          break;
-        }
-        load_a(st - 1 + kTcRing);
-      }
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 :: "r"(smem_u32(&bars[2 * kTcRing])) : "memory");
-    return ok;
-  };
-  // thread 0, after a wait ran out: wait (bounded) for the copies still in
-  // flight, so that none lands after the CTA has left
-  auto drain = [&]() {
-    for (int st = consumed; st < loaded; ++st)
-      if (!tc_wait(smem_u32(&bars[st % kTcRing]), (unsigned)(st / kTcRing) & 1u)) break;
-  };
-  auto tmem_alloc = [&](unsigned cols) {   // warp 0
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_s)), "r"(cols) : "memory");
-  };
-  auto tmem_free = [&](unsigned tm, unsigned cols) {   // warp 0
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-                 :: "r"(tm), "r"(cols) : "memory");
   };
   if (tid == 0)
     for (int st = 0; st < kTcRing; ++st) load_a(st);
@@ -358,40 +265,78 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   // tensor memory only now, for the products and the read-back (another CTA
   // on this SM may hold it meanwhile: the allocation waits for it)
-  if (warp == 0) tmem_alloc(kTcTmemCols);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_s)), "r"(kTcTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  unsigned tmem = tmem_s;
+  const unsigned tmem = tmem_s;
 
-  // 2. the inverse slice products (thread 0 issues them)
-  if (tid == 0 && !issue(0, kTcStages, tmem, smem_u32(sB), false)) abort_s = 1;
+  // 2. the slice products (thread 0 issues them)
+  if (tid == 0) {
+    bool ok = true;
+    for (int st = 0; st < kTcStages && ok; ++st) {
+      const int i = st / kTcChunks, ch = st - i * kTcChunks, buf = st % kTcRing;
+      if (!tc_wait(smem_u32(&bars[buf]), (unsigned)(st / kTcRing) & 1u)) {
+        ok = false;
+        break;
+      }
+      consumed = st + 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // A = slice i of the DFT matrix (this chunk), B = data slices 0 .. 6 - i
+      // stacked along N, D = level blocks i .. 6
+      const int nB = (kTcLev - i) * kTcN;
+      const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                             ((unsigned)(nB >> 3) << 17) | ((unsigned)(kTcM >> 4) << 24);
+      const unsigned abase = smem_u32(sA + buf * kTcAChunk);
+      const unsigned dcol = tmem + (unsigned)(i * kTcN);
+#pragma unroll
+      for (int t = 0; t < kTcKc / 16; ++t) {
+        const unsigned long long ad = tc_desc(abase + t * 256, 128, (kTcKc / 8) * 128);
+        const unsigned long long bd =
+            tc_desc(smem_u32(sB) + (ch * (kTcKc / 8) + 2 * t) * 128, 128, (kTcK / 8) * 128);
+        // the first product (slice 0, coefficients 0..15) initialises every block
+        const unsigned en = (st == 0 && t == 0) ? 0u : 1u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(en) : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&bars[kTcRing + buf])) : "memory");
+      // refill the buffer of the previous stage once its products are done
+      if (st >= 1 && st - 1 + kTcRing < kTcStages) {
+        const int pb = (st - 1) % kTcRing;
+        if (!tc_wait(smem_u32(&bars[kTcRing + pb]), (unsigned)((st - 1) / kTcRing) & 1u)) {
+          ok = false;
+          break;
+        }
+        load_a(st - 1 + kTcRing);
+      }
+    }
+    // the done barrier is signalled either way, once the products issued are done
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(&bars[2 * kTcRing])) : "memory");
+    if (!ok) abort_s = 1;
+  }
   __syncthreads();
   // the same verdict in every thread
-  bool done = __syncthreads_and(tc_wait(smem_u32(&bars[2 * kTcRing]), 0u)) && abort_s == 0;
+  const bool done = __syncthreads_and(tc_wait(smem_u32(&bars[2 * kTcRing]), 0u)) && abort_s == 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!done && tid == 0) {
     atomicOr(timeout, 1);
-    drain();
+    // wait (bounded) for the copies still in flight, so that none lands
+    // after the CTA has left
+    for (int st = consumed; st < loaded; ++st)
+      if (!tc_wait(smem_u32(&bars[st % kTcRing]), (unsigned)(st / kTcRing) & 1u)) break;
   }
   // 3. accumulators -> physical fields P[n][j] (FP64), lane = theta row.
   // Warp w reads TMEM lanes 32 (w % 4) ..; warps 0-3 take columns 0-15,
   // warps 4-7 columns 16-31.
   double *P = reinterpret_cast<double *>(sm);   // over the data slices: the products are done
-  auto combine = [](const unsigned (&v)[kTcLev], int E) -> double {
-    // level L holds the integer S_L of weight 2^(-8L): Horner in units of
-    // 2^-40, the last level rounded to that unit
-    long long I = (long long)__float2int_rn(__uint_as_float(v[0]));
-#pragma unroll
-    for (int L = 1; L < kTcLev - 1; ++L)
-      I = I * 256 + (long long)__float2int_rn(__uint_as_float(v[L]));
-    I += (long long)__float2int_rn(__uint_as_float(v[kTcLev - 1]) * 0.00390625f);
-    // value = I 2^-40 2^-16 2^(E+1): the matrix (halved) and x/2^E each
-    // carry a 2^-8, the matrix's 1/2 is restored
-    unsigned long long bits = ll_to_double_bits(I);
-    if (bits & 0x7FFFFFFFFFFFFFFFull) bits += (unsigned long long)(long long)(E - 55) << 52;
-    return __longlong_as_double((long long)bits);
-  };
   if (done) {
     const int wq = warp & 3;
     const int j = wq * 32 + lane;
@@ -412,33 +357,41 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int n = cb * 8 + t;
-        unsigned lv[kTcLev];
+        // level L holds the integer S_L of weight 2^(-8L): Horner in units of
+        // 2^-40, the last level rounded to that unit
+        long long I = (long long)__float2int_rn(__uint_as_float(v[0][t]));
 #pragma unroll
-        for (int L = 0; L < kTcLev; ++L) lv[L] = v[L][t];
-        P[n * kTcM + j] = combine(lv, colE[n]);
+        for (int L = 1; L < kTcLev - 1; ++L)
+          I = I * 256 + (long long)__float2int_rn(__uint_as_float(v[L][t]));
+        I += (long long)__float2int_rn(__uint_as_float(v[kTcLev - 1][t]) * 0.00390625f);
+        // value = I 2^-40 2^-16 2^(E+1): F/2 and x/2^E each carry a 2^-8
+        unsigned long long bits = ll_to_double_bits(I);
+        if (bits & 0x7FFFFFFFFFFFFFFFull) bits += (unsigned long long)(long long)(colE[n] - 55) << 52;
+        P[n * kTcM + j] = __longlong_as_double((long long)bits);
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) tmem_free(tmem, kTcTmemCols);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(tmem), "r"(kTcTmemCols) : "memory");
   if (!done) return;
 
-  // 4. products on the physical grid (as k_theta): one point per thread,
-  // the four products of z row li into columns 4 li .. 4 li + 3 of Pf
-  double *Pf = reinterpret_cast<double *>(sm + kTcPfOff);
+  // 4. products on the physical grid (as k_theta), forward FFT, unpack
+  double2 *out = reinterpret_cast<double2 *>(sm + kTcN * kTcM * sizeof(double));
+  double2 *scratch = out + 2 * LB * Ntp;
+  double2 *tw = scratch + 2 * LB * Ntp;
+  load_tw<double>(tw, p.twt, p.twt32, Nt);
   const double rr = p.rad.r[r];
   const double inv_r = p.rad.inv_r[r];
+  unsigned long long mr = 0ull, mt = 0ull, mz = 0ull;
   const bool centrifugal = p.eps_c != 0.0;
   auto bitsabs = [](double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
   };
-  unsigned long long mr = 0ull, mt = 0ull, mz = 0ull;
-  unsigned hmax[4] = {0u, 0u, 0u, 0u};
-  int my_li = -1;
-  if (tid < nl * Nt) {   // nl * Nt <= 256 threads
-    const int li = tid / Nt, j = tid - li * Nt;
-    my_li = li;
+  for (int t = tid; t < nl * Nt; t += blockDim.x) {
+    const int li = t / Nt, j = t - li * Nt;
     const double *f = P + (li * ncol) * kTcM + j;   // field c, q at f[(4c + q) kTcM]
     const double ur = f[0], ur_t = f[kTcM], ur_r = f[2 * kTcM], ur_z = f[3 * kTcM];
     const double ut = f[4 * kTcM], ut_t = f[5 * kTcM], ut_r_ = f[6 * kTcM], ut_z = f[7 * kTcM];
@@ -462,29 +415,15 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
       Nz_ += p.Gr * T;
       NT_ = -(ur * T_r + ut_r * T_t + uz * T_z);
     }
-    double *o = Pf + (li * 4) * kTcM + j;
-    o[0] = Nr_;
-    o[kTcM] = Nt_;
-    o[2 * kTcM] = Nz_;
-    o[3 * kTcM] = NT_;
-    hmax[0] = (unsigned)(bitsabs(Nr_) >> 32);
-    hmax[1] = (unsigned)(bitsabs(Nt_) >> 32);
-    hmax[2] = (unsigned)(bitsabs(Nz_) >> 32);
-    hmax[3] = (unsigned)(bitsabs(NT_) >> 32);
+    double2 *o = out + li * 2 * Ntp + spad(j);
+    o[0] = double2{Nr_, Nt_};
+    o[Ntp] = double2{Nz_, NT_};
     if (rate_bits) {
-      mr = bitsabs(ur);
-      mt = bitsabs(ut);
-      mz = bitsabs(uz);
+      mr = max(mr, bitsabs(ur));
+      mt = max(mt, bitsabs(ut));
+      mz = max(mz, bitsabs(uz));
     }
   }
-  // column maxima (their high words carry the exponent), per z row
-#pragma unroll
-  for (int li = 0; li < kTcLB; ++li)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const unsigned m = __reduce_max_sync(0xffffffffu, my_li == li ? hmax[c] : 0u);
-      if (lane == 0 && m) atomicMax(&colMax[li * 4 + c], m);
-    }
   if (rate_bits) {
     for (int o = 16; o > 0; o >>= 1) {
       mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, o));
@@ -504,156 +443,75 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
                              fmax(val(cfl_cta[1]) / (rr * p.dth), val(cfl_cta[2]) / p.dz));
     atomicMax(rate_bits, (unsigned long long)__double_as_longlong(rate));
   }
-
-  // 5. the products sliced (forward data operand, over the physical fields):
-  // thread t: column n = t / 32, theta points 4 (t % 32) .. + 3; block 7 zero
-  unsigned char *fB = sm;
-  {
-    const int n = tid >> 5, j0 = 4 * (tid & 31);
-    const unsigned hm = colMax[n];
-    const int E = hm ? (int)((hm >> 20) & 0x7FF) - 1022 : 0;
-    double xv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      xv[u] = ((n >> 2) < nl && j0 + u < Nt) ? Pf[n * kTcM + j0 + u] : 0.0;
-    unsigned f[4][kTcS];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) slice_value(xv[u], E, f[u]);
-    const int off = (j0 >> 3) * 128 + n * 16 + (j0 & 7) * 2;
-#pragma unroll
-    for (int sl = 0; sl < kTcS; ++sl) {
-      uint2 w;
-      w.x = __byte_perm(f[0][sl], f[1][sl], 0x7632);
-      w.y = __byte_perm(f[2][sl], f[3][sl], 0x7632);
-      *reinterpret_cast<uint2 *>(fB + sl * kTcFBlock + off) = w;
-    }
-    *reinterpret_cast<uint2 *>(fB + kTcS * kTcFBlock + tid * 8) = make_uint2(0u, 0u);
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (warp == 0) {
-    tmem_alloc(kTcFTmemCols);
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  tmem = tmem_s;
-
-  // 6. the forward slice products, then W = 2 sum_j P_j e^(-i m theta_j)
-  // (the unnormalised DFT doubled, as k_theta's unpacking leaves it)
-  if (tid == 0 && !issue(kTcStages, kTcAll, tmem, smem_u32(fB), true)) abort_s = 1;
-  __syncthreads();
-  done = __syncthreads_and(tc_wait(smem_u32(&bars[2 * kTcRing]), 1u)) && abort_s == 0;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!done && tid == 0) {
-    atomicOr(timeout, 1);
-    drain();
-  }
-  if (done) {
-    // warp w: coefficient rows 32 (w % 4) + lane (k = 2 m + h), z row w / 4
-    const int wq = warp & 3, li = warp >> 2;
-    const int k = wq * 32 + lane, m = k >> 1;
-    unsigned v[kTcLev][4];
-#pragma unroll
-    for (int L = 0; L < kTcLev; ++L) {
-      const unsigned ta = tmem + ((unsigned)(wq * 32) << 16) + (unsigned)(L * kTcFN + li * 4);
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                   : "=r"(v[L][0]), "=r"(v[L][1]), "=r"(v[L][2]), "=r"(v[L][3])
-                   : "r"(ta));
-    }
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  double2 *sp = fft_batch<-1>(out, scratch, p.pt, nl * 2, Ntp, tw, false, tile_rot(blockIdx.x, r));
+  // unpack two real transforms: X_m = (Z_m + conj Z_-m)/2, Y_m = (Z_m - conj Z_-m)/(2i);
+  // the factor 1/2 is left to k_zfwd's final scaling (as in k_theta)
+  for (int t = tid; t < nl * s.NM; t += blockDim.x) {
+    const int li = t / s.NM, m = t - li * s.NM;
+    const double2 *z0 = sp + li * 2 * Ntp;
     const long long off = ((long long)r * s.Nz + l0 + li) * s.NM + m;
+    const int mm = m == 0 ? 0 : Nt - m;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const unsigned hm = colMax[li * 4 + c];
-      const int E = hm ? (int)((hm >> 20) & 0x7FF) - 1022 : 0;
-      unsigned lv[kTcLev];
-#pragma unroll
-      for (int L = 0; L < kTcLev; ++L) lv[L] = v[L][c];
-      const double x = combine(lv, E);
-      const double y = __shfl_down_sync(0xffffffffu, x, 1);   // Im from row 2 m + 1
-      if (!(k & 1) && m <= M && li < nl && c < s.nf &&
-          dbg_in(c * fs + off, (long long)s.nf * fs, DBG_THETA_W))
-        W[c * fs + off] = double2{x, y};
+    for (int h = 0; h < 2; ++h) {
+      const double2 a = z0[h * Ntp + spad(m)];
+      const double2 b = z0[h * Ntp + spad(mm)];
+      const double2 x = double2{a.x + b.x, a.y - b.y};
+      const double2 y = double2{a.y + b.y, b.x - a.x};
+      if (dbg_in((2 * h) * fs + off, (long long)s.nf * fs, DBG_THETA_W)) W[(2 * h) * fs + off] = x;
+      if (2 * h + 1 < s.nf && dbg_in((2 * h + 1) * fs + off, (long long)s.nf * fs, DBG_THETA_W))
+        W[(2 * h + 1) * fs + off] = y;
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) tmem_free(tmem, kTcFTmemCols);
 }
 
-// Host copy of the scaling and of the digit split: the DFT matrices' slices.
+// Host copy of scaled_int and of the digit split: the DFT matrix's slices.
 long long host_scaled_int(long double y) {   // round(y 2^56), |y| <= 1
   return std::llround(std::ldexp(y, 56));
 }
 
-// BF16 bits of an integer |d| <= 256 (exact).
-unsigned short host_bf16(int d) {
-  if (d == 0) return 0;
-  const unsigned sgn = d < 0 ? 0x8000u : 0u;
-  const unsigned a = (unsigned)(d < 0 ? -d : d);
-  int e = 0;
-  while ((a >> (e + 1)) != 0u) ++e;
-  const unsigned mant = e >= 7 ? (a >> (e - 7)) & 0x7Fu : (a << (7 - e)) & 0x7Fu;
-  return (unsigned short)(sgn | ((unsigned)(127 + e) << 7) | mant);
-}
-
-// The 7 balanced base-256 digits of round(y 2^56), |y| <= 1, most
-// significant first, written as BF16 at out[sl * stride + off / 2].
-void host_slices(long double y, unsigned short *out, size_t stride, int off) {
-  long long Y = host_scaled_int(y);
-  int dig[kTcS];
-  for (int sl = kTcS - 1; sl >= 1; --sl) {
-    int lo = (int)(Y & 255ll);
-    if (lo >= 128) lo -= 256;
-    dig[sl] = lo;
-    Y = (Y - lo) / 256;
-  }
-  dig[0] = (int)Y;
-  for (int sl = 0; sl < kTcS; ++sl) out[sl * stride + off / 2] = host_bf16(dig[sl]);
-}
-
 }  // namespace
 
-// The DFT matrices for Ntheta = Nt, M = Mmax, halved (entries in [-1, 1]),
-// in chunks of the A operand layout (128 rows x 32 contraction elements,
-// kTcAChunk bytes each):
-//   chunks 0..20, inverse F/2 [theta point j][coefficient k = 2 m + h]:
-//     slice i, coefficients 32 ch .. 32 ch + 31 in chunk 3 i + ch;
-//     F/2 = 1/2 (m = h = 0), 0 (m = 0, h = 1), cos(m theta_j) (h = 0),
-//     -sin(m theta_j) (h = 1);
-//   chunks 21..48, forward G/2 [coefficient k = 2 m + h][theta point j]:
-//     slice i, theta points 32 ch .. 32 ch + 31 in chunk 21 + 4 i + ch;
-//     G/2 = cos(m theta_j) (h = 0), -sin(m theta_j) (h = 1).
-// Rows beyond the matrix (j >= Nt, k >= 2 (M + 1)) are zero.
+// The DFT matrix F/2 for Ntheta = Nt, M = Mmax, in 21 chunks of the A operand
+// layout (slice i, coefficients 32 ch .. 32 ch + 31 at (3 i + ch) * kTcAChunk
+// bytes).
 void build_theta_dft(int Nt, int Mm, std::vector<unsigned short> &out) {
-  out.assign((size_t)kTcAll * kTcAChunk / 2, 0);
+  out.assign((size_t)kTcStages * kTcAChunk / 2, 0);
+  auto bf16 = [](int d, int sl) -> unsigned short {
+    if (d == 0) return 0;
+    const unsigned sgn = d < 0 ? 0x8000u : 0u;
+    const unsigned a = (unsigned)(d < 0 ? -d : d);
+    int e = 0;
+    while ((a >> (e + 1)) != 0u) ++e;
+    const unsigned mant = e >= 7 ? (a >> (e - 7)) & 0x7Fu : (a << (7 - e)) & 0x7Fu;
+    (void)sl;
+    return (unsigned short)(sgn | ((unsigned)(127 + e) << 7) | mant);
+  };
   const long double pi = 3.141592653589793238462643383279502884L;
-  auto entry = [&](int j, int k) -> long double {   // F/2 (inverse) = G/2^T except at m = 0
-    const int m = k >> 1, h = k & 1;
-    if (j >= Nt || m > Mm) return 0.0L;
-    if (m == 0) return 0.0L;
-    const long double ang = 2.0L * pi * (long double)((long long)m * j % Nt) / Nt;
-    return h ? -std::sin(ang) : std::cos(ang);
-  };
-  auto a_off = [](int row, int kl) {
-    return ((row >> 3) * (kTcKc / 8) + (kl >> 3)) * 128 + (row & 7) * 16 + (kl & 7) * 2;
-  };
-  const size_t stride = (size_t)kTcAChunk / 2;
   for (int j = 0; j < kTcM; ++j)
-    for (int k = 0; k < kTcK; ++k) {   // inverse: row j, column k
-      long double y = entry(j, k);
-      if (k == 0 && j < Nt) y = 0.5L;
-      const int ch = k / kTcKc;
-      host_slices(y, out.data() + (size_t)ch * stride, kTcChunks * stride, a_off(j, k - ch * kTcKc));
-    }
-  unsigned short *fwd = out.data() + (size_t)kTcStages * stride;
-  for (int k = 0; k < kTcM; ++k)
-    for (int j = 0; j < kTcM; ++j) {   // forward: row k, column j
-      long double y = k < kTcK ? entry(j, k) : 0.0L;
-      if (k == 0 && j < Nt) y = 1.0L;
-      const int ch = j / kTcKc;
-      host_slices(y, fwd + (size_t)ch * stride, kTcFChunks * stride, a_off(k, j - ch * kTcKc));
+    for (int k = 0; k < kTcK; ++k) {
+      long double y = 0.0L;   // F/2; column k = 2 m + h
+      const int m = k >> 1, h = k & 1;
+      if (j < Nt && m <= Mm) {
+        if (m == 0) {
+          y = h ? 0.0L : 0.5L;
+        } else {
+          const long double ang = 2.0L * pi * (long double)((long long)m * j % Nt) / Nt;
+          y = h ? -std::sin(ang) : std::cos(ang);
+        }
+      }
+      long long Y = host_scaled_int(y);
+      int dig[kTcS];
+      for (int sl = kTcS - 1; sl >= 1; --sl) {
+        int lo = (int)(Y & 255ll);
+        if (lo >= 128) lo -= 256;
+        dig[sl] = lo;
+        Y = (Y - lo) / 256;
+      }
+      dig[0] = (int)Y;
+      const int ch = k / kTcKc, kl = k - ch * kTcKc;
+      const int off = ((j >> 3) * (kTcKc / 8) + (kl >> 3)) * 128 + (j & 7) * 16 + (kl & 7) * 2;
+      for (int sl = 0; sl < kTcS; ++sl)
+        out[((size_t)(kTcChunks * sl + ch) * kTcAChunk + off) / 2] = bf16(dig[sl], sl);
     }
 }
 
@@ -661,7 +519,7 @@ bool theta_tc_supported(const Sizes &s) {
   return s.Nt <= kTcM && 2 * (s.M + 1) <= kTcK && kTcLB * 4 * s.nf <= kTcN;
 }
 
-size_t theta_tc_table_bytes() { return (size_t)kTcAll * kTcAChunk; }
+size_t theta_tc_table_bytes() { return (size_t)kTcStages * kTcAChunk; }
 
 void setup_theta_tc() {
   allow_smem(k_theta_tc);
