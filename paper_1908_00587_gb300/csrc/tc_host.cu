@@ -725,7 +725,10 @@ tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz, double Re
     upload_tables(c);
     setup_nonlinear(c);
     setup_linear(c);
-    if (theta_tc_supported(s)) {   // the DFT matrix's slices for the tensor-core transforms
+    alignas(64) unsigned char vmap[128];
+    // the DFT matrix's slices for the tensor-core transforms (and a TMA
+    // tensor map of V that the driver accepts)
+    if (theta_tc_supported(s) && theta_tc_map(vmap, c->V, s)) {
       std::vector<unsigned short> tab;
       build_theta_dft(s.Nt, s.M, tab);
       c->d_dft_tc = dalloc<unsigned char>(c, theta_tc_table_bytes());

@@ -361,7 +361,10 @@ bool theta_tc_supported(const Sizes &s);
 size_t theta_tc_table_bytes();
 void build_theta_dft(int Nt, int M, std::vector<unsigned short> &out);
 void setup_theta_tc();
-void launch_theta_tc(cudaStream_t st, const double2 *V, double2 *W, const NLParams &p,
+// Encode the TMA tensor map of V for k_theta_tc into map (128 bytes, 64-byte
+// aligned); false if the driver refuses it (the caller runs k_theta instead).
+bool theta_tc_map(void *map, const double2 *V, const Sizes &s);
+void launch_theta_tc(cudaStream_t st, const void *map, double2 *W, const NLParams &p,
                      const unsigned char *dft, unsigned long long *rate_bits, int *timeout);
 
 }  // namespace tc

@@ -39,6 +39,8 @@
 // Every wait is bounded (1 s); a wait that runs out sets the timeout flag of
 // the context, and the CTA waits (bounded) for its copies in flight, frees
 // its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -70,7 +72,8 @@ constexpr int kTcThreads = 256;
 constexpr int kTcBSlice = (kTcN / 8) * (kTcK / 8) * 128;       // 6144 B per data slice
 constexpr int kTcBBytes = kTcS * kTcBSlice;                     // 43008
 constexpr int kTcAChunk = (kTcM / 8) * (kTcKc / 8) * 128;      // 8192 B per chunk
-constexpr int kTcSmem = kTcBBytes + kTcRing * kTcAChunk;        // 75776: three CTAs per SM
+// + 128 bytes to align the base for the tiled TMA copy: 75904, three CTAs per SM
+constexpr int kTcSmem = kTcBBytes + kTcRing * kTcAChunk + 128;
 constexpr int kTcTmemCols = 256;
 constexpr long long kTcWaitNs = 1000000000LL;
 
@@ -160,7 +163,7 @@ __device__ __forceinline__ unsigned long long ll_to_double_bits(long long v) {
 }
 
 __global__ void __launch_bounds__(kTcThreads, 3)
-k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
+k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLParams p,
            const unsigned char *__restrict__ dft, unsigned long long *__restrict__ rate_bits,
            int *__restrict__ timeout) {
   constexpr int LB = kTcLB;
@@ -172,10 +175,11 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
   const int Ntp = padlen(Nt);
   const int M = s.M;
   const int ncol = 4 * s.nf;                      // data columns per z row
-  extern __shared__ __align__(128) unsigned char sm[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  unsigned char *sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);
   unsigned char *sB = sm;
   unsigned char *sA = sm + kTcBBytes;
-  __shared__ __align__(8) unsigned long long bars[2 * kTcRing + 1];   // full, free, done
+  __shared__ __align__(8) unsigned long long bars[2 * kTcRing + 2];   // full, free, done, V
   __shared__ unsigned tmem_s;
   __shared__ int colE[kTcN];
   __shared__ int abort_s;
@@ -184,7 +188,7 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
 
   if (tid == 0) {
     abort_s = 0;
-    for (int i = 0; i < 2 * kTcRing + 1; ++i)
+    for (int i = 0; i < 2 * kTcRing + 2; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bars[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -205,8 +209,24 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
            "r"((unsigned)kTcAChunk), "r"(bar)
         : "memory");
   };
-  if (tid == 0)
+  // this tile's block of V: one tiled TMA copy of the box {2 NM doubles, 2 z
+  // rows, 1 radius, 3 nf planes} (rows past Nz read as zeros) into the space
+  // of data slices 4..6, which the slicing below overwrites only after every
+  // thread has read its values
+  const double2 *Vs = reinterpret_cast<const double2 *>(sB + 4 * kTcBSlice);
+  const unsigned vbar = smem_u32(&bars[2 * kTcRing + 1]);
+  if (tid == 0) {
+    const unsigned vbytes = (unsigned)(3 * s.nf * 2 * s.NM) * 16u;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(vbar), "r"(vbytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        :: "r"(smem_u32(Vs)), "l"(reinterpret_cast<unsigned long long>(&tmV)), "r"(0), "r"(l0),
+           "r"(r), "r"(0), "r"(vbar)
+        : "memory");
     for (int st = 0; st < kTcRing; ++st) load_a(st);
+  }
 
   // 1. the data columns of this tile, sliced.  Thread t: column n = t / 8,
   // part s8 = t % 8.  Column n = li ncol + 4 c + q: z row li, field c, q = 0
@@ -215,24 +235,35 @@ k_theta_tc(const double2 *__restrict__ Vin, double2 *__restrict__ W, NLParams p,
   // does); the thread holds m = 16 g + 2 s8 + {0, 1}, g = 0..2, so that one
   // group g is four adjacent coefficients (one 8-byte store per slice).
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
+  // the V block, waited for by every thread (the same verdict in all)
+  if (!__syncthreads_and(tc_wait(vbar, 0u))) {
+    if (tid == 0) {
+      atomicOr(timeout, 1);
+      tc_wait(vbar, 0u);   // the V copy, if still in flight (bounded)
+      for (int st = consumed; st < loaded; ++st)
+        if (!tc_wait(smem_u32(&bars[st % kTcRing]), (unsigned)(st / kTcRing) & 1u)) break;
+    }
+    return;
+  }
   {
     const int n = tid >> 3, s8 = tid & 7;
     const int li = n / ncol, cq = n - li * ncol, c = cq >> 2, q = cq & 3;
     const bool col = li < nl && cq < ncol;
     const int d = q <= 1 ? 0 : q - 1;
-    const long long base = (3LL * c + d) * fs + ((long long)r * s.Nz + l0 + li) * s.NM;
+    const int base = ((3 * c + d) * 2 + li) * s.NM;   // in the V block
     double2 a[6];
 #pragma unroll
     for (int u = 0; u < 6; ++u) {   // all loads first
       const int m = 16 * (u >> 1) + 2 * s8 + (u & 1);
       double2 v = double2{0.0, 0.0};
-      if (col && m <= M && dbg_in(base + m, 3LL * s.nf * fs, DBG_THETA_V)) {
-        v = Vin[base + m];
+      if (col && m <= M && dbg_in(base + m, 6LL * s.nf * s.NM, DBG_THETA_V)) {
+        v = Vs[base + m];
         if (m == 0) v.y = 0.0;
         if (q == 1) v = double2{-(double)m * v.y, (double)m * v.x};   // i m a_m
       }
       a[u] = v;
     }
+    __syncthreads();   // the V block is read: the slices may overwrite it
     // exponent of the column: E with max |x| < 2^E (the 8 threads of a column
     // are 8 adjacent lanes)
     unsigned long long mb = 0ull;
@@ -525,11 +556,39 @@ void setup_theta_tc() {
   allow_smem(k_theta_tc);
 }
 
-void launch_theta_tc(cudaStream_t st, const double2 *V, double2 *W, const NLParams &p,
+// V as a 4-D FP64 tensor for the tiled TMA copy: {2 NM (Re, Im per m), Nz,
+// Nr, 3 nf planes}, box {2 NM, 2, 1, 3 nf} (at most 96 x 2 x 1 x 12 doubles,
+// 18 KB: the space of three data slices).  Row strides are multiples of 16
+// bytes (16 NM per z row).
+bool theta_tc_map(void *map, const double2 *V, const Sizes &s) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode || 2 * s.NM > kTcK || 3 * s.nf * 2 * s.NM * 16 > 3 * kTcBSlice) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)(2 * s.NM), (cuuint64_t)s.Nz, (cuuint64_t)s.Nr,
+                              (cuuint64_t)(3 * s.nf)};
+  const cuuint64_t strides[3] = {(cuuint64_t)s.NM * 16, (cuuint64_t)s.NM * 16 * s.Nz,
+                                 (cuuint64_t)s.NM * 16 * s.Nz * s.Nr};
+  const cuuint32_t box[4] = {(cuuint32_t)(2 * s.NM), (cuuint32_t)kTcLB, 1u,
+                             (cuuint32_t)(3 * s.nf)};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  return encode(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                const_cast<double2 *>(V), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void launch_theta_tc(cudaStream_t st, const void *map, double2 *W, const NLParams &p,
                      const unsigned char *dft, unsigned long long *rate_bits, int *timeout) {
   const Sizes &s = p.sz;
   k_theta_tc<<<dim3((s.Nz + kTcLB - 1) / kTcLB, s.Nr), kTcThreads, kTcSmem, st>>>(
-      V, W, p, dft, rate_bits, timeout);
+      *static_cast<const CUtensorMap *>(map), W, p, dft, rate_bits, timeout);
 }
 
 }  // namespace tc

@@ -48,6 +48,8 @@ def test_tensor_theta_matches_fft_theta(tc, wl):
     outs, rates = [], []
     for flag in (1, 0):
         tc.tc_set_option(run.ctx, "tensor_theta", flag)
+        # the tensor path is available at these sizes (table built, TMA map accepted)
+        assert tc.tc_get_info(run.ctx).tensor_theta == flag
         out = dev(np.zeros_like(X))
         rates.append(tc.tc_nonlinear(run.ctx, dev(X), out))
         outs.append(out.cpu().numpy())
