@@ -20,7 +20,7 @@ namespace tc {
 const char *const kKernelNames[KNUM] = {
     "k_zinv", "k_theta", "k_zfwd", "k_dt_policy", "k_factor", "k_influence",
     "k_rhs", "k_prhs", "k_psolve", "k_hrhs", "k_hsolve", "k_alpha", "k_correct", "k_diag", "k_check",
-    "k_flux", "k_regrid"};
+    "k_flux", "k_regrid", "k_adjoint", "k_theta_tc"};
 
 LaunchScope::LaunchScope(tc_ctx *c_, int id_) : c(c_), id(id_) {
   c->launches++;

@@ -191,7 +191,7 @@ namespace tc {
 // Kernels with per-launch timing (option "timing").
 enum KernelId {
   KZINV, KTHETA, KZFWD, KDT, KFACTH, KINFL, KRHS, KPRHS, KPOIS, KHRHS, KHELM, KALPHA, KCORR,
-  KDIAG, KCHECK, KFLUX, KREGRID, KADJ, KNUM
+  KDIAG, KCHECK, KFLUX, KREGRID, KADJ, KTHETATC, KNUM
 };
 extern const char *const kKernelNames[KNUM];
 

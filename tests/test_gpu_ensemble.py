@@ -48,13 +48,14 @@ def test_ensemble_members_match_single_runs_bitwise(tc, mode):
     ens = tc.tc_ensemble_create(members, autotune_tiles=True)
     tc.tc_ensemble_set_mode(ens, mode)
     assert tc.tc_ensemble_get_mode(ens) == mode
-    dts, shapes = [], []
+    dts, shapes, tensor = [], [], []
     for i, wl in enumerate(members):
         dt, shape = _init(tc, tc.tc_ensemble_member(ens, i), wl)
         dts.append(dt)
         shapes.append(shape)
         info = tc.tc_get_info(tc.tc_ensemble_member(ens, i))
         assert info.tile_mb >= 1 and info.tile_lb >= 1
+        tensor.append(info.tensor_theta)
     tc.tc_ensemble_step(ens, 7, dts)
     tc.tc_ensemble_step(ens, 5, dts)       # the same plan (graph) again
     if mode == 1:
@@ -69,6 +70,9 @@ def test_ensemble_members_match_single_runs_bitwise(tc, mode):
     tc.tc_ensemble_destroy(ens)
     for i, wl in enumerate(members):
         run = tc.Run.from_workload(wl)       # default tiles, plain launches
+        # the azimuthal path the tuner chose for this member's size class
+        # (tiles change nothing; the tensor-core path changes round-off)
+        tc.tc_set_option(run.ctx, "tensor_theta", tensor[i])
         dt, _ = _init(tc, run.ctx, wl)
         assert dt == dts[i]
         run.step(12, dt)
