@@ -85,7 +85,6 @@ typedef struct {
   int tile_mb, tile_lb;         /* nonlinear-stage tiles in use (see "tile_mb") */
   int tile_mbf;                 /* m columns per CTA of the forward axial kernel */
   int tensor_theta;             /* 1: the azimuthal stage runs on the tensor cores */
-  int tile_lb_tc;               /* z rows per CTA of that stage (option "tile_lb_tc") */
 } tc_info;
 
 /* Device time of one kernel accumulated while option "timing" is 1. */
@@ -170,16 +169,10 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               path to ~4e-16 of the largest term).  Needs Ntheta <= 128 and
  *               precision 0 (otherwise the FFT path runs).  0 (default): the
  *               FP64 FFT.  Which one is faster depends on the size (measured
- *               on GB300: 0.28 against 0.41 ms a launch at 64 x 128 x 128 with
- *               temperature, 0.12 against 0.09 ms at 64 x 64 x 64, where most
+ *               on GB300: 0.38 against 0.41 ms a launch at 64 x 128 x 128 with
+ *               temperature, 0.16 against 0.09 ms at 64 x 64 x 64, where most
  *               of the 128 rows of each product are padding); tc_autotune
- *               times both and keeps the faster.  The tile's block of the
- *               input arrives by a tiled TMA copy; if the driver refuses its
- *               tensor map at tc_create, the option has no effect.
- *   "tile_lb_tc"  z rows per CTA of the tensor-core azimuthal stage, 2
- *               (default: 32 data columns, three CTAs per SM) or 1 (16
- *               columns, four CTAs per SM, the DFT slices streamed twice as
- *               often).  Results are identical for both.
+ *               times both and keeps the faster.
  *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
  *               never start their shared-memory copies, so each of their
  *               bounded waits runs out (about 1 s) and tc_step returns
@@ -451,8 +444,7 @@ tc_status tc_ensemble_get_mode(const tc_ens *e, int *mode);
 /* Tile autotuner for one context (the one the ensemble runs per size
  * class): times the nonlinear stage on the context's current state for tile
  * shapes {1, 2, 3, 4, 5, 6, 8} of "tile_mb", then {1, 2, 3, 4, 8} of
- * "tile_lb", then (precision 0, Ntheta <= 128) "tensor_theta" 1 with
- * "tile_lb_tc" 2 and 1 against "tensor_theta" 0,
+ * "tile_lb", then (precision 0, Ntheta <= 128) "tensor_theta" 1 against 0,
  * then {1, 2, 3, 4, 5, 6, 8} of "tile_mbf", keeps the fastest and returns the
  * first two (host, nullable; tc_get_info reports all four).  Results do not
  * depend on the tiles; the tensor-core azimuthal stage changes them only at

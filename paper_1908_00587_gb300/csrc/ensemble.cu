@@ -118,19 +118,8 @@ tc_status autotune(tc_ctx *c, int *best_mb, int *best_lb) {
   // the azimuthal stage on the tensor cores, where it applies, against the
   // FFT kernel with the tile just chosen
   if (c->precision == 0 && c->d_dft_tc) {
-    int tt = 0, tlb = 2;
     tc_set_option(c, "tensor_theta", 1);
-    for (int lb : {2, 1}) {
-      tc_set_option(c, "tile_lb_tc", lb);
-      const float t = time_nonlinear(c, a, b, 3);
-      if (t < best) {
-        best = t;
-        tt = 1;
-        tlb = lb;
-      }
-    }
-    tc_set_option(c, "tile_lb_tc", tlb);
-    tc_set_option(c, "tensor_theta", tt);
+    if (time_nonlinear(c, a, b, 3) >= best) tc_set_option(c, "tensor_theta", 0);
   }
   // the forward axial kernel's own width (its grid fills the SMs differently)
   best = 1e30f;
@@ -739,8 +728,8 @@ tc_status tc_ensemble_create(int n, const tc_params *p, int autotune_tiles, tc_e
     tc_set_stream(c, s);
   }
   if (autotune_tiles) {
-    // tuned (tile_mb, tile_lb, tile_mbf, tensor_theta, tile_lb_tc) per size class
-    std::map<ClassKey, std::tuple<int, int, int, int, int>> tuned;
+    // tuned (tile_mb, tile_lb, tile_mbf, tensor_theta) per size class
+    std::map<ClassKey, std::tuple<int, int, int, int>> tuned;
     for (tc_ctx *c : e->m) {
       const ClassKey k = class_of(c);
       auto it = tuned.find(k);
@@ -748,10 +737,9 @@ tc_status tc_ensemble_create(int n, const tc_params *p, int autotune_tiles, tc_e
         int mb = 0, lb = 0;
         tc_status st = autotune(c, &mb, &lb);
         if (st != TC_OK) return fail(st);
-        tuned[k] = std::make_tuple(mb, lb, c->tile_mbf, c->tensor_theta, c->tile_lb_tc);
+        tuned[k] = std::make_tuple(mb, lb, c->tile_mbf, c->tensor_theta);
       } else {
-        const auto [mb, lb, mbf, tt, tlb] = it->second;
-        tc_set_option(c, "tile_lb_tc", tlb);
+        const auto [mb, lb, mbf, tt] = it->second;
         if (mb) tc_set_option(c, "tile_mb", mb);
         if (lb) tc_set_option(c, "tile_lb", lb);
         if (mbf) tc_set_option(c, "tile_mbf", mbf);

@@ -177,11 +177,9 @@ void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long lon
   }
   const int nlb = (s.Nz + p.LB - 1) / p.LB;
   alignas(64) unsigned char vmap[128];
-  if (mode == 0 && !phys_out && c->tensor_theta && c->d_dft_tc &&
-      theta_tc_map(vmap, c->V, s, c->tile_lb_tc)) {
+  if (mode == 0 && !phys_out && c->tensor_theta && c->d_dft_tc && theta_tc_map(vmap, c->V, s)) {
     LaunchScope ls(c, KTHETATC);
-    launch_theta_tc(c->stream, vmap, c->tile_lb_tc, c->W, p, c->d_dft_tc, rate_bits,
-                    &c->scal->timeout);
+    launch_theta_tc(c->stream, vmap, c->W, p, c->d_dft_tc, rate_bits, &c->scal->timeout);
   } else {
     LaunchScope ls(c, KTHETA);
     k_theta<double><<<dim3(nlb, s.Nr), 256, c->smem_theta, c->stream>>>(

@@ -728,8 +728,7 @@ tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz, double Re
     alignas(64) unsigned char vmap[128];
     // the DFT matrix's slices for the tensor-core transforms (and a TMA
     // tensor map of V that the driver accepts)
-    if (theta_tc_supported(s) && theta_tc_map(vmap, c->V, s, 1) &&
-        theta_tc_map(vmap, c->V, s, 2)) {
+    if (theta_tc_supported(s) && theta_tc_map(vmap, c->V, s)) {
       std::vector<unsigned short> tab;
       build_theta_dft(s.Nt, s.M, tab);
       c->d_dft_tc = dalloc<unsigned char>(c, theta_tc_table_bytes());
@@ -854,9 +853,6 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
   } else if (k == "tensor_theta") {
     if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
     c->tensor_theta = (int)v;
-  } else if (k == "tile_lb_tc") {
-    if (v != 1.0 && v != 2.0) return TC_ERR_ARG;
-    c->tile_lb_tc = (int)v;
   } else if (k == "selftest_no_copy") {
     c->selftest_no_copy = v != 0.0;
   } else if (k == "timing") {
@@ -891,7 +887,6 @@ tc_status tc_get_info(const tc_ctx *c, tc_info *o) {
   o->tile_lb = (c->precision == 1) ? c->nl32.LB : c->nl.LB;
   o->tile_mbf = (c->precision == 1) ? c->nl32.MBf : c->nl.MBf;
   o->tensor_theta = (c->precision == 0 && c->tensor_theta && c->d_dft_tc) ? 1 : 0;
-  o->tile_lb_tc = c->tile_lb_tc;
   return TC_OK;
 }
 

@@ -259,7 +259,6 @@ struct tc_ctx {
   // BF16 slices (device, null when the size is not supported) and the option
   unsigned char *d_dft_tc = nullptr;
   int tensor_theta = 0;
-  int tile_lb_tc = 2;   // z rows per CTA of k_theta_tc (1 or 2)
   int flux = 0;                 // axial-flux constraint on the (0,0) u_z mode
   double eps_c = 0.0;           // centrifugal buoyancy coefficient
   double *flux_ug = nullptr;    // device (Nr): unit-forcing response of the (0,0) u_z operator
@@ -362,11 +361,10 @@ bool theta_tc_supported(const Sizes &s);
 size_t theta_tc_table_bytes();
 void build_theta_dft(int Nt, int M, std::vector<unsigned short> &out);
 void setup_theta_tc();
-// Encode the TMA tensor map of V for k_theta_tc with lb (1 or 2) z rows per
-// CTA into map (128 bytes, 64-byte aligned); false if the driver refuses it
-// (the caller runs k_theta instead).
-bool theta_tc_map(void *map, const double2 *V, const Sizes &s, int lb);
-void launch_theta_tc(cudaStream_t st, const void *map, int lb, double2 *W, const NLParams &p,
+// Encode the TMA tensor map of V for k_theta_tc into map (128 bytes, 64-byte
+// aligned); false if the driver refuses it (the caller runs k_theta instead).
+bool theta_tc_map(void *map, const double2 *V, const Sizes &s);
+void launch_theta_tc(cudaStream_t st, const void *map, double2 *W, const NLParams &p,
                      const unsigned char *dft, unsigned long long *rate_bits, int *timeout);
 
 }  // namespace tc

@@ -25,8 +25,7 @@
 // terms, buoyancy and the CFL rate) in FP64 on the physical grid, then the
 // forward theta FFT in FP64 and the unpacking into W.
 //
-// Data path of one CTA (LB = 1 or 2 z rows of one radial level, 16 LB data
-// columns; the numbers below are for LB = 2):
+// Data path of one CTA (2 z rows of one radial level, 32 data columns):
 //   1. all threads (8 per column): read V, slice the 32 columns into 7 BF16
 //      operand tiles in shared memory (K-major core-matrix layout, no
 //      swizzle), one exponent per column;
@@ -58,31 +57,24 @@ namespace {
 
 constexpr int kTcM = 128;      // theta rows per MMA (Ntheta <= 128; zero rows beyond)
 constexpr int kTcK = 96;       // real coefficients per data column, padded (2 (M + 1) <= 96)
+constexpr int kTcN = 32;       // data columns per CTA: 2 z rows x 4 nf real fields (+ zeros)
+constexpr int kTcLB = 2;       // z rows per CTA
 constexpr int kTcS = 7;        // slices of each operand
-constexpr int kTcLev = 7;      // level blocks of N TMEM columns each
+constexpr int kTcLev = 7;      // level blocks of kTcN TMEM columns each
 constexpr int kTcKc = 32;      // coefficients per streamed chunk of a DFT-matrix slice
 constexpr int kTcChunks = kTcK / kTcKc;   // 3 per slice
 constexpr int kTcStages = kTcChunks * kTcS;   // 21
 constexpr int kTcRing = 4;     // chunks in flight
+constexpr int kTcThreads = 256;
+// Operand layouts in shared memory (K-major, no swizzle): core matrices of 8
+// rows x 16 bytes (8 BF16), the K-neighbour of a core matrix 128 B further,
+// the next group of 8 rows one K extent further.
+constexpr int kTcBSlice = (kTcN / 8) * (kTcK / 8) * 128;       // 6144 B per data slice
+constexpr int kTcBBytes = kTcS * kTcBSlice;                     // 43008
 constexpr int kTcAChunk = (kTcM / 8) * (kTcKc / 8) * 128;      // 8192 B per chunk
-// Tile of LB z rows (1 or 2) of one radius: N = 16 LB data columns (4 nf real
-// fields per z row, zeros beyond), 128 LB threads (8 per column).  Operand
-// layouts in shared memory (K-major, no swizzle): core matrices of 8 rows x
-// 16 bytes (8 BF16), the K-neighbour of a core matrix 128 B further, the next
-// group of 8 rows one K extent further.  Shared memory: the 7 data slices,
-// the ring, 128 bytes to align the base for the tiled TMA copy (LB = 2:
-// 75,904 B, three CTAs per SM; LB = 1: 54,400 B, four).  TMEM: 7 level
-// blocks of N columns, rounded up to a power of two.
-template <int LB>
-struct TcTile {
-  static constexpr int N = 16 * LB;
-  static constexpr int Threads = 128 * LB;
-  static constexpr int BSlice = (N / 8) * (kTcK / 8) * 128;
-  static constexpr int BBytes = kTcS * BSlice;
-  static constexpr int Smem = BBytes + kTcRing * kTcAChunk + 128;
-  static constexpr int TmemCols = LB == 2 ? 256 : 128;
-  static constexpr int MinBlocks = LB == 2 ? 3 : 4;
-};
+// + 128 bytes to align the base for the tiled TMA copy: 75904, three CTAs per SM
+constexpr int kTcSmem = kTcBBytes + kTcRing * kTcAChunk + 128;
+constexpr int kTcTmemCols = 256;
 constexpr long long kTcWaitNs = 1000000000LL;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -170,15 +162,11 @@ __device__ __forceinline__ unsigned long long ll_to_double_bits(long long v) {
   return sgn | bits;
 }
 
-template <int LB>
-__global__ void __launch_bounds__(TcTile<LB>::Threads, TcTile<LB>::MinBlocks)
+__global__ void __launch_bounds__(kTcThreads, 3)
 k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLParams p,
            const unsigned char *__restrict__ dft, unsigned long long *__restrict__ rate_bits,
            int *__restrict__ timeout) {
-  constexpr int kTcN = TcTile<LB>::N;
-  constexpr int kTcBSlice = TcTile<LB>::BSlice;
-  constexpr int kTcBBytes = TcTile<LB>::BBytes;
-  constexpr int kTcTmemCols = TcTile<LB>::TmemCols;
+  constexpr int LB = kTcLB;
   const Sizes &s = p.sz;
   const int l0 = blockIdx.x * LB;
   const int nl = min(LB, s.Nz - l0);
@@ -221,14 +209,14 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
            "r"((unsigned)kTcAChunk), "r"(bar)
         : "memory");
   };
-  // this tile's block of V: one tiled TMA copy of the box {2 NM doubles, LB z
+  // this tile's block of V: one tiled TMA copy of the box {2 NM doubles, 2 z
   // rows, 1 radius, 3 nf planes} (rows past Nz read as zeros) into the space
   // of data slices 4..6, which the slicing below overwrites only after every
   // thread has read its values
   const double2 *Vs = reinterpret_cast<const double2 *>(sB + 4 * kTcBSlice);
   const unsigned vbar = smem_u32(&bars[2 * kTcRing + 1]);
   if (tid == 0) {
-    const unsigned vbytes = (unsigned)(3 * s.nf * LB * s.NM) * 16u;
+    const unsigned vbytes = (unsigned)(3 * s.nf * 2 * s.NM) * 16u;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                  :: "r"(vbar), "r"(vbytes) : "memory");
     asm volatile(
@@ -262,13 +250,13 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
     const int li = n / ncol, cq = n - li * ncol, c = cq >> 2, q = cq & 3;
     const bool col = li < nl && cq < ncol;
     const int d = q <= 1 ? 0 : q - 1;
-    const int base = ((3 * c + d) * LB + li) * s.NM;   // in the V block
+    const int base = ((3 * c + d) * 2 + li) * s.NM;   // in the V block
     double2 a[6];
 #pragma unroll
     for (int u = 0; u < 6; ++u) {   // all loads first
       const int m = 16 * (u >> 1) + 2 * s8 + (u & 1);
       double2 v = double2{0.0, 0.0};
-      if (col && m <= M && dbg_in(base + m, 3LL * LB * s.nf * s.NM, DBG_THETA_V)) {
+      if (col && m <= M && dbg_in(base + m, 6LL * s.nf * s.NM, DBG_THETA_V)) {
         v = Vs[base + m];
         if (m == 0) v.y = 0.0;
         if (q == 1) v = double2{-(double)m * v.y, (double)m * v.x};   // i m a_m
@@ -377,15 +365,15 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
       if (!tc_wait(smem_u32(&bars[st % kTcRing]), (unsigned)(st / kTcRing) & 1u)) break;
   }
   // 3. accumulators -> physical fields P[n][j] (FP64), lane = theta row.
-  // Warp w reads TMEM lanes 32 (w % 4) ..; warps 4 g .. 4 g + 3 take
-  // columns 16 g .. 16 g + 15.
+  // Warp w reads TMEM lanes 32 (w % 4) ..; warps 0-3 take columns 0-15,
+  // warps 4-7 columns 16-31.
   double *P = reinterpret_cast<double *>(sm);   // over the data slices: the products are done
   if (done) {
     const int wq = warp & 3;
     const int j = wq * 32 + lane;
 #pragma unroll 1
-    for (int cc = 0; cc < 2; ++cc) {   // LB groups of 4 warps, 2 column blocks each
-      const int cb = (warp >> 2) * 2 + cc;
+    for (int cc = 0; cc < kTcN / 16; ++cc) {
+      const int cb = (warp >> 2) * (kTcN / 16) + cc;
       unsigned v[kTcLev][8];
 #pragma unroll
       for (int L = 0; L < kTcLev; ++L) {
@@ -559,21 +547,20 @@ void build_theta_dft(int Nt, int Mm, std::vector<unsigned short> &out) {
 }
 
 bool theta_tc_supported(const Sizes &s) {
-  return s.Nt <= kTcM && 2 * (s.M + 1) <= kTcK && 4 * s.nf <= 16;
+  return s.Nt <= kTcM && 2 * (s.M + 1) <= kTcK && kTcLB * 4 * s.nf <= kTcN;
 }
 
 size_t theta_tc_table_bytes() { return (size_t)kTcStages * kTcAChunk; }
 
 void setup_theta_tc() {
-  allow_smem(k_theta_tc<1>);
-  allow_smem(k_theta_tc<2>);
+  allow_smem(k_theta_tc);
 }
 
 // V as a 4-D FP64 tensor for the tiled TMA copy: {2 NM (Re, Im per m), Nz,
-// Nr, 3 nf planes}, box {2 NM, lb, 1, 3 nf} (at most 96 x lb x 1 x 12
-// doubles, 9 KB per z row: the space of three data slices).  Row strides are
-// multiples of 16 bytes (16 NM per z row).
-bool theta_tc_map(void *map, const double2 *V, const Sizes &s, int lb) {
+// Nr, 3 nf planes}, box {2 NM, 2, 1, 3 nf} (at most 96 x 2 x 1 x 12 doubles,
+// 18 KB: the space of three data slices).  Row strides are multiples of 16
+// bytes (16 NM per z row).
+bool theta_tc_map(void *map, const double2 *V, const Sizes &s) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -583,15 +570,12 @@ bool theta_tc_map(void *map, const double2 *V, const Sizes &s, int lb) {
       fn = nullptr;
     return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }();
-  if (!encode || (lb != 1 && lb != 2) || 2 * s.NM > kTcK) return false;
-  // the block must fit in the space of three data slices
-  if (3 * s.nf * lb * 2 * s.NM * 8 > 3 * (lb == 2 ? TcTile<2>::BSlice : TcTile<1>::BSlice))
-    return false;
+  if (!encode || 2 * s.NM > kTcK || 3 * s.nf * 2 * s.NM * 16 > 3 * kTcBSlice) return false;
   const cuuint64_t dims[4] = {(cuuint64_t)(2 * s.NM), (cuuint64_t)s.Nz, (cuuint64_t)s.Nr,
                               (cuuint64_t)(3 * s.nf)};
   const cuuint64_t strides[3] = {(cuuint64_t)s.NM * 16, (cuuint64_t)s.NM * 16 * s.Nz,
                                  (cuuint64_t)s.NM * 16 * s.Nz * s.Nr};
-  const cuuint32_t box[4] = {(cuuint32_t)(2 * s.NM), (cuuint32_t)lb, 1u,
+  const cuuint32_t box[4] = {(cuuint32_t)(2 * s.NM), (cuuint32_t)kTcLB, 1u,
                              (cuuint32_t)(3 * s.nf)};
   const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   return encode(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
@@ -600,16 +584,11 @@ bool theta_tc_map(void *map, const double2 *V, const Sizes &s, int lb) {
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-void launch_theta_tc(cudaStream_t st, const void *map, int lb, double2 *W, const NLParams &p,
+void launch_theta_tc(cudaStream_t st, const void *map, double2 *W, const NLParams &p,
                      const unsigned char *dft, unsigned long long *rate_bits, int *timeout) {
   const Sizes &s = p.sz;
-  const CUtensorMap &m = *static_cast<const CUtensorMap *>(map);
-  if (lb == 1)
-    k_theta_tc<1><<<dim3(s.Nz, s.Nr), TcTile<1>::Threads, TcTile<1>::Smem, st>>>(
-        m, W, p, dft, rate_bits, timeout);
-  else
-    k_theta_tc<2><<<dim3((s.Nz + 1) / 2, s.Nr), TcTile<2>::Threads, TcTile<2>::Smem, st>>>(
-        m, W, p, dft, rate_bits, timeout);
+  k_theta_tc<<<dim3((s.Nz + kTcLB - 1) / kTcLB, s.Nr), kTcThreads, kTcSmem, st>>>(
+      *static_cast<const CUtensorMap *>(map), W, p, dft, rate_bits, timeout);
 }
 
 }  // namespace tc
