@@ -169,10 +169,12 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               path to ~4e-16 of the largest term).  Needs Ntheta <= 128 and
  *               precision 0 (otherwise the FFT path runs).  0 (default): the
  *               FP64 FFT.  Which one is faster depends on the size (measured
- *               on GB300: 0.38 against 0.41 ms a launch at 64 x 128 x 128 with
- *               temperature, 0.16 against 0.09 ms at 64 x 64 x 64, where most
+ *               on GB300: 0.29 against 0.41 ms a launch at 64 x 128 x 128 with
+ *               temperature, 0.12 against 0.09 ms at 64 x 64 x 64, where most
  *               of the 128 rows of each product are padding); tc_autotune
- *               times both and keeps the faster.
+ *               times both and keeps the faster.  The tile's block of the
+ *               input arrives by a tiled TMA copy; if the driver refuses its
+ *               tensor map at tc_create, the option has no effect.
  *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
  *               never start their shared-memory copies, so each of their
  *               bounded waits runs out (about 1 s) and tc_step returns
