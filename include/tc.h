@@ -176,10 +176,12 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               input arrives by a tiled TMA copy; if the driver refuses its
  *               tensor map at tc_create, the option has no effect.
  *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
- *               never start their shared-memory copies, so each of their
- *               bounded waits runs out (about 1 s) and tc_step returns
- *               TC_ERR_TIMEOUT with the state left invalid.  Exercises the
- *               device-side timeout path without faulting the GPU.
+ *               and the tensor-core azimuthal kernel ("tensor_theta") never
+ *               start their shared-memory copies of factors or DFT slices, so
+ *               each of their bounded waits runs out (about 1 s) and tc_step
+ *               or tc_nonlinear returns TC_ERR_TIMEOUT with its output left
+ *               invalid.  Exercises the device-side timeout path without
+ *               faulting the GPU.
  * Errors: TC_ERR_ARG for an unknown key or out-of-range value. */
 tc_status tc_set_option(tc_ctx *ctx, const char *key, double value);
 
@@ -270,6 +272,8 @@ tc_status tc_diagnostics(tc_ctx *ctx, tc_diag *out);
  *   spectral state given on the device (layout of the state), written to a
  *   device buffer of the same size; *cfl_rate (host, nullable) receives
  *   max(|u_r|/dr, |u_theta|/(r dtheta), |u_z|/dz) over the physical grid.
+ *   TC_ERR_TIMEOUT if a bounded device wait ran out (output invalid; the
+ *   context stays usable).
  * tc_stage_solve: one implicit stage.  rhs (device) holds the explicit
  *   right-hand side in +- form [R+, R-, R_z(, R_T)] at every radial node
  *   (R+- = R_r +- i R_theta); the solution of (I/dt - L/2) X = R - grad p,

@@ -179,7 +179,8 @@ void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long lon
   alignas(64) unsigned char vmap[128];
   if (mode == 0 && !phys_out && c->tensor_theta && c->d_dft_tc && theta_tc_map(vmap, c->V, s)) {
     LaunchScope ls(c, KTHETATC);
-    launch_theta_tc(c->stream, vmap, c->W, p, c->d_dft_tc, rate_bits, &c->scal->timeout);
+    launch_theta_tc(c->stream, vmap, c->W, p, c->d_dft_tc, rate_bits, &c->scal->timeout,
+                    !c->selftest_no_copy);
   } else {
     LaunchScope ls(c, KTHETA);
     k_theta<double><<<dim3(nlb, s.Nr), 256, c->smem_theta, c->stream>>>(

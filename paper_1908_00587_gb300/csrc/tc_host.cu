@@ -1138,15 +1138,19 @@ tc_status tc_nonlinear(tc_ctx *c, const void *state_dev, void *n_dev, double *cf
   try {
     unsigned long long *rb = &c->scal->rate_bits;
     unsigned long long z = 0ull;
+    int zero = 0, to = 0;
     ck(cudaMemcpyAsync(rb, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream));
+    ck(cudaMemcpyAsync(&c->scal->timeout, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
     launch_nonlinear(c, static_cast<const double2 *>(state_dev), static_cast<double2 *>(n_dev), rb,
                      0);
     ck(cudaGetLastError());
     unsigned long long bits;
     ck(cudaMemcpyAsync(&bits, rb, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
     ck(cudaMemcpyAsync(rb, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream));
+    ck(cudaMemcpyAsync(&to, &c->scal->timeout, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     ck(cudaStreamSynchronize(c->stream));
     if (cfl_rate) std::memcpy(cfl_rate, &bits, sizeof(double));
+    if (to) return TC_ERR_TIMEOUT;   // a bounded wait of the tensor-core kernel ran out
   } catch (const CudaError &e) {
     return fail_cuda(c, e.e);
   }

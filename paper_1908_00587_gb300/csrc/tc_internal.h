@@ -364,7 +364,10 @@ void setup_theta_tc();
 // Encode the TMA tensor map of V for k_theta_tc into map (128 bytes, 64-byte
 // aligned); false if the driver refuses it (the caller runs k_theta instead).
 bool theta_tc_map(void *map, const double2 *V, const Sizes &s);
+// arm = false (test hook "selftest_no_copy"): the DFT chunk copies never
+// start, so each CTA's first wait runs out and the timeout flag is set.
 void launch_theta_tc(cudaStream_t st, const void *map, double2 *W, const NLParams &p,
-                     const unsigned char *dft, unsigned long long *rate_bits, int *timeout);
+                     const unsigned char *dft, unsigned long long *rate_bits, int *timeout,
+                     bool arm);
 
 }  // namespace tc

@@ -84,3 +84,27 @@ def test_tensor_theta_step_matches_oracle(tc):
     err = max(float(np.sqrt(np.sum(w * np.abs(got[f] - X[f]) ** 2) / np.sum(w * np.abs(X[f]) ** 2)))
               for f in range(X.shape[0]))
     assert err <= 1e-10, err
+
+
+def test_tensor_theta_wait_timeout_is_reported(tc):
+    """The tensor-core kernel waits on its DFT-slice copies with a 1 s bound:
+    with the copies never started (test hook) the waits run out, the CTAs
+    free their tensor memory and return, tc_nonlinear reports TC_ERR_TIMEOUT,
+    and the same context then computes the stage correctly."""
+    wl = CASES[3]
+    run = tc.Run.from_workload(wl)
+    X = dev(random_state(77, run.nf, wl.Nr, run.M, run.K))
+    out = dev(np.zeros(X.shape, dtype=np.complex128))
+    tc.tc_set_option(run.ctx, "tensor_theta", 1)
+    tc.tc_set_option(run.ctx, "selftest_no_copy", 1)
+    with pytest.raises(tc.TCError) as e:
+        tc.tc_nonlinear(run.ctx, X, out)
+    assert e.value.name == "TC_ERR_TIMEOUT"
+    tc.tc_set_option(run.ctx, "selftest_no_copy", 0)
+    tc.tc_nonlinear(run.ctx, X, out)
+    a = out.cpu().numpy()
+    tc.tc_set_option(run.ctx, "tensor_theta", 0)
+    tc.tc_nonlinear(run.ctx, X, out)
+    b = out.cpu().numpy()
+    run.close()
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
