@@ -85,6 +85,7 @@ typedef struct {
   int tile_mb, tile_lb;         /* nonlinear-stage tiles in use (see "tile_mb") */
   int tile_mbf;                 /* m columns per CTA of the forward axial kernel */
   int tensor_theta;             /* 1: the azimuthal stage runs on the tensor cores */
+  int tensor_z;                 /* 1: the inverse axial stage runs on the tensor cores */
 } tc_info;
 
 /* Device time of one kernel accumulated while option "timing" is 1. */
@@ -175,8 +176,19 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               times both and keeps the faster.  The tile's block of the
  *               input arrives by a tiled TMA copy; if the driver refuses its
  *               tensor map at tc_create, the option has no effect.
+ *   "tensor_z"  1: the inverse axial transforms of the FP64 nonlinear stage
+ *               (of the state, of its radial derivative and of its axial
+ *               derivative) run as products of the folded axial DFT matrix
+ *               on the tensor cores, with the same 7-slice split and exact
+ *               integer combination as "tensor_theta": FP64-accurate.  The
+ *               matrix stacks the cosine rows j = 0 .. Nz/2 over the sine rows
+ *               j = 1 .. (Nz-1)/2, and each output v_j, v_(Nz-j) is the exact
+ *               sum of one cosine and one sine row before its rounding.
+ *               Needs Nz <= 128 and precision 0 (otherwise the FFT path
+ *               runs).  0 (default): the FP64 FFT.  tc_autotune times both.
  *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
- *               and the tensor-core azimuthal kernel ("tensor_theta") never
+ *               and the tensor-core transform kernels ("tensor_theta",
+ *               "tensor_z") never
  *               start their shared-memory copies of factors or DFT slices, so
  *               each of their bounded waits runs out (about 1 s) and tc_step
  *               or tc_nonlinear returns TC_ERR_TIMEOUT with its output left
@@ -379,7 +391,9 @@ tc_status tc_measure_fp64_rate(double target_ms, void *stream, double *tflops);
  * device (make it before any stream capture); the address is kept for the
  * life of the process, so do not call this entry point on a device after
  * cudaDeviceReset of that device.  Each call copies its small radial and
- * twiddle tables in from a host buffer of its own on `stream`.  All calls share the array and
+ * twiddle tables (a few tens of KB) in on `stream` from a buffer on its own
+ * host stack; that memory is pageable, so the driver may hold the copy, and
+ * the call, until the work already queued on `stream` is done.  All calls share the array and
  * each call overwrites the previous call's contents (the CFL slot is cleared
  * every call), so calls that overlap on the GPU race: serialise them.  Work
  * runs on `stream` (NULL: default stream); *cfl_rate (host, nullable) as in
@@ -451,10 +465,11 @@ tc_status tc_ensemble_get_mode(const tc_ens *e, int *mode);
  * class): times the nonlinear stage on the context's current state for tile
  * shapes {1, 2, 3, 4, 5, 6, 8} of "tile_mb", then {1, 2, 3, 4, 8} of
  * "tile_lb", then (precision 0, Ntheta <= 128) "tensor_theta" 1 against 0,
- * then {1, 2, 3, 4, 5, 6, 8} of "tile_mbf", keeps the fastest and returns the
- * first two (host, nullable; tc_get_info reports all four).  Results do not
- * depend on the tiles; the tensor-core azimuthal stage changes them only at
- * round-off (see "tensor_theta"). */
+ * then (precision 0, Nz <= 128) "tensor_z" 1 against 0, then
+ * {1, 2, 3, 4, 5, 6, 8} of "tile_mbf", keeps the fastest and returns the
+ * first two (host, nullable; tc_get_info reports all five).  Results do not
+ * depend on the tiles; the tensor-core stages change them only at round-off
+ * (see "tensor_theta", "tensor_z"). */
 tc_status tc_autotune(tc_ctx *ctx, int *tile_mb, int *tile_lb);
 
 /* Kernel launches per tc_ensemble_step step: the kernels one graph replay
