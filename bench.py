@@ -206,22 +206,37 @@ def kernel_flops(name, wl):
     if name == "k_theta_tc":
         # the part of the same stage that runs on the FP64 pipe: the 2 forward
         # complex FFTs and the products per z-row (the inverse transforms run
-        # as BF16 slice products on the tensor cores: theta_tc_tensor_flops)
+        # as BF16 slice products on the tensor cores: tensor_flops)
         return wl.Nr * wl.Nz * (2 * fft_flops(wl.Ntheta) + 30 * wl.Ntheta)
     if name == "k_zinv":
         # 3 fields per component and m column, plus the 9-point d/dr (72 flops/coeff)
         return wl.Nr * nf * NM * (3 * fft_flops(wl.Nz) + 72 * NK)
+    if name == "k_zinv_tc":
+        # the part of the same stage that runs on the FP64 pipe: the 9-point
+        # d/dr (the transforms run as BF16 slice products: tensor_flops)
+        return wl.Nr * nf * NM * 72 * NK
     if name == "k_zfwd":
         return wl.Nr * nf * NM * fft_flops(wl.Nz)
     return None
 
 
-def theta_tc_tensor_flops(wl):
-    """BF16 tensor flops one launch of k_theta_tc issues: per CTA (2 z rows,
-    32 data columns, 128 theta rows, 96 coefficients) the products of DFT
-    slice i with data slices 0..6-i, 28 slice pairs of 128 x 32 x 96."""
-    ctas = wl.Nr * ((wl.Nz + 1) // 2)
+def tensor_flops(name, wl):
+    """BF16 tensor flops one launch of a tensor-core transform kernel issues:
+    per CTA (32 data columns, 128 rows of the DFT matrix, 96 coefficients)
+    the products of matrix slice i with data slices 0..6-i, 28 slice pairs of
+    128 x 32 x 96.  k_theta_tc: a CTA per 2 z rows of a radius; k_zinv_tc: a
+    CTA per 5 m columns of a radius and field."""
+    if name == "k_theta_tc":
+        ctas = wl.Nr * ((wl.Nz + 1) // 2)
+    else:
+        nf = 4 if wl.Ra else 3
+        NM = (wl.Ntheta - 1) // 3 + 1
+        ctas = wl.Nr * nf * ((NM + 4) // 5)
     return ctas * 28 * 2.0 * 128 * 32 * 96
+
+
+# tensor-core kernel -> the FFT kernel of the same stage (same algorithmic count)
+TENSOR_STAGE = {"k_theta_tc": "k_theta", "k_zinv_tc": "k_zinv"}
 
 
 def step_flops(wl):
@@ -331,6 +346,8 @@ def run_gb300(args):
     tiles = (info.tile_mb, info.tile_lb, info.tile_mbf)
     azimuthal = ("tensor cores: DFT-matrix products of 7 BF16 slices (k_theta_tc)"
                  if info.tensor_theta else "FP64 FFT (k_theta)")
+    axial = ("tensor cores: folded DFT-matrix products of 7 BF16 slices (k_zinv_tc)"
+             if info.tensor_z else "FP64 FFT (k_zinv)")
 
     for _ in range(args.warmup):
         run.step(1, wl.dt)                  # the first one also captures the step graph
@@ -425,11 +442,11 @@ def run_gb300(args):
     mixed = int(getattr(wl, "precision", 0))
     dom = max(timing, key=lambda k: timing[k][1])
     nl, ms = timing[dom]
-    tensor_dom = dom == "k_theta_tc"
+    tensor_dom = dom in TENSOR_STAGE
     # algorithmic flops of the dominant kernel's stage (SURVEY-style count:
     # the transforms as FFTs plus the products); for the tensor-core
-    # azimuthal kernel that is the same count as for the FFT kernel k_theta
-    fl = kernel_flops("k_theta" if tensor_dom else dom, wl)
+    # transform kernels that is the same count as for their FFT kernels
+    fl = kernel_flops(TENSOR_STAGE.get(dom, dom), wl)
     fp32_dom = mixed and dom in ("k_theta", "k_zinv", "k_zfwd")
     peak = FP32_PEAK_TFLOPS if fp32_dom else FP64_PEAK_TFLOPS
     roof = {"kernel": dom, "bound": "alu", "unit": "TFLOP/s", "peak": peak,
@@ -445,21 +462,23 @@ def run_gb300(args):
     else:
         roof.update({"achieved": None, "frac": None})
     if tensor_dom:
-        # the azimuthal stage with its inverse transforms on the tensor cores:
-        # achieved is the stage's algorithmic count over the kernel's time,
-        # so frac may exceed 1 (the FP64 FFT kernel k_theta cannot): the FP64
-        # pipe runs only the forward FFTs and the products (fp64_pipe), the
-        # inverse transforms run as BF16 slice products (tensor)
-        tf = theta_tc_tensor_flops(wl)
+        # a stage with its inverse transforms on the tensor cores: achieved is
+        # the stage's algorithmic count over the kernel's time, so frac may
+        # exceed 1 (the FP64 FFT kernels cannot): the FP64 pipe runs only the
+        # rest of the stage (fp64_pipe: forward FFTs and products, or the
+        # d/dr stencil), the inverse transforms run as BF16 slice products
+        # (tensor)
+        tf = tensor_flops(dom, wl)
         bf16 = measured_bf16_peak()
-        f64 = kernel_flops("k_theta_tc", wl)
-        roof["how"] = ("algorithmic flops of the azimuthal stage (FFT count, as for k_theta) over "
-                       "the tensor-core kernel's time; its inverse transforms run on the tensor "
-                       "cores, so the FP64 peak does not cap it")
+        f64 = kernel_flops(dom, wl)
+        roof["how"] = (f"algorithmic flops of the stage (FFT count, as for {TENSOR_STAGE[dom]}) "
+                       "over the tensor-core kernel's time; its inverse transforms run on the "
+                       "tensor cores, so the FP64 peak does not cap it")
         roof["fp64_pipe"] = {
             "flops_per_launch": f64, "achieved_tflops": f64 / (ms / nl * 1e-3) / 1e12,
             "frac": f64 / (ms / nl * 1e-3) / 1e12 / peak,
-            "how": "the flops run on the FP64 pipe (forward FFTs, products) over the kernel's time"}
+            "how": ("the flops run on the FP64 pipe (forward FFTs and products, or the "
+                    "d/dr stencil) over the kernel's time")}
         roof["tensor"] = {"bf16_flops_per_launch": tf,
                           "achieved_tflops": tf / (ms / nl * 1e-3) / 1e12,
                           "peak_tflops": bf16,
@@ -514,6 +533,7 @@ def run_gb300(args):
                                      "parallelism": f"replicas x{world}",
                                      "tiles_mb_lb_mbf": list(tiles),
                                      "azimuthal_transforms": azimuthal,
+                                     "axial_inverse_transforms": axial,
                                      "launch": "one step captured as a CUDA graph, replayed per step",
                                      "stated_error": (
                                          "rel L2 <= 1.3e-11 vs the FP64 path after 50 steps at "

@@ -22,7 +22,7 @@ LIB = os.path.join(PKG, "libtc.so")
 LIB_DEBUG = os.path.join(PKG, "libtc_debug.so")
 
 SOURCES = ["tc_host.cu", "nonlinear.cu", "linear.cu", "diag.cu", "ensemble.cu", "restart.cu",
-           "theta_tc.cu"]
+           "theta_tc.cu", "zinv_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

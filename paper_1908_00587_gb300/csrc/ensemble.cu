@@ -92,6 +92,7 @@ tc_status autotune(tc_ctx *c, int *best_mb, int *best_lb) {
   // searched, so that search sees only the inverse kernel change
   tc_set_option(c, "tile_mbf", (c->precision == 1) ? c->nl32.MBf : c->nl.MBf);
   tc_set_option(c, "tensor_theta", 0);
+  tc_set_option(c, "tensor_z", 0);
   float best = 1e30f;
   int bm = 0;
   for (int mb : cand_mb) {
@@ -119,7 +120,15 @@ tc_status autotune(tc_ctx *c, int *best_mb, int *best_lb) {
   // FFT kernel with the tile just chosen
   if (c->precision == 0 && c->d_dft_tc) {
     tc_set_option(c, "tensor_theta", 1);
-    if (time_nonlinear(c, a, b, 3) >= best) tc_set_option(c, "tensor_theta", 0);
+    const float t = time_nonlinear(c, a, b, 3);
+    if (t >= best) tc_set_option(c, "tensor_theta", 0);
+    else best = t;
+  }
+  // the inverse axial stage on the tensor cores, where it applies, against
+  // the FFT kernel with the choices made so far
+  if (c->precision == 0 && c->d_dft_ztc) {
+    tc_set_option(c, "tensor_z", 1);
+    if (time_nonlinear(c, a, b, 3) >= best) tc_set_option(c, "tensor_z", 0);
   }
   // the forward axial kernel's own width (its grid fills the SMs differently)
   best = 1e30f;
@@ -728,8 +737,8 @@ tc_status tc_ensemble_create(int n, const tc_params *p, int autotune_tiles, tc_e
     tc_set_stream(c, s);
   }
   if (autotune_tiles) {
-    // tuned (tile_mb, tile_lb, tile_mbf, tensor_theta) per size class
-    std::map<ClassKey, std::tuple<int, int, int, int>> tuned;
+    // tuned (tile_mb, tile_lb, tile_mbf, tensor_theta, tensor_z) per size class
+    std::map<ClassKey, std::tuple<int, int, int, int, int>> tuned;
     for (tc_ctx *c : e->m) {
       const ClassKey k = class_of(c);
       auto it = tuned.find(k);
@@ -737,13 +746,14 @@ tc_status tc_ensemble_create(int n, const tc_params *p, int autotune_tiles, tc_e
         int mb = 0, lb = 0;
         tc_status st = autotune(c, &mb, &lb);
         if (st != TC_OK) return fail(st);
-        tuned[k] = std::make_tuple(mb, lb, c->tile_mbf, c->tensor_theta);
+        tuned[k] = std::make_tuple(mb, lb, c->tile_mbf, c->tensor_theta, c->tensor_z);
       } else {
-        const auto [mb, lb, mbf, tt] = it->second;
+        const auto [mb, lb, mbf, tt, tz] = it->second;
         if (mb) tc_set_option(c, "tile_mb", mb);
         if (lb) tc_set_option(c, "tile_lb", lb);
         if (mbf) tc_set_option(c, "tile_mbf", mbf);
         tc_set_option(c, "tensor_theta", tt);
+        tc_set_option(c, "tensor_z", tz);
       }
     }
   }

@@ -171,7 +171,10 @@ void launch_nonlinear(tc_ctx *c, const double2 *X, double2 *N, unsigned long lon
   NLParams p = c->nl;
   p.phys_out = phys_out;
   const int nmb = (s.NM + p.MB - 1) / p.MB;
-  {
+  if (mode == 0 && !phys_out && c->tensor_z && c->d_dft_ztc) {
+    LaunchScope ls(c, KZINVTC);
+    launch_zinv_tc(c->stream, X, c->V, p, c->d_dft_ztc, &c->scal->timeout, !c->selftest_no_copy);
+  } else {
     LaunchScope ls(c, KZINV);
     k_zinv<double><<<dim3(nmb, s.Nr, s.nf), 256, c->smem_zinv, c->stream>>>(X, c->V, p);
   }

@@ -20,7 +20,7 @@ namespace tc {
 const char *const kKernelNames[KNUM] = {
     "k_zinv", "k_theta", "k_zfwd", "k_dt_policy", "k_factor", "k_influence",
     "k_rhs", "k_prhs", "k_psolve", "k_hrhs", "k_hsolve", "k_alpha", "k_correct", "k_diag", "k_check",
-    "k_flux", "k_regrid", "k_adjoint", "k_theta_tc"};
+    "k_flux", "k_regrid", "k_adjoint", "k_theta_tc", "k_zinv_tc"};
 
 LaunchScope::LaunchScope(tc_ctx *c_, int id_) : c(c_), id(id_) {
   c->launches++;
@@ -735,6 +735,13 @@ tc_status tc_create(int Nr, int Ntheta, int Nz, double eta, double Lz, double Re
       ck(cudaMemcpy(c->d_dft_tc, tab.data(), theta_tc_table_bytes(), cudaMemcpyHostToDevice));
       setup_theta_tc();
     }
+    if (zinv_tc_supported(s)) {
+      std::vector<unsigned short> tab;
+      build_zinv_dft(s.Nz, s.K, tab);
+      c->d_dft_ztc = dalloc<unsigned char>(c, zinv_tc_table_bytes());
+      ck(cudaMemcpy(c->d_dft_ztc, tab.data(), zinv_tc_table_bytes(), cudaMemcpyHostToDevice));
+      setup_zinv_tc();
+    }
     if (c->smem_zinv > 227 * 1024 || c->smem_theta > 227 * 1024 || c->smem_zfwd > 227 * 1024 ||
         c->smem32_zinv > 227 * 1024 || c->smem32_theta > 227 * 1024 ||
         c->smem32_zfwd > 227 * 1024) {
@@ -853,6 +860,9 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
   } else if (k == "tensor_theta") {
     if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
     c->tensor_theta = (int)v;
+  } else if (k == "tensor_z") {
+    if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
+    c->tensor_z = (int)v;
   } else if (k == "selftest_no_copy") {
     c->selftest_no_copy = v != 0.0;
   } else if (k == "timing") {
@@ -887,6 +897,7 @@ tc_status tc_get_info(const tc_ctx *c, tc_info *o) {
   o->tile_lb = (c->precision == 1) ? c->nl32.LB : c->nl.LB;
   o->tile_mbf = (c->precision == 1) ? c->nl32.MBf : c->nl.MBf;
   o->tensor_theta = (c->precision == 0 && c->tensor_theta && c->d_dft_tc) ? 1 : 0;
+  o->tensor_z = (c->precision == 0 && c->tensor_z && c->d_dft_ztc) ? 1 : 0;
   return TC_OK;
 }
 

@@ -191,7 +191,7 @@ namespace tc {
 // Kernels with per-launch timing (option "timing").
 enum KernelId {
   KZINV, KTHETA, KZFWD, KDT, KFACTH, KINFL, KRHS, KPRHS, KPOIS, KHRHS, KHELM, KALPHA, KCORR,
-  KDIAG, KCHECK, KFLUX, KREGRID, KADJ, KTHETATC, KNUM
+  KDIAG, KCHECK, KFLUX, KREGRID, KADJ, KTHETATC, KZINVTC, KNUM
 };
 extern const char *const kKernelNames[KNUM];
 
@@ -259,6 +259,11 @@ struct tc_ctx {
   // BF16 slices (device, null when the size is not supported) and the option
   unsigned char *d_dft_tc = nullptr;
   int tensor_theta = 0;
+  // inverse axial transforms on the tensor cores (zinv_tc.cu): the folded
+  // axial DFT matrix's BF16 slices (device, null when not supported) and the
+  // option
+  unsigned char *d_dft_ztc = nullptr;
+  int tensor_z = 0;
   int flux = 0;                 // axial-flux constraint on the (0,0) u_z mode
   double eps_c = 0.0;           // centrifugal buoyancy coefficient
   double *flux_ug = nullptr;    // device (Nr): unit-forcing response of the (0,0) u_z operator
@@ -369,5 +374,17 @@ bool theta_tc_map(void *map, const double2 *V, const Sizes &s);
 void launch_theta_tc(cudaStream_t st, const void *map, double2 *W, const NLParams &p,
                      const unsigned char *dft, unsigned long long *rate_bits, int *timeout,
                      bool arm);
+
+// zinv_tc.cu: the inverse axial transforms of the FP64 nonlinear stage (with
+// the d/dr stencil and the z derivative) as BF16 slice products of the folded
+// axial DFT matrix on the tensor cores (FP64-accurate); writes V as k_zinv
+bool zinv_tc_supported(const Sizes &s);
+size_t zinv_tc_table_bytes();
+void build_zinv_dft(int Nz, int K, std::vector<unsigned short> &out);
+void setup_zinv_tc();
+// arm = false (test hook "selftest_no_copy"): the matrix chunk copies never
+// start, so each CTA's first wait runs out and the timeout flag is set.
+void launch_zinv_tc(cudaStream_t st, const double2 *X, double2 *V, const NLParams &p,
+                    const unsigned char *dft, int *timeout, bool arm);
 
 }  // namespace tc

@@ -48,7 +48,8 @@ class tc_info(ctypes.Structure):
                 ("coeffs_per_field", ctypes.c_longlong), ("state_bytes", ctypes.c_longlong),
                 ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_longlong),
                 ("tile_mb", ctypes.c_int), ("tile_lb", ctypes.c_int),
-                ("tile_mbf", ctypes.c_int), ("tensor_theta", ctypes.c_int)]
+                ("tile_mbf", ctypes.c_int), ("tensor_theta", ctypes.c_int),
+                ("tensor_z", ctypes.c_int)]
 
 
 class tc_params(ctypes.Structure):

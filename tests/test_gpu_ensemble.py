@@ -55,7 +55,7 @@ def test_ensemble_members_match_single_runs_bitwise(tc, mode):
         shapes.append(shape)
         info = tc.tc_get_info(tc.tc_ensemble_member(ens, i))
         assert info.tile_mb >= 1 and info.tile_lb >= 1
-        tensor.append(info.tensor_theta)
+        tensor.append((info.tensor_theta, info.tensor_z))
     tc.tc_ensemble_step(ens, 7, dts)
     tc.tc_ensemble_step(ens, 5, dts)       # the same plan (graph) again
     if mode == 1:
@@ -70,9 +70,10 @@ def test_ensemble_members_match_single_runs_bitwise(tc, mode):
     tc.tc_ensemble_destroy(ens)
     for i, wl in enumerate(members):
         run = tc.Run.from_workload(wl)       # default tiles, plain launches
-        # the azimuthal path the tuner chose for this member's size class
-        # (tiles change nothing; the tensor-core path changes round-off)
-        tc.tc_set_option(run.ctx, "tensor_theta", tensor[i])
+        # the transform paths the tuner chose for this member's size class
+        # (tiles change nothing; the tensor-core paths change round-off)
+        tc.tc_set_option(run.ctx, "tensor_theta", tensor[i][0])
+        tc.tc_set_option(run.ctx, "tensor_z", tensor[i][1])
         dt, _ = _init(tc, run.ctx, wl)
         assert dt == dts[i]
         run.step(12, dt)

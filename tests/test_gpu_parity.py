@@ -227,7 +227,7 @@ def _run_both(tc, wl, nsteps, transform="naive", tuned=False):
         tc.tc_autotune(run.ctx)
         info = tc.tc_get_info(run.ctx)
         print(f"{wl.name}: tuned tiles {info.tile_mb, info.tile_lb, info.tile_mbf}, "
-              f"tensor_theta {info.tensor_theta}")
+              f"tensor_theta {info.tensor_theta}, tensor_z {info.tensor_z}")
     dts = run.step(nsteps, wl.dt)
     got = run.get_state()
     dg = run.diagnostics()
