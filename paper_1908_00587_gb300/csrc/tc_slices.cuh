@@ -29,7 +29,7 @@ constexpr int kTcLev = 7;      // level blocks of kTcN TMEM columns each
 constexpr int kTcKc = 32;      // coefficients per streamed chunk of a DFT-matrix slice
 constexpr int kTcChunks = kTcK / kTcKc;   // 3 per slice
 constexpr int kTcStages = kTcChunks * kTcS;   // 21
-constexpr int kTcRing = 4;     // chunks in flight
+constexpr int kTcRing = 4;     // chunks in flight (the default ring depth)
 // Operand layouts in shared memory (K-major, no swizzle): core matrices of 8
 // rows x 16 bytes (8 BF16), the K-neighbour of a core matrix 128 B further,
 // the next group of 8 rows one K extent further.
@@ -125,24 +125,24 @@ __device__ __forceinline__ unsigned long long ll_to_double_bits(long long v) {
 }
 
 // Thread 0 of a CTA: the kTcStages chunk stages of A's slices through the
-// kTcRing-deep ring in sA, each followed by its MMAs.  bars[b] (b < kTcRing)
-// is the full barrier of ring buffer b, bars[kTcRing + b] its free barrier
-// (signalled when the products that read it are done), bars[2 kTcRing] the
-// done barrier.  load_a(st) starts the copy of chunk st (the first kTcRing
-// were started by the caller).  Stage st = 3 i + ch holds coefficients
+// Ring-deep ring in sA, each followed by its MMAs.  bars[b] (b < Ring) is the
+// full barrier of ring buffer b, bars[Ring + b] its free barrier (signalled
+// when the products that read it are done), bars[2 Ring] the done barrier.
+// load_a(st) starts the copy of chunk st (the first Ring were started by the
+// caller).  Stage st = 3 i + ch holds coefficients
 // 32 ch .. 32 ch + 31 of slice i; its MMAs take B = data slices 0 .. 6 - i
 // (stacked along N) and add into level blocks i .. 6.  consumed counts the
 // chunks waited for.  Returns false if a wait ran out; the done barrier is
 // signalled either way, once the products issued are done.
-template <class LoadA>
+template <int Ring, class LoadA>
 __device__ __forceinline__ bool issue_slice_products(unsigned long long *bars,
                                                      const unsigned char *sA,
                                                      const unsigned char *sB, unsigned tmem,
                                                      int &consumed, LoadA &&load_a) {
   bool ok = true;
   for (int st = 0; st < kTcStages && ok; ++st) {
-    const int i = st / kTcChunks, ch = st - i * kTcChunks, buf = st % kTcRing;
-    if (!tc_wait(smem_u32(&bars[buf]), (unsigned)(st / kTcRing) & 1u)) {
+    const int i = st / kTcChunks, ch = st - i * kTcChunks, buf = st % Ring;
+    if (!tc_wait(smem_u32(&bars[buf]), (unsigned)(st / Ring) & 1u)) {
       ok = false;
       break;
     }
@@ -168,20 +168,20 @@ __device__ __forceinline__ bool issue_slice_products(unsigned long long *bars,
           :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(en) : "memory");
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 :: "r"(smem_u32(&bars[kTcRing + buf])) : "memory");
+                 :: "r"(smem_u32(&bars[Ring + buf])) : "memory");
     // refill the buffer of the previous stage once its products are done
-    if (st >= 1 && st - 1 + kTcRing < kTcStages) {
-      const int pb = (st - 1) % kTcRing;
-      if (!tc_wait(smem_u32(&bars[kTcRing + pb]), (unsigned)((st - 1) / kTcRing) & 1u)) {
+    if (st >= 1 && st - 1 + Ring < kTcStages) {
+      const int pb = (st - 1) % Ring;
+      if (!tc_wait(smem_u32(&bars[Ring + pb]), (unsigned)((st - 1) / Ring) & 1u)) {
         ok = false;
         break;
       }
-      load_a(st - 1 + kTcRing);
+      load_a(st - 1 + Ring);
     }
   }
   // the done barrier is signalled either way, once the products issued are done
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-               :: "r"(smem_u32(&bars[2 * kTcRing])) : "memory");
+               :: "r"(smem_u32(&bars[2 * Ring])) : "memory");
   return ok;
 }
 

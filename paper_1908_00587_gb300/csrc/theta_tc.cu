@@ -58,7 +58,9 @@ namespace {
 
 constexpr int kTcLB = 2;       // z rows per CTA
 constexpr int kTcThreads = 256;
-// + 128 bytes to align the base for the tiled TMA copy: 75904, three CTAs per SM
+// + 128 bytes to align the base for the tiled TMA copy: 75904, three CTAs per
+// SM.  (A ring of 8 chunks, two CTAs per SM, was slower: 0.360 against 0.291
+// ms a launch at 64 x 128 x 128 with temperature.)
 constexpr int kTcSmem = kTcBBytes + kTcRing * kTcAChunk + 128;
 
 __global__ void __launch_bounds__(kTcThreads, 3)
@@ -208,7 +210,7 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
 
   // 2. the slice products (thread 0 issues them)
   if (tid == 0) {
-    if (!issue_slice_products(bars, sA, sB, tmem, consumed, load_a)) abort_s = 1;
+    if (!issue_slice_products<kTcRing>(bars, sA, sB, tmem, consumed, load_a)) abort_s = 1;
   }
   __syncthreads();
   // the same verdict in every thread

@@ -22,8 +22,10 @@
 // and one sine row (both in units of 2^(E-56), E the exponent of the complex
 // column), rounded once to FP64.
 //
-// Data path of one CTA (5 m columns of one radius and field: 30 real data
-// columns, 2 of the 32 left zero):
+// Data path of one CTA (5 consecutive (r, c, m) columns, m fastest: 30 real
+// data columns, 2 of the 32 left zero; numbering the columns across radii
+// and fields, rather than tiling each (r, c) plane, makes the tiles fill the
+// GPU's CTA slots in nearly whole waves):
 //   1. all threads: the value, the d/dr stencil (FP64, the same arithmetic
 //      as k_zinv) and i beta a of each coefficient, staged as FP64 over data
 //      slices 3..6; then 8 threads per data column slice it into the 7 BF16
@@ -50,9 +52,11 @@
 namespace tc {
 namespace {
 
-constexpr int kZtcMB = 5;        // m columns per CTA: 5 x 3 complex = 30 real data columns
+constexpr int kZtcMB = 5;        // columns per CTA: 5 x 3 complex = 30 real data columns
 constexpr int kZtcThreads = 256;
-// + 128 bytes to align the operand base: 75904, three CTAs per SM
+// + 128 bytes to align the operand base: 75904, three CTAs per SM (two of
+// them holding tensor memory at a time).  A ring of 8 chunks, two CTAs per
+// SM, was slower: 0.161 against 0.131 ms a launch at 64 x 128 x 128 with T.
 constexpr int kZtcSmem = kTcBBytes + kTcRing * kTcAChunk + 128;
 static_assert(6 * kZtcMB <= kTcN, "data columns of a tile");
 static_assert(kTcN * kTcK * 8 <= 4 * kTcBSlice, "FP64 staging fits data slices 3..6");
@@ -76,10 +80,9 @@ __global__ void __launch_bounds__(kZtcThreads, 3)
 k_zinv_tc(const double2 *__restrict__ X, double2 *__restrict__ Vout, NLParams p,
           const unsigned char *__restrict__ dft, int *__restrict__ timeout, int arm) {
   const Sizes &s = p.sz;
-  const int m0 = blockIdx.x * kZtcMB;
-  const int nm = min(kZtcMB, s.NM - m0);
-  const int r = blockIdx.y;
-  const int c = blockIdx.z;
+  // columns g = (r nf + c) NM + m, kZtcMB of them per CTA
+  const int g0 = blockIdx.x * kZtcMB;
+  const int nm = min(kZtcMB, s.Nr * s.nf * s.NM - g0);
   const int Nz = s.Nz, NK = s.NK;
   const int h = Nz >> 1;          // cosine rows j = 0 .. h
   const int hq = (Nz - 1) >> 1;   // sine rows j = 1 .. hq, at lane h + j
@@ -91,8 +94,16 @@ k_zinv_tc(const double2 *__restrict__ X, double2 *__restrict__ Vout, NLParams p,
   __shared__ unsigned tmem_s;
   __shared__ int colE[kTcN / 2];
   __shared__ int abort_s;
+  __shared__ int colm[kZtcMB], colr[kZtcMB], colc[kZtcMB];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
+  if (tid < nm) {
+    const int g = g0 + tid;
+    const int rc = fdiv(g, p.fNM);
+    colm[tid] = g - rc * s.NM;
+    colr[tid] = rc / s.nf;
+    colc[tid] = rc - (rc / s.nf) * s.nf;
+  }
   if (tid == 0) {
     abort_s = 0;
     for (int i = 0; i < 2 * kTcRing + 1; ++i)
@@ -124,16 +135,15 @@ k_zinv_tc(const double2 *__restrict__ X, double2 *__restrict__ Vout, NLParams p,
   // d = 0 value, 1 d/dr, 2 d/dz; kk the stored axial index
   double *Xs = reinterpret_cast<double *>(sB + 3 * kTcBSlice);
   {
-    const int st = p.rad.s0[r];
-    double d1[kStencil];
-#pragma unroll
-    for (int q = 0; q < kStencil; ++q) d1[q] = p.rad.D1[r * kStencil + q];
-    const double2 *Xc = X + (long long)c * s.S;
-    const long long nX = (long long)(s.nf - c) * s.S;   // entries of X from Xc on
     for (int t = tid; t < nm * NK; t += blockDim.x) {
       const int mi = fdiv(t, p.fNK);
       const int kk = t - mi * NK;
-      const long long col = (long long)(m0 + mi) * NK + kk;
+      const int r = colr[mi], c = colc[mi];
+      const int st = p.rad.s0[r];
+      const double *d1 = p.rad.D1 + r * kStencil;
+      const double2 *Xc = X + (long long)c * s.S;
+      const long long nX = (long long)(s.nf - c) * s.S;   // entries of X from Xc on
+      const long long col = (long long)colm[mi] * NK + kk;
       double2 val = {0.0, 0.0}, dr = {0.0, 0.0};
 #pragma unroll
       for (int q = 0; q < kStencil; ++q) {
@@ -208,7 +218,7 @@ k_zinv_tc(const double2 *__restrict__ X, double2 *__restrict__ Vout, NLParams p,
 
   // 2. the slice products (thread 0 issues them)
   if (tid == 0) {
-    if (!issue_slice_products(bars, sA, sB, tmem, consumed, load_a)) abort_s = 1;
+    if (!issue_slice_products<kTcRing>(bars, sA, sB, tmem, consumed, load_a)) abort_s = 1;
   }
   __syncthreads();
   // the same verdict in every thread
@@ -261,7 +271,8 @@ k_zinv_tc(const double2 *__restrict__ X, double2 *__restrict__ Vout, NLParams p,
       Qi = Ib[(n + 1) * kTcM + h + j];
     }
     const int e = colE[n >> 1] - 56;
-    const long long io = (((long long)(3 * c + d) * s.Nr + r) * Nz + j) * s.NM + m0 + mi;
+    const long long io =
+        (((long long)(3 * colc[mi] + d) * s.Nr + colr[mi]) * Nz + j) * s.NM + colm[mi];
     if (dbg_in(io, vsz, DBG_ZINV_V))
       Vout[io] = double2{scaled_int_to_double(Pr - Qi, e), scaled_int_to_double(Pi + Qr, e)};
     if (mirror) {
@@ -303,8 +314,9 @@ void setup_zinv_tc() { allow_smem(k_zinv_tc); }
 void launch_zinv_tc(cudaStream_t st, const double2 *X, double2 *V, const NLParams &p,
                     const unsigned char *dft, int *timeout, bool arm) {
   const Sizes &s = p.sz;
-  k_zinv_tc<<<dim3((s.NM + kZtcMB - 1) / kZtcMB, s.Nr, s.nf), kZtcThreads, kZtcSmem, st>>>(
-      X, V, p, dft, timeout, arm ? 1 : 0);
+  const int ncol = s.Nr * s.nf * s.NM;
+  k_zinv_tc<<<(ncol + kZtcMB - 1) / kZtcMB, kZtcThreads, kZtcSmem, st>>>(X, V, p, dft, timeout,
+                                                                          arm ? 1 : 0);
 }
 
 }  // namespace tc
