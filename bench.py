@@ -56,6 +56,10 @@ def parse():
                     help="skip the differentiation-form measurement")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="benchmark the batched form: N uneven runs replayed as one graph")
+    ap.add_argument("--config", default=None,
+                    help="MB,LB,MBF,TT,TZ: fixed nonlinear-stage tiles and tensor-core paths "
+                         "(tensor_theta, tensor_z) instead of the autotuner's choice, so that "
+                         "a profiler run launches the same kernels as the timed one")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the mixed-precision and ensemble forms (N = 1 only)")
     return ap.parse_args()
@@ -341,7 +345,13 @@ def run_gb300(args):
     tco = temperature_coefficients(wl.seed, wl.mp, wl.kp) if wl.Ra else None
     run.init_perturbation(psi, wl.amp, tco, wl.amp_T)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    tc.tc_autotune(run.ctx)                 # tile shapes of the nonlinear stage
+    if args.config:                         # a fixed configuration (profiler runs)
+        mb, lb, mbf, tt, tz = (int(v) for v in args.config.split(","))
+        for key, val in (("tile_mb", mb), ("tile_lb", lb), ("tile_mbf", mbf),
+                         ("tensor_theta", tt), ("tensor_z", tz)):
+            tc.tc_set_option(run.ctx, key, val)
+    else:
+        tc.tc_autotune(run.ctx)             # tile shapes of the nonlinear stage
     info = tc.tc_get_info(run.ctx)
     tiles = (info.tile_mb, info.tile_lb, info.tile_mbf)
     azimuthal = ("tensor cores: DFT-matrix products of 7 BF16 slices (k_theta_tc)"
