@@ -110,6 +110,43 @@ __device__ __forceinline__ void slice_value(double x, int E, unsigned out[kTcS])
   out[0] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(hi, 0x4B40u, 0x5432)), sg, c0));
 }
 
+// |x| = mag 2^eu with mag < 2^53 an integer (finite x): the significand and
+// the exponent of its last place.
+__device__ __forceinline__ unsigned long long mag_of(double x, int &eu) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int be = (int)((b >> 52) & 0x7FF);
+  unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  if (be) mant |= 1ull << 52;
+  eu = max(be, 1) - 1075;
+  return mant;
+}
+
+// round(mag 2^(eu + 56 - E)) for mag < 2^62 and mag 2^eu < 2^E (ties away
+// from zero): the value's 56-bit magnitude in units of 2^(E - 56).
+__device__ __forceinline__ unsigned long long scaled_int(unsigned long long mag, int eu, int E) {
+  const int sh = eu + 56 - E;
+  if (sh >= 0) return mag << sh;             // < 2^56 since mag 2^eu < 2^E
+  const int rs = -sh;
+  if (rs >= 63) return 0ull;                 // mag + 2^(rs-1) < 2^rs
+  return (mag + (1ull << (rs - 1))) >> rs;
+}
+
+// The 7 slices of the value with 56-bit magnitude q (units of 2^(E - 56))
+// and sign neg, as slice_value forms them.
+__device__ __forceinline__ void slice_int(unsigned long long q, bool neg, unsigned out[kTcS]) {
+  const unsigned long long t = q + 0x0080808080808080ull;
+  const unsigned lo = (unsigned)t, hi = (unsigned)(t >> 32);
+  const float sg = neg ? -1.0f : 1.0f;
+  const float c0 = -12583040.0f * sg;        // -(1.5 2^23 + 128)
+#pragma unroll
+  for (int b = 0; b < 4; ++b)   // bytes 0..3 -> slices 6..3
+    out[kTcS - 1 - b] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(lo, 0x4B40u, 0x5460 | b)), sg, c0));
+#pragma unroll
+  for (int b = 0; b < 2; ++b)   // bytes 4, 5 -> slices 2, 1
+    out[2 - b] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(hi, 0x4B40u, 0x5460 | b)), sg, c0));
+  out[0] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(hi, 0x4B40u, 0x5432)), sg, c0));
+}
+
 // Nearest double to a 64-bit integer, as bits (round to nearest even).
 __device__ __forceinline__ unsigned long long ll_to_double_bits(long long v) {
   if (v == 0) return 0ull;

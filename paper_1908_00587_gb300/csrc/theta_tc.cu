@@ -43,6 +43,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -136,6 +137,12 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
   // h = 0 Re a_m, h = 1 Im a_m (Im a_0 taken as 0, as the real inverse FFT
   // does); the thread holds m = 16 g + 2 s8 + {0, 1}, g = 0..2, so that one
   // group g is four adjacent coefficients (one 8-byte store per slice).
+  // Each coefficient is held as sign, integer magnitude and the exponent of
+  // its last place.  The theta derivative's coefficients i m a_m =
+  // (-m Im a_m, m Re a_m) are formed there exactly (the 53-bit significand
+  // times m in 64-bit integers, one rounding at the split): no FP64
+  // instruction, which in a warp where one column in four takes the
+  // derivative would cost the whole warp's turn on the FP64 unit.
   const long long fs = (long long)s.Nr * s.Nz * s.NM;
   // the V block, waited for by every thread (the same verdict in all)
   if (!__syncthreads_and(tc_wait(vbar, 0u))) {
@@ -154,6 +161,15 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
     const int d = q <= 1 ? 0 : q - 1;
     const int base = ((3 * c + d) * 2 + li) * s.NM;   // in the V block
     double2 a[6];
+    int et = INT_MIN;   // largest exponent of a leading bit in the column part
+    // the data pair of coefficient u: (Re a, Im a), or (-m Im a, m Re a) for
+    // the derivative, as magnitudes mag 2^eu (times m) and signs
+    auto pair = [&](int u, int h, int &e, bool &neg) -> unsigned long long {
+      const int m = 16 * (u >> 1) + 2 * s8 + (u & 1);
+      const double x = (q == 1) == (h == 0) ? a[u].y : a[u].x;
+      neg = (__double_as_longlong(x) < 0) != (q == 1 && h == 0);
+      return mag_of(x, e) * (q == 1 ? (unsigned long long)m : 1ull);
+    };
 #pragma unroll
     for (int u = 0; u < 6; ++u) {   // all loads first
       const int m = 16 * (u >> 1) + 2 * s8 + (u & 1);
@@ -161,29 +177,33 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
       if (col && m <= M && dbg_in(base + m, 6LL * s.nf * s.NM, DBG_THETA_V)) {
         v = Vs[base + m];
         if (m == 0) v.y = 0.0;
-        if (q == 1) v = double2{-(double)m * v.y, (double)m * v.x};   // i m a_m
       }
       a[u] = v;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int e;
+        bool neg;
+        const unsigned long long mg = pair(u, h, e, neg);
+        if (mg) et = max(et, e + 63 - __clzll((long long)mg));
+      }
     }
     __syncthreads();   // the V block is read: the slices may overwrite it
     // exponent of the column: E with max |x| < 2^E (the 8 threads of a column
     // are 8 adjacent lanes)
-    unsigned long long mb = 0ull;
 #pragma unroll
-    for (int u = 0; u < 6; ++u) {
-      mb = max(mb, (unsigned long long)__double_as_longlong(a[u].x) & 0x7FFFFFFFFFFFFFFFull);
-      mb = max(mb, (unsigned long long)__double_as_longlong(a[u].y) & 0x7FFFFFFFFFFFFFFFull);
-    }
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-    const int E = mb ? (int)((mb >> 52) & 0x7FF) - 1022 : 0;   // 2^(e) <= max < 2^(e+1) = 2^E
+    for (int o = 1; o < 8; o <<= 1) et = max(et, __shfl_xor_sync(0xffffffffu, et, o));
+    const int E = et == INT_MIN ? 0 : et + 1;   // 2^et <= max < 2^(et+1) = 2^E
     if (s8 == 0) colE[n] = E;
 #pragma unroll
     for (int g = 0; g < 3; ++g) {
-      const double xv[4] = {a[2 * g].x, a[2 * g].y, a[2 * g + 1].x, a[2 * g + 1].y};
       unsigned f[4][kTcS];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) slice_value(xv[v], E, f[v]);
+      for (int v = 0; v < 4; ++v) {
+        int e;
+        bool neg;
+        const unsigned long long mg = pair(2 * g + (v >> 1), v & 1, e, neg);
+        slice_int(scaled_int(mg, e, E), neg, f[v]);
+      }
       const int k0 = 32 * g + 4 * s8;
 #pragma unroll
       for (int sl = 0; sl < kTcS; ++sl) {

@@ -98,3 +98,47 @@ def test_split_product_matches_exact_dft_product():
         approx = Fraction(I) * Fraction(2) ** (E - 56)           # (F/2) x
         exact = sum(a * v for a, v in zip(row, x))
         assert abs(approx - exact) <= 8 * Fraction(2) ** (E - 56), (trial, float(approx - exact))
+
+
+def mag_of(x):
+    """|x| = mag 2^eu with mag < 2^53 an integer (the kernels' mag_of)."""
+    m, e = math.frexp(abs(x))           # |x| = m 2^e, 0.5 <= m < 1
+    if x == 0:
+        return 0, -1074
+    eu = max(e - 53, -1074)
+    return int(Fraction(abs(x)) / Fraction(2) ** eu), eu
+
+
+def scaled_int(mag, eu, E):
+    """round(mag 2^(eu + 56 - E)), ties away from zero (the kernels' scaled_int)."""
+    sh = eu + 56 - E
+    if sh >= 0:
+        return mag << sh
+    rs = -sh
+    if rs >= 63:
+        return 0
+    return (mag + (1 << (rs - 1))) >> rs
+
+
+def test_derivative_magnitudes_exact_before_the_split():
+    """The theta derivative's coefficients m |x| are formed as the integer
+    significand times m (below 2^59) and rounded once, at the split, to
+    units of 2^(E - 56): the result is round(m |x| 2^(56 - E)) of the exact
+    product, ties away from zero."""
+    rng = random.Random(11)
+    for _ in range(5000):
+        x = rng.uniform(-1, 1) * 10 ** rng.uniform(-300, 300)
+        m = rng.randrange(0, 48)
+        mag, eu = mag_of(x)
+        assert Fraction(mag) * Fraction(2) ** eu == abs(Fraction(x))
+        mm = mag * m
+        assert mm < 2 ** 59
+        if mm == 0:
+            continue
+        top = eu + mm.bit_length() - 1                       # 2^top <= m |x| < 2^(top+1)
+        for E in (top + 1, top + 2, top + 9):                # the column maximum may be larger
+            got = scaled_int(mm, eu, E)
+            exact = m * abs(Fraction(x)) * Fraction(2) ** (56 - E)
+            want = int(exact + Fraction(1, 2))               # ties away from zero (exact >= 0)
+            assert got == want, (x, m, E)
+            assert got < 2 ** 56
