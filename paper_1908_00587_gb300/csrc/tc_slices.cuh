@@ -249,13 +249,12 @@ __device__ __forceinline__ long long levels_to_int(const unsigned (&v)[kTcLev][8
   return I;
 }
 
-// Host: the 7 slices of a kTcM x kTcK matrix y(row, coefficient) with entries
-// in [-1, 1], as BF16 in the A-operand layout, chunk by chunk (slice i,
-// coefficients 32 ch .. 32 ch + 31 at (kTcChunks i + ch) kTcAChunk bytes).
+// Host: the 7 slices of a kTcM x kTcK matrix y[row kTcK + coefficient] with
+// entries in [-1, 1], as BF16 in the A-operand layout, chunk by chunk (slice
+// i, coefficients 32 ch .. 32 ch + 31 at (kTcChunks i + ch) kTcAChunk bytes).
 // Each entry is rounded to a multiple of 2^-56 and cut into balanced base-256
 // digits, the top one in [-256, 256].
-template <class Entry>
-void pack_dft_slices(Entry &&y, std::vector<unsigned short> &out) {
+inline void pack_dft_slices(const std::vector<long double> &y, std::vector<unsigned short> &out) {
   out.assign((size_t)kTcStages * kTcAChunk / 2, 0);
   auto bf16 = [](int d) -> unsigned short {   // an integer of at most 8 significant bits
     if (d == 0) return 0;
@@ -268,7 +267,7 @@ void pack_dft_slices(Entry &&y, std::vector<unsigned short> &out) {
   };
   for (int j = 0; j < kTcM; ++j)
     for (int k = 0; k < kTcK; ++k) {
-      long long Y = std::llround(std::ldexp((long double)y(j, k), 56));   // round(y 2^56)
+      long long Y = std::llround(std::ldexp(y[(size_t)j * kTcK + k], 56));   // round(y 2^56)
       int dig[kTcS];
       for (int sl = kTcS - 1; sl >= 1; --sl) {
         int lo = (int)(Y & 255ll);

@@ -164,9 +164,9 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
     int et = INT_MIN;   // largest exponent of a leading bit in the column part
     // the data pair of coefficient u: (Re a, Im a), or (-m Im a, m Re a) for
     // the derivative, as magnitudes mag 2^eu (times m) and signs
-    auto pair = [&](int u, int h, int &e, bool &neg) -> unsigned long long {
+    auto pair = [&](const double2 &au, int u, int h, int &e, bool &neg) -> unsigned long long {
       const int m = 16 * (u >> 1) + 2 * s8 + (u & 1);
-      const double x = (q == 1) == (h == 0) ? a[u].y : a[u].x;
+      const double x = (q == 1) == (h == 0) ? au.y : au.x;
       neg = (__double_as_longlong(x) < 0) != (q == 1 && h == 0);
       return mag_of(x, e) * (q == 1 ? (unsigned long long)m : 1ull);
     };
@@ -183,7 +183,7 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
       for (int h = 0; h < 2; ++h) {
         int e;
         bool neg;
-        const unsigned long long mg = pair(u, h, e, neg);
+        const unsigned long long mg = pair(a[u], u, h, e, neg);
         if (mg) et = max(et, e + 63 - __clzll((long long)mg));
       }
     }
@@ -201,7 +201,7 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
       for (int v = 0; v < 4; ++v) {
         int e;
         bool neg;
-        const unsigned long long mg = pair(2 * g + (v >> 1), v & 1, e, neg);
+        const unsigned long long mg = pair(a[2 * g + (v >> 1)], 2 * g + (v >> 1), v & 1, e, neg);
         slice_int(scaled_int(mg, e, E), neg, f[v]);
       }
       const int k0 = 32 * g + 4 * s8;
@@ -366,15 +366,21 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
 // bytes).
 void build_theta_dft(int Nt, int Mm, std::vector<unsigned short> &out) {
   const long double pi = 3.141592653589793238462643383279502884L;
-  pack_dft_slices(
-      [&](int j, int k) -> long double {
-        const int m = k >> 1, h = k & 1;   // column k = 2 m + h
-        if (j >= Nt || m > Mm) return 0.0L;
-        if (m == 0) return h ? 0.0L : 0.5L;
+  std::vector<long double> y((size_t)kTcM * kTcK, 0.0L);
+  for (int j = 0; j < kTcM && j < Nt; ++j)
+    for (int k = 0; k < kTcK; ++k) {
+      const int m = k >> 1, h = k & 1;   // column k = 2 m + h
+      if (m > Mm) continue;
+      long double v;
+      if (m == 0) {
+        v = h ? 0.0L : 0.5L;
+      } else {
         const long double ang = 2.0L * pi * (long double)((long long)m * j % Nt) / Nt;
-        return h ? -std::sin(ang) : std::cos(ang);
-      },
-      out);
+        v = h ? -std::sin(ang) : std::cos(ang);
+      }
+      y[(size_t)j * kTcK + k] = v;
+    }
+  pack_dft_slices(y, out);
 }
 
 bool theta_tc_supported(const Sizes &s) {

@@ -292,17 +292,17 @@ k_zinv_tc(const double2 *__restrict__ X, double2 *__restrict__ Vout, NLParams p,
 void build_zinv_dft(int Nz, int K, std::vector<unsigned short> &out) {
   const long double pi = 3.141592653589793238462643383279502884L;
   const int NK = 2 * K + 1, h = Nz / 2;
-  pack_dft_slices(
-      [&](int row, int kk) -> long double {
-        if (row >= Nz || kk >= NK) return 0.0L;
-        const long long k = kk <= K ? kk : kk - NK;
-        const bool sine = row > h;
-        const long long j = sine ? row - h : row;
-        const long long kj = ((k * j) % Nz + Nz) % Nz;   // exact reduction of the angle
-        const long double ang = 2.0L * pi * (long double)kj / Nz;
-        return sine ? std::sin(ang) : std::cos(ang);
-      },
-      out);
+  std::vector<long double> y((size_t)kTcM * kTcK, 0.0L);
+  for (int row = 0; row < Nz && row < kTcM; ++row)
+    for (int kk = 0; kk < NK && kk < kTcK; ++kk) {
+      const long long k = kk <= K ? kk : kk - NK;
+      const bool sine = row > h;
+      const long long j = sine ? row - h : row;
+      const long long kj = ((k * j) % Nz + Nz) % Nz;   // exact reduction of the angle
+      const long double ang = 2.0L * pi * (long double)kj / Nz;
+      y[(size_t)row * kTcK + kk] = sine ? std::sin(ang) : std::cos(ang);
+    }
+  pack_dft_slices(y, out);
 }
 
 bool zinv_tc_supported(const Sizes &s) { return s.Nz <= kTcM && s.NK <= kTcK; }
