@@ -246,7 +246,6 @@ __device__ __forceinline__ void theta_body(const V2<T> *__restrict__ Vin, V2<T> 
   __syncthreads();
   V2<T> *ph = fft_batch<+1>(A, B, p.pt, nl * npair, Ntp, tw, zmid_ok(p.pt, s.M), tile_rot(bx, by));
   V2<T> *out = (ph == A) ? B : A;
-  const double rr = p.rad.r[r];
   T inv_r;
   if constexpr (sizeof(T) == 4) inv_r = p.inv_r32[r];
   else inv_r = p.rad.inv_r[r];
@@ -344,8 +343,8 @@ __device__ __forceinline__ void theta_body(const V2<T> *__restrict__ Vin, V2<T> 
     return;
   }
   // CTA maxima of the bit patterns (integer operations only), then one thread
-  // divides by the spacings: the same rate as the max over points of the
-  // per-point rates, since division by a positive constant is monotone
+  // scales them by the inverse spacings: the max over points of the
+  // per-point rates, since scaling by a positive constant is monotone
   if (rate_bits) {
     for (int o = 16; o > 0; o >>= 1) {
       mr = max(mr, (CflBits)__shfl_xor_sync(0xffffffffu, mr, o));
@@ -360,8 +359,8 @@ __device__ __forceinline__ void theta_body(const V2<T> *__restrict__ Vin, V2<T> 
   }
   __syncthreads();
   if (rate_bits && threadIdx.x == 0) {
-    const double rate = fmax(val(cfl_cta[0]) / p.rad.dr_min[r],
-                             fmax(val(cfl_cta[1]) / (rr * p.dth), val(cfl_cta[2]) / p.dz));
+    const double rate = fmax(val(cfl_cta[0]) * p.cfl_inv[2 * r],
+                             fmax(val(cfl_cta[1]) * p.cfl_inv[2 * r + 1], val(cfl_cta[2]) * p.inv_dz));
     atomic_max_pos(rate_bits, rate);
   }
   V2<T> *scratch = (out == A) ? B : A;

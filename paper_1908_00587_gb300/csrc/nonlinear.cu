@@ -227,7 +227,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte offsets of the pieces inside the scratch array.
 struct NoAllocLayout {
-  size_t r, inv_r, dr, D1, s0, twz, twt, rate, table_end, V, W, end;
+  size_t r, inv_r, dr, cinv, D1, s0, twz, twt, rate, table_end, V, W, end;
 };
 
 NoAllocLayout noalloc_layout(const Sizes &s) {
@@ -236,6 +236,7 @@ NoAllocLayout noalloc_layout(const Sizes &s) {
   L.r = o;      o = align256(o + sizeof(double) * s.Nr);
   L.inv_r = o;  o = align256(o + sizeof(double) * s.Nr);
   L.dr = o;     o = align256(o + sizeof(double) * s.Nr);
+  L.cinv = o;   o = align256(o + sizeof(double) * 2 * s.Nr);
   L.D1 = o;     o = align256(o + sizeof(double) * s.Nr * kStencil);
   L.s0 = o;     o = align256(o + sizeof(int) * s.Nr);
   L.twz = o;    o = align256(o + sizeof(double2) * s.Nz);
@@ -251,7 +252,8 @@ NoAllocLayout noalloc_layout(const Sizes &s) {
 
 // Largest table segment a call can need (host staging block on the stack).
 constexpr size_t kTableMaxBytes =
-    3 * (kNoAllocMaxNr * 8 + 256) + (kNoAllocMaxNr * kStencil * 8 + 256) +
+    3 * (kNoAllocMaxNr * 8 + 256) + (2 * kNoAllocMaxNr * 8 + 256) +
+    (kNoAllocMaxNr * kStencil * 8 + 256) +
     (kNoAllocMaxNr * 4 + 256) + 2 * (kNoAllocMaxN * 16 + 256) + 256;
 
 bool smooth235_na(int n) {
@@ -329,6 +331,7 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
   double *r = reinterpret_cast<double *>(host + L.r);
   double *inv_r = reinterpret_cast<double *>(host + L.inv_r);
   double *drm = reinterpret_cast<double *>(host + L.dr);
+  double *cinv = reinterpret_cast<double *>(host + L.cinv);
   double *D1 = reinterpret_cast<double *>(host + L.D1);
   int *s0 = reinterpret_cast<int *>(host + L.s0);
   for (int j = 0; j < Nr; ++j) {
@@ -344,6 +347,8 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
     const double lo = j > 0 ? r[j] - r[j - 1] : 1e300;
     const double hi = j < Nr - 1 ? r[j + 1] - r[j] : 1e300;
     drm[j] = std::min(lo, hi);
+    cinv[2 * j] = 1.0 / drm[j];
+    cinv[2 * j + 1] = 1.0 / (r[j] * (2.0 * M_PI / Ntheta));
   }
   fill_plan_twiddles(make_plan(Nz), reinterpret_cast<double2 *>(host + L.twz));
   fill_plan_twiddles(make_plan(Ntheta), reinterpret_cast<double2 *>(host + L.twt));
@@ -363,6 +368,8 @@ extern "C" tc_status tc_nonlinear_noalloc(int Nr, int Ntheta, int Nz, double eta
   p.Gr = (Ra != 0.0) ? Ra / Pr : 0.0;
   p.dth = 2.0 * M_PI / s.Nt;
   p.dz = Lz / s.Nz;
+  p.inv_dz = 1.0 / p.dz;
+  p.cfl_inv = reinterpret_cast<const double *>(base + L.cinv);
   p.zscale = 0.5 / ((double)s.Nt * (double)s.Nz);
   p.pz = make_plan(s.Nz);
   p.pt = make_plan(s.Nt);

@@ -393,6 +393,7 @@ void allocate(tc_ctx *c) {
   c->d_Dw = dalloc<double>(c, (size_t)s.Nr * kStencil);
   c->d_tj = dalloc<int>(c, (size_t)s.Nr * kTrans);
   c->d_dr = dalloc<double>(c, s.Nr);
+  c->d_cflinv = dalloc<double>(c, (size_t)2 * s.Nr);
   c->d_wr = dalloc<double>(c, s.Nr);
   c->d_s0 = dalloc<int>(c, s.Nr);
   c->d_twz = dalloc<double2>(c, s.Nz);
@@ -476,6 +477,16 @@ void upload_tables(tc_ctx *c) {
   p.Gr = c->Gr;
   p.dth = 2.0 * M_PI / s.Nt;
   p.dz = c->Lz / s.Nz;
+  p.inv_dz = 1.0 / p.dz;
+  {
+    std::vector<double> ci((size_t)2 * s.Nr);
+    for (int j = 0; j < s.Nr; ++j) {
+      ci[2 * j] = 1.0 / c->dr_min[j];
+      ci[2 * j + 1] = 1.0 / (c->r[j] * p.dth);
+    }
+    ck(cudaMemcpy(c->d_cflinv, ci.data(), ci.size() * sizeof(double), cudaMemcpyHostToDevice));
+    p.cfl_inv = c->d_cflinv;
+  }
   p.zscale = 0.5 / ((double)s.Nt * (double)s.Nz);
   p.pz = make_plan(s.Nz);
   p.pt = make_plan(s.Nt);
@@ -529,6 +540,7 @@ void upload_tables(tc_ctx *c) {
     ck(cudaMemcpy(c->d_kmtab, km.data(), km.size() * sizeof(double), cudaMemcpyHostToDevice));
     l.betak = c->d_kmtab;
     l.mval = c->d_kmtab + s.NK;
+    p.betak = c->d_kmtab;
   }
 }
 

@@ -131,6 +131,13 @@ struct NLParams {
   double alpha;         // 2 pi / Lz
   double Gr;            // Ra / Pr
   double dth, dz;       // grid spacings in theta and z
+  // CFL rate without divisions on the device: [r][2] = 1/dr_min(r),
+  // 1/(r dth), and 1/dz (the one thread per CTA that scales the CTA's maxima
+  // would otherwise run three FP64 divisions, each a chain of FP64
+  // instructions that costs the whole warp's turns)
+  const double *cfl_inv;
+  double inv_dz;
+  const double *betak;  // alpha k per stored axial index (FP64)
   double zscale;        // 1/(2 Ntheta Nz): forward scale with the 1/2 of k_theta's unpacking
   int MB;               // m columns per CTA in k_zinv (and the adjoint z kernels)
   int MBf;              // m columns per CTA in k_zfwd
@@ -233,6 +240,7 @@ struct tc_ctx {
   float *d_f32;          // FP32 tables of NLParams (twiddles, d/dr weights, beta, 1/r)
   float *d_prof32;       // [Nr][2] FP32 mean profiles (mixed form)
   double *d_kmtab;       // LinParams::betak (NK) then mval (NM)
+  double *d_cflinv;      // NLParams::cfl_inv (2 Nr)
   double *LP, *UP, *LH, *UH, *LT, *UT, *infl, *Ainv;
   double *dt_hist;
   int dt_hist_cap = 0;

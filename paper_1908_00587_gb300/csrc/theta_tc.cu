@@ -278,7 +278,6 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
   double2 *scratch = out + 2 * LB * Ntp;
   double2 *tw = scratch + 2 * LB * Ntp;
   load_tw<double>(tw, p.twt, p.twt32, Nt);
-  const double rr = p.rad.r[r];
   const double inv_r = p.rad.inv_r[r];
   unsigned long long mr = 0ull, mt = 0ull, mz = 0ull;
   const bool centrifugal = p.eps_c != 0.0;
@@ -334,8 +333,8 @@ k_theta_tc(const __grid_constant__ CUtensorMap tmV, double2 *__restrict__ W, NLP
   __syncthreads();
   if (rate_bits && tid == 0) {
     auto val = [](unsigned long long b) { return __longlong_as_double((long long)b); };
-    const double rate = fmax(val(cfl_cta[0]) / p.rad.dr_min[r],
-                             fmax(val(cfl_cta[1]) / (rr * p.dth), val(cfl_cta[2]) / p.dz));
+    const double rate = fmax(val(cfl_cta[0]) * p.cfl_inv[2 * r],
+                             fmax(val(cfl_cta[1]) * p.cfl_inv[2 * r + 1], val(cfl_cta[2]) * p.inv_dz));
     atomicMax(rate_bits, (unsigned long long)__double_as_longlong(rate));
   }
   double2 *sp = fft_batch<-1>(out, scratch, p.pt, nl * 2, Ntp, tw, false, tile_rot(blockIdx.x, r));

@@ -153,7 +153,7 @@ k_zinv_tc(const double2 *__restrict__ X, double2 *__restrict__ Vout, NLParams p,
         dr.y += d1[q] * x.y;
         if (st + q == r) val = x;
       }
-      const double beta = p.alpha * kval(kk, s.K, NK);
+      const double beta = p.betak[kk];   // alpha k, as k_zinv forms it
       double *o = Xs + (6 * mi) * kTcK + kk;
       o[0] = val.x;
       o[kTcK] = val.y;
