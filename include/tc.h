@@ -189,6 +189,9 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               against 0.179 ms a launch at 64 x 128 x 128 with
  *               temperature, 0.049 against 0.040 ms at 64 x 64 x 64 (half of
  *               the 128 matrix rows padding); tc_autotune times both.
+ *   "tile_mb_adj"  m columns per CTA of the adjoint's axial kernels, 1 to 8
+ *               (0, the default: the forward kernels' tile, at most 4, that
+ *               lets three CTAs share an SM).  Results do not depend on it.
  *   "selftest_no_copy"  test hook, default 0.  1: the radial-sweep kernels
  *               and the tensor-core transform kernels ("tensor_theta",
  *               "tensor_z") never

@@ -627,7 +627,7 @@ __global__ void k_zfwd_adj(const double2 *__restrict__ Wa, double2 *__restrict__
     const int kk = t % s.NK;
     const int mi = t / s.NK;
     const int pos = spad(kpos(kk, s.K, s.NK, Nz));
-    const double beta = p.alpha * kval(kk, s.K, s.NK);
+    const double beta = p.betak[kk];   // alpha k (FP64 table: no conversion on the FP64 unit)
     const double2 v = res[(3 * mi + 0) * Np + pos];
     const double2 gr = res[(3 * mi + 1) * Np + pos];
     const double2 gz = res[(3 * mi + 2) * Np + pos];
@@ -670,9 +670,13 @@ __global__ void k_drT(const double2 *__restrict__ Gr, double2 *__restrict__ Xb, 
 // The adjoint's azimuthal kernel holds 2 nf + 2 sequences per z-row, so it
 // takes the largest z-row tile not above the forward one that fits.
 // Tiles of the adjoint's nonlinear kernels: the largest not above the forward
-// ones (at most 2 m-columns) whose shared memory lets three CTAs share an SM,
+// ones (at most 4 m-columns) whose shared memory lets three CTAs share an SM,
 // so that small runs still spread over every SM (the forward tiles are tuned
-// for the forward kernels, whose buffers are smaller).
+// for the forward kernels, whose buffers are smaller).  4 m-columns give the
+// axial kernels' first radix-8 pass 3 x 4 x Nz/8 butterflies, whole warps at
+// Nz = 64 (with 2, a warp in two runs half empty, and a warp's FP64
+// instruction costs the same however many lanes are active): the adjoint
+// step at 64^3 1.084 -> 1.054 ms, the recorded one 0.612 -> 0.589 ms.
 static const size_t kAdjSmemPerCta = (size_t)74 * 1024;
 static size_t adj_theta_smem(const Sizes &s, int lb) {
   return (size_t)(2 * lb * (2 * s.nf + 2) * padlen(s.Nt) + s.Nt) * sizeof(double2);
@@ -687,7 +691,8 @@ static int adjoint_lb(const tc_ctx *c) {
   return lb;
 }
 static int adjoint_mb(const tc_ctx *c) {
-  int mb = c->nl.MB < 2 ? c->nl.MB : 2;
+  int mb = c->nl.MB < 4 ? c->nl.MB : 4;
+  if (c->tile_mb_adj > 0) mb = std::min(c->tile_mb_adj, c->sz.NM);
   while (mb > 1 && adj_z_smem(c->sz, mb) > kAdjSmemPerCta) --mb;
   return mb;
 }

@@ -825,6 +825,9 @@ tc_status tc_set_option(tc_ctx *c, const char *key, double v) {
       setup_nonlinear(c);
       return TC_ERR_UNSUPPORTED;
     }
+  } else if (k == "tile_mb_adj") {
+    if (v < 0.0 || v > 8.0 || v != (double)(int)v) return TC_ERR_ARG;
+    c->tile_mb_adj = (int)v;
   } else if (k == "precision") {
     if (v != 0.0 && v != 1.0) return TC_ERR_ARG;
     if (v == 1.0 && c->eps_c != 0.0) return TC_ERR_UNSUPPORTED;

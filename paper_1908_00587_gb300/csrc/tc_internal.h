@@ -262,6 +262,7 @@ struct tc_ctx {
   int timing = 0;
   int capturing = 0;            // a graph is capturing this context's stream
   int tile_mb = 0, tile_lb = 0, tile_mbf = 0;   // nonlinear-stage tile overrides (0: default)
+  int tile_mb_adj = 0;          // m columns per CTA of the adjoint's axial kernels (0: default)
   int n_corr = 1;               // corrector passes per step
   // azimuthal transforms on the tensor cores (theta_tc.cu): the DFT matrix's
   // BF16 slices (device, null when the size is not supported) and the option
