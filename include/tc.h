@@ -170,9 +170,9 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               path to ~4e-16 of the largest term).  Needs Ntheta <= 128 and
  *               precision 0 (otherwise the FFT path runs).  0 (default): the
  *               FP64 FFT.  Which one is faster depends on the size (measured
- *               on GB300: 0.29 against 0.41 ms a launch at 64 x 128 x 128 with
- *               temperature, 0.12 against 0.09 ms at 64 x 64 x 64, where most
- *               of the 128 rows of each product are padding); tc_autotune
+ *               on GB300: 0.235 against 0.41 ms a launch at 64 x 128 x 128
+ *               with temperature, 0.114 against 0.09 ms at 64 x 64 x 64, where
+ *               most of the 128 rows of each product are padding); tc_autotune
  *               times both and keeps the faster.  The tile's block of the
  *               input arrives by a tiled TMA copy; if the driver refuses its
  *               tensor map at tc_create, the option has no effect.
