@@ -423,6 +423,9 @@ void allocate(tc_ctx *c) {
   c->scal = dalloc<DevScalars>(c, 1);
   c->dt_hist_cap = 1024;
   c->dt_hist = dalloc<double>(c, c->dt_hist_cap);
+  ck(cudaHostAlloc(reinterpret_cast<void **>(&c->h_step),
+                   tc_ctx::kPinnedScal + sizeof(double) * tc_ctx::kPinnedHist,
+                   cudaHostAllocDefault));
 }
 
 void upload_tables(tc_ctx *c) {
@@ -786,6 +789,7 @@ tc_status tc_destroy(tc_ctx *c) {
   }
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void *p : c->allocs) cudaFree(p);
+  if (c->h_step) cudaFreeHost(c->h_step);
   for (auto &t : c->timers)
     for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
   delete c;
@@ -1110,14 +1114,22 @@ tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
       for (int n = 0; n < nsteps; ++n) enqueue_step(c, dt_fixed, n);
     }
     ck(cudaGetLastError());
-    std::vector<double> hist(nsteps);
-    ck(cudaMemcpyAsync(hist.data(), c->dt_hist, sizeof(double) * nsteps, cudaMemcpyDeviceToHost,
+    // the step history and the device scalars, into pinned memory when the
+    // history fits (asynchronous copies, one wait)
+    std::vector<double> hist_big;
+    DevScalars sc_big;
+    const bool pinned = nsteps <= tc_ctx::kPinnedHist;
+    if (!pinned) hist_big.resize(nsteps);
+    double *hist = pinned ? reinterpret_cast<double *>(c->h_step + tc_ctx::kPinnedScal)
+                          : hist_big.data();
+    DevScalars *scp = pinned ? reinterpret_cast<DevScalars *>(c->h_step) : &sc_big;
+    ck(cudaMemcpyAsync(hist, c->dt_hist, sizeof(double) * nsteps, cudaMemcpyDeviceToHost,
                        c->stream));
-    DevScalars sc;
-    ck(cudaMemcpyAsync(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    ck(cudaMemcpyAsync(scp, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     ck(cudaStreamSynchronize(c->stream));
+    const DevScalars sc = *scp;
     for (int n = 0; n < nsteps; ++n) c->t += hist[n];
-    if (dt_used) std::memcpy(dt_used, hist.data(), sizeof(double) * nsteps);
+    if (dt_used) std::memcpy(dt_used, hist, sizeof(double) * nsteps);
     if (sc.timeout) return TC_ERR_TIMEOUT;
     if (c->check && sc.nonfinite) return TC_ERR_NONFINITE;
     if (c->cfl_limit > 0.0 && sc.rate_last * sc.dt > c->cfl_limit) return TC_ERR_CFL;

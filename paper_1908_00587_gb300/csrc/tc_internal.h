@@ -241,6 +241,12 @@ struct tc_ctx {
   float *d_prof32;       // [Nr][2] FP32 mean profiles (mixed form)
   double *d_kmtab;       // LinParams::betak (NK) then mval (NM)
   double *d_cflinv;      // NLParams::cfl_inv (2 Nr)
+  // pinned host buffer that tc_step reads the device scalars and the step
+  // history into (kPinnedHist steps; longer calls use pageable memory): the
+  // copies are then asynchronous, and the call waits once for the stream
+  static constexpr int kPinnedHist = 1024;
+  static constexpr size_t kPinnedScal = (sizeof(tc::DevScalars) + 63) / 64 * 64;
+  unsigned char *h_step = nullptr;
   double *LP, *UP, *LH, *UH, *LT, *UT, *infl, *Ainv;
   double *dt_hist;
   int dt_hist_cap = 0;
