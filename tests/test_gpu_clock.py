@@ -112,3 +112,23 @@ def test_host_restart_with_clock_follows_device_run(tc):
     np.testing.assert_allclose(dB, dA, rtol=1e-12, atol=0.0)
     assert abs(t - tA) <= 1e-12 * tA
     assert _rel_l2(X, XA) <= 1e-10
+
+
+def test_long_call_matches_split_calls(tc):
+    """tc_step reads the step history through a pinned buffer of 1024 steps
+    and through pageable memory for longer calls: one call of 1100 dynamic
+    steps and calls of 1000 and 100 give the same steps, clock and state,
+    bit for bit (a tiny grid, so that the steps are quick)."""
+    wl = WORKLOADS["tc_fp64_nr32_n32"].scaled(Nr=12, Ntheta=8, Nz=12, mp=2, kp=2)
+    res = []
+    for split in ((1100,), (1000, 100)):
+        run = tc.Run.from_workload(wl)
+        run.init_perturbation(psi_coefficients(wl.seed, wl.mp, wl.kp), wl.amp)
+        used = np.concatenate([run.step(n, 0.0) for n in split])
+        res.append((used, run.get_clock(), run.get_state()))
+        run.close()
+    assert len(res[0][0]) == 1100
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1][1] == res[1][1][1]
+    assert abs(res[0][1][0] - res[1][1][0]) <= 1e-12 * res[0][1][0]
+    assert np.array_equal(res[0][2], res[1][2])
