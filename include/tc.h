@@ -185,7 +185,7 @@ tc_status tc_destroy(tc_ctx *ctx);
  *               j = 1 .. (Nz-1)/2, and each output v_j, v_(Nz-j) is the exact
  *               sum of one cosine and one sine row before its rounding.
  *               Needs Nz <= 128 and precision 0 (otherwise the FFT path
- *               runs).  0 (default): the FP64 FFT.  Measured on GB300: 0.131
+ *               runs).  0 (default): the FP64 FFT.  Measured on GB300: 0.129
  *               against 0.179 ms a launch at 64 x 128 x 128 with
  *               temperature, 0.049 against 0.040 ms at 64 x 64 x 64 (half of
  *               the 128 matrix rows padding); tc_autotune times both.
