@@ -420,9 +420,15 @@ void allocate(tc_ctx *c) {
   c->Ainv = dalloc<double>(c, (size_t)4 * c->lin.nopP);
   c->diag_part = dalloc<double>(c, (size_t)s.Nr * 7);
   c->diag_out = dalloc<double>(c, 16);
-  c->scal = dalloc<DevScalars>(c, 1);
-  c->dt_hist_cap = 1024;
-  c->dt_hist = dalloc<double>(c, c->dt_hist_cap);
+  {
+    static_assert(sizeof(DevScalars) <= tc_ctx::kPinnedScal, "scalars fit their slot");
+    unsigned char *blk =
+        dalloc<unsigned char>(c, tc_ctx::kPinnedScal + sizeof(double) * tc_ctx::kPinnedHist);
+    c->scal = reinterpret_cast<DevScalars *>(blk);
+    c->dt_hist = reinterpret_cast<double *>(blk + tc_ctx::kPinnedScal);
+    c->dt_hist_cap = tc_ctx::kPinnedHist;
+    c->dt_hist_own = false;
+  }
   ck(cudaHostAlloc(reinterpret_cast<void **>(&c->h_step),
                    tc_ctx::kPinnedScal + sizeof(double) * tc_ctx::kPinnedHist,
                    cudaHostAllocDefault));
@@ -566,8 +572,10 @@ tc_status commit_staged_state(tc_ctx *c) {
     ck(cudaMemsetAsync(base + offsetof(DevScalars, nonfinite), 0, sizeof(int), c->stream));
     launch_state_check(c, c->Xp);
     ck(cudaGetLastError());
-    ck(cudaMemcpyAsync(&sc, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    // the check's verdict through the context's pinned buffer (asynchronous copy)
+    ck(cudaMemcpyAsync(c->h_step, c->scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
     ck(cudaStreamSynchronize(c->stream));
+    std::memcpy(&sc, c->h_step, sizeof(sc));
     if (sc.nonfinite) return TC_ERR_NONFINITE;
     double amax, defect;
     std::memcpy(&amax, &sc.chk_bits[0], sizeof(double));
@@ -937,10 +945,10 @@ tc_status tc_get_state(const tc_ctx *c, void *spec, int where) {
   if (!c || !spec || (where != 0 && where != 1)) return TC_ERR_ARG;
   if (c->poisoned) return TC_ERR_CUDA;
   const size_t bytes = (size_t)16 * c->sz.nf * c->sz.S;
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(spec, c->X, bytes,
-                        where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream);
+  // the copy is ordered after the work queued on the stream; one wait
+  cudaError_t e = cudaMemcpyAsync(spec, c->X, bytes,
+                                  where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                  c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail_cuda(const_cast<tc_ctx *>(c), e);
   return TC_OK;
@@ -949,11 +957,9 @@ tc_status tc_get_state(const tc_ctx *c, void *spec, int where) {
 tc_status tc_get_pressure(const tc_ctx *c, void *spec, int where) {
   if (!c || !spec || (where != 0 && where != 1)) return TC_ERR_ARG;
   if (c->poisoned) return TC_ERR_CUDA;
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(spec, c->P, (size_t)16 * c->sz.S,
-                        where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
-                        c->stream);
+  cudaError_t e = cudaMemcpyAsync(spec, c->P, (size_t)16 * c->sz.S,
+                                  where == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                  c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail_cuda(const_cast<tc_ctx *>(c), e);
   return TC_OK;
@@ -1077,7 +1083,10 @@ tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
   if (nsteps == 0) return TC_OK;
   try {
     if (nsteps > c->dt_hist_cap) {
-      const size_t grow = sizeof(double) * (size_t)(nsteps - c->dt_hist_cap);
+      // device memory added: the difference when the old history is freed,
+      // the whole new one when the old one stays (inside the scalars' block)
+      const size_t grow = sizeof(double) * (size_t)(c->dt_hist_own ? nsteps - c->dt_hist_cap
+                                                                   : nsteps);
       if (over_budget(c, grow)) return TC_ERR_OOM;
       double *h = nullptr;
       if (cudaMalloc(&h, sizeof(double) * nsteps) != cudaSuccess) {
@@ -1085,17 +1094,23 @@ tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
         return TC_ERR_OOM;
       }
       ck(cudaStreamSynchronize(c->stream));   // the old history may still be in use
-      cudaFree(c->dt_hist);
-      for (auto &p : c->allocs)
-        if (p == c->dt_hist) p = h;
+      if (c->dt_hist_own) {
+        cudaFree(c->dt_hist);
+        for (auto &p : c->allocs)
+          if (p == c->dt_hist) p = h;
+      } else {   // the first history lives in the scalars' allocation
+        c->allocs.push_back(h);
+      }
       c->dt_hist = h;
+      c->dt_hist_own = true;
       c->device_bytes += grow;
       c->dt_hist_cap = nsteps;
       ++c->gen;   // the history pointer is a kernel argument
     }
     char *sb = reinterpret_cast<char *>(c->scal);
-    ck(cudaMemsetAsync(sb + offsetof(DevScalars, nonfinite), 0, sizeof(int), c->stream));
-    ck(cudaMemsetAsync(sb + offsetof(DevScalars, hist_pos), 0, sizeof(int), c->stream));
+    static_assert(offsetof(DevScalars, hist_pos) == offsetof(DevScalars, nonfinite) + sizeof(int),
+                  "nonfinite and hist_pos are cleared together");
+    ck(cudaMemsetAsync(sb + offsetof(DevScalars, nonfinite), 0, 2 * sizeof(int), c->stream));
     const double dt_fixed = dt > 0.0 ? dt : 0.0;
     if (c->use_graph && !c->timing) {
       const cudaError_t ge = ensure_step_graph(c, dt_fixed);
@@ -1123,9 +1138,14 @@ tc_status tc_step(tc_ctx *c, int nsteps, double dt, double *dt_used) {
     double *hist = pinned ? reinterpret_cast<double *>(c->h_step + tc_ctx::kPinnedScal)
                           : hist_big.data();
     DevScalars *scp = pinned ? reinterpret_cast<DevScalars *>(c->h_step) : &sc_big;
-    ck(cudaMemcpyAsync(hist, c->dt_hist, sizeof(double) * nsteps, cudaMemcpyDeviceToHost,
-                       c->stream));
-    ck(cudaMemcpyAsync(scp, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    if (pinned && !c->dt_hist_own) {   // scalars and history in one copy
+      ck(cudaMemcpyAsync(c->h_step, c->scal, tc_ctx::kPinnedScal + sizeof(double) * nsteps,
+                         cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      ck(cudaMemcpyAsync(hist, c->dt_hist, sizeof(double) * nsteps, cudaMemcpyDeviceToHost,
+                         c->stream));
+      ck(cudaMemcpyAsync(scp, c->scal, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    }
     ck(cudaStreamSynchronize(c->stream));
     const DevScalars sc = *scp;
     for (int n = 0; n < nsteps; ++n) c->t += hist[n];

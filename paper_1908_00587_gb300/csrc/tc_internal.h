@@ -112,9 +112,10 @@ struct DevScalars {
   double rate_last;     // rate read by the policy
   int refactor;         // 1 when the factors must be rebuilt this step
   int nonfinite;        // set when a solve produced NaN/Inf
+  int hist_pos;         // next slot of the step history of the current tc_step call
+                        // (next to nonfinite: tc_step clears both with one memset)
   int timeout;          // set when a bounded device-side wait gave up
   unsigned long long corr_bits;   // max |X_corr - X_prev| of the last corrector
-  int hist_pos;         // next slot of the step history of the current tc_step call
   // 1 while X, Yb, N1 and P are the last corrector's state, right-hand side,
   // nonlinear term and pressure (k_correct sets it; every entry point that
   // changes one of them outside a step clears it): k_rhs may then take L X
@@ -247,6 +248,11 @@ struct tc_ctx {
   static constexpr int kPinnedHist = 1024;
   static constexpr size_t kPinnedScal = (sizeof(tc::DevScalars) + 63) / 64 * 64;
   unsigned char *h_step = nullptr;
+  // the device scalars and, kPinnedScal bytes after them in the same
+  // allocation, the step history of up to kPinnedHist steps, so that tc_step
+  // reads both with one copy; dt_hist_own: the history outgrew it and has an
+  // allocation of its own
+  bool dt_hist_own = false;
   double *LP, *UP, *LH, *UH, *LT, *UT, *infl, *Ainv;
   double *dt_hist;
   int dt_hist_cap = 0;
