@@ -453,8 +453,8 @@ def run_gb300(args):
     dom = max(timing, key=lambda k: timing[k][1])
     nl, ms = timing[dom]
     tensor_dom = dom in TENSOR_STAGE
-    # algorithmic flops of the dominant kernel's stage (SURVEY-style count:
-    # the transforms as FFTs plus the products); for the tensor-core
+    # algorithmic flops of the dominant kernel's stage (nominal count: the
+    # transforms as 5 n log2 n FFTs plus the products); for the tensor-core
     # transform kernels that is the same count as for their FFT kernels
     fl = kernel_flops(TENSOR_STAGE.get(dom, dom), wl)
     fp32_dom = mixed and dom in ("k_theta", "k_zinv", "k_zfwd")
